@@ -1,0 +1,175 @@
+/*
+ * afqmc.h -- C ABI of the GB300 (sm_103a) phaseless-AFQMC walker step.
+ *
+ * The operation is the batched walker step of phaseless auxiliary-field QMC for
+ * the Hamiltonian of Sec. V, Eq. (1),
+ *     H = sum_ij h_ij c+_i c_j + 1/2 sum_ijkl v_ijkl c+_i c+_j c_l c_k + E0,
+ * with the two-electron tensor given by the modified-Cholesky factorisation of
+ * Sec. V, Eq. (3),  v_ijkl = sum_n L^n_ik L^n*_lj  (Nchol = x_c M vectors; the
+ * paper notes that any 3-index tensor of this form is accepted).  The step
+ * itself (overlap, half-rotated Green's function, force bias, HS propagator,
+ * local energy, phaseless weights, QR) is the algorithm the paper cites for its
+ * AFQMC implementation (Zhang & Krakauer 2003; Motta & Zhang 2018); Table II
+ * gives its dense 3-index costs: O(N M^2) propagation and O(x_c N^2 M^2) energy
+ * per walker.
+ *
+ * Conventions for every entry point
+ *   - Return value: AFQMC_OK (0) or a negative AFQMC_ERR_* code.  No exception
+ *     crosses the ABI.  afqmc_last_error() gives a message for the calling
+ *     thread's last failure.
+ *   - Pointers: any data pointer may be host memory (pageable or pinned) or
+ *     device memory of the current device.  The library tells them apart with
+ *     cudaPointerGetAttributes.  Inputs are copied (caller keeps ownership and
+ *     may free them when the call returns).  Device outputs are written
+ *     asynchronously on `stream`; host outputs are complete when the call
+ *     returns (the call synchronises `stream`).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work of a call is ordered on it.
+ *   - Layouts are row-major and contiguous.  "complex" means interleaved
+ *     (re, im) pairs of doubles, i.e. numpy complex128 / C double _Complex.
+ *   - Handles own their device memory; destroy them with the matching
+ *     afqmc_destroy_* call.  A handle must not be used from two threads at once.
+ */
+#ifndef AFQMC_GB300_H
+#define AFQMC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define AFQMC_OK               0
+#define AFQMC_ERR_BADARG      -1  /* null handle/pointer, bad option value      */
+#define AFQMC_ERR_SHAPE       -2  /* sizes out of the supported range           */
+#define AFQMC_ERR_OOM         -3  /* device allocation failed                   */
+#define AFQMC_ERR_NONFINITE   -4  /* NaN/Inf met in an input or a result        */
+#define AFQMC_ERR_SINGULAR    -5  /* trial/walker overlap is exactly singular   */
+#define AFQMC_ERR_TIMEOUT     -6  /* a bounded device wait gave up              */
+#define AFQMC_ERR_CUDA        -7  /* a CUDA runtime call failed                 */
+#define AFQMC_ERR_UNSUPPORTED -8  /* valid request this build does not handle   */
+
+/* ---- options ----------------------------------------------------------- */
+#define AFQMC_PREC_FP64    0  /* every contraction in FP64 (DFMA)                       */
+#define AFQMC_PREC_BF16X3  1  /* contractions on tcgen05 tensor cores, each operand split
+                                 into bf16 hi + lo, three products, FP32 accumulation;
+                                 LU/inverse/log-det, QR and reductions stay FP64        */
+
+#define AFQMC_WEIGHT_PHASELESS 0  /* w <- w |I| max(0, cos dtheta)  (hybrid form)        */
+#define AFQMC_WEIGHT_FREE      1  /* free projection: complex weights, no cap, no cos   */
+
+typedef struct afqmc_opts {
+    int    precision;    /* AFQMC_PREC_*                                           */
+    int    k_taylor;     /* order K of the Taylor series for exp(i sqrt(tau) A), 1..32 */
+    int    k_qr;         /* re-orthonormalise every k_qr steps (0 = never)         */
+    int    weight_mode;  /* AFQMC_WEIGHT_*                                          */
+    double fb_cap;       /* cap |xbar_n| <= fb_cap per component (<= 0: no cap)    */
+    int    reserved[8];  /* must be zero                                           */
+} afqmc_opts;
+
+/* Fills the defaults: FP64, K = 6, k_qr = 5, phaseless, fb_cap = 1.0. */
+void afqmc_default_opts(afqmc_opts* opts);
+
+typedef struct afqmc_ham*     afqmc_ham_t;
+typedef struct afqmc_walkers* afqmc_wk_t;
+
+/* ---- Hamiltonian (Sec. V, Eqs. (1) and (3)) ----------------------------
+ * h     [M][M]        real symmetric one-body matrix h_ij.
+ * L     [Nchol][M][M] real Cholesky vectors L^n_ik, each symmetric
+ *                     (v_ijkl = sum_n L^n_ik L^n_jl).
+ * E0    constant energy (E_II of Eq. (1)).
+ * Sizes: 1 <= M <= 1024, 1 <= Nchol.
+ * The library keeps FP64 copies of h and L, forms h' = h - 1/2 sum_n L_n L_n^T
+ * and the split-precision copies the tensor-core path needs on first use.
+ * Errors: BADARG (null), SHAPE, NONFINITE (NaN/Inf in h or L), OOM, CUDA. */
+int afqmc_create_hamiltonian(const double* h, const double* L, double E0, int M, int Nchol,
+                             void* stream, afqmc_ham_t* out);
+int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
+
+/* ---- Walker set ---------------------------------------------------------
+ * Psi_up [M][Nup], Psi_dn [M][Ndn]  complex trial orbitals (single determinant
+ *                                   per spin).
+ * W      number of walkers (>= 1).
+ * Phi0   complex [W][M*Nup + M*Ndn] initial walkers (per walker: spin-up M x Nup
+ *        then spin-down M x Ndn, row-major) or NULL to start every walker at the
+ *        trial.
+ * tau    imaginary time step (> 0).
+ * opts   NULL for defaults.
+ * Sets w = 1 and E_T = E_L(trial) (the trial's own mixed energy).
+ * Sizes: 1 <= Nup, Ndn <= min(M, 128).  BF16X3 additionally needs Nup == Ndn,
+ * M % 64 == 0, Nchol % 8 == 0 and a real trial (UNSUPPORTED otherwise).
+ * Errors: BADARG, SHAPE, UNSUPPORTED, SINGULAR (a walker with zero overlap),
+ * NONFINITE, OOM, CUDA. */
+int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn,
+                       int W, const double* Phi0, double tau, const afqmc_opts* opts, void* stream,
+                       afqmc_wk_t* out);
+int afqmc_destroy_walkers(afqmc_wk_t wk);
+
+/* ---- The walker step -----------------------------------------------------
+ * Runs `nsteps` phaseless steps.  Each step, for every walker with w != 0:
+ *   S = Psi^+ Phi, Theta = Phi S^-1, t_n = sum_s Tr(Psi_s^+ L_n Theta_s),
+ *   xbar_n = -i sqrt(tau) t_n (capped), A = sum_n (x_n - xbar_n) L_n,
+ *   Phi' = B T_K(i sqrt(tau) A) B Phi with B = exp(-tau h'/2),
+ *   w <- w |r e^{x.xbar - xbar.xbar/2}| e^{tau (E_T - E0)} max(0, cos arg r),
+ *   r = <Psi|Phi'>/<Psi|Phi>; every k_qr-th step Phi = Q R, Phi <- Q.
+ * x            fields [nsteps][W][Nchol] doubles, or NULL to draw them on the
+ *              device from Philox4x32-10 keyed by `seed` (counter = (n/4, walker,
+ *              global step index, 0), Box-Muller; see afqmc_philox_fields).
+ * measure_every  if > 0, the mixed energy E_mix = sum w E_L / sum w (weights
+ *              and walkers before the step's update) is measured at every step
+ *              s (0-based within this call) with s % measure_every == 0 and
+ *              written to E_mix_trace as complex values
+ *              [ceil(nsteps / measure_every)]; 0 = no measurement.
+ * Errors: BADARG, NONFINITE (NaN/Inf fields or energies), CUDA. */
+int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int measure_every,
+               double* E_mix_trace, void* stream);
+
+/* ---- Mixed-estimator local energy of the current walkers -----------------
+ * E_L  complex [W] local energies <Psi|H|Phi_w>/<Psi|Phi_w>
+ * w    [W] weights (real part only for free projection: see afqmc_get_walkers)
+ * logS complex [W] sum_s log det(Psi_s^+ Phi_s) (imaginary part in (-pi, pi])
+ * E_mix complex scalar sum_w w E_L / sum_w w
+ * Any output may be NULL. */
+int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_mix, void* stream);
+
+/* ---- Adjoint of the local energy and log-overlap -------------------------
+ * For the real loss  ell = sum_w Re(conj(dE_w) E_L,w + conj(dlogS_w) logS_w)
+ * at the current walkers (Phi held fixed), writes
+ *   dPsi_up [M][Nup], dPsi_dn [M][Ndn] complex: d ell/d Re Psi + i d ell/d Im Psi
+ *   dL      [Nchol][M][M] real: d ell / d L^n_ik over the full (unsymmetrised)
+ *           tensor.
+ * dE, dlogS complex [W]; either may be NULL (treated as zero).  Theta is
+ * recomputed, never stored.  Outputs may be NULL to skip them.
+ * Computed in FP64 whatever the walker set's precision. */
+int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, double* dPsi_up,
+                          double* dPsi_dn, double* dL, void* stream);
+
+/* ---- Walker state (checkpoint / resume and inspection) -------------------
+ * Phi  complex [W][M*Nup + M*Ndn] (layout of Phi0), w [W] (complex [W] for
+ * free projection), step = global step counter (drives the Philox counter).
+ * afqmc_set_walkers restores a state saved by afqmc_get_walkers; a resumed run
+ * with the same seed reproduces the uninterrupted one. */
+int afqmc_get_walkers(afqmc_wk_t wk, double* Phi, double* w, int64_t* step, void* stream);
+int afqmc_set_walkers(afqmc_wk_t wk, const double* Phi, const double* w, int64_t step, void* stream);
+
+/* ---- Philox fields -------------------------------------------------------
+ * Writes the fields afqmc_step would draw: x [W][Nchol] for global step
+ * `step` and `seed` (device or host pointer).  Counter (n/4, walker, step, 0),
+ * key (seed & 0xffffffff, seed >> 32), Box-Muller on (u1, u2) =
+ * ((a + 0.5) 2^-32, (b + 0.5) 2^-32): x = sqrt(-2 ln u1) (cos, sin)(2 pi u2). */
+int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, void* stream);
+
+/* ---- Diagnostics -----------------------------------------------------------
+ * Device time of the last afqmc_step's energy contraction (ms) and the number
+ * of kernels it launched per step; -1 when unknown. */
+int afqmc_last_step_stats(afqmc_wk_t wk, double* energy_kernel_ms, int* kernels_per_step);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* afqmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFQMC_GB300_H */

@@ -1,0 +1,551 @@
+// C-ABI front end of the AFQMC library: argument validation, host/device pointer
+// handling, handle lifetime, set-up of the rotated Cholesky tensor, one-body
+// propagator and trial energy, and the step loop.  The operations are those of
+// Sec. V (Eqs. (1), (3)) and the phaseless algorithm it cites; see include/afqmc.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "state.cuh"
+
+namespace afqmc {
+
+namespace {
+thread_local std::string g_last_error;
+
+__global__ void cplx_real_part_kernel(const cplx* s, double* d, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = s[i].re;
+}
+
+// out[b][c][r] = in[b][r][c] for `nb` matrices of rows x cols
+template <typename T>
+__global__ void batched_transpose_kernel(const T* in, T* out, int nb, int rows, int cols) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)rows * cols;
+    if (i >= per * nb) return;
+    const int64_t b = i / per, e = i % per;
+    const int r = (int)(e / cols), c = (int)(e % cols);
+    out[b * per + (int64_t)c * rows + r] = in[i];
+}
+
+__global__ void max_abs_imag_kernel(const cplx* p, int64_t n, unsigned* flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && p[i].im != 0.0) atomicOr(flag, 1u);
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+void set_error(int code, const std::string& msg) {
+    (void)code;
+    g_last_error = msg;
+}
+
+int fail(int code, const std::string& msg) {
+    set_error(code, msg);
+    return code;
+}
+
+// true if p is device (or managed) memory
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) return AFQMC_OK;
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return AFQMC_OK;
+}
+
+// Copy device data to a caller pointer; synchronise if the destination is host memory.
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st, bool* needs_sync) {
+    if (!dst || bytes == 0) return AFQMC_OK;
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    if (!is_device_ptr(dst)) *needs_sync = true;
+    return AFQMC_OK;
+}
+
+int read_flags(unsigned* dflags, cudaStream_t st, unsigned* out) {
+    unsigned h = 0;
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(&h, dflags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = h;
+    return AFQMC_OK;
+}
+
+int flags_to_error(unsigned f, const char* where) {
+    if (f & FLAG_TIMEOUT) return fail(AFQMC_ERR_TIMEOUT, std::string(where) + ": a bounded device wait gave up");
+    if (f & FLAG_NONFINITE) return fail(AFQMC_ERR_NONFINITE, std::string(where) + ": NaN/Inf in input or result");
+    if (f & FLAG_SINGULAR) return fail(AFQMC_ERR_SINGULAR, std::string(where) + ": singular overlap matrix");
+    return AFQMC_OK;
+}
+
+}  // namespace afqmc
+
+using namespace afqmc;
+
+extern "C" {
+
+void afqmc_default_opts(afqmc_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = AFQMC_PREC_FP64;
+    o->k_taylor = 6;
+    o->k_qr = 5;
+    o->weight_mode = AFQMC_WEIGHT_PHASELESS;
+    o->fb_cap = 1.0;
+}
+
+const char* afqmc_last_error(void) { return afqmc::g_last_error.c_str(); }
+
+int afqmc_create_hamiltonian(const double* h, const double* L, double E0, int M, int Nchol, void* stream,
+                             afqmc_ham_t* out) {
+    if (!out) return fail(AFQMC_ERR_BADARG, "create_hamiltonian: out is NULL");
+    *out = nullptr;
+    if (!h || !L) return fail(AFQMC_ERR_BADARG, "create_hamiltonian: h or L is NULL");
+    if (M < 1 || M > 1024 || Nchol < 1) return fail(AFQMC_ERR_SHAPE, "create_hamiltonian: need 1 <= M <= 1024, Nchol >= 1");
+    if (!isfinite(E0)) return fail(AFQMC_ERR_NONFINITE, "create_hamiltonian: E0 not finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    afqmc_ham* H = new afqmc_ham();
+    AFQMC_CUDA_TRY(cudaGetDevice(&H->device));
+    H->M = M;
+    H->Nchol = Nchol;
+    H->E0 = E0;
+    const size_t mm = (size_t)M * M;
+    auto cleanup = [&](int rc) {
+        if (H->h) cudaFree(H->h);
+        if (H->L) cudaFree(H->L);
+        if (H->hp) cudaFree(H->hp);
+        if (H->flags) cudaFree(H->flags);
+        delete H;
+        return rc;
+    };
+    if (cudaMalloc(&H->h, mm * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&H->L, mm * Nchol * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&H->hp, mm * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&H->flags, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(AFQMC_ERR_OOM, "create_hamiltonian: device allocation failed"));
+    }
+    int rc = copy_in(H->h, h, mm * sizeof(double), st);
+    if (rc == AFQMC_OK) rc = copy_in(H->L, L, mm * Nchol * sizeof(double), st);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    cudaMemsetAsync(H->flags, 0, sizeof(unsigned), st);
+    check_finite(H->h, (int64_t)mm, H->flags, st);
+    check_finite(H->L, (int64_t)mm * Nchol, H->flags, st);
+    check_symmetric(H->L, M, Nchol, H->flags, st);
+    unsigned f = 0;
+    rc = read_flags(H->flags, st, &f);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    if (f & FLAG_NONFINITE) return cleanup(fail(AFQMC_ERR_NONFINITE, "create_hamiltonian: NaN/Inf in h or L"));
+    if (f & 8u) return cleanup(fail(AFQMC_ERR_UNSUPPORTED, "create_hamiltonian: each L_n must be symmetric"));
+    build_hprime(H->h, H->L, M, Nchol, H->hp, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cleanup(fail(AFQMC_ERR_CUDA, std::string("create_hamiltonian: ") + cudaGetErrorString(e)));
+    *out = H;
+    return AFQMC_OK;
+}
+
+int afqmc_destroy_hamiltonian(afqmc_ham_t H) {
+    if (!H) return fail(AFQMC_ERR_BADARG, "destroy_hamiltonian: NULL handle");
+    if (H->live_walker_sets > 0) return fail(AFQMC_ERR_BADARG, "destroy_hamiltonian: walker sets still use it");
+    cudaFree(H->h);
+    cudaFree(H->L);
+    cudaFree(H->hp);
+    cudaFree(H->flags);
+    delete H;
+    return AFQMC_OK;
+}
+
+static void free_walkers(afqmc_walkers* wk) {
+    fp64_free(wk);
+    tc_free(wk);
+    void* ps[] = {wk->weight, wk->logS_old, wk->logS_new, wk->E_L, wk->xbar, wk->coef,
+                  wk->accept, wk->x, wk->emix, wk->flags};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (wk->ev0) cudaEventDestroy(wk->ev0);
+    if (wk->ev1) cudaEventDestroy(wk->ev1);
+    delete wk;
+}
+
+int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn, int W,
+                       const double* Phi0, double tau, const afqmc_opts* opts, void* stream, afqmc_wk_t* out) {
+    if (!out) return fail(AFQMC_ERR_BADARG, "init_walkers: out is NULL");
+    *out = nullptr;
+    if (!ham || !Psi_up || !Psi_dn) return fail(AFQMC_ERR_BADARG, "init_walkers: NULL handle or trial");
+    afqmc_opts o;
+    afqmc_default_opts(&o);
+    if (opts) o = *opts;
+    const int M = ham->M;
+    if (Nup < 1 || Ndn < 1 || Nup > std::min(M, 128) || Ndn > std::min(M, 128) || W < 1)
+        return fail(AFQMC_ERR_SHAPE, "init_walkers: need 1 <= Nup, Ndn <= min(M, 128) and W >= 1");
+    if (!(tau > 0.0) || !isfinite(tau)) return fail(AFQMC_ERR_BADARG, "init_walkers: tau must be > 0");
+    if (o.k_taylor < 1 || o.k_taylor > 32 || o.k_qr < 0 ||
+        (o.weight_mode != AFQMC_WEIGHT_PHASELESS && o.weight_mode != AFQMC_WEIGHT_FREE) ||
+        (o.precision != AFQMC_PREC_FP64 && o.precision != AFQMC_PREC_BF16X3) || !isfinite(o.fb_cap))
+        return fail(AFQMC_ERR_BADARG, "init_walkers: invalid option value");
+    for (int r : o.reserved)
+        if (r != 0) return fail(AFQMC_ERR_BADARG, "init_walkers: reserved options must be zero");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    AFQMC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != ham->device) return fail(AFQMC_ERR_BADARG, "init_walkers: current device differs from the Hamiltonian's");
+
+    afqmc_walkers* wk = new afqmc_walkers();
+    wk->ham = ham;
+    wk->device = dev;
+    wk->M = M;
+    wk->Nchol = ham->Nchol;
+    wk->N[0] = Nup;
+    wk->N[1] = Ndn;
+    wk->W = W;
+    wk->tau = tau;
+    wk->opts = o;
+    const int nch = ham->Nchol;
+    auto bail = [&](int rc) {
+        free_walkers(wk);
+        return rc;
+    };
+    auto al = [&](void** p, size_t bytes) -> int {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(AFQMC_ERR_OOM, "init_walkers: device allocation failed");
+        }
+        return AFQMC_OK;
+    };
+    int rc = AFQMC_OK;
+    rc = rc ? rc : al((void**)&wk->weight, sizeof(cplx) * W);
+    rc = rc ? rc : al((void**)&wk->logS_old, sizeof(cplx) * W);
+    rc = rc ? rc : al((void**)&wk->logS_new, sizeof(cplx) * W);
+    rc = rc ? rc : al((void**)&wk->E_L, sizeof(cplx) * W);
+    rc = rc ? rc : al((void**)&wk->xbar, sizeof(cplx) * W * nch);
+    rc = rc ? rc : al((void**)&wk->coef, sizeof(cplx) * W * nch);
+    rc = rc ? rc : al((void**)&wk->accept, sizeof(int) * W);
+    rc = rc ? rc : al((void**)&wk->x, sizeof(double) * W * nch);
+    rc = rc ? rc : al((void**)&wk->emix, sizeof(cplx) * 64);
+    rc = rc ? rc : al((void**)&wk->flags, 2 * sizeof(unsigned));
+    if (rc) return bail(rc);
+    wk->x_cap = 1;
+    wk->emix_cap = 64;
+    rc = fp64_alloc(wk);
+    if (rc) return bail(rc);
+    cudaEventCreate(&wk->ev0);
+    cudaEventCreate(&wk->ev1);
+
+    Fp64Buffers& f = wk->f;
+    const double* psis[2] = {Psi_up, Psi_dn};
+    // flags[0]: latched status bits; flags[1]: scratch word (imaginary part of the trial)
+    cudaMemsetAsync(wk->flags, 0, 2 * sizeof(unsigned), st);
+    for (int s = 0; s < 2; ++s) {
+        rc = copy_in(f.Psi[s], psis[s], sizeof(cplx) * M * wk->N[s], st);
+        if (rc) return bail(rc);
+        check_finite(reinterpret_cast<const double*>(f.Psi[s]), 2LL * M * wk->N[s], wk->flags, st);
+        max_abs_imag_kernel<<<nblk((int64_t)M * wk->N[s]), 256, 0, st>>>(f.Psi[s], (int64_t)M * wk->N[s],
+                                                                          wk->flags + 1);
+    }
+    {
+        unsigned fl[2] = {0, 0};
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(fl, wk->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (fl[0] & FLAG_NONFINITE) return bail(fail(AFQMC_ERR_NONFINITE, "init_walkers: NaN/Inf in the trial"));
+        wk->trial_real = fl[1] == 0;
+    }
+    if (o.precision == AFQMC_PREC_BF16X3) {
+        if (!wk->trial_real || Nup != Ndn || M % 64 != 0 || nch % 8 != 0)
+            return bail(fail(AFQMC_ERR_UNSUPPORTED,
+                             "init_walkers: BF16X3 needs a real trial, Nup == Ndn, M % 64 == 0, Nchol % 8 == 0"));
+    }
+    // rotated Cholesky tensor, its transpose, rotated one-body matrix
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        cplx* tmp = nullptr;
+        if (cudaMallocAsync(&tmp, sizeof(cplx) * (size_t)nch * N * M, st) != cudaSuccess)
+            return bail(fail(AFQMC_ERR_OOM, "init_walkers: workspace"));
+        GemmArgs g;   // tmp[n] = Psi^+ L_n   [N][M]
+        g.m = N; g.n = M; g.k = M; g.nb1 = nch;
+        g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = N;
+        g.B.ptr = ham->L; g.B.real = true; g.B.ld = M; g.B.s1 = (int64_t)M * M;
+        g.C = tmp; g.ldc = M; g.sc1 = (int64_t)N * M;
+        zgemm(g, st);
+        const int64_t tot = (int64_t)nch * N * M;
+        if (wk->trial_real) {
+            double* Lr = static_cast<double*>(f.Lt[s]);
+            cplx_real_part_kernel<<<nblk(tot), 256, 0, st>>>(tmp, Lr, tot);
+            batched_transpose_kernel<double><<<nblk(tot), 256, 0, st>>>(Lr, static_cast<double*>(f.LtT[s]), nch, N, M);
+        } else {
+            cudaMemcpyAsync(f.Lt[s], tmp, sizeof(cplx) * tot, cudaMemcpyDeviceToDevice, st);
+            batched_transpose_kernel<cplx><<<nblk(tot), 256, 0, st>>>(tmp, static_cast<cplx*>(f.LtT[s]), nch, N, M);
+        }
+        GemmArgs gh;  // ht = Psi^+ h   [N][M]
+        gh.m = N; gh.n = M; gh.k = M;
+        gh.A.ptr = f.Psi[s]; gh.A.op = OP_C; gh.A.ld = N;
+        gh.B.ptr = ham->h; gh.B.real = true; gh.B.ld = M;
+        gh.C = f.ht[s]; gh.ldc = M;
+        zgemm(gh, st);
+        cudaFreeAsync(tmp, st);
+    }
+    rc = expm_real(ham->hp, -0.5 * tau, M, f.Bh, st);
+    if (rc) return bail(rc);
+    // trial energy E_T from walker 0 placed at the trial
+    for (int s = 0; s < 2; ++s)
+        cudaMemcpyAsync(f.Phi[s], f.Psi[s], sizeof(cplx) * M * wk->N[s], cudaMemcpyDeviceToDevice, st);
+    fill_cplx(wk->weight, W, cplx{1.0, 0.0}, st);
+    rc = fp64_measure(wk, true, st, 1);
+    if (rc) return bail(rc);
+    cplx et;
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(&et, wk->E_L, sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    wk->E_T = et.re;
+    // walkers
+    if (Phi0) {
+        const size_t per = (size_t)M * (Nup + Ndn) * sizeof(cplx);
+        for (int s = 0; s < 2; ++s) {
+            const size_t off = (s == 0 ? 0 : (size_t)M * Nup * sizeof(cplx));
+            cudaError_t e = cudaMemcpy2DAsync(f.Phi[s], (size_t)M * wk->N[s] * sizeof(cplx),
+                                              reinterpret_cast<const char*>(Phi0) + off, per,
+                                              (size_t)M * wk->N[s] * sizeof(cplx), W, cudaMemcpyDefault, st);
+            if (e != cudaSuccess) return bail(fail(AFQMC_ERR_CUDA, std::string("init_walkers: ") + cudaGetErrorString(e)));
+            check_finite(reinterpret_cast<const double*>(f.Phi[s]), 2LL * W * M * wk->N[s], wk->flags, st);
+        }
+    } else {
+        for (int s = 0; s < 2; ++s)
+            replicate(f.Phi[s], f.Psi[s], (int64_t)M * wk->N[s], W, (int64_t)M * wk->N[s], st);
+    }
+    cudaMemsetAsync(wk->flags, 0, sizeof(unsigned), st);
+    if (o.precision == AFQMC_PREC_BF16X3) {
+        rc = tc_alloc(wk, st);
+        if (rc) return bail(rc);
+    }
+    // check the walkers' overlaps once
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        GemmArgs g;
+        g.m = N; g.n = N; g.k = M; g.nb1 = W;
+        g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = N;
+        g.B.ptr = f.Phi[s]; g.B.ld = N; g.B.s1 = (int64_t)M * N;
+        g.C = f.S[s]; g.ldc = N; g.sc1 = (int64_t)N * N;
+        zgemm(g, st);
+        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, wk->flags, st);
+    }
+    unsigned fl = 0;
+    rc = read_flags(wk->flags, st, &fl);
+    if (rc) return bail(rc);
+    rc = flags_to_error(fl, "init_walkers");
+    if (rc) return bail(rc);
+    if (!isfinite(wk->E_T)) return bail(fail(AFQMC_ERR_NONFINITE, "init_walkers: trial energy not finite"));
+    ham->live_walker_sets++;
+    *out = wk;
+    return AFQMC_OK;
+}
+
+int afqmc_destroy_walkers(afqmc_wk_t wk) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "destroy_walkers: NULL handle");
+    wk->ham->live_walker_sets--;
+    cudaDeviceSynchronize();
+    free_walkers(wk);
+    return AFQMC_OK;
+}
+
+static int ensure_x(afqmc_walkers* wk, int steps) {
+    if (steps <= wk->x_cap) return AFQMC_OK;
+    cudaFree(wk->x);
+    wk->x = nullptr;
+    if (cudaMalloc(&wk->x, sizeof(double) * (size_t)steps * wk->W * wk->Nchol) != cudaSuccess) {
+        cudaGetLastError();
+        wk->x_cap = 0;
+        return fail(AFQMC_ERR_OOM, "step: field buffer");
+    }
+    wk->x_cap = steps;
+    return AFQMC_OK;
+}
+
+static int ensure_emix(afqmc_walkers* wk, int n) {
+    if (n <= wk->emix_cap) return AFQMC_OK;
+    cudaFree(wk->emix);
+    wk->emix = nullptr;
+    if (cudaMalloc(&wk->emix, sizeof(cplx) * n) != cudaSuccess) {
+        cudaGetLastError();
+        wk->emix_cap = 0;
+        return fail(AFQMC_ERR_OOM, "step: trace buffer");
+    }
+    wk->emix_cap = n;
+    return AFQMC_OK;
+}
+
+int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int measure_every, double* E_mix_trace,
+               void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "step: NULL handle");
+    if (nsteps < 0 || measure_every < 0) return fail(AFQMC_ERR_BADARG, "step: negative nsteps or measure_every");
+    if (nsteps == 0) return AFQMC_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t per_step = (int64_t)wk->W * wk->Nchol;
+    const bool x_dev = x && is_device_ptr(x);
+    // caller fields: device pointers are used in place, host fields are staged per step
+    if (x && !x_dev) AFQMC_TRY(ensure_x(wk, 1));
+    if (!x) AFQMC_TRY(ensure_x(wk, 1));
+    const int nmeas = measure_every > 0 ? (nsteps + measure_every - 1) / measure_every : 0;
+    AFQMC_TRY(ensure_emix(wk, std::max(nmeas, 1)));
+    const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
+    wk->ev_valid = false;
+    for (int s = 0; s < nsteps; ++s) {
+        const bool meas = measure_every > 0 && s % measure_every == 0;
+        AFQMC_TRY(tc ? tc_measure(wk, meas, st) : fp64_measure(wk, meas, st));
+        if (meas) mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix + s / measure_every, st);
+        const double* xs;
+        if (x_dev) {
+            xs = x + (int64_t)s * per_step;
+        } else if (x) {
+            AFQMC_TRY(copy_in(wk->x, x + (int64_t)s * per_step, sizeof(double) * per_step, st));
+            xs = wk->x;
+        } else {
+            philox_fields(seed, wk->step, wk->W, wk->Nchol, wk->x, st);
+            xs = wk->x;
+        }
+        AFQMC_TRY(tc ? tc_propagate_and_weight(wk, xs, st) : fp64_propagate_and_weight(wk, xs, st));
+        wk->step++;
+        if (wk->opts.k_qr > 0 && wk->step % wk->opts.k_qr == 0) AFQMC_TRY(tc ? tc_qr(wk, st) : fp64_qr(wk, st));
+    }
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("step: launch failed: ") + cudaGetErrorString(le));
+    bool sync = false;
+    if (E_mix_trace && nmeas > 0) AFQMC_TRY(copy_out(E_mix_trace, wk->emix, sizeof(cplx) * nmeas, st, &sync));
+    unsigned fl = 0;
+    AFQMC_TRY(read_flags(wk->flags, st, &fl));
+    return flags_to_error(fl, "step");
+}
+
+int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_mix, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "energy: NULL handle");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
+    if (tc) AFQMC_TRY(tc_sync_walkers_to_fp64(wk, st));
+    AFQMC_TRY(tc ? tc_measure(wk, true, st) : fp64_measure(wk, true, st));
+    mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix, st);
+    bool sync = false;
+    const int W = wk->W;
+    AFQMC_TRY(copy_out(E_L, wk->E_L, sizeof(cplx) * W, st, &sync));
+    AFQMC_TRY(copy_out(logS, wk->logS_old, sizeof(cplx) * W, st, &sync));
+    AFQMC_TRY(copy_out(E_mix, wk->emix, sizeof(cplx), st, &sync));
+    if (w) {
+        if (wk->opts.weight_mode == AFQMC_WEIGHT_FREE) {
+            AFQMC_TRY(copy_out(w, wk->weight, sizeof(cplx) * W, st, &sync));
+        } else {
+            // real parts: strided copy
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(w, sizeof(double), wk->weight, sizeof(cplx), sizeof(double), W,
+                                             cudaMemcpyDefault, st));
+        }
+    }
+    unsigned fl = 0;
+    AFQMC_TRY(read_flags(wk->flags, st, &fl));
+    return flags_to_error(fl, "energy");
+}
+
+int afqmc_get_walkers(afqmc_wk_t wk, double* Phi, double* w, int64_t* step, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "get_walkers: NULL handle");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (wk->opts.precision == AFQMC_PREC_BF16X3) AFQMC_TRY(tc_sync_walkers_to_fp64(wk, st));
+    const int M = wk->M, W = wk->W;
+    const size_t per = (size_t)M * (wk->N[0] + wk->N[1]) * sizeof(cplx);
+    if (Phi) {
+        for (int s = 0; s < 2; ++s) {
+            const size_t off = s == 0 ? 0 : (size_t)M * wk->N[0] * sizeof(cplx);
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(reinterpret_cast<char*>(Phi) + off, per, wk->f.Phi[s],
+                                             (size_t)M * wk->N[s] * sizeof(cplx), (size_t)M * wk->N[s] * sizeof(cplx),
+                                             W, cudaMemcpyDefault, st));
+        }
+    }
+    if (w) {
+        if (wk->opts.weight_mode == AFQMC_WEIGHT_FREE)
+            AFQMC_CUDA_TRY(cudaMemcpyAsync(w, wk->weight, sizeof(cplx) * W, cudaMemcpyDefault, st));
+        else
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(w, sizeof(double), wk->weight, sizeof(cplx), sizeof(double), W,
+                                             cudaMemcpyDefault, st));
+    }
+    if (step) *step = wk->step;
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFQMC_OK;
+}
+
+int afqmc_set_walkers(afqmc_wk_t wk, const double* Phi, const double* w, int64_t step, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "set_walkers: NULL handle");
+    if (step < 0) return fail(AFQMC_ERR_BADARG, "set_walkers: negative step");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int M = wk->M, W = wk->W;
+    const size_t per = (size_t)M * (wk->N[0] + wk->N[1]) * sizeof(cplx);
+    if (Phi) {
+        for (int s = 0; s < 2; ++s) {
+            const size_t off = s == 0 ? 0 : (size_t)M * wk->N[0] * sizeof(cplx);
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(wk->f.Phi[s], (size_t)M * wk->N[s] * sizeof(cplx),
+                                             reinterpret_cast<const char*>(Phi) + off, per,
+                                             (size_t)M * wk->N[s] * sizeof(cplx), W, cudaMemcpyDefault, st));
+        }
+    }
+    if (w) {
+        if (wk->opts.weight_mode == AFQMC_WEIGHT_FREE) {
+            AFQMC_CUDA_TRY(cudaMemcpyAsync(wk->weight, w, sizeof(cplx) * W, cudaMemcpyDefault, st));
+        } else {
+            fill_cplx(wk->weight, W, cplx{0.0, 0.0}, st);
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(wk->weight, sizeof(cplx), w, sizeof(double), sizeof(double), W,
+                                             cudaMemcpyDefault, st));
+        }
+    }
+    wk->step = step;
+    if (wk->opts.precision == AFQMC_PREC_BF16X3) AFQMC_TRY(tc_sync_walkers_from_fp64(wk, st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFQMC_OK;
+}
+
+int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, void* stream) {
+    if (!x || W < 1 || Nchol < 1 || step < 0) return fail(AFQMC_ERR_BADARG, "philox_fields: bad argument");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (is_device_ptr(x)) {
+        philox_fields(seed, step, W, Nchol, x, st);
+        AFQMC_CUDA_TRY(cudaGetLastError());
+        return AFQMC_OK;
+    }
+    double* d = nullptr;
+    AFQMC_CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * (size_t)W * Nchol, st));
+    philox_fields(seed, step, W, Nchol, d, st);
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(x, d, sizeof(double) * (size_t)W * Nchol, cudaMemcpyDeviceToHost, st));
+    cudaFreeAsync(d, st);
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFQMC_OK;
+}
+
+int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, double* dPsi_up, double* dPsi_dn,
+                          double* dL, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "energy_backward: NULL handle");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return fp64_backward(wk, reinterpret_cast<const cplx*>(dE), reinterpret_cast<const cplx*>(dlogS),
+                         reinterpret_cast<cplx*>(dPsi_up), reinterpret_cast<cplx*>(dPsi_dn), dL, st);
+}
+
+int afqmc_last_step_stats(afqmc_wk_t wk, double* energy_kernel_ms, int* kernels_per_step) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "last_step_stats: NULL handle");
+    if (energy_kernel_ms) {
+        *energy_kernel_ms = -1.0;
+        if (wk->ev_valid) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(wk->ev1) == cudaSuccess && cudaEventElapsedTime(&ms, wk->ev0, wk->ev1) == cudaSuccess)
+                *energy_kernel_ms = ms;
+            else
+                cudaGetLastError();
+        }
+    }
+    if (kernels_per_step) *kernels_per_step = wk->kernels_per_step;
+    return AFQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Shared device/host helpers of the AFQMC library (complex FP64 arithmetic,
+// error plumbing, launch declarations).  Internal to the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/afqmc.h"
+
+namespace afqmc {
+
+// ---------------------------------------------------------------- complex FP64
+struct cplx {
+    double re, im;
+};
+
+__host__ __device__ __forceinline__ cplx mk(double r, double i) { return cplx{r, i}; }
+__host__ __device__ __forceinline__ cplx operator+(cplx a, cplx b) { return {a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cplx operator-(cplx a, cplx b) { return {a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cplx operator*(cplx a, cplx b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cplx operator*(double s, cplx a) { return {s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cplx conjg(cplx a) { return {a.re, -a.im}; }
+__host__ __device__ __forceinline__ double abs1(cplx a) { return fabs(a.re) + fabs(a.im); }
+// a += b * c  (complex fused multiply-add on FP64 pipes)
+__host__ __device__ __forceinline__ void cfma(cplx& a, cplx b, cplx c) {
+    a.re = fma(b.re, c.re, fma(-b.im, c.im, a.re));
+    a.im = fma(b.re, c.im, fma(b.im, c.re, a.im));
+}
+__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+    // Smith's algorithm for a / b
+    if (fabs(b.re) >= fabs(b.im)) {
+        double r = b.im / b.re, d = b.re + b.im * r;
+        return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+    } else {
+        double r = b.re / b.im, d = b.im + b.re * r;
+        return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+    }
+}
+
+// ---------------------------------------------------------------- error state
+struct Status {
+    int code = AFQMC_OK;
+    std::string msg;
+};
+void set_error(int code, const std::string& msg);
+int fail(int code, const std::string& msg);  // sets and returns code
+
+#define AFQMC_CUDA_TRY(expr)                                                                   \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess)                                                                  \
+            return ::afqmc::fail(AFQMC_ERR_CUDA, std::string(#expr " failed: ") +              \
+                                                     cudaGetErrorString(_e));                   \
+    } while (0)
+
+#define AFQMC_TRY(expr)                \
+    do {                               \
+        int _rc = (expr);              \
+        if (_rc != AFQMC_OK) return _rc; \
+    } while (0)
+
+// ---------------------------------------------------------------- device flags
+// Bits of the per-walker-set device status word (latched, read by the host).
+enum : unsigned {
+    FLAG_NONFINITE = 1u,
+    FLAG_SINGULAR = 2u,
+    FLAG_TIMEOUT = 4u,
+};
+
+}  // namespace afqmc

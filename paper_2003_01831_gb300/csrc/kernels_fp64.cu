@@ -1,0 +1,691 @@
+// FP64 (DFMA) kernels of the AFQMC walker step: batched complex GEMM, Gauss-Jordan
+// inverse / log-det, trace epilogue, local energy and force bias, Philox fields,
+// phaseless weights, Gram-Schmidt re-orthonormalisation, estimator reduction.
+//
+// The formulas follow the phaseless algorithm the paper cites in Sec. V (Zhang &
+// Krakauer 2003; Motta & Zhang 2018) for the Hamiltonian of Sec. V, Eq. (1) with
+// the Cholesky factorisation of Eq. (3).  All reductions run in a fixed order for
+// a fixed launch shape, so results are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "kernels_fp64.cuh"
+
+namespace afqmc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// Fixed-order block reduction of a complex value (all threads get the result).
+__device__ cplx block_sum(cplx v, cplx* sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] = sh[t] + sh[t + s];
+        __syncthreads();
+    }
+    cplx r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_sum_d(double v, double* sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (t < s) sh[t] += sh[t + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ bool finite_c(cplx a) { return isfinite(a.re) && isfinite(a.im); }
+
+// ------------------------------------------------------------------ batched GEMM
+template <bool R>
+struct Elem {
+    using T = cplx;
+};
+template <>
+struct Elem<true> {
+    using T = double;
+};
+
+__device__ __forceinline__ void load_elem(double& dst, const void* base, int64_t idx, bool conj) {
+    dst = static_cast<const double*>(base)[idx];
+}
+__device__ __forceinline__ void load_elem(cplx& dst, const void* base, int64_t idx, bool conj) {
+    const double2 v = static_cast<const double2*>(base)[idx];
+    dst.re = v.x;
+    dst.im = conj ? -v.y : v.y;
+}
+__device__ __forceinline__ void zero_elem(double& d) { d = 0.0; }
+__device__ __forceinline__ void zero_elem(cplx& d) { d = cplx{0.0, 0.0}; }
+
+__device__ __forceinline__ void mac(cplx& acc, double a, double b) { acc.re = fma(a, b, acc.re); }
+__device__ __forceinline__ void mac(cplx& acc, double a, cplx b) {
+    acc.re = fma(a, b.re, acc.re);
+    acc.im = fma(a, b.im, acc.im);
+}
+__device__ __forceinline__ void mac(cplx& acc, cplx a, double b) {
+    acc.re = fma(a.re, b, acc.re);
+    acc.im = fma(a.im, b, acc.im);
+}
+__device__ __forceinline__ void mac(cplx& acc, cplx a, cplx b) { cfma(acc, a, b); }
+
+template <bool AR, bool BR>
+__global__ void __launch_bounds__(kThreads) zgemm_kernel(GemmArgs g) {
+    constexpr int BM = 64, BN = 64, BK = 8;
+    using TA = typename Elem<AR>::T;
+    using TB = typename Elem<BR>::T;
+    __shared__ TA As[BK][BM + 1];
+    __shared__ TB Bs[BK][BN + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nbatch = g.nb1 * g.nb2;
+    for (int b = blockIdx.z; b < nbatch; b += gridDim.z) {
+        const int b1 = b / g.nb2, b2 = b % g.nb2;
+        const int64_t offA = b1 * g.A.s1 + b2 * g.A.s2;
+        const int64_t offB = b1 * g.B.s1 + b2 * g.B.s2;
+        cplx acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = cplx{0.0, 0.0};
+
+        for (int k0 = 0; k0 < g.k; k0 += BK) {
+            for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
+                int r, kk;
+                if (g.A.op == OP_N) { r = e / BK; kk = e % BK; }
+                else { kk = e / BM; r = e % BM; }
+                const int gr = m0 + r, gk = k0 + kk;
+                TA v;
+                zero_elem(v);
+                if (gr < g.m && gk < g.k) {
+                    const int64_t idx = offA + (g.A.op == OP_N ? (int64_t)gr * g.A.ld + gk
+                                                                : (int64_t)gk * g.A.ld + gr);
+                    load_elem(v, g.A.ptr, idx, g.A.op == OP_C);
+                }
+                As[kk][r] = v;
+            }
+            for (int e = threadIdx.x; e < BN * BK; e += kThreads) {
+                int c, kk;
+                if (g.B.op == OP_N) { kk = e / BN; c = e % BN; }
+                else { c = e / BK; kk = e % BK; }
+                const int gc = n0 + c, gk = k0 + kk;
+                TB v;
+                zero_elem(v);
+                if (gc < g.n && gk < g.k) {
+                    const int64_t idx = offB + (g.B.op == OP_N ? (int64_t)gk * g.B.ld + gc
+                                                                : (int64_t)gc * g.B.ld + gk);
+                    load_elem(v, g.B.ptr, idx, g.B.op == OP_C);
+                }
+                Bs[kk][c] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                TA a[4];
+                TB bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], bv[j]);
+            }
+            __syncthreads();
+        }
+        const bool use_beta = (g.beta.re != 0.0 || g.beta.im != 0.0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = m0 + ty + 16 * i;
+            if (r >= g.m) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = n0 + tx + 16 * j;
+                if (c >= g.n) continue;
+                cplx v = g.alpha * acc[i][j];
+                cplx* cp = g.C + b1 * g.sc1 + b2 * g.sc2 + (int64_t)r * g.ldc + c;
+                if (use_beta) v = v + g.beta * (*cp);
+                *cp = v;
+                if (g.D) {
+                    cplx* dp = g.D + b1 * g.sd1 + b2 * g.sd2 + (int64_t)r * g.ldd + c;
+                    *dp = *dp + v;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Gauss-Jordan
+__global__ void __launch_bounds__(kThreads)
+    gj_kernel(cplx* Sbase, int64_t stride, int N, cplx* logdet, int with_inverse, unsigned* flags) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx* prow = reinterpret_cast<cplx*>(smem_raw);  // N (scaled pivot row)
+    cplx* pcol = prow + N;                           // N (pivot column)
+    int* perm = reinterpret_cast<int*>(pcol + N);    // N
+    __shared__ double red_v[kThreads];
+    __shared__ int red_i[kThreads];
+    __shared__ int s_piv;
+    __shared__ int s_singular;
+    cplx* A = Sbase + (int64_t)blockIdx.x * stride;
+    const int t = threadIdx.x;
+    double logabs = 0.0, phase = 0.0;  // meaningful in thread 0
+    if (t == 0) s_singular = 0;
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+        // pivot: max |re|+|im| over rows k..N-1 of column k, lowest index on ties
+        double best = -1.0;
+        int bi = N;
+        for (int i = k + t; i < N; i += kThreads) {
+            const double v = abs1(A[(int64_t)i * N + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+        red_v[t] = best;
+        red_i[t] = bi;
+        __syncthreads();
+        for (int s = kThreads / 2; s > 0; s >>= 1) {
+            if (t < s) {
+                const double v2 = red_v[t + s];
+                const int i2 = red_i[t + s];
+                if (v2 > red_v[t] || (v2 == red_v[t] && i2 < red_i[t])) { red_v[t] = v2; red_i[t] = i2; }
+            }
+            __syncthreads();
+        }
+        if (t == 0) {
+            s_piv = red_i[0];
+            if (!(red_v[0] > 0.0)) s_singular = isnan(red_v[0]) ? 2 : 1;
+            perm[k] = red_i[0];
+        }
+        __syncthreads();
+        if (s_singular) break;
+        const int p = s_piv;
+        if (p != k) {
+            for (int j = t; j < N; j += kThreads) {
+                const cplx a = A[(int64_t)k * N + j];
+                A[(int64_t)k * N + j] = A[(int64_t)p * N + j];
+                A[(int64_t)p * N + j] = a;
+            }
+            __syncthreads();
+        }
+        const cplx piv = A[(int64_t)k * N + k];
+        const cplx inv = cdiv(cplx{1.0, 0.0}, piv);
+        if (t == 0) {
+            logabs += log(hypot(piv.re, piv.im));
+            phase += atan2(piv.im, piv.re) + (p != k ? M_PI : 0.0);
+        }
+        for (int j = t; j < N; j += kThreads) {
+            prow[j] = A[(int64_t)k * N + j] * inv;
+            pcol[j] = A[(int64_t)j * N + k];
+        }
+        __syncthreads();
+        if (with_inverse) {
+            for (int64_t e = t; e < (int64_t)N * N; e += kThreads) {
+                const int i = (int)(e / N), j = (int)(e % N);
+                cplx v;
+                if (i == k) v = (j == k) ? inv : prow[j];
+                else if (j == k) v = cplx{0.0, 0.0} - pcol[i] * inv;
+                else { v = A[e]; cfma(v, cplx{0.0, 0.0} - pcol[i], prow[j]); }
+                A[e] = v;
+            }
+        } else {
+            const int nr = N - k - 1;
+            for (int64_t e = t; e < (int64_t)nr * nr; e += kThreads) {
+                const int i = k + 1 + (int)(e / nr), j = k + 1 + (int)(e % nr);
+                cplx v = A[(int64_t)i * N + j];
+                cfma(v, cplx{0.0, 0.0} - pcol[i], prow[j]);
+                A[(int64_t)i * N + j] = v;
+            }
+        }
+        __syncthreads();
+    }
+    if (s_singular) {
+        if (t == 0) {
+            logdet[blockIdx.x] = cplx{-INFINITY, 0.0};
+            atomicOr(flags, s_singular == 2 ? FLAG_NONFINITE : FLAG_SINGULAR);
+        }
+        return;
+    }
+    if (with_inverse) {
+        for (int k = N - 1; k >= 0; --k) {
+            const int p = perm[k];
+            if (p != k) {
+                for (int i = t; i < N; i += kThreads) {
+                    const cplx a = A[(int64_t)i * N + k];
+                    A[(int64_t)i * N + k] = A[(int64_t)i * N + p];
+                    A[(int64_t)i * N + p] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (t == 0) logdet[blockIdx.x] = cplx{logabs, atan2(sin(phase), cos(phase))};
+}
+
+// ------------------------------------------------------------------ traces of T
+__global__ void __launch_bounds__(kThreads)
+    trace_kernel(const cplx* T, int W, int N, int n0, cplx* t_out, cplx* X_out, int64_t ldo) {
+    __shared__ cplx sh[kThreads];
+    const int w = blockIdx.x, c = blockIdx.y;
+    const cplx* Tm = T + ((int64_t)c * W + w) * N * N;
+    cplx tr{0.0, 0.0}, x{0.0, 0.0};
+    for (int64_t e = threadIdx.x; e < (int64_t)N * N; e += kThreads) {
+        const int a = (int)(e / N), b = (int)(e % N);
+        const cplx tab = Tm[e];
+        cfma(x, tab, Tm[(int64_t)b * N + a]);
+        if (a == b) tr = tr + tab;
+    }
+    tr = block_sum(tr, sh);
+    x = block_sum(x, sh);
+    if (threadIdx.x == 0) {
+        t_out[(int64_t)w * ldo + n0 + c] = tr;
+        X_out[(int64_t)w * ldo + n0 + c] = x;
+    }
+}
+
+// ------------------------------------------------------------------ local energy
+__global__ void __launch_bounds__(kThreads) local_energy_kernel(LocalEnergyArgs a) {
+    __shared__ cplx sh[kThreads];
+    const int w = blockIdx.x;
+    cplx e1{0.0, 0.0};
+    for (int s = 0; s < 2; ++s) {
+        const int Ns = s == 0 ? a.Nup : a.Ndn;
+        const cplx* Th = a.Theta[s] + (int64_t)w * a.M * Ns;
+        const cplx* ht = a.ht[s];
+        for (int64_t e = threadIdx.x; e < (int64_t)a.M * Ns; e += kThreads) {
+            const int k = (int)(e / Ns), b = (int)(e % Ns);
+            cfma(e1, ht[(int64_t)b * a.M + k], Th[e]);
+        }
+    }
+    const double sq = sqrt(a.tau);
+    cplx e2{0.0, 0.0};
+    const bool energy = a.X[0] != nullptr;
+    for (int n = threadIdx.x; n < a.Nchol; n += kThreads) {
+        const int64_t i = (int64_t)w * a.Nchol + n;
+        const cplx ts = a.t[0][i] + a.t[1][i];
+        if (energy) {
+            cfma(e2, ts, ts);
+            e2 = e2 - a.X[0][i] - a.X[1][i];
+        }
+        cplx xb{sq * ts.im, -sq * ts.re};  // -i sqrt(tau) ts
+        if (a.fb_cap > 0.0) {
+            const double mag = hypot(xb.re, xb.im);
+            if (mag > a.fb_cap) xb = (a.fb_cap / mag) * xb;
+        }
+        a.xbar[i] = xb;
+    }
+    if (energy) {
+        e1 = block_sum(e1, sh);
+        e2 = block_sum(e2, sh);
+        if (threadIdx.x == 0) {
+            const cplx E = cplx{a.E0 + e1.re + 0.5 * e2.re, e1.im + 0.5 * e2.im};
+            a.E_L[w] = E;
+            if (!finite_c(E)) atomicOr(a.flags, FLAG_NONFINITE);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                             uint32_t k0, uint32_t k1) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+}
+
+__global__ void philox_kernel(uint64_t seed, int64_t step, int W, int Nchol, double* x) {
+    const int nq = (Nchol + 3) / 4;
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)W * nq) return;
+    const int w = (int)(id / nq), q = (int)(id % nq);
+    uint32_t c0 = (uint32_t)q, c1 = (uint32_t)w, c2 = (uint32_t)step, c3 = 0u;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        philox_round(c0, c1, c2, c3, k0, k1);
+    }
+    const double inv = 2.3283064365386963e-10;  // 2^-32
+    const uint32_t o[4] = {c0, c1, c2, c3};
+    double* xr = x + (int64_t)w * Nchol;
+    for (int p = 0; p < 2; ++p) {
+        const double u1 = ((double)o[2 * p] + 0.5) * inv;
+        const double u2 = ((double)o[2 * p + 1] + 0.5) * inv;
+        const double r = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        const int n = 4 * q + 2 * p;
+        if (n < Nchol) xr[n] = r * cs;
+        if (n + 1 < Nchol) xr[n + 1] = r * sn;
+    }
+}
+
+// ------------------------------------------------------------------ small kernels
+__global__ void hs_coeff_kernel(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol,
+                                cplx* c, unsigned* flags) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)W * Nchol) return;
+    const int w = (int)(id / Nchol);
+    const double xv = x[id];
+    if (!isfinite(xv)) atomicOr(flags, FLAG_NONFINITE);
+    const bool alive = weight[w].re != 0.0 || weight[w].im != 0.0;
+    c[id] = alive ? cplx{xv - xbar[id].re, -xbar[id].im} : cplx{0.0, 0.0};
+}
+
+__global__ void __launch_bounds__(kThreads) weight_kernel(WeightArgs a) {
+    __shared__ cplx sh[kThreads];
+    const int w = blockIdx.x;
+    cplx s{0.0, 0.0};
+    for (int n = threadIdx.x; n < a.Nchol; n += kThreads) {
+        const int64_t i = (int64_t)w * a.Nchol + n;
+        const cplx xb = a.xbar[i];
+        // x xbar - xbar^2 / 2
+        s = s + a.x[i] * xb;
+        cfma(s, cplx{-0.5, 0.0} * xb, xb);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x != 0) return;
+    const cplx w0 = a.weight[w];
+    const bool alive = w0.re != 0.0 || w0.im != 0.0;
+    if (!alive) { a.accept[w] = 0; return; }
+    const cplx ln = a.logS_new[w];
+    if (!finite_c(ln)) { a.accept[w] = 0; a.weight[w] = cplx{0.0, 0.0}; return; }
+    const cplx dl = ln - a.logS_old[w];
+    const cplx ex = cplx{dl.re + s.re + a.tau * (a.E_T - a.E0), dl.im + s.im};
+    if (a.mode == AFQMC_WEIGHT_FREE) {
+        const double m = exp(ex.re);
+        a.weight[w] = w0 * cplx{m * cos(ex.im), m * sin(ex.im)};
+    } else {
+        const double c = cos(dl.im);
+        a.weight[w] = cplx{w0.re * exp(ex.re) * (c > 0.0 ? c : 0.0), 0.0};
+    }
+    a.accept[w] = 1;
+}
+
+__global__ void commit_kernel(cplx* Phi, const cplx* Phi_new, const int* accept, int W, int64_t per) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)W * per) return;
+    if (accept[id / per]) Phi[id] = Phi_new[id];
+}
+
+__global__ void __launch_bounds__(kThreads)
+    qr_kernel(cplx* Phi, int64_t stride, int M, int N, const cplx* weight) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx* v = reinterpret_cast<cplx*>(smem_raw);  // M
+    cplx* r = v + M;                              // N
+    __shared__ double shd[kThreads];
+    const int w = blockIdx.x;
+    if (weight[w].re == 0.0 && weight[w].im == 0.0) return;
+    cplx* Q = Phi + (int64_t)w * stride;
+    const int t = threadIdx.x;
+    for (int j = 0; j < N; ++j) {
+        for (int k = t; k < M; k += kThreads) v[k] = Q[(int64_t)k * N + j];
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int i = t; i < j; i += kThreads) {
+                cplx acc{0.0, 0.0};
+                for (int k = 0; k < M; ++k) cfma(acc, conjg(Q[(int64_t)k * N + i]), v[k]);
+                r[i] = acc;
+            }
+            __syncthreads();
+            for (int k = t; k < M; k += kThreads) {
+                cplx acc = v[k];
+                for (int i = 0; i < j; ++i) cfma(acc, cplx{0.0, 0.0} - Q[(int64_t)k * N + i], r[i]);
+                v[k] = acc;
+            }
+            __syncthreads();
+        }
+        double nrm = 0.0;
+        for (int k = t; k < M; k += kThreads) nrm += v[k].re * v[k].re + v[k].im * v[k].im;
+        nrm = block_sum_d(nrm, shd);
+        const double inv = 1.0 / sqrt(nrm);
+        for (int k = t; k < M; k += kThreads) Q[(int64_t)k * N + j] = inv * v[k];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) emix_kernel(const cplx* weight, const cplx* E_L, int W, cplx* out) {
+    __shared__ cplx sh[kThreads];
+    cplx num{0.0, 0.0}, den{0.0, 0.0};
+    for (int w = threadIdx.x; w < W; w += kThreads) {
+        cfma(num, weight[w], E_L[w]);
+        den = den + weight[w];
+    }
+    num = block_sum(num, sh);
+    den = block_sum(den, sh);
+    if (threadIdx.x == 0) out[0] = cdiv(num, den);
+}
+
+__global__ void fill_kernel(cplx* p, int64_t n, cplx v) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) p[id] = v;
+}
+
+__global__ void replicate_kernel(cplx* dst, const cplx* src, int64_t n, int copies, int64_t dst_stride) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n * copies) return;
+    const int c = (int)(id / n);
+    const int64_t e = id % n;
+    dst[c * dst_stride + e] = src[e];
+}
+
+__global__ void r2c_kernel(const double* s, cplx* d, int64_t n) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) d[id] = cplx{s[id], 0.0};
+}
+
+__global__ void finite_kernel(const double* p, int64_t n, unsigned* flags) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n && !isfinite(p[id])) atomicOr(flags, FLAG_NONFINITE);
+}
+
+__global__ void sym_kernel(const double* L, int M, int Nchol, unsigned* flags) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)Nchol * M * M) return;
+    const int n = (int)(id / ((int64_t)M * M));
+    const int64_t e = id % ((int64_t)M * M);
+    const int i = (int)(e / M), k = (int)(e % M);
+    if (k <= i) return;
+    const double a = L[id], b = L[(int64_t)n * M * M + (int64_t)k * M + i];
+    if (fabs(a - b) > 1e-10 * fmax(1.0, fabs(a))) atomicOr(flags, 8u);
+}
+
+__global__ void hprime_reduce_kernel(const double* h, const cplx* parts, int nparts, int M, double* hp) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M * M) return;
+    double acc = 0.0;
+    for (int p = 0; p < nparts; ++p) acc += parts[(int64_t)p * M * M + id].re;
+    hp[id] = h[id] - 0.5 * acc;
+}
+
+__global__ void c2r_scale_kernel(const cplx* s, double* d, int64_t n) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) d[id] = s[id].re;
+}
+
+__global__ void add_identity_kernel(cplx* A, int M, double s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) A[(int64_t)i * M + i].re += s;
+}
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ================================================================== launchers
+void zgemm(const GemmArgs& g, cudaStream_t st) {
+    if (g.m <= 0 || g.n <= 0) return;
+    const int nbatch = g.nb1 * g.nb2;
+    dim3 grid((g.n + 63) / 64, (g.m + 63) / 64, std::min(nbatch, 65535));
+    if (g.A.real && g.B.real) zgemm_kernel<true, true><<<grid, kThreads, 0, st>>>(g);
+    else if (g.A.real) zgemm_kernel<true, false><<<grid, kThreads, 0, st>>>(g);
+    else if (g.B.real) zgemm_kernel<false, true><<<grid, kThreads, 0, st>>>(g);
+    else zgemm_kernel<false, false><<<grid, kThreads, 0, st>>>(g);
+}
+
+void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet, bool with_inverse,
+                            unsigned* flags, cudaStream_t st) {
+    if (count <= 0) return;
+    const size_t sm = (size_t)N * (2 * sizeof(cplx) + sizeof(int));
+    gj_kernel<<<count, kThreads, sm, st>>>(S, stride, N, logdet, with_inverse ? 1 : 0, flags);
+}
+
+void trace_terms(const cplx* T, int nc, int W, int N, int n0, cplx* t_out, cplx* X_out, int64_t ldo,
+                 cudaStream_t st) {
+    dim3 grid(W, nc);
+    trace_kernel<<<grid, kThreads, 0, st>>>(T, W, N, n0, t_out, X_out, ldo);
+}
+
+void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st) {
+    local_energy_kernel<<<a.W, kThreads, 0, st>>>(a);
+}
+
+void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st) {
+    const int64_t n = (int64_t)W * ((Nchol + 3) / 4);
+    philox_kernel<<<blocks_for(n), kThreads, 0, st>>>(seed, step, W, Nchol, x);
+}
+
+void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol, cplx* c,
+                     unsigned* flags, cudaStream_t st) {
+    hs_coeff_kernel<<<blocks_for((int64_t)W * Nchol), kThreads, 0, st>>>(x, xbar, weight, W, Nchol, c, flags);
+}
+
+void weight_update(const WeightArgs& a, cudaStream_t st) { weight_kernel<<<a.W, kThreads, 0, st>>>(a); }
+
+void commit_walkers(cplx* Phi, const cplx* Phi_new, const int* accept, int W, int64_t per, cudaStream_t st) {
+    commit_kernel<<<blocks_for((int64_t)W * per), kThreads, 0, st>>>(Phi, Phi_new, accept, W, per);
+}
+
+void qr_reorthonormalise(cplx* Phi, int64_t stride, int M, int N, int W, const cplx* weight,
+                         cudaStream_t st) {
+    const size_t sm = (size_t)(M + N) * sizeof(cplx);
+    qr_kernel<<<W, kThreads, sm, st>>>(Phi, stride, M, N, weight);
+}
+
+void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st) {
+    emix_kernel<<<1, kThreads, 0, st>>>(weight, E_L, W, out);
+}
+
+void fill_cplx(cplx* p, int64_t n, cplx v, cudaStream_t st) {
+    if (n > 0) fill_kernel<<<blocks_for(n), kThreads, 0, st>>>(p, n, v);
+}
+
+void replicate(cplx* dst, const cplx* src, int64_t n, int copies, int64_t dst_stride, cudaStream_t st) {
+    replicate_kernel<<<blocks_for(n * copies), kThreads, 0, st>>>(dst, src, n, copies, dst_stride);
+}
+
+void real_to_cplx(const double* src, cplx* dst, int64_t n, cudaStream_t st) {
+    r2c_kernel<<<blocks_for(n), kThreads, 0, st>>>(src, dst, n);
+}
+
+void check_finite(const double* p, int64_t n, unsigned* flags, cudaStream_t st) {
+    if (n > 0) finite_kernel<<<blocks_for(n), kThreads, 0, st>>>(p, n, flags);
+}
+
+void check_symmetric(const double* L, int M, int Nchol, unsigned* flags, cudaStream_t st) {
+    const int64_t n = (int64_t)Nchol * M * M;
+    sym_kernel<<<blocks_for(n), kThreads, 0, st>>>(L, M, Nchol, flags);
+}
+
+void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp, cudaStream_t st) {
+    // L_n symmetric: sum_n L_n L_n^T = X^T X with X[(n, k)][i] = L[n][k][i], a contiguous
+    // [Nchol*M][M] matrix.  Split the K = Nchol*M reduction into `parts` batched GEMMs
+    // (fixed split, fixed-order reduction) to fill the GPU.
+    const int parts = std::min(Nchol, 16);
+    const int per = (Nchol + parts - 1) / parts;  // Cholesky vectors per part
+    cplx* buf = nullptr;
+    if (cudaMallocAsync(&buf, sizeof(cplx) * (size_t)parts * M * M, st) != cudaSuccess) {
+        fail(AFQMC_ERR_OOM, "hprime workspace");
+        return;
+    }
+    fill_cplx(buf, (int64_t)parts * M * M, cplx{0.0, 0.0}, st);
+    for (int p = 0; p < parts; ++p) {
+        const int n0 = p * per, n1 = std::min(Nchol, n0 + per);
+        if (n1 <= n0) continue;
+        GemmArgs g;
+        g.m = g.n = M;
+        g.k = (n1 - n0) * M;
+        const double* X = L + (int64_t)n0 * M * M;
+        g.A.ptr = X; g.A.real = true; g.A.op = OP_T; g.A.ld = M;
+        g.B.ptr = X; g.B.real = true; g.B.op = OP_N; g.B.ld = M;
+        g.C = buf + (int64_t)p * M * M; g.ldc = M;
+        zgemm(g, st);
+    }
+    hprime_reduce_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(h, buf, parts, M, hp);
+    cudaFreeAsync(buf, st);
+}
+
+int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
+    // exp(s X) = (T_q(s X / 2^j))^(2^j): Taylor order 18 by Horner, j squarings so that
+    // ||s X / 2^j||_1 <= 1/4 (truncation error below 1e-20 relative).
+    std::vector<double> hX((size_t)M * M);
+    cudaError_t e = cudaMemcpyAsync(hX.data(), X, sizeof(double) * M * M, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, "expm copy");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, "expm sync");
+    double nrm = 0.0;
+    for (int j = 0; j < M; ++j) {
+        double c = 0.0;
+        for (int i = 0; i < M; ++i) c += fabs(hX[(size_t)i * M + j]);
+        nrm = std::max(nrm, c);
+    }
+    nrm *= fabs(s);
+    int sq = 0;
+    while (nrm > 0.25 && sq < 60) { nrm *= 0.5; ++sq; }
+    const double sc = s / ldexp(1.0, sq);
+    cplx *Y = nullptr, *E = nullptr, *Tm = nullptr;
+    const size_t bytes = sizeof(cplx) * M * M;
+    if (cudaMallocAsync(&Y, bytes, st) != cudaSuccess || cudaMallocAsync(&E, bytes, st) != cudaSuccess ||
+        cudaMallocAsync(&Tm, bytes, st) != cudaSuccess)
+        return fail(AFQMC_ERR_OOM, "expm workspace");
+    real_to_cplx(X, Y, (int64_t)M * M, st);
+    // E = I
+    fill_cplx(E, (int64_t)M * M, cplx{0.0, 0.0}, st);
+    add_identity_kernel<<<blocks_for(M), kThreads, 0, st>>>(E, M, 1.0);
+    const int order = 18;
+    for (int k = order; k >= 1; --k) {
+        // E <- I + (sc / k) Y E
+        GemmArgs g;
+        g.m = g.n = g.k = M;
+        g.A.ptr = Y; g.A.ld = M;
+        g.B.ptr = E; g.B.ld = M;
+        g.alpha = cplx{sc / k, 0.0};
+        g.C = Tm; g.ldc = M;
+        zgemm(g, st);
+        add_identity_kernel<<<blocks_for(M), kThreads, 0, st>>>(Tm, M, 1.0);
+        std::swap(E, Tm);
+    }
+    for (int q = 0; q < sq; ++q) {
+        GemmArgs g;
+        g.m = g.n = g.k = M;
+        g.A.ptr = E; g.A.ld = M;
+        g.B.ptr = E; g.B.ld = M;
+        g.C = Tm; g.ldc = M;
+        zgemm(g, st);
+        std::swap(E, Tm);
+    }
+    c2r_scale_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(E, out, (int64_t)M * M);
+    cudaFreeAsync(Y, st);
+    cudaFreeAsync(E, st);
+    cudaFreeAsync(Tm, st);
+    return AFQMC_OK;
+}
+
+}  // namespace afqmc

@@ -1,0 +1,106 @@
+// Launch interfaces of the FP64 (DFMA) kernels.  Internal to the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace afqmc {
+
+// Operand of a batched GEMM: element (row r, col c) of op(X) for batch (b1, b2) is read at
+//   ptr + b1*s1 + b2*s2 + (op == N ? r*ld + c : c*ld + r), conjugated when op == C.
+enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
+
+struct GemmOperand {
+    const void* ptr = nullptr;
+    bool real = false;  // true: doubles, imaginary part zero
+    int op = OP_N;
+    int64_t ld = 0;
+    int64_t s1 = 0, s2 = 0;
+};
+
+// C[b] = alpha op(A[b]) op(B[b]) + beta C[b];  if D != null also D[b] += (that result).
+// batch index b = b1 * nb2 + b2, nbatch = nb1 * nb2.
+struct GemmArgs {
+    int m = 0, n = 0, k = 0;
+    int nb1 = 1, nb2 = 1;
+    GemmOperand A, B;
+    cplx alpha{1.0, 0.0}, beta{0.0, 0.0};
+    cplx* C = nullptr;
+    int64_t ldc = 0, sc1 = 0, sc2 = 0;
+    cplx* D = nullptr;
+    int64_t ldd = 0, sd1 = 0, sd2 = 0;
+};
+
+void zgemm(const GemmArgs& g, cudaStream_t st);
+
+// In-place Gauss-Jordan inverse (with_inverse) or LU elimination (log-det only) of `count`
+// complex N x N matrices at S + i*stride, partial pivoting on max |re|+|im|.  logdet[i] =
+// log|det| + i arg(det) (arg wrapped to (-pi, pi]); sets FLAG_SINGULAR on an exact zero pivot.
+void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet,
+                            bool with_inverse, unsigned* flags, cudaStream_t st);
+
+// Traces of T[c][w] (N x N, chunk of Nchol entries): t = Tr T, X = Tr(T T), written to
+// t_out[w*ldo + n0 + c], X_out[...].  T layout [nc][W][N][N].
+void trace_terms(const cplx* T, int nc, int W, int N, int n0, cplx* t_out, cplx* X_out,
+                 int64_t ldo, cudaStream_t st);
+
+// Per walker: E_L = E0 + sum_s Tr(ht_s Theta_s) + 1/2 sum_n [(t_up + t_dn)^2 - X_up - X_dn];
+// xbar_n = -i sqrt(tau) (t_up + t_dn), capped.  ht_s [N_s][M], Theta_s [W][M][N_s],
+// t/X [W][Nchol] per spin.  X may be null (energy skipped, E_L untouched).
+struct LocalEnergyArgs {
+    int W, M, Nchol, Nup, Ndn;
+    const cplx* ht[2];
+    const cplx* Theta[2];
+    const cplx* t[2];
+    const cplx* X[2];
+    double E0, tau, fb_cap;
+    cplx* E_L;
+    cplx* xbar;
+    unsigned* flags;
+};
+void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st);
+
+// Philox4x32-10 + Box-Muller fields x[w][n] for global step `step`.
+void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st);
+
+// c[w][n] = x[w][n] - xbar[w][n] for walkers with w != 0, else 0; flags NaN/Inf fields.
+void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol,
+                     cplx* c, unsigned* flags, cudaStream_t st);
+
+// Weight update (phaseless or free) and acceptance mask.
+struct WeightArgs {
+    int W, Nchol, mode;
+    const double* x;
+    const cplx* xbar;
+    const cplx* logS_old;
+    const cplx* logS_new;
+    double tau, E_T, E0;
+    cplx* weight;      // in/out
+    int* accept;       // out: 1 = take Phi'
+};
+void weight_update(const WeightArgs& a, cudaStream_t st);
+
+// Phi[w] <- Phi_new[w] where accept[w]; `per_walker` complex elements per walker.
+void commit_walkers(cplx* Phi, const cplx* Phi_new, const int* accept, int W, int64_t per_walker,
+                    cudaStream_t st);
+
+// In-place Gram-Schmidt (classical, twice) of the N columns of each M x N complex matrix
+// Phi[w] (row-major, stride `stride`), diag R > 0; skipped where weight == 0.
+void qr_reorthonormalise(cplx* Phi, int64_t stride, int M, int N, int W, const cplx* weight,
+                         cudaStream_t st);
+
+// E_mix = sum_w w E_L / sum_w w (single block, fixed order); writes out[0].
+void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st);
+
+// small helpers
+void fill_cplx(cplx* p, int64_t n, cplx v, cudaStream_t st);
+void replicate(cplx* dst, const cplx* src, int64_t n, int copies, int64_t dst_stride, cudaStream_t st);
+void real_to_cplx(const double* src, cplx* dst, int64_t n, cudaStream_t st);
+void check_finite(const double* p, int64_t n, unsigned* flags, cudaStream_t st);
+// h' = h - 1/2 sum_n L_n L_n^T (real, FP64)
+void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp, cudaStream_t st);
+// exp(s * X) for a real symmetric M x M matrix by scaling-and-squaring of a Taylor series (FP64).
+int expm_real(const double* X, double s, int M, double* out, cudaStream_t st);
+// max |L_n - L_n^T| > tol * max|L| sets FLAG_NONFINITE-independent flag 8
+void check_symmetric(const double* L, int M, int Nchol, unsigned* flags, cudaStream_t st);
+
+}  // namespace afqmc

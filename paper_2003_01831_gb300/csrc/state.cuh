@@ -1,0 +1,102 @@
+// Handle structures shared by the C-ABI front end and the step drivers.  Internal.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+#include "kernels_fp64.cuh"
+
+struct afqmc_ham {
+    int device = 0;
+    int M = 0, Nchol = 0;
+    double E0 = 0.0;
+    double* h = nullptr;    // [M][M]
+    double* L = nullptr;    // [Nchol][M][M]
+    double* hp = nullptr;   // h' = h - 1/2 sum L L^T
+    unsigned* flags = nullptr;
+    int live_walker_sets = 0;
+};
+
+namespace afqmc {
+
+struct TcState;  // tensor-core buffers (kernels_tc.cu)
+
+// Device buffers of the FP64 path.  Walkers, Green's functions and traces are kept per
+// spin; complex arrays are interleaved FP64 pairs.
+struct Fp64Buffers {
+    cplx* Psi[2] = {nullptr, nullptr};     // [M][N_s]
+    void* Lt[2] = {nullptr, nullptr};      // Psi_s^+ L_n: [Nchol][N_s][M] (double if trial real)
+    void* LtT[2] = {nullptr, nullptr};     // transposed: [Nchol][M][N_s] (force-bias-only path)
+    cplx* ht[2] = {nullptr, nullptr};      // Psi_s^+ h: [N_s][M]
+    double* Bh = nullptr;                  // exp(-tau h'/2): [M][M]
+    cplx* Phi[2] = {nullptr, nullptr};     // [W][M][N_s]
+    cplx* Pnew[2] = {nullptr, nullptr};    // propagated walkers / Taylor accumulator
+    cplx* Pa[2] = {nullptr, nullptr};      // Taylor term ping
+    cplx* Pb[2] = {nullptr, nullptr};      // Taylor term pong
+    cplx* S[2] = {nullptr, nullptr};       // [W][N_s][N_s] overlap, inverted in place
+    cplx* ld[2] = {nullptr, nullptr};      // [W] per-spin log det
+    cplx* Theta[2] = {nullptr, nullptr};   // [W][M][N_s]
+    cplx* t[2] = {nullptr, nullptr};       // [W][Nchol]
+    cplx* X[2] = {nullptr, nullptr};       // [W][Nchol]
+    cplx* T = nullptr;                     // trace chunk [nc][W][N][N]
+    int nc = 0;
+    cplx* A = nullptr;                     // [W][M][M] HS potential
+};
+
+}  // namespace afqmc
+
+struct afqmc_walkers {
+    afqmc_ham* ham = nullptr;
+    int device = 0;
+    int M = 0, Nchol = 0, N[2] = {0, 0}, W = 0;
+    double tau = 0.0;
+    afqmc_opts opts{};
+    bool trial_real = false;
+    double E_T = 0.0;
+    int64_t step = 0;
+
+    afqmc::Fp64Buffers f;
+    afqmc::TcState* tc = nullptr;
+
+    // shared per-walker arrays
+    afqmc::cplx* weight = nullptr;    // [W]
+    afqmc::cplx* logS_old = nullptr;  // [W]
+    afqmc::cplx* logS_new = nullptr;  // [W]
+    afqmc::cplx* E_L = nullptr;       // [W]
+    afqmc::cplx* xbar = nullptr;      // [W][Nchol]
+    afqmc::cplx* coef = nullptr;      // [W][Nchol]
+    int* accept = nullptr;            // [W]
+    double* x = nullptr;              // fields, x_cap steps of [W][Nchol]
+    int x_cap = 0;
+    afqmc::cplx* emix = nullptr;      // measurement trace, emix_cap entries
+    int emix_cap = 0;
+    unsigned* flags = nullptr;
+
+    // timing of the energy contraction (device events around it in the last step)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_valid = false;
+    int kernels_per_step = -1;
+};
+
+namespace afqmc {
+
+// step drivers (step_fp64.cu / step_tc.cu)
+int fp64_alloc(afqmc_walkers* wk);
+void fp64_free(afqmc_walkers* wk);
+// Green's function, traces, local energy and force bias at the current walkers.
+// measure = compute exchange too.  Leaves logS of the current walkers in wk->logS_old.
+int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm = 0);
+int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st);
+int fp64_qr(afqmc_walkers* wk, cudaStream_t st);
+int fp64_backward(afqmc_walkers* wk, const cplx* dE, const cplx* dlogS, cplx* dPsi_up, cplx* dPsi_dn,
+                  double* dL, cudaStream_t st);
+
+int tc_alloc(afqmc_walkers* wk, cudaStream_t st);
+void tc_free(afqmc_walkers* wk);
+int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st);
+int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st);
+int tc_qr(afqmc_walkers* wk, cudaStream_t st);
+int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st);
+int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st);
+
+}  // namespace afqmc

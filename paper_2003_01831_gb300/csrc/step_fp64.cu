@@ -1,0 +1,209 @@
+// FP64 walker-step driver: the phaseless AFQMC step (Sec. V; Zhang & Krakauer 2003,
+// Motta & Zhang 2018) as a sequence of DFMA kernels.  This is the precision reference
+// of the GPU path; the tensor-core path (step_tc.cu) replaces its contractions.
+#include <algorithm>
+
+#include "state.cuh"
+
+namespace afqmc {
+
+namespace {
+
+__global__ void add_logdet_kernel(const cplx* a, const cplx* b, cplx* out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const cplx s = a[i] + b[i];
+    out[i] = cplx{s.re, atan2(sin(s.im), cos(s.im))};
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+    if (e != cudaSuccess) return fail(AFQMC_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
+
+void add_logdet(const cplx* a, const cplx* b, cplx* out, int n, cudaStream_t st) {
+    add_logdet_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, b, out, n);
+}
+
+// Y[w] = op(X) Phi[w]-style helpers --------------------------------------------------------
+// S_w = Psi^+ Phi_w   (N x N)
+void overlap(const cplx* Psi, const cplx* Phi, cplx* S, int M, int N, int W, cudaStream_t st) {
+    GemmArgs g;
+    g.m = N; g.n = N; g.k = M; g.nb1 = W;
+    g.A.ptr = Psi; g.A.op = OP_C; g.A.ld = N;
+    g.B.ptr = Phi; g.B.op = OP_N; g.B.ld = N; g.B.s1 = (int64_t)M * N;
+    g.C = S; g.ldc = N; g.sc1 = (int64_t)N * N;
+    zgemm(g, st);
+}
+
+}  // namespace
+
+int fp64_alloc(afqmc_walkers* wk) {
+    Fp64Buffers& f = wk->f;
+    const int M = wk->M, W = wk->W, nch = wk->Nchol;
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        const size_t mn = (size_t)M * N;
+        AFQMC_TRY(dalloc(&f.Psi[s], mn));
+        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.Lt[s]), (size_t)nch * mn));
+        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.LtT[s]), (size_t)nch * mn));
+        AFQMC_TRY(dalloc(&f.ht[s], mn));
+        AFQMC_TRY(dalloc(&f.Phi[s], (size_t)W * mn));
+        AFQMC_TRY(dalloc(&f.Pnew[s], (size_t)W * mn));
+        AFQMC_TRY(dalloc(&f.Pa[s], (size_t)W * mn));
+        AFQMC_TRY(dalloc(&f.Pb[s], (size_t)W * mn));
+        AFQMC_TRY(dalloc(&f.S[s], (size_t)W * N * N));
+        AFQMC_TRY(dalloc(&f.ld[s], (size_t)W));
+        AFQMC_TRY(dalloc(&f.Theta[s], (size_t)W * mn));
+        AFQMC_TRY(dalloc(&f.t[s], (size_t)W * nch));
+        AFQMC_TRY(dalloc(&f.X[s], (size_t)W * nch));
+    }
+    AFQMC_TRY(dalloc(&f.Bh, (size_t)M * M));
+    const int Nmax = std::max(wk->N[0], wk->N[1]);
+    const size_t per_n = (size_t)W * Nmax * Nmax * sizeof(cplx);
+    const size_t budget = (size_t)512 << 20;
+    f.nc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nch, budget / std::max<size_t>(per_n, 1)));
+    f.nc = std::min(f.nc, 65535);
+    AFQMC_TRY(dalloc(&f.T, (size_t)f.nc * W * Nmax * Nmax));
+    AFQMC_TRY(dalloc(&f.A, (size_t)W * M * M));
+    return AFQMC_OK;
+}
+
+void fp64_free(afqmc_walkers* wk) {
+    Fp64Buffers& f = wk->f;
+    for (int s = 0; s < 2; ++s) {
+        void* ps[] = {f.Psi[s], f.Lt[s], f.LtT[s], f.ht[s], f.Phi[s], f.Pnew[s], f.Pa[s], f.Pb[s],
+                      f.S[s], f.ld[s], f.Theta[s], f.t[s], f.X[s]};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+    }
+    if (f.Bh) cudaFree(f.Bh);
+    if (f.T) cudaFree(f.T);
+    if (f.A) cudaFree(f.A);
+    f = Fp64Buffers{};
+}
+
+int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
+    Fp64Buffers& f = wk->f;
+    const int M = wk->M, nch = wk->Nchol;
+    const int W = Wm > 0 ? Wm : wk->W;
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        overlap(f.Psi[s], f.Phi[s], f.S[s], M, N, W, st);
+        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], true, wk->flags, st);
+        {   // Theta_w = Phi_w S_w^-1
+            GemmArgs g;
+            g.m = M; g.n = N; g.k = N; g.nb1 = W;
+            g.A.ptr = f.Phi[s]; g.A.ld = N; g.A.s1 = (int64_t)M * N;
+            g.B.ptr = f.S[s]; g.B.ld = N; g.B.s1 = (int64_t)N * N;
+            g.C = f.Theta[s]; g.ldc = N; g.sc1 = (int64_t)M * N;
+            zgemm(g, st);
+        }
+        if (s == 0 && wk->ev0) cudaEventRecord(wk->ev0, st);
+        if (measure) {
+            for (int n0 = 0; n0 < nch; n0 += f.nc) {
+                const int nc = std::min(f.nc, nch - n0);
+                GemmArgs g;   // T[c][w] = Lt_{n0+c} Theta_w
+                g.m = N; g.n = N; g.k = M; g.nb1 = nc; g.nb2 = W;
+                g.A.real = wk->trial_real;
+                g.A.ptr = wk->trial_real
+                              ? (const void*)(static_cast<const double*>(f.Lt[s]) + (int64_t)n0 * N * M)
+                              : (const void*)(static_cast<const cplx*>(f.Lt[s]) + (int64_t)n0 * N * M);
+                g.A.ld = M; g.A.s1 = (int64_t)N * M; g.A.s2 = 0;
+                g.B.ptr = f.Theta[s]; g.B.ld = N; g.B.s1 = 0; g.B.s2 = (int64_t)M * N;
+                g.C = f.T; g.ldc = N; g.sc1 = (int64_t)W * N * N; g.sc2 = (int64_t)N * N;
+                zgemm(g, st);
+                trace_terms(f.T, nc, W, N, n0, f.t[s], f.X[s], nch, st);
+            }
+        } else {
+            // force bias only: t[w][n] = sum_{k,a} Theta_w[k][a] LtT_n[k][a]
+            GemmArgs g;
+            g.m = W; g.n = nch; g.k = M * N;
+            g.A.ptr = f.Theta[s]; g.A.op = OP_N; g.A.ld = (int64_t)M * N;
+            g.B.real = wk->trial_real; g.B.ptr = f.LtT[s]; g.B.op = OP_T; g.B.ld = (int64_t)M * N;
+            g.C = f.t[s]; g.ldc = nch;
+            zgemm(g, st);
+        }
+        if (s == 1 && wk->ev1) { cudaEventRecord(wk->ev1, st); wk->ev_valid = true; }
+    }
+    add_logdet(f.ld[0], f.ld[1], wk->logS_old, W, st);
+    LocalEnergyArgs a;
+    a.W = W; a.M = M; a.Nchol = nch; a.Nup = wk->N[0]; a.Ndn = wk->N[1];
+    for (int s = 0; s < 2; ++s) {
+        a.ht[s] = f.ht[s]; a.Theta[s] = f.Theta[s]; a.t[s] = f.t[s];
+        a.X[s] = measure ? f.X[s] : nullptr;
+    }
+    a.E0 = wk->ham->E0; a.tau = wk->tau;
+    a.fb_cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
+    a.E_L = wk->E_L; a.xbar = wk->xbar; a.flags = wk->flags;
+    local_energy_forcebias(a, st);
+    return AFQMC_OK;
+}
+
+int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st) {
+    Fp64Buffers& f = wk->f;
+    const int M = wk->M, W = wk->W, nch = wk->Nchol;
+    hs_coefficients(x, wk->xbar, wk->weight, W, nch, wk->coef, wk->flags, st);
+    {   // A_w = sum_n c[w][n] L_n
+        GemmArgs g;
+        g.m = W; g.n = M * M; g.k = nch;
+        g.A.ptr = wk->coef; g.A.ld = nch;
+        g.B.ptr = wk->ham->L; g.B.real = true; g.B.ld = (int64_t)M * M;
+        g.C = f.A; g.ldc = (int64_t)M * M;
+        zgemm(g, st);
+    }
+    const double sq = sqrt(wk->tau);
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        const int64_t mn = (int64_t)M * N;
+        cplx* P0 = f.Pa[s];
+        cplx* P1 = f.Pb[s];
+        GemmArgs g;   // P0 = B Phi
+        g.m = M; g.n = N; g.k = M; g.nb1 = W;
+        g.A.ptr = f.Bh; g.A.real = true; g.A.ld = M;
+        g.B.ptr = f.Phi[s]; g.B.ld = N; g.B.s1 = mn;
+        g.C = P0; g.ldc = N; g.sc1 = mn;
+        zgemm(g, st);
+        cudaMemcpyAsync(f.Pnew[s], P0, sizeof(cplx) * W * mn, cudaMemcpyDeviceToDevice, st);
+        for (int k = 1; k <= wk->opts.k_taylor; ++k) {
+            GemmArgs t;   // P1 = (i sqrt(tau) / k) A_w P0 ;  Pnew += P1
+            t.m = M; t.n = N; t.k = M; t.nb1 = W;
+            t.A.ptr = f.A; t.A.ld = M; t.A.s1 = (int64_t)M * M;
+            t.B.ptr = P0; t.B.ld = N; t.B.s1 = mn;
+            t.alpha = cplx{0.0, sq / k};
+            t.C = P1; t.ldc = N; t.sc1 = mn;
+            t.D = f.Pnew[s]; t.ldd = N; t.sd1 = mn;
+            zgemm(t, st);
+            std::swap(P0, P1);
+        }
+        GemmArgs b2;  // Phi' = B Pnew  -> Pa
+        b2.m = M; b2.n = N; b2.k = M; b2.nb1 = W;
+        b2.A.ptr = f.Bh; b2.A.real = true; b2.A.ld = M;
+        b2.B.ptr = f.Pnew[s]; b2.B.ld = N; b2.B.s1 = mn;
+        b2.C = f.Pa[s]; b2.ldc = N; b2.sc1 = mn;
+        zgemm(b2, st);
+        overlap(f.Psi[s], f.Pa[s], f.S[s], M, N, W, st);
+        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, wk->flags, st);
+    }
+    add_logdet(f.ld[0], f.ld[1], wk->logS_new, W, st);
+    WeightArgs a;
+    a.W = W; a.Nchol = nch; a.mode = wk->opts.weight_mode;
+    a.x = x; a.xbar = wk->xbar; a.logS_old = wk->logS_old; a.logS_new = wk->logS_new;
+    a.tau = wk->tau; a.E_T = wk->E_T; a.E0 = wk->ham->E0;
+    a.weight = wk->weight; a.accept = wk->accept;
+    weight_update(a, st);
+    for (int s = 0; s < 2; ++s)
+        commit_walkers(f.Phi[s], f.Pa[s], wk->accept, W, (int64_t)M * wk->N[s], st);
+    return AFQMC_OK;
+}
+
+int fp64_qr(afqmc_walkers* wk, cudaStream_t st) {
+    for (int s = 0; s < 2; ++s)
+        qr_reorthonormalise(wk->f.Phi[s], (int64_t)wk->M * wk->N[s], wk->M, wk->N[s], wk->W, wk->weight, st);
+    return AFQMC_OK;
+}
+
+}  // namespace afqmc

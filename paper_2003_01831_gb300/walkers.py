@@ -1,0 +1,111 @@
+"""Convenience wrapper over the C ABI: one Hamiltonian plus one walker set.
+
+Argument marshalling only -- every step of the method runs in the CUDA
+library (``include/afqmc.h``).  Inputs are numpy arrays on the host; outputs
+come back as numpy arrays.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+
+from . import api
+
+
+class AFQMC:
+    """Owns an ``afqmc_ham_t`` and an ``afqmc_wk_t``; release with ``close()``."""
+
+    def __init__(self, h, L, E0, Psi_up, Psi_dn, W, tau, Phi0=None, precision=api.PREC_FP64,
+                 k_taylor=6, k_qr=5, fb_cap=1.0, weight_mode=api.WEIGHT_PHASELESS, stream=None):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        L = np.ascontiguousarray(L, dtype=np.float64)
+        self.M = h.shape[0]
+        self.Nchol = L.shape[0]
+        self.Psi = [np.ascontiguousarray(Psi_up, dtype=np.complex128),
+                    np.ascontiguousarray(Psi_dn, dtype=np.complex128)]
+        self.N = [self.Psi[0].shape[1], self.Psi[1].shape[1]]
+        self.W = int(W)
+        self.weight_mode = weight_mode
+        self.stream = stream
+        self.ham = api.afqmc_create_hamiltonian(h, L, E0, self.M, self.Nchol, stream)
+        opts = api.afqmc_default_opts()
+        opts.precision = precision
+        opts.k_taylor = k_taylor
+        opts.k_qr = k_qr
+        opts.fb_cap = fb_cap
+        opts.weight_mode = weight_mode
+        phi0 = None
+        if Phi0 is not None:
+            phi0 = np.ascontiguousarray(np.concatenate(
+                [np.asarray(Phi0[0]).reshape(self.W, -1), np.asarray(Phi0[1]).reshape(self.W, -1)], axis=1),
+                dtype=np.complex128)
+        try:
+            self.wk = api.afqmc_init_walkers(self.ham, self.Psi[0], self.Psi[1], self.N[0], self.N[1], self.W,
+                                             phi0, tau, opts, stream)
+        except Exception:
+            api.afqmc_destroy_hamiltonian(self.ham)
+            raise
+
+    # ---------------------------------------------------------------- stepping
+    def step(self, nsteps: int, x: Optional[np.ndarray] = None, seed: int = 0, measure_every: int = 0):
+        """Run nsteps; returns the complex E_mix trace (empty if measure_every == 0)."""
+        nmeas = (nsteps + measure_every - 1) // measure_every if measure_every > 0 else 0
+        trace = np.zeros(max(nmeas, 1), dtype=np.complex128)
+        if x is not None:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            assert x.size == nsteps * self.W * self.Nchol
+        api.afqmc_step(self.wk, nsteps, x, seed, measure_every, trace if nmeas else None, self.stream)
+        return trace[:nmeas]
+
+    def energy(self):
+        """(E_L [W] complex, w [W], logS [W] complex, E_mix complex) at the current walkers."""
+        E_L = np.zeros(self.W, dtype=np.complex128)
+        logS = np.zeros(self.W, dtype=np.complex128)
+        w = np.zeros(self.W, dtype=np.complex128 if self.weight_mode == api.WEIGHT_FREE else np.float64)
+        E = np.zeros(1, dtype=np.complex128)
+        api.afqmc_energy(self.wk, E_L, w, logS, E, self.stream)
+        return E_L, w, logS, E[0]
+
+    def walkers(self):
+        """(Phi_up [W, M, Nup], Phi_dn [W, M, Ndn], w [W], step)."""
+        M, (Nu, Nd) = self.M, self.N
+        Phi = np.zeros((self.W, M * (Nu + Nd)), dtype=np.complex128)
+        w = np.zeros(self.W, dtype=np.complex128 if self.weight_mode == api.WEIGHT_FREE else np.float64)
+        step = api.afqmc_get_walkers(self.wk, Phi, w, self.stream)
+        return Phi[:, :M * Nu].reshape(self.W, M, Nu), Phi[:, M * Nu:].reshape(self.W, M, Nd), w, step
+
+    def set_walkers(self, Phi_up, Phi_dn, w, step: int):
+        Phi = np.ascontiguousarray(np.concatenate(
+            [np.asarray(Phi_up).reshape(self.W, -1), np.asarray(Phi_dn).reshape(self.W, -1)], axis=1),
+            dtype=np.complex128)
+        api.afqmc_set_walkers(self.wk, Phi, np.ascontiguousarray(w), step, self.stream)
+
+    def backward(self, dE=None, dlogS=None, want_L: bool = True):
+        dE = None if dE is None else np.ascontiguousarray(dE, dtype=np.complex128)
+        dlogS = None if dlogS is None else np.ascontiguousarray(dlogS, dtype=np.complex128)
+        dPu = np.zeros((self.M, self.N[0]), dtype=np.complex128)
+        dPd = np.zeros((self.M, self.N[1]), dtype=np.complex128)
+        dL = np.zeros((self.Nchol, self.M, self.M), dtype=np.float64) if want_L else None
+        api.afqmc_energy_backward(self.wk, dE, dlogS, dPu, dPd, dL, self.stream)
+        return dPu, dPd, dL
+
+    def close(self):
+        if getattr(self, "wk", None):
+            api.afqmc_destroy_walkers(self.wk)
+            self.wk = None
+        if getattr(self, "ham", None):
+            api.afqmc_destroy_hamiltonian(self.ham)
+            self.ham = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,71 @@
+"""Host-side checks of the C-ABI library: it builds, loads, exports every symbol
+include/afqmc.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2003_01831_gb300 import api, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.lib()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(afqmc_\w+)\s*\(", src))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "afqmc_step" in names and "afqmc_energy_backward" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(api.EXPORTED) <= names
+
+
+def test_default_opts(lib):
+    o = api.afqmc_default_opts()
+    assert (o.precision, o.k_taylor, o.k_qr, o.weight_mode, o.fb_cap) == (0, 6, 5, 0, 1.0)
+    assert list(o.reserved) == [0] * 8
+
+
+def test_opts_struct_layout_matches_header():
+    # int, int, int, int, double, int[8]
+    assert ctypes.sizeof(api.Opts) == 4 * 4 + 8 + 8 * 4
+
+
+def test_bad_arguments_are_rejected_without_a_gpu(lib):
+    out = ctypes.c_void_p()
+    h = np.zeros((4, 4))
+    L = np.zeros((2, 4, 4))
+    assert lib.afqmc_create_hamiltonian(h.ctypes.data, L.ctypes.data, 0.0, 4, 2, None, None) == -1
+    assert lib.afqmc_create_hamiltonian(None, L.ctypes.data, 0.0, 4, 2, None, ctypes.byref(out)) == -1
+    assert lib.afqmc_create_hamiltonian(h.ctypes.data, L.ctypes.data, 0.0, 0, 2, None, ctypes.byref(out)) == -2
+    assert lib.afqmc_create_hamiltonian(h.ctypes.data, L.ctypes.data, float("nan"), 4, 2, None,
+                                        ctypes.byref(out)) == -4
+    assert b"E0" in lib.afqmc_last_error()
+    assert lib.afqmc_step(None, 1, None, 0, 0, None, None) == -1
+    assert lib.afqmc_energy(None, None, None, None, None, None) == -1
+    assert lib.afqmc_destroy_walkers(None) == -1
+    assert lib.afqmc_destroy_hamiltonian(None) == -1
+    assert lib.afqmc_philox_fields(0, 0, 0, 4, None, None) == -1
+    assert lib.afqmc_init_walkers(None, None, None, 1, 1, 1, None, 0.01, None, None, ctypes.byref(out)) == -1
+
+
+def test_python_binding_raises(lib):
+    with pytest.raises(api.AfqmcError) as e:
+        api.afqmc_create_hamiltonian(np.zeros((2, 2)), np.zeros((1, 2, 2)), 0.0, 0, 1)
+    assert e.value.code == -2
