@@ -50,7 +50,7 @@ def energy_logdet_backward(ham: Hamiltonian, Psi: Sequence[np.ndarray], Phi: Seq
             N = Th.shape[1]
             inner = ham.h @ Th
             U = Th[None, :, :] * c[:, None, None] - np.matmul(Th[None], Ts[s])   # Theta (c_n I - T_n)
-            inner = inner + np.einsum("nik,nka->ia", ham.L, U)
+            inner = inner + np.einsum("nik,nka->ia", ham.L, U, optimize=True)
             FT = (I - Th @ Q) @ inner                                       # dE/dQ^T  [M, N]
             dPsi[s] += gE * FT + gS * Th
             # dE/dL_n: F_n^T = c_n Theta Q - Theta T_n Q

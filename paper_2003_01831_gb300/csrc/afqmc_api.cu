@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -45,6 +46,10 @@ void set_error(int code, const std::string& msg) {
     (void)code;
     g_last_error = msg;
 }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int fail(int code, const std::string& msg) {
     set_error(code, msg);
@@ -252,6 +257,7 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         rc = copy_in(f.Psi[s], psis[s], sizeof(cplx) * M * wk->N[s], st);
         if (rc) return bail(rc);
         check_finite(reinterpret_cast<const double*>(f.Psi[s]), 2LL * M * wk->N[s], wk->flags, st);
+        count_launch();
         max_abs_imag_kernel<<<nblk((int64_t)M * wk->N[s]), 256, 0, st>>>(f.Psi[s], (int64_t)M * wk->N[s],
                                                                           wk->flags + 1);
     }
@@ -282,10 +288,13 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         const int64_t tot = (int64_t)nch * N * M;
         if (wk->trial_real) {
             double* Lr = static_cast<double*>(f.Lt[s]);
+            count_launch();
             cplx_real_part_kernel<<<nblk(tot), 256, 0, st>>>(tmp, Lr, tot);
+            count_launch();
             batched_transpose_kernel<double><<<nblk(tot), 256, 0, st>>>(Lr, static_cast<double*>(f.LtT[s]), nch, N, M);
         } else {
             cudaMemcpyAsync(f.Lt[s], tmp, sizeof(cplx) * tot, cudaMemcpyDeviceToDevice, st);
+            count_launch();
             batched_transpose_kernel<cplx><<<nblk(tot), 256, 0, st>>>(tmp, static_cast<cplx*>(f.LtT[s]), nch, N, M);
         }
         GemmArgs gh;  // ht = Psi^+ h   [N][M]
@@ -399,6 +408,7 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
     AFQMC_TRY(ensure_emix(wk, std::max(nmeas, 1)));
     const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
     wk->ev_valid = false;
+    const long long launches0 = launch_count();
     for (int s = 0; s < nsteps; ++s) {
         const bool meas = measure_every > 0 && s % measure_every == 0;
         AFQMC_TRY(tc ? tc_measure(wk, meas, st) : fp64_measure(wk, meas, st));
@@ -417,6 +427,7 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
         wk->step++;
         if (wk->opts.k_qr > 0 && wk->step % wk->opts.k_qr == 0) AFQMC_TRY(tc ? tc_qr(wk, st) : fp64_qr(wk, st));
     }
+    wk->kernels_per_step = (int)((launch_count() - launches0) / nsteps);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("step: launch failed: ") + cudaGetErrorString(le));
     bool sync = false;

@@ -49,6 +49,10 @@ struct Status {
 void set_error(int code, const std::string& msg);
 int fail(int code, const std::string& msg);  // sets and returns code
 
+// Number of kernels this library has launched (diagnostics: kernels per step).
+void count_launch();
+long long launch_count();
+
 #define AFQMC_CUDA_TRY(expr)                                                                   \
     do {                                                                                        \
         cudaError_t _e = (expr);                                                                \

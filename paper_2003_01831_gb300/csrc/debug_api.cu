@@ -1,0 +1,106 @@
+// Diagnostic entry points (include/afqmc_debug.h): one tensor-core building block per
+// call, host arrays in and out, for isolated parity tests.
+#include <string>
+#include <vector>
+
+#include "../../include/afqmc_debug.h"
+#include "kernels_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace afqmc {
+namespace {
+
+__global__ void split_kernel(const double* src, bf16* hi, bf16* lo, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tc::split_bf16(src[i], hi[i], lo[i]);
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+int upload_split(const double* h, int64_t n, DevBuf& d64, DevBuf& hi, DevBuf& lo) {
+    if (cudaMalloc(&d64.p, n * 8) != cudaSuccess || cudaMalloc(&hi.p, n * 2) != cudaSuccess ||
+        cudaMalloc(&lo.p, n * 2) != cudaSuccess)
+        return fail(AFQMC_ERR_OOM, "debug: allocation");
+    AFQMC_CUDA_TRY(cudaMemcpy(d64.p, h, n * 8, cudaMemcpyHostToDevice));
+    split_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<double*>(d64.p), static_cast<bf16*>(hi.p),
+                                                       static_cast<bf16*>(lo.p), n);
+    return AFQMC_OK;
+}
+
+__global__ void f32_to_f64(const float* s, double* d, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = s[i];
+}
+
+}  // namespace
+}  // namespace afqmc
+
+using namespace afqmc;
+
+extern "C" int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int rows, int cols, int K, int BN,
+                                      double* C) {
+    if (!A || !B || !C || nbatch < 1 || rows < 1 || cols < 1 || K < 8 || K % 8)
+        return fail(AFQMC_ERR_BADARG, "debug_split_gemm: bad arguments");
+    const int64_t na = (int64_t)nbatch * rows * K, nb = (int64_t)nbatch * cols * K, nc = (int64_t)nbatch * rows * cols;
+    DevBuf a64, ahi, alo, b64, bhi, blo, c32, c64, flags;
+    AFQMC_TRY(upload_split(A, na, a64, ahi, alo));
+    AFQMC_TRY(upload_split(B, nb, b64, bhi, blo));
+    if (cudaMalloc(&c32.p, nc * 4) != cudaSuccess || cudaMalloc(&c64.p, nc * 8) != cudaSuccess ||
+        cudaMalloc(&flags.p, 4) != cudaSuccess)
+        return fail(AFQMC_ERR_OOM, "debug: allocation");
+    cudaMemset(flags.p, 0, 4);
+    cudaMemset(c32.p, 0, nc * 4);
+    SplitMat sa, sb;
+    sa.hi = static_cast<bf16*>(ahi.p); sa.lo = static_cast<bf16*>(alo.p);
+    sa.K = K; sa.rows = rows; sa.batch = nbatch; sa.row_stride = K; sa.batch_stride = (int64_t)rows * K;
+    sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
+    sb.K = K; sb.rows = cols; sb.batch = nbatch; sb.row_stride = K; sb.batch_stride = (int64_t)cols * K;
+    EpiParams e;
+    e.kind = EPI_F32;
+    e.rows_valid = rows; e.cols_valid = cols; e.ld = cols; e.ob = (int64_t)rows * cols;
+    e.out_f32 = static_cast<float*>(c32.p);
+    BatchMap bm;
+    if (nbatch > 1) bm = BatchMap{1, nbatch};
+    AFQMC_TRY(tc_gemm(sa, bm, sb, bm, rows, cols, K, nbatch, e, BN, static_cast<unsigned*>(flags.p), 0));
+    f32_to_f64<<<(unsigned)((nc + 255) / 256), 256>>>(static_cast<float*>(c32.p), static_cast<double*>(c64.p), nc);
+    AFQMC_CUDA_TRY(cudaDeviceSynchronize());
+    unsigned fl = 0;
+    AFQMC_CUDA_TRY(cudaMemcpy(&fl, flags.p, 4, cudaMemcpyDeviceToHost));
+    if (fl & FLAG_TIMEOUT) return fail(AFQMC_ERR_TIMEOUT, "debug_split_gemm: device wait timed out");
+    AFQMC_CUDA_TRY(cudaMemcpy(C, c64.p, nc * 8, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, double* t,
+                                  double* X) {
+    if (!Lt || !ThetaT || !t || !X || Nchol < 1 || nws < 1 || M < 64)
+        return fail(AFQMC_ERR_BADARG, "debug_energy: bad arguments");
+    const int64_t na = (int64_t)Nchol * Np * M, nb = (int64_t)nws * 2 * Np * M;
+    DevBuf a64, ahi, alo, b64, bhi, blo, dt, dx, flags;
+    AFQMC_TRY(upload_split(Lt, na, a64, ahi, alo));
+    AFQMC_TRY(upload_split(ThetaT, nb, b64, bhi, blo));
+    const int64_t no = (int64_t)nws * Nchol;
+    if (cudaMalloc(&dt.p, no * 16) != cudaSuccess || cudaMalloc(&dx.p, no * 16) != cudaSuccess ||
+        cudaMalloc(&flags.p, 4) != cudaSuccess)
+        return fail(AFQMC_ERR_OOM, "debug: allocation");
+    cudaMemset(flags.p, 0, 4);
+    SplitMat sa, sb;
+    sa.hi = static_cast<bf16*>(ahi.p); sa.lo = static_cast<bf16*>(alo.p);
+    sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M;
+    sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
+    sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M;
+    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p),
+                        static_cast<unsigned*>(flags.p), 0));
+    AFQMC_CUDA_TRY(cudaDeviceSynchronize());
+    unsigned fl = 0;
+    AFQMC_CUDA_TRY(cudaMemcpy(&fl, flags.p, 4, cudaMemcpyDeviceToHost));
+    if (fl & FLAG_TIMEOUT) return fail(AFQMC_ERR_TIMEOUT, "debug_energy: device wait timed out");
+    AFQMC_CUDA_TRY(cudaMemcpy(t, dt.p, no * 16, cudaMemcpyDeviceToHost));
+    AFQMC_CUDA_TRY(cudaMemcpy(X, dx.p, no * 16, cudaMemcpyDeviceToHost));
+    return AFQMC_OK;
+}

@@ -534,6 +534,7 @@ void zgemm(const GemmArgs& g, cudaStream_t st) {
     if (g.m <= 0 || g.n <= 0) return;
     const int nbatch = g.nb1 * g.nb2;
     dim3 grid((g.n + 63) / 64, (g.m + 63) / 64, std::min(nbatch, 65535));
+    count_launch();
     if (g.A.real && g.B.real) zgemm_kernel<true, true><<<grid, kThreads, 0, st>>>(g);
     else if (g.A.real) zgemm_kernel<true, false><<<grid, kThreads, 0, st>>>(g);
     else if (g.B.real) zgemm_kernel<false, true><<<grid, kThreads, 0, st>>>(g);
@@ -544,63 +545,79 @@ void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* log
                             unsigned* flags, cudaStream_t st) {
     if (count <= 0) return;
     const size_t sm = (size_t)N * (2 * sizeof(cplx) + sizeof(int));
+    count_launch();
     gj_kernel<<<count, kThreads, sm, st>>>(S, stride, N, logdet, with_inverse ? 1 : 0, flags);
 }
 
 void trace_terms(const cplx* T, int nc, int W, int N, int n0, cplx* t_out, cplx* X_out, int64_t ldo,
                  cudaStream_t st) {
     dim3 grid(W, nc);
+    count_launch();
     trace_kernel<<<grid, kThreads, 0, st>>>(T, W, N, n0, t_out, X_out, ldo);
 }
 
 void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st) {
+    count_launch();
     local_energy_kernel<<<a.W, kThreads, 0, st>>>(a);
 }
 
 void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st) {
     const int64_t n = (int64_t)W * ((Nchol + 3) / 4);
+    count_launch();
     philox_kernel<<<blocks_for(n), kThreads, 0, st>>>(seed, step, W, Nchol, x);
 }
 
 void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol, cplx* c,
                      unsigned* flags, cudaStream_t st) {
+    count_launch();
     hs_coeff_kernel<<<blocks_for((int64_t)W * Nchol), kThreads, 0, st>>>(x, xbar, weight, W, Nchol, c, flags);
 }
 
-void weight_update(const WeightArgs& a, cudaStream_t st) { weight_kernel<<<a.W, kThreads, 0, st>>>(a); }
+void weight_update(const WeightArgs& a, cudaStream_t st) {
+    count_launch();
+    weight_kernel<<<a.W, kThreads, 0, st>>>(a);
+}
 
 void commit_walkers(cplx* Phi, const cplx* Phi_new, const int* accept, int W, int64_t per, cudaStream_t st) {
+    count_launch();
     commit_kernel<<<blocks_for((int64_t)W * per), kThreads, 0, st>>>(Phi, Phi_new, accept, W, per);
 }
 
 void qr_reorthonormalise(cplx* Phi, int64_t stride, int M, int N, int W, const cplx* weight,
                          cudaStream_t st) {
     const size_t sm = (size_t)(M + N) * sizeof(cplx);
+    count_launch();
     qr_kernel<<<W, kThreads, sm, st>>>(Phi, stride, M, N, weight);
 }
 
 void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st) {
+    count_launch();
     emix_kernel<<<1, kThreads, 0, st>>>(weight, E_L, W, out);
 }
 
 void fill_cplx(cplx* p, int64_t n, cplx v, cudaStream_t st) {
+    if (n > 0) count_launch();
     if (n > 0) fill_kernel<<<blocks_for(n), kThreads, 0, st>>>(p, n, v);
 }
 
 void replicate(cplx* dst, const cplx* src, int64_t n, int copies, int64_t dst_stride, cudaStream_t st) {
+    count_launch();
     replicate_kernel<<<blocks_for(n * copies), kThreads, 0, st>>>(dst, src, n, copies, dst_stride);
 }
 
 void real_to_cplx(const double* src, cplx* dst, int64_t n, cudaStream_t st) {
+    count_launch();
     r2c_kernel<<<blocks_for(n), kThreads, 0, st>>>(src, dst, n);
 }
 
 void check_finite(const double* p, int64_t n, unsigned* flags, cudaStream_t st) {
+    if (n > 0) count_launch();
     if (n > 0) finite_kernel<<<blocks_for(n), kThreads, 0, st>>>(p, n, flags);
 }
 
 void check_symmetric(const double* L, int M, int Nchol, unsigned* flags, cudaStream_t st) {
     const int64_t n = (int64_t)Nchol * M * M;
+    count_launch();
     sym_kernel<<<blocks_for(n), kThreads, 0, st>>>(L, M, Nchol, flags);
 }
 
@@ -628,6 +645,7 @@ void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp
         g.C = buf + (int64_t)p * M * M; g.ldc = M;
         zgemm(g, st);
     }
+    count_launch();
     hprime_reduce_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(h, buf, parts, M, hp);
     cudaFreeAsync(buf, st);
 }
@@ -658,6 +676,7 @@ int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
     real_to_cplx(X, Y, (int64_t)M * M, st);
     // E = I
     fill_cplx(E, (int64_t)M * M, cplx{0.0, 0.0}, st);
+    count_launch();
     add_identity_kernel<<<blocks_for(M), kThreads, 0, st>>>(E, M, 1.0);
     const int order = 18;
     for (int k = order; k >= 1; --k) {
@@ -669,6 +688,7 @@ int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
         g.alpha = cplx{sc / k, 0.0};
         g.C = Tm; g.ldc = M;
         zgemm(g, st);
+        count_launch();
         add_identity_kernel<<<blocks_for(M), kThreads, 0, st>>>(Tm, M, 1.0);
         std::swap(E, Tm);
     }
@@ -681,6 +701,7 @@ int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
         zgemm(g, st);
         std::swap(E, Tm);
     }
+    count_launch();
     c2r_scale_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(E, out, (int64_t)M * M);
     cudaFreeAsync(Y, st);
     cudaFreeAsync(E, st);

@@ -1,0 +1,693 @@
+// tcgen05 + TMA split-precision GEMM engine for sm_103a.
+//
+// Every dense contraction of the mixed-precision walker step (overlap Psi^+ Phi, Green's
+// function Phi S^-1, the Cholesky energy contraction Ltilde_n Theta, the HS potential
+// sum_n c_n L_n, the Taylor terms A^k Phi and the one-body factors B Phi; Sec. V and the
+// phaseless algorithm it cites) is a real GEMM C = A B^T on K-major bf16 operands stored as
+// (hi, lo) pairs: x ~= hi + lo, C ~= Ahi Bhi + Ahi Blo + Alo Bhi, accumulated in fp32 in
+// tensor memory.  Complex products are split into real GEMMs by the operand layouts
+// (planar or "doubled" [[Re, -Im], [Im, Re]] operands) chosen by the step driver.
+//
+// Kernel structure (one CTA per SM, persistent over output tiles):
+//   warp 0      TMA producer: 64-wide K chunks of A (128 rows) and B (BN rows), hi and lo,
+//               into a ring of shared-memory stages (128-byte swizzle).
+//   warp 1      allocates tensor memory and issues tcgen05.mma (M=128, N=BN, K=16), three
+//               per 16-wide K slice, into one of two TMEM accumulators.
+//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns at a time and write the tile.
+// Every wait is bounded; on timeout the kernel sets FLAG_TIMEOUT, drains what it issued,
+// frees tensor memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kernels_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace afqmc {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;  // bf16 elements per K chunk (128 bytes)
+constexpr int kGemmThreads = 192;
+
+template <int BN>
+struct Cfg {
+    static constexpr int kStages = BN == 256 ? 2 : 3;
+    static constexpr int kABytes = kBM * kBK * 2;  // one plane
+    static constexpr int kBBytes = BN * kBK * 2;
+    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+    static constexpr int kTmemCols = 2 * BN;
+};
+
+struct TileShape {
+    int64_t rows, cols, K;
+    int nbatch;
+    int rt, ct;      // row / column tiles per batch
+    int nk;          // K chunks
+    int64_t tiles;
+    BatchMap am, bm;
+};
+
+struct SharedCtl {
+    uint64_t full[4];
+    uint64_t empty[4];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t done;
+    uint32_t tmem_base;
+    int abort;
+    double red[8][4];   // energy epilogue: per-warp (t.re, t.im, X.re, X.im)
+};
+
+__device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kTimeoutCycles) return false;
+    return true;
+}
+
+// --------------------------------------------------------------------------- epilogues
+__device__ __forceinline__ void store_split(bf16* hi, bf16* lo, int64_t idx, float v) {
+    bf16 h, l;
+    split_bf16(v, h, l);
+    hi[idx] = h;
+    lo[idx] = l;
+}
+
+// Writes 32 consecutive output columns [c0, c0+32) of row r (per batch b).
+__device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, const float (&v)[32]) {
+    if (r >= e.rows_valid) return;
+    const int ncol = (int)(e.cols_valid - c0 < 32 ? e.cols_valid - c0 : 32);
+    if (ncol <= 0) return;
+    switch (e.kind) {
+        case EPI_F32: {
+            float* o = e.out_f32 + b * e.ob + r * e.ld + c0;
+            for (int j = 0; j < ncol; ++j) o[j] = v[j];
+            break;
+        }
+        case EPI_SPLIT: {
+            const int64_t base = b * e.ob + r * e.ld + c0;
+            for (int j = 0; j < ncol; ++j) store_split(e.out_hi, e.out_lo, base + j, v[j]);
+            break;
+        }
+        case EPI_HSPOT: {
+            // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
+            const int64_t w = r >> 1, c = r & 1;
+            for (int j = 0; j < ncol; ++j) {
+                const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
+                store_split(e.out_hi, e.out_lo, (w * e.M + i) * (2 * e.M) + c * e.M + k, v[j]);
+            }
+            break;
+        }
+        case EPI_BFIRST: {
+            // row r = ((w*2 + s)*2 + c)*N + j over all walkers; P_c[j][i] for i in [c0, c0+32)
+            const int64_t N = e.N, M = e.M;
+            const int64_t ws = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
+            const int64_t re_row = (ws * 2 + 0) * N + jj, im_row = (ws * 2 + 1) * N + jj;
+            for (int j = 0; j < ncol; ++j) {
+                const int64_t i = c0 + j;
+                const float p = v[j];
+                e.acc[r * M + i] = p;
+                if (c == 0) {
+                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + i, p);
+                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + M + i, p);
+                } else {
+                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + M + i, -p);
+                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + i, p);
+                }
+            }
+            break;
+        }
+        case EPI_TAYLOR: {
+            // batch b = walker; row r = (s*2 + c)*N + j; C = (P A^T)_c[j][i]; new = i*scale*C
+            const int64_t N = e.N, M = e.M;
+            const int64_t s = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
+            const int64_t ws = (int64_t)b * 2 + s;
+            const int64_t re_row = (ws * 2 + 0) * N + jj, im_row = (ws * 2 + 1) * N + jj;
+            const float sc = e.scale;
+            for (int j = 0; j < ncol; ++j) {
+                const int64_t i = c0 + j;
+                if (c == 0) {  // C_re -> new_im = sc * C_re
+                    const float ni = sc * v[j];
+                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + M + i, -ni);
+                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + i, ni);
+                    e.acc[im_row * M + i] += ni;
+                } else {       // C_im -> new_re = -sc * C_im
+                    const float nr = -sc * v[j];
+                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + i, nr);
+                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + M + i, nr);
+                    e.acc[re_row * M + i] += nr;
+                }
+            }
+            break;
+        }
+        case EPI_BFINAL: {
+            const int64_t base = r * e.ld + c0;
+            for (int j = 0; j < ncol; ++j) {
+                e.out_f64[base + j] = (double)v[j];
+                store_split(e.out_hi, e.out_lo, base + j, v[j]);
+            }
+            break;
+        }
+        default:
+            break;
+    }
+}
+
+__device__ __forceinline__ void tile_coords(const TileShape& s, int64_t t, int& b, int& rt, int& ct) {
+    const int64_t per = (int64_t)s.rt * s.ct;
+    b = (int)(t / per);
+    const int64_t rem = t % per;
+    ct = (int)(rem / s.rt);
+    rt = (int)(rem % s.rt);
+}
+
+// --------------------------------------------------------------------------- mainloop roles
+template <int BN>
+__device__ __forceinline__ uint8_t* stage_ptr(uint8_t* base, int st) {
+    return base + (size_t)st * Cfg<BN>::kStageBytes;
+}
+
+template <int BN, typename TileFn>
+__device__ void producer_loop(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
+                              const CUtensorMap* tBh, const CUtensorMap* tBl, int64_t ntiles, int nk, TileFn coords,
+                              bool a3d, bool b3d) {
+    using C = Cfg<BN>;
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int ax, ay, az, bx, by, bz;
+        coords(t, ay, az, by, bz);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
+            if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
+            uint8_t* s = stage_ptr<BN>(sbase, st);
+            mbar_arrive_expect_tx(&ctl->full[st], C::kStageBytes);
+            ax = bx = kb * kBK;
+            if (a3d) {
+                tma_load_3d(s, tAh, &ctl->full[st], ax, ay, az);
+                tma_load_3d(s + C::kABytes, tAl, &ctl->full[st], ax, ay, az);
+            } else {
+                tma_load_2d(s, tAh, &ctl->full[st], ax, ay);
+                tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], ax, ay);
+            }
+            if (b3d) {
+                tma_load_3d(s + 2 * C::kABytes, tBh, &ctl->full[st], bx, by, bz);
+                tma_load_3d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], bx, by, bz);
+            } else {
+                tma_load_2d(s + 2 * C::kABytes, tBh, &ctl->full[st], bx, by);
+                tma_load_2d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], bx, by);
+            }
+        }
+    }
+    if (!ok) {
+        // drain: wait (bounded) for the copies of the last stages still in flight
+        const int64_t first = g > C::kStages ? g - C::kStages : 0;
+        for (int64_t j = first; j < g; ++j)
+            wait_drain(&ctl->full[j % C::kStages], (uint32_t)((j / C::kStages) & 1));
+    }
+}
+
+template <int BN>
+__device__ void mma_loop(uint8_t* sbase, SharedCtl* ctl, int64_t ntiles, int nk) {
+    using C = Cfg<BN>;
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    const uint32_t tmem = ctl->tmem_base;
+    int64_t g = 0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t u = (uint32_t)(it >> 1);
+        if (!mbar_wait(&ctl->tempty[acc], (u & 1u) ^ 1u, &ctl->abort)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
+            if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(stage_ptr<BN>(sbase, st));
+            const uint32_t sal = sa + C::kABytes;
+            const uint32_t sb = sa + 2 * C::kABytes;
+            const uint32_t sbl = sb + C::kBBytes;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint64_t ah = desc_sw128(sa + off), al = desc_sw128(sal + off);
+                const uint64_t bh = desc_sw128(sb + off), bl = desc_sw128(sbl + off);
+                mma_bf16(d, ah, bh, idesc, (kb | kk) != 0 ? 1u : 0u);
+                mma_bf16(d, ah, bl, idesc, 1u);
+                mma_bf16(d, al, bh, idesc, 1u);
+            }
+            mma_commit(&ctl->empty[st]);
+        }
+        if (!ok) break;
+        mma_commit(&ctl->tfull[acc]);
+    }
+    // make sure nothing this thread issued is still running before TMEM is released
+    mma_commit(&ctl->done);
+    wait_drain(&ctl->done, 0);
+}
+
+// Epilogue-warp wait: lane 0 polls, the warp follows.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    return ok != 0;
+}
+
+// --------------------------------------------------------------------------- generic GEMM
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, TileShape sh,
+                   EpiParams epi, unsigned* flags) {
+    using C = Cfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(sbase + C::kStages * C::kStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::kStages; ++i) {
+            mbar_init(&ctl->full[i], 1);
+            mbar_init(&ctl->empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->tfull[i], 1);
+            mbar_init(&ctl->tempty[i], 128);
+        }
+        mbar_init(&ctl->done, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&ctl->tmem_base, C::kTmemCols);
+        tmem_relinquish();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&tAh);
+        tma_prefetch_desc(&tAl);
+        tma_prefetch_desc(&tBh);
+        tma_prefetch_desc(&tBl);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const bool a3d = sh.am.mod != (1 << 30) || sh.nbatch > 1;
+    if (warp == 0) {
+        if (lane == 0) {
+            auto coords = [&](int64_t t, int& ay, int& az, int& by, int& bz) {
+                int b, rt, ct;
+                tile_coords(sh, t, b, rt, ct);
+                ay = rt * kBM;
+                az = (b / sh.am.div) % sh.am.mod;
+                by = ct * BN;
+                bz = (b / sh.bm.div) % sh.bm.mod;
+            };
+            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, sh.tiles, sh.nk, coords, a3d, a3d);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) mma_loop<BN>(sbase, ctl, sh.tiles, sh.nk);
+    } else {
+        const int g4 = warp & 3;
+        const uint32_t lane_base = (uint32_t)(g4 * 32) << 16;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < sh.tiles; t += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t u = (uint32_t)(it >> 1);
+            if (!warp_wait(&ctl->tfull[acc], u & 1u, &ctl->abort)) break;
+            tc_fence_after();
+            int b, rt, ct;
+            tile_coords(sh, t, b, rt, ct);
+            const int64_t r = (int64_t)rt * kBM + g4 * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(ctl->tmem_base + lane_base + (uint32_t)(acc * BN + c * 32), v);
+                epilogue_row(epi, b, r, (int64_t)ct * BN + c * 32, v);
+            }
+            tc_fence_before();
+            mbar_arrive(&ctl->tempty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(ctl->tmem_base, C::kTmemCols);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+// --------------------------------------------------------------------------- energy kernel
+// Tiles: (n-group of G = 128/Np Cholesky vectors) x (group of G walker-spin pairs).
+// Accumulator columns of one ws: [re b = 0..Np) [im b = 0..Np).
+struct EnergyShape {
+    int Np, Q, G;
+    int Nchol, nws;
+    int n_groups, ws_groups;
+    int ws_super;     // ws groups per L2 super-block
+    int64_t tiles;
+    int nk;
+    cplx* t_out;
+    cplx* X_out;
+};
+
+__device__ __forceinline__ void energy_tile(const EnergyShape& s, int64_t t, int& ng, int& wg) {
+    const int64_t per_super = (int64_t)s.ws_super * s.n_groups;
+    const int64_t sup = t / per_super;
+    const int64_t rem = t % per_super;
+    const int64_t first = sup * s.ws_super;
+    const int width = (int)(s.ws_groups - first < s.ws_super ? s.ws_groups - first : s.ws_super);
+    ng = (int)(rem / width);
+    wg = (int)(first + rem % width);
+}
+
+__device__ __forceinline__ void named_bar_epi() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// AND of `pred` over the 128 epilogue threads (named barrier 1).
+__device__ __forceinline__ int named_bar_and(int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred)
+        : "memory");
+    return r;
+}
+
+template <int Np>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tc_energy_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                     const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+                     EnergyShape es, unsigned* flags) {
+    constexpr int BN = 256;
+    constexpr int Q = Np / 32;
+    constexpr int G = 128 / Np;
+    constexpr int kSlotFloats = 2 * 32 * 33;  // re, im planes of a padded 32 x 32 block
+    using C = Cfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* xch = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(xch + 4 * kSlotFloats);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::kStages; ++i) {
+            mbar_init(&ctl->full[i], 1);
+            mbar_init(&ctl->empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&ctl->tfull[i], 1);
+            mbar_init(&ctl->tempty[i], 128);
+        }
+        mbar_init(&ctl->done, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&ctl->tmem_base, C::kTmemCols);
+        tmem_relinquish();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&tAh);
+        tma_prefetch_desc(&tAl);
+        tma_prefetch_desc(&tBh);
+        tma_prefetch_desc(&tBl);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            auto coords = [&](int64_t t, int& ay, int& az, int& by, int& bz) {
+                int ng, wg;
+                energy_tile(es, t, ng, wg);
+                ay = ng * 128;
+                by = wg * 256;
+                az = bz = 0;
+            };
+            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es.tiles, es.nk, coords, false, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) mma_loop<BN>(sbase, ctl, es.tiles, es.nk);
+    } else {
+        const int g4 = warp & 3;               // row sub-block: rows 32*g4 .. +31
+        const int i_blk = g4 / Q;              // n within the group
+        const int mu = g4 % Q;                 // sub-block index inside the Np x Np block
+        const uint32_t lane_base = (uint32_t)(g4 * 32) << 16;
+        float* my_slot = xch + g4 * kSlotFloats;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t u = (uint32_t)(it >> 1);
+            const bool got = warp_wait(&ctl->tfull[acc], u & 1u, &ctl->abort);
+            if (!named_bar_and(got ? 1 : 0)) break;   // all four warps leave together
+            tc_fence_after();
+            int ng, wg;
+            energy_tile(es, t, ng, wg);
+            const uint32_t tbase = ctl->tmem_base + lane_base + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int j = 0; j < G; ++j) {
+                double tr = 0.0, ti = 0.0, xr = 0.0, xi = 0.0;
+#pragma unroll 1
+                for (int rho = 0; rho < Q; ++rho) {
+                    const int wsub = (mu - rho + Q) % Q;   // sub-block I publish
+                    const int beta = (mu + rho) % Q;       // partner sub-block I read
+                    float vr[32], vi[32];
+                    // publish T[my rows][block wsub] (re, im) for the warp that needs it
+                    tmem_ld32(tbase + (uint32_t)(j * 2 * Np + 32 * wsub), vr);
+                    tmem_ld32(tbase + (uint32_t)(j * 2 * Np + Np + 32 * wsub), vi);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        my_slot[lane * 33 + q] = vr[q];
+                        my_slot[32 * 33 + lane * 33 + q] = vi[q];
+                    }
+                    named_bar_epi();
+                    if (beta != wsub) {
+                        tmem_ld32(tbase + (uint32_t)(j * 2 * Np + 32 * beta), vr);
+                        tmem_ld32(tbase + (uint32_t)(j * 2 * Np + Np + 32 * beta), vi);
+                    }
+                    const float* ps = xch + (i_blk * Q + beta) * kSlotFloats;
+                    float ar = 0.f, ai = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const float pr = ps[q * 33 + lane], pi = ps[32 * 33 + q * 33 + lane];
+                        ar = fmaf(vr[q], pr, fmaf(-vi[q], pi, ar));
+                        ai = fmaf(vr[q], pi, fmaf(vi[q], pr, ai));
+                    }
+                    xr += ar;
+                    xi += ai;
+                    if (rho == 0) {
+                        // diagonal element T[a][a] sits in column `lane` of my own block
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            if (q == lane) { tr += vr[q]; ti += vi[q]; }
+                    }
+                    named_bar_epi();
+                }
+                // warp reduction, then across the Q warps of this n
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    tr += __shfl_xor_sync(0xffffffffu, tr, o);
+                    ti += __shfl_xor_sync(0xffffffffu, ti, o);
+                    xr += __shfl_xor_sync(0xffffffffu, xr, o);
+                    xi += __shfl_xor_sync(0xffffffffu, xi, o);
+                }
+                if (lane == 0) {
+                    ctl->red[g4][0] = tr;
+                    ctl->red[g4][1] = ti;
+                    ctl->red[g4][2] = xr;
+                    ctl->red[g4][3] = xi;
+                }
+                named_bar_epi();
+                if (mu == 0 && lane == 0) {
+                    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                    for (int q = 0; q < Q; ++q) {
+                        s0 += ctl->red[i_blk * Q + q][0];
+                        s1 += ctl->red[i_blk * Q + q][1];
+                        s2 += ctl->red[i_blk * Q + q][2];
+                        s3 += ctl->red[i_blk * Q + q][3];
+                    }
+                    const int n = ng * G + i_blk;
+                    const int ws = wg * G + j;
+                    if (n < es.Nchol && ws < es.nws) {
+                        es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
+                        es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
+                    }
+                }
+                named_bar_epi();
+            }
+            tc_fence_before();
+            mbar_arrive(&ctl->tempty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(ctl->tmem_base, C::kTmemCols);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+// --------------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 3-D map over [batch][rows][K] bf16 with box {64, box_rows, 1} and 128-byte swizzle.
+int make_map(CUtensorMap* m, const bf16* base, int64_t K, int64_t rows, int64_t batch, int64_t row_stride,
+             int64_t batch_stride, int box_rows, bool three_d) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_stride * 2) % 16 || (batch_stride * 2) % 16)
+        return fail(AFQMC_ERR_SHAPE, "tensor map: base/stride not 16-byte aligned");
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)std::max<int64_t>(batch, 1)};
+    cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 2), (cuuint64_t)(batch_stride * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, three_d ? 3 : 2, const_cast<bf16*>(base), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return AFQMC_OK;
+}
+
+template <int BN>
+size_t gemm_smem() {
+    return 1024 + (size_t)Cfg<BN>::kStages * Cfg<BN>::kStageBytes + sizeof(SharedCtl);
+}
+
+size_t energy_smem() { return 1024 + (size_t)Cfg<256>::kStages * Cfg<256>::kStageBytes + 4 * 2 * 32 * 33 * 4 + sizeof(SharedCtl); }
+
+int g_num_sms = 0;
+
+}  // namespace
+
+int tc_num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, int64_t rows, int64_t cols,
+            int64_t K, int nbatch, const EpiParams& epi, int BN, unsigned* flags, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || K <= 0 || nbatch <= 0) return AFQMC_OK;
+    if (BN != 128 && BN != 256) return fail(AFQMC_ERR_BADARG, "tc_gemm: BN must be 128 or 256");
+    const bool three_d = nbatch > 1 || amap.mod != (1 << 30);
+    CUtensorMap m[4];
+    AFQMC_TRY(make_map(&m[0], A.hi, A.K, A.rows, A.batch, A.row_stride, A.batch_stride, kBM, three_d));
+    AFQMC_TRY(make_map(&m[1], A.lo, A.K, A.rows, A.batch, A.row_stride, A.batch_stride, kBM, three_d));
+    AFQMC_TRY(make_map(&m[2], B.hi, B.K, B.rows, B.batch, B.row_stride, B.batch_stride, BN, three_d));
+    AFQMC_TRY(make_map(&m[3], B.lo, B.K, B.rows, B.batch, B.row_stride, B.batch_stride, BN, three_d));
+    TileShape sh;
+    sh.rows = rows;
+    sh.cols = cols;
+    sh.K = K;
+    sh.nbatch = nbatch;
+    sh.rt = (int)((rows + kBM - 1) / kBM);
+    sh.ct = (int)((cols + BN - 1) / BN);
+    sh.nk = (int)((K + kBK - 1) / kBK);
+    sh.tiles = (int64_t)sh.rt * sh.ct * nbatch;
+    sh.am = amap;
+    sh.bm = bmap;
+    if (!three_d) {
+        sh.am = BatchMap{1, 1 << 30};
+        sh.bm = BatchMap{1, 1 << 30};
+    }
+    const int grid = (int)std::min<int64_t>(sh.tiles, tc_num_sms());
+    if (BN == 256) {
+        const size_t sm = gemm_smem<256>();
+        cudaFuncSetAttribute(tc_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        count_launch();
+        tc_gemm_kernel<256><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], sh, epi, flags);
+    } else {
+        const size_t sm = gemm_smem<128>();
+        cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        count_launch();
+        tc_gemm_kernel<128><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], sh, epi, flags);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_gemm launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
+
+int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
+              cplx* X_out, unsigned* flags, cudaStream_t st) {
+    if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
+    if (M % kBK) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64");
+    CUtensorMap m[4];
+    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false));
+    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false));
+    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false));
+    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false));
+    EnergyShape es;
+    es.Np = Np;
+    es.Q = Np / 32;
+    es.G = 128 / Np;
+    es.Nchol = Nchol;
+    es.nws = nws;
+    es.n_groups = (Nchol + es.G - 1) / es.G;
+    es.ws_groups = (nws + es.G - 1) / es.G;
+    es.ws_super = std::min(es.ws_groups, 128);
+    es.tiles = (int64_t)es.n_groups * es.ws_groups;
+    es.nk = M / kBK;
+    es.t_out = t_out;
+    es.X_out = X_out;
+    const int grid = (int)std::min<int64_t>(es.tiles, tc_num_sms());
+    const size_t sm = energy_smem();
+    cudaError_t e;
+    switch (Np) {
+        case 32:
+            cudaFuncSetAttribute(tc_energy_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            count_launch();
+            tc_energy_kernel<32><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
+            break;
+        case 64:
+            cudaFuncSetAttribute(tc_energy_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            count_launch();
+            tc_energy_kernel<64><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
+            break;
+        default:
+            cudaFuncSetAttribute(tc_energy_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            count_launch();
+            tc_energy_kernel<128><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
+            break;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
+
+}  // namespace afqmc

@@ -1,0 +1,67 @@
+// Tensor-core (tcgen05 + TMA) split-precision GEMMs of the mixed-precision walker step.
+// Internal to the library.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace afqmc {
+
+using bf16 = __nv_bfloat16;
+
+// A K-major bf16 matrix stored as two planes (hi, lo) of identical layout
+// [batch][rows][K] with the given element strides.  The tensor-core kernels read
+// (hi, lo) pairs and form hi*hi + hi*lo + lo*hi.
+struct SplitMat {
+    const bf16* hi = nullptr;
+    const bf16* lo = nullptr;
+    int64_t K = 0, rows = 0, batch = 1;
+    int64_t row_stride = 0;    // elements between rows (>= K, multiple of 8)
+    int64_t batch_stride = 0;  // elements between batches
+};
+
+// Which batch coordinate each operand uses: z = (batch / div) % mod.
+struct BatchMap {
+    int div = 1;
+    int mod = 1 << 30;
+};
+
+// Output tile epilogues of the generic GEMM (kind selects the write pattern).
+enum EpiKind : int {
+    EPI_F32 = 0,       // out_f32[b*ob + r*ld + c]
+    EPI_SPLIT = 1,     // out_hi/out_lo[b*ob + r*ld + c]  (bf16 pair)
+    EPI_HSPOT = 2,     // A potential: row (w, c), col (i, k) -> hi/lo[w][i][c*M + k]
+    EPI_BFIRST = 3,    // B Phi: doubled operand for the Taylor series + accumulator init
+    EPI_TAYLOR = 4,    // (i s) P A^T: doubled operand of the next term + accumulator update
+    EPI_BFINAL = 5,    // B P: FP64 walker + its bf16 pair
+};
+
+struct EpiParams {
+    int kind = EPI_F32;
+    int64_t rows_valid = 0, cols_valid = 0;  // per batch
+    int64_t ld = 0, ob = 0;                  // row / batch strides of the output (elements)
+    float* out_f32 = nullptr;
+    bf16* out_hi = nullptr;
+    bf16* out_lo = nullptr;
+    double* out_f64 = nullptr;
+    float* acc = nullptr;                    // Taylor accumulator (fp32)
+    int M = 0, N = 0;                        // orbitals, electrons per spin
+    float scale = 1.0f;                      // Taylor factor sqrt(tau)/k
+};
+
+// C[b] = A[b] . B[b]^T (split-3 bf16, fp32 accumulation in TMEM), 128 x BN tiles.
+int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, int64_t rows, int64_t cols,
+            int64_t K, int nbatch, const EpiParams& epi, int BN, unsigned* flags, cudaStream_t st);
+
+// Fused energy contraction: T_{n,ws} = Lt_n Theta_ws^T (Np x Np complex, Np | 128) for
+// all n and walker-spin pairs ws; emits t = Tr T and X = Tr(T T) per (ws, n) into
+// t_out/X_out [nws][Nchol] (complex FP64).  Lt: [Nchol*Np][M], ThetaT: [nws*2*Np][M]
+// (rows (ws, re/im, b)).
+int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
+              cplx* X_out, unsigned* flags, cudaStream_t st);
+
+int tc_num_sms();
+
+}  // namespace afqmc

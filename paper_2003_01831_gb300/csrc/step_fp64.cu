@@ -25,6 +25,7 @@ int dalloc(T** p, size_t count) {
 }
 
 void add_logdet(const cplx* a, const cplx* b, cplx* out, int n, cudaStream_t st) {
+    count_launch();
     add_logdet_kernel<<<(n + 255) / 256, 256, 0, st>>>(a, b, out, n);
 }
 

@@ -45,6 +45,8 @@ class AFQMC:
                                              phi0, tau, opts, stream)
         except Exception:
             api.afqmc_destroy_hamiltonian(self.ham)
+            self.ham = None
+            self.wk = None
             raise
 
     # ---------------------------------------------------------------- stepping
