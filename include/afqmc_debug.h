@@ -15,20 +15,36 @@ extern "C" {
 #endif
 
 /* C[b] = A[b] B[b]^T for A [nbatch][rows][K], B [nbatch][cols][K] (float64, host), computed
- * by the tcgen05 split-bf16 GEMM (each operand rounded to a bf16 hi + lo pair, three
- * products, fp32 accumulation) and returned as float64 C [nbatch][rows][cols].
- * BN = 128 or 256 (tile width).  K must be a multiple of 8.  This is the contraction
- * primitive behind every dense product of the step (Sec. V; Table II costs). */
+ * by the tcgen05 split-bf16 GEMM and returned as float64 C [nbatch][rows][cols].
+ * exact = 0: plain split (hi = bf16(x), lo = bf16(x - hi)), all three products in one fp32
+ *            accumulator; BN = 128 or 256.
+ * exact = 1: row-scaled split (hi an integer in [-128, 128] times a per-row power of two),
+ *            hi*hi summed exactly in its own accumulator; BN must be 128 and K <= 1024.
+ * K must be a multiple of 8.  This is the contraction primitive behind every dense product
+ * of the step (Sec. V; Table II costs). */
 int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int rows, int cols, int K, int BN,
-                           double* C);
+                           int exact, double* C);
 
-/* The fused energy contraction on its own: for Lt [Nchol][Np][M] (real) and walker-spin
+/* The fused energy contraction on its own (row-scaled operands, exact leading product):
+ * for Lt [Nchol][Np][M] (real) and walker-spin
  * Green's functions ThetaT [nws][2][Np][M] (re plane then im plane of Theta^T), returns
  * t [nws][Nchol] = Tr(Lt_n Theta_ws) and X [nws][Nchol] = Tr((Lt_n Theta_ws)^2) as complex
  * (interleaved float64).  Np in {32, 64, 128}, M % 64 == 0.  These traces give the force
  * bias and the Coulomb / exchange energies of the mixed estimator. */
 int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, double* t,
                        double* X);
+
+/* Intermediates of one measurement of a BF16X3 walker set (wk from afqmc_init_walkers with
+ * AFQMC_PREC_BF16X3): runs the overlap / Green's function / energy contractions on the
+ * current walkers and copies out, as float64 (host pointers, any may be NULL):
+ *   ST     [W][2][2][N][N]  overlap transposed, planar: ST[w][s][c][b][a] = (re|im) S[a][b]
+ *   Sinv   [W][2][N][N]     complex inverse of S
+ *   ThetaT [W][2][2][N][M]  Theta^T per walker, spin, re/im plane (Theta = Phi (Psi^T Phi)^-1)
+ *   t, X   [W][2][Nchol]    complex traces Tr(Ltilde_n Theta), Tr((Ltilde_n Theta)^2)
+ *   E1     [W]              complex one-body energy sum_s Tr(Psi_s^T h Theta_s) */
+typedef struct afqmc_walkers* afqmc_wk_debug_t;
+int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X,
+                            double* E1);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,7 @@
 
 #include "../../include/afqmc_debug.h"
 #include "kernels_tc.cuh"
+#include "state.cuh"
 #include "tc_ptx.cuh"
 
 namespace afqmc {
@@ -22,13 +23,20 @@ struct DevBuf {
     }
 };
 
-int upload_split(const double* h, int64_t n, DevBuf& d64, DevBuf& hi, DevBuf& lo) {
+// Upload n = rows * K values; plain split, or row-scaled split when sc is given.
+int upload_split(const double* h, int64_t rows, int64_t K, DevBuf& d64, DevBuf& hi, DevBuf& lo, DevBuf* sc) {
+    const int64_t n = rows * K;
     if (cudaMalloc(&d64.p, n * 8) != cudaSuccess || cudaMalloc(&hi.p, n * 2) != cudaSuccess ||
-        cudaMalloc(&lo.p, n * 2) != cudaSuccess)
+        cudaMalloc(&lo.p, n * 2) != cudaSuccess || (sc && cudaMalloc(&sc->p, rows * 4) != cudaSuccess))
         return fail(AFQMC_ERR_OOM, "debug: allocation");
     AFQMC_CUDA_TRY(cudaMemcpy(d64.p, h, n * 8, cudaMemcpyHostToDevice));
-    split_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<double*>(d64.p), static_cast<bf16*>(hi.p),
-                                                       static_cast<bf16*>(lo.p), n);
+    if (sc) {
+        split_rows(static_cast<double*>(d64.p), K, rows, K, static_cast<bf16*>(hi.p), static_cast<bf16*>(lo.p),
+                   static_cast<float*>(sc->p), 0);
+    } else {
+        split_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<double*>(d64.p), static_cast<bf16*>(hi.p),
+                                                           static_cast<bf16*>(lo.p), n);
+    }
     return AFQMC_OK;
 }
 
@@ -43,13 +51,13 @@ __global__ void f32_to_f64(const float* s, double* d, int64_t n) {
 using namespace afqmc;
 
 extern "C" int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int rows, int cols, int K, int BN,
-                                      double* C) {
+                                      int exact, double* C) {
     if (!A || !B || !C || nbatch < 1 || rows < 1 || cols < 1 || K < 8 || K % 8)
         return fail(AFQMC_ERR_BADARG, "debug_split_gemm: bad arguments");
     const int64_t na = (int64_t)nbatch * rows * K, nb = (int64_t)nbatch * cols * K, nc = (int64_t)nbatch * rows * cols;
-    DevBuf a64, ahi, alo, b64, bhi, blo, c32, c64, flags;
-    AFQMC_TRY(upload_split(A, na, a64, ahi, alo));
-    AFQMC_TRY(upload_split(B, nb, b64, bhi, blo));
+    DevBuf a64, ahi, alo, b64, bhi, blo, c32, c64, flags, asc, bsc;
+    AFQMC_TRY(upload_split(A, na / K, K, a64, ahi, alo, exact ? &asc : nullptr));
+    AFQMC_TRY(upload_split(B, nb / K, K, b64, bhi, blo, exact ? &bsc : nullptr));
     if (cudaMalloc(&c32.p, nc * 4) != cudaSuccess || cudaMalloc(&c64.p, nc * 8) != cudaSuccess ||
         cudaMalloc(&flags.p, 4) != cudaSuccess)
         return fail(AFQMC_ERR_OOM, "debug: allocation");
@@ -58,15 +66,17 @@ extern "C" int afqmc_debug_split_gemm(const double* A, const double* B, int nbat
     SplitMat sa, sb;
     sa.hi = static_cast<bf16*>(ahi.p); sa.lo = static_cast<bf16*>(alo.p);
     sa.K = K; sa.rows = rows; sa.batch = nbatch; sa.row_stride = K; sa.batch_stride = (int64_t)rows * K;
+    sa.scale = exact ? static_cast<float*>(asc.p) : nullptr;
     sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
     sb.K = K; sb.rows = cols; sb.batch = nbatch; sb.row_stride = K; sb.batch_stride = (int64_t)cols * K;
+    sb.scale = exact ? static_cast<float*>(bsc.p) : nullptr;
     EpiParams e;
     e.kind = EPI_F32;
     e.rows_valid = rows; e.cols_valid = cols; e.ld = cols; e.ob = (int64_t)rows * cols;
     e.out_f32 = static_cast<float*>(c32.p);
     BatchMap bm;
     if (nbatch > 1) bm = BatchMap{1, nbatch};
-    AFQMC_TRY(tc_gemm(sa, bm, sb, bm, rows, cols, K, nbatch, e, BN, static_cast<unsigned*>(flags.p), 0));
+    AFQMC_TRY(tc_gemm(sa, bm, sb, bm, rows, cols, K, nbatch, e, BN, exact != 0, static_cast<unsigned*>(flags.p), 0));
     f32_to_f64<<<(unsigned)((nc + 255) / 256), 256>>>(static_cast<float*>(c32.p), static_cast<double*>(c64.p), nc);
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
     unsigned fl = 0;
@@ -81,9 +91,9 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     if (!Lt || !ThetaT || !t || !X || Nchol < 1 || nws < 1 || M < 64)
         return fail(AFQMC_ERR_BADARG, "debug_energy: bad arguments");
     const int64_t na = (int64_t)Nchol * Np * M, nb = (int64_t)nws * 2 * Np * M;
-    DevBuf a64, ahi, alo, b64, bhi, blo, dt, dx, flags;
-    AFQMC_TRY(upload_split(Lt, na, a64, ahi, alo));
-    AFQMC_TRY(upload_split(ThetaT, nb, b64, bhi, blo));
+    DevBuf a64, ahi, alo, b64, bhi, blo, dt, dx, flags, asc, bsc;
+    AFQMC_TRY(upload_split(Lt, na / M, M, a64, ahi, alo, &asc));
+    AFQMC_TRY(upload_split(ThetaT, nb / M, M, b64, bhi, blo, &bsc));
     const int64_t no = (int64_t)nws * Nchol;
     if (cudaMalloc(&dt.p, no * 16) != cudaSuccess || cudaMalloc(&dx.p, no * 16) != cudaSuccess ||
         cudaMalloc(&flags.p, 4) != cudaSuccess)
@@ -91,9 +101,9 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     cudaMemset(flags.p, 0, 4);
     SplitMat sa, sb;
     sa.hi = static_cast<bf16*>(ahi.p); sa.lo = static_cast<bf16*>(alo.p);
-    sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M;
+    sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M; sa.scale = static_cast<float*>(asc.p);
     sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
-    sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M;
+    sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M; sb.scale = static_cast<float*>(bsc.p);
     AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p),
                         static_cast<unsigned*>(flags.p), 0));
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
@@ -103,4 +113,10 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     AFQMC_CUDA_TRY(cudaMemcpy(t, dt.p, no * 16, cudaMemcpyDeviceToHost));
     AFQMC_CUDA_TRY(cudaMemcpy(X, dx.p, no * 16, cudaMemcpyDeviceToHost));
     return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t,
+                                       double* X, double* E1) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "debug_mixed_terms: NULL handle");
+    return tc_debug_terms(wk, ST, Sinv, ThetaT, t, X, E1);
 }

@@ -8,6 +8,13 @@
 // tensor memory.  Complex products are split into real GEMMs by the operand layouts
 // (planar or "doubled" [[Re, -Im], [Im, Re]] operands) chosen by the step driver.
 //
+// The tensor cores round their fp32 accumulation toward zero, which biases long sums by a
+// few 1e-6 relative.  The precision-critical contractions (overlap, Green's function,
+// energy) therefore use row-scaled fp16 operands whose hi parts are integers with row 2-norm
+// <= 2^11: the hi*hi products then sum exactly in one TMEM accumulator, and only the small
+// remainder terms hi*lo + lo*hi + lo*lo (second accumulator) see the rounding ("exact" mode,
+// kind::f16 with f16 inputs, four products).
+//
 // Kernel structure (one CTA per SM, persistent over output tiles):
 //   warp 0      TMA producer: 64-wide K chunks of A (128 rows) and B (BN rows), hi and lo,
 //               into a ring of shared-memory stages (128-byte swizzle).
@@ -41,7 +48,14 @@ struct Cfg {
     static constexpr int kABytes = kBM * kBK * 2;  // one plane
     static constexpr int kBBytes = BN * kBK * 2;
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kTmemCols = 2 * BN;
+};
+
+// TMEM layout: NBUF accumulator buffers of (EXACT ? 2 : 1) x BN fp32 columns.
+template <int BN, bool EXACT, int NBUF>
+struct Tmem {
+    static constexpr int kBufCols = EXACT ? 2 * BN : BN;
+    static constexpr int kCols = NBUF * kBufCols;
+    static_assert(kCols <= 512, "TMEM has 512 columns");
 };
 
 struct TileShape {
@@ -51,6 +65,9 @@ struct TileShape {
     int nk;          // K chunks
     int64_t tiles;
     BatchMap am, bm;
+    const float* a_scale;  // [batch][a_rows] or null
+    const float* b_scale;  // [batch][b_rows] or null
+    int64_t a_rows, b_rows;
 };
 
 struct SharedCtl {
@@ -88,6 +105,11 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
         case EPI_F32: {
             float* o = e.out_f32 + b * e.ob + r * e.ld + c0;
             for (int j = 0; j < ncol; ++j) o[j] = v[j];
+            break;
+        }
+        case EPI_F64: {
+            double* o = e.out_f64 + b * e.ob + r * e.ld + c0;
+            for (int j = 0; j < ncol; ++j) o[j] = (double)v[j];
             break;
         }
         case EPI_SPLIT: {
@@ -146,14 +168,6 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
             }
             break;
         }
-        case EPI_BFINAL: {
-            const int64_t base = r * e.ld + c0;
-            for (int j = 0; j < ncol; ++j) {
-                e.out_f64[base + j] = (double)v[j];
-                store_split(e.out_hi, e.out_lo, base + j, v[j]);
-            }
-            break;
-        }
         default:
             break;
     }
@@ -176,12 +190,12 @@ __device__ __forceinline__ uint8_t* stage_ptr(uint8_t* base, int st) {
 template <int BN, typename TileFn>
 __device__ void producer_loop(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
                               const CUtensorMap* tBh, const CUtensorMap* tBl, int64_t ntiles, int nk, TileFn coords,
-                              bool a3d, bool b3d) {
+                              bool three_d) {
     using C = Cfg<BN>;
     int64_t g = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        int ax, ay, az, bx, by, bz;
+        int ay, az, by, bz;
         coords(t, ay, az, by, bz);
         for (int kb = 0; kb < nk; ++kb, ++g) {
             const int st = (int)(g % C::kStages);
@@ -189,20 +203,17 @@ __device__ void producer_loop(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap*
             if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
             uint8_t* s = stage_ptr<BN>(sbase, st);
             mbar_arrive_expect_tx(&ctl->full[st], C::kStageBytes);
-            ax = bx = kb * kBK;
-            if (a3d) {
-                tma_load_3d(s, tAh, &ctl->full[st], ax, ay, az);
-                tma_load_3d(s + C::kABytes, tAl, &ctl->full[st], ax, ay, az);
+            const int x = kb * kBK;
+            if (three_d) {
+                tma_load_3d(s, tAh, &ctl->full[st], x, ay, az);
+                tma_load_3d(s + C::kABytes, tAl, &ctl->full[st], x, ay, az);
+                tma_load_3d(s + 2 * C::kABytes, tBh, &ctl->full[st], x, by, bz);
+                tma_load_3d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], x, by, bz);
             } else {
-                tma_load_2d(s, tAh, &ctl->full[st], ax, ay);
-                tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], ax, ay);
-            }
-            if (b3d) {
-                tma_load_3d(s + 2 * C::kABytes, tBh, &ctl->full[st], bx, by, bz);
-                tma_load_3d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], bx, by, bz);
-            } else {
-                tma_load_2d(s + 2 * C::kABytes, tBh, &ctl->full[st], bx, by);
-                tma_load_2d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], bx, by);
+                tma_load_2d(s, tAh, &ctl->full[st], x, ay);
+                tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], x, ay);
+                tma_load_2d(s + 2 * C::kABytes, tBh, &ctl->full[st], x, by);
+                tma_load_2d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], x, by);
             }
         }
     }
@@ -214,20 +225,25 @@ __device__ void producer_loop(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap*
     }
 }
 
-template <int BN>
+// Issues the MMAs of every tile of this CTA.  EXACT: hi*hi into accumulator 1 (exact for
+// row-scaled operands), hi*lo + lo*hi + lo*lo into accumulator 2; else hi*hi + hi*lo + lo*hi
+// into one accumulator.
+template <int BN, bool EXACT, int NBUF>
 __device__ void mma_loop(uint8_t* sbase, SharedCtl* ctl, int64_t ntiles, int nk) {
     using C = Cfg<BN>;
-    constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+    using T = Tmem<BN, EXACT, NBUF>;
+    constexpr uint32_t idesc = idesc_bf16(kBM, BN, EXACT);   // exact mode: fp16 planes
     const uint32_t tmem = ctl->tmem_base;
     int64_t g = 0;
     int it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-        const int acc = it & 1;
-        const uint32_t u = (uint32_t)(it >> 1);
-        if (!mbar_wait(&ctl->tempty[acc], (u & 1u) ^ 1u, &ctl->abort)) break;
+        const int buf = it % NBUF;
+        const uint32_t u = (uint32_t)(it / NBUF);
+        if (!mbar_wait(&ctl->tempty[buf], (u & 1u) ^ 1u, &ctl->abort)) break;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        const uint32_t d1 = tmem + (uint32_t)(buf * T::kBufCols);
+        const uint32_t d2 = EXACT ? d1 + BN : d1;
         for (int kb = 0; kb < nk; ++kb, ++g) {
             const int st = (int)(g % C::kStages);
             const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
@@ -242,14 +258,16 @@ __device__ void mma_loop(uint8_t* sbase, SharedCtl* ctl, int64_t ntiles, int nk)
                 const uint32_t off = kk * 32;
                 const uint64_t ah = desc_sw128(sa + off), al = desc_sw128(sal + off);
                 const uint64_t bh = desc_sw128(sb + off), bl = desc_sw128(sbl + off);
-                mma_bf16(d, ah, bh, idesc, (kb | kk) != 0 ? 1u : 0u);
-                mma_bf16(d, ah, bl, idesc, 1u);
-                mma_bf16(d, al, bh, idesc, 1u);
+                const uint32_t first = (kb | kk) != 0 ? 1u : 0u;
+                mma_bf16(d1, ah, bh, idesc, first);
+                mma_bf16(d2, ah, bl, idesc, EXACT ? first : 1u);
+                mma_bf16(d2, al, bh, idesc, 1u);
+                if (EXACT) mma_bf16(d2, al, bl, idesc, 1u);
             }
             mma_commit(&ctl->empty[st]);
         }
         if (!ok) break;
-        mma_commit(&ctl->tfull[acc]);
+        mma_commit(&ctl->tfull[buf]);
     }
     // make sure nothing this thread issued is still running before TMEM is released
     mma_commit(&ctl->done);
@@ -264,23 +282,41 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
     return ok != 0;
 }
 
-// --------------------------------------------------------------------------- generic GEMM
-template <int BN>
-__global__ void __launch_bounds__(kGemmThreads, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, TileShape sh,
-                   EpiParams epi, unsigned* flags) {
-    using C = Cfg<BN>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(sbase + C::kStages * C::kStageBytes);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// 32 columns of an accumulator pair: v = acc1 (+ acc2); both loads issued before one wait.
+template <bool EXACT>
+__device__ __forceinline__ void load_acc32(uint32_t taddr1, uint32_t taddr2, float (&v)[32]) {
+    uint32_t a[32], b[32];
+    tmem_ld32_nw(taddr1, a);
+    if (EXACT) tmem_ld32_nw(taddr2, b);
+    tmem_ld_wait();
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = EXACT ? __uint_as_float(a[q]) + __uint_as_float(b[q]) : __uint_as_float(a[q]);
+}
+
+// re and im blocks (32 columns each) of an exact accumulator pair: four loads, one wait.
+__device__ __forceinline__ void load_cplx_block(uint32_t t1, uint32_t t2, int cr, int ci, float (&vr)[32],
+                                                float (&vi)[32]) {
+    uint32_t a[32], b[32], c[32], d[32];
+    tmem_ld32_nw(t1 + cr, a);
+    tmem_ld32_nw(t2 + cr, b);
+    tmem_ld32_nw(t1 + ci, c);
+    tmem_ld32_nw(t2 + ci, d);
+    tmem_ld_wait();
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        vr[q] = __uint_as_float(a[q]) + __uint_as_float(b[q]);
+        vi[q] = __uint_as_float(c[q]) + __uint_as_float(d[q]);
+    }
+}
+
+template <int BN, bool EXACT, int NBUF>
+__device__ void setup_ctl(SharedCtl* ctl, int warp) {
     if (threadIdx.x == 0) {
-        for (int i = 0; i < C::kStages; ++i) {
+        for (int i = 0; i < Cfg<BN>::kStages; ++i) {
             mbar_init(&ctl->full[i], 1);
             mbar_init(&ctl->empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&ctl->tfull[i], 1);
             mbar_init(&ctl->tempty[i], 128);
         }
@@ -289,20 +325,47 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(&ctl->tmem_base, C::kTmemCols);
+        tmem_alloc(&ctl->tmem_base, Tmem<BN, EXACT, NBUF>::kCols);
         tmem_relinquish();
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+template <int BN, bool EXACT, int NBUF>
+__device__ void teardown(SharedCtl* ctl, int warp, unsigned* flags) {
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(ctl->tmem_base, Tmem<BN, EXACT, NBUF>::kCols);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+// --------------------------------------------------------------------------- generic GEMM
+template <int BN, bool EXACT>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                   const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, TileShape sh,
+                   EpiParams epi, unsigned* flags) {
+    using C = Cfg<BN>;
+    constexpr int NBUF = 2;
+    using T = Tmem<BN, EXACT, NBUF>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(sbase + C::kStages * C::kStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tAh);
         tma_prefetch_desc(&tAl);
         tma_prefetch_desc(&tBh);
         tma_prefetch_desc(&tBl);
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    setup_ctl<BN, EXACT, NBUF>(ctl, warp);
 
-    const bool a3d = sh.am.mod != (1 << 30) || sh.nbatch > 1;
+    const bool three_d = sh.am.mod != (1 << 30) || sh.nbatch > 1;
     if (warp == 0) {
         if (lane == 0) {
             auto coords = [&](int64_t t, int& ay, int& az, int& by, int& bz) {
@@ -313,44 +376,52 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 by = ct * BN;
                 bz = (b / sh.bm.div) % sh.bm.mod;
             };
-            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, sh.tiles, sh.nk, coords, a3d, a3d);
+            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, sh.tiles, sh.nk, coords, three_d);
         }
     } else if (warp == 1) {
-        if (lane == 0) mma_loop<BN>(sbase, ctl, sh.tiles, sh.nk);
+        if (lane == 0) mma_loop<BN, EXACT, NBUF>(sbase, ctl, sh.tiles, sh.nk);
     } else {
         const int g4 = warp & 3;
         const uint32_t lane_base = (uint32_t)(g4 * 32) << 16;
         int it = 0;
         for (int64_t t = blockIdx.x; t < sh.tiles; t += gridDim.x, ++it) {
-            const int acc = it & 1;
-            const uint32_t u = (uint32_t)(it >> 1);
-            if (!warp_wait(&ctl->tfull[acc], u & 1u, &ctl->abort)) break;
+            const int buf = it % NBUF;
+            const uint32_t u = (uint32_t)(it / NBUF);
+            if (!warp_wait(&ctl->tfull[buf], u & 1u, &ctl->abort)) break;
             tc_fence_after();
             int b, rt, ct;
             tile_coords(sh, t, b, rt, ct);
             const int64_t r = (int64_t)rt * kBM + g4 * 32 + lane;
+            const int az = three_d ? (b / sh.am.div) % sh.am.mod : 0;
+            const int bz = three_d ? (b / sh.bm.div) % sh.bm.mod : 0;
+            const float sa = (sh.a_scale && r < sh.a_rows) ? sh.a_scale[(int64_t)az * sh.a_rows + r] : 1.0f;
+            const uint32_t tb = ctl->tmem_base + lane_base + (uint32_t)(buf * T::kBufCols);
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 float v[32];
-                tmem_ld32(ctl->tmem_base + lane_base + (uint32_t)(acc * BN + c * 32), v);
-                epilogue_row(epi, b, r, (int64_t)ct * BN + c * 32, v);
+                load_acc32<EXACT>(tb + c * 32, tb + BN + c * 32, v);
+                const int64_t c0 = (int64_t)ct * BN + c * 32;
+                if (sh.a_scale || sh.b_scale) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int64_t col = c0 + q;
+                        const float sb = (sh.b_scale && col < sh.b_rows) ? sh.b_scale[(int64_t)bz * sh.b_rows + col] : 1.0f;
+                        v[q] *= sa * sb;
+                    }
+                }
+                epilogue_row(epi, b, r, c0, v);
             }
             tc_fence_before();
-            mbar_arrive(&ctl->tempty[acc]);
+            mbar_arrive(&ctl->tempty[buf]);
         }
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(ctl->tmem_base, C::kTmemCols);
-    }
-    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+    teardown<BN, EXACT, NBUF>(ctl, warp, flags);
 }
 
 // --------------------------------------------------------------------------- energy kernel
 // Tiles: (n-group of G = 128/Np Cholesky vectors) x (group of G walker-spin pairs).
-// Accumulator columns of one ws: [re b = 0..Np) [im b = 0..Np).
+// Accumulator columns of one ws: [re b = 0..Np) [im b = 0..Np).  Exact mode, one TMEM
+// buffer (accumulator 1 in columns 0..255, accumulator 2 in 256..511).
 struct EnergyShape {
     int Np, Q, G;
     int Nchol, nws;
@@ -358,6 +429,8 @@ struct EnergyShape {
     int ws_super;     // ws groups per L2 super-block
     int64_t tiles;
     int nk;
+    const float* a_scale;   // [Nchol*Np]
+    const float* b_scale;   // [nws*2*Np]
     cplx* t_out;
     cplx* X_out;
 };
@@ -388,6 +461,8 @@ __device__ __forceinline__ int named_bar_and(int pred) {
     return r;
 }
 
+constexpr int kSlotFloats = 2 * 32 * 32;  // re, im planes of a 32 x 32 block (XOR-swizzled)
+
 template <int Np>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_energy_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
@@ -396,39 +471,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     constexpr int BN = 256;
     constexpr int Q = Np / 32;
     constexpr int G = 128 / Np;
-    constexpr int kSlotFloats = 2 * 32 * 33;  // re, im planes of a padded 32 x 32 block
+    constexpr int NBUF = 1;
     using C = Cfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float* xch = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
-    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(xch + 4 * kSlotFloats);
+    float* colscale = xch + 4 * kSlotFloats;                       // 256 column scales of the tile
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(colscale + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < C::kStages; ++i) {
-            mbar_init(&ctl->full[i], 1);
-            mbar_init(&ctl->empty[i], 1);
-        }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&ctl->tfull[i], 1);
-            mbar_init(&ctl->tempty[i], 128);
-        }
-        mbar_init(&ctl->done, 1);
-        ctl->abort = 0;
-        fence_mbar_init();
-    }
-    if (warp == 1) {
-        tmem_alloc(&ctl->tmem_base, C::kTmemCols);
-        tmem_relinquish();
-    }
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tAh);
         tma_prefetch_desc(&tAl);
         tma_prefetch_desc(&tBh);
         tma_prefetch_desc(&tBl);
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    setup_ctl<BN, true, NBUF>(ctl, warp);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -439,26 +496,35 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 by = wg * 256;
                 az = bz = 0;
             };
-            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es.tiles, es.nk, coords, false, false);
+            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es.tiles, es.nk, coords, false);
         }
     } else if (warp == 1) {
-        if (lane == 0) mma_loop<BN>(sbase, ctl, es.tiles, es.nk);
+        if (lane == 0) mma_loop<BN, true, NBUF>(sbase, ctl, es.tiles, es.nk);
     } else {
         const int g4 = warp & 3;               // row sub-block: rows 32*g4 .. +31
         const int i_blk = g4 / Q;              // n within the group
         const int mu = g4 % Q;                 // sub-block index inside the Np x Np block
+        const int et = threadIdx.x - 64;       // 0..127 over the epilogue warps
         const uint32_t lane_base = (uint32_t)(g4 * 32) << 16;
         float* my_slot = xch + g4 * kSlotFloats;
         int it = 0;
         for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
-            const int acc = it & 1;
-            const uint32_t u = (uint32_t)(it >> 1);
-            const bool got = warp_wait(&ctl->tfull[acc], u & 1u, &ctl->abort);
+            const uint32_t u = (uint32_t)it;
+            const bool got = warp_wait(&ctl->tfull[0], u & 1u, &ctl->abort);
             if (!named_bar_and(got ? 1 : 0)) break;   // all four warps leave together
             tc_fence_after();
             int ng, wg;
             energy_tile(es, t, ng, wg);
-            const uint32_t tbase = ctl->tmem_base + lane_base + (uint32_t)(acc * BN);
+            // stage the tile's column scales; my row's scale
+            for (int c = et; c < 256; c += 128) {
+                const int64_t row = (int64_t)wg * 256 + c;
+                colscale[c] = row < (int64_t)es.nws * 2 * Np ? es.b_scale[row] : 0.0f;
+            }
+            const int64_t arow = (int64_t)ng * 128 + g4 * 32 + lane;
+            const float sa = arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
+            named_bar_epi();
+            const uint32_t t1 = ctl->tmem_base + lane_base;
+            const uint32_t t2 = t1 + BN;
 #pragma unroll 1
             for (int j = 0; j < G; ++j) {
                 double tr = 0.0, ti = 0.0, xr = 0.0, xi = 0.0;
@@ -467,24 +533,34 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     const int wsub = (mu - rho + Q) % Q;   // sub-block I publish
                     const int beta = (mu + rho) % Q;       // partner sub-block I read
                     float vr[32], vi[32];
-                    // publish T[my rows][block wsub] (re, im) for the warp that needs it
-                    tmem_ld32(tbase + (uint32_t)(j * 2 * Np + 32 * wsub), vr);
-                    tmem_ld32(tbase + (uint32_t)(j * 2 * Np + Np + 32 * wsub), vi);
+                    // publish T[my rows][block wsub] (re, im), scaled to true units
+                    {
+                        const int cr = j * 2 * Np + 32 * wsub, ci = cr + Np;
+                        load_cplx_block(t1, t2, cr, ci, vr, vi);
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        my_slot[lane * 33 + q] = vr[q];
-                        my_slot[32 * 33 + lane * 33 + q] = vi[q];
+                        for (int q = 0; q < 32; ++q) {
+                            vr[q] *= sa * colscale[cr + q];
+                            vi[q] *= sa * colscale[ci + q];
+                            my_slot[lane * 32 + (q ^ lane)] = vr[q];
+                            my_slot[32 * 32 + lane * 32 + (q ^ lane)] = vi[q];
+                        }
                     }
                     named_bar_epi();
                     if (beta != wsub) {
-                        tmem_ld32(tbase + (uint32_t)(j * 2 * Np + 32 * beta), vr);
-                        tmem_ld32(tbase + (uint32_t)(j * 2 * Np + Np + 32 * beta), vi);
+                        const int cr = j * 2 * Np + 32 * beta, ci = cr + Np;
+                        load_cplx_block(t1, t2, cr, ci, vr, vi);
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            vr[q] *= sa * colscale[cr + q];
+                            vi[q] *= sa * colscale[ci + q];
+                        }
                     }
                     const float* ps = xch + (i_blk * Q + beta) * kSlotFloats;
                     float ar = 0.f, ai = 0.f;
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
-                        const float pr = ps[q * 33 + lane], pi = ps[32 * 33 + q * 33 + lane];
+                        // partner row q, column = my lane
+                        const float pr = ps[q * 32 + (lane ^ q)], pi = ps[32 * 32 + q * 32 + (lane ^ q)];
                         ar = fmaf(vr[q], pr, fmaf(-vi[q], pi, ar));
                         ai = fmaf(vr[q], pi, fmaf(vi[q], pr, ai));
                     }
@@ -531,16 +607,37 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 named_bar_epi();
             }
             tc_fence_before();
-            mbar_arrive(&ctl->tempty[acc]);
+            mbar_arrive(&ctl->tempty[0]);
         }
     }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc(ctl->tmem_base, C::kTmemCols);
+    teardown<BN, true, NBUF>(ctl, warp, flags);
+}
+
+// --------------------------------------------------------------------------- row split
+// One warp per row: scale = 2^(e-11) with ||x||_2 < 2^e, hi = rint(x/scale) (|hi| <= 2048, an
+// integer, exact in fp16), lo = fp16(x/scale - hi).  ||hi||_2 <= 2^11 + sqrt(K)/2, so by
+// Cauchy-Schwarz every partial sum of hi_A . hi_B is an integer below 2^23: exact in fp32.
+template <typename Src>
+__global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t src_stride, int64_t rows, int64_t K,
+                                                         __half* hi, __half* lo, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const Src* x = src + r * src_stride;
+    double ss = 0.0;
+    for (int64_t k = lane; k < K; k += 32) ss += (double)x[k] * (double)x[k];
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double nrm = sqrt(ss);
+    int e = 0;
+    if (nrm > 0.0) frexp(nrm, &e);        // nrm < 2^e
+    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+    if (lane == 0) scale[r] = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    for (int64_t k = lane; k < K; k += 32) {
+        const double y = (double)x[k] * inv;   // |y| < 2048
+        const double s1 = rint(y);
+        hi[r * K + k] = __double2half(s1);
+        lo[r * K + k] = __double2half(y - s1);
     }
-    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
 }
 
 // --------------------------------------------------------------------------- host side
@@ -562,18 +659,18 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3-D map over [batch][rows][K] bf16 with box {64, box_rows, 1} and 128-byte swizzle.
+// 2-D or 3-D map over [batch][rows][K] bf16 with box {64, box_rows, 1} and 128-byte swizzle.
 int make_map(CUtensorMap* m, const bf16* base, int64_t K, int64_t rows, int64_t batch, int64_t row_stride,
-             int64_t batch_stride, int box_rows, bool three_d) {
+             int64_t batch_stride, int box_rows, bool three_d, bool fp16 = false) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_stride * 2) % 16 || (batch_stride * 2) % 16)
         return fail(AFQMC_ERR_SHAPE, "tensor map: base/stride not 16-byte aligned");
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)std::max<int64_t>(batch, 1)};
-    cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 2), (cuuint64_t)(batch_stride * 2)};
+    cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 2), (cuuint64_t)(std::max<int64_t>(batch_stride, row_stride) * 2)};
     cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, three_d ? 3 : 2, const_cast<bf16*>(base), dims, strides,
+    CUresult r = fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, three_d ? 3 : 2, const_cast<bf16*>(base), dims, strides,
                     box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -585,9 +682,35 @@ size_t gemm_smem() {
     return 1024 + (size_t)Cfg<BN>::kStages * Cfg<BN>::kStageBytes + sizeof(SharedCtl);
 }
 
-size_t energy_smem() { return 1024 + (size_t)Cfg<256>::kStages * Cfg<256>::kStageBytes + 4 * 2 * 32 * 33 * 4 + sizeof(SharedCtl); }
+size_t energy_smem() {
+    return 1024 + (size_t)Cfg<256>::kStages * Cfg<256>::kStageBytes + 4 * kSlotFloats * 4 + 256 * 4 + sizeof(SharedCtl);
+}
 
 int g_num_sms = 0;
+
+template <int BN, bool EXACT>
+int launch_gemm(const CUtensorMap* m, const TileShape& sh, const EpiParams& epi, unsigned* flags, cudaStream_t st) {
+    const size_t sm = gemm_smem<BN>();
+    cudaFuncSetAttribute(tc_gemm_kernel<BN, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int grid = (int)std::min<int64_t>(sh.tiles, tc_num_sms());
+    count_launch();
+    tc_gemm_kernel<BN, EXACT><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], sh, epi, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_gemm launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
+
+template <int Np>
+int launch_energy(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
+    const size_t sm = energy_smem();
+    cudaFuncSetAttribute(tc_energy_kernel<Np>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int grid = (int)std::min<int64_t>(es.tiles, tc_num_sms());
+    count_launch();
+    tc_energy_kernel<Np><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
 
 }  // namespace
 
@@ -602,15 +725,17 @@ int tc_num_sms() {
 }
 
 int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, int64_t rows, int64_t cols,
-            int64_t K, int nbatch, const EpiParams& epi, int BN, unsigned* flags, cudaStream_t st) {
+            int64_t K, int nbatch, const EpiParams& epi, int BN, bool exact, unsigned* flags, cudaStream_t st) {
     if (rows <= 0 || cols <= 0 || K <= 0 || nbatch <= 0) return AFQMC_OK;
     if (BN != 128 && BN != 256) return fail(AFQMC_ERR_BADARG, "tc_gemm: BN must be 128 or 256");
+    if (exact && (BN != 128 || !A.scale || !B.scale))
+        return fail(AFQMC_ERR_BADARG, "tc_gemm: exact mode needs BN = 128 and row-scaled operands");
     const bool three_d = nbatch > 1 || amap.mod != (1 << 30);
     CUtensorMap m[4];
-    AFQMC_TRY(make_map(&m[0], A.hi, A.K, A.rows, A.batch, A.row_stride, A.batch_stride, kBM, three_d));
-    AFQMC_TRY(make_map(&m[1], A.lo, A.K, A.rows, A.batch, A.row_stride, A.batch_stride, kBM, three_d));
-    AFQMC_TRY(make_map(&m[2], B.hi, B.K, B.rows, B.batch, B.row_stride, B.batch_stride, BN, three_d));
-    AFQMC_TRY(make_map(&m[3], B.lo, B.K, B.rows, B.batch, B.row_stride, B.batch_stride, BN, three_d));
+    AFQMC_TRY(make_map(&m[0], A.hi, A.K, A.rows, A.batch, A.row_stride, A.batch_stride, kBM, three_d, exact));
+    AFQMC_TRY(make_map(&m[1], A.lo, A.K, A.rows, A.batch, A.row_stride, A.batch_stride, kBM, three_d, exact));
+    AFQMC_TRY(make_map(&m[2], B.hi, B.K, B.rows, B.batch, B.row_stride, B.batch_stride, BN, three_d, exact));
+    AFQMC_TRY(make_map(&m[3], B.lo, B.K, B.rows, B.batch, B.row_stride, B.batch_stride, BN, three_d, exact));
     TileShape sh;
     sh.rows = rows;
     sh.cols = cols;
@@ -620,38 +745,27 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
     sh.ct = (int)((cols + BN - 1) / BN);
     sh.nk = (int)((K + kBK - 1) / kBK);
     sh.tiles = (int64_t)sh.rt * sh.ct * nbatch;
-    sh.am = amap;
-    sh.bm = bmap;
-    if (!three_d) {
-        sh.am = BatchMap{1, 1 << 30};
-        sh.bm = BatchMap{1, 1 << 30};
-    }
-    const int grid = (int)std::min<int64_t>(sh.tiles, tc_num_sms());
-    if (BN == 256) {
-        const size_t sm = gemm_smem<256>();
-        cudaFuncSetAttribute(tc_gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        count_launch();
-        tc_gemm_kernel<256><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], sh, epi, flags);
-    } else {
-        const size_t sm = gemm_smem<128>();
-        cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        count_launch();
-        tc_gemm_kernel<128><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], sh, epi, flags);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_gemm launch: ") + cudaGetErrorString(e));
-    return AFQMC_OK;
+    sh.am = three_d ? amap : BatchMap{1, 1 << 30};
+    sh.bm = three_d ? bmap : BatchMap{1, 1 << 30};
+    sh.a_scale = A.scale;
+    sh.b_scale = B.scale;
+    sh.a_rows = A.rows;
+    sh.b_rows = B.rows;
+    if (exact) return launch_gemm<128, true>(m, sh, epi, flags, st);
+    if (BN == 256) return launch_gemm<256, false>(m, sh, epi, flags, st);
+    return launch_gemm<128, false>(m, sh, epi, flags, st);
 }
 
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
               cplx* X_out, unsigned* flags, cudaStream_t st) {
     if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
-    if (M % kBK) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64");
+    if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
+    if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
     CUtensorMap m[4];
-    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false));
-    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false));
-    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false));
-    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false));
+    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true));
+    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true));
+    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true));
+    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true));
     EnergyShape es;
     es.Np = Np;
     es.Q = Np / 32;
@@ -663,31 +777,31 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     es.ws_super = std::min(es.ws_groups, 128);
     es.tiles = (int64_t)es.n_groups * es.ws_groups;
     es.nk = M / kBK;
+    es.a_scale = Lt.scale;
+    es.b_scale = ThetaT.scale;
     es.t_out = t_out;
     es.X_out = X_out;
-    const int grid = (int)std::min<int64_t>(es.tiles, tc_num_sms());
-    const size_t sm = energy_smem();
-    cudaError_t e;
     switch (Np) {
-        case 32:
-            cudaFuncSetAttribute(tc_energy_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            count_launch();
-            tc_energy_kernel<32><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
-            break;
-        case 64:
-            cudaFuncSetAttribute(tc_energy_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            count_launch();
-            tc_energy_kernel<64><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
-            break;
-        default:
-            cudaFuncSetAttribute(tc_energy_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            count_launch();
-            tc_energy_kernel<128><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
-            break;
+        case 32: return launch_energy<32>(m, es, flags, st);
+        case 64: return launch_energy<64>(m, es, flags, st);
+        default: return launch_energy<128>(m, es, flags, st);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy launch: ") + cudaGetErrorString(e));
-    return AFQMC_OK;
+}
+
+void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
+                cudaStream_t st) {
+    if (rows <= 0) return;
+    count_launch();
+    split_rows_kernel<double><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+        src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale);
+}
+
+void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
+                cudaStream_t st) {
+    if (rows <= 0) return;
+    count_launch();
+    split_rows_kernel<float><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+        src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale);
 }
 
 }  // namespace afqmc

@@ -11,12 +11,24 @@ namespace afqmc {
 
 using bf16 = __nv_bfloat16;
 
-// A K-major bf16 matrix stored as two planes (hi, lo) of identical layout
-// [batch][rows][K] with the given element strides.  The tensor-core kernels read
-// (hi, lo) pairs and form hi*hi + hi*lo + lo*hi.
+// A K-major 16-bit matrix stored as two planes (hi, lo) of identical layout
+// [batch][rows][K] with the given element strides, plus optional per-row scales
+// ([batch][rows], contiguous).  Element value = (hi + lo) * scale[row].
+//
+// Two encodings are used:
+//  * plain (bf16):      hi = bf16(x), lo = bf16(x - hi), no scale (scale == nullptr);
+//  * row-scaled (fp16): scale = 2^(e - 11) with ||x_row||_2 < 2^e, hi = rint(x / scale) an
+//                       integer in [-2048, 2048] (exact in fp16), lo = fp16(x / scale - hi).
+// With row-scaled operands on both sides the hi*hi products are integers and, by
+// Cauchy-Schwarz, every partial sum stays below 2^23, so their fp32 tensor-memory sums are
+// exact whatever rounding the tensor cores apply (they round toward zero); the remainder
+// terms hi*lo + lo*hi + lo*lo go to a second accumulator ("exact" GEMMs).  Plain GEMMs put
+// hi*hi + hi*lo + lo*hi in one accumulator.  The pointers are typed bf16 for both
+// encodings; row-scaled planes hold IEEE fp16 bit patterns.
 struct SplitMat {
     const bf16* hi = nullptr;
     const bf16* lo = nullptr;
+    const float* scale = nullptr;
     int64_t K = 0, rows = 0, batch = 1;
     int64_t row_stride = 0;    // elements between rows (>= K, multiple of 8)
     int64_t batch_stride = 0;  // elements between batches
@@ -31,11 +43,11 @@ struct BatchMap {
 // Output tile epilogues of the generic GEMM (kind selects the write pattern).
 enum EpiKind : int {
     EPI_F32 = 0,       // out_f32[b*ob + r*ld + c]
-    EPI_SPLIT = 1,     // out_hi/out_lo[b*ob + r*ld + c]  (bf16 pair)
+    EPI_SPLIT = 1,     // out_hi/out_lo[b*ob + r*ld + c]  (plain bf16 pair)
     EPI_HSPOT = 2,     // A potential: row (w, c), col (i, k) -> hi/lo[w][i][c*M + k]
     EPI_BFIRST = 3,    // B Phi: doubled operand for the Taylor series + accumulator init
     EPI_TAYLOR = 4,    // (i s) P A^T: doubled operand of the next term + accumulator update
-    EPI_BFINAL = 5,    // B P: FP64 walker + its bf16 pair
+    EPI_F64 = 5,       // out_f64[b*ob + r*ld + c]
 };
 
 struct EpiParams {
@@ -51,16 +63,24 @@ struct EpiParams {
     float scale = 1.0f;                      // Taylor factor sqrt(tau)/k
 };
 
-// C[b] = A[b] . B[b]^T (split-3 bf16, fp32 accumulation in TMEM), 128 x BN tiles.
+// C[b] = A[b] . B[b]^T (split bf16, fp32 accumulation in TMEM), 128 x BN tiles.
+// exact = true needs row-scaled A and B and BN = 128.
 int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, int64_t rows, int64_t cols,
-            int64_t K, int nbatch, const EpiParams& epi, int BN, unsigned* flags, cudaStream_t st);
+            int64_t K, int nbatch, const EpiParams& epi, int BN, bool exact, unsigned* flags, cudaStream_t st);
 
 // Fused energy contraction: T_{n,ws} = Lt_n Theta_ws^T (Np x Np complex, Np | 128) for
 // all n and walker-spin pairs ws; emits t = Tr T and X = Tr(T T) per (ws, n) into
 // t_out/X_out [nws][Nchol] (complex FP64).  Lt: [Nchol*Np][M], ThetaT: [nws*2*Np][M]
-// (rows (ws, re/im, b)).
+// (rows (ws, re/im, b)), both row-scaled; exact accumulation of the leading product.
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
               cplx* X_out, unsigned* flags, cudaStream_t st);
+
+// Row-scaled (fp16) split of `rows` rows of length K (row r at src + r*src_stride) into
+// hi/lo [rows][K] (row stride K) and scale[rows].  FP64 or FP32 source.
+void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
+                cudaStream_t st);
+void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
+                cudaStream_t st);
 
 int tc_num_sms();
 

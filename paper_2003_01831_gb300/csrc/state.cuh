@@ -98,5 +98,6 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
 int tc_qr(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st);
+int tc_debug_terms(afqmc_walkers* wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X, double* E1);
 
 }  // namespace afqmc

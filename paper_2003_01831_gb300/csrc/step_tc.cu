@@ -5,16 +5,23 @@
 //
 // Device layouts (W walkers, both spins, N electrons per spin, complex stored planar):
 //   PhiT   [W][2][2][N][M] FP64 master walkers, transposed (row (s, c, j) = column j of
-//          Phi_s, re/im plane c), plus its bf16 (hi, lo) pair
-//   Phi    [W][2][M][2N]   bf16 pair, untransposed with re | im columns (Theta GEMM operand)
-//   ThT    [W][2][2][N][M] Theta^T = (Phi S^-1)^T, bf16 pair (energy GEMM operand)
-//   Lt     [Nchol][N][M]   Ltilde_n = Psi^T L_n, bf16 pair (trial is real, same both spins)
-//   LT     [M*M][Nchol]    L transposed, bf16 pair (HS potential GEMM operand)
-//   A      [W][M][2M]      HS potential sum_n c_n L_n, re | im columns, bf16 pair
+//          Phi_s, re/im plane c), plus its row-scaled fp16 pair and a plain bf16 pair
+//   Phi    [W][2][M][2N]   row-scaled fp16 pair, untransposed with re | im columns
+//          (Green's-function GEMM operand)
+//   ThT    [W][2][2][N][M] Theta^T = (Phi S^-1)^T: fp32, and its row-scaled fp16 pair
+//          (energy GEMM operand)
+//   Lt     [Nchol][N][M]   Ltilde_n = Psi^T L_n (trial real, same for both spins): row-scaled
+//          pair for the energy, plain pair for the force-bias-only contraction
+//   LT     [M*M][Nchol]    L transposed, plain pair (HS potential GEMM operand)
+//   A      [W][M][2M]      HS potential sum_n c_n L_n, re | im columns, plain pair
 //   PD     [W][2][2N][2M]  Taylor term in doubled form [[Re, -Im], [Im, Re]] (ping-pong)
 //   Pacc   [W][2][2][N][M] fp32 Taylor accumulator
+// The overlap, Green's function and energy contractions use row-scaled fp16 operands and the
+// exact-accumulation GEMM mode (kernels_tc.cu); the propagation uses plain pairs, whose
+// small accumulation bias only rescales walkers (a gauge factor common to all of them).
 #include <algorithm>
 #include <utility>
+#include <vector>
 
 #include "kernels_tc.cuh"
 #include "state.cuh"
@@ -24,26 +31,40 @@ namespace afqmc {
 
 struct TcState {
     int N = 0, M = 0, Nchol = 0, W = 0;
+    // static operands
     bf16 *Lt_h = nullptr, *Lt_l = nullptr;
+    float* Lt_s = nullptr;
+    bf16 *Ltp_h = nullptr, *Ltp_l = nullptr;
     bf16 *LT_h = nullptr, *LT_l = nullptr;
     bf16 *Bh_h = nullptr, *Bh_l = nullptr;
     bf16 *PsiT_h = nullptr, *PsiT_l = nullptr;
+    float* PsiT_s = nullptr;
+    double* PsiT_f = nullptr;
+    // walkers
     double* PhiT[2] = {nullptr, nullptr};
     bf16 *PhiT_h[2] = {nullptr, nullptr}, *PhiT_l[2] = {nullptr, nullptr};
+    float* PhiT_s[2] = {nullptr, nullptr};
     bf16 *Phi_h = nullptr, *Phi_l = nullptr;
+    float* Phi_s = nullptr;
+    bf16 *PhiTp_h = nullptr, *PhiTp_l = nullptr;   // plain bf16 pair of the current walkers
+    // Green's function and energy
     float* ST = nullptr;
     cplx* S = nullptr;
     cplx* ld = nullptr;
     bf16 *SD_h = nullptr, *SD_l = nullptr;
+    float* SD_s = nullptr;
+    float* ThT_f = nullptr;
     bf16 *ThT_h = nullptr, *ThT_l = nullptr;
+    float* ThT_s = nullptr;
     cplx *tE = nullptr, *XE = nullptr;
     float* tFB = nullptr;
+    cplx* E1 = nullptr;
+    // propagation
     bf16 *cf_h = nullptr, *cf_l = nullptr;
     bf16 *A_h = nullptr, *A_l = nullptr;
     bf16 *PD_h[2] = {nullptr, nullptr}, *PD_l[2] = {nullptr, nullptr};
     float* Pacc = nullptr;
     bf16 *Pacc_h = nullptr, *Pacc_l = nullptr;
-    cplx* E1 = nullptr;
     int cur = 0;
     std::vector<void*> owned;
 };
@@ -72,14 +93,14 @@ __global__ void split_f32_kernel(const float* src, bf16* hi, bf16* lo, int64_t n
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) tc::split_bf16(src[i], hi[i], lo[i]);
 }
-// Psi [M][N] complex (real part) -> PsiT [N][M]
-__global__ void psiT_kernel(const cplx* Psi, int M, int N, bf16* hi, bf16* lo) {
+// Psi [M][N] complex (real part) -> PsiT [N][M] FP64
+__global__ void psiT_kernel(const cplx* Psi, int M, int N, double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)M * N) return;
     const int a = (int)(i / M), k = (int)(i % M);
-    tc::split_bf16(Psi[(int64_t)k * N + a].re, hi[i], lo[i]);
+    out[i] = Psi[(int64_t)k * N + a].re;
 }
-// L [Nchol][MM] -> LT [MM][Nchol], 32 x 32 tiles through shared memory
+// L [Nchol][MM] -> LT [MM][Nchol] plain pair, 32 x 32 tiles through shared memory
 __global__ void LT_kernel(const double* L, int64_t MM, int nch, bf16* hi, bf16* lo) {
     __shared__ double tile[32][33];
     const int64_t c0 = (int64_t)blockIdx.x * 32;  // along MM
@@ -117,29 +138,49 @@ __global__ void phiT_to_canon_kernel(const double* PhiT, int s, int W, int M, in
     const int64_t base = (((int64_t)w * 2 + s) * 2) * N * M;
     Phi[i] = cplx{PhiT[base + (int64_t)j * M + k], PhiT[base + (int64_t)N * M + (int64_t)j * M + k]};
 }
-// PhiT pair [WS][2N][M] -> Phi pair [WS][M][2N] (32 x 32 tiles)
-__global__ void phiT_to_phi_kernel(const bf16* th, const bf16* tl, int M, int N2, bf16* ph, bf16* pl) {
-    __shared__ bf16 sh[32][34], sl[32][34];
-    const int64_t ws = blockIdx.z;
-    const int r0 = blockIdx.y * 32;  // rows of PhiT (c, j)
-    const int k0 = blockIdx.x * 32;  // columns k
-    const bf16* TH = th + ws * (int64_t)N2 * M;
-    const bf16* TL = tl + ws * (int64_t)N2 * M;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int row = r0 + r, k = k0 + threadIdx.x;
-        if (row < N2 && k < M) {
-            sh[r][threadIdx.x] = TH[(int64_t)row * M + k];
-            sl[r][threadIdx.x] = TL[(int64_t)row * M + k];
-        }
+// PhiT FP64 [WS][2N][M] -> Phi [WS][M][2N] row-scaled fp16 pair (row = orbital k over the 2N
+// values re | im).  Block = (32 orbitals, one walker-spin); the 2N x 32 tile sits in
+// shared memory, each orbital's scale comes from the 2-norm of its column of the tile.
+__global__ void __launch_bounds__(kT) phi_untranspose_split_kernel(const double* PhiT, int M, int N2, __half* hi,
+                                                                     __half* lo, float* scale) {
+    extern __shared__ double tile[];  // [N2][33]
+    __shared__ double cmax[8][32];
+    __shared__ double inv_s[32];
+    const int64_t ws = blockIdx.y;
+    const int k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const double* src = PhiT + ws * (int64_t)N2 * M;
+    double m = 0.0;
+    for (int r = ty; r < N2; r += 8) {
+        const int k = k0 + tx;
+        const double v = k < M ? src[(int64_t)r * M + k] : 0.0;
+        tile[r * 33 + tx] = v;
+        m += v * v;
+    }
+    cmax[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+        double ss = cmax[0][tx];
+        for (int q = 1; q < 8; ++q) ss += cmax[q][tx];
+        const double nrm = sqrt(ss);
+        int e = 0;
+        if (nrm > 0.0) frexp(nrm, &e);
+        inv_s[tx] = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+        const int k = k0 + tx;
+        if (k < M) scale[ws * M + k] = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
     }
     __syncthreads();
-    bf16* PH = ph + ws * (int64_t)N2 * M;
-    bf16* PL = pl + ws * (int64_t)N2 * M;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int k = k0 + r, row = r0 + threadIdx.x;
-        if (row < N2 && k < M) {
-            PH[(int64_t)k * N2 + row] = sh[threadIdx.x][r];
-            PL[(int64_t)k * N2 + row] = sl[threadIdx.x][r];
+    // write: row k (= k0 + kk) has N2 contiguous outputs; threads along the row
+    for (int kk = ty; kk < 32; kk += 8) {
+        const int k = k0 + kk;
+        if (k >= M) continue;
+        __half* H = hi + (ws * M + k) * (int64_t)N2;
+        __half* Lo = lo + (ws * M + k) * (int64_t)N2;
+        for (int r = tx; r < N2; r += 32) {
+            const double y = tile[r * 33 + kk] * inv_s[kk];
+            const double s1 = rint(y);
+            H[r] = __double2half(s1);
+            Lo[r] = __double2half(y - s1);
         }
     }
 }
@@ -153,20 +194,42 @@ __global__ void st_to_S_kernel(const float* ST, int WS, int N, cplx* S) {
     const float* base = ST + ws * 2 * N * N;
     S[i] = cplx{(double)base[(int64_t)b * N + a], (double)base[(int64_t)N * N + (int64_t)b * N + a]};
 }
-// S^-1 [WS][N][N] -> SD [WS][2N][2N]: row (0,b) = [Re Si[j][b] | -Im Si[j][b]], row (1,b) = [Im | Re]
-__global__ void sinv_doubled_kernel(const cplx* Si, int WS, int N, bf16* hi, bf16* lo) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t per = (int64_t)4 * N * N;
-    if (i >= (int64_t)WS * per) return;
-    const int64_t ws = i / per;
-    const int64_t e = i % per;
-    const int row = (int)(e / (2 * N)), col = (int)(e % (2 * N));
-    const int c = row / N, b = row % N, cp = col / N, j = col % N;
-    const cplx v = Si[ws * N * N + (int64_t)j * N + b];
-    double x;
-    if (c == 0) x = (cp == 0) ? v.re : -v.im;
-    else x = (cp == 0) ? v.im : v.re;
-    tc::split_bf16(x, hi[i], lo[i]);
+// S^-1 [WS][N][N] -> SD [WS][2N][2N] row-scaled fp16 pair: row (0,b) = [Re Si[j][b] | -Im Si[j][b]],
+// row (1,b) = [Im | Re]; both rows of b share the scale (2-norm of column b of S^-1).
+__global__ void __launch_bounds__(kT) sinv_doubled_kernel(const cplx* Si, int WS, int N, __half* hi, __half* lo,
+                                                            float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // (ws, b)
+    const int lane = threadIdx.x & 31;
+    if (r >= (int64_t)WS * N) return;
+    const int64_t ws = r / N;
+    const int b = (int)(r % N);
+    const cplx* col = Si + ws * N * N + b;
+    double ss = 0.0;
+    for (int j = lane; j < N; j += 32) {
+        const cplx v = col[(int64_t)j * N];
+        ss += v.re * v.re + v.im * v.im;
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double nrm = sqrt(ss);          // 2-norm of either doubled row
+    int e = 0;
+    if (nrm > 0.0) frexp(nrm, &e);
+    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+    const float sc = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    const int64_t row0 = ws * 2 * N + b, row1 = row0 + N;  // rows (ws, 0, b), (ws, 1, b)
+    if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
+    const int64_t K2 = 2 * N;
+    for (int j = lane; j < N; j += 32) {
+        const cplx v = col[(int64_t)j * N];
+        const double yr = v.re * inv, yi = v.im * inv;
+        const double hr = rint(yr), hiI = rint(yi);
+        const __half Hr = __double2half(hr), Lr = __double2half(yr - hr);
+        const __half Hi = __double2half(hiI), Li = __double2half(yi - hiI);
+        const __half nHi = __double2half(-hiI), nLi = __double2half(-(yi - hiI));
+        hi[row0 * K2 + j] = Hr;      lo[row0 * K2 + j] = Lr;        // Re
+        hi[row0 * K2 + N + j] = nHi; lo[row0 * K2 + N + j] = nLi;   // -Im
+        hi[row1 * K2 + j] = Hi;      lo[row1 * K2 + j] = Li;        // Im
+        hi[row1 * K2 + N + j] = Hr;  lo[row1 * K2 + N + j] = Lr;    // Re
+    }
 }
 __global__ void coef_split_kernel(const cplx* c, int64_t W, int nch, bf16* hi, bf16* lo) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,9 +250,9 @@ __global__ void logS_pair_kernel(const cplx* ld, int W, cplx* out) {
     const cplx s = ld[2 * w] + ld[2 * w + 1];
     out[w] = cplx{s.re, atan2(sin(s.im), cos(s.im))};
 }
-// E1[w] = sum_s sum_{b,k} ht_s[b][k] (ThT_re + i ThT_im)[w, s][b][k]
-__global__ void __launch_bounds__(kT) e1_kernel(const cplx* ht0, const cplx* ht1, const bf16* th, const bf16* tl,
-                                                int M, int N, cplx* E1) {
+// E1[w] = sum_s sum_{b,k} ht_s[b][k] (ThT_re + i ThT_im)[w, s][b][k]  (fp32 Theta, FP64 sum)
+__global__ void __launch_bounds__(kT) e1_kernel(const cplx* ht0, const cplx* ht1, const float* th, int M, int N,
+                                                cplx* E1) {
     __shared__ cplx sh[kT];
     const int w = blockIdx.x;
     cplx acc{0.0, 0.0};
@@ -197,11 +260,8 @@ __global__ void __launch_bounds__(kT) e1_kernel(const cplx* ht0, const cplx* ht1
     for (int s = 0; s < 2; ++s) {
         const cplx* ht = s == 0 ? ht0 : ht1;
         const int64_t base = ((int64_t)w * 2 + s) * 2 * NM;
-        for (int64_t e = threadIdx.x; e < NM; e += kT) {
-            const double re = (double)__bfloat162float(th[base + e]) + (double)__bfloat162float(tl[base + e]);
-            const double im = (double)__bfloat162float(th[base + NM + e]) + (double)__bfloat162float(tl[base + NM + e]);
-            cfma(acc, ht[e], cplx{re, im});
-        }
+        for (int64_t e = threadIdx.x; e < NM; e += kT)
+            cfma(acc, ht[e], cplx{(double)th[base + e], (double)th[base + NM + e]});
     }
     sh[threadIdx.x] = acc;
     __syncthreads();
@@ -247,14 +307,10 @@ __global__ void __launch_bounds__(kT) le_mixed_kernel(const cplx* E1, const cplx
     }
 }
 // rejected walkers keep their old state: copy cur -> nxt where accept == 0
-__global__ void keep_rejected_kernel(const int* accept, int W, int64_t per, const double* old64, double* new64,
-                                     const bf16* oh, const bf16* ol, bf16* nh, bf16* nl) {
+__global__ void keep_rejected_kernel(const int* accept, int W, int64_t per, const double* old64, double* new64) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)W * per) return;
-    if (accept[i / per]) return;
-    new64[i] = old64[i];
-    nh[i] = oh[i];
-    nl[i] = ol[i];
+    if (!accept[i / per]) new64[i] = old64[i];
 }
 // Classical Gram-Schmidt (twice) on the N columns of one walker-spin, stored as planar
 // rows of PhiT: column j = (re row j, im row j), length M.  diag R > 0.
@@ -319,11 +375,12 @@ __global__ void __launch_bounds__(kT) qr_planar_kernel(double* PhiT, int M, int 
     }
 }
 
-SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t batch = 1, int64_t row_stride = -1,
-              int64_t batch_stride = -1) {
+SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t batch = 1, const float* scale = nullptr,
+              int64_t row_stride = -1, int64_t batch_stride = -1) {
     SplitMat m;
     m.hi = h;
     m.lo = l;
+    m.scale = scale;
     m.K = K;
     m.rows = rows;
     m.batch = batch;
@@ -332,19 +389,31 @@ SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t bat
     return m;
 }
 
-// refresh the bf16 pair and the untransposed operand of the current walkers
-void refresh_operands(TcState* s, cudaStream_t st) {
-    const int64_t n = (int64_t)s->W * 4 * s->N * s->M;
-    count_launch();
-    split_f64_kernel<<<nb(n), kT, 0, st>>>(s->PhiT[s->cur], s->PhiT_h[s->cur], s->PhiT_l[s->cur], n);
-    dim3 g((s->M + 31) / 32, (2 * s->N + 31) / 32, 2 * s->W);
-    count_launch();
-    phiT_to_phi_kernel<<<g, dim3(32, 8), 0, st>>>(s->PhiT_h[s->cur], s->PhiT_l[s->cur], s->M, 2 * s->N, s->Phi_h,
-                                                  s->Phi_l);
+// row-scaled pair of the walkers in buffer b
+void split_walkers(TcState* s, int b, cudaStream_t st) {
+    split_rows(s->PhiT[b], s->M, (int64_t)s->W * 4 * s->N, s->M, s->PhiT_h[b], s->PhiT_l[b], s->PhiT_s[b], st);
 }
 
-// S = Psi^T Phi for the walkers held in (h, l) -> s->S; logdet into s->ld; optional inverse
-int overlap_logdet(afqmc_walkers* wk, const bf16* h, const bf16* l, bool inverse, cudaStream_t st) {
+// untransposed operand of the current walkers (Green's-function GEMM)
+void untranspose_walkers(TcState* s, cudaStream_t st) {
+    dim3 g((s->M + 31) / 32, 2 * s->W);
+    const size_t sm = (size_t)2 * s->N * 33 * sizeof(double);
+    cudaFuncSetAttribute(phi_untranspose_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
+    phi_untranspose_split_kernel<<<g, kT, sm, st>>>(s->PhiT[s->cur], s->M, 2 * s->N, reinterpret_cast<__half*>(s->Phi_h),
+                                                    reinterpret_cast<__half*>(s->Phi_l), s->Phi_s);
+}
+
+void refresh_operands(TcState* s, cudaStream_t st) {
+    split_walkers(s, s->cur, st);
+    untranspose_walkers(s, st);
+    const int64_t n = (int64_t)s->W * 4 * s->N * s->M;
+    count_launch();
+    split_f64_kernel<<<nb(n), kT, 0, st>>>(s->PhiT[s->cur], s->PhiTp_h, s->PhiTp_l, n);
+}
+
+// S = Psi^T Phi for the walkers in buffer b -> s->S; logdet into s->ld; optional inverse
+int overlap_logdet(afqmc_walkers* wk, int b, bool inverse, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, WS = 2 * s->W;
     EpiParams e;
@@ -354,8 +423,9 @@ int overlap_logdet(afqmc_walkers* wk, const bf16* h, const bf16* l, bool inverse
     e.ld = N;
     e.ob = 2LL * N * N;
     e.out_f32 = s->ST;
-    AFQMC_TRY(tc_gemm(smat(h, l, M, 2 * N, WS), BatchMap{1, WS}, smat(s->PsiT_h, s->PsiT_l, M, N, 1), BatchMap{1, 1},
-                      2 * N, N, M, WS, e, 128, wk->flags, st));
+    AFQMC_TRY(tc_gemm(smat(s->PhiT_h[b], s->PhiT_l[b], M, 2 * N, WS, s->PhiT_s[b]), BatchMap{1, WS},
+                      smat(s->PsiT_h, s->PsiT_l, M, N, 1, s->PsiT_s), BatchMap{1, 1}, 2 * N, N, M, WS, e, 128, true,
+                      wk->flags, st));
     count_launch();
     st_to_S_kernel<<<nb((int64_t)WS * N * N), kT, 0, st>>>(s->ST, WS, N, s->S);
     batched_inverse_logdet(s->S, (int64_t)N * N, N, WS, s->ld, inverse, wk->flags, st);
@@ -375,29 +445,41 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     const int64_t NM = (int64_t)N * M, MM = (int64_t)M * M;
     AFQMC_TRY(talloc(s, &s->Lt_h, nch * NM));
     AFQMC_TRY(talloc(s, &s->Lt_l, nch * NM));
+    AFQMC_TRY(talloc(s, &s->Lt_s, (int64_t)nch * N));
+    AFQMC_TRY(talloc(s, &s->Ltp_h, nch * NM));
+    AFQMC_TRY(talloc(s, &s->Ltp_l, nch * NM));
     AFQMC_TRY(talloc(s, &s->LT_h, MM * nch));
     AFQMC_TRY(talloc(s, &s->LT_l, MM * nch));
     AFQMC_TRY(talloc(s, &s->Bh_h, MM));
     AFQMC_TRY(talloc(s, &s->Bh_l, MM));
     AFQMC_TRY(talloc(s, &s->PsiT_h, NM));
     AFQMC_TRY(talloc(s, &s->PsiT_l, NM));
+    AFQMC_TRY(talloc(s, &s->PsiT_s, N));
+    AFQMC_TRY(talloc(s, &s->PsiT_f, NM));
     const int64_t wall = (int64_t)W * 4 * NM;  // PhiT elements
     for (int b = 0; b < 2; ++b) {
         AFQMC_TRY(talloc(s, &s->PhiT[b], wall));
         AFQMC_TRY(talloc(s, &s->PhiT_h[b], wall));
         AFQMC_TRY(talloc(s, &s->PhiT_l[b], wall));
+        AFQMC_TRY(talloc(s, &s->PhiT_s[b], (int64_t)W * 4 * N));
         AFQMC_TRY(talloc(s, &s->PD_h[b], (int64_t)W * 2 * 2 * N * 2 * M));
         AFQMC_TRY(talloc(s, &s->PD_l[b], (int64_t)W * 2 * 2 * N * 2 * M));
     }
     AFQMC_TRY(talloc(s, &s->Phi_h, wall));
     AFQMC_TRY(talloc(s, &s->Phi_l, wall));
+    AFQMC_TRY(talloc(s, &s->Phi_s, (int64_t)W * 2 * M));
+    AFQMC_TRY(talloc(s, &s->PhiTp_h, wall));
+    AFQMC_TRY(talloc(s, &s->PhiTp_l, wall));
     AFQMC_TRY(talloc(s, &s->ST, (int64_t)W * 2 * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->S, (int64_t)W * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->ld, (int64_t)W * 2));
     AFQMC_TRY(talloc(s, &s->SD_h, (int64_t)W * 2 * 4 * N * N));
     AFQMC_TRY(talloc(s, &s->SD_l, (int64_t)W * 2 * 4 * N * N));
+    AFQMC_TRY(talloc(s, &s->SD_s, (int64_t)W * 2 * 2 * N));
+    AFQMC_TRY(talloc(s, &s->ThT_f, wall));
     AFQMC_TRY(talloc(s, &s->ThT_h, wall));
     AFQMC_TRY(talloc(s, &s->ThT_l, wall));
+    AFQMC_TRY(talloc(s, &s->ThT_s, (int64_t)W * 4 * N));
     AFQMC_TRY(talloc(s, &s->tE, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->XE, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->tFB, (int64_t)W * 4 * nch));
@@ -411,15 +493,17 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->E1, W));
     // static operands
     const double* Ltr = static_cast<const double*>(wk->f.Lt[0]);  // real [Nchol][N][M]
+    split_rows(Ltr, M, (int64_t)nch * N, M, s->Lt_h, s->Lt_l, s->Lt_s, st);
     count_launch();
-    split_f64_kernel<<<nb(nch * NM), kT, 0, st>>>(Ltr, s->Lt_h, s->Lt_l, nch * NM);
+    split_f64_kernel<<<nb(nch * NM), kT, 0, st>>>(Ltr, s->Ltp_h, s->Ltp_l, nch * NM);
     dim3 gl((unsigned)((MM + 31) / 32), (unsigned)((nch + 31) / 32));
     count_launch();
     LT_kernel<<<gl, dim3(32, 8), 0, st>>>(wk->ham->L, MM, nch, s->LT_h, s->LT_l);
     count_launch();
     split_f64_kernel<<<nb(MM), kT, 0, st>>>(wk->f.Bh, s->Bh_h, s->Bh_l, MM);
     count_launch();
-    psiT_kernel<<<nb(NM), kT, 0, st>>>(wk->f.Psi[0], M, N, s->PsiT_h, s->PsiT_l);
+    psiT_kernel<<<nb(NM), kT, 0, st>>>(wk->f.Psi[0], M, N, s->PsiT_f);
+    split_rows(s->PsiT_f, M, N, M, s->PsiT_h, s->PsiT_l, s->PsiT_s, st);
     return tc_sync_walkers_from_fp64(wk, st);
 }
 
@@ -456,29 +540,34 @@ int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
 int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, W = s->W, WS = 2 * W, nch = s->Nchol;
-    AFQMC_TRY(overlap_logdet(wk, s->PhiT_h[s->cur], s->PhiT_l[s->cur], true, st));
+    AFQMC_TRY(overlap_logdet(wk, s->cur, true, st));
     count_launch();
     logS_pair_kernel<<<nb(W), kT, 0, st>>>(s->ld, W, wk->logS_old);
     count_launch();
-    sinv_doubled_kernel<<<nb((int64_t)WS * 4 * N * N), kT, 0, st>>>(s->S, WS, N, s->SD_h, s->SD_l);
-    {   // Theta^T = (Phi S^-1)^T  [WS][2N][M]
+    sinv_doubled_kernel<<<(unsigned)(((int64_t)WS * N + 7) / 8), kT, 0, st>>>(
+        s->S, WS, N, reinterpret_cast<__half*>(s->SD_h), reinterpret_cast<__half*>(s->SD_l), s->SD_s);
+    {   // Theta^T = (Phi S^-1)^T  [WS][2N][M] fp32, then its row-scaled pair
         EpiParams e;
-        e.kind = EPI_SPLIT;
+        e.kind = EPI_F32;
         e.rows_valid = 2 * N;
         e.cols_valid = M;
         e.ld = M;
         e.ob = 2LL * N * M;
-        e.out_hi = s->ThT_h;
-        e.out_lo = s->ThT_l;
-        AFQMC_TRY(tc_gemm(smat(s->SD_h, s->SD_l, 2 * N, 2 * N, WS), BatchMap{1, WS},
-                          smat(s->Phi_h, s->Phi_l, 2 * N, M, WS), BatchMap{1, WS}, 2 * N, M, 2 * N, WS, e,
-                          M % 256 == 0 ? 256 : 128, wk->flags, st));
+        e.out_f32 = s->ThT_f;
+        AFQMC_TRY(tc_gemm(smat(s->SD_h, s->SD_l, 2 * N, 2 * N, WS, s->SD_s), BatchMap{1, WS},
+                          smat(s->Phi_h, s->Phi_l, 2 * N, M, WS, s->Phi_s), BatchMap{1, WS}, 2 * N, M, 2 * N, WS, e,
+                          128, true, wk->flags, st));
+        split_rows(s->ThT_f, M, (int64_t)WS * 2 * N, M, s->ThT_h, s->ThT_l, s->ThT_s, st);
     }
     if (wk->ev0) cudaEventRecord(wk->ev0, st);
     if (measure) {
-        AFQMC_TRY(tc_energy(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N), smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N),
-                            N, nch, WS, M, s->tE, s->XE, wk->flags, st));
+        AFQMC_TRY(tc_energy(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N, 1, s->Lt_s),
+                            smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N, 1, s->ThT_s), N, nch, WS, M, s->tE,
+                            s->XE, wk->flags, st));
     } else {
+        const int64_t n = (int64_t)WS * 2 * N * M;
+        count_launch();
+        split_f32_kernel<<<nb(n), kT, 0, st>>>(s->ThT_f, s->Pacc_h, s->Pacc_l, n);  // plain pair (scratch)
         EpiParams e;
         e.kind = EPI_F32;
         e.rows_valid = 2LL * WS;
@@ -486,8 +575,8 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
         e.ld = nch;
         e.out_f32 = s->tFB;
         const int64_t K = (int64_t)N * M;
-        AFQMC_TRY(tc_gemm(smat(s->ThT_h, s->ThT_l, K, 2LL * WS), BatchMap{}, smat(s->Lt_h, s->Lt_l, K, nch),
-                          BatchMap{}, 2LL * WS, nch, K, 1, e, 256, wk->flags, st));
+        AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, K, 2LL * WS), BatchMap{}, smat(s->Ltp_h, s->Ltp_l, K, nch),
+                          BatchMap{}, 2LL * WS, nch, K, 1, e, 256, false, wk->flags, st));
         count_launch();
         fb_combine_kernel<<<nb((int64_t)WS * nch), kT, 0, st>>>(s->tFB, WS, nch, s->tE);
     }
@@ -495,7 +584,10 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
         cudaEventRecord(wk->ev1, st);
         wk->ev_valid = true;
     }
-    if (measure) e1_kernel<<<W, kT, 0, st>>>(wk->f.ht[0], wk->f.ht[1], s->ThT_h, s->ThT_l, M, N, s->E1);
+    if (measure) {
+        count_launch();
+        e1_kernel<<<W, kT, 0, st>>>(wk->f.ht[0], wk->f.ht[1], s->ThT_f, M, N, s->E1);
+    }
     const double cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
     count_launch();
     le_mixed_kernel<<<W, kT, 0, st>>>(s->E1, s->tE, s->XE, nch, wk->ham->E0, wk->tau, cap, measure ? 1 : 0, wk->E_L,
@@ -520,7 +612,7 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
         e.out_hi = s->A_h;
         e.out_lo = s->A_l;
         AFQMC_TRY(tc_gemm(smat(s->cf_h, s->cf_l, nch, 2LL * W), BatchMap{}, smat(s->LT_h, s->LT_l, nch, MM), BatchMap{},
-                          2LL * W, MM, nch, 1, e, 256, wk->flags, st));
+                          2LL * W, MM, nch, 1, e, 256, false, wk->flags, st));
     }
     const int64_t rowsAll = (int64_t)W * 4 * N;
     {   // P0 = B Phi -> doubled operand + accumulator
@@ -533,8 +625,8 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
         e.out_hi = s->PD_h[0];
         e.out_lo = s->PD_l[0];
         e.acc = s->Pacc;
-        AFQMC_TRY(tc_gemm(smat(s->PhiT_h[s->cur], s->PhiT_l[s->cur], M, rowsAll), BatchMap{},
-                          smat(s->Bh_h, s->Bh_l, M, M), BatchMap{}, rowsAll, M, M, 1, e, BNm, wk->flags, st));
+        AFQMC_TRY(tc_gemm(smat(s->PhiTp_h, s->PhiTp_l, M, rowsAll), BatchMap{}, smat(s->Bh_h, s->Bh_l, M, M),
+                          BatchMap{}, rowsAll, M, M, 1, e, BNm, false, wk->flags, st));
     }
     const float sq = (float)sqrt(wk->tau);
     for (int k = 1; k <= wk->opts.k_taylor; ++k) {
@@ -550,26 +642,25 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
         e.acc = s->Pacc;
         e.scale = sq / (float)k;
         AFQMC_TRY(tc_gemm(smat(s->PD_h[src], s->PD_l[src], 2LL * M, 4LL * N, W), BatchMap{1, W},
-                          smat(s->A_h, s->A_l, 2LL * M, M, W), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, BNm,
+                          smat(s->A_h, s->A_l, 2LL * M, M, W), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, BNm, false,
                           wk->flags, st));
     }
     const int nxt = s->cur ^ 1;
-    {
+    {   // Phi' = B Pacc  (FP64 master of the proposed walkers)
         const int64_t n = rowsAll * M;
         count_launch();
         split_f32_kernel<<<nb(n), kT, 0, st>>>(s->Pacc, s->Pacc_h, s->Pacc_l, n);
         EpiParams e;
-        e.kind = EPI_BFINAL;
+        e.kind = EPI_F64;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
         e.ld = M;
         e.out_f64 = s->PhiT[nxt];
-        e.out_hi = s->PhiT_h[nxt];
-        e.out_lo = s->PhiT_l[nxt];
         AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, M, rowsAll), BatchMap{}, smat(s->Bh_h, s->Bh_l, M, M), BatchMap{},
-                          rowsAll, M, M, 1, e, BNm, wk->flags, st));
+                          rowsAll, M, M, 1, e, BNm, false, wk->flags, st));
     }
-    AFQMC_TRY(overlap_logdet(wk, s->PhiT_h[nxt], s->PhiT_l[nxt], false, st));
+    split_walkers(s, nxt, st);
+    AFQMC_TRY(overlap_logdet(wk, nxt, false, st));
     count_launch();
     logS_pair_kernel<<<nb(W), kT, 0, st>>>(s->ld, W, wk->logS_new);
     WeightArgs a;
@@ -588,13 +679,34 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     weight_update(a, st);
     const int64_t per = 4LL * N * M;
     count_launch();
-    keep_rejected_kernel<<<nb((int64_t)W * per), kT, 0, st>>>(wk->accept, W, per, s->PhiT[s->cur], s->PhiT[nxt],
-                                                              s->PhiT_h[s->cur], s->PhiT_l[s->cur], s->PhiT_h[nxt],
-                                                              s->PhiT_l[nxt]);
+    keep_rejected_kernel<<<nb((int64_t)W * per), kT, 0, st>>>(wk->accept, W, per, s->PhiT[s->cur], s->PhiT[nxt]);
     s->cur = nxt;
-    dim3 g((M + 31) / 32, (2 * N + 31) / 32, 2 * W);
-    count_launch();
-    phiT_to_phi_kernel<<<g, dim3(32, 8), 0, st>>>(s->PhiT_h[s->cur], s->PhiT_l[s->cur], M, 2 * N, s->Phi_h, s->Phi_l);
+    refresh_operands(s, st);
+    return AFQMC_OK;
+}
+
+int tc_debug_terms(afqmc_walkers* wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X, double* E1) {
+    TcState* s = wk->tc;
+    if (!s) return fail(AFQMC_ERR_BADARG, "debug_mixed_terms: not a BF16X3 walker set");
+    AFQMC_TRY(tc_measure(wk, true, 0));
+    AFQMC_CUDA_TRY(cudaDeviceSynchronize());
+    const int64_t nst = (int64_t)s->W * 4 * s->N * s->N;
+    if (ST) {
+        std::vector<float> h(nst);
+        AFQMC_CUDA_TRY(cudaMemcpy(h.data(), s->ST, nst * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nst; ++i) ST[i] = h[i];
+    }
+    if (Sinv) AFQMC_CUDA_TRY(cudaMemcpy(Sinv, s->S, (nst / 2) * 16, cudaMemcpyDeviceToHost));
+    const int64_t nth = (int64_t)s->W * 4 * s->N * s->M;
+    if (ThetaT) {
+        std::vector<float> h(nth);
+        AFQMC_CUDA_TRY(cudaMemcpy(h.data(), s->ThT_f, nth * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nth; ++i) ThetaT[i] = h[i];
+    }
+    const int64_t nt = (int64_t)s->W * 2 * s->Nchol;
+    if (t) AFQMC_CUDA_TRY(cudaMemcpy(t, s->tE, nt * 16, cudaMemcpyDeviceToHost));
+    if (X) AFQMC_CUDA_TRY(cudaMemcpy(X, s->XE, nt * 16, cudaMemcpyDeviceToHost));
+    if (E1) AFQMC_CUDA_TRY(cudaMemcpy(E1, s->E1, (int64_t)s->W * 16, cudaMemcpyDeviceToHost));
     return AFQMC_OK;
 }
 

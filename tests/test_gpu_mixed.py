@@ -34,8 +34,9 @@ def test_energy_at_start_matches_fp64(M, N, nch, W):
     h, L, E0, Psi = system(M, N, nch, 11)
     rng = np.random.default_rng(5)
     Phi0 = []
+    amp = 0.8 / np.sqrt(M)       # perturbation norm ~1 per column: overlap condition numbers O(10)
     for s in range(2):
-        z = Psi[s][None] + 0.1 * (rng.standard_normal((W, M, N)) + 1j * rng.standard_normal((W, M, N)))
+        z = Psi[s][None] + amp * (rng.standard_normal((W, M, N)) + 1j * rng.standard_normal((W, M, N)))
         Phi0.append(np.linalg.qr(z)[0])
     a, b = pair(h, L, E0, Psi, W, 0.005, 5, Phi0)
     with a, b:

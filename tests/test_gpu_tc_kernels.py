@@ -30,11 +30,26 @@ def split(x):
     return hi, lo
 
 
-def emul(A, B):
-    Ah, Al = split(A)
-    Bh, Bl = split(B)
+def split_rows(x):
+    """Row-scaled split: scale = 2^(e-11) with ||x_row||_2 < 2^e, hi = rint(x/scale) (an
+    integer, |hi| <= 2048), lo = fp16(x/scale - hi).  Returns (hi*scale, lo*scale)."""
+    nrm = np.sqrt(np.sum(x * x, axis=-1, keepdims=True))
+    e = np.frexp(np.where(nrm > 0, nrm, 1.0))[1]
+    sc = np.where(nrm > 0, np.ldexp(1.0, e - 11), 1.0)
+    y = x / sc
+    hi = np.rint(y)
+    lo = (y - hi).astype(np.float16).astype(np.float64)
+    return hi * sc, lo * sc
+
+
+def emul(A, B, exact=False):
+    """What the tensor cores form: hi*hi + hi*lo + lo*hi (plain) or + lo*lo (exact mode)."""
+    sp = split_rows if exact else split
+    Ah, Al = sp(A)
+    Bh, Bl = sp(B)
     mm = lambda a, b: np.matmul(a, np.swapaxes(b, -1, -2))
-    return mm(Ah, Bh) + mm(Ah, Bl) + mm(Al, Bh)
+    C = mm(Ah, Bh) + mm(Ah, Bl) + mm(Al, Bh)
+    return C + mm(Al, Bl) if exact else C
 
 
 @pytest.fixture(scope="module")
@@ -46,7 +61,7 @@ def dbg():
     vp = ctypes.c_void_p
     L.afqmc_debug_split_gemm.restype = ctypes.c_int
     L.afqmc_debug_split_gemm.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_int, vp]
+                                         ctypes.c_int, ctypes.c_int, vp]
     L.afqmc_debug_energy.restype = ctypes.c_int
     L.afqmc_debug_energy.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     return L
@@ -64,7 +79,7 @@ def test_split_gemm_matches_split_emulation(dbg, nb, rows, cols, K, BN):
     A = rng.standard_normal((nb, rows, K))
     B = rng.standard_normal((nb, cols, K))
     C = np.zeros((nb, rows, cols))
-    rc = dbg.afqmc_debug_split_gemm(A.ctypes.data, B.ctypes.data, nb, rows, cols, K, BN, C.ctypes.data)
+    rc = dbg.afqmc_debug_split_gemm(A.ctypes.data, B.ctypes.data, nb, rows, cols, K, BN, 0, C.ctypes.data)
     assert rc == 0, api.afqmc_last_error()
     ref = emul(A, B)
     exact = np.matmul(A, np.swapaxes(B, -1, -2))
@@ -79,6 +94,42 @@ def test_split_gemm_matches_split_emulation(dbg, nb, rows, cols, K, BN):
     assert np.max(np.abs(C - exact)) < 3e-5 * big
 
 
+@pytest.mark.parametrize("nb,rows,cols,K", [(1, 256, 384, 512), (3, 130, 100, 136), (2, 64, 128, 1024)])
+def test_exact_mode_is_unbiased(dbg, nb, rows, cols, K):
+    """Row-scaled operands: the hi*hi sum is exact, so the only accumulation error left is
+    the rounding of the 2^-8 smaller cross terms -- no systematic bias toward zero."""
+    rng = np.random.default_rng(rows * 3 + K)
+    A = rng.standard_normal((nb, rows, K)) * np.exp(rng.uniform(-3, 3, (nb, rows, 1)))
+    B = rng.standard_normal((nb, cols, K)) * np.exp(rng.uniform(-3, 3, (nb, cols, 1)))
+    C = np.zeros((nb, rows, cols))
+    rc = dbg.afqmc_debug_split_gemm(A.ctypes.data, B.ctypes.data, nb, rows, cols, K, 128, 1, C.ctypes.data)
+    assert rc == 0, api.afqmc_last_error()
+    ref = emul(A, B, exact=True)
+    scale = np.linalg.norm(A, axis=-1)[:, :, None] * np.linalg.norm(B, axis=-1)[:, None, :]
+    err = (C - ref) / scale
+    exact = np.matmul(A, np.swapaxes(B, -1, -2))
+    print(f"exact gemm K={K}: max err/(|a||b|) {np.max(np.abs(err)):.2e}, mean signed "
+          f"{np.mean((C - ref) * np.sign(ref) / scale):.2e}, vs float64 {np.max(np.abs(C - exact) / scale):.2e}")
+    assert np.max(np.abs(err)) < 5e-8
+    assert abs(np.mean((C - ref) * np.sign(ref) / scale)) < 1e-10
+    assert np.max(np.abs(C - exact) / scale) < 1e-6
+
+
+def test_exact_mode_integer_products_are_exact(dbg):
+    """Integer rows with 2-norm in [1024, 2048): scale 1, lo = 0, results must be exact."""
+    rng = np.random.default_rng(3)
+    K = 1024
+    A = rng.integers(-60, 61, (1, 128, K)).astype(np.float64)
+    B = rng.integers(-60, 61, (1, 128, K)).astype(np.float64)
+    for Z in (A, B):
+        n = np.sqrt((Z * Z).sum(-1))
+        assert np.all((n >= 1024) & (n < 2048))
+    C = np.zeros((1, 128, 128))
+    rc = dbg.afqmc_debug_split_gemm(A.ctypes.data, B.ctypes.data, 1, 128, 128, K, 128, 1, C.ctypes.data)
+    assert rc == 0, api.afqmc_last_error()
+    assert np.array_equal(C, np.matmul(A, np.swapaxes(B, -1, -2)))
+
+
 @pytest.mark.parametrize("Np,Nchol,nws,M", [(128, 3, 2, 128), (64, 5, 3, 192), (32, 9, 5, 128), (128, 2, 3, 512)])
 def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M):
     rng = np.random.default_rng(Np * 7 + Nchol)
@@ -88,10 +139,72 @@ def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M):
     X = np.zeros((nws, Nchol), dtype=np.complex128)
     rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, t.ctypes.data, X.ctypes.data)
     assert rc == 0, api.afqmc_last_error()
-    Tr = np.stack([emul(Lt, np.broadcast_to(Th[w, 0], (Nchol, Np, M))) for w in range(nws)])
-    Ti = np.stack([emul(Lt, np.broadcast_to(Th[w, 1], (Nchol, Np, M))) for w in range(nws)])
+    Tr = np.stack([emul(Lt, np.broadcast_to(Th[w, 0], (Nchol, Np, M)), exact=True) for w in range(nws)])
+    Ti = np.stack([emul(Lt, np.broadcast_to(Th[w, 1], (Nchol, Np, M)), exact=True) for w in range(nws)])
     T = Tr + 1j * Ti                                     # [nws, Nchol, Np, Np]: T[a][b] = Lt[a] . Th^T[b]
     t_ref = np.trace(T, axis1=2, axis2=3)
     X_ref = np.einsum("wnab,wnba->wn", T, T)
-    assert np.max(np.abs(t - t_ref)) < 1e-5 * np.max(np.abs(t_ref)) + 1e-6
-    assert np.max(np.abs(X - X_ref)) < 1e-5 * np.max(np.abs(X_ref)) + 1e-6
+    print(f"energy Np={Np}: t err {np.max(np.abs(t - t_ref)) / np.max(np.abs(t_ref)):.2e}, "
+          f"X err {np.max(np.abs(X - X_ref)) / np.max(np.abs(X_ref)):.2e}")
+    assert np.max(np.abs(t - t_ref)) < 2e-6 * np.max(np.abs(t_ref)) + 1e-9
+    assert np.max(np.abs(X - X_ref)) < 2e-6 * np.max(np.abs(X_ref)) + 1e-9
+
+
+@pytest.mark.parametrize("M,N,nch,W", [(128, 32, 96, 3), (256, 128, 64, 2)])
+def test_mixed_intermediates_match_numpy(dbg, M, N, nch, W):
+    """Theta^T, the traces and the one-body energy of a BF16X3 walker set against numpy."""
+    from paper_2003_01831_gb300 import synthetic as syn
+    from paper_2003_01831_gb300.walkers import AFQMC
+    rng = np.random.default_rng(17)
+    h, L, E0 = syn.make_hamiltonian(M, nch, rng)
+    Psi = syn.make_trial(h, N, N)
+    Phi0 = []
+    for s in range(2):
+        z = Psi[s][None] + 0.1 * (rng.standard_normal((W, M, N)) + 1j * rng.standard_normal((W, M, N)))
+        Phi0.append(np.linalg.qr(z)[0])
+    dbg.afqmc_debug_mixed_terms.restype = ctypes.c_int
+    dbg.afqmc_debug_mixed_terms.argtypes = [ctypes.c_void_p] * 7
+    with AFQMC(h, L, E0, Psi[0], Psi[1], W, 0.01, Phi0=Phi0, precision=api.PREC_BF16X3) as g:
+        ST = np.zeros((W, 2, 2, N, N))
+        Si = np.zeros((W, 2, N, N), complex)
+        ThT = np.zeros((W, 2, 2, N, M))
+        t = np.zeros((W, 2, nch), complex)
+        X = np.zeros((W, 2, nch), complex)
+        E1 = np.zeros(W, complex)
+        rc = dbg.afqmc_debug_mixed_terms(g.wk, ST.ctypes.data, Si.ctypes.data, ThT.ctypes.data, t.ctypes.data,
+                                         X.ctypes.data, E1.ctypes.data)
+        assert rc == 0, api.afqmc_last_error()
+    P = Psi[0].real
+    for w in range(W):
+        e1 = 0
+        for s in range(2):
+            S = P.T @ Phi0[s][w]
+            Sg = (ST[w, s, 0] + 1j * ST[w, s, 1]).T
+            print(f"M={M} N={N} w={w} s={s}: S err {np.max(np.abs(Sg - S)) / np.max(np.abs(S)):.2e}, "
+                  f"Sinv err {np.max(np.abs(Si[w, s] - np.linalg.inv(S))) / np.max(np.abs(np.linalg.inv(S))):.2e}, "
+                  f"cond {np.linalg.cond(S):.1f}")
+            if w == 0 and s == 0:
+                A = np.ascontiguousarray(np.concatenate([Phi0[s][w].real.T, Phi0[s][w].imag.T])[None])
+                B = np.ascontiguousarray(P.T[None])
+                for ex in (0, 1):
+                    C = np.zeros((1, 2 * N, N))
+                    assert dbg.afqmc_debug_split_gemm(A.ctypes.data, B.ctypes.data, 1, 2 * N, N, M, 128, ex,
+                                                      C.ctypes.data) == 0
+                    Sd = (C[0, :N] + 1j * C[0, N:]).T
+                    print(f"   standalone exact={ex}: S err {np.max(np.abs(Sd - S)) / np.max(np.abs(S)):.2e}, "
+                          f"vs pipeline {np.max(np.abs(Sd - Sg)) / np.max(np.abs(S)):.2e}")
+            Th = Phi0[s][w] @ np.linalg.inv(S)                                  # [M, N]
+            got = ThT[w, s, 0] + 1j * ThT[w, s, 1]                               # [N, M]
+            err = np.max(np.abs(got - Th.T)) / np.max(np.abs(Th))
+            print(f"M={M} N={N} w={w} s={s}: Theta err {err:.2e}")
+            assert err < 2e-7 * np.linalg.cond(S) + 1e-6
+            Lt = np.einsum("ka,nkl->nal", P, L)
+            T = np.matmul(Lt, Th)
+            tr = np.trace(T, axis1=1, axis2=2)
+            Xr = np.einsum("nab,nba->n", T, T)
+            et = np.max(np.abs(t[w, s] - tr)) / np.max(np.abs(tr))
+            ex = np.max(np.abs(X[w, s] - Xr)) / np.max(np.abs(Xr))
+            print(f"   t err {et:.2e}  X err {ex:.2e}")
+            assert et < 5e-7 * np.linalg.cond(S) + 2e-6 and ex < 5e-7 * np.linalg.cond(S) + 2e-6
+            e1 += np.sum((P.T @ h) * Th.T)
+        assert abs(E1[w] - e1) < 1e-5 * abs(e1)
