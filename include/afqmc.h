@@ -160,6 +160,30 @@ int afqmc_set_walkers(afqmc_wk_t wk, const double* Phi, const double* w, int64_t
  * ((a + 0.5) 2^-32, (b + 0.5) 2^-32): x = sqrt(-2 ln u1) (cos, sin)(2 pi u2). */
 int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, void* stream);
 
+/* ---- Allocation-free log-overlap ---------------------------------------------
+ * This entry point has no counterpart in the paper; it exists for callers that must not
+ * allocate device memory when they call it -- e.g. a service that gave the whole device to
+ * its own memory pool (where a cudaMalloc can fail at run time) or a latency-critical loop
+ * that must stay off the allocator (which can synchronise the device).
+ *
+ * logS[w] = sum_s log det(Psi_s^+ Phi_s[w]) for W walkers, the same quantity afqmc_energy
+ * reports, computed in FP64 (batched overlap GEMM + Gauss-Jordan log-determinant).
+ *   Psi_up [M][Nup], Psi_dn [M][Ndn]  complex trial orbitals (device memory)
+ *   Phi    complex [W][M*Nup + M*Ndn]  walkers in the layout of afqmc_init_walkers' Phi0
+ *                                      (device memory)
+ *   logS   complex [W] output (device memory), imaginary part in (-pi, pi]
+ * Scratch: a fixed 16 MiB device array inside the library (every GPU that loads the library
+ * holds it until the process exits); the call needs W*(Nup^2 + Ndn^2 + 2)*16 + 256 bytes of
+ * it and returns AFQMC_ERR_SHAPE beyond that.  No device memory is allocated or freed.
+ * The first call on a device looks up that device's scratch address (cudaGetSymbolAddress,
+ * with the device current); make that first call before any stream capture.
+ * Every call shares the one scratch array and leaves its contents behind; calls whose device
+ * work overlaps (different streams or threads on the same device) race on it, so serialise
+ * them.  The call synchronises `stream` to read its status word.
+ * Errors: BADARG (NULL or host pointer), SHAPE, NONFINITE, SINGULAR, CUDA. */
+int afqmc_log_overlap_noalloc(const double* Psi_up, const double* Psi_dn, int Nup, int Ndn, int M, int W,
+                              const double* Phi, double* logS, void* stream);
+
 /* ---- Diagnostics -----------------------------------------------------------
  * Device time of the last afqmc_step's energy contraction (ms) and the number
  * of kernels it launched per step; -1 when unknown. */

@@ -33,7 +33,7 @@ EXPORTED = [
     "afqmc_default_opts", "afqmc_create_hamiltonian", "afqmc_destroy_hamiltonian",
     "afqmc_init_walkers", "afqmc_destroy_walkers", "afqmc_step", "afqmc_energy",
     "afqmc_energy_backward", "afqmc_get_walkers", "afqmc_set_walkers",
-    "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error",
+    "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
 ]
 
 
@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
         "afqmc_philox_fields": (i, [u64, i64, i, i, vp, vp]),
         "afqmc_last_step_stats": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i)]),
         "afqmc_last_error": (ctypes.c_char_p, []),
+        "afqmc_log_overlap_noalloc": (i, [vp, vp, i, i, i, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -192,3 +193,8 @@ def afqmc_last_step_stats(wk: int):
 
 def afqmc_last_error() -> str:
     return lib().afqmc_last_error().decode()
+
+
+def afqmc_log_overlap_noalloc(Psi_up, Psi_dn, Nup: int, Ndn: int, M: int, W: int, Phi, logS, stream=None):
+    _check(lib().afqmc_log_overlap_noalloc(_ptr(Psi_up), _ptr(Psi_dn), int(Nup), int(Ndn), int(M), int(W), _ptr(Phi),
+                                           _ptr(logS), _stream(stream)))
