@@ -187,27 +187,34 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     for (int k = 0; k < N; ++k) {
         // pivot: max |re|+|im| over rows k..N-1 of column k, lowest index on ties
+        // (warp shuffles, then one pass over the per-warp winners)
         double best = -1.0;
         int bi = N;
         for (int i = k + t; i < N; i += kThreads) {
             const double v = abs1(A[(int64_t)i * N + k]);
-            if (v > best) { best = v; bi = i; }
+            if (v > best || (v != v && best == best)) { best = v; bi = i; }
         }
-        red_v[t] = best;
-        red_i[t] = bi;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (v2 > best || (v2 == best && i2 < bi) || (v2 != v2 && best == best)) { best = v2; bi = i2; }
+        }
+        if ((t & 31) == 0) {
+            red_v[t >> 5] = best;
+            red_i[t >> 5] = bi;
+        }
         __syncthreads();
-        for (int s = kThreads / 2; s > 0; s >>= 1) {
-            if (t < s) {
-                const double v2 = red_v[t + s];
-                const int i2 = red_i[t + s];
-                if (v2 > red_v[t] || (v2 == red_v[t] && i2 < red_i[t])) { red_v[t] = v2; red_i[t] = i2; }
-            }
-            __syncthreads();
-        }
         if (t == 0) {
-            s_piv = red_i[0];
-            if (!(red_v[0] > 0.0)) s_singular = isnan(red_v[0]) ? 2 : 1;
-            perm[k] = red_i[0];
+            double bv = red_v[0];
+            int bidx = red_i[0];
+            for (int q = 1; q < kThreads / 32; ++q) {
+                const double v2 = red_v[q];
+                const int i2 = red_i[q];
+                if (v2 > bv || (v2 == bv && i2 < bidx) || (v2 != v2 && bv == bv)) { bv = v2; bidx = i2; }
+            }
+            s_piv = bidx;
+            if (!(bv > 0.0)) s_singular = (bv != bv) ? 2 : 1;
+            perm[k] = bidx;
         }
         __syncthreads();
         if (s_singular) break;

@@ -96,33 +96,97 @@ __device__ __forceinline__ void store_split(bf16* hi, bf16* lo, int64_t idx, flo
     lo[idx] = l;
 }
 
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+// 32 consecutive values (times sgn) as a plain bf16 pair, 16-byte stores when aligned.
+__device__ __forceinline__ void store_split32(bf16* hi, bf16* lo, int64_t base, const float (&v)[32], float sgn) {
+    bf16* H = hi + base;
+    bf16* L = lo + base;
+    if (aligned16(H) && aligned16(L)) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            uint32_t ph[4], pl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                bf16 h0, l0, h1, l1;
+                split_bf16(sgn * v[8 * g + 2 * q], h0, l0);
+                split_bf16(sgn * v[8 * g + 2 * q + 1], h1, l1);
+                ph[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                pl[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            reinterpret_cast<uint4*>(H)[g] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+            reinterpret_cast<uint4*>(L)[g] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+        }
+    } else {
+        for (int q = 0; q < 32; ++q) store_split(hi, lo, base + q, sgn * v[q]);
+    }
+}
+
+// acc[base + q] (+)= sgn * v[q], 16-byte accesses when aligned
+__device__ __forceinline__ void acc32(float* acc, int64_t base, const float (&v)[32], float sgn, bool add) {
+    float* A = acc + base;
+    if (aligned16(A)) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            float4 o = add ? reinterpret_cast<float4*>(A)[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+            o.x += sgn * v[4 * g];
+            o.y += sgn * v[4 * g + 1];
+            o.z += sgn * v[4 * g + 2];
+            o.w += sgn * v[4 * g + 3];
+            reinterpret_cast<float4*>(A)[g] = o;
+        }
+    } else {
+        for (int q = 0; q < 32; ++q) A[q] = (add ? A[q] : 0.f) + sgn * v[q];
+    }
+}
+
 // Writes 32 consecutive output columns [c0, c0+32) of row r (per batch b).
 __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, const float (&v)[32]) {
     if (r >= e.rows_valid) return;
     const int ncol = (int)(e.cols_valid - c0 < 32 ? e.cols_valid - c0 : 32);
     if (ncol <= 0) return;
+    const bool full = ncol == 32;
     switch (e.kind) {
         case EPI_F32: {
             float* o = e.out_f32 + b * e.ob + r * e.ld + c0;
-            for (int j = 0; j < ncol; ++j) o[j] = v[j];
+            if (full && aligned16(o)) {
+#pragma unroll
+                for (int g = 0; g < 8; ++g)
+                    reinterpret_cast<float4*>(o)[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            } else {
+                for (int j = 0; j < ncol; ++j) o[j] = v[j];
+            }
             break;
         }
         case EPI_F64: {
             double* o = e.out_f64 + b * e.ob + r * e.ld + c0;
-            for (int j = 0; j < ncol; ++j) o[j] = (double)v[j];
+            if (full && aligned16(o)) {
+#pragma unroll
+                for (int g = 0; g < 16; ++g)
+                    reinterpret_cast<double2*>(o)[g] = make_double2((double)v[2 * g], (double)v[2 * g + 1]);
+            } else {
+                for (int j = 0; j < ncol; ++j) o[j] = (double)v[j];
+            }
             break;
         }
         case EPI_SPLIT: {
             const int64_t base = b * e.ob + r * e.ld + c0;
-            for (int j = 0; j < ncol; ++j) store_split(e.out_hi, e.out_lo, base + j, v[j]);
+            if (full) store_split32(e.out_hi, e.out_lo, base, v, 1.0f);
+            else
+                for (int j = 0; j < ncol; ++j) store_split(e.out_hi, e.out_lo, base + j, v[j]);
             break;
         }
         case EPI_HSPOT: {
             // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
             const int64_t w = r >> 1, c = r & 1;
-            for (int j = 0; j < ncol; ++j) {
-                const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
-                store_split(e.out_hi, e.out_lo, (w * e.M + i) * (2 * e.M) + c * e.M + k, v[j]);
+            const int64_t i0 = c0 / e.M, k0 = c0 % e.M;
+            if (full && k0 + 32 <= e.M) {
+                store_split32(e.out_hi, e.out_lo, (w * e.M + i0) * (2 * e.M) + c * e.M + k0, v, 1.0f);
+            } else {
+                for (int j = 0; j < ncol; ++j) {
+                    const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
+                    store_split(e.out_hi, e.out_lo, (w * e.M + i) * (2 * e.M) + c * e.M + k, v[j]);
+                }
             }
             break;
         }
@@ -131,6 +195,17 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
             const int64_t N = e.N, M = e.M;
             const int64_t ws = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
             const int64_t re_row = (ws * 2 + 0) * N + jj, im_row = (ws * 2 + 1) * N + jj;
+            if (full) {
+                acc32(e.acc, r * M + c0, v, 1.0f, false);
+                if (c == 0) {
+                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + c0, v, 1.0f);
+                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + M + c0, v, 1.0f);
+                } else {
+                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + M + c0, v, -1.0f);
+                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + c0, v, 1.0f);
+                }
+                break;
+            }
             for (int j = 0; j < ncol; ++j) {
                 const int64_t i = c0 + j;
                 const float p = v[j];
@@ -152,14 +227,26 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
             const int64_t ws = (int64_t)b * 2 + s;
             const int64_t re_row = (ws * 2 + 0) * N + jj, im_row = (ws * 2 + 1) * N + jj;
             const float sc = e.scale;
+            if (full) {
+                if (c == 0) {  // C_re -> new_im = sc * C_re
+                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + M + c0, v, -sc);
+                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + c0, v, sc);
+                    acc32(e.acc, im_row * M + c0, v, sc, true);
+                } else {       // C_im -> new_re = -sc * C_im
+                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + c0, v, -sc);
+                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + M + c0, v, -sc);
+                    acc32(e.acc, re_row * M + c0, v, -sc, true);
+                }
+                break;
+            }
             for (int j = 0; j < ncol; ++j) {
                 const int64_t i = c0 + j;
-                if (c == 0) {  // C_re -> new_im = sc * C_re
+                if (c == 0) {
                     const float ni = sc * v[j];
                     store_split(e.out_hi, e.out_lo, re_row * 2 * M + M + i, -ni);
                     store_split(e.out_hi, e.out_lo, im_row * 2 * M + i, ni);
                     e.acc[im_row * M + i] += ni;
-                } else {       // C_im -> new_re = -sc * C_im
+                } else {
                     const float nr = -sc * v[j];
                     store_split(e.out_hi, e.out_lo, re_row * 2 * M + i, nr);
                     store_split(e.out_hi, e.out_lo, im_row * 2 * M + M + i, nr);
@@ -532,46 +619,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 for (int rho = 0; rho < Q; ++rho) {
                     const int wsub = (mu - rho + Q) % Q;   // sub-block I publish
                     const int beta = (mu + rho) % Q;       // partner sub-block I read
-                    float vr[32], vi[32];
                     // publish T[my rows][block wsub] (re, im), scaled to true units
                     {
+                        float pr_[32], pi_[32];
                         const int cr = j * 2 * Np + 32 * wsub, ci = cr + Np;
-                        load_cplx_block(t1, t2, cr, ci, vr, vi);
+                        load_cplx_block(t1, t2, cr, ci, pr_, pi_);
 #pragma unroll
                         for (int q = 0; q < 32; ++q) {
-                            vr[q] *= sa * colscale[cr + q];
-                            vi[q] *= sa * colscale[ci + q];
-                            my_slot[lane * 32 + (q ^ lane)] = vr[q];
-                            my_slot[32 * 32 + lane * 32 + (q ^ lane)] = vi[q];
+                            my_slot[lane * 32 + (q ^ lane)] = pr_[q] * (sa * colscale[cr + q]);
+                            my_slot[32 * 32 + lane * 32 + (q ^ lane)] = pi_[q] * (sa * colscale[ci + q]);
                         }
                     }
+                    // my own block for the product: issue its TMEM loads before the barrier
+                    uint32_t a1[32], a2[32], b1[32], b2[32];
+                    const int ocr = j * 2 * Np + 32 * beta, oci = ocr + Np;
+                    tmem_ld32_nw(t1 + ocr, a1);
+                    tmem_ld32_nw(t2 + ocr, a2);
+                    tmem_ld32_nw(t1 + oci, b1);
+                    tmem_ld32_nw(t2 + oci, b2);
                     named_bar_epi();
-                    if (beta != wsub) {
-                        const int cr = j * 2 * Np + 32 * beta, ci = cr + Np;
-                        load_cplx_block(t1, t2, cr, ci, vr, vi);
+                    if (rho == 0) {
+                        // diagonal T[a][a]: column `lane` of my own published block
+                        tr += my_slot[lane * 32];
+                        ti += my_slot[32 * 32 + lane * 32];
+                    }
+                    tmem_ld_wait();
+                    float vr[32], vi[32];
 #pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            vr[q] *= sa * colscale[cr + q];
-                            vi[q] *= sa * colscale[ci + q];
-                        }
+                    for (int q = 0; q < 32; ++q) {
+                        vr[q] = (__uint_as_float(a1[q]) + __uint_as_float(a2[q])) * (sa * colscale[ocr + q]);
+                        vi[q] = (__uint_as_float(b1[q]) + __uint_as_float(b2[q])) * (sa * colscale[oci + q]);
                     }
                     const float* ps = xch + (i_blk * Q + beta) * kSlotFloats;
-                    float ar = 0.f, ai = 0.f;
+                    float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         // partner row q, column = my lane
                         const float pr = ps[q * 32 + (lane ^ q)], pi = ps[32 * 32 + q * 32 + (lane ^ q)];
-                        ar = fmaf(vr[q], pr, fmaf(-vi[q], pi, ar));
-                        ai = fmaf(vr[q], pi, fmaf(vi[q], pr, ai));
+                        ar[q & 3] = fmaf(vr[q], pr, fmaf(-vi[q], pi, ar[q & 3]));
+                        ai[q & 3] = fmaf(vr[q], pi, fmaf(vi[q], pr, ai[q & 3]));
                     }
-                    xr += ar;
-                    xi += ai;
-                    if (rho == 0) {
-                        // diagonal element T[a][a] sits in column `lane` of my own block
-#pragma unroll
-                        for (int q = 0; q < 32; ++q)
-                            if (q == lane) { tr += vr[q]; ti += vi[q]; }
-                    }
+                    xr += (double)((ar[0] + ar[1]) + (ar[2] + ar[3]));
+                    xi += (double)((ai[0] + ai[1]) + (ai[2] + ai[3]));
                     named_bar_epi();
                 }
                 // warp reduction, then across the Q warps of this n
