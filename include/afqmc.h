@@ -65,7 +65,12 @@ typedef struct afqmc_opts {
     int    k_qr;         /* re-orthonormalise every k_qr steps (0 = never)         */
     int    weight_mode;  /* AFQMC_WEIGHT_*                                          */
     double fb_cap;       /* cap |xbar_n| <= fb_cap per component (<= 0: no cap)    */
-    int    reserved[8];  /* must be zero                                           */
+    int    walker_offset;/* global index of walker 0 in the Philox counter (>= 0): a
+                            population split over processes as consecutive walker
+                            ranges draws exactly the fields of the whole population  */
+    int    energy_terms; /* BF16X3 energy contraction: 3 = hi*hi + hi*lo + lo*hi,
+                            4 = + lo*lo, 0 = library default                         */
+    int    reserved[6];  /* must be zero                                           */
 } afqmc_opts;
 
 /* Fills the defaults: FP64, K = 6, k_qr = 5, phaseless, fb_cap = 1.0. */
@@ -114,8 +119,9 @@ int afqmc_destroy_walkers(afqmc_wk_t wk);
  *   w <- w |r e^{x.xbar - xbar.xbar/2}| e^{tau (E_T - E0)} max(0, cos arg r),
  *   r = <Psi|Phi'>/<Psi|Phi>; every k_qr-th step Phi = Q R, Phi <- Q.
  * x            fields [nsteps][W][Nchol] doubles, or NULL to draw them on the
- *              device from Philox4x32-10 keyed by `seed` (counter = (n/4, walker,
- *              global step index, 0), Box-Muller; see afqmc_philox_fields).
+ *              device from Philox4x32-10 keyed by `seed` (counter = (n/4,
+ *              walker_offset + walker, global step index, 0), Box-Muller; see
+ *              afqmc_philox_fields).
  * measure_every  if > 0, the mixed energy E_mix = sum w E_L / sum w (weights
  *              and walkers before the step's update) is measured at every step
  *              s (0-based within this call) with s % measure_every == 0 and
@@ -159,6 +165,72 @@ int afqmc_set_walkers(afqmc_wk_t wk, const double* Phi, const double* w, int64_t
  * key (seed & 0xffffffff, seed >> 32), Box-Muller on (u1, u2) =
  * ((a + 0.5) 2^-32, (b + 0.5) 2^-32): x = sqrt(-2 ln u1) (cos, sin)(2 pi u2). */
 int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, void* stream);
+
+/* ---- Batches of independent systems ----------------------------------------
+ * Several independent problems -- each its own Hamiltonian (Sec. V, Eqs. (1), (3)), trial,
+ * shape (M, N, Nchol) and walker count -- advanced together.  Every afqmc_batch_step step
+ * replays one CUDA graph holding the whole step of every system (one chain of kernels per
+ * system; the chains run as parallel graph branches, so small systems fill the GPU
+ * together).  The per-system arithmetic is exactly that of afqmc_step.
+ *
+ * Systems the tensor-core path cannot tile (BF16X3 with M % 64 != 0, N not 32/64/128 or
+ * Nchol % 8 != 0), and every system under AFQMC_PAD_ALWAYS, are padded exactly: extra
+ * orbitals on which h and every L_n vanish, one extra electron per extra orbital in the
+ * trial and in every walker (S = diag(S, 1), so overlaps, Green's function block, force
+ * bias and energies are unchanged), and zero Cholesky vectors up to a multiple of 8.
+ * Padded shapes: N' = 32, 64 or 128 (the smallest >= N), M' = the smallest multiple of 64
+ * >= M + N' - N, Nchol' = Nchol rounded up to a multiple of 8.  Padding needs Nup == Ndn.
+ * Fields come from Philox (see afqmc_philox_fields) with key seed + s * 0x9E3779B97F4A7C15
+ * (mod 2^64) for system s and the batch's global step; x[w][n] does not depend on Nchol,
+ * so a padded system draws the fields of its unpadded self. */
+#define AFQMC_PAD_AUTO    0   /* pad only what the precision needs                    */
+#define AFQMC_PAD_ALWAYS  1   /* pad every system to the tensor-core shapes           */
+
+typedef struct afqmc_system {
+    const double* h;       /* [M][M] real symmetric                                     */
+    const double* L;       /* [Nchol][M][M] real, each L_n symmetric                     */
+    double E0;
+    int M, Nchol;
+    const double* Psi_up;  /* complex [M][Nup]                                           */
+    const double* Psi_dn;  /* complex [M][Ndn]                                           */
+    int Nup, Ndn;
+    int W;                 /* walkers of this system (>= 1)                               */
+    const double* Phi0;    /* complex [W][M*Nup + M*Ndn] or NULL (start at the trial)      */
+} afqmc_system;
+
+typedef struct afqmc_batch* afqmc_batch_t;
+
+/* Creates every system (copies of the inputs, host or device pointers) with the common
+ * tau and opts (NULL = defaults; k_qr applies to the batch's global step).
+ * Errors: BADARG, SHAPE, UNSUPPORTED, SINGULAR, NONFINITE, OOM, CUDA (message names the
+ * failing system). */
+int afqmc_create_batch(int nsys, const afqmc_system* sys, double tau, const afqmc_opts* opts, int pad_mode,
+                       void* stream, afqmc_batch_t* out);
+int afqmc_destroy_batch(afqmc_batch_t b);
+
+/* nsteps steps of every system, Philox fields (see above), E_mix measured at steps
+ * s % measure_every == 0 (0 = never) into E_mix_trace, complex [nmeas][nsys]
+ * (nmeas = ceil(nsteps / measure_every); NULL to skip).  Synchronises `stream` at the end
+ * to read the status words.  Errors: BADARG, NONFINITE, TIMEOUT, OOM, CUDA. */
+int afqmc_batch_step(afqmc_batch_t b, int nsteps, uint64_t seed, int measure_every, double* E_mix_trace,
+                     void* stream);
+
+/* afqmc_energy / afqmc_get_walkers of system `sys` (walkers in the caller's unpadded layout). */
+int afqmc_batch_energy(afqmc_batch_t b, int sys, double* E_L, double* w, double* logS, double* E_mix,
+                       void* stream);
+int afqmc_batch_get_walkers(afqmc_batch_t b, int sys, double* Phi, double* w, int64_t* step, void* stream);
+
+/* shape[6] = {M', N', Nchol' of system sys, graph branches, widest plain-GEMM tile,
+ * persistent grid cap (0 = one CTA per SM)}; kernels_per_step = kernels in the measuring
+ * step graph (-1 before the first step).  Either output may be NULL. */
+int afqmc_batch_info(afqmc_batch_t b, int sys, int* shape, int* kernels_per_step);
+
+/* Autotuner: times the measuring step graph (`reps` replays after one warm-up) for a
+ * coordinate search over the graph's branch count (1, 2, 4, ... up to 32), the widest
+ * plain-GEMM tile (256 or 128 columns) and the persistent grid size (all SMs, 1/2, 1/4),
+ * keeps the fastest and restores the walkers, weights and step counters it advanced.
+ * best_ms (may be NULL) = the chosen shape's time per step. */
+int afqmc_batch_autotune(afqmc_batch_t b, int reps, double* best_ms, void* stream);
 
 /* ---- Allocation-free log-overlap ---------------------------------------------
  * This entry point has no counterpart in the paper; it exists for callers that must not

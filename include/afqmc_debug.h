@@ -25,14 +25,15 @@ extern "C" {
 int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int rows, int cols, int K, int BN,
                            int exact, double* C);
 
-/* The fused energy contraction on its own (row-scaled operands, exact leading product):
+/* The fused energy contraction on its own (row-scaled operands, exact leading product;
+ * terms = 3: hi*hi + hi*lo + lo*hi, terms = 4: + lo*lo):
  * for Lt [Nchol][Np][M] (real) and walker-spin
  * Green's functions ThetaT [nws][2][Np][M] (re plane then im plane of Theta^T), returns
  * t [nws][Nchol] = Tr(Lt_n Theta_ws) and X [nws][Nchol] = Tr((Lt_n Theta_ws)^2) as complex
  * (interleaved float64).  Np in {32, 64, 128}, M % 64 == 0.  These traces give the force
  * bias and the Coulomb / exchange energies of the mixed estimator. */
-int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, double* t,
-                       double* X);
+int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, int terms,
+                       double* t, double* X);
 
 /* Intermediates of one measurement of a BF16X3 walker set (wk from afqmc_init_walkers with
  * AFQMC_PREC_BF16X3): runs the overlap / Green's function / energy contractions on the

@@ -34,7 +34,11 @@ EXPORTED = [
     "afqmc_init_walkers", "afqmc_destroy_walkers", "afqmc_step", "afqmc_energy",
     "afqmc_energy_backward", "afqmc_get_walkers", "afqmc_set_walkers",
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
+    "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
+    "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune",
 ]
+PAD_AUTO, PAD_ALWAYS = 0, 1
+SEED_STRIDE = 0x9E3779B97F4A7C15   # system s of a batch draws with key seed + s * SEED_STRIDE
 
 
 class AfqmcError(RuntimeError):
@@ -50,7 +54,25 @@ class Opts(ctypes.Structure):
         ("k_qr", ctypes.c_int),
         ("weight_mode", ctypes.c_int),
         ("fb_cap", ctypes.c_double),
-        ("reserved", ctypes.c_int * 8),
+        ("walker_offset", ctypes.c_int),
+        ("energy_terms", ctypes.c_int),
+        ("reserved", ctypes.c_int * 6),
+    ]
+
+
+class System(ctypes.Structure):
+    _fields_ = [
+        ("h", ctypes.c_void_p),
+        ("L", ctypes.c_void_p),
+        ("E0", ctypes.c_double),
+        ("M", ctypes.c_int),
+        ("Nchol", ctypes.c_int),
+        ("Psi_up", ctypes.c_void_p),
+        ("Psi_dn", ctypes.c_void_p),
+        ("Nup", ctypes.c_int),
+        ("Ndn", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("Phi0", ctypes.c_void_p),
     ]
 
 
@@ -82,6 +104,13 @@ def lib() -> ctypes.CDLL:
         "afqmc_last_step_stats": (i, [vp, ctypes.POINTER(d), ctypes.POINTER(i)]),
         "afqmc_last_error": (ctypes.c_char_p, []),
         "afqmc_log_overlap_noalloc": (i, [vp, vp, i, i, i, i, vp, vp, vp]),
+        "afqmc_create_batch": (i, [i, ctypes.POINTER(System), d, ctypes.POINTER(Opts), i, vp, ctypes.POINTER(vp)]),
+        "afqmc_destroy_batch": (i, [vp]),
+        "afqmc_batch_step": (i, [vp, i, u64, i, vp, vp]),
+        "afqmc_batch_energy": (i, [vp, i, vp, vp, vp, vp, vp]),
+        "afqmc_batch_get_walkers": (i, [vp, i, vp, vp, ctypes.POINTER(i64), vp]),
+        "afqmc_batch_info": (i, [vp, i, vp, ctypes.POINTER(i)]),
+        "afqmc_batch_autotune": (i, [vp, i, ctypes.POINTER(d), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -198,3 +227,44 @@ def afqmc_last_error() -> str:
 def afqmc_log_overlap_noalloc(Psi_up, Psi_dn, Nup: int, Ndn: int, M: int, W: int, Phi, logS, stream=None):
     _check(lib().afqmc_log_overlap_noalloc(_ptr(Psi_up), _ptr(Psi_dn), int(Nup), int(Ndn), int(M), int(W), _ptr(Phi),
                                            _ptr(logS), _stream(stream)))
+
+
+def afqmc_create_batch(systems, tau: float, opts: Optional[Opts] = None, pad_mode: int = PAD_AUTO,
+                       stream=None) -> int:
+    """systems: sequence of System structures (their arrays must stay alive for the call)."""
+    arr = (System * len(systems))(*systems)
+    out = ctypes.c_void_p()
+    _check(lib().afqmc_create_batch(len(systems), arr, float(tau), ctypes.byref(opts) if opts is not None else None,
+                                    int(pad_mode), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def afqmc_destroy_batch(b: int):
+    _check(lib().afqmc_destroy_batch(b))
+
+
+def afqmc_batch_step(b: int, nsteps: int, seed: int = 0, measure_every: int = 0, E_mix_trace=None, stream=None):
+    _check(lib().afqmc_batch_step(b, int(nsteps), int(seed), int(measure_every), _ptr(E_mix_trace), _stream(stream)))
+
+
+def afqmc_batch_energy(b: int, sys: int, E_L=None, w=None, logS=None, E_mix=None, stream=None):
+    _check(lib().afqmc_batch_energy(b, int(sys), _ptr(E_L), _ptr(w), _ptr(logS), _ptr(E_mix), _stream(stream)))
+
+
+def afqmc_batch_get_walkers(b: int, sys: int, Phi=None, w=None, stream=None) -> int:
+    step = ctypes.c_int64()
+    _check(lib().afqmc_batch_get_walkers(b, int(sys), _ptr(Phi), _ptr(w), ctypes.byref(step), _stream(stream)))
+    return step.value
+
+
+def afqmc_batch_info(b: int, sys: int):
+    shape = np.zeros(6, dtype=np.int32)
+    k = ctypes.c_int()
+    _check(lib().afqmc_batch_info(b, int(sys), _ptr(shape), ctypes.byref(k)))
+    return shape, k.value
+
+
+def afqmc_batch_autotune(b: int, reps: int = 2, stream=None) -> float:
+    ms = ctypes.c_double()
+    _check(lib().afqmc_batch_autotune(b, int(reps), ctypes.byref(ms), _stream(stream)))
+    return ms.value

@@ -47,6 +47,20 @@ void set_error(int code, const std::string& msg) {
     g_last_error = msg;
 }
 
+LaunchPolicy& launch_policy() {
+    static thread_local LaunchPolicy p;
+    return p;
+}
+
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
@@ -203,6 +217,9 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         return fail(AFQMC_ERR_BADARG, "init_walkers: invalid option value");
     for (int r : o.reserved)
         if (r != 0) return fail(AFQMC_ERR_BADARG, "init_walkers: reserved options must be zero");
+    if (o.walker_offset < 0) return fail(AFQMC_ERR_BADARG, "init_walkers: walker_offset must be >= 0");
+    if (o.energy_terms != 0 && o.energy_terms != 3 && o.energy_terms != 4)
+        return fail(AFQMC_ERR_BADARG, "init_walkers: energy_terms must be 0, 3 or 4");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     AFQMC_CUDA_TRY(cudaGetDevice(&dev));
@@ -420,7 +437,7 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
             AFQMC_TRY(copy_in(wk->x, x + (int64_t)s * per_step, sizeof(double) * per_step, st));
             xs = wk->x;
         } else {
-            philox_fields(seed, wk->step, wk->W, wk->Nchol, wk->x, st);
+            philox_fields(seed, wk->step, wk->W, wk->Nchol, wk->x, st, wk->opts.walker_offset);
             xs = wk->x;
         }
         AFQMC_TRY(tc ? tc_propagate_and_weight(wk, xs, st) : fp64_propagate_and_weight(wk, xs, st));

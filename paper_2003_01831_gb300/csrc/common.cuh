@@ -53,6 +53,18 @@ int fail(int code, const std::string& msg);  // sets and returns code
 void count_launch();
 long long launch_count();
 
+// Launch-shape knobs of the persistent tensor-core kernels, read when a kernel is launched
+// (or captured into a graph) on the calling thread.  Defaults: one CTA per SM, the widest
+// tile a call site allows.  The batch autotuner sets them around each candidate capture.
+struct LaunchPolicy {
+    int grid_cap = 0;    // > 0: at most this many CTAs per persistent launch
+    int bn_max = 256;    // 128: narrow every plain GEMM tile to 128 columns
+};
+LaunchPolicy& launch_policy();
+
+// true while `st` is being captured into a CUDA graph (timing events are then skipped)
+bool stream_capturing(cudaStream_t st);
+
 #define AFQMC_CUDA_TRY(expr)                                                                   \
     do {                                                                                        \
         cudaError_t _e = (expr);                                                                \

@@ -86,8 +86,8 @@ extern "C" int afqmc_debug_split_gemm(const double* A, const double* B, int nbat
     return AFQMC_OK;
 }
 
-extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, double* t,
-                                  double* X) {
+extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, int terms,
+                                  double* t, double* X) {
     if (!Lt || !ThetaT || !t || !X || Nchol < 1 || nws < 1 || M < 64)
         return fail(AFQMC_ERR_BADARG, "debug_energy: bad arguments");
     const int64_t na = (int64_t)Nchol * Np * M, nb = (int64_t)nws * 2 * Np * M;
@@ -104,7 +104,7 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M; sa.scale = static_cast<float*>(asc.p);
     sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
     sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M; sb.scale = static_cast<float*>(bsc.p);
-    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p),
+    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p), terms,
                         static_cast<unsigned*>(flags.p), 0));
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
     unsigned fl = 0;

@@ -358,12 +358,19 @@ __device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_
     c3 = lo0;
 }
 
-__global__ void philox_kernel(uint64_t seed, int64_t step, int W, int Nchol, double* x) {
+// params (optional, device): {seed, step} read at run time (graph replays), the key being
+// params[0] + seed; otherwise seed and step as given.
+__global__ void philox_kernel(uint64_t seed, int64_t step, const int64_t* params, int W, int w0, int Nchol,
+                              double* x) {
     const int nq = (Nchol + 3) / 4;
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= (int64_t)W * nq) return;
+    if (params) {
+        seed += (uint64_t)params[0];
+        step = params[1];
+    }
     const int w = (int)(id / nq), q = (int)(id % nq);
-    uint32_t c0 = (uint32_t)q, c1 = (uint32_t)w, c2 = (uint32_t)step, c3 = 0u;
+    uint32_t c0 = (uint32_t)q, c1 = (uint32_t)(w0 + w), c2 = (uint32_t)step, c3 = 0u;
     uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {
         if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
@@ -568,10 +575,17 @@ void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st) {
     local_energy_kernel<<<a.W, kThreads, 0, st>>>(a);
 }
 
-void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st) {
+void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st, int w0) {
     const int64_t n = (int64_t)W * ((Nchol + 3) / 4);
     count_launch();
-    philox_kernel<<<blocks_for(n), kThreads, 0, st>>>(seed, step, W, Nchol, x);
+    philox_kernel<<<blocks_for(n), kThreads, 0, st>>>(seed, step, nullptr, W, w0, Nchol, x);
+}
+
+void philox_fields_dev(const int64_t* params, uint64_t seed_add, int W, int Nchol, double* x, cudaStream_t st,
+                       int w0) {
+    const int64_t n = (int64_t)W * ((Nchol + 3) / 4);
+    count_launch();
+    philox_kernel<<<blocks_for(n), kThreads, 0, st>>>(seed_add, 0, params, W, w0, Nchol, x);
 }
 
 void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol, cplx* c,

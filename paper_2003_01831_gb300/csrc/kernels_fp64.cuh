@@ -60,7 +60,12 @@ struct LocalEnergyArgs {
 void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st);
 
 // Philox4x32-10 + Box-Muller fields x[w][n] for global step `step`.
-void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st);
+// x[w][n] for walkers w0 + w (w < W): counter (n/4, w0 + w, step, 0)
+void philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x, cudaStream_t st, int w0 = 0);
+// Same fields with key params[0] + seed_add and step params[1] read from device memory
+// when the kernel runs (so a captured graph draws fresh fields at every replay).
+void philox_fields_dev(const int64_t* params, uint64_t seed_add, int W, int Nchol, double* x, cudaStream_t st,
+                       int w0 = 0);
 
 // c[w][n] = x[w][n] - xbar[w][n] for walkers with w != 0, else 0; flags NaN/Inf fields.
 void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol,

@@ -380,22 +380,6 @@ __device__ __forceinline__ void load_acc32(uint32_t taddr1, uint32_t taddr2, flo
     for (int q = 0; q < 32; ++q) v[q] = EXACT ? __uint_as_float(a[q]) + __uint_as_float(b[q]) : __uint_as_float(a[q]);
 }
 
-// re and im blocks (32 columns each) of an exact accumulator pair: four loads, one wait.
-__device__ __forceinline__ void load_cplx_block(uint32_t t1, uint32_t t2, int cr, int ci, float (&vr)[32],
-                                                float (&vi)[32]) {
-    uint32_t a[32], b[32], c[32], d[32];
-    tmem_ld32_nw(t1 + cr, a);
-    tmem_ld32_nw(t2 + cr, b);
-    tmem_ld32_nw(t1 + ci, c);
-    tmem_ld32_nw(t2 + ci, d);
-    tmem_ld_wait();
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        vr[q] = __uint_as_float(a[q]) + __uint_as_float(b[q]);
-        vi[q] = __uint_as_float(c[q]) + __uint_as_float(d[q]);
-    }
-}
-
 template <int BN, bool EXACT, int NBUF>
 __device__ void setup_ctl(SharedCtl* ctl, int warp) {
     if (threadIdx.x == 0) {
@@ -516,6 +500,7 @@ struct EnergyShape {
     int ws_super;     // ws groups per L2 super-block
     int64_t tiles;
     int nk;
+    int lolo;               // 1: also form lo*lo (four products), 0: three
     const float* a_scale;   // [Nchol*Np]
     const float* b_scale;   // [nws*2*Np]
     cplx* t_out;
@@ -548,23 +533,95 @@ __device__ __forceinline__ int named_bar_and(int pred) {
     return r;
 }
 
-constexpr int kSlotFloats = 2 * 32 * 32;  // re, im planes of a 32 x 32 block (XOR-swizzled)
+// Energy kernel pipeline: 32-wide K chunks with 64-byte swizzle, two stages of 48 KB, one TMEM
+// buffer (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  The epilogue drains
+// both accumulators into a 128 x 256 fp32 tile in shared memory (XOR-swizzled within 32-column
+// groups so row and column reads are both conflict-free), releases TMEM at once, and computes
+// the traces from shared memory while the tensor cores run the next tile.
+constexpr int kEBK = 32;
+constexpr int kEStages = 2;
+constexpr int kEABytes = kBM * kEBK * 2;            // 8 KB per plane
+constexpr int kEBBytes = 256 * kEBK * 2;            // 16 KB per plane
+constexpr int kEStageBytes = 2 * kEABytes + 2 * kEBBytes;
+constexpr int kETileFloats = 128 * 256;
+
+__device__ __forceinline__ int swz(int row, int col) { return row * 256 + ((col & ~31) | ((col ^ row) & 31)); }
+
+__device__ void energy_producer(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
+                                const CUtensorMap* tBh, const CUtensorMap* tBl, const EnergyShape& es) {
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < es.tiles && ok; t += gridDim.x) {
+        int ng, wg;
+        energy_tile(es, t, ng, wg);
+        for (int kb = 0; kb < es.nk; ++kb, ++g) {
+            const int st = (int)(g % kEStages);
+            const uint32_t ph = (uint32_t)((g / kEStages) & 1);
+            if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
+            uint8_t* s = sbase + (size_t)st * kEStageBytes;
+            mbar_arrive_expect_tx(&ctl->full[st], kEStageBytes);
+            const int x = kb * kEBK;
+            tma_load_2d(s, tAh, &ctl->full[st], x, ng * 128);
+            tma_load_2d(s + kEABytes, tAl, &ctl->full[st], x, ng * 128);
+            tma_load_2d(s + 2 * kEABytes, tBh, &ctl->full[st], x, wg * 256);
+            tma_load_2d(s + 2 * kEABytes + kEBBytes, tBl, &ctl->full[st], x, wg * 256);
+        }
+    }
+    if (!ok) {
+        const int64_t first = g > kEStages ? g - kEStages : 0;
+        for (int64_t j = first; j < g; ++j) wait_drain(&ctl->full[j % kEStages], (uint32_t)((j / kEStages) & 1));
+    }
+}
+
+__device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es) {
+    constexpr uint32_t idesc = idesc_bf16(kBM, 256, true);   // fp16 planes, M=128, N=256
+    const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
+    int64_t g = 0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < es.tiles && ok; t += gridDim.x, ++it) {
+        if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < es.nk; ++kb, ++g) {
+            const int st = (int)(g % kEStages);
+            const uint32_t ph = (uint32_t)((g / kEStages) & 1);
+            if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(sbase + (size_t)st * kEStageBytes);
+            const uint32_t sal = sa + kEABytes, sb = sa + 2 * kEABytes, sbl = sb + kEBBytes;
+#pragma unroll
+            for (int kk = 0; kk < kEBK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                const uint64_t ah = desc_sw64(sa + off), al = desc_sw64(sal + off);
+                const uint64_t bh = desc_sw64(sb + off), bl = desc_sw64(sbl + off);
+                const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+                mma_bf16(d1, ah, bh, idesc, acc);
+                mma_bf16(d2, ah, bl, idesc, acc);
+                mma_bf16(d2, al, bh, idesc, 1u);
+                if (es.lolo) mma_bf16(d2, al, bl, idesc, 1u);
+            }
+            mma_commit(&ctl->empty[st]);
+        }
+        if (!ok) break;
+        mma_commit(&ctl->tfull[0]);
+    }
+    mma_commit(&ctl->done);
+    wait_drain(&ctl->done, 0);
+}
 
 template <int Np>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_energy_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                      const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                      EnergyShape es, unsigned* flags) {
-    constexpr int BN = 256;
     constexpr int Q = Np / 32;
     constexpr int G = 128 / Np;
-    constexpr int NBUF = 1;
-    using C = Cfg<BN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* xch = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
-    float* colscale = xch + 4 * kSlotFloats;                       // 256 column scales of the tile
-    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(colscale + 256);
+    float* tile = reinterpret_cast<float*>(sbase + kEStages * kEStageBytes);
+    float* colscale = tile + kETileFloats;                       // 256 column scales of the tile
+    double* ered = reinterpret_cast<double*>(colscale + 256);    // [4 warps][4 j][4]
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(ered + 64);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tAh);
@@ -572,134 +629,127 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tma_prefetch_desc(&tBh);
         tma_prefetch_desc(&tBl);
     }
-    setup_ctl<BN, true, NBUF>(ctl, warp);
+    // set-up: two stages, one TMEM buffer of 512 columns
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kEStages; ++i) {
+            mbar_init(&ctl->full[i], 1);
+            mbar_init(&ctl->empty[i], 1);
+        }
+        mbar_init(&ctl->tfull[0], 1);
+        mbar_init(&ctl->tempty[0], 128);
+        mbar_init(&ctl->done, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&ctl->tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0) {
-            auto coords = [&](int64_t t, int& ay, int& az, int& by, int& bz) {
-                int ng, wg;
-                energy_tile(es, t, ng, wg);
-                ay = ng * 128;
-                by = wg * 256;
-                az = bz = 0;
-            };
-            producer_loop<BN>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es.tiles, es.nk, coords, false);
-        }
+        if (lane == 0) energy_producer(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es);
     } else if (warp == 1) {
-        if (lane == 0) mma_loop<BN, true, NBUF>(sbase, ctl, es.tiles, es.nk);
+        if (lane == 0) energy_mma(sbase, ctl, es);
     } else {
-        const int g4 = warp & 3;               // row sub-block: rows 32*g4 .. +31
-        const int i_blk = g4 / Q;              // n within the group
-        const int mu = g4 % Q;                 // sub-block index inside the Np x Np block
-        const int et = threadIdx.x - 64;       // 0..127 over the epilogue warps
-        const uint32_t lane_base = (uint32_t)(g4 * 32) << 16;
-        float* my_slot = xch + g4 * kSlotFloats;
+        const int g4 = warp & 3;               // TMEM lane quadrant = rows 32*g4 .. +31
+        const int row = g4 * 32 + lane;        // tile row = (n-block i, a')
+        const int i_blk = row / Np, ap = row % Np;
+        const int mu = (row % Np) / 32;        // which 32-row slice of the n-block
+        const int et = threadIdx.x - 64;       // 0..127
+        const uint32_t t1 = ctl->tmem_base + ((uint32_t)(g4 * 32) << 16);
+        const uint32_t t2 = t1 + 256;
         int it = 0;
         for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
-            const uint32_t u = (uint32_t)it;
-            const bool got = warp_wait(&ctl->tfull[0], u & 1u, &ctl->abort);
-            if (!named_bar_and(got ? 1 : 0)) break;   // all four warps leave together
-            tc_fence_after();
             int ng, wg;
             energy_tile(es, t, ng, wg);
-            // stage the tile's column scales; my row's scale
             for (int c = et; c < 256; c += 128) {
-                const int64_t row = (int64_t)wg * 256 + c;
-                colscale[c] = row < (int64_t)es.nws * 2 * Np ? es.b_scale[row] : 0.0f;
+                const int64_t brow = (int64_t)wg * 256 + c;
+                colscale[c] = brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
             }
-            const int64_t arow = (int64_t)ng * 128 + g4 * 32 + lane;
+            const int64_t arow = (int64_t)ng * 128 + row;
             const float sa = arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
             named_bar_epi();
-            const uint32_t t1 = ctl->tmem_base + lane_base;
-            const uint32_t t2 = t1 + BN;
+            const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
+            if (!named_bar_and(got ? 1 : 0)) break;   // all four warps leave together
+            tc_fence_after();
+            // drain TMEM into the shared tile, scaled to true units
+#pragma unroll 1
+            for (int c = 0; c < 8; ++c) {
+                uint32_t a1[32], a2[32];
+                tmem_ld32_nw(t1 + c * 32, a1);
+                tmem_ld32_nw(t2 + c * 32, a2);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int col = c * 32 + q;
+                    tile[swz(row, col)] = (__uint_as_float(a1[q]) + __uint_as_float(a2[q])) * (sa * colscale[col]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&ctl->tempty[0]);              // tensor memory free: next tile's MMAs start
+            named_bar_epi();
+            // traces of every (n, ws) block this row belongs to
 #pragma unroll 1
             for (int j = 0; j < G; ++j) {
-                double tr = 0.0, ti = 0.0, xr = 0.0, xi = 0.0;
-#pragma unroll 1
-                for (int rho = 0; rho < Q; ++rho) {
-                    const int wsub = (mu - rho + Q) % Q;   // sub-block I publish
-                    const int beta = (mu + rho) % Q;       // partner sub-block I read
-                    // publish T[my rows][block wsub] (re, im), scaled to true units
-                    {
-                        float pr_[32], pi_[32];
-                        const int cr = j * 2 * Np + 32 * wsub, ci = cr + Np;
-                        load_cplx_block(t1, t2, cr, ci, pr_, pi_);
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) {
-                            my_slot[lane * 32 + (q ^ lane)] = pr_[q] * (sa * colscale[cr + q]);
-                            my_slot[32 * 32 + lane * 32 + (q ^ lane)] = pi_[q] * (sa * colscale[ci + q]);
-                        }
-                    }
-                    // my own block for the product: issue its TMEM loads before the barrier
-                    uint32_t a1[32], a2[32], b1[32], b2[32];
-                    const int ocr = j * 2 * Np + 32 * beta, oci = ocr + Np;
-                    tmem_ld32_nw(t1 + ocr, a1);
-                    tmem_ld32_nw(t2 + ocr, a2);
-                    tmem_ld32_nw(t1 + oci, b1);
-                    tmem_ld32_nw(t2 + oci, b2);
-                    named_bar_epi();
-                    if (rho == 0) {
-                        // diagonal T[a][a]: column `lane` of my own published block
-                        tr += my_slot[lane * 32];
-                        ti += my_slot[32 * 32 + lane * 32];
-                    }
-                    tmem_ld_wait();
-                    float vr[32], vi[32];
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        vr[q] = (__uint_as_float(a1[q]) + __uint_as_float(a2[q])) * (sa * colscale[ocr + q]);
-                        vi[q] = (__uint_as_float(b1[q]) + __uint_as_float(b2[q])) * (sa * colscale[oci + q]);
-                    }
-                    const float* ps = xch + (i_blk * Q + beta) * kSlotFloats;
-                    float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        // partner row q, column = my lane
-                        const float pr = ps[q * 32 + (lane ^ q)], pi = ps[32 * 32 + q * 32 + (lane ^ q)];
-                        ar[q & 3] = fmaf(vr[q], pr, fmaf(-vi[q], pi, ar[q & 3]));
-                        ai[q & 3] = fmaf(vr[q], pi, fmaf(vi[q], pr, ai[q & 3]));
-                    }
-                    xr += (double)((ar[0] + ar[1]) + (ar[2] + ar[3]));
-                    xi += (double)((ai[0] + ai[1]) + (ai[2] + ai[3]));
-                    named_bar_epi();
+                const int cre = j * 2 * Np, cim = cre + Np;
+                float xr[4] = {0.f, 0.f, 0.f, 0.f}, xi[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+                for (int b = 0; b < Np; ++b) {
+                    const float orr = tile[swz(row, cre + b)], oi = tile[swz(row, cim + b)];
+                    const int rb = i_blk * Np + b;
+                    const float pr = tile[swz(rb, cre + ap)], pi = tile[swz(rb, cim + ap)];
+                    xr[b & 3] = fmaf(orr, pr, fmaf(-oi, pi, xr[b & 3]));
+                    xi[b & 3] = fmaf(orr, pi, fmaf(oi, pr, xi[b & 3]));
                 }
-                // warp reduction, then across the Q warps of this n
+                double tr = tile[swz(row, cre + ap)], ti = tile[swz(row, cim + ap)];
+                double Xr = (double)((xr[0] + xr[1]) + (xr[2] + xr[3]));
+                double Xi = (double)((xi[0] + xi[1]) + (xi[2] + xi[3]));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     tr += __shfl_xor_sync(0xffffffffu, tr, o);
                     ti += __shfl_xor_sync(0xffffffffu, ti, o);
-                    xr += __shfl_xor_sync(0xffffffffu, xr, o);
-                    xi += __shfl_xor_sync(0xffffffffu, xi, o);
+                    Xr += __shfl_xor_sync(0xffffffffu, Xr, o);
+                    Xi += __shfl_xor_sync(0xffffffffu, Xi, o);
                 }
                 if (lane == 0) {
-                    ctl->red[g4][0] = tr;
-                    ctl->red[g4][1] = ti;
-                    ctl->red[g4][2] = xr;
-                    ctl->red[g4][3] = xi;
+                    double* e = ered + (g4 * 4 + j) * 4;
+                    e[0] = tr;
+                    e[1] = ti;
+                    e[2] = Xr;
+                    e[3] = Xi;
                 }
-                named_bar_epi();
-                if (mu == 0 && lane == 0) {
-                    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                    for (int q = 0; q < Q; ++q) {
-                        s0 += ctl->red[i_blk * Q + q][0];
-                        s1 += ctl->red[i_blk * Q + q][1];
-                        s2 += ctl->red[i_blk * Q + q][2];
-                        s3 += ctl->red[i_blk * Q + q][3];
-                    }
-                    const int n = ng * G + i_blk;
-                    const int ws = wg * G + j;
-                    if (n < es.Nchol && ws < es.nws) {
-                        es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
-                        es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
-                    }
-                }
-                named_bar_epi();
             }
-            tc_fence_before();
-            mbar_arrive(&ctl->tempty[0]);
+            named_bar_epi();
+            // one lane per (n-block, j) adds the Q warp partials of its n-block
+            if (mu == 0 && lane < G) {
+                const int j = lane;
+                double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                for (int q = 0; q < Q; ++q) {
+                    const double* e = ered + ((g4 + q) * 4 + j) * 4;
+                    s0 += e[0];
+                    s1 += e[1];
+                    s2 += e[2];
+                    s3 += e[3];
+                }
+                const int n = ng * G + i_blk;
+                const int ws = wg * G + j;
+                if (n < es.Nchol && ws < es.nws) {
+                    es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
+                    es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
+                }
+            }
         }
     }
-    teardown<BN, true, NBUF>(ctl, warp, flags);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(ctl->tmem_base, 512);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
 }
 
 // --------------------------------------------------------------------------- row split
@@ -750,17 +800,17 @@ EncodeTiledFn encode_fn() {
 
 // 2-D or 3-D map over [batch][rows][K] bf16 with box {64, box_rows, 1} and 128-byte swizzle.
 int make_map(CUtensorMap* m, const bf16* base, int64_t K, int64_t rows, int64_t batch, int64_t row_stride,
-             int64_t batch_stride, int box_rows, bool three_d, bool fp16 = false) {
+             int64_t batch_stride, int box_rows, bool three_d, bool fp16 = false, bool sw64 = false) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_stride * 2) % 16 || (batch_stride * 2) % 16)
         return fail(AFQMC_ERR_SHAPE, "tensor map: base/stride not 16-byte aligned");
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)std::max<int64_t>(batch, 1)};
     cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 2), (cuuint64_t)(std::max<int64_t>(batch_stride, row_stride) * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(sw64 ? kEBK : kBK), (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, three_d ? 3 : 2, const_cast<bf16*>(base), dims, strides,
-                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return AFQMC_OK;
@@ -772,7 +822,7 @@ size_t gemm_smem() {
 }
 
 size_t energy_smem() {
-    return 1024 + (size_t)Cfg<256>::kStages * Cfg<256>::kStageBytes + 4 * kSlotFloats * 4 + 256 * 4 + sizeof(SharedCtl);
+    return 1024 + (size_t)kEStages * kEStageBytes + (size_t)kETileFloats * 4 + 256 * 4 + 64 * 8 + sizeof(SharedCtl);
 }
 
 int g_num_sms = 0;
@@ -781,7 +831,8 @@ template <int BN, bool EXACT>
 int launch_gemm(const CUtensorMap* m, const TileShape& sh, const EpiParams& epi, unsigned* flags, cudaStream_t st) {
     const size_t sm = gemm_smem<BN>();
     cudaFuncSetAttribute(tc_gemm_kernel<BN, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const int grid = (int)std::min<int64_t>(sh.tiles, tc_num_sms());
+    const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
+    const int grid = (int)std::min<int64_t>(sh.tiles, cap);
     count_launch();
     tc_gemm_kernel<BN, EXACT><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], sh, epi, flags);
     cudaError_t e = cudaGetLastError();
@@ -793,7 +844,8 @@ template <int Np>
 int launch_energy(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
     const size_t sm = energy_smem();
     cudaFuncSetAttribute(tc_energy_kernel<Np>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const int grid = (int)std::min<int64_t>(es.tiles, tc_num_sms());
+    const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
+    const int grid = (int)std::min<int64_t>(es.tiles, cap);
     count_launch();
     tc_energy_kernel<Np><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
     cudaError_t e = cudaGetLastError();
@@ -817,6 +869,7 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
             int64_t K, int nbatch, const EpiParams& epi, int BN, bool exact, unsigned* flags, cudaStream_t st) {
     if (rows <= 0 || cols <= 0 || K <= 0 || nbatch <= 0) return AFQMC_OK;
     if (BN != 128 && BN != 256) return fail(AFQMC_ERR_BADARG, "tc_gemm: BN must be 128 or 256");
+    if (!exact && BN == 256 && launch_policy().bn_max < 256) BN = 128;   // epilogues are per 32 columns
     if (exact && (BN != 128 || !A.scale || !B.scale))
         return fail(AFQMC_ERR_BADARG, "tc_gemm: exact mode needs BN = 128 and row-scaled operands");
     const bool three_d = nbatch > 1 || amap.mod != (1 << 30);
@@ -846,15 +899,16 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
 }
 
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
-              cplx* X_out, unsigned* flags, cudaStream_t st) {
+              cplx* X_out, int terms, unsigned* flags, cudaStream_t st) {
+    if (terms != 3 && terms != 4) return fail(AFQMC_ERR_BADARG, "tc_energy: terms must be 3 or 4");
     if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
     if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
     CUtensorMap m[4];
-    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true));
-    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true));
-    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true));
-    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true));
+    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, true));
+    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, true));
+    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, true));
+    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, true));
     EnergyShape es;
     es.Np = Np;
     es.Q = Np / 32;
@@ -865,7 +919,8 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     es.ws_groups = (nws + es.G - 1) / es.G;
     es.ws_super = std::min(es.ws_groups, 128);
     es.tiles = (int64_t)es.n_groups * es.ws_groups;
-    es.nk = M / kBK;
+    es.nk = M / kEBK;
+    es.lolo = terms == 4 ? 1 : 0;
     es.a_scale = Lt.scale;
     es.b_scale = ThetaT.scale;
     es.t_out = t_out;

@@ -72,8 +72,9 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
 // all n and walker-spin pairs ws; emits t = Tr T and X = Tr(T T) per (ws, n) into
 // t_out/X_out [nws][Nchol] (complex FP64).  Lt: [Nchol*Np][M], ThetaT: [nws*2*Np][M]
 // (rows (ws, re/im, b)), both row-scaled; exact accumulation of the leading product.
+// terms = 3 (hi*hi exact, hi*lo + lo*hi) or 4 (+ lo*lo) split products.
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
-              cplx* X_out, unsigned* flags, cudaStream_t st);
+              cplx* X_out, int terms, unsigned* flags, cudaStream_t st);
 
 // Row-scaled (fp16) split of `rows` rows of length K (row r at src + r*src_stride) into
 // hi/lo [rows][K] (row stride K) and scale[rows].  FP64 or FP32 source.

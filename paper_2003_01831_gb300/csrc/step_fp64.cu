@@ -91,6 +91,7 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
     Fp64Buffers& f = wk->f;
     const int M = wk->M, nch = wk->Nchol;
     const int W = Wm > 0 ? Wm : wk->W;
+    const bool timed = !stream_capturing(st);
     for (int s = 0; s < 2; ++s) {
         const int N = wk->N[s];
         overlap(f.Psi[s], f.Phi[s], f.S[s], M, N, W, st);
@@ -103,7 +104,7 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
             g.C = f.Theta[s]; g.ldc = N; g.sc1 = (int64_t)M * N;
             zgemm(g, st);
         }
-        if (s == 0 && wk->ev0) cudaEventRecord(wk->ev0, st);
+        if (s == 0 && wk->ev0 && timed) cudaEventRecord(wk->ev0, st);
         if (measure) {
             for (int n0 = 0; n0 < nch; n0 += f.nc) {
                 const int nc = std::min(f.nc, nch - n0);
@@ -128,7 +129,7 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
             g.C = f.t[s]; g.ldc = nch;
             zgemm(g, st);
         }
-        if (s == 1 && wk->ev1) { cudaEventRecord(wk->ev1, st); wk->ev_valid = true; }
+        if (s == 1 && wk->ev1 && timed) { cudaEventRecord(wk->ev1, st); wk->ev_valid = true; }
     }
     add_logdet(f.ld[0], f.ld[1], wk->logS_old, W, st);
     LocalEnergyArgs a;

@@ -5,7 +5,9 @@
 //
 // Device layouts (W walkers, both spins, N electrons per spin, complex stored planar):
 //   PhiT   [W][2][2][N][M] FP64 master walkers, transposed (row (s, c, j) = column j of
-//          Phi_s, re/im plane c), plus its row-scaled fp16 pair and a plain bf16 pair
+//          Phi_s, re/im plane c), plus its row-scaled fp16 pair and a plain bf16 pair; a
+//          second buffer holds the proposals, copied over the current walkers on acceptance
+//          (the current walkers never change buffer, so captured step graphs replay)
 //   Phi    [W][2][M][2N]   row-scaled fp16 pair, untransposed with re | im columns
 //          (Green's-function GEMM operand)
 //   ThT    [W][2][2][N][M] Theta^T = (Phi S^-1)^T: fp32, and its row-scaled fp16 pair
@@ -72,6 +74,9 @@ struct TcState {
 namespace {
 
 constexpr int kT = 256;
+// Split products of the energy contraction when the options leave it open: hi*hi (exact),
+// hi*lo and lo*hi; the lo*lo term is below the rounding of the second accumulator's sum.
+constexpr int kDefaultEnergyTerms = 4;
 inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 
 template <typename T>
@@ -306,11 +311,12 @@ __global__ void __launch_bounds__(kT) le_mixed_kernel(const cplx* E1, const cplx
         if (!(isfinite(E.re) && isfinite(E.im))) atomicOr(flags, FLAG_NONFINITE);
     }
 }
-// rejected walkers keep their old state: copy cur -> nxt where accept == 0
-__global__ void keep_rejected_kernel(const int* accept, int W, int64_t per, const double* old64, double* new64) {
+// accepted walkers take their proposal: copy nxt -> cur where accept != 0 (the current
+// walkers stay in one buffer, so a captured step graph can be replayed)
+__global__ void commit_accepted_kernel(const int* accept, int W, int64_t per, const double* new64, double* cur64) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)W * per) return;
-    if (!accept[i / per]) new64[i] = old64[i];
+    if (accept[i / per]) cur64[i] = new64[i];
 }
 // Classical Gram-Schmidt (twice) on the N columns of one walker-spin, stored as planar
 // rows of PhiT: column j = (re row j, im row j), length M.  diag R > 0.
@@ -559,11 +565,13 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
                           128, true, wk->flags, st));
         split_rows(s->ThT_f, M, (int64_t)WS * 2 * N, M, s->ThT_h, s->ThT_l, s->ThT_s, st);
     }
-    if (wk->ev0) cudaEventRecord(wk->ev0, st);
+    const bool timed = !stream_capturing(st);
+    if (wk->ev0 && timed) cudaEventRecord(wk->ev0, st);
     if (measure) {
         AFQMC_TRY(tc_energy(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N, 1, s->Lt_s),
                             smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N, 1, s->ThT_s), N, nch, WS, M, s->tE,
-                            s->XE, wk->flags, st));
+                            s->XE, wk->opts.energy_terms > 0 ? wk->opts.energy_terms : kDefaultEnergyTerms,
+                            wk->flags, st));
     } else {
         const int64_t n = (int64_t)WS * 2 * N * M;
         count_launch();
@@ -580,7 +588,7 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
         count_launch();
         fb_combine_kernel<<<nb((int64_t)WS * nch), kT, 0, st>>>(s->tFB, WS, nch, s->tE);
     }
-    if (wk->ev1) {
+    if (wk->ev1 && timed) {
         cudaEventRecord(wk->ev1, st);
         wk->ev_valid = true;
     }
@@ -679,8 +687,7 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     weight_update(a, st);
     const int64_t per = 4LL * N * M;
     count_launch();
-    keep_rejected_kernel<<<nb((int64_t)W * per), kT, 0, st>>>(wk->accept, W, per, s->PhiT[s->cur], s->PhiT[nxt]);
-    s->cur = nxt;
+    commit_accepted_kernel<<<nb((int64_t)W * per), kT, 0, st>>>(wk->accept, W, per, s->PhiT[nxt], s->PhiT[s->cur]);
     refresh_operands(s, st);
     return AFQMC_OK;
 }

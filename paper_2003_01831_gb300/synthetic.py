@@ -40,6 +40,7 @@ __all__ = [
     "WORKLOADS",
     "workload",
     "uneven_batch",
+    "make_uneven_system",
 ]
 
 
@@ -152,3 +153,12 @@ def uneven_batch(n_systems: int = 64, seed: int = 1003) -> List[UnevenSystem]:
         W = int(rng.integers(32, 257))
         out.append(UnevenSystem(M=M, N=M // 4, Nchol=5 * M, W=W))
     return out
+
+
+def make_uneven_system(sysdims: UnevenSystem, index: int, seed: int = 1003, decay: float = 20.0,
+                       reading: str = "R1"):
+    """Hamiltonian and trial of system ``index`` of an uneven batch: the molecule-like
+    generators above with ``default_rng([seed, index])``.  Returns ``(h, L, E0, Psi)``."""
+    rng = np.random.default_rng([seed, index])
+    h, L, E0 = make_hamiltonian(sysdims.M, sysdims.Nchol, rng, decay=decay, reading=reading)
+    return h, L, E0, make_trial(h, sysdims.N, sysdims.N)

@@ -17,7 +17,8 @@ class AFQMC:
     """Owns an ``afqmc_ham_t`` and an ``afqmc_wk_t``; release with ``close()``."""
 
     def __init__(self, h, L, E0, Psi_up, Psi_dn, W, tau, Phi0=None, precision=api.PREC_FP64,
-                 k_taylor=6, k_qr=5, fb_cap=1.0, weight_mode=api.WEIGHT_PHASELESS, stream=None):
+                 k_taylor=6, k_qr=5, fb_cap=1.0, weight_mode=api.WEIGHT_PHASELESS, walker_offset=0, energy_terms=0,
+                 stream=None):
         h = np.ascontiguousarray(h, dtype=np.float64)
         L = np.ascontiguousarray(L, dtype=np.float64)
         self.M = h.shape[0]
@@ -35,6 +36,8 @@ class AFQMC:
         opts.k_qr = k_qr
         opts.fb_cap = fb_cap
         opts.weight_mode = weight_mode
+        opts.walker_offset = walker_offset
+        opts.energy_terms = energy_terms
         phi0 = None
         if Phi0 is not None:
             phi0 = np.ascontiguousarray(np.concatenate(
@@ -99,6 +102,83 @@ class AFQMC:
         if getattr(self, "ham", None):
             api.afqmc_destroy_hamiltonian(self.ham)
             self.ham = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns an ``afqmc_batch_t``: independent systems (h, L, E0, Psi_up, Psi_dn, W) stepped
+    together, one CUDA-graph launch per step; release with ``close()``."""
+
+    def __init__(self, systems, tau, precision=api.PREC_FP64, k_taylor=6, k_qr=5, fb_cap=1.0,
+                 weight_mode=api.WEIGHT_PHASELESS, pad_mode=api.PAD_AUTO, stream=None):
+        self.stream = stream
+        self.weight_mode = weight_mode
+        keep, structs = [], []
+        self.shapes = []
+        for (h, L, E0, Pu, Pd, W) in systems:
+            h = np.ascontiguousarray(h, dtype=np.float64)
+            L = np.ascontiguousarray(L, dtype=np.float64)
+            Pu = np.ascontiguousarray(Pu, dtype=np.complex128)
+            Pd = np.ascontiguousarray(Pd, dtype=np.complex128)
+            keep += [h, L, Pu, Pd]
+            M, nch = h.shape[0], L.shape[0]
+            self.shapes.append((M, Pu.shape[1], Pd.shape[1], nch, int(W)))
+            structs.append(api.System(h=h.ctypes.data, L=L.ctypes.data, E0=float(E0), M=M, Nchol=nch,
+                                      Psi_up=Pu.ctypes.data, Psi_dn=Pd.ctypes.data, Nup=Pu.shape[1],
+                                      Ndn=Pd.shape[1], W=int(W), Phi0=None))
+        opts = api.afqmc_default_opts()
+        opts.precision = precision
+        opts.k_taylor = k_taylor
+        opts.k_qr = k_qr
+        opts.fb_cap = fb_cap
+        opts.weight_mode = weight_mode
+        self.n = len(structs)
+        self.b = api.afqmc_create_batch(structs, tau, opts, pad_mode, stream)
+
+    def step(self, nsteps: int, seed: int = 0, measure_every: int = 0):
+        """Run nsteps; returns the complex E_mix trace [nmeas][nsys]."""
+        nmeas = (nsteps + measure_every - 1) // measure_every if measure_every > 0 else 0
+        trace = np.zeros((max(nmeas, 1), self.n), dtype=np.complex128)
+        api.afqmc_batch_step(self.b, nsteps, seed, measure_every, trace if nmeas else None, self.stream)
+        return trace[:nmeas]
+
+    def energy(self, s: int):
+        W = self.shapes[s][4]
+        E_L = np.zeros(W, dtype=np.complex128)
+        logS = np.zeros(W, dtype=np.complex128)
+        w = np.zeros(W, dtype=np.complex128 if self.weight_mode == api.WEIGHT_FREE else np.float64)
+        E = np.zeros(1, dtype=np.complex128)
+        api.afqmc_batch_energy(self.b, s, E_L, w, logS, E, self.stream)
+        return E_L, w, logS, E[0]
+
+    def walkers(self, s: int):
+        M, Nu, Nd, _, W = self.shapes[s]
+        Phi = np.zeros((W, M * (Nu + Nd)), dtype=np.complex128)
+        w = np.zeros(W, dtype=np.complex128 if self.weight_mode == api.WEIGHT_FREE else np.float64)
+        step = api.afqmc_batch_get_walkers(self.b, s, Phi, w, self.stream)
+        return Phi[:, :M * Nu].reshape(W, M, Nu), Phi[:, M * Nu:].reshape(W, M, Nd), w, step
+
+    def info(self, s: int = 0):
+        return api.afqmc_batch_info(self.b, s)
+
+    def autotune(self, reps: int = 2) -> float:
+        return api.afqmc_batch_autotune(self.b, reps, self.stream)
+
+    def close(self):
+        if getattr(self, "b", None):
+            api.afqmc_destroy_batch(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_opts(lib):
     o = api.afqmc_default_opts()
     assert (o.precision, o.k_taylor, o.k_qr, o.weight_mode, o.fb_cap) == (0, 6, 5, 0, 1.0)
-    assert list(o.reserved) == [0] * 8
+    assert o.walker_offset == 0 and o.energy_terms == 0 and list(o.reserved) == [0] * 6
 
 
 def test_opts_struct_layout_matches_header():
@@ -69,3 +69,40 @@ def test_python_binding_raises(lib):
     with pytest.raises(api.AfqmcError) as e:
         api.afqmc_create_hamiltonian(np.zeros((2, 2)), np.zeros((1, 2, 2)), 0.0, 0, 1)
     assert e.value.code == -2
+
+
+def test_system_struct_layout_matches_header():
+    # void* h, void* L, double E0, int M, int Nchol, void* Psi_up, void* Psi_dn, int Nup, int Ndn,
+    # int W, (pad), void* Phi0
+    assert ctypes.sizeof(api.System) == 8 + 8 + 8 + 4 + 4 + 8 + 8 + 4 + 4 + 4 + 4 + 8
+    assert api.System.Phi0.offset == 64
+
+
+def test_batch_bad_arguments_without_a_gpu(lib):
+    out = ctypes.c_void_p()
+    h = np.zeros((4, 4))
+    L = np.zeros((2, 4, 4))
+    P = np.zeros((4, 1), dtype=np.complex128)
+    ok = api.System(h=h.ctypes.data, L=L.ctypes.data, E0=0.0, M=4, Nchol=2, Psi_up=P.ctypes.data,
+                    Psi_dn=P.ctypes.data, Nup=1, Ndn=1, W=2, Phi0=None)
+    arr = (api.System * 1)(ok)
+    assert lib.afqmc_create_batch(1, arr, 0.01, None, 0, None, None) == -1          # out NULL
+    assert lib.afqmc_create_batch(0, arr, 0.01, None, 0, None, ctypes.byref(out)) == -1
+    assert lib.afqmc_create_batch(1, arr, -1.0, None, 0, None, ctypes.byref(out)) == -1
+    assert lib.afqmc_create_batch(1, arr, 0.01, None, 7, None, ctypes.byref(out)) == -1   # pad mode
+    bad = (api.System * 1)(api.System(h=h.ctypes.data, L=L.ctypes.data, E0=0.0, M=4, Nchol=2,
+                                      Psi_up=P.ctypes.data, Psi_dn=P.ctypes.data, Nup=5, Ndn=1, W=2, Phi0=None))
+    assert lib.afqmc_create_batch(1, bad, 0.01, None, 0, None, ctypes.byref(out)) == -2
+    assert b"system 0" in lib.afqmc_last_error()
+    o = api.afqmc_default_opts()
+    o.precision = api.PREC_BF16X3
+    uneven = (api.System * 1)(api.System(h=h.ctypes.data, L=L.ctypes.data, E0=0.0, M=4, Nchol=2,
+                                         Psi_up=P.ctypes.data, Psi_dn=P.ctypes.data, Nup=1, Ndn=2, W=2,
+                                         Phi0=None))
+    assert lib.afqmc_create_batch(1, uneven, 0.01, ctypes.byref(o), 0, None, ctypes.byref(out)) == -8
+    assert lib.afqmc_batch_step(None, 1, 0, 0, None, None) == -1
+    assert lib.afqmc_batch_energy(None, 0, None, None, None, None, None) == -1
+    assert lib.afqmc_batch_get_walkers(None, 0, None, None, None, None) == -1
+    assert lib.afqmc_batch_info(None, 0, None, None) == -1
+    assert lib.afqmc_batch_autotune(None, 1, None, None) == -1
+    assert lib.afqmc_destroy_batch(None) == -1

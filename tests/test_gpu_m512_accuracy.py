@@ -1,0 +1,34 @@
+"""Throughput workload accuracy: BF16X3 vs FP64 GPU paths at M=512, N=128+128, Nchol=2560.
+
+Same walkers, same fields; the mixed-estimator energy of every measured step must agree to
+1 mHa (the bar for the tensor-core path).  Sampled at 16 walkers x 4 steps to keep the FP64
+path's run short (its energy contraction costs ~1.7e11 flops per walker-step)."""
+import numpy as np
+import pytest
+
+from paper_2003_01831_gb300 import api, synthetic as syn
+from paper_2003_01831_gb300.walkers import AFQMC
+
+pytestmark = pytest.mark.gpu
+
+MHA = 1e-3
+
+
+def test_m512_mixed_matches_fp64_within_1mha():
+    wl = syn.WORKLOADS["m512"]
+    rng = wl.rng()
+    h, L, E0 = syn.make_hamiltonian(wl.M, wl.Nchol, rng, decay=wl.decay, band=wl.band)
+    Psi = syn.make_trial(h, wl.Nup, wl.Ndn)
+    W, steps = 16, 4
+    x = syn.make_fields(steps, W, wl.Nchol, seed=0)
+    traces = {}
+    for name, prec, terms in (("fp64", api.PREC_FP64, 0), ("bf16x3", api.PREC_BF16X3, 4),
+                              ("bf16x3_3", api.PREC_BF16X3, 3)):
+        with AFQMC(h, L, E0, Psi[0], Psi[1], W, wl.tau, k_qr=wl.k_qr, precision=prec, energy_terms=terms) as g:
+            traces[name] = g.step(steps, x, measure_every=1)
+            traces[name + "_E"] = g.energy()[0]
+    for name in ("bf16x3", "bf16x3_3"):
+        d = np.abs(traces["fp64"] - traces[name])
+        print(name, "E_mix fp64", traces["fp64"].real, "max |dE_mix| (Ha)", d.max(),
+              "max per-walker |dE_L| (Ha)", np.max(np.abs(traces["fp64_E"] - traces[name + "_E"])))
+        assert np.max(d) < MHA

@@ -42,14 +42,17 @@ def split_rows(x):
     return hi * sc, lo * sc
 
 
-def emul(A, B, exact=False):
-    """What the tensor cores form: hi*hi + hi*lo + lo*hi (plain) or + lo*lo (exact mode)."""
+def emul(A, B, exact=False, lolo=None):
+    """What the tensor cores form: hi*hi + hi*lo + lo*hi (plain) or + lo*lo (exact mode;
+    lolo=False drops that fourth product)."""
     sp = split_rows if exact else split
     Ah, Al = sp(A)
     Bh, Bl = sp(B)
     mm = lambda a, b: np.matmul(a, np.swapaxes(b, -1, -2))
     C = mm(Ah, Bh) + mm(Ah, Bl) + mm(Al, Bh)
-    return C + mm(Al, Bl) if exact else C
+    if lolo is None:
+        lolo = exact
+    return C + mm(Al, Bl) if lolo else C
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +66,8 @@ def dbg():
     L.afqmc_debug_split_gemm.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, vp]
     L.afqmc_debug_energy.restype = ctypes.c_int
-    L.afqmc_debug_energy.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.afqmc_debug_energy.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     vp, vp]
     return L
 
 
@@ -130,17 +134,20 @@ def test_exact_mode_integer_products_are_exact(dbg):
     assert np.array_equal(C, np.matmul(A, np.swapaxes(B, -1, -2)))
 
 
+@pytest.mark.parametrize("terms", [3, 4])
 @pytest.mark.parametrize("Np,Nchol,nws,M", [(128, 3, 2, 128), (64, 5, 3, 192), (32, 9, 5, 128), (128, 2, 3, 512)])
-def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M):
+def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M, terms):
     rng = np.random.default_rng(Np * 7 + Nchol)
     Lt = rng.standard_normal((Nchol, Np, M)) * 0.1
     Th = rng.standard_normal((nws, 2, Np, M)) * 0.1
     t = np.zeros((nws, Nchol), dtype=np.complex128)
     X = np.zeros((nws, Nchol), dtype=np.complex128)
-    rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, t.ctypes.data, X.ctypes.data)
+    rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, terms, t.ctypes.data,
+                                X.ctypes.data)
     assert rc == 0, api.afqmc_last_error()
-    Tr = np.stack([emul(Lt, np.broadcast_to(Th[w, 0], (Nchol, Np, M)), exact=True) for w in range(nws)])
-    Ti = np.stack([emul(Lt, np.broadcast_to(Th[w, 1], (Nchol, Np, M)), exact=True) for w in range(nws)])
+    lolo = terms == 4
+    Tr = np.stack([emul(Lt, np.broadcast_to(Th[w, 0], (Nchol, Np, M)), exact=True, lolo=lolo) for w in range(nws)])
+    Ti = np.stack([emul(Lt, np.broadcast_to(Th[w, 1], (Nchol, Np, M)), exact=True, lolo=lolo) for w in range(nws)])
     T = Tr + 1j * Ti                                     # [nws, Nchol, Np, Np]: T[a][b] = Lt[a] . Th^T[b]
     t_ref = np.trace(T, axis1=2, axis2=3)
     X_ref = np.einsum("wnab,wnba->wn", T, T)
