@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kThreads) zgemm_kernel(GemmArgs g) {
 }
 
 // ------------------------------------------------------------------ Gauss-Jordan
+constexpr int kGJU = 8;   // element updates in flight per thread
 __global__ void __launch_bounds__(kThreads)
     gj_kernel(cplx* Sbase, int64_t stride, int N, cplx* logdet, int with_inverse, unsigned* flags) {
     extern __shared__ unsigned char smem_raw[];
@@ -238,22 +239,46 @@ __global__ void __launch_bounds__(kThreads)
             pcol[j] = A[(int64_t)j * N + k];
         }
         __syncthreads();
+        // Element updates, kGJU per thread in flight: all loads are issued before any
+        // arithmetic, so a thread waits on the memory system once per batch, not per element.
         if (with_inverse) {
-            for (int64_t e = t; e < (int64_t)N * N; e += kThreads) {
-                const int i = (int)(e / N), j = (int)(e % N);
-                cplx v;
-                if (i == k) v = (j == k) ? inv : prow[j];
-                else if (j == k) v = cplx{0.0, 0.0} - pcol[i] * inv;
-                else { v = A[e]; cfma(v, cplx{0.0, 0.0} - pcol[i], prow[j]); }
-                A[e] = v;
+            const int64_t NN = (int64_t)N * N;
+            for (int64_t e0 = t; e0 < NN; e0 += (int64_t)kThreads * kGJU) {
+                cplx v[kGJU];
+#pragma unroll
+                for (int u = 0; u < kGJU; ++u) {
+                    const int64_t e = e0 + (int64_t)u * kThreads;
+                    if (e < NN) v[u] = A[e];
+                }
+#pragma unroll
+                for (int u = 0; u < kGJU; ++u) {
+                    const int64_t e = e0 + (int64_t)u * kThreads;
+                    if (e >= NN) continue;
+                    const int i = (int)(e / N), j = (int)(e % N);
+                    if (i == k) v[u] = (j == k) ? inv : prow[j];
+                    else if (j == k) v[u] = cplx{0.0, 0.0} - pcol[i] * inv;
+                    else cfma(v[u], cplx{0.0, 0.0} - pcol[i], prow[j]);
+                    A[e] = v[u];
+                }
             }
         } else {
             const int nr = N - k - 1;
-            for (int64_t e = t; e < (int64_t)nr * nr; e += kThreads) {
-                const int i = k + 1 + (int)(e / nr), j = k + 1 + (int)(e % nr);
-                cplx v = A[(int64_t)i * N + j];
-                cfma(v, cplx{0.0, 0.0} - pcol[i], prow[j]);
-                A[(int64_t)i * N + j] = v;
+            const int64_t nn = (int64_t)nr * nr;
+            for (int64_t e0 = t; e0 < nn; e0 += (int64_t)kThreads * kGJU) {
+                cplx v[kGJU];
+#pragma unroll
+                for (int u = 0; u < kGJU; ++u) {
+                    const int64_t e = e0 + (int64_t)u * kThreads;
+                    if (e < nn) v[u] = A[(int64_t)(k + 1 + e / nr) * N + k + 1 + e % nr];
+                }
+#pragma unroll
+                for (int u = 0; u < kGJU; ++u) {
+                    const int64_t e = e0 + (int64_t)u * kThreads;
+                    if (e >= nn) continue;
+                    const int i = k + 1 + (int)(e / nr), j = k + 1 + (int)(e % nr);
+                    cfma(v[u], cplx{0.0, 0.0} - pcol[i], prow[j]);
+                    A[(int64_t)i * N + j] = v[u];
+                }
             }
         }
         __syncthreads();

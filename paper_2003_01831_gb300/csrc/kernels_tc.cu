@@ -255,6 +255,51 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
             }
             break;
         }
+        case EPI_HSPOT_F32: {
+            // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
+            const int64_t w = r >> 1, c = r & 1;
+            const int64_t i0 = c0 / e.M, k0 = c0 % e.M;
+            if (full && k0 + 32 <= e.M) {
+                float* o = e.out_f32 + (w * e.M + i0) * (2 * e.M) + c * e.M + k0;
+                if (aligned16(o)) {
+#pragma unroll
+                    for (int g = 0; g < 8; ++g)
+                        reinterpret_cast<float4*>(o)[g] =
+                            make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+                } else {
+                    for (int j = 0; j < 32; ++j) o[j] = v[j];
+                }
+            } else {
+                for (int j = 0; j < ncol; ++j) {
+                    const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
+                    e.out_f32[(w * e.M + i) * (2 * e.M) + c * e.M + k] = v[j];
+                }
+            }
+            break;
+        }
+        case EPI_TAYLOR_F32: {
+            // batch b = walker; row r = (s*2 + c)*N + j of the doubled operand; C = (P A^T)_c[j][i].
+            // New term i*scale*C: C_re (c = 0) -> imaginary row, C_im (c = 1) -> real row, negated.
+            const int64_t N = e.N, M = e.M;
+            const int64_t s = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
+            const int64_t ws = (int64_t)b * 2 + s;
+            const int64_t row = (ws * 2 + (c == 0 ? 1 : 0)) * N + jj;
+            const float sg = c == 0 ? e.scale : -e.scale;
+            float* o = e.out_f32 + row * M + c0;
+            if (full && aligned16(o)) {
+#pragma unroll
+                for (int g = 0; g < 8; ++g)
+                    reinterpret_cast<float4*>(o)[g] =
+                        make_float4(sg * v[4 * g], sg * v[4 * g + 1], sg * v[4 * g + 2], sg * v[4 * g + 3]);
+                acc32(e.acc, row * M + c0, v, sg, true);
+            } else {
+                for (int j = 0; j < ncol; ++j) {
+                    o[j] = sg * v[j];
+                    e.acc[row * M + c0 + j] += sg * v[j];
+                }
+            }
+            break;
+        }
         default:
             break;
     }

@@ -48,6 +48,8 @@ enum EpiKind : int {
     EPI_BFIRST = 3,    // B Phi: doubled operand for the Taylor series + accumulator init
     EPI_TAYLOR = 4,    // (i s) P A^T: doubled operand of the next term + accumulator update
     EPI_F64 = 5,       // out_f64[b*ob + r*ld + c]
+    EPI_HSPOT_F32 = 6, // A potential in fp32: row (w, c), col (i, k) -> out_f32[w][i][c*M + k]
+    EPI_TAYLOR_F32 = 7,// next Taylor term i*scale*C in fp32 (planar rows) + accumulator update
 };
 
 struct EpiParams {

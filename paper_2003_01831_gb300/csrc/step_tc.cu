@@ -14,13 +14,16 @@
 //          (energy GEMM operand)
 //   Lt     [Nchol][N][M]   Ltilde_n = Psi^T L_n (trial real, same for both spins): row-scaled
 //          pair for the energy, plain pair for the force-bias-only contraction
-//   LT     [M*M][Nchol]    L transposed, plain pair (HS potential GEMM operand)
-//   A      [W][M][2M]      HS potential sum_n c_n L_n, re | im columns, plain pair
-//   PD     [W][2][2N][2M]  Taylor term in doubled form [[Re, -Im], [Im, Re]] (ping-pong)
-//   Pacc   [W][2][2][N][M] fp32 Taylor accumulator
-// The overlap, Green's function and energy contractions use row-scaled fp16 operands and the
-// exact-accumulation GEMM mode (kernels_tc.cu); the propagation uses plain pairs, whose
-// small accumulation bias only rescales walkers (a gauge factor common to all of them).
+//   LT     [M*M][Nchol]    L transposed, row-scaled pair (HS potential GEMM operand)
+//   A      [W][M][2M]      HS potential sum_n c_n L_n, re | im columns: fp32, then its
+//                          row-scaled pair (Taylor GEMM operand)
+//   Pk     [W][2][2][N][M] fp32 Taylor term; PD [W][2][2N][2M] its doubled form
+//                          [[Re, -Im], [Im, Re]] as a row-scaled pair
+//   Pacc   [W][2][2][N][M] fp32 Taylor accumulator (row-scaled pair for the final B product)
+// Every contraction of the step uses row-scaled fp16 operands and the exact-accumulation GEMM
+// mode (kernels_tc.cu): hi*hi summed exactly, the remainder products in a second accumulator.
+// (Plain bf16 pairs, whose fp32 accumulation the tensor cores truncate, perturb each walker by
+// ~1e-5 per step -- tens of mHa in E_mix after a few steps at M = 512.)
 #include <algorithm>
 #include <utility>
 #include <vector>
@@ -38,7 +41,9 @@ struct TcState {
     float* Lt_s = nullptr;
     bf16 *Ltp_h = nullptr, *Ltp_l = nullptr;
     bf16 *LT_h = nullptr, *LT_l = nullptr;
+    float* LT_s = nullptr;
     bf16 *Bh_h = nullptr, *Bh_l = nullptr;
+    float* Bh_s = nullptr;
     bf16 *PsiT_h = nullptr, *PsiT_l = nullptr;
     float* PsiT_s = nullptr;
     double* PsiT_f = nullptr;
@@ -48,7 +53,6 @@ struct TcState {
     float* PhiT_s[2] = {nullptr, nullptr};
     bf16 *Phi_h = nullptr, *Phi_l = nullptr;
     float* Phi_s = nullptr;
-    bf16 *PhiTp_h = nullptr, *PhiTp_l = nullptr;   // plain bf16 pair of the current walkers
     // Green's function and energy
     float* ST = nullptr;
     cplx* S = nullptr;
@@ -62,11 +66,18 @@ struct TcState {
     float* tFB = nullptr;
     cplx* E1 = nullptr;
     // propagation
+    double* cfp = nullptr;                 // [W][2][Nchol] HS coefficients, planar
     bf16 *cf_h = nullptr, *cf_l = nullptr;
+    float* cf_s = nullptr;
+    float* A_f = nullptr;
     bf16 *A_h = nullptr, *A_l = nullptr;
-    bf16 *PD_h[2] = {nullptr, nullptr}, *PD_l[2] = {nullptr, nullptr};
+    float* A_s = nullptr;
+    float* Pk = nullptr;
+    bf16 *PD_h = nullptr, *PD_l = nullptr;
+    float* PD_s = nullptr;
     float* Pacc = nullptr;
-    bf16 *Pacc_h = nullptr, *Pacc_l = nullptr;
+    bf16 *Pacc_h = nullptr, *Pacc_l = nullptr;   // row-scaled pair (also plain scratch, see tc_measure)
+    float* Pacc_s = nullptr;
     int cur = 0;
     std::vector<void*> owned;
 };
@@ -105,8 +116,8 @@ __global__ void psiT_kernel(const cplx* Psi, int M, int N, double* out) {
     const int a = (int)(i / M), k = (int)(i % M);
     out[i] = Psi[(int64_t)k * N + a].re;
 }
-// L [Nchol][MM] -> LT [MM][Nchol] plain pair, 32 x 32 tiles through shared memory
-__global__ void LT_kernel(const double* L, int64_t MM, int nch, bf16* hi, bf16* lo) {
+// L [Nchol][MM] -> LT [MM][Nchol] FP64, 32 x 32 tiles through shared memory
+__global__ void LT_kernel(const double* L, int64_t MM, int nch, double* LT) {
     __shared__ double tile[32][33];
     const int64_t c0 = (int64_t)blockIdx.x * 32;  // along MM
     const int n0 = blockIdx.y * 32;               // along Nchol
@@ -119,7 +130,7 @@ __global__ void LT_kernel(const double* L, int64_t MM, int nch, bf16* hi, bf16* 
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t c = c0 + r;
         const int n = n0 + threadIdx.x;
-        if (c < MM && n < nch) tc::split_bf16(tile[threadIdx.x][r], hi[c * nch + n], lo[c * nch + n]);
+        if (c < MM && n < nch) LT[c * nch + n] = tile[threadIdx.x][r];
     }
 }
 // canonical Phi_s [W][M][N] complex  <->  PhiT [W][2][2][N][M]
@@ -236,12 +247,50 @@ __global__ void __launch_bounds__(kT) sinv_doubled_kernel(const cplx* Si, int WS
         hi[row1 * K2 + N + j] = Hr;  lo[row1 * K2 + N + j] = Lr;    // Re
     }
 }
-__global__ void coef_split_kernel(const cplx* c, int64_t W, int nch, bf16* hi, bf16* lo) {
+// HS coefficients c [W][Nchol] complex -> planar rows [W][2][Nchol]
+__global__ void coef_planar_kernel(const cplx* c, int64_t W, int nch, double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * nch) return;
     const int64_t w = i / nch, n = i % nch;
-    tc::split_bf16(c[i].re, hi[(w * 2) * nch + n], lo[(w * 2) * nch + n]);
-    tc::split_bf16(c[i].im, hi[(w * 2 + 1) * nch + n], lo[(w * 2 + 1) * nch + n]);
+    out[(w * 2) * nch + n] = c[i].re;
+    out[(w * 2 + 1) * nch + n] = c[i].im;
+}
+// Taylor term P (fp32 rows (ws, c, j) of length M, c = re / im) -> doubled operand as a
+// row-scaled fp16 pair: row (ws, 0, j) = [Re P_j | -Im P_j], row (ws, 1, j) = [Im P_j | Re P_j]
+// (length 2M), both rows with the scale of the complex 2-norm of P_j.
+__global__ void __launch_bounds__(kT) split_doubled_kernel(const float* P, int64_t WS, int N, int M, __half* hi,
+                                                             __half* lo, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // (ws, j)
+    const int lane = threadIdx.x & 31;
+    if (r >= WS * N) return;
+    const int64_t ws = r / N;
+    const int j = (int)(r % N);
+    const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;
+    const float* pr = P + row0 * M;
+    const float* pi = P + row1 * M;
+    double ss = 0.0;
+    for (int k = lane; k < M; k += 32) {
+        const double a = pr[k], b = pi[k];
+        ss += a * a + b * b;
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double nrm = sqrt(ss);
+    int e = 0;
+    if (nrm > 0.0) frexp(nrm, &e);
+    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+    const float sc = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
+    const int64_t K2 = 2LL * M;
+    for (int k = lane; k < M; k += 32) {
+        const double yr = pr[k] * inv, yi = pi[k] * inv;
+        const double hr = rint(yr), hI = rint(yi);
+        const __half Hr = __double2half(hr), Lr = __double2half(yr - hr);
+        const __half Hi = __double2half(hI), Li = __double2half(yi - hI);
+        hi[row0 * K2 + k] = Hr;                       lo[row0 * K2 + k] = Lr;                       // Re
+        hi[row0 * K2 + M + k] = __double2half(-hI);   lo[row0 * K2 + M + k] = __double2half(hI - yi); // -Im
+        hi[row1 * K2 + k] = Hi;                       lo[row1 * K2 + k] = Li;                       // Im
+        hi[row1 * K2 + M + k] = Hr;                   lo[row1 * K2 + M + k] = Lr;                   // Re
+    }
 }
 __global__ void fb_combine_kernel(const float* tFB, int64_t WS, int nch, cplx* t) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -413,9 +462,6 @@ void untranspose_walkers(TcState* s, cudaStream_t st) {
 void refresh_operands(TcState* s, cudaStream_t st) {
     split_walkers(s, s->cur, st);
     untranspose_walkers(s, st);
-    const int64_t n = (int64_t)s->W * 4 * s->N * s->M;
-    count_launch();
-    split_f64_kernel<<<nb(n), kT, 0, st>>>(s->PhiT[s->cur], s->PhiTp_h, s->PhiTp_l, n);
 }
 
 // S = Psi^T Phi for the walkers in buffer b -> s->S; logdet into s->ld; optional inverse
@@ -456,8 +502,10 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->Ltp_l, nch * NM));
     AFQMC_TRY(talloc(s, &s->LT_h, MM * nch));
     AFQMC_TRY(talloc(s, &s->LT_l, MM * nch));
+    AFQMC_TRY(talloc(s, &s->LT_s, MM));
     AFQMC_TRY(talloc(s, &s->Bh_h, MM));
     AFQMC_TRY(talloc(s, &s->Bh_l, MM));
+    AFQMC_TRY(talloc(s, &s->Bh_s, M));
     AFQMC_TRY(talloc(s, &s->PsiT_h, NM));
     AFQMC_TRY(talloc(s, &s->PsiT_l, NM));
     AFQMC_TRY(talloc(s, &s->PsiT_s, N));
@@ -468,14 +516,14 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
         AFQMC_TRY(talloc(s, &s->PhiT_h[b], wall));
         AFQMC_TRY(talloc(s, &s->PhiT_l[b], wall));
         AFQMC_TRY(talloc(s, &s->PhiT_s[b], (int64_t)W * 4 * N));
-        AFQMC_TRY(talloc(s, &s->PD_h[b], (int64_t)W * 2 * 2 * N * 2 * M));
-        AFQMC_TRY(talloc(s, &s->PD_l[b], (int64_t)W * 2 * 2 * N * 2 * M));
     }
+    AFQMC_TRY(talloc(s, &s->PD_h, (int64_t)W * 2 * 2 * N * 2 * M));
+    AFQMC_TRY(talloc(s, &s->PD_l, (int64_t)W * 2 * 2 * N * 2 * M));
+    AFQMC_TRY(talloc(s, &s->PD_s, (int64_t)W * 4 * N));
+    AFQMC_TRY(talloc(s, &s->Pk, wall));
     AFQMC_TRY(talloc(s, &s->Phi_h, wall));
     AFQMC_TRY(talloc(s, &s->Phi_l, wall));
     AFQMC_TRY(talloc(s, &s->Phi_s, (int64_t)W * 2 * M));
-    AFQMC_TRY(talloc(s, &s->PhiTp_h, wall));
-    AFQMC_TRY(talloc(s, &s->PhiTp_l, wall));
     AFQMC_TRY(talloc(s, &s->ST, (int64_t)W * 2 * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->S, (int64_t)W * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->ld, (int64_t)W * 2));
@@ -489,24 +537,38 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->tE, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->XE, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->tFB, (int64_t)W * 4 * nch));
+    AFQMC_TRY(talloc(s, &s->cfp, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->cf_h, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->cf_l, (int64_t)W * 2 * nch));
+    AFQMC_TRY(talloc(s, &s->cf_s, (int64_t)W * 2));
+    AFQMC_TRY(talloc(s, &s->A_f, (int64_t)W * M * 2 * M));
     AFQMC_TRY(talloc(s, &s->A_h, (int64_t)W * M * 2 * M));
     AFQMC_TRY(talloc(s, &s->A_l, (int64_t)W * M * 2 * M));
+    AFQMC_TRY(talloc(s, &s->A_s, (int64_t)W * M));
     AFQMC_TRY(talloc(s, &s->Pacc, wall));
     AFQMC_TRY(talloc(s, &s->Pacc_h, wall));
     AFQMC_TRY(talloc(s, &s->Pacc_l, wall));
+    AFQMC_TRY(talloc(s, &s->Pacc_s, (int64_t)W * 4 * N));
     AFQMC_TRY(talloc(s, &s->E1, W));
     // static operands
     const double* Ltr = static_cast<const double*>(wk->f.Lt[0]);  // real [Nchol][N][M]
     split_rows(Ltr, M, (int64_t)nch * N, M, s->Lt_h, s->Lt_l, s->Lt_s, st);
     count_launch();
     split_f64_kernel<<<nb(nch * NM), kT, 0, st>>>(Ltr, s->Ltp_h, s->Ltp_l, nch * NM);
-    dim3 gl((unsigned)((MM + 31) / 32), (unsigned)((nch + 31) / 32));
-    count_launch();
-    LT_kernel<<<gl, dim3(32, 8), 0, st>>>(wk->ham->L, MM, nch, s->LT_h, s->LT_l);
-    count_launch();
-    split_f64_kernel<<<nb(MM), kT, 0, st>>>(wk->f.Bh, s->Bh_h, s->Bh_l, MM);
+    {   // L^T [M*M][Nchol] in FP64 (temporary), then its row-scaled pair
+        double* LTd = nullptr;
+        if (cudaMalloc(&LTd, sizeof(double) * (size_t)MM * nch) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(AFQMC_ERR_OOM, "BF16X3 workspace allocation failed");
+        }
+        dim3 gl((unsigned)((MM + 31) / 32), (unsigned)((nch + 31) / 32));
+        count_launch();
+        LT_kernel<<<gl, dim3(32, 8), 0, st>>>(wk->ham->L, MM, nch, LTd);
+        split_rows(LTd, nch, MM, nch, s->LT_h, s->LT_l, s->LT_s, st);
+        cudaStreamSynchronize(st);
+        cudaFree(LTd);
+    }
+    split_rows(wk->f.Bh, M, M, M, s->Bh_h, s->Bh_l, s->Bh_s, st);   // B is symmetric: rows = columns
     count_launch();
     psiT_kernel<<<nb(NM), kT, 0, st>>>(wk->f.Psi[0], M, N, s->PsiT_f);
     split_rows(s->PsiT_f, M, N, M, s->PsiT_h, s->PsiT_l, s->PsiT_s, st);
@@ -607,65 +669,67 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, W = s->W, nch = s->Nchol;
     const int64_t MM = (int64_t)M * M;
-    const int BNm = M % 256 == 0 ? 256 : 128;
     hs_coefficients(x, wk->xbar, wk->weight, W, nch, wk->coef, wk->flags, st);
     count_launch();
-    coef_split_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->coef, W, nch, s->cf_h, s->cf_l);
-    {   // A_w = sum_n c_wn L_n  -> [W][M][2M]
+    coef_planar_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->coef, W, nch, s->cfp);
+    split_rows(s->cfp, nch, 2LL * W, nch, s->cf_h, s->cf_l, s->cf_s, st);
+    {   // A_w = sum_n c_wn L_n  -> fp32 [W][M][2M], then its row-scaled pair
         EpiParams e;
-        e.kind = EPI_HSPOT;
+        e.kind = EPI_HSPOT_F32;
         e.rows_valid = 2LL * W;
         e.cols_valid = MM;
         e.M = M;
-        e.out_hi = s->A_h;
-        e.out_lo = s->A_l;
-        AFQMC_TRY(tc_gemm(smat(s->cf_h, s->cf_l, nch, 2LL * W), BatchMap{}, smat(s->LT_h, s->LT_l, nch, MM), BatchMap{},
-                          2LL * W, MM, nch, 1, e, 256, false, wk->flags, st));
+        e.out_f32 = s->A_f;
+        AFQMC_TRY(tc_gemm(smat(s->cf_h, s->cf_l, nch, 2LL * W, 1, s->cf_s), BatchMap{},
+                          smat(s->LT_h, s->LT_l, nch, MM, 1, s->LT_s), BatchMap{}, 2LL * W, MM, nch, 1, e, 128, true,
+                          wk->flags, st));
+        split_rows(s->A_f, 2LL * M, (int64_t)W * M, 2LL * M, s->A_h, s->A_l, s->A_s, st);
     }
     const int64_t rowsAll = (int64_t)W * 4 * N;
-    {   // P0 = B Phi -> doubled operand + accumulator
+    const int64_t WS = 2LL * W;
+    {   // P0 = B Phi -> accumulator (fp32), then the doubled operand of the first term
         EpiParams e;
-        e.kind = EPI_BFIRST;
+        e.kind = EPI_F32;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
-        e.M = M;
-        e.N = N;
-        e.out_hi = s->PD_h[0];
-        e.out_lo = s->PD_l[0];
-        e.acc = s->Pacc;
-        AFQMC_TRY(tc_gemm(smat(s->PhiTp_h, s->PhiTp_l, M, rowsAll), BatchMap{}, smat(s->Bh_h, s->Bh_l, M, M),
-                          BatchMap{}, rowsAll, M, M, 1, e, BNm, false, wk->flags, st));
+        e.ld = M;
+        e.out_f32 = s->Pacc;
+        AFQMC_TRY(tc_gemm(smat(s->PhiT_h[s->cur], s->PhiT_l[s->cur], M, rowsAll, 1, s->PhiT_s[s->cur]), BatchMap{},
+                          smat(s->Bh_h, s->Bh_l, M, M, 1, s->Bh_s), BatchMap{}, rowsAll, M, M, 1, e, 128, true,
+                          wk->flags, st));
     }
     const float sq = (float)sqrt(wk->tau);
     for (int k = 1; k <= wk->opts.k_taylor; ++k) {
-        const int src = (k - 1) & 1, dst = k & 1;
-        EpiParams e;
-        e.kind = EPI_TAYLOR;
+        // doubled operand of the previous term (P0 = the accumulator before any term is added)
+        count_launch();
+        split_doubled_kernel<<<(unsigned)((WS * N + 7) / 8), kT, 0, st>>>(
+            k == 1 ? s->Pacc : s->Pk, WS, N, M, reinterpret_cast<__half*>(s->PD_h), reinterpret_cast<__half*>(s->PD_l),
+            s->PD_s);
+        EpiParams e;   // P_k = (i sqrt(tau) / k) P_{k-1} A^T  -> Pk (fp32), Pacc += P_k
+        e.kind = EPI_TAYLOR_F32;
         e.rows_valid = 4LL * N;
         e.cols_valid = M;
         e.M = M;
         e.N = N;
-        e.out_hi = s->PD_h[dst];
-        e.out_lo = s->PD_l[dst];
+        e.out_f32 = s->Pk;
         e.acc = s->Pacc;
         e.scale = sq / (float)k;
-        AFQMC_TRY(tc_gemm(smat(s->PD_h[src], s->PD_l[src], 2LL * M, 4LL * N, W), BatchMap{1, W},
-                          smat(s->A_h, s->A_l, 2LL * M, M, W), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, BNm, false,
-                          wk->flags, st));
+        AFQMC_TRY(tc_gemm(smat(s->PD_h, s->PD_l, 2LL * M, 4LL * N, W, s->PD_s), BatchMap{1, W},
+                          smat(s->A_h, s->A_l, 2LL * M, M, W, s->A_s), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, 128,
+                          true, wk->flags, st));
     }
     const int nxt = s->cur ^ 1;
     {   // Phi' = B Pacc  (FP64 master of the proposed walkers)
-        const int64_t n = rowsAll * M;
-        count_launch();
-        split_f32_kernel<<<nb(n), kT, 0, st>>>(s->Pacc, s->Pacc_h, s->Pacc_l, n);
+        split_rows(s->Pacc, M, rowsAll, M, s->Pacc_h, s->Pacc_l, s->Pacc_s, st);
         EpiParams e;
         e.kind = EPI_F64;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
         e.ld = M;
         e.out_f64 = s->PhiT[nxt];
-        AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, M, rowsAll), BatchMap{}, smat(s->Bh_h, s->Bh_l, M, M), BatchMap{},
-                          rowsAll, M, M, 1, e, BNm, false, wk->flags, st));
+        AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, M, rowsAll, 1, s->Pacc_s), BatchMap{},
+                          smat(s->Bh_h, s->Bh_l, M, M, 1, s->Bh_s), BatchMap{}, rowsAll, M, M, 1, e, 128, true,
+                          wk->flags, st));
     }
     split_walkers(s, nxt, st);
     AFQMC_TRY(overlap_logdet(wk, nxt, false, st));
