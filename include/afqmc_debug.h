@@ -44,6 +44,12 @@ int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol
  *   t, X   [W][2][Nchol]    complex traces Tr(Ltilde_n Theta), Tr((Ltilde_n Theta)^2)
  *   E1     [W]              complex one-body energy sum_s Tr(Psi_s^T h Theta_s) */
 typedef struct afqmc_walkers* afqmc_wk_debug_t;
+
+/* Launch-shape knobs of the calling thread's later tensor-core launches (0 = default):
+ * grid_cap = most CTAs per persistent launch, bn_max = 128 to narrow plain GEMM tiles,
+ * energy_bk = 16 or 32, the K chunk of the fused energy kernel.  For tuning experiments;
+ * results do not depend on them. */
+int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk);
 int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X,
                             double* E1);
 

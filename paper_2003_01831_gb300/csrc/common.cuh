@@ -59,6 +59,7 @@ long long launch_count();
 struct LaunchPolicy {
     int grid_cap = 0;    // > 0: at most this many CTAs per persistent launch
     int bn_max = 256;    // 128: narrow every plain GEMM tile to 128 columns
+    int energy_bk = 0;   // K chunk of the fused energy kernel: 16 (default) or 32
 };
 LaunchPolicy& launch_policy();
 

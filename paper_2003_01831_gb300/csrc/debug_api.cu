@@ -120,3 +120,14 @@ extern "C" int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* 
     if (!wk) return fail(AFQMC_ERR_BADARG, "debug_mixed_terms: NULL handle");
     return tc_debug_terms(wk, ST, Sinv, ThetaT, t, X, E1);
 }
+
+extern "C" int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk) {
+    if (grid_cap < 0 || (bn_max != 0 && bn_max != 128 && bn_max != 256) ||
+        (energy_bk != 0 && energy_bk != 16 && energy_bk != 32))
+        return fail(AFQMC_ERR_BADARG, "debug_set_launch_policy: bad knob value");
+    LaunchPolicy& p = launch_policy();
+    p.grid_cap = grid_cap;
+    p.bn_max = bn_max == 0 ? 256 : bn_max;
+    p.energy_bk = energy_bk;
+    return AFQMC_OK;
+}

@@ -306,6 +306,253 @@ __global__ void __launch_bounds__(kThreads)
     if (t == 0) logdet[blockIdx.x] = cplx{logabs, atan2(sin(phase), cos(phase))};
 }
 
+// ------------------------------------------------------- Gauss-Jordan in shared memory
+// The same elimination (pivot max |re|+|im|, lowest index on ties; physical row swaps; the
+// in-place inverse with its column permutation undone at the end) with the matrix held on
+// chip: one CTA for N <= kGJSmemOne, else a cluster of two CTAs that own alternate columns
+// (column j lives in CTA j % 2 at local column j / 2) and exchange the pivot column and the
+// pivot index through distributed shared memory, two cluster barriers per elimination step.
+// FP64 throughput, not memory latency, then bounds the elimination.
+constexpr int kGJSmemOne = 96;      // largest N done by one CTA (N^2 complex in shared memory)
+constexpr int kGJSmemMax = 128;     // largest N done by the two-CTA cluster
+constexpr int kGJT = 512;           // threads per CTA
+// local columns per lane: COLS = ceil(H / 32) <= 3 (template parameter)
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+    uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p)), r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_peer_f64(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer_s32(uint32_t addr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+template <int C>
+__device__ __forceinline__ void gj_sync() {
+    if (C == 1) __syncthreads();
+    else cluster_sync_all();
+}
+
+template <int C, int COLS>
+__global__ void __launch_bounds__(kGJT)
+    gj_smem_kernel(cplx* Sbase, int64_t stride, int N, cplx* logdet, int with_inverse, unsigned* flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int H = (N + C - 1) / C;                   // local columns
+    cplx* A = reinterpret_cast<cplx*>(smem_raw);     // [N][H]
+    cplx* pcol = A + (size_t)N * H;                  // pivot column (before this step's swap)
+    cplx* prow = pcol + N;                           // scaled pivot row, local columns
+    int* perm = reinterpret_cast<int*>(prow + H);    // pivot row of every step
+    int* pos = perm + N;                             // final column of each stored column
+    __shared__ double red_v[kGJT / 32];
+    __shared__ int red_i[kGJT / 32];
+    __shared__ int s_piv;
+    __shared__ int s_singular;
+    constexpr int R = COLS <= 2 ? 4 : 2;               // rows per warp in flight
+    const int rank = C == 1 ? 0 : (int)cluster_rank();
+    const int64_t mat = C == 1 ? blockIdx.x : blockIdx.x / C;
+    cplx* G = Sbase + mat * stride;
+    const int t = threadIdx.x;
+    const int NH = N * H;
+    // load my columns: global column j = c*C + rank
+    for (int e = t; e < NH; e += kGJT) {
+        const int i = e / H, c = e % H, j = c * C + rank;
+        A[e] = j < N ? G[(int64_t)i * N + j] : cplx{0.0, 0.0};
+    }
+    if (t == 0) s_singular = 0;
+    double logabs = 0.0, phase = 0.0;   // thread 0 of rank 0
+    gj_sync<C>();
+    for (int k = 0; k < N; ++k) {
+        const int owner = k % C, lk = k / C;
+        if (rank == owner) {
+            double best = -1.0;
+            int bi = N;
+            for (int i = k + t; i < N; i += kGJT) {
+                const double v = abs1(A[i * H + lk]);
+                if (v > best || (v != v && best == best)) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > best || (v2 == best && i2 < bi) || (v2 != v2 && best == best)) { best = v2; bi = i2; }
+            }
+            if ((t & 31) == 0) { red_v[t >> 5] = best; red_i[t >> 5] = bi; }
+            // the pivot column (pre-swap) to both CTAs
+            for (int i = t; i < N; i += kGJT) {
+                const cplx v = A[i * H + lk];
+                pcol[i] = v;
+                if (C > 1) {
+                    const uint32_t a = peer_addr(&pcol[i], (uint32_t)(owner ^ 1));
+                    st_peer_f64(a, v.re);
+                    st_peer_f64(a + 8, v.im);
+                }
+            }
+            __syncthreads();
+            if (t == 0) {
+                double bv = red_v[0];
+                int bidx = red_i[0];
+                for (int q = 1; q < kGJT / 32; ++q) {
+                    const double v2 = red_v[q];
+                    const int i2 = red_i[q];
+                    if (v2 > bv || (v2 == bv && i2 < bidx) || (v2 != v2 && bv == bv)) { bv = v2; bidx = i2; }
+                }
+                const int sing = (bv > 0.0) ? 0 : ((bv != bv) ? 2 : 1);
+                s_piv = bidx;
+                s_singular = sing;
+                if (C > 1) {
+                    st_peer_s32(peer_addr(&s_piv, (uint32_t)(owner ^ 1)), bidx);
+                    st_peer_s32(peer_addr(&s_singular, (uint32_t)(owner ^ 1)), sing);
+                }
+            }
+        }
+        gj_sync<C>();
+        if (s_singular) break;
+        const int p = s_piv;
+        if (p != k) {
+            for (int c = t; c < H; c += kGJT) {
+                const cplx a = A[k * H + c];
+                A[k * H + c] = A[p * H + c];
+                A[p * H + c] = a;
+            }
+        }
+        __syncthreads();
+        if (t == 0) {
+            perm[k] = p;
+            if (p != k) {
+                const cplx a = pcol[k];
+                pcol[k] = pcol[p];
+                pcol[p] = a;
+            }
+        }
+        __syncthreads();
+        const cplx piv = pcol[k];
+        const cplx inv = cdiv(cplx{1.0, 0.0}, piv);
+        if (t == 0 && rank == 0) {
+            logabs += log(hypot(piv.re, piv.im));
+            phase += atan2(piv.im, piv.re) + (p != k ? M_PI : 0.0);
+        }
+        for (int c = t; c < H; c += kGJT) prow[c] = A[k * H + c] * inv;
+        __syncthreads();
+        // Rank-1 update: warps over rows, lanes over (at most COLS) local columns, so the
+        // multiplier pcol[i] is one broadcast per row and the pivot row sits in registers.
+        // Padding columns (j >= N) hold zeros and stay zero.
+        const int warp = t >> 5, lane = t & 31;
+        const bool own_k = rank == owner;
+        // R rows per warp at a time: all their loads are issued before any arithmetic, so
+        // a lane has R * COLS independent updates in flight.
+        if (with_inverse) {
+            cplx pr[COLS];
+#pragma unroll
+            for (int u = 0; u < COLS; ++u) pr[u] = (lane + 32 * u < H) ? prow[lane + 32 * u] : cplx{0.0, 0.0};
+            for (int i0 = warp; i0 < N; i0 += R * (kGJT / 32)) {
+                cplx m[R], a[R][COLS];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = i0 + r * (kGJT / 32);
+                    const bool live = i < N && i != k;
+                    m[r] = live ? cplx{0.0, 0.0} - pcol[i] : cplx{0.0, 0.0};
+#pragma unroll
+                    for (int u = 0; u < COLS; ++u) {
+                        const int c = lane + 32 * u;
+                        if (live && c < H) a[r][u] = A[i * H + c];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = i0 + r * (kGJT / 32);
+                    if (i >= N || i == k) continue;
+#pragma unroll
+                    for (int u = 0; u < COLS; ++u) {
+                        const int c = lane + 32 * u;
+                        if (c >= H) continue;
+                        if (own_k && c == lk) a[r][u] = m[r] * inv;   // column k of the inverse
+                        else cfma(a[r][u], m[r], pr[u]);
+                        A[i * H + c] = a[r][u];
+                    }
+                }
+            }
+            for (int c = t; c < H; c += kGJT) A[k * H + c] = (own_k && c == lk) ? inv : prow[c];
+        } else {
+            // trailing block only: rows i > k, columns j > k
+            const int c0 = (k + 1 - rank + C - 1) / C;   // first local column with j > k
+            cplx pr[COLS];
+#pragma unroll
+            for (int u = 0; u < COLS; ++u) {
+                const int c = c0 + lane + 32 * u;
+                pr[u] = c < H ? prow[c] : cplx{0.0, 0.0};
+            }
+            for (int i0 = k + 1 + warp; i0 < N; i0 += R * (kGJT / 32)) {
+                cplx m[R], a[R][COLS];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = i0 + r * (kGJT / 32);
+                    m[r] = i < N ? cplx{0.0, 0.0} - pcol[i] : cplx{0.0, 0.0};
+#pragma unroll
+                    for (int u = 0; u < COLS; ++u) {
+                        const int c = c0 + lane + 32 * u;
+                        if (i < N && c < H) a[r][u] = A[i * H + c];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = i0 + r * (kGJT / 32);
+                    if (i >= N) continue;
+#pragma unroll
+                    for (int u = 0; u < COLS; ++u) {
+                        const int c = c0 + lane + 32 * u;
+                        if (c >= H) continue;
+                        cfma(a[r][u], m[r], pr[u]);
+                        A[i * H + c] = a[r][u];
+                    }
+                }
+            }
+        }
+        gj_sync<C>();
+    }
+    if (s_singular) {
+        if (t == 0 && rank == 0) {
+            logdet[mat] = cplx{-INFINITY, 0.0};
+            atomicOr(flags, s_singular == 2 ? FLAG_NONFINITE : FLAG_SINGULAR);
+        }
+        if (C > 1) cluster_sync_all();   // keep the peer's shared memory alive until both are done
+        return;
+    }
+    if (with_inverse) {
+        // undo the pivoting on the columns: for k = N-1..0 swap columns k and perm[k]
+        if (t == 0) {
+            for (int j = 0; j < N; ++j) pos[j] = j;    // pos: stored column -> final column, via idx
+            int* idx = pos;                             // idx[j] = stored column at final position j
+            for (int k = N - 1; k >= 0; --k) {
+                const int q = perm[k];
+                const int a = idx[k];
+                idx[k] = idx[q];
+                idx[q] = a;
+            }
+        }
+        __syncthreads();
+        // pos currently holds idx; write stored column s = idx[j] to final column j
+        for (int e = t; e < N * N; e += kGJT) {
+            const int i = e / N, j = e % N;
+            const int sc = pos[j];
+            if (sc % C != rank) continue;
+            G[(int64_t)i * N + j] = A[i * H + sc / C];
+        }
+    }
+    if (t == 0 && rank == 0) logdet[mat] = cplx{logabs, atan2(sin(phase), cos(phase))};
+    if (C > 1) cluster_sync_all();
+}
+
 // ------------------------------------------------------------------ traces of T
 __global__ void __launch_bounds__(kThreads)
     trace_kernel(const cplx* T, int W, int N, int n0, cplx* t_out, cplx* X_out, int64_t ldo) {
@@ -583,6 +830,39 @@ void zgemm(const GemmArgs& g, cudaStream_t st) {
 void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet, bool with_inverse,
                             unsigned* flags, cudaStream_t st) {
     if (count <= 0) return;
+    if (N <= kGJSmemMax) {
+        const int C = N <= kGJSmemOne ? 1 : 2;
+        const int H = (N + C - 1) / C;
+        const int cols = (H + 31) / 32;
+        const size_t sm = (size_t)N * H * sizeof(cplx) + (size_t)(N + H) * sizeof(cplx) + 2 * N * sizeof(int);
+        const int wi = with_inverse ? 1 : 0;
+        count_launch();
+        if (C == 1) {
+            auto launch1 = [&](auto kern) {
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                kern<<<count, kGJT, sm, st>>>(S, stride, N, logdet, wi, flags);
+            };
+            if (cols == 1) launch1(gj_smem_kernel<1, 1>);
+            else if (cols == 2) launch1(gj_smem_kernel<1, 2>);
+            else launch1(gj_smem_kernel<1, 3>);
+        } else {
+            cudaFuncSetAttribute(gj_smem_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)count * 2);
+            cfg.blockDim = dim3(kGJT);
+            cfg.dynamicSmemBytes = sm;
+            cfg.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaLaunchKernelEx(&cfg, gj_smem_kernel<2, 2>, S, stride, N, logdet, wi, flags);   // H <= 64
+        }
+        return;
+    }
     const size_t sm = (size_t)N * (2 * sizeof(cplx) + sizeof(int));
     count_launch();
     gj_kernel<<<count, kThreads, sm, st>>>(S, stride, N, logdet, with_inverse ? 1 : 0, flags);

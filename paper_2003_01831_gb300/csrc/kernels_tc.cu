@@ -578,47 +578,62 @@ __device__ __forceinline__ int named_bar_and(int pred) {
     return r;
 }
 
-// Energy kernel pipeline: 32-wide K chunks with 64-byte swizzle, two stages of 48 KB, one TMEM
-// buffer (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  The epilogue drains
-// both accumulators into a 128 x 256 fp32 tile in shared memory (XOR-swizzled within 32-column
-// groups so row and column reads are both conflict-free), releases TMEM at once, and computes
-// the traces from shared memory while the tensor cores run the next tile.
-constexpr int kEBK = 32;
-constexpr int kEStages = 2;
-constexpr int kEABytes = kBM * kEBK * 2;            // 8 KB per plane
-constexpr int kEBBytes = 256 * kEBK * 2;            // 16 KB per plane
-constexpr int kEStageBytes = 2 * kEABytes + 2 * kEBBytes;
+// Energy kernel pipeline: K chunks of BK = 16 (32-byte swizzle, four 24 KB stages) or 32
+// (64-byte swizzle, two 48 KB stages) in 96 KB of shared memory, one TMEM buffer
+// (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  The epilogue drains both
+// accumulators into a 128 x 256 fp32 tile in shared memory (XOR-swizzled within 32-column groups
+// so row and column reads are both conflict-free), releases TMEM at once, and computes the
+// traces from shared memory while the tensor cores run the next tile.  The operands come from
+// L2 at ~1 us latency; the narrower chunks keep three stages in flight instead of one.
+constexpr int kEStageRing = 96 * 1024;
+template <int BK>
+struct ECfg {
+    static constexpr int kABytes = kBM * BK * 2;       // per plane
+    static constexpr int kBBytes = 256 * BK * 2;       // per plane
+    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
+    static constexpr int kStages = kEStageRing / kStageBytes;
+    static_assert(kStages >= 2 && kStages <= 4, "stage ring");
+};
+constexpr int kEBKDefault = 16;
 constexpr int kETileFloats = 128 * 256;
 
-__device__ __forceinline__ int swz(int row, int col) { return row * 256 + ((col & ~31) | ((col ^ row) & 31)); }
+template <int BK>
+__device__ __forceinline__ uint64_t edesc(uint32_t saddr) {
+    return BK == 16 ? desc_sw32(saddr) : desc_sw64(saddr);
+}
 
+
+template <int BK>
 __device__ void energy_producer(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
                                 const CUtensorMap* tBh, const CUtensorMap* tBl, const EnergyShape& es) {
+    using C = ECfg<BK>;
     int64_t g = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < es.tiles && ok; t += gridDim.x) {
         int ng, wg;
         energy_tile(es, t, ng, wg);
         for (int kb = 0; kb < es.nk; ++kb, ++g) {
-            const int st = (int)(g % kEStages);
-            const uint32_t ph = (uint32_t)((g / kEStages) & 1);
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
             if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
-            uint8_t* s = sbase + (size_t)st * kEStageBytes;
-            mbar_arrive_expect_tx(&ctl->full[st], kEStageBytes);
-            const int x = kb * kEBK;
+            uint8_t* s = sbase + (size_t)st * C::kStageBytes;
+            mbar_arrive_expect_tx(&ctl->full[st], C::kStageBytes);
+            const int x = kb * BK;
             tma_load_2d(s, tAh, &ctl->full[st], x, ng * 128);
-            tma_load_2d(s + kEABytes, tAl, &ctl->full[st], x, ng * 128);
-            tma_load_2d(s + 2 * kEABytes, tBh, &ctl->full[st], x, wg * 256);
-            tma_load_2d(s + 2 * kEABytes + kEBBytes, tBl, &ctl->full[st], x, wg * 256);
+            tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], x, ng * 128);
+            tma_load_2d(s + 2 * C::kABytes, tBh, &ctl->full[st], x, wg * 256);
+            tma_load_2d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], x, wg * 256);
         }
     }
     if (!ok) {
-        const int64_t first = g > kEStages ? g - kEStages : 0;
-        for (int64_t j = first; j < g; ++j) wait_drain(&ctl->full[j % kEStages], (uint32_t)((j / kEStages) & 1));
+        const int64_t first = g > C::kStages ? g - C::kStages : 0;
+        for (int64_t j = first; j < g; ++j) wait_drain(&ctl->full[j % C::kStages], (uint32_t)((j / C::kStages) & 1));
     }
 }
 
+template <int BK>
 __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es) {
+    using C = ECfg<BK>;
     constexpr uint32_t idesc = idesc_bf16(kBM, 256, true);   // fp16 planes, M=128, N=256
     const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
     int64_t g = 0;
@@ -628,17 +643,17 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
         if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
         tc_fence_after();
         for (int kb = 0; kb < es.nk; ++kb, ++g) {
-            const int st = (int)(g % kEStages);
-            const uint32_t ph = (uint32_t)((g / kEStages) & 1);
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
             if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sa = smem_u32(sbase + (size_t)st * kEStageBytes);
-            const uint32_t sal = sa + kEABytes, sb = sa + 2 * kEABytes, sbl = sb + kEBBytes;
+            const uint32_t sa = smem_u32(sbase + (size_t)st * C::kStageBytes);
+            const uint32_t sal = sa + C::kABytes, sb = sa + 2 * C::kABytes, sbl = sb + C::kBBytes;
 #pragma unroll
-            for (int kk = 0; kk < kEBK / 16; ++kk) {
+            for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint32_t off = kk * 32;
-                const uint64_t ah = desc_sw64(sa + off), al = desc_sw64(sal + off);
-                const uint64_t bh = desc_sw64(sb + off), bl = desc_sw64(sbl + off);
+                const uint64_t ah = edesc<BK>(sa + off), al = edesc<BK>(sal + off);
+                const uint64_t bh = edesc<BK>(sb + off), bl = edesc<BK>(sbl + off);
                 const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
                 mma_bf16(d1, ah, bh, idesc, acc);
                 mma_bf16(d2, ah, bl, idesc, acc);
@@ -654,19 +669,47 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
     wait_drain(&ctl->done, 0);
 }
 
-template <int Np>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+// Energy CTA: warp 0 = TMA producer, warp 1 = TMEM allocator + MMA issuer, warps 2..9 = epilogue
+// (two warps per TMEM lane quadrant; warp w drains lanes 32 (w % 4) .. + 31, half (w - 2) / 4 of
+// the columns, and computes half of the traces of those rows).
+constexpr int kEThreads = 320;
+constexpr int kEEpi = 256;
+__device__ __forceinline__ void ebar() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+__device__ __forceinline__ int ebar_and(int pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 256, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred)
+        : "memory");
+    return r;
+}
+// Tile element (row, col) of the 128 x 256 fp32 tile: 16-byte groups XOR-swizzled by the row
+// within each 32-column block, so a row's 4-column group is one conflict-free 16-byte access
+// and a column read across 32 rows hits 32 different banks.
+__device__ __forceinline__ int swz4(int row, int col) {
+    return row * 256 + (col & ~31) + ((((col >> 2) ^ row) & 7) << 2) + (col & 3);
+}
+
+template <int Np, int BK>
+__global__ void __launch_bounds__(kEThreads, 1)
     tc_energy_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                      const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
                      EnergyShape es, unsigned* flags) {
-    constexpr int Q = Np / 32;
-    constexpr int G = 128 / Np;
+    constexpr int Q = Np / 32;     // TMEM quadrants per n-block
+    constexpr int G = 128 / Np;    // n-blocks (rows) and walker-spins (columns) per tile
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    float* tile = reinterpret_cast<float*>(sbase + kEStages * kEStageBytes);
-    float* colscale = tile + kETileFloats;                       // 256 column scales of the tile
-    double* ered = reinterpret_cast<double*>(colscale + 256);    // [4 warps][4 j][4]
-    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(ered + 64);
+    using C = ECfg<BK>;
+    float* tile = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
+    // 256 column scales of the tile, reused after the drain for the partial traces
+    // ered[((h * 4 + q) * 4 + j) * 4 + v]
+    float* colscale = tile + kETileFloats;
+    double* ered = reinterpret_cast<double*>(colscale);
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(colscale + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tAh);
@@ -674,14 +717,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tma_prefetch_desc(&tBh);
         tma_prefetch_desc(&tBl);
     }
-    // set-up: two stages, one TMEM buffer of 512 columns
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kEStages; ++i) {
+        for (int i = 0; i < C::kStages; ++i) {
             mbar_init(&ctl->full[i], 1);
             mbar_init(&ctl->empty[i], 1);
         }
         mbar_init(&ctl->tfull[0], 1);
-        mbar_init(&ctl->tempty[0], 128);
+        mbar_init(&ctl->tempty[0], kEEpi);
         mbar_init(&ctl->done, 1);
         ctl->abort = 0;
         fence_mbar_init();
@@ -695,63 +737,99 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0) energy_producer(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es);
+        if (lane == 0) energy_producer<BK>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es);
     } else if (warp == 1) {
-        if (lane == 0) energy_mma(sbase, ctl, es);
+        if (lane == 0) energy_mma<BK>(sbase, ctl, es);
     } else {
-        const int g4 = warp & 3;               // TMEM lane quadrant = rows 32*g4 .. +31
-        const int row = g4 * 32 + lane;        // tile row = (n-block i, a')
+        const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
+        const int h = (warp - 2) >> 2;         // column half (drain) / trace half
+        const int row = q * 32 + lane;         // tile row = (n-block i_blk, a')
         const int i_blk = row / Np, ap = row % Np;
-        const int mu = (row % Np) / 32;        // which 32-row slice of the n-block
-        const int et = threadIdx.x - 64;       // 0..127
-        const uint32_t t1 = ctl->tmem_base + ((uint32_t)(g4 * 32) << 16);
+        const int et = threadIdx.x - 64;       // 0..255
+        const uint32_t t1 = ctl->tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
         const uint32_t t2 = t1 + 256;
+        // trace work of this half: G >= 2: walker-spins j in [h G/2, (h+1) G/2), every b;
+        // G == 1: j = 0, b in [h Np/2, (h+1) Np/2)
+        constexpr int JH = G >= 2 ? G / 2 : 1;
+        const int j0 = G >= 2 ? h * JH : 0;
+        const int b0 = G >= 2 ? 0 : h * (Np / 2);
+        constexpr int NB = G >= 2 ? Np : Np / 2;
+        const int r7 = row & 7;
         int it = 0;
         for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
             int ng, wg;
             energy_tile(es, t, ng, wg);
-            for (int c = et; c < 256; c += 128) {
-                const int64_t brow = (int64_t)wg * 256 + c;
-                colscale[c] = brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
+            {
+                const int64_t brow = (int64_t)wg * 256 + et;
+                colscale[et] = brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
             }
             const int64_t arow = (int64_t)ng * 128 + row;
             const float sa = arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
-            named_bar_epi();
+            ebar();
             const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
-            if (!named_bar_and(got ? 1 : 0)) break;   // all four warps leave together
+            if (!ebar_and(got ? 1 : 0)) break;   // all eight warps leave together
             tc_fence_after();
-            // drain TMEM into the shared tile, scaled to true units
+            // drain this half's 128 columns of both accumulators, scaled to true units
 #pragma unroll 1
-            for (int c = 0; c < 8; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 uint32_t a1[32], a2[32];
                 tmem_ld32_nw(t1 + c * 32, a1);
                 tmem_ld32_nw(t2 + c * 32, a2);
                 tmem_ld_wait();
+                const int col0 = h * 128 + c * 32;
+                float* trow = tile + row * 256 + col0;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int col = c * 32 + q;
-                    tile[swz(row, col)] = (__uint_as_float(a1[q]) + __uint_as_float(a2[q])) * (sa * colscale[col]);
+                for (int g = 0; g < 8; ++g) {
+                    const float4 cs = *reinterpret_cast<const float4*>(colscale + col0 + 4 * g);   // broadcast
+                    float4 v;
+                    v.x = (__uint_as_float(a1[4 * g]) + __uint_as_float(a2[4 * g])) * (sa * cs.x);
+                    v.y = (__uint_as_float(a1[4 * g + 1]) + __uint_as_float(a2[4 * g + 1])) * (sa * cs.y);
+                    v.z = (__uint_as_float(a1[4 * g + 2]) + __uint_as_float(a2[4 * g + 2])) * (sa * cs.z);
+                    v.w = (__uint_as_float(a1[4 * g + 3]) + __uint_as_float(a2[4 * g + 3])) * (sa * cs.w);
+                    *reinterpret_cast<float4*>(trow + ((g ^ r7) << 2)) = v;
                 }
             }
             tc_fence_before();
             mbar_arrive(&ctl->tempty[0]);              // tensor memory free: next tile's MMAs start
-            named_bar_epi();
-            // traces of every (n, ws) block this row belongs to
-#pragma unroll 1
-            for (int j = 0; j < G; ++j) {
+            ebar();                                    // tile complete; colscale no longer needed
+            float part[JH][4];                         // [j of this half][tr, ti, Xr, Xi]
+#pragma unroll
+            for (int jl = 0; jl < JH; ++jl) {
+                const int j = j0 + jl;
                 const int cre = j * 2 * Np, cim = cre + Np;
+                const float* own = tile + row * 256;
+                // Partner column cre + ap (cim + ap: Np further, same swizzle) in rows
+                // rb = i_blk Np + b + u.  With b a multiple of 8 the swizzle slot of row rb is
+                // ((cre + ap) / 4 ^ u) & 7, so the 8 offsets are set up once.
+                const int pc = cre + ap;
+                int poff[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) poff[u] = (pc & ~31) + (((((pc >> 2) & 7) ^ u)) << 2) + (pc & 3) + u * 256;
                 float xr[4] = {0.f, 0.f, 0.f, 0.f}, xi[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-                for (int b = 0; b < Np; ++b) {
-                    const float orr = tile[swz(row, cre + b)], oi = tile[swz(row, cim + b)];
-                    const int rb = i_blk * Np + b;
-                    const float pr = tile[swz(rb, cre + ap)], pi = tile[swz(rb, cim + ap)];
-                    xr[b & 3] = fmaf(orr, pr, fmaf(-oi, pi, xr[b & 3]));
-                    xi[b & 3] = fmaf(orr, pi, fmaf(oi, pr, xi[b & 3]));
+#pragma unroll 1
+                for (int b = b0; b < b0 + NB; b += 8) {
+                    const float* prow0 = tile + (i_blk * Np + b) * 256;
+#pragma unroll
+                    for (int hq = 0; hq < 2; ++hq) {   // b .. b+3, b+4 .. b+7
+                        const int slot = ((((b >> 2) + hq) ^ row) & 7) << 2;
+                        const float4 orv = *reinterpret_cast<const float4*>(own + ((cre + b) & ~31) + slot);
+                        const float4 oiv = *reinterpret_cast<const float4*>(own + ((cim + b) & ~31) + slot);
+                        const float orr[4] = {orv.x, orv.y, orv.z, orv.w}, oii[4] = {oiv.x, oiv.y, oiv.z, oiv.w};
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float pr = prow0[poff[4 * hq + u]], pi = prow0[poff[4 * hq + u] + Np];
+                            xr[u] = fmaf(orr[u], pr, fmaf(-oii[u], pi, xr[u]));
+                            xi[u] = fmaf(orr[u], pi, fmaf(oii[u], pr, xi[u]));
+                        }
+                    }
                 }
-                double tr = tile[swz(row, cre + ap)], ti = tile[swz(row, cim + ap)];
-                double Xr = (double)((xr[0] + xr[1]) + (xr[2] + xr[3]));
-                double Xi = (double)((xi[0] + xi[1]) + (xi[2] + xi[3]));
+                float tr = 0.f, ti = 0.f;
+                if (ap >= b0 && ap < b0 + NB) {      // the diagonal element lies in this half
+                    tr = tile[swz4(row, cre + ap)];
+                    ti = tile[swz4(row, cim + ap)];
+                }
+                float Xr = (xr[0] + xr[1]) + (xr[2] + xr[3]);
+                float Xi = (xi[0] + xi[1]) + (xi[2] + xi[3]);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -759,33 +837,42 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     Xr += __shfl_xor_sync(0xffffffffu, Xr, o);
                     Xi += __shfl_xor_sync(0xffffffffu, Xi, o);
                 }
-                if (lane == 0) {
-                    double* e = ered + (g4 * 4 + j) * 4;
-                    e[0] = tr;
-                    e[1] = ti;
-                    e[2] = Xr;
-                    e[3] = Xi;
-                }
+                part[jl][0] = tr;
+                part[jl][1] = ti;
+                part[jl][2] = Xr;
+                part[jl][3] = Xi;
             }
-            named_bar_epi();
-            // one lane per (n-block, j) adds the Q warp partials of its n-block
-            if (mu == 0 && lane < G) {
-                const int j = lane;
+            if (lane < 16) {   // ered[h][q][j][v] for every j slot (zeros where this half has none)
+                const int jj = lane >> 2, v = lane & 3;
+                float val = 0.f;
+#pragma unroll
+                for (int jl = 0; jl < JH; ++jl)
+                    if (jj == j0 + jl)
+                        val = v == 0 ? part[jl][0] : (v == 1 ? part[jl][1] : (v == 2 ? part[jl][2] : part[jl][3]));
+                ered[((h * 4 + q) * 4 + jj) * 4 + v] = val;
+            }
+            ebar();
+            // one thread per (n-block, walker-spin) output: sum over the n-block's quadrants and
+            // the two halves
+            if (et < G * G) {
+                const int ib = et / G, j = et % G;
                 double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                for (int q = 0; q < Q; ++q) {
-                    const double* e = ered + ((g4 + q) * 4 + j) * 4;
-                    s0 += e[0];
-                    s1 += e[1];
-                    s2 += e[2];
-                    s3 += e[3];
-                }
-                const int n = ng * G + i_blk;
+                for (int hh = 0; hh < 2; ++hh)
+                    for (int qq = ib * Q; qq < (ib + 1) * Q; ++qq) {
+                        const double* e = ered + ((hh * 4 + qq) * 4 + j) * 4;
+                        s0 += e[0];
+                        s1 += e[1];
+                        s2 += e[2];
+                        s3 += e[3];
+                    }
+                const int n = ng * G + ib;
                 const int ws = wg * G + j;
                 if (n < es.Nchol && ws < es.nws) {
                     es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
                     es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
                 }
             }
+            ebar();   // ered (aliasing colscale) is read before the next tile rewrites it
         }
     }
     tc_fence_before();
@@ -801,6 +888,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // One warp per row: scale = 2^(e-11) with ||x||_2 < 2^e, hi = rint(x/scale) (|hi| <= 2048, an
 // integer, exact in fp16), lo = fp16(x/scale - hi).  ||hi||_2 <= 2^11 + sqrt(K)/2, so by
 // Cauchy-Schwarz every partial sum of hi_A . hi_B is an integer below 2^23: exact in fp32.
+__device__ __forceinline__ void load4(const float* p, double (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+// four halves at an 8-byte aligned address
+__device__ __forceinline__ void store4h(__half* p, const __half (&h)[4]) {
+    uint2 u;
+    u.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+    u.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+    *reinterpret_cast<uint2*>(p) = u;
+}
+
 template <typename Src>
 __global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t src_stride, int64_t rows, int64_t K,
                                                          __half* hi, __half* lo, float* scale) {
@@ -808,19 +911,95 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
     const Src* x = src + r * src_stride;
+    // four consecutive values per lane when rows allow 16-byte (float) / 32-byte (double) loads
+    const bool vec = (K & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & (4 * sizeof(Src) - 1)) == 0;
     double ss = 0.0;
-    for (int64_t k = lane; k < K; k += 32) ss += (double)x[k] * (double)x[k];
+    if (vec) {
+        for (int64_t k = 4 * lane; k < K; k += 128) {
+            double v[4];
+            load4(x + k, v);
+            ss += v[0] * v[0] + v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+        }
+    } else {
+        for (int64_t k = lane; k < K; k += 32) ss += (double)x[k] * (double)x[k];
+    }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     const double nrm = sqrt(ss);
     int e = 0;
     if (nrm > 0.0) frexp(nrm, &e);        // nrm < 2^e
     const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
     if (lane == 0) scale[r] = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
-    for (int64_t k = lane; k < K; k += 32) {
-        const double y = (double)x[k] * inv;   // |y| < 2048
-        const double s1 = rint(y);
-        hi[r * K + k] = __double2half(s1);
-        lo[r * K + k] = __double2half(y - s1);
+    if (vec) {
+        for (int64_t k = 4 * lane; k < K; k += 128) {
+            double v[4];
+            load4(x + k, v);
+            __half h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double y = v[q] * inv;   // |y| < 2048
+                const double s1 = rint(y);
+                h[q] = __double2half(s1);
+                l[q] = __double2half(y - s1);
+            }
+            store4h(hi + r * K + k, h);
+            store4h(lo + r * K + k, l);
+        }
+    } else {
+        for (int64_t k = lane; k < K; k += 32) {
+            const double y = (double)x[k] * inv;
+            const double s1 = rint(y);
+            hi[r * K + k] = __double2half(s1);
+            lo[r * K + k] = __double2half(y - s1);
+        }
+    }
+}
+
+// fp32 rows: the same split in single precision (FMA/ALU pipes; the FP64 pipe is narrow).  The
+// row norm is summed in fp32 and raised by 2^-10 before the exponent is taken, so
+// ||x||_2 < 2^e still holds (rows at most 2^-10 below a power of two get the next scale up);
+// y = x / scale is exact (a power of two), rint(y) and y - rint(y) are exact in fp32.
+__global__ void __launch_bounds__(256) split_rows_f32_kernel(const float* src, int64_t src_stride, int64_t rows,
+                                                             int64_t K, __half* hi, __half* lo, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float* x = src + r * src_stride;
+    const bool vec = (K & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+    float ss = 0.f;
+    if (vec) {
+        for (int64_t k = 4 * lane; k < K; k += 128) {
+            const float4 a = *reinterpret_cast<const float4*>(x + k);
+            ss = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, ss))));
+        }
+    } else {
+        for (int64_t k = lane; k < K; k += 32) ss = fmaf(x[k], x[k], ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const float nrm = sqrtf(ss) * (1.0f + 0x1p-10f);
+    int e = 0;
+    if (nrm > 0.f) frexpf(nrm, &e);
+    const float inv = nrm > 0.f ? ldexpf(1.0f, 11 - e) : 0.f;
+    if (lane == 0) scale[r] = nrm > 0.f ? ldexpf(1.0f, e - 11) : 1.0f;
+    if (vec) {
+        for (int64_t k = 4 * lane; k < K; k += 128) {
+            const float4 a = *reinterpret_cast<const float4*>(x + k);
+            const float v[4] = {a.x, a.y, a.z, a.w};
+            __half h[4], l[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float y = v[q] * inv, s1 = rintf(y);
+                h[q] = __float2half_rn(s1);
+                l[q] = __float2half_rn(y - s1);
+            }
+            store4h(hi + r * K + k, h);
+            store4h(lo + r * K + k, l);
+        }
+    } else {
+        for (int64_t k = lane; k < K; k += 32) {
+            const float y = x[k] * inv, s1 = rintf(y);
+            hi[r * K + k] = __float2half_rn(s1);
+            lo[r * K + k] = __float2half_rn(y - s1);
+        }
     }
 }
 
@@ -845,17 +1024,19 @@ EncodeTiledFn encode_fn() {
 
 // 2-D or 3-D map over [batch][rows][K] bf16 with box {64, box_rows, 1} and 128-byte swizzle.
 int make_map(CUtensorMap* m, const bf16* base, int64_t K, int64_t rows, int64_t batch, int64_t row_stride,
-             int64_t batch_stride, int box_rows, bool three_d, bool fp16 = false, bool sw64 = false) {
+             int64_t batch_stride, int box_rows, bool three_d, bool fp16 = false, int swizzle = 128) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
     if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_stride * 2) % 16 || (batch_stride * 2) % 16)
         return fail(AFQMC_ERR_SHAPE, "tensor map: base/stride not 16-byte aligned");
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)std::max<int64_t>(batch, 1)};
     cuuint64_t strides[2] = {(cuuint64_t)(row_stride * 2), (cuuint64_t)(std::max<int64_t>(batch_stride, row_stride) * 2)};
-    cuuint32_t box[3] = {(cuuint32_t)(sw64 ? kEBK : kBK), (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(swizzle / 2), (cuuint32_t)box_rows, 1};   // one swizzle row of 16-bit values
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, three_d ? 3 : 2, const_cast<bf16*>(base), dims, strides,
-                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                  : (swizzle == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B),
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(AFQMC_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return AFQMC_OK;
@@ -867,7 +1048,7 @@ size_t gemm_smem() {
 }
 
 size_t energy_smem() {
-    return 1024 + (size_t)kEStages * kEStageBytes + (size_t)kETileFloats * 4 + 256 * 4 + 64 * 8 + sizeof(SharedCtl);
+    return 1024 + (size_t)kEStageRing + (size_t)kETileFloats * 4 + 256 * 4 + sizeof(SharedCtl);
 }
 
 int g_num_sms = 0;
@@ -885,14 +1066,14 @@ int launch_gemm(const CUtensorMap* m, const TileShape& sh, const EpiParams& epi,
     return AFQMC_OK;
 }
 
-template <int Np>
+template <int Np, int BK>
 int launch_energy(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
     const size_t sm = energy_smem();
-    cudaFuncSetAttribute(tc_energy_kernel<Np>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(tc_energy_kernel<Np, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
     const int grid = (int)std::min<int64_t>(es.tiles, cap);
     count_launch();
-    tc_energy_kernel<Np><<<grid, kGemmThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
+    tc_energy_kernel<Np, BK><<<grid, kEThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy launch: ") + cudaGetErrorString(e));
     return AFQMC_OK;
@@ -949,11 +1130,13 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
     if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
+    const int BK = launch_policy().energy_bk == 32 ? 32 : kEBKDefault;
+    const int swz = 2 * BK;   // bytes per swizzled row of the K chunk
     CUtensorMap m[4];
-    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, true));
-    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, true));
-    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, true));
-    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, true));
+    AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, swz));
+    AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, swz));
+    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, swz));
+    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, swz));
     EnergyShape es;
     es.Np = Np;
     es.Q = Np / 32;
@@ -964,16 +1147,23 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     es.ws_groups = (nws + es.G - 1) / es.G;
     es.ws_super = std::min(es.ws_groups, 128);
     es.tiles = (int64_t)es.n_groups * es.ws_groups;
-    es.nk = M / kEBK;
+    es.nk = M / BK;
     es.lolo = terms == 4 ? 1 : 0;
     es.a_scale = Lt.scale;
     es.b_scale = ThetaT.scale;
     es.t_out = t_out;
     es.X_out = X_out;
+    if (BK == 32) {
+        switch (Np) {
+            case 32: return launch_energy<32, 32>(m, es, flags, st);
+            case 64: return launch_energy<64, 32>(m, es, flags, st);
+            default: return launch_energy<128, 32>(m, es, flags, st);
+        }
+    }
     switch (Np) {
-        case 32: return launch_energy<32>(m, es, flags, st);
-        case 64: return launch_energy<64>(m, es, flags, st);
-        default: return launch_energy<128>(m, es, flags, st);
+        case 32: return launch_energy<32, 16>(m, es, flags, st);
+        case 64: return launch_energy<64, 16>(m, es, flags, st);
+        default: return launch_energy<128, 16>(m, es, flags, st);
     }
 }
 
@@ -989,7 +1179,7 @@ void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, b
                 cudaStream_t st) {
     if (rows <= 0) return;
     count_launch();
-    split_rows_kernel<float><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+    split_rows_f32_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
         src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale);
 }
 

@@ -247,6 +247,13 @@ __global__ void __launch_bounds__(kT) sinv_doubled_kernel(const cplx* Si, int WS
         hi[row1 * K2 + N + j] = Hr;  lo[row1 * K2 + N + j] = Lr;    // Re
     }
 }
+// four halves at an 8-byte aligned address
+__device__ __forceinline__ void store4h(__half* p, const __half (&h)[4]) {
+    uint2 u;
+    u.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
+    u.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
+    *reinterpret_cast<uint2*>(p) = u;
+}
 // HS coefficients c [W][Nchol] complex -> planar rows [W][2][Nchol]
 __global__ void coef_planar_kernel(const cplx* c, int64_t W, int nch, double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,28 +275,41 @@ __global__ void __launch_bounds__(kT) split_doubled_kernel(const float* P, int64
     const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;
     const float* pr = P + row0 * M;
     const float* pi = P + row1 * M;
-    double ss = 0.0;
-    for (int k = lane; k < M; k += 32) {
-        const double a = pr[k], b = pi[k];
-        ss += a * a + b * b;
+    // four consecutive orbitals per lane (M is a multiple of 64: 16-byte loads, 8-byte stores);
+    // single precision throughout, the norm raised by 2^-10 so that ||x||_2 < 2^e is guaranteed
+    float ss = 0.f;
+    for (int k = 4 * lane; k < M; k += 128) {
+        const float4 a = *reinterpret_cast<const float4*>(pr + k), b = *reinterpret_cast<const float4*>(pi + k);
+        ss = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, ss))));
+        ss = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, ss))));
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const double nrm = sqrt(ss);
+    const float nrm = sqrtf(ss) * (1.0f + 0x1p-10f);
     int e = 0;
-    if (nrm > 0.0) frexp(nrm, &e);
-    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
-    const float sc = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    if (nrm > 0.f) frexpf(nrm, &e);
+    const float inv = nrm > 0.f ? ldexpf(1.0f, 11 - e) : 0.f;
+    const float sc = nrm > 0.f ? ldexpf(1.0f, e - 11) : 1.0f;
     if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
     const int64_t K2 = 2LL * M;
-    for (int k = lane; k < M; k += 32) {
-        const double yr = pr[k] * inv, yi = pi[k] * inv;
-        const double hr = rint(yr), hI = rint(yi);
-        const __half Hr = __double2half(hr), Lr = __double2half(yr - hr);
-        const __half Hi = __double2half(hI), Li = __double2half(yi - hI);
-        hi[row0 * K2 + k] = Hr;                       lo[row0 * K2 + k] = Lr;                       // Re
-        hi[row0 * K2 + M + k] = __double2half(-hI);   lo[row0 * K2 + M + k] = __double2half(hI - yi); // -Im
-        hi[row1 * K2 + k] = Hi;                       lo[row1 * K2 + k] = Li;                       // Im
-        hi[row1 * K2 + M + k] = Hr;                   lo[row1 * K2 + M + k] = Lr;                   // Re
+    for (int k = 4 * lane; k < M; k += 128) {
+        const float4 a = *reinterpret_cast<const float4*>(pr + k), b = *reinterpret_cast<const float4*>(pi + k);
+        const float re[4] = {a.x, a.y, a.z, a.w}, im[4] = {b.x, b.y, b.z, b.w};
+        __half Hr[4], Lr[4], Hi[4], Li[4], nHi[4], nLi[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float yr = re[q] * inv, yi = im[q] * inv;
+            const float hr = rintf(yr), hI = rintf(yi);
+            Hr[q] = __float2half_rn(hr);
+            Lr[q] = __float2half_rn(yr - hr);
+            Hi[q] = __float2half_rn(hI);
+            Li[q] = __float2half_rn(yi - hI);
+            nHi[q] = __float2half_rn(-hI);
+            nLi[q] = __float2half_rn(hI - yi);
+        }
+        store4h(hi + row0 * K2 + k, Hr);      store4h(lo + row0 * K2 + k, Lr);       // Re
+        store4h(hi + row0 * K2 + M + k, nHi); store4h(lo + row0 * K2 + M + k, nLi);  // -Im
+        store4h(hi + row1 * K2 + k, Hi);      store4h(lo + row1 * K2 + k, Li);       // Im
+        store4h(hi + row1 * K2 + M + k, Hr);  store4h(lo + row1 * K2 + M + k, Lr);   // Re
     }
 }
 __global__ void fb_combine_kernel(const float* tFB, int64_t WS, int nch, cplx* t) {
@@ -367,67 +387,208 @@ __global__ void commit_accepted_kernel(const int* accept, int W, int64_t per, co
     if (i >= (int64_t)W * per) return;
     if (accept[i / per]) cur64[i] = new64[i];
 }
-// Classical Gram-Schmidt (twice) on the N columns of one walker-spin, stored as planar
-// rows of PhiT: column j = (re row j, im row j), length M.  diag R > 0.
-__global__ void __launch_bounds__(kT) qr_planar_kernel(double* PhiT, int M, int N, const cplx* weight) {
-    extern __shared__ double qs[];
-    double* vr = qs;       // M
-    double* vi = qs + M;   // M
-    double* rr = vi + M;   // N
-    double* ri = rr + N;   // N
-    __shared__ double red[kT];
-    const int ws = blockIdx.x, w = ws / 2;
-    if (weight[w].re == 0.0 && weight[w].im == 0.0) return;
-    double* Qr = PhiT + (int64_t)ws * 2 * N * M;
-    double* Qi = Qr + (int64_t)N * M;
-    const int t = threadIdx.x;
-    for (int j = 0; j < N; ++j) {
-        for (int k = t; k < M; k += kT) { vr[k] = Qr[(int64_t)j * M + k]; vi[k] = Qi[(int64_t)j * M + k]; }
-        __syncthreads();
-        for (int pass = 0; pass < 2; ++pass) {
-            // r_i = <q_i, v> for i < j: one warp per i, lanes over k
-            const int warp = t >> 5, lane = t & 31;
-            for (int i = warp; i < j; i += kT / 32) {
-                double ar = 0.0, ai = 0.0;
-                for (int k = lane; k < M; k += 32) {
-                    const double qr = Qr[(int64_t)i * M + k], qi = Qi[(int64_t)i * M + k];
-                    ar += qr * vr[k] + qi * vi[k];   // conj(q) v
-                    ai += qr * vi[k] - qi * vr[k];
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    ar += __shfl_xor_sync(0xffffffffu, ar, o);
-                    ai += __shfl_xor_sync(0xffffffffu, ai, o);
-                }
-                if (lane == 0) { rr[i] = ar; ri[i] = ai; }
-            }
-            __syncthreads();
-            for (int k = t; k < M; k += kT) {
-                double ar = vr[k], ai = vi[k];
-                for (int i = 0; i < j; ++i) {
-                    const double qr = Qr[(int64_t)i * M + k], qi = Qi[(int64_t)i * M + k];
-                    ar -= qr * rr[i] - qi * ri[i];
-                    ai -= qr * ri[i] + qi * rr[i];
-                }
-                vr[k] = ar;
-                vi[k] = ai;
-            }
-            __syncthreads();
+// ------------------------------------------------------------- Cholesky QR (FP64)
+// Phi = Q R with diag R > 0 in three FP64 kernels, as Q = Phi R^-1 with R^H R = Phi^H Phi:
+// the Gram matrix (a batched GEMM over the M orbitals), its Cholesky factor and the factor's
+// inverse (on chip), and the triangular product.  Walkers are re-orthonormalised every few
+// steps, so Phi stays well conditioned and one Cholesky pass leaves ||Q^H Q - I|| ~ cond(Phi)^2
+// times the FP64 rounding -- the same Q as Gram-Schmidt or Householder, with about half the
+// flops of Gram-Schmidt twice, all in GEMM-shaped loops.
+constexpr int kQT = 64;    // output tile (rows and columns)
+constexpr int kQK = 16;    // reduction chunk
+
+// G[ws] = Phi^H Phi: G[i][j] = sum_k conj(Phi[k][i]) Phi[k][j]; Phi's column j is the planar
+// row pair j of PhiT[ws].  Tiles with ti <= tj are computed and mirrored (G is Hermitian).
+__global__ void __launch_bounds__(kT) gram_planar_kernel(const double* PhiT, int M, int N, const cplx* weight,
+                                                         cplx* G) {
+    const int ti = blockIdx.x, tj = blockIdx.y, ws = blockIdx.z;
+    if (ti > tj) return;
+    if (weight[ws / 2].re == 0.0 && weight[ws / 2].im == 0.0) return;
+    __shared__ double xr[kQK][kQT + 1], xi[kQK][kQT + 1], yr[kQK][kQT + 1], yi[kQK][kQT + 1];
+    const double* Pr = PhiT + (int64_t)ws * 2 * N * M;
+    const double* Pi = Pr + (int64_t)N * M;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double ar[4][4] = {}, ai[4][4] = {};
+    for (int k0 = 0; k0 < M; k0 += kQK) {
+        for (int e = threadIdx.x; e < kQK * kQT; e += kT) {
+            const int r = e / kQK, k = e % kQK;   // consecutive threads along k: coalesced rows
+            const int i = ti * kQT + r, j = tj * kQT + r, kk = k0 + k;
+            const bool ok = kk < M;
+            xr[k][r] = (ok && i < N) ? Pr[(int64_t)i * M + kk] : 0.0;
+            xi[k][r] = (ok && i < N) ? Pi[(int64_t)i * M + kk] : 0.0;
+            yr[k][r] = (ok && j < N) ? Pr[(int64_t)j * M + kk] : 0.0;
+            yi[k][r] = (ok && j < N) ? Pi[(int64_t)j * M + kk] : 0.0;
         }
-        double p = 0.0;
-        for (int k = t; k < M; k += kT) p += vr[k] * vr[k] + vi[k] * vi[k];
-        red[t] = p;
         __syncthreads();
-        for (int o = kT / 2; o > 0; o >>= 1) {
-            if (t < o) red[t] += red[t + o];
-            __syncthreads();
-        }
-        const double inv = 1.0 / sqrt(red[0]);
-        for (int k = t; k < M; k += kT) {
-            Qr[(int64_t)j * M + k] = vr[k] * inv;
-            Qi[(int64_t)j * M + k] = vi[k] * inv;
+#pragma unroll 4
+        for (int k = 0; k < kQK; ++k) {
+            double a_r[4], a_i[4], b_r[4], b_i[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a_r[q] = xr[k][ty + 16 * q];
+                a_i[q] = xi[k][ty + 16 * q];
+                b_r[q] = yr[k][tx + 16 * q];
+                b_i[q] = yi[k][tx + 16 * q];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {   // conj(x) y
+                    ar[a][b] = fma(a_r[a], b_r[b], fma(a_i[a], b_i[b], ar[a][b]));
+                    ai[a][b] = fma(a_r[a], b_i[b], fma(-a_i[a], b_r[b], ai[a][b]));
+                }
         }
         __syncthreads();
     }
+    cplx* Gw = G + (int64_t)ws * N * N;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = ti * kQT + ty + 16 * a, j = tj * kQT + tx + 16 * b;
+            if (i < N && j < N) {
+                Gw[(int64_t)i * N + j] = cplx{ar[a][b], ai[a][b]};
+                if (ti != tj) Gw[(int64_t)j * N + i] = cplx{ar[a][b], -ai[a][b]};
+            }
+        }
+}
+
+// In place on G[ws]: upper Cholesky factor R (G = R^H R, real positive diagonal), then its
+// inverse, left in the upper triangle (the strict lower triangle is zeroed).  The upper
+// triangle is staged in shared memory, packed row by row.  A non-positive or non-finite
+// pivot sets FLAG_NONFINITE and leaves the identity (the walker keeps its orbitals).
+__device__ __forceinline__ int upk(int i, int j, int N) { return i * N - (i * (i - 1)) / 2 + (j - i); }
+
+__global__ void __launch_bounds__(kT) chol_inv_kernel(cplx* G, int N, const cplx* weight, unsigned* flags) {
+    extern __shared__ __align__(16) unsigned char qsm[];
+    cplx* U = reinterpret_cast<cplx*>(qsm);        // packed upper triangle, N (N+1) / 2
+    __shared__ int s_bad;
+    const int ws = blockIdx.x, t = threadIdx.x;
+    cplx* Gw = G + (int64_t)ws * N * N;
+    const bool dead = weight[ws / 2].re == 0.0 && weight[ws / 2].im == 0.0;
+    const int NP = N * (N + 1) / 2;
+    if (t == 0) s_bad = 0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + t; j < N; j += kT) U[upk(i, j, N)] = dead ? cplx{i == j ? 1.0 : 0.0, 0.0} : Gw[(int64_t)i * N + j];
+    __syncthreads();
+    if (!dead) {
+        // right-looking Cholesky: row k of R, then the trailing upper triangle
+        for (int k = 0; k < N; ++k) {
+            const double d2 = U[upk(k, k, N)].re;
+            if (!(d2 > 0.0) || !isfinite(d2)) {
+                if (t == 0) s_bad = 1;
+                break;
+            }
+            const double d = sqrt(d2), id = 1.0 / d;
+            __syncthreads();
+            for (int j = k + t; j < N; j += kT) {
+                const cplx v = U[upk(k, j, N)];
+                U[upk(k, j, N)] = j == k ? cplx{d, 0.0} : id * v;
+            }
+            __syncthreads();
+            const int nr = N - k - 1;
+            for (int e = t; e < nr * nr; e += kT) {   // trailing upper triangle k < i <= j
+                const int ii = k + 1 + e / nr, jj = k + 1 + e % nr;
+                if (jj < ii) continue;
+                const cplx rki = U[upk(k, ii, N)], rkj = U[upk(k, jj, N)];
+                cfma(U[upk(ii, jj, N)], cplx{0.0, 0.0} - conjg(rki), rkj);
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!s_bad) {
+            // inverse of the upper triangular R, in place, column by column:
+            // X[j][j] = 1 / R[j][j]; X[i][j] = -(sum_{p=i..j-1} X[i][p] R[p][j]) / R[j][j]
+            // (N <= kT: thread i owns row i of column j)
+            for (int j = 0; j < N; ++j) {
+                const double rjj = U[upk(j, j, N)].re;
+                const double ir = 1.0 / rjj;
+                // row i < j reads X[i][p] (p < j, final) and R[p][j] (column j, still R): the new
+                // column is written only after every row has read it
+                cplx val{0.0, 0.0};
+                if (t < j) {
+                    cplx acc{0.0, 0.0};
+                    for (int p = t; p < j; ++p) cfma(acc, U[upk(t, p, N)], U[upk(p, j, N)]);
+                    val = cplx{-acc.re * ir, -acc.im * ir};
+                }
+                __syncthreads();
+                if (t < j) U[upk(t, j, N)] = val;
+                if (t == 0) U[upk(j, j, N)] = cplx{ir, 0.0};
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    if (s_bad) {
+        if (t == 0) atomicOr(flags, FLAG_NONFINITE);
+        for (int e = t; e < NP; e += kT) U[e] = cplx{0.0, 0.0};
+        __syncthreads();
+        for (int i = t; i < N; i += kT) U[upk(i, i, N)] = cplx{1.0, 0.0};
+        __syncthreads();
+    }
+    for (int e = t; e < N * N; e += kT) {
+        const int i = e / N, j = e % N;
+        Gw[e] = i <= j ? U[upk(i, j, N)] : cplx{0.0, 0.0};
+    }
+}
+
+// Q^T rows: out[ws][j] = sum_{i <= j} X[i][j] * PhiT[ws] row i (complex, planar), X = R^-1
+// upper triangular.  Tile: 64 rows j x 64 orbitals k.
+__global__ void __launch_bounds__(kT) apply_rinv_kernel(const double* PhiT, const cplx* X, int M, int N,
+                                                        double* out) {
+    const int tk = blockIdx.x, tj = blockIdx.y, ws = blockIdx.z;
+    __shared__ double xr_[kQK][kQT + 1], xi_[kQK][kQT + 1], pr_[kQK][kQT + 1], pi_[kQK][kQT + 1];
+    const double* Pr = PhiT + (int64_t)ws * 2 * N * M;
+    const double* Pi = Pr + (int64_t)N * M;
+    const cplx* Xw = X + (int64_t)ws * N * N;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    double ar[4][4] = {}, ai[4][4] = {};
+    const int imax = min(N, (tj + 1) * kQT);   // rows i <= j only
+    for (int i0 = 0; i0 < imax; i0 += kQK) {
+        for (int e = threadIdx.x; e < kQK * kQT; e += kT) {
+            const int r = e % kQT, q = e / kQT;    // consecutive threads along the fast index
+            const int i = i0 + q;
+            const int j = tj * kQT + r, k = tk * kQT + r;
+            const bool iok = i < N;
+            const cplx xv = (iok && j < N) ? Xw[(int64_t)i * N + j] : cplx{0.0, 0.0};
+            xr_[q][r] = xv.re;
+            xi_[q][r] = xv.im;
+            pr_[q][r] = (iok && k < M) ? Pr[(int64_t)i * M + k] : 0.0;
+            pi_[q][r] = (iok && k < M) ? Pi[(int64_t)i * M + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int q = 0; q < kQK; ++q) {
+            double a_r[4], a_i[4], b_r[4], b_i[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a_r[u] = xr_[q][ty + 16 * u];
+                a_i[u] = xi_[q][ty + 16 * u];
+                b_r[u] = pr_[q][tx + 16 * u];
+                b_i[u] = pi_[q][tx + 16 * u];
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    ar[a][b] = fma(a_r[a], b_r[b], fma(-a_i[a], b_i[b], ar[a][b]));
+                    ai[a][b] = fma(a_r[a], b_i[b], fma(a_i[a], b_r[b], ai[a][b]));
+                }
+        }
+        __syncthreads();
+    }
+    double* Or = out + (int64_t)ws * 2 * N * M;
+    double* Oi = Or + (int64_t)N * M;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int j = tj * kQT + ty + 16 * a, k = tk * kQT + tx + 16 * b;
+            if (j < N && k < M) {
+                Or[(int64_t)j * M + k] = ar[a][b];
+                Oi[(int64_t)j * M + k] = ai[a][b];
+            }
+        }
 }
 
 SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t batch = 1, const float* scale = nullptr,
@@ -783,9 +944,22 @@ int tc_debug_terms(afqmc_walkers* wk, double* ST, double* Sinv, double* ThetaT, 
 
 int tc_qr(afqmc_walkers* wk, cudaStream_t st) {
     TcState* s = wk->tc;
-    const size_t sm = (size_t)(2 * s->M + 2 * s->N) * sizeof(double);
+    const int N = s->N, M = s->M, WS = 2 * s->W;
+    if (N > kT) return fail(AFQMC_ERR_UNSUPPORTED, "tc_qr: N above the Cholesky kernel's row limit");
+    const int nt = (N + kQT - 1) / kQT;
+    // Gram matrices into the (idle) overlap buffer S [WS][N][N]
     count_launch();
-    qr_planar_kernel<<<2 * s->W, kT, sm, st>>>(s->PhiT[s->cur], s->M, s->N, wk->weight);
+    gram_planar_kernel<<<dim3(nt, nt, WS), kT, 0, st>>>(s->PhiT[s->cur], M, N, wk->weight, s->S);
+    const size_t sm = (size_t)N * (N + 1) / 2 * sizeof(cplx);
+    cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    count_launch();
+    chol_inv_kernel<<<WS, kT, sm, st>>>(s->S, N, wk->weight, wk->flags);
+    // Q^T into the proposal buffer, then back over the current walkers (dead walkers: X = I)
+    const int nxt = s->cur ^ 1;
+    count_launch();
+    apply_rinv_kernel<<<dim3((M + kQT - 1) / kQT, nt, WS), kT, 0, st>>>(s->PhiT[s->cur], s->S, M, N, s->PhiT[nxt]);
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(s->PhiT[s->cur], s->PhiT[nxt], sizeof(double) * (size_t)WS * 2 * N * M,
+                                   cudaMemcpyDeviceToDevice, st));
     refresh_operands(s, st);
     return AFQMC_OK;
 }

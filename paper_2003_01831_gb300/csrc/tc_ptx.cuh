@@ -163,6 +163,18 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
     return d;
 }
 
+// Same for a tile written with 32-byte swizzle (rows of 16 16-bit values = 32 B, 8-row groups
+// of 256 B, 256-B aligned base).  One K = 16 MMA step covers the whole row.
+__device__ __forceinline__ uint64_t desc_sw32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);        // start address >> 4
+    d |= (uint64_t)1u << 16;                          // leading byte offset (unused here)
+    d |= (uint64_t)(256u >> 4) << 32;                 // stride byte offset: 8 rows x 32 B
+    d |= (uint64_t)1u << 46;                          // descriptor version (sm_100 family)
+    d |= (uint64_t)6u << 61;                          // 32-byte swizzle
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D f32, A/B bf16 (or f16 when fp16 = true), both
 // K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool fp16 = false) {
