@@ -1003,6 +1003,203 @@ __global__ void __launch_bounds__(256) split_rows_f32_kernel(const float* src, i
     }
 }
 
+// --------------------------------------------------------------------------- three-slice overlap
+// S = Psi^T Phi to ~1e-9 (the overlap's log-determinant sets the phaseless weights, whose
+// relative errors multiply the spread of the local energies in E_mix).  Rows are split into
+// three fp16 slices with the row scale s = 2^(e-11) of the two-slice mode:
+//   y = x / s,  h = rint(y) (|h| <= 2048),  m = rint((y - h) 2^7) (|m| <= 64),
+//   l = fp16((y - h) 2^7 - m),  x = s (h + 2^-7 (m + l)).
+// Products x_a x_b = s_a s_b [h h' + 2^-7 (h m' + m h') + 2^-7 (h l' + l h') + 2^-14 m m' + ...];
+// the four kept groups go to four TMEM accumulators.  For K <= 1024 the partial sums of h h',
+// h m' + m h' and m m' are integers below 2^24 (Cauchy-Schwarz), hence exact in fp32; the
+// l terms are 2^-7 smaller and only rounded.  The dropped 2^-14 (m l' + l m' + l l') terms are
+// ~1e-9 of |x_a||x_b|.
+constexpr double kS3 = 1.0 / 128.0;
+
+__global__ void __launch_bounds__(256) split3_rows_kernel(const double* src, int64_t rows, int64_t K, __half* h,
+                                                          __half* m, __half* l, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const double* x = src + r * K;
+    double ss = 0.0;
+    for (int64_t k = lane; k < K; k += 32) ss += x[k] * x[k];
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double nrm = sqrt(ss);
+    int e = 0;
+    if (nrm > 0.0) frexp(nrm, &e);
+    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+    if (lane == 0) scale[r] = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    for (int64_t k = lane; k < K; k += 32) {
+        const double y = x[k] * inv;
+        const double hv = rint(y);
+        const double rr = (y - hv) * 128.0;
+        const double mv = rint(rr);
+        h[r * K + k] = __double2half(hv);
+        m[r * K + k] = __double2half(mv);
+        l[r * K + k] = __double2half(rr - mv);
+    }
+}
+
+struct Ovl3Shape {
+    int N, M;         // electrons (B rows, output columns), orbitals (K)
+    int rows;         // A rows per walker-spin (2N)
+    int rt;           // row tiles per walker-spin
+    int nws;
+    int nk;
+    int64_t tiles;
+    const float* a_scale;   // [nws][rows]
+    const float* b_scale;   // [N]
+    double* out;            // [nws][rows][N]
+};
+
+constexpr int kO3Planes = 3;
+constexpr int kO3ABytes = kBM * kBK * 2;          // one plane, 128 rows x 64
+constexpr int kO3BBytes = 128 * kBK * 2;          // B tile: 128 rows (N <= 128)
+constexpr int kO3StageBytes = kO3Planes * (kO3ABytes + kO3BBytes);   // 96 KB
+constexpr int kO3Stages = 2;
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tc_overlap3_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                       const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+                       const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, Ovl3Shape sh,
+                       unsigned* flags) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(sbase + kO3Stages * kO3StageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kO3Stages; ++i) {
+            mbar_init(&ctl->full[i], 1);
+            mbar_init(&ctl->empty[i], 1);
+        }
+        mbar_init(&ctl->tfull[0], 1);
+        mbar_init(&ctl->tempty[0], 128);
+        mbar_init(&ctl->done, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&ctl->tmem_base, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        if (lane == 0) {
+            const CUtensorMap* A[3] = {&tA0, &tA1, &tA2};
+            const CUtensorMap* B[3] = {&tB0, &tB1, &tB2};
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < sh.tiles && ok; t += gridDim.x) {
+                const int ws = (int)(t / sh.rt), rt = (int)(t % sh.rt);
+                for (int kb = 0; kb < sh.nk; ++kb, ++g) {
+                    const int st = (int)(g % kO3Stages);
+                    const uint32_t ph = (uint32_t)((g / kO3Stages) & 1);
+                    if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
+                    uint8_t* sp = sbase + (size_t)st * kO3StageBytes;
+                    mbar_arrive_expect_tx(&ctl->full[st], kO3StageBytes);
+                    const int x = kb * kBK;
+                    for (int q = 0; q < 3; ++q) {
+                        tma_load_3d(sp + q * kO3ABytes, A[q], &ctl->full[st], x, rt * kBM, ws);
+                        tma_load_2d(sp + 3 * kO3ABytes + q * kO3BBytes, B[q], &ctl->full[st], x, 0);
+                    }
+                }
+            }
+            if (!ok) {
+                const int64_t first = g > kO3Stages ? g - kO3Stages : 0;
+                for (int64_t j = first; j < g; ++j)
+                    wait_drain(&ctl->full[j % kO3Stages], (uint32_t)((j / kO3Stages) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(kBM, 128, true);
+            const uint32_t d1 = ctl->tmem_base, d2 = d1 + 128, d3 = d1 + 256, d4 = d1 + 384;
+            int64_t g = 0;
+            int it = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < sh.tiles && ok; t += gridDim.x, ++it) {
+                if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
+                tc_fence_after();
+                for (int kb = 0; kb < sh.nk; ++kb, ++g) {
+                    const int st = (int)(g % kO3Stages);
+                    const uint32_t ph = (uint32_t)((g / kO3Stages) & 1);
+                    if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(sbase + (size_t)st * kO3StageBytes);
+                    const uint32_t sb = sa + 3 * kO3ABytes;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint64_t ah = desc_sw128(sa + off), am = desc_sw128(sa + kO3ABytes + off),
+                                       al = desc_sw128(sa + 2 * kO3ABytes + off);
+                        const uint64_t bh = desc_sw128(sb + off), bm = desc_sw128(sb + kO3BBytes + off),
+                                       bl = desc_sw128(sb + 2 * kO3BBytes + off);
+                        const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+                        mma_bf16(d1, ah, bh, idesc, acc);
+                        mma_bf16(d2, ah, bm, idesc, acc);
+                        mma_bf16(d2, am, bh, idesc, 1u);
+                        mma_bf16(d3, ah, bl, idesc, acc);
+                        mma_bf16(d3, al, bh, idesc, 1u);
+                        mma_bf16(d4, am, bm, idesc, acc);
+                    }
+                    mma_commit(&ctl->empty[st]);
+                }
+                if (!ok) break;
+                mma_commit(&ctl->tfull[0]);
+            }
+            mma_commit(&ctl->done);
+            wait_drain(&ctl->done, 0);
+        }
+    } else {
+        const int g4 = warp & 3;
+        const uint32_t tb = ctl->tmem_base + ((uint32_t)(g4 * 32) << 16);
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < sh.tiles; t += gridDim.x, ++it) {
+            if (!warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort)) break;
+            tc_fence_after();
+            const int ws = (int)(t / sh.rt), rt = (int)(t % sh.rt);
+            const int r = rt * kBM + g4 * 32 + lane;
+            const double sa = r < sh.rows ? (double)sh.a_scale[(int64_t)ws * sh.rows + r] : 0.0;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                uint32_t a1[32], a2[32];
+                tmem_ld32_nw(tb + c * 32, a1);
+                tmem_ld32_nw(tb + 128 + c * 32, a2);
+                tmem_ld_wait();
+                double v[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = (double)__uint_as_float(a1[q]) + kS3 * (double)__uint_as_float(a2[q]);
+                tmem_ld32_nw(tb + 256 + c * 32, a1);
+                tmem_ld32_nw(tb + 384 + c * 32, a2);
+                tmem_ld_wait();
+                if (r < sh.rows) {
+                    double* o = sh.out + ((int64_t)ws * sh.rows + r) * sh.N;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int col = c * 32 + q;
+                        if (col < sh.N)
+                            o[col] = (v[q] + kS3 * (double)__uint_as_float(a1[q]) +
+                                      kS3 * kS3 * (double)__uint_as_float(a2[q])) *
+                                     sa * (double)sh.b_scale[col];
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&ctl->tempty[0]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(ctl->tmem_base, 512);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
 // --------------------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1165,6 +1362,46 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
         case 64: return launch_energy<64, 16>(m, es, flags, st);
         default: return launch_energy<128, 16>(m, es, flags, st);
     }
+}
+
+void split3_rows(const double* src, int64_t rows, int64_t K, bf16* h, bf16* m, bf16* l, float* scale,
+                 cudaStream_t st) {
+    if (rows <= 0) return;
+    count_launch();
+    split3_rows_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(src, rows, K, reinterpret_cast<__half*>(h),
+                                                                   reinterpret_cast<__half*>(m),
+                                                                   reinterpret_cast<__half*>(l), scale);
+}
+
+int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, const bf16* const* b,
+                const float* b_scale, int N, int M, double* out, unsigned* flags, cudaStream_t st) {
+    if (N > 128 || M % 8 || M > 1024 || rows <= 0 || nws <= 0)
+        return fail(AFQMC_ERR_UNSUPPORTED, "tc_overlap3: needs N <= 128, M % 8 == 0, M <= 1024");
+    CUtensorMap m[6];
+    for (int q = 0; q < 3; ++q) {
+        AFQMC_TRY(make_map(&m[q], a[q], M, rows, nws, M, (int64_t)rows * M, kBM, true, true));
+        AFQMC_TRY(make_map(&m[3 + q], b[q], M, N, 1, M, 0, 128, false, true));
+    }
+    Ovl3Shape sh;
+    sh.N = N;
+    sh.M = M;
+    sh.rows = rows;
+    sh.rt = (rows + kBM - 1) / kBM;
+    sh.nws = nws;
+    sh.nk = (M + kBK - 1) / kBK;
+    sh.tiles = (int64_t)nws * sh.rt;
+    sh.a_scale = a_scale;
+    sh.b_scale = b_scale;
+    sh.out = out;
+    const size_t smem = 1024 + (size_t)kO3Stages * kO3StageBytes + sizeof(SharedCtl);
+    cudaFuncSetAttribute(tc_overlap3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
+    const int grid = (int)std::min<int64_t>(sh.tiles, cap);
+    count_launch();
+    tc_overlap3_kernel<<<grid, kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], sh, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_overlap3 launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
 }
 
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,

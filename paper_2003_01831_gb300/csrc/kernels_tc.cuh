@@ -78,6 +78,14 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
               cplx* X_out, int terms, unsigned* flags, cudaStream_t st);
 
+// Three-slice row split (see kernels_tc.cu): h, m, l fp16 planes [rows][K] and row scales.
+void split3_rows(const double* src, int64_t rows, int64_t K, bf16* h, bf16* m, bf16* l, float* scale,
+                 cudaStream_t st);
+// out[ws][r][c] = sum_k A[ws][r][k] B[c][k] (FP64 out, ~1e-9 relative) from three-slice operands:
+// a[3] planes [nws][rows][M] with scales [nws][rows], b[3] planes [N][M] with scales [N].
+int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, const bf16* const* b,
+                const float* b_scale, int N, int M, double* out, unsigned* flags, cudaStream_t st);
+
 // Row-scaled (fp16) split of `rows` rows of length K (row r at src + r*src_stride) into
 // hi/lo [rows][K] (row stride K) and scale[rows].  FP64 or FP32 source.
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,

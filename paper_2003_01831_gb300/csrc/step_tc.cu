@@ -39,7 +39,8 @@ struct TcState {
     // static operands
     bf16 *Lt_h = nullptr, *Lt_l = nullptr;
     float* Lt_s = nullptr;
-    bf16 *Ltp_h = nullptr, *Ltp_l = nullptr;
+    bf16 *Ltp_h = nullptr, *Ltp_l = nullptr;      // Ltilde rows n over all N*M entries, row-scaled
+    float* Ltp_s = nullptr;
     bf16 *LT_h = nullptr, *LT_l = nullptr;
     float* LT_s = nullptr;
     bf16 *Bh_h = nullptr, *Bh_l = nullptr;
@@ -49,14 +50,20 @@ struct TcState {
     double* PsiT_f = nullptr;
     // walkers
     double* PhiT[2] = {nullptr, nullptr};
-    bf16 *PhiT_h[2] = {nullptr, nullptr}, *PhiT_l[2] = {nullptr, nullptr};
+    bf16 *PhiT_h[2] = {nullptr, nullptr}, *PhiT_l[2] = {nullptr, nullptr};   // current walkers only ([cur])
     float* PhiT_s[2] = {nullptr, nullptr};
+    bf16 *PhiT3[3] = {nullptr, nullptr, nullptr};   // three-slice split of the walkers being overlapped
+    float* PhiT3_s = nullptr;
+    bf16 *PsiT3[3] = {nullptr, nullptr, nullptr};   // three-slice split of the trial (static)
+    float* PsiT3_s = nullptr;
+    double* ST64 = nullptr;                         // [WS][2N][N] overlap (transposed, planar), FP64
     bf16 *Phi_h = nullptr, *Phi_l = nullptr;
     float* Phi_s = nullptr;
     // Green's function and energy
-    float* ST = nullptr;
-    cplx* S = nullptr;
-    cplx* ld = nullptr;
+    cplx* S = nullptr;      // scratch: proposals' overlap inverse, Gram matrices of the QR
+    cplx* ld = nullptr;     // scratch: proposals' per-spin log-determinants
+    cplx* Si = nullptr;     // [W][2][N][N] S^-1 of the current walkers
+    cplx* ldc = nullptr;    // [W][2] their per-spin log-determinants
     bf16 *SD_h = nullptr, *SD_l = nullptr;
     float* SD_s = nullptr;
     float* ThT_f = nullptr;
@@ -101,13 +108,16 @@ int talloc(TcState* s, T** p, size_t count) {
 }
 
 // ----------------------------------------------------------------------------- pack kernels
-__global__ void split_f64_kernel(const double* src, bf16* hi, bf16* lo, int64_t n) {
+// accepted walkers take their proposal's overlap inverse and log-determinants (both spins)
+__global__ void commit_inverse_kernel(const int* accept, int W, int N, const cplx* Snew, const cplx* ldnew, cplx* Si,
+                                      cplx* ldc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) tc::split_bf16(src[i], hi[i], lo[i]);
-}
-__global__ void split_f32_kernel(const float* src, bf16* hi, bf16* lo, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) tc::split_bf16(src[i], hi[i], lo[i]);
+    const int64_t per = 2LL * N * N;
+    if (i >= (int64_t)W * per) return;
+    const int64_t w = i / per;
+    if (!accept[w]) return;
+    Si[i] = Snew[i];
+    if (i % ((int64_t)N * N) == 0) ldc[i / ((int64_t)N * N)] = ldnew[i / ((int64_t)N * N)];
 }
 // Psi [M][N] complex (real part) -> PsiT [N][M] FP64
 __global__ void psiT_kernel(const cplx* Psi, int M, int N, double* out) {
@@ -200,15 +210,15 @@ __global__ void __launch_bounds__(kT) phi_untranspose_split_kernel(const double*
         }
     }
 }
-// ST [WS][2N][N] (rows (c, b), cols a) -> S [WS][N][N] complex, S[a][b]
-__global__ void st_to_S_kernel(const float* ST, int WS, int N, cplx* S) {
+// ST64 [WS][2N][N] (rows (c, b), cols a) -> S [WS][N][N] complex, S[a][b]
+__global__ void st64_to_S_kernel(const double* ST, int WS, int N, cplx* S) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)WS * N * N) return;
     const int64_t ws = i / ((int64_t)N * N);
     const int64_t e = i % ((int64_t)N * N);
     const int a = (int)(e / N), b = (int)(e % N);
-    const float* base = ST + ws * 2 * N * N;
-    S[i] = cplx{(double)base[(int64_t)b * N + a], (double)base[(int64_t)N * N + (int64_t)b * N + a]};
+    const double* base = ST + ws * 2 * N * N;
+    S[i] = cplx{base[(int64_t)b * N + a], base[(int64_t)N * N + (int64_t)b * N + a]};
 }
 // S^-1 [WS][N][N] -> SD [WS][2N][2N] row-scaled fp16 pair: row (0,b) = [Re Si[j][b] | -Im Si[j][b]],
 // row (1,b) = [Im | Re]; both rows of b share the scale (2-norm of column b of S^-1).
@@ -625,24 +635,26 @@ void refresh_operands(TcState* s, cudaStream_t st) {
     untranspose_walkers(s, st);
 }
 
-// S = Psi^T Phi for the walkers in buffer b -> s->S; logdet into s->ld; optional inverse
-int overlap_logdet(afqmc_walkers* wk, int b, bool inverse, cudaStream_t st) {
+// S = Psi^T Phi for the walkers in buffer b -> Sout (inverted in place when `inverse`), per-spin
+// log-determinants -> ldout
+int overlap_logdet(afqmc_walkers* wk, int b, bool inverse, cplx* Sout, cplx* ldout, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, WS = 2 * s->W;
-    EpiParams e;
-    e.kind = EPI_F32;
-    e.rows_valid = 2 * N;
-    e.cols_valid = N;
-    e.ld = N;
-    e.ob = 2LL * N * N;
-    e.out_f32 = s->ST;
-    AFQMC_TRY(tc_gemm(smat(s->PhiT_h[b], s->PhiT_l[b], M, 2 * N, WS, s->PhiT_s[b]), BatchMap{1, WS},
-                      smat(s->PsiT_h, s->PsiT_l, M, N, 1, s->PsiT_s), BatchMap{1, 1}, 2 * N, N, M, WS, e, 128, true,
-                      wk->flags, st));
+    // three-slice operands: the log-determinant sets the weights, so S is formed to ~1e-9
+    split3_rows(s->PhiT[b], (int64_t)WS * 2 * N, M, s->PhiT3[0], s->PhiT3[1], s->PhiT3[2], s->PhiT3_s, st);
+    const bf16* a3[3] = {s->PhiT3[0], s->PhiT3[1], s->PhiT3[2]};
+    const bf16* b3[3] = {s->PsiT3[0], s->PsiT3[1], s->PsiT3[2]};
+    AFQMC_TRY(tc_overlap3(a3, s->PhiT3_s, WS, 2 * N, b3, s->PsiT3_s, N, M, s->ST64, wk->flags, st));
     count_launch();
-    st_to_S_kernel<<<nb((int64_t)WS * N * N), kT, 0, st>>>(s->ST, WS, N, s->S);
-    batched_inverse_logdet(s->S, (int64_t)N * N, N, WS, s->ld, inverse, wk->flags, st);
+    st64_to_S_kernel<<<nb((int64_t)WS * N * N), kT, 0, st>>>(s->ST64, WS, N, Sout);
+    batched_inverse_logdet(Sout, (int64_t)N * N, N, WS, ldout, inverse, wk->flags, st);
     return AFQMC_OK;
+}
+
+// S^-1 and log det of the current walkers, recomputed (after initialisation, QR, set_walkers)
+int refresh_inverse(afqmc_walkers* wk, cudaStream_t st) {
+    TcState* s = wk->tc;
+    return overlap_logdet(wk, s->cur, true, s->Si, s->ldc, st);
 }
 
 }  // namespace
@@ -661,6 +673,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->Lt_s, (int64_t)nch * N));
     AFQMC_TRY(talloc(s, &s->Ltp_h, nch * NM));
     AFQMC_TRY(talloc(s, &s->Ltp_l, nch * NM));
+    AFQMC_TRY(talloc(s, &s->Ltp_s, nch));
     AFQMC_TRY(talloc(s, &s->LT_h, MM * nch));
     AFQMC_TRY(talloc(s, &s->LT_l, MM * nch));
     AFQMC_TRY(talloc(s, &s->LT_s, MM));
@@ -672,12 +685,17 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->PsiT_s, N));
     AFQMC_TRY(talloc(s, &s->PsiT_f, NM));
     const int64_t wall = (int64_t)W * 4 * NM;  // PhiT elements
-    for (int b = 0; b < 2; ++b) {
-        AFQMC_TRY(talloc(s, &s->PhiT[b], wall));
-        AFQMC_TRY(talloc(s, &s->PhiT_h[b], wall));
-        AFQMC_TRY(talloc(s, &s->PhiT_l[b], wall));
-        AFQMC_TRY(talloc(s, &s->PhiT_s[b], (int64_t)W * 4 * N));
+    for (int b = 0; b < 2; ++b) AFQMC_TRY(talloc(s, &s->PhiT[b], wall));
+    AFQMC_TRY(talloc(s, &s->PhiT_h[0], wall));
+    AFQMC_TRY(talloc(s, &s->PhiT_l[0], wall));
+    AFQMC_TRY(talloc(s, &s->PhiT_s[0], (int64_t)W * 4 * N));
+    for (int q = 0; q < 3; ++q) {
+        AFQMC_TRY(talloc(s, &s->PhiT3[q], wall));
+        AFQMC_TRY(talloc(s, &s->PsiT3[q], NM));
     }
+    AFQMC_TRY(talloc(s, &s->PhiT3_s, (int64_t)W * 4 * N));
+    AFQMC_TRY(talloc(s, &s->PsiT3_s, N));
+    AFQMC_TRY(talloc(s, &s->ST64, (int64_t)W * 2 * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->PD_h, (int64_t)W * 2 * 2 * N * 2 * M));
     AFQMC_TRY(talloc(s, &s->PD_l, (int64_t)W * 2 * 2 * N * 2 * M));
     AFQMC_TRY(talloc(s, &s->PD_s, (int64_t)W * 4 * N));
@@ -685,9 +703,10 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->Phi_h, wall));
     AFQMC_TRY(talloc(s, &s->Phi_l, wall));
     AFQMC_TRY(talloc(s, &s->Phi_s, (int64_t)W * 2 * M));
-    AFQMC_TRY(talloc(s, &s->ST, (int64_t)W * 2 * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->S, (int64_t)W * 2 * N * N));
     AFQMC_TRY(talloc(s, &s->ld, (int64_t)W * 2));
+    AFQMC_TRY(talloc(s, &s->Si, (int64_t)W * 2 * N * N));
+    AFQMC_TRY(talloc(s, &s->ldc, (int64_t)W * 2));
     AFQMC_TRY(talloc(s, &s->SD_h, (int64_t)W * 2 * 4 * N * N));
     AFQMC_TRY(talloc(s, &s->SD_l, (int64_t)W * 2 * 4 * N * N));
     AFQMC_TRY(talloc(s, &s->SD_s, (int64_t)W * 2 * 2 * N));
@@ -714,8 +733,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     // static operands
     const double* Ltr = static_cast<const double*>(wk->f.Lt[0]);  // real [Nchol][N][M]
     split_rows(Ltr, M, (int64_t)nch * N, M, s->Lt_h, s->Lt_l, s->Lt_s, st);
-    count_launch();
-    split_f64_kernel<<<nb(nch * NM), kT, 0, st>>>(Ltr, s->Ltp_h, s->Ltp_l, nch * NM);
+    split_rows(Ltr, NM, nch, NM, s->Ltp_h, s->Ltp_l, s->Ltp_s, st);   // force-bias-only operand
     {   // L^T [M*M][Nchol] in FP64 (temporary), then its row-scaled pair
         double* LTd = nullptr;
         if (cudaMalloc(&LTd, sizeof(double) * (size_t)MM * nch) != cudaSuccess) {
@@ -733,6 +751,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     count_launch();
     psiT_kernel<<<nb(NM), kT, 0, st>>>(wk->f.Psi[0], M, N, s->PsiT_f);
     split_rows(s->PsiT_f, M, N, M, s->PsiT_h, s->PsiT_l, s->PsiT_s, st);
+    split3_rows(s->PsiT_f, N, M, s->PsiT3[0], s->PsiT3[1], s->PsiT3[2], s->PsiT3_s, st);
     return tc_sync_walkers_from_fp64(wk, st);
 }
 
@@ -752,7 +771,7 @@ int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st) {
         canon_to_phiT_kernel<<<nb(n), kT, 0, st>>>(wk->f.Phi[sp], sp, s->W, s->M, s->N, s->PhiT[s->cur]);
     }
     refresh_operands(s, st);
-    return AFQMC_OK;
+    return refresh_inverse(wk, st);
 }
 
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
@@ -769,12 +788,13 @@ int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
 int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, W = s->W, WS = 2 * W, nch = s->Nchol;
-    AFQMC_TRY(overlap_logdet(wk, s->cur, true, st));
+    // S^-1 of the current walkers is kept from the step that produced them (the proposals'
+    // inverse, committed with them) or recomputed after QR / initialisation
     count_launch();
-    logS_pair_kernel<<<nb(W), kT, 0, st>>>(s->ld, W, wk->logS_old);
+    logS_pair_kernel<<<nb(W), kT, 0, st>>>(s->ldc, W, wk->logS_old);
     count_launch();
     sinv_doubled_kernel<<<(unsigned)(((int64_t)WS * N + 7) / 8), kT, 0, st>>>(
-        s->S, WS, N, reinterpret_cast<__half*>(s->SD_h), reinterpret_cast<__half*>(s->SD_l), s->SD_s);
+        s->Si, WS, N, reinterpret_cast<__half*>(s->SD_h), reinterpret_cast<__half*>(s->SD_l), s->SD_s);
     {   // Theta^T = (Phi S^-1)^T  [WS][2N][M] fp32, then its row-scaled pair
         EpiParams e;
         e.kind = EPI_F32;
@@ -796,18 +816,19 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
                             s->XE, wk->opts.energy_terms > 0 ? wk->opts.energy_terms : kDefaultEnergyTerms,
                             wk->flags, st));
     } else {
-        const int64_t n = (int64_t)WS * 2 * N * M;
-        count_launch();
-        split_f32_kernel<<<nb(n), kT, 0, st>>>(s->ThT_f, s->Pacc_h, s->Pacc_l, n);  // plain pair (scratch)
+        // force bias only: t[ws][n] = sum_{a,k} ThetaT[ws][a][k] Ltilde[n][a][k], one exact-mode GEMM
+        // with K = N*M over rows (ws, re/im) of Theta^T (row-scaled pair in the Pacc scratch)
+        const int64_t K = (int64_t)N * M;
+        split_rows(s->ThT_f, K, 2LL * WS, K, s->Pacc_h, s->Pacc_l, s->Pacc_s, st);
         EpiParams e;
         e.kind = EPI_F32;
         e.rows_valid = 2LL * WS;
         e.cols_valid = nch;
         e.ld = nch;
         e.out_f32 = s->tFB;
-        const int64_t K = (int64_t)N * M;
-        AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, K, 2LL * WS), BatchMap{}, smat(s->Ltp_h, s->Ltp_l, K, nch),
-                          BatchMap{}, 2LL * WS, nch, K, 1, e, 256, false, wk->flags, st));
+        AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, K, 2LL * WS, 1, s->Pacc_s), BatchMap{},
+                          smat(s->Ltp_h, s->Ltp_l, K, nch, 1, s->Ltp_s), BatchMap{}, 2LL * WS, nch, K, 1, e, 128,
+                          true, wk->flags, st));
         count_launch();
         fb_combine_kernel<<<nb((int64_t)WS * nch), kT, 0, st>>>(s->tFB, WS, nch, s->tE);
     }
@@ -892,8 +913,8 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
                           smat(s->Bh_h, s->Bh_l, M, M, 1, s->Bh_s), BatchMap{}, rowsAll, M, M, 1, e, 128, true,
                           wk->flags, st));
     }
-    split_walkers(s, nxt, st);
-    AFQMC_TRY(overlap_logdet(wk, nxt, false, st));
+    // the proposals' inverse is the next step's S^-1 for every accepted walker
+    AFQMC_TRY(overlap_logdet(wk, nxt, true, s->S, s->ld, st));
     count_launch();
     logS_pair_kernel<<<nb(W), kT, 0, st>>>(s->ld, W, wk->logS_new);
     WeightArgs a;
@@ -913,6 +934,8 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     const int64_t per = 4LL * N * M;
     count_launch();
     commit_accepted_kernel<<<nb((int64_t)W * per), kT, 0, st>>>(wk->accept, W, per, s->PhiT[nxt], s->PhiT[s->cur]);
+    count_launch();
+    commit_inverse_kernel<<<nb((int64_t)W * 2 * N * N), kT, 0, st>>>(wk->accept, W, N, s->S, s->ld, s->Si, s->ldc);
     refresh_operands(s, st);
     return AFQMC_OK;
 }
@@ -920,15 +943,12 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
 int tc_debug_terms(afqmc_walkers* wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X, double* E1) {
     TcState* s = wk->tc;
     if (!s) return fail(AFQMC_ERR_BADARG, "debug_mixed_terms: not a BF16X3 walker set");
+    AFQMC_TRY(refresh_inverse(wk, 0));   // overlap of the current walkers into ST64 and Si
     AFQMC_TRY(tc_measure(wk, true, 0));
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
     const int64_t nst = (int64_t)s->W * 4 * s->N * s->N;
-    if (ST) {
-        std::vector<float> h(nst);
-        AFQMC_CUDA_TRY(cudaMemcpy(h.data(), s->ST, nst * 4, cudaMemcpyDeviceToHost));
-        for (int64_t i = 0; i < nst; ++i) ST[i] = h[i];
-    }
-    if (Sinv) AFQMC_CUDA_TRY(cudaMemcpy(Sinv, s->S, (nst / 2) * 16, cudaMemcpyDeviceToHost));
+    if (ST) AFQMC_CUDA_TRY(cudaMemcpy(ST, s->ST64, nst * 8, cudaMemcpyDeviceToHost));
+    if (Sinv) AFQMC_CUDA_TRY(cudaMemcpy(Sinv, s->Si, (nst / 2) * 16, cudaMemcpyDeviceToHost));
     const int64_t nth = (int64_t)s->W * 4 * s->N * s->M;
     if (ThetaT) {
         std::vector<float> h(nth);
@@ -961,7 +981,7 @@ int tc_qr(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_CUDA_TRY(cudaMemcpyAsync(s->PhiT[s->cur], s->PhiT[nxt], sizeof(double) * (size_t)WS * 2 * N * M,
                                    cudaMemcpyDeviceToDevice, st));
     refresh_operands(s, st);
-    return AFQMC_OK;
+    return refresh_inverse(wk, st);
 }
 
 }  // namespace afqmc

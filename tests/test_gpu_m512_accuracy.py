@@ -1,8 +1,8 @@
 """Throughput workload accuracy: BF16X3 vs FP64 GPU paths at M=512, N=128+128, Nchol=2560.
 
 Same walkers, same fields; the mixed-estimator energy of every measured step must agree to
-1 mHa (the bar for the tensor-core path).  Sampled at 16 walkers x 4 steps to keep the FP64
-path's run short (its energy contraction costs ~1.7e11 flops per walker-step)."""
+1 mHa (the bar for the tensor-core path).  Sampled at 16 walkers x 10 steps (two QRs) to keep
+the FP64 path's run short (its energy contraction costs ~1.7e11 flops per walker-step)."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,7 @@ def test_m512_mixed_matches_fp64_within_1mha():
     rng = wl.rng()
     h, L, E0 = syn.make_hamiltonian(wl.M, wl.Nchol, rng, decay=wl.decay, band=wl.band)
     Psi = syn.make_trial(h, wl.Nup, wl.Ndn)
-    W, steps = 16, 4
+    W, steps = 16, 10
     x = syn.make_fields(steps, W, wl.Nchol, seed=0)
     traces = {}
     for name, prec, terms in (("fp64", api.PREC_FP64, 0), ("bf16x3", api.PREC_BF16X3, 4),

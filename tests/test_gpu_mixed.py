@@ -66,6 +66,8 @@ def test_trajectory_matches_fp64_within_1mha(M, N, nch, W, steps, me):
         # E_mix depends on relative weights only; a common factor per step (the split
         # representation of B = exp(-tau h'/2) is the same for every walker) cancels
         ra, rb = wa / np.mean(wa), wb / np.mean(wb)
+        print(f"M={M} N={N} every {me}: |dE_mix| {np.max(np.abs(ta - tb)):.2e}, |dE_L| {np.max(np.abs(Ea - Eb)):.2e}, "
+              f"relative weights {np.max(np.abs(ra - rb) / np.abs(ra)):.2e}")
         assert np.max(np.abs(ra - rb) / np.abs(ra)) < 1e-3
         Pa = a.walkers()
         Pb = b.walkers()
