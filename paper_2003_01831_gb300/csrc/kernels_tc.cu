@@ -305,6 +305,76 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
     }
 }
 
+// FP64 epilogue of the three-slice GEMM: 32 consecutive columns [c0, c0+32) of row r.
+__device__ void epilogue_row64(const EpiParams& e, int b, int64_t r, int64_t c0, const double (&v)[32]) {
+    if (r >= e.rows_valid) return;
+    const int ncol = (int)(e.cols_valid - c0 < 32 ? e.cols_valid - c0 : 32);
+    if (ncol <= 0) return;
+    const bool full = ncol == 32;
+    switch (e.kind) {
+        case EPI3_F64: {
+            double* o = e.out_f64 + b * e.ob + r * e.ld + c0;
+            if (full && aligned16(o)) {
+#pragma unroll
+                for (int g = 0; g < 16; ++g) reinterpret_cast<double2*>(o)[g] = make_double2(v[2 * g], v[2 * g + 1]);
+            } else {
+                for (int j = 0; j < ncol; ++j) o[j] = v[j];
+            }
+            break;
+        }
+        case EPI3_HSPOT: {
+            // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
+            const int64_t w = r >> 1, c = r & 1;
+            const int64_t i0 = c0 / e.M, k0 = c0 % e.M;
+            if (full && k0 + 32 <= e.M) {
+                double* o = e.out_f64 + (w * e.M + i0) * (2 * e.M) + c * e.M + k0;
+                if (aligned16(o)) {
+#pragma unroll
+                    for (int g = 0; g < 16; ++g) reinterpret_cast<double2*>(o)[g] = make_double2(v[2 * g], v[2 * g + 1]);
+                } else {
+                    for (int j = 0; j < 32; ++j) o[j] = v[j];
+                }
+            } else {
+                for (int j = 0; j < ncol; ++j) {
+                    const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
+                    e.out_f64[(w * e.M + i) * (2 * e.M) + c * e.M + k] = v[j];
+                }
+            }
+            break;
+        }
+        case EPI3_TAYLOR: {
+            // batch b = walker; row r = (s*2 + c)*N + j of the doubled operand; new term i*scale*C:
+            // C_re (c = 0) -> imaginary row, C_im (c = 1) -> real row, negated
+            const int64_t N = e.N, M = e.M;
+            const int64_t s = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
+            const int64_t ws = (int64_t)b * 2 + s;
+            const int64_t row = (ws * 2 + (c == 0 ? 1 : 0)) * N + jj;
+            const double sg = c == 0 ? e.scale64 : -e.scale64;
+            double* o = e.out_f64 + row * M + c0;
+            double* a = e.acc64 + row * M + c0;
+            if (full && aligned16(o) && aligned16(a)) {
+#pragma unroll
+                for (int g = 0; g < 16; ++g) {
+                    const double2 t = make_double2(sg * v[2 * g], sg * v[2 * g + 1]);
+                    reinterpret_cast<double2*>(o)[g] = t;
+                    double2 q = reinterpret_cast<double2*>(a)[g];
+                    q.x += t.x;
+                    q.y += t.y;
+                    reinterpret_cast<double2*>(a)[g] = q;
+                }
+            } else {
+                for (int j = 0; j < ncol; ++j) {
+                    o[j] = sg * v[j];
+                    a[j] += sg * v[j];
+                }
+            }
+            break;
+        }
+        default:
+            break;
+    }
+}
+
 __device__ __forceinline__ void tile_coords(const TileShape& s, int64_t t, int& b, int& rt, int& ct) {
     const int64_t per = (int64_t)s.rt * s.ct;
     b = (int)(t / per);
@@ -1041,35 +1111,23 @@ __global__ void __launch_bounds__(256) split3_rows_kernel(const double* src, int
     }
 }
 
-struct Ovl3Shape {
-    int N, M;         // electrons (B rows, output columns), orbitals (K)
-    int rows;         // A rows per walker-spin (2N)
-    int rt;           // row tiles per walker-spin
-    int nws;
-    int nk;
-    int64_t tiles;
-    const float* a_scale;   // [nws][rows]
-    const float* b_scale;   // [N]
-    double* out;            // [nws][rows][N]
-};
-
-constexpr int kO3Planes = 3;
-constexpr int kO3ABytes = kBM * kBK * 2;          // one plane, 128 rows x 64
-constexpr int kO3BBytes = 128 * kBK * 2;          // B tile: 128 rows (N <= 128)
-constexpr int kO3StageBytes = kO3Planes * (kO3ABytes + kO3BBytes);   // 96 KB
-constexpr int kO3Stages = 2;
+constexpr int kG3ABytes = kBM * kBK * 2;          // one plane, 128 rows x 64
+constexpr int kG3BBytes = 128 * kBK * 2;          // B tile: 128 rows
+constexpr int kG3StageBytes = 3 * (kG3ABytes + kG3BBytes);   // 96 KB
+constexpr int kG3Stages = 2;
 
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    tc_overlap3_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
-                       const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
-                       const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, Ovl3Shape sh,
-                       unsigned* flags) {
+    tc_gemm3_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+                    const __grid_constant__ CUtensorMap tA2, const __grid_constant__ CUtensorMap tB0,
+                    const __grid_constant__ CUtensorMap tB1, const __grid_constant__ CUtensorMap tB2, TileShape sh,
+                    EpiParams epi, unsigned* flags) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(sbase + kO3Stages * kO3StageBytes);
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(sbase + kG3Stages * kG3StageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool three_d = sh.am.mod != (1 << 30) || sh.nbatch > 1;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kO3Stages; ++i) {
+        for (int i = 0; i < kG3Stages; ++i) {
             mbar_init(&ctl->full[i], 1);
             mbar_init(&ctl->empty[i], 1);
         }
@@ -1093,24 +1151,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             int64_t g = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < sh.tiles && ok; t += gridDim.x) {
-                const int ws = (int)(t / sh.rt), rt = (int)(t % sh.rt);
+                int b, rt, ct;
+                tile_coords(sh, t, b, rt, ct);
+                const int az = three_d ? (b / sh.am.div) % sh.am.mod : 0;
+                const int bz = three_d ? (b / sh.bm.div) % sh.bm.mod : 0;
                 for (int kb = 0; kb < sh.nk; ++kb, ++g) {
-                    const int st = (int)(g % kO3Stages);
-                    const uint32_t ph = (uint32_t)((g / kO3Stages) & 1);
+                    const int st = (int)(g % kG3Stages);
+                    const uint32_t ph = (uint32_t)((g / kG3Stages) & 1);
                     if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
-                    uint8_t* sp = sbase + (size_t)st * kO3StageBytes;
-                    mbar_arrive_expect_tx(&ctl->full[st], kO3StageBytes);
+                    uint8_t* sp = sbase + (size_t)st * kG3StageBytes;
+                    mbar_arrive_expect_tx(&ctl->full[st], kG3StageBytes);
                     const int x = kb * kBK;
                     for (int q = 0; q < 3; ++q) {
-                        tma_load_3d(sp + q * kO3ABytes, A[q], &ctl->full[st], x, rt * kBM, ws);
-                        tma_load_2d(sp + 3 * kO3ABytes + q * kO3BBytes, B[q], &ctl->full[st], x, 0);
+                        if (three_d) {
+                            tma_load_3d(sp + q * kG3ABytes, A[q], &ctl->full[st], x, rt * kBM, az);
+                            tma_load_3d(sp + 3 * kG3ABytes + q * kG3BBytes, B[q], &ctl->full[st], x, ct * 128, bz);
+                        } else {
+                            tma_load_2d(sp + q * kG3ABytes, A[q], &ctl->full[st], x, rt * kBM);
+                            tma_load_2d(sp + 3 * kG3ABytes + q * kG3BBytes, B[q], &ctl->full[st], x, ct * 128);
+                        }
                     }
                 }
             }
             if (!ok) {
-                const int64_t first = g > kO3Stages ? g - kO3Stages : 0;
+                const int64_t first = g > kG3Stages ? g - kG3Stages : 0;
                 for (int64_t j = first; j < g; ++j)
-                    wait_drain(&ctl->full[j % kO3Stages], (uint32_t)((j / kO3Stages) & 1));
+                    wait_drain(&ctl->full[j % kG3Stages], (uint32_t)((j / kG3Stages) & 1));
             }
         }
     } else if (warp == 1) {
@@ -1124,19 +1190,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
                 tc_fence_after();
                 for (int kb = 0; kb < sh.nk; ++kb, ++g) {
-                    const int st = (int)(g % kO3Stages);
-                    const uint32_t ph = (uint32_t)((g / kO3Stages) & 1);
+                    const int st = (int)(g % kG3Stages);
+                    const uint32_t ph = (uint32_t)((g / kG3Stages) & 1);
                     if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(sbase + (size_t)st * kO3StageBytes);
-                    const uint32_t sb = sa + 3 * kO3ABytes;
+                    const uint32_t sa = smem_u32(sbase + (size_t)st * kG3StageBytes);
+                    const uint32_t sb = sa + 3 * kG3ABytes;
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
                         const uint32_t off = kk * 32;
-                        const uint64_t ah = desc_sw128(sa + off), am = desc_sw128(sa + kO3ABytes + off),
-                                       al = desc_sw128(sa + 2 * kO3ABytes + off);
-                        const uint64_t bh = desc_sw128(sb + off), bm = desc_sw128(sb + kO3BBytes + off),
-                                       bl = desc_sw128(sb + 2 * kO3BBytes + off);
+                        const uint64_t ah = desc_sw128(sa + off), am = desc_sw128(sa + kG3ABytes + off),
+                                       al = desc_sw128(sa + 2 * kG3ABytes + off);
+                        const uint64_t bh = desc_sw128(sb + off), bm = desc_sw128(sb + kG3BBytes + off),
+                                       bl = desc_sw128(sb + 2 * kG3BBytes + off);
                         const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
                         mma_bf16(d1, ah, bh, idesc, acc);
                         mma_bf16(d2, ah, bm, idesc, acc);
@@ -1160,9 +1226,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int64_t t = blockIdx.x; t < sh.tiles; t += gridDim.x, ++it) {
             if (!warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort)) break;
             tc_fence_after();
-            const int ws = (int)(t / sh.rt), rt = (int)(t % sh.rt);
-            const int r = rt * kBM + g4 * 32 + lane;
-            const double sa = r < sh.rows ? (double)sh.a_scale[(int64_t)ws * sh.rows + r] : 0.0;
+            int b, rt, ct;
+            tile_coords(sh, t, b, rt, ct);
+            const int az = three_d ? (b / sh.am.div) % sh.am.mod : 0;
+            const int bz = three_d ? (b / sh.bm.div) % sh.bm.mod : 0;
+            const int64_t r = (int64_t)rt * kBM + g4 * 32 + lane;
+            const double sa = r < sh.a_rows ? (double)sh.a_scale[(int64_t)az * sh.a_rows + r] : 0.0;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 uint32_t a1[32], a2[32];
@@ -1175,17 +1244,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 tmem_ld32_nw(tb + 256 + c * 32, a1);
                 tmem_ld32_nw(tb + 384 + c * 32, a2);
                 tmem_ld_wait();
-                if (r < sh.rows) {
-                    double* o = sh.out + ((int64_t)ws * sh.rows + r) * sh.N;
+                const int64_t c0 = (int64_t)ct * 128 + c * 32;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int col = c * 32 + q;
-                        if (col < sh.N)
-                            o[col] = (v[q] + kS3 * (double)__uint_as_float(a1[q]) +
-                                      kS3 * kS3 * (double)__uint_as_float(a2[q])) *
-                                     sa * (double)sh.b_scale[col];
-                    }
+                for (int q = 0; q < 32; ++q) {
+                    const int64_t col = c0 + q;
+                    const double sb = col < sh.b_rows ? (double)sh.b_scale[(int64_t)bz * sh.b_rows + col] : 0.0;
+                    v[q] = (v[q] + kS3 * (double)__uint_as_float(a1[q]) + kS3 * kS3 * (double)__uint_as_float(a2[q])) *
+                           sa * sb;
                 }
+                epilogue_row64(epi, b, r, c0, v);
             }
             tc_fence_before();
             mbar_arrive(&ctl->tempty[0]);
@@ -1198,6 +1265,41 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         tmem_dealloc(ctl->tmem_base, 512);
     }
     if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+// doubled three-slice split of a planar FP64 term (see split3_doubled)
+__global__ void __launch_bounds__(256) split3_doubled_kernel(const double* P, int64_t WS, int N, int M, __half* h,
+                                                             __half* m, __half* l, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // (ws, j)
+    const int lane = threadIdx.x & 31;
+    if (r >= WS * N) return;
+    const int64_t ws = r / N;
+    const int j = (int)(r % N);
+    const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;
+    const double* pr = P + row0 * M;
+    const double* pi = P + row1 * M;
+    double ss = 0.0;
+    for (int k = lane; k < M; k += 32) ss += pr[k] * pr[k] + pi[k] * pi[k];
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double nrm = sqrt(ss);
+    int e = 0;
+    if (nrm > 0.0) frexp(nrm, &e);
+    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+    const float sc = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
+    const int64_t K2 = 2LL * M;
+    for (int k = lane; k < M; k += 32) {
+        const double yr = pr[k] * inv, yi = pi[k] * inv;
+        const double hr = rint(yr), hI = rint(yi);
+        const double rr = (yr - hr) * 128.0, ri = (yi - hI) * 128.0;
+        const double mr = rint(rr), mI = rint(ri);
+        const __half Hr = __double2half(hr), Mr = __double2half(mr), Lr = __double2half(rr - mr);
+        const __half Hi = __double2half(hI), Mi = __double2half(mI), Li = __double2half(ri - mI);
+        h[row0 * K2 + k] = Hr;  m[row0 * K2 + k] = Mr;  l[row0 * K2 + k] = Lr;                  // Re
+        h[row0 * K2 + M + k] = __hneg(Hi);  m[row0 * K2 + M + k] = __hneg(Mi);  l[row0 * K2 + M + k] = __hneg(Li);  // -Im
+        h[row1 * K2 + k] = Hi;  m[row1 * K2 + k] = Mi;  l[row1 * K2 + k] = Li;                  // Im
+        h[row1 * K2 + M + k] = Hr;  m[row1 * K2 + M + k] = Mr;  l[row1 * K2 + M + k] = Lr;      // Re
+    }
 }
 
 // --------------------------------------------------------------------------- host side
@@ -1373,35 +1475,77 @@ void split3_rows(const double* src, int64_t rows, int64_t K, bf16* h, bf16* m, b
                                                                    reinterpret_cast<__half*>(l), scale);
 }
 
-int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, const bf16* const* b,
-                const float* b_scale, int N, int M, double* out, unsigned* flags, cudaStream_t st) {
-    if (N > 128 || M % 8 || M > 1024 || rows <= 0 || nws <= 0)
-        return fail(AFQMC_ERR_UNSUPPORTED, "tc_overlap3: needs N <= 128, M % 8 == 0, M <= 1024");
+int tc_gemm3(const Split3& A, BatchMap amap, const Split3& B, BatchMap bmap, int64_t rows, int64_t cols, int64_t K,
+             int nbatch, const EpiParams& epi, unsigned* flags, cudaStream_t st) {
+    if (rows <= 0 || cols <= 0 || K <= 0 || nbatch <= 0) return AFQMC_OK;
+    if (!A.scale || !B.scale) return fail(AFQMC_ERR_BADARG, "tc_gemm3: row scales required");
+    const bool three_d = nbatch > 1 || amap.mod != (1 << 30);
     CUtensorMap m[6];
     for (int q = 0; q < 3; ++q) {
-        AFQMC_TRY(make_map(&m[q], a[q], M, rows, nws, M, (int64_t)rows * M, kBM, true, true));
-        AFQMC_TRY(make_map(&m[3 + q], b[q], M, N, 1, M, 0, 128, false, true));
+        AFQMC_TRY(make_map(&m[q], A.p[q], A.K, A.rows, A.batch, A.K, A.batch_stride, kBM, three_d, true));
+        AFQMC_TRY(make_map(&m[3 + q], B.p[q], B.K, B.rows, B.batch, B.K, B.batch_stride, 128, three_d, true));
     }
-    Ovl3Shape sh;
-    sh.N = N;
-    sh.M = M;
+    TileShape sh;
     sh.rows = rows;
-    sh.rt = (rows + kBM - 1) / kBM;
-    sh.nws = nws;
-    sh.nk = (M + kBK - 1) / kBK;
-    sh.tiles = (int64_t)nws * sh.rt;
-    sh.a_scale = a_scale;
-    sh.b_scale = b_scale;
-    sh.out = out;
-    const size_t smem = 1024 + (size_t)kO3Stages * kO3StageBytes + sizeof(SharedCtl);
-    cudaFuncSetAttribute(tc_overlap3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sh.cols = cols;
+    sh.K = K;
+    sh.nbatch = nbatch;
+    sh.rt = (int)((rows + kBM - 1) / kBM);
+    sh.ct = (int)((cols + 127) / 128);
+    sh.nk = (int)((K + kBK - 1) / kBK);
+    sh.tiles = (int64_t)sh.rt * sh.ct * nbatch;
+    // unbatched: 2-D maps and batch coordinate 0 (the kernel tests the same condition)
+    sh.am = three_d ? amap : BatchMap{1, 1 << 30};
+    sh.bm = three_d ? bmap : BatchMap{1, 1 << 30};
+    sh.a_scale = A.scale;
+    sh.b_scale = B.scale;
+    sh.a_rows = A.rows;
+    sh.b_rows = B.rows;
+    const size_t smem = 1024 + (size_t)kG3Stages * kG3StageBytes + sizeof(SharedCtl);
+    cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
     const int grid = (int)std::min<int64_t>(sh.tiles, cap);
     count_launch();
-    tc_overlap3_kernel<<<grid, kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], sh, flags);
+    tc_gemm3_kernel<<<grid, kGemmThreads, smem, st>>>(m[0], m[1], m[2], m[3], m[4], m[5], sh, epi, flags);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_overlap3 launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_gemm3 launch: ") + cudaGetErrorString(e));
     return AFQMC_OK;
+}
+
+int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, const bf16* const* b,
+                const float* b_scale, int N, int M, double* out, unsigned* flags, cudaStream_t st) {
+    if (N > 128 || M % 8 || rows <= 0 || nws <= 0)
+        return fail(AFQMC_ERR_UNSUPPORTED, "tc_overlap3: needs N <= 128, M % 8 == 0");
+    Split3 A, B;
+    for (int q = 0; q < 3; ++q) {
+        A.p[q] = a[q];
+        B.p[q] = b[q];
+    }
+    A.scale = a_scale;
+    A.K = M;
+    A.rows = rows;
+    A.batch = nws;
+    A.batch_stride = (int64_t)rows * M;
+    B.scale = b_scale;
+    B.K = M;
+    B.rows = N;
+    B.batch = 1;
+    EpiParams e;
+    e.kind = EPI3_F64;
+    e.rows_valid = rows;
+    e.cols_valid = N;
+    e.ld = N;
+    e.ob = (int64_t)rows * N;
+    e.out_f64 = out;
+    return tc_gemm3(A, BatchMap{1, nws}, B, BatchMap{1, 1}, rows, N, M, nws, e, flags, st);
+}
+
+void split3_doubled(const double* P, int64_t WS, int N, int M, bf16* h, bf16* m, bf16* l, float* scale,
+                    cudaStream_t st) {
+    if (WS * N <= 0) return;
+    count_launch();
+    split3_doubled_kernel<<<(unsigned)((WS * N + 7) / 8), 256, 0, st>>>(
+        P, WS, N, M, reinterpret_cast<__half*>(h), reinterpret_cast<__half*>(m), reinterpret_cast<__half*>(l), scale);
 }
 
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,

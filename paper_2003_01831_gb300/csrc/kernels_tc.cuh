@@ -50,6 +50,10 @@ enum EpiKind : int {
     EPI_F64 = 5,       // out_f64[b*ob + r*ld + c]
     EPI_HSPOT_F32 = 6, // A potential in fp32: row (w, c), col (i, k) -> out_f32[w][i][c*M + k]
     EPI_TAYLOR_F32 = 7,// next Taylor term i*scale*C in fp32 (planar rows) + accumulator update
+    // three-slice GEMM (tc_gemm3) epilogues, FP64 values:
+    EPI3_F64 = 8,      // out_f64[b*ob + r*ld + c]
+    EPI3_HSPOT = 9,    // A potential: row (w, c), col (i, k) -> out_f64[w][i][c*M + k]
+    EPI3_TAYLOR = 10,  // next Taylor term i*scale*C -> out_f64 (planar rows), acc64 += term
 };
 
 struct EpiParams {
@@ -61,9 +65,30 @@ struct EpiParams {
     bf16* out_lo = nullptr;
     double* out_f64 = nullptr;
     float* acc = nullptr;                    // Taylor accumulator (fp32)
+    double* acc64 = nullptr;                 // Taylor accumulator (FP64, three-slice GEMM)
     int M = 0, N = 0;                        // orbitals, electrons per spin
     float scale = 1.0f;                      // Taylor factor sqrt(tau)/k
+    double scale64 = 1.0;                    // the same in FP64 (three-slice GEMM)
 };
+
+// Three fp16 slices of a matrix [batch][rows][K] (planes h, m, l; see split3_rows) with
+// per-row scales [batch][rows]: value = scale (h + 2^-7 (m + l)).
+struct Split3 {
+    const bf16* p[3] = {nullptr, nullptr, nullptr};
+    const float* scale = nullptr;
+    int64_t K = 0, rows = 0, batch = 1;
+    int64_t batch_stride = 0;   // elements between batches (row stride = K)
+};
+
+// C[b] = A[b] . B[b]^T from three-slice operands, ~1e-9 relative, FP64 epilogue (EPI3_*),
+// 128 x 128 tiles.  K <= 1024 keeps the integer accumulators exact; larger K only loses
+// exactness of the h*m sums (still ~1e-8).
+int tc_gemm3(const Split3& A, BatchMap amap, const Split3& B, BatchMap bmap, int64_t rows, int64_t cols, int64_t K,
+             int nbatch, const EpiParams& epi, unsigned* flags, cudaStream_t st);
+// Doubled complex operand of a planar FP64 term P [WS][2][N][M] as three slices:
+// row (ws, 0, j) = [Re P_j | -Im P_j], row (ws, 1, j) = [Im P_j | Re P_j] (length 2M).
+void split3_doubled(const double* P, int64_t WS, int N, int M, bf16* h, bf16* m, bf16* l, float* scale,
+                    cudaStream_t st);
 
 // C[b] = A[b] . B[b]^T (split bf16, fp32 accumulation in TMEM), 128 x BN tiles.
 // exact = true needs row-scaled A and B and BN = 128.

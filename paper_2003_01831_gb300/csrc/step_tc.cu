@@ -5,25 +5,25 @@
 //
 // Device layouts (W walkers, both spins, N electrons per spin, complex stored planar):
 //   PhiT   [W][2][2][N][M] FP64 master walkers, transposed (row (s, c, j) = column j of
-//          Phi_s, re/im plane c), plus its row-scaled fp16 pair and a plain bf16 pair; a
-//          second buffer holds the proposals, copied over the current walkers on acceptance
-//          (the current walkers never change buffer, so captured step graphs replay)
+//          Phi_s, re/im plane c); a second buffer holds the proposals, copied over the current
+//          walkers on acceptance (the current walkers never change buffer, so captured step
+//          graphs replay); PhiT3 is the three-slice split of whichever is being multiplied
 //   Phi    [W][2][M][2N]   row-scaled fp16 pair, untransposed with re | im columns
 //          (Green's-function GEMM operand)
+//   Si     [W][2][N][N]    S^-1 of the current walkers (kept from the step that made them)
 //   ThT    [W][2][2][N][M] Theta^T = (Phi S^-1)^T: fp32, and its row-scaled fp16 pair
 //          (energy GEMM operand)
 //   Lt     [Nchol][N][M]   Ltilde_n = Psi^T L_n (trial real, same for both spins): row-scaled
-//          pair for the energy, plain pair for the force-bias-only contraction
-//   LT     [M*M][Nchol]    L transposed, row-scaled pair (HS potential GEMM operand)
-//   A      [W][M][2M]      HS potential sum_n c_n L_n, re | im columns: fp32, then its
-//                          row-scaled pair (Taylor GEMM operand)
-//   Pk     [W][2][2][N][M] fp32 Taylor term; PD [W][2][2N][2M] its doubled form
-//                          [[Re, -Im], [Im, Re]] as a row-scaled pair
-//   Pacc   [W][2][2][N][M] fp32 Taylor accumulator (row-scaled pair for the final B product)
-// Every contraction of the step uses row-scaled fp16 operands and the exact-accumulation GEMM
-// mode (kernels_tc.cu): hi*hi summed exactly, the remainder products in a second accumulator.
-// (Plain bf16 pairs, whose fp32 accumulation the tensor cores truncate, perturb each walker by
-// ~1e-5 per step -- tens of mHa in E_mix after a few steps at M = 512.)
+//          pair for the energy; Ltp the same rows over all N*M entries (force bias only)
+//   LT3    [M*M][Nchol]    L transposed, three slices (HS potential GEMM operand)
+//   A64    [W][M][2M]      HS potential sum_n c_n L_n, re | im columns, FP64 (+ three slices)
+//   Pk64   [W][2][2][N][M] Taylor term, FP64; PD3 [W][2][2N][2M] its doubled form
+//                          [[Re, -Im], [Im, Re]] as three slices
+//   Pacc64 [W][2][2][N][M] Taylor sum, FP64 (three slices for the final B product)
+// Contractions use row-scaled fp16 operands with exact accumulation of the leading products
+// (kernels_tc.cu): the Green's-function and energy contractions with two slices (hi*hi summed
+// exactly, remainders in a second accumulator), the overlap and the whole propagation with
+// three slices and FP64 intermediates (~1e-9), because the walkers' overlaps set the weights.
 #include <algorithm>
 #include <utility>
 #include <vector>
@@ -41,18 +41,16 @@ struct TcState {
     float* Lt_s = nullptr;
     bf16 *Ltp_h = nullptr, *Ltp_l = nullptr;      // Ltilde rows n over all N*M entries, row-scaled
     float* Ltp_s = nullptr;
-    bf16 *LT_h = nullptr, *LT_l = nullptr;
-    float* LT_s = nullptr;
-    bf16 *Bh_h = nullptr, *Bh_l = nullptr;
-    float* Bh_s = nullptr;
+    bf16* LT3[3] = {nullptr, nullptr, nullptr};    // L^T [M*M][Nchol], three slices
+    float* LT3_s = nullptr;
+    bf16* Bh3[3] = {nullptr, nullptr, nullptr};    // B = exp(-tau h'/2) [M][M], three slices
+    float* Bh3_s = nullptr;
     bf16 *PsiT_h = nullptr, *PsiT_l = nullptr;
     float* PsiT_s = nullptr;
     double* PsiT_f = nullptr;
     // walkers
     double* PhiT[2] = {nullptr, nullptr};
-    bf16 *PhiT_h[2] = {nullptr, nullptr}, *PhiT_l[2] = {nullptr, nullptr};   // current walkers only ([cur])
-    float* PhiT_s[2] = {nullptr, nullptr};
-    bf16 *PhiT3[3] = {nullptr, nullptr, nullptr};   // three-slice split of the walkers being overlapped
+    bf16 *PhiT3[3] = {nullptr, nullptr, nullptr};   // three-slice split of the walkers being multiplied
     float* PhiT3_s = nullptr;
     bf16 *PsiT3[3] = {nullptr, nullptr, nullptr};   // three-slice split of the trial (static)
     float* PsiT3_s = nullptr;
@@ -72,18 +70,20 @@ struct TcState {
     cplx *tE = nullptr, *XE = nullptr;
     float* tFB = nullptr;
     cplx* E1 = nullptr;
-    // propagation
+    // propagation (three-slice operands, FP64 intermediates)
     double* cfp = nullptr;                 // [W][2][Nchol] HS coefficients, planar
-    bf16 *cf_h = nullptr, *cf_l = nullptr;
-    float* cf_s = nullptr;
-    float* A_f = nullptr;
-    bf16 *A_h = nullptr, *A_l = nullptr;
-    float* A_s = nullptr;
-    float* Pk = nullptr;
-    bf16 *PD_h = nullptr, *PD_l = nullptr;
-    float* PD_s = nullptr;
-    float* Pacc = nullptr;
-    bf16 *Pacc_h = nullptr, *Pacc_l = nullptr;   // row-scaled pair (also plain scratch, see tc_measure)
+    bf16* cf3[3] = {nullptr, nullptr, nullptr};
+    float* cf3_s = nullptr;
+    double* A64 = nullptr;                 // [W][M][2M] HS potential, re | im columns
+    bf16* A3[3] = {nullptr, nullptr, nullptr};
+    float* A3_s = nullptr;
+    double* Pk64 = nullptr;                // [W][2][2][N][M] Taylor term
+    bf16* PD3[3] = {nullptr, nullptr, nullptr};   // its doubled form [W][2][2N][2M]
+    float* PD3_s = nullptr;
+    double* Pacc64 = nullptr;              // Taylor sum
+    bf16* Pacc3[3] = {nullptr, nullptr, nullptr};
+    float* Pacc3_s = nullptr;
+    bf16 *Pacc_h = nullptr, *Pacc_l = nullptr;   // scratch pair of the force-bias-only contraction
     float* Pacc_s = nullptr;
     int cur = 0;
     std::vector<void*> owned;
@@ -93,7 +93,8 @@ namespace {
 
 constexpr int kT = 256;
 // Split products of the energy contraction when the options leave it open: hi*hi (exact),
-// hi*lo and lo*hi; the lo*lo term is below the rounding of the second accumulator's sum.
+// hi*lo, lo*hi and lo*lo.  The two-body energy is a difference of large Coulomb and exchange
+// sums, so at energies of ~1e3 Ha the lo*lo term is worth keeping.
 constexpr int kDefaultEnergyTerms = 4;
 inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 
@@ -257,13 +258,6 @@ __global__ void __launch_bounds__(kT) sinv_doubled_kernel(const cplx* Si, int WS
         hi[row1 * K2 + N + j] = Hr;  lo[row1 * K2 + N + j] = Lr;    // Re
     }
 }
-// four halves at an 8-byte aligned address
-__device__ __forceinline__ void store4h(__half* p, const __half (&h)[4]) {
-    uint2 u;
-    u.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
-    u.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
-    *reinterpret_cast<uint2*>(p) = u;
-}
 // HS coefficients c [W][Nchol] complex -> planar rows [W][2][Nchol]
 __global__ void coef_planar_kernel(const cplx* c, int64_t W, int nch, double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -271,56 +265,6 @@ __global__ void coef_planar_kernel(const cplx* c, int64_t W, int nch, double* ou
     const int64_t w = i / nch, n = i % nch;
     out[(w * 2) * nch + n] = c[i].re;
     out[(w * 2 + 1) * nch + n] = c[i].im;
-}
-// Taylor term P (fp32 rows (ws, c, j) of length M, c = re / im) -> doubled operand as a
-// row-scaled fp16 pair: row (ws, 0, j) = [Re P_j | -Im P_j], row (ws, 1, j) = [Im P_j | Re P_j]
-// (length 2M), both rows with the scale of the complex 2-norm of P_j.
-__global__ void __launch_bounds__(kT) split_doubled_kernel(const float* P, int64_t WS, int N, int M, __half* hi,
-                                                             __half* lo, float* scale) {
-    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // (ws, j)
-    const int lane = threadIdx.x & 31;
-    if (r >= WS * N) return;
-    const int64_t ws = r / N;
-    const int j = (int)(r % N);
-    const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;
-    const float* pr = P + row0 * M;
-    const float* pi = P + row1 * M;
-    // four consecutive orbitals per lane (M is a multiple of 64: 16-byte loads, 8-byte stores);
-    // single precision throughout, the norm raised by 2^-10 so that ||x||_2 < 2^e is guaranteed
-    float ss = 0.f;
-    for (int k = 4 * lane; k < M; k += 128) {
-        const float4 a = *reinterpret_cast<const float4*>(pr + k), b = *reinterpret_cast<const float4*>(pi + k);
-        ss = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(a.z, a.z, fmaf(a.w, a.w, ss))));
-        ss = fmaf(b.x, b.x, fmaf(b.y, b.y, fmaf(b.z, b.z, fmaf(b.w, b.w, ss))));
-    }
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const float nrm = sqrtf(ss) * (1.0f + 0x1p-10f);
-    int e = 0;
-    if (nrm > 0.f) frexpf(nrm, &e);
-    const float inv = nrm > 0.f ? ldexpf(1.0f, 11 - e) : 0.f;
-    const float sc = nrm > 0.f ? ldexpf(1.0f, e - 11) : 1.0f;
-    if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
-    const int64_t K2 = 2LL * M;
-    for (int k = 4 * lane; k < M; k += 128) {
-        const float4 a = *reinterpret_cast<const float4*>(pr + k), b = *reinterpret_cast<const float4*>(pi + k);
-        const float re[4] = {a.x, a.y, a.z, a.w}, im[4] = {b.x, b.y, b.z, b.w};
-        __half Hr[4], Lr[4], Hi[4], Li[4], nHi[4], nLi[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float yr = re[q] * inv, yi = im[q] * inv;
-            const float hr = rintf(yr), hI = rintf(yi);
-            Hr[q] = __float2half_rn(hr);
-            Lr[q] = __float2half_rn(yr - hr);
-            Hi[q] = __float2half_rn(hI);
-            Li[q] = __float2half_rn(yi - hI);
-            nHi[q] = __float2half_rn(-hI);
-            nLi[q] = __float2half_rn(hI - yi);
-        }
-        store4h(hi + row0 * K2 + k, Hr);      store4h(lo + row0 * K2 + k, Lr);       // Re
-        store4h(hi + row0 * K2 + M + k, nHi); store4h(lo + row0 * K2 + M + k, nLi);  // -Im
-        store4h(hi + row1 * K2 + k, Hi);      store4h(lo + row1 * K2 + k, Li);       // Im
-        store4h(hi + row1 * K2 + M + k, Hr);  store4h(lo + row1 * K2 + M + k, Lr);   // Re
-    }
 }
 __global__ void fb_combine_kernel(const float* tFB, int64_t WS, int nch, cplx* t) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -615,11 +559,6 @@ SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t bat
     return m;
 }
 
-// row-scaled pair of the walkers in buffer b
-void split_walkers(TcState* s, int b, cudaStream_t st) {
-    split_rows(s->PhiT[b], s->M, (int64_t)s->W * 4 * s->N, s->M, s->PhiT_h[b], s->PhiT_l[b], s->PhiT_s[b], st);
-}
-
 // untransposed operand of the current walkers (Green's-function GEMM)
 void untranspose_walkers(TcState* s, cudaStream_t st) {
     dim3 g((s->M + 31) / 32, 2 * s->W);
@@ -630,10 +569,7 @@ void untranspose_walkers(TcState* s, cudaStream_t st) {
                                                     reinterpret_cast<__half*>(s->Phi_l), s->Phi_s);
 }
 
-void refresh_operands(TcState* s, cudaStream_t st) {
-    split_walkers(s, s->cur, st);
-    untranspose_walkers(s, st);
-}
+void refresh_operands(TcState* s, cudaStream_t st) { untranspose_walkers(s, st); }
 
 // S = Psi^T Phi for the walkers in buffer b -> Sout (inverted in place when `inverse`), per-spin
 // log-determinants -> ldout
@@ -674,21 +610,18 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->Ltp_h, nch * NM));
     AFQMC_TRY(talloc(s, &s->Ltp_l, nch * NM));
     AFQMC_TRY(talloc(s, &s->Ltp_s, nch));
-    AFQMC_TRY(talloc(s, &s->LT_h, MM * nch));
-    AFQMC_TRY(talloc(s, &s->LT_l, MM * nch));
-    AFQMC_TRY(talloc(s, &s->LT_s, MM));
-    AFQMC_TRY(talloc(s, &s->Bh_h, MM));
-    AFQMC_TRY(talloc(s, &s->Bh_l, MM));
-    AFQMC_TRY(talloc(s, &s->Bh_s, M));
+    for (int q = 0; q < 3; ++q) {
+        AFQMC_TRY(talloc(s, &s->LT3[q], MM * nch));
+        AFQMC_TRY(talloc(s, &s->Bh3[q], MM));
+    }
+    AFQMC_TRY(talloc(s, &s->LT3_s, MM));
+    AFQMC_TRY(talloc(s, &s->Bh3_s, M));
     AFQMC_TRY(talloc(s, &s->PsiT_h, NM));
     AFQMC_TRY(talloc(s, &s->PsiT_l, NM));
     AFQMC_TRY(talloc(s, &s->PsiT_s, N));
     AFQMC_TRY(talloc(s, &s->PsiT_f, NM));
     const int64_t wall = (int64_t)W * 4 * NM;  // PhiT elements
     for (int b = 0; b < 2; ++b) AFQMC_TRY(talloc(s, &s->PhiT[b], wall));
-    AFQMC_TRY(talloc(s, &s->PhiT_h[0], wall));
-    AFQMC_TRY(talloc(s, &s->PhiT_l[0], wall));
-    AFQMC_TRY(talloc(s, &s->PhiT_s[0], (int64_t)W * 4 * N));
     for (int q = 0; q < 3; ++q) {
         AFQMC_TRY(talloc(s, &s->PhiT3[q], wall));
         AFQMC_TRY(talloc(s, &s->PsiT3[q], NM));
@@ -696,10 +629,19 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->PhiT3_s, (int64_t)W * 4 * N));
     AFQMC_TRY(talloc(s, &s->PsiT3_s, N));
     AFQMC_TRY(talloc(s, &s->ST64, (int64_t)W * 2 * 2 * N * N));
-    AFQMC_TRY(talloc(s, &s->PD_h, (int64_t)W * 2 * 2 * N * 2 * M));
-    AFQMC_TRY(talloc(s, &s->PD_l, (int64_t)W * 2 * 2 * N * 2 * M));
-    AFQMC_TRY(talloc(s, &s->PD_s, (int64_t)W * 4 * N));
-    AFQMC_TRY(talloc(s, &s->Pk, wall));
+    for (int q = 0; q < 3; ++q) {
+        AFQMC_TRY(talloc(s, &s->PD3[q], (int64_t)W * 2 * 2 * N * 2 * M));
+        AFQMC_TRY(talloc(s, &s->Pacc3[q], wall));
+        AFQMC_TRY(talloc(s, &s->A3[q], (int64_t)W * M * 2 * M));
+        AFQMC_TRY(talloc(s, &s->cf3[q], (int64_t)W * 2 * nch));
+    }
+    AFQMC_TRY(talloc(s, &s->PD3_s, (int64_t)W * 4 * N));
+    AFQMC_TRY(talloc(s, &s->Pacc3_s, (int64_t)W * 4 * N));
+    AFQMC_TRY(talloc(s, &s->A3_s, (int64_t)W * M));
+    AFQMC_TRY(talloc(s, &s->cf3_s, (int64_t)W * 2));
+    AFQMC_TRY(talloc(s, &s->Pk64, wall));
+    AFQMC_TRY(talloc(s, &s->Pacc64, wall));
+    AFQMC_TRY(talloc(s, &s->A64, (int64_t)W * M * 2 * M));
     AFQMC_TRY(talloc(s, &s->Phi_h, wall));
     AFQMC_TRY(talloc(s, &s->Phi_l, wall));
     AFQMC_TRY(talloc(s, &s->Phi_s, (int64_t)W * 2 * M));
@@ -718,14 +660,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->XE, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->tFB, (int64_t)W * 4 * nch));
     AFQMC_TRY(talloc(s, &s->cfp, (int64_t)W * 2 * nch));
-    AFQMC_TRY(talloc(s, &s->cf_h, (int64_t)W * 2 * nch));
-    AFQMC_TRY(talloc(s, &s->cf_l, (int64_t)W * 2 * nch));
-    AFQMC_TRY(talloc(s, &s->cf_s, (int64_t)W * 2));
-    AFQMC_TRY(talloc(s, &s->A_f, (int64_t)W * M * 2 * M));
-    AFQMC_TRY(talloc(s, &s->A_h, (int64_t)W * M * 2 * M));
-    AFQMC_TRY(talloc(s, &s->A_l, (int64_t)W * M * 2 * M));
-    AFQMC_TRY(talloc(s, &s->A_s, (int64_t)W * M));
-    AFQMC_TRY(talloc(s, &s->Pacc, wall));
+
     AFQMC_TRY(talloc(s, &s->Pacc_h, wall));
     AFQMC_TRY(talloc(s, &s->Pacc_l, wall));
     AFQMC_TRY(talloc(s, &s->Pacc_s, (int64_t)W * 4 * N));
@@ -743,11 +678,11 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
         dim3 gl((unsigned)((MM + 31) / 32), (unsigned)((nch + 31) / 32));
         count_launch();
         LT_kernel<<<gl, dim3(32, 8), 0, st>>>(wk->ham->L, MM, nch, LTd);
-        split_rows(LTd, nch, MM, nch, s->LT_h, s->LT_l, s->LT_s, st);
+        split3_rows(LTd, MM, nch, s->LT3[0], s->LT3[1], s->LT3[2], s->LT3_s, st);
         cudaStreamSynchronize(st);
         cudaFree(LTd);
     }
-    split_rows(wk->f.Bh, M, M, M, s->Bh_h, s->Bh_l, s->Bh_s, st);   // B is symmetric: rows = columns
+    split3_rows(wk->f.Bh, M, M, s->Bh3[0], s->Bh3[1], s->Bh3[2], s->Bh3_s, st);   // B symmetric: rows = columns
     count_launch();
     psiT_kernel<<<nb(NM), kT, 0, st>>>(wk->f.Psi[0], M, N, s->PsiT_f);
     split_rows(s->PsiT_f, M, N, M, s->PsiT_h, s->PsiT_l, s->PsiT_s, st);
@@ -854,64 +789,69 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     hs_coefficients(x, wk->xbar, wk->weight, W, nch, wk->coef, wk->flags, st);
     count_launch();
     coef_planar_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->coef, W, nch, s->cfp);
-    split_rows(s->cfp, nch, 2LL * W, nch, s->cf_h, s->cf_l, s->cf_s, st);
-    {   // A_w = sum_n c_wn L_n  -> fp32 [W][M][2M], then its row-scaled pair
+    split3_rows(s->cfp, 2LL * W, nch, s->cf3[0], s->cf3[1], s->cf3[2], s->cf3_s, st);
+    auto sp3 = [](bf16* const* p, const float* sc, int64_t K, int64_t rows, int64_t batch = 1) {
+        Split3 x;
+        for (int q = 0; q < 3; ++q) x.p[q] = p[q];
+        x.scale = sc;
+        x.K = K;
+        x.rows = rows;
+        x.batch = batch;
+        x.batch_stride = rows * K;
+        return x;
+    };
+    {   // A_w = sum_n c_wn L_n  -> FP64 [W][M][2M], then its three slices
         EpiParams e;
-        e.kind = EPI_HSPOT_F32;
+        e.kind = EPI3_HSPOT;
         e.rows_valid = 2LL * W;
         e.cols_valid = MM;
         e.M = M;
-        e.out_f32 = s->A_f;
-        AFQMC_TRY(tc_gemm(smat(s->cf_h, s->cf_l, nch, 2LL * W, 1, s->cf_s), BatchMap{},
-                          smat(s->LT_h, s->LT_l, nch, MM, 1, s->LT_s), BatchMap{}, 2LL * W, MM, nch, 1, e, 128, true,
-                          wk->flags, st));
-        split_rows(s->A_f, 2LL * M, (int64_t)W * M, 2LL * M, s->A_h, s->A_l, s->A_s, st);
+        e.out_f64 = s->A64;
+        AFQMC_TRY(tc_gemm3(sp3(s->cf3, s->cf3_s, nch, 2LL * W), BatchMap{}, sp3(s->LT3, s->LT3_s, nch, MM),
+                           BatchMap{}, 2LL * W, MM, nch, 1, e, wk->flags, st));
+        split3_rows(s->A64, (int64_t)W * M, 2LL * M, s->A3[0], s->A3[1], s->A3[2], s->A3_s, st);
     }
     const int64_t rowsAll = (int64_t)W * 4 * N;
     const int64_t WS = 2LL * W;
-    {   // P0 = B Phi -> accumulator (fp32), then the doubled operand of the first term
+    {   // P0 = B Phi -> Taylor sum (FP64)
+        split3_rows(s->PhiT[s->cur], rowsAll, M, s->PhiT3[0], s->PhiT3[1], s->PhiT3[2], s->PhiT3_s, st);
         EpiParams e;
-        e.kind = EPI_F32;
+        e.kind = EPI3_F64;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
         e.ld = M;
-        e.out_f32 = s->Pacc;
-        AFQMC_TRY(tc_gemm(smat(s->PhiT_h[s->cur], s->PhiT_l[s->cur], M, rowsAll, 1, s->PhiT_s[s->cur]), BatchMap{},
-                          smat(s->Bh_h, s->Bh_l, M, M, 1, s->Bh_s), BatchMap{}, rowsAll, M, M, 1, e, 128, true,
-                          wk->flags, st));
+        e.out_f64 = s->Pacc64;
+        AFQMC_TRY(tc_gemm3(sp3(s->PhiT3, s->PhiT3_s, M, rowsAll), BatchMap{}, sp3(s->Bh3, s->Bh3_s, M, M), BatchMap{},
+                           rowsAll, M, M, 1, e, wk->flags, st));
     }
-    const float sq = (float)sqrt(wk->tau);
+    const double sq = sqrt(wk->tau);
     for (int k = 1; k <= wk->opts.k_taylor; ++k) {
-        // doubled operand of the previous term (P0 = the accumulator before any term is added)
-        count_launch();
-        split_doubled_kernel<<<(unsigned)((WS * N + 7) / 8), kT, 0, st>>>(
-            k == 1 ? s->Pacc : s->Pk, WS, N, M, reinterpret_cast<__half*>(s->PD_h), reinterpret_cast<__half*>(s->PD_l),
-            s->PD_s);
-        EpiParams e;   // P_k = (i sqrt(tau) / k) P_{k-1} A^T  -> Pk (fp32), Pacc += P_k
-        e.kind = EPI_TAYLOR_F32;
+        // doubled operand of the previous term (P0 = the sum before any term is added)
+        split3_doubled(k == 1 ? s->Pacc64 : s->Pk64, WS, N, M, s->PD3[0], s->PD3[1], s->PD3[2], s->PD3_s, st);
+        EpiParams e;   // P_k = (i sqrt(tau) / k) P_{k-1} A^T  -> Pk64, Pacc64 += P_k
+        e.kind = EPI3_TAYLOR;
         e.rows_valid = 4LL * N;
         e.cols_valid = M;
         e.M = M;
         e.N = N;
-        e.out_f32 = s->Pk;
-        e.acc = s->Pacc;
-        e.scale = sq / (float)k;
-        AFQMC_TRY(tc_gemm(smat(s->PD_h, s->PD_l, 2LL * M, 4LL * N, W, s->PD_s), BatchMap{1, W},
-                          smat(s->A_h, s->A_l, 2LL * M, M, W, s->A_s), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, 128,
-                          true, wk->flags, st));
+        e.out_f64 = s->Pk64;
+        e.acc64 = s->Pacc64;
+        e.scale64 = sq / (double)k;
+        AFQMC_TRY(tc_gemm3(sp3(s->PD3, s->PD3_s, 2LL * M, 4LL * N, W), BatchMap{1, W},
+                           sp3(s->A3, s->A3_s, 2LL * M, M, W), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, wk->flags,
+                           st));
     }
     const int nxt = s->cur ^ 1;
     {   // Phi' = B Pacc  (FP64 master of the proposed walkers)
-        split_rows(s->Pacc, M, rowsAll, M, s->Pacc_h, s->Pacc_l, s->Pacc_s, st);
+        split3_rows(s->Pacc64, rowsAll, M, s->Pacc3[0], s->Pacc3[1], s->Pacc3[2], s->Pacc3_s, st);
         EpiParams e;
-        e.kind = EPI_F64;
+        e.kind = EPI3_F64;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
         e.ld = M;
         e.out_f64 = s->PhiT[nxt];
-        AFQMC_TRY(tc_gemm(smat(s->Pacc_h, s->Pacc_l, M, rowsAll, 1, s->Pacc_s), BatchMap{},
-                          smat(s->Bh_h, s->Bh_l, M, M, 1, s->Bh_s), BatchMap{}, rowsAll, M, M, 1, e, 128, true,
-                          wk->flags, st));
+        AFQMC_TRY(tc_gemm3(sp3(s->Pacc3, s->Pacc3_s, M, rowsAll), BatchMap{}, sp3(s->Bh3, s->Bh3_s, M, M), BatchMap{},
+                           rowsAll, M, M, 1, e, wk->flags, st));
     }
     // the proposals' inverse is the next step's S^-1 for every accepted walker
     AFQMC_TRY(overlap_logdet(wk, nxt, true, s->S, s->ld, st));
