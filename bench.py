@@ -35,6 +35,30 @@ WORKLOAD = ("solid-like synthetic Hamiltonian: M=512, N_up=N_dn=128, Nchol=2560,
             "L_n decay exp(-n/200), W=1024 walkers/GPU, tau=0.005, QR/5, energy measured every step")
 
 
+# DRAM bytes of one launch of the energy kernel at this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, one ncu capture of this script; the summary and its command are in
+# profiles/).  The figure holds for the kernel source it was taken on: a digest of that source
+# (the energy-kernel section of kernels_tc.cu and the PTX wrappers) gates it.
+ENERGY_TRAFFIC = {"bytes": 172671584128, "src_digest": "c30cb62d1cedcdf6"}
+
+
+def energy_src_digest() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2003_01831_gb300", "csrc")
+    src = open(os.path.join(csrc, "kernels_tc.cu")).read()
+    a = src.index("// --------------------------------------------------------------------------- energy kernel")
+    b = src.index("// --------------------------------------------------------------------------- row split")
+    h = hashlib.sha1(src[a:b].encode())
+    h.update(open(os.path.join(csrc, "tc_ptx.cuh")).read().encode())
+    return h.hexdigest()[:16]
+
+
+def energy_traffic():
+    if ENERGY_TRAFFIC["bytes"] is None or ENERGY_TRAFFIC["src_digest"] != energy_src_digest():
+        return None
+    return ENERGY_TRAFFIC["bytes"]
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -216,7 +240,7 @@ def run_batch(args, rank, world):
     line = {"metric": "walker-steps/sec, 64 uneven systems (M~U{32..256}, N=M/4, Nchol=5M, W~U{32..256})",
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3 (split hi+lo, fp32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
+            "dtype": "f16 row-scaled splits (2-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
             "data": "synthetic",
             "config": {"workload": f"64 uneven molecule-like systems, {Wtot} walkers in total, tau=0.01, QR/10, "
                                    "energy every step, padded to tensor-core shapes, one graph launch per step",
@@ -351,13 +375,13 @@ def main():
     if e_avg:
         ach = alg_flops / (e_avg / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s",
-                "frac": ach / bf16_sust, "traffic": None, "kernel": "tc_energy_kernel<128>",
+                "frac": ach / bf16_sust, "traffic": energy_traffic() if args.walkers == 0 else None, "kernel": "tc_energy_kernel<128>",
                 "avg_launch_ms": e_avg, "issued_over_algorithmic": float(args.energy_terms or 4),
                 "peak_source": f"bf16_tflops_sustained of {src} peaks (kernel timed inside a long step)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16x3 (split hi+lo, fp32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
+            "dtype": "f16 row-scaled splits (2-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.walkers == 0 else WORKLOAD.replace("W=1024", f"W={wl.W}"),
                        "l2": "inputs larger than L2 (Ltilde 0.67 GB, Theta 1.1 GB per step)",

@@ -18,8 +18,9 @@ extern "C" {
  * by the tcgen05 split-bf16 GEMM and returned as float64 C [nbatch][rows][cols].
  * exact = 0: plain split (hi = bf16(x), lo = bf16(x - hi)), all three products in one fp32
  *            accumulator; BN = 128 or 256.
- * exact = 1: row-scaled split (hi an integer in [-128, 128] times a per-row power of two),
- *            hi*hi summed exactly in its own accumulator; BN must be 128 and K <= 1024.
+ * exact = 1: row-scaled fp16 split: per row a power of two s = 2^(e-11) with ||x||_2 < 2^e,
+ *            hi = rint(x/s) (an integer, |hi| <= 2048), lo = fp16(x/s - hi); hi*hi summed
+ *            exactly in its own accumulator, hi*lo + lo*hi + lo*lo in a second; BN must be 128.
  * K must be a multiple of 8.  This is the contraction primitive behind every dense product
  * of the step (Sec. V; Table II costs). */
 int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int rows, int cols, int K, int BN,
@@ -50,6 +51,25 @@ typedef struct afqmc_walkers* afqmc_wk_debug_t;
  * energy_bk = 16 or 32, the K chunk of the fused energy kernel.  For tuning experiments;
  * results do not depend on them. */
 int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk);
+
+/* Batched inverse and log-determinant of count complex N x N matrices S (host, interleaved
+ * float64, row-major [count][N][N]) by FP64 Gauss-Jordan elimination with partial pivoting
+ * (the LU / inverse / log-det row of the walker step, Sec. V).  logdet [count] complex
+ * receives log|det S| + i arg det S; with_inverse = 1 also writes the inverses to Sout (same
+ * layout).  variant: 0 = the kernel the
+ * step uses, 1 = the shared-memory kernel, 2 = the register kernel (32 < N <= 128 with
+ * with_inverse; other cases fall back to 1).  *ms (if not NULL) receives the kernel time.
+ * Returns AFQMC_ERR_SINGULAR / AFQMC_ERR_NONFINITE (logdet = -inf + 0i for such a matrix,
+ * its inverse unwritten) if a pivot column is zero / not finite. */
+int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with_inverse, double* Sout,
+                        double* logdet, float* ms);
+
+/* Tile order of the calling thread's later energy-kernel launches: the (Cholesky vector,
+ * walker-spin) tiles run in windows of ws_super walker-spin groups (0 = default), sweeping
+ * every Cholesky vector inside a window, so the window's Green's functions stay in L2 while
+ * Ltilde streams through once per window.  For tuning experiments; results do not depend
+ * on it. */
+int afqmc_debug_set_energy_window(int ws_super);
 int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X,
                             double* E1);
 

@@ -59,7 +59,9 @@ long long launch_count();
 struct LaunchPolicy {
     int grid_cap = 0;    // > 0: at most this many CTAs per persistent launch
     int bn_max = 256;    // 128: narrow every plain GEMM tile to 128 columns
-    int energy_bk = 0;   // K chunk of the fused energy kernel: 16 (default) or 32
+    int energy_bk = 0;   // K chunk of the fused energy kernel: 16 or 32 (default)
+    int energy_ws_super = 0;   // walker-spin groups per L2 window of the energy kernel (0: default)
+    int gj_variant = 0;        // batched inverse: 0 auto, 1 shared-memory kernel, 2 register kernel
 };
 LaunchPolicy& launch_policy();
 

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "../../include/afqmc_debug.h"
+#include "kernels_fp64.cuh"
 #include "kernels_tc.cuh"
 #include "state.cuh"
 #include "tc_ptx.cuh"
@@ -119,6 +120,51 @@ extern "C" int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* 
                                        double* X, double* E1) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "debug_mixed_terms: NULL handle");
     return tc_debug_terms(wk, ST, Sinv, ThetaT, t, X, E1);
+}
+
+extern "C" int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with_inverse, double* Sout,
+                                   double* logdet, float* ms) {
+    if (!S || !logdet || N < 1 || count < 1 || variant < 0 || variant > 2 || (with_inverse && !Sout))
+        return fail(AFQMC_ERR_BADARG, "debug_inverse: bad arguments");
+    const int64_t n = (int64_t)count * N * N;
+    DevBuf ds, dl, flags;
+    if (cudaMalloc(&ds.p, n * 16) != cudaSuccess || cudaMalloc(&dl.p, (int64_t)count * 16) != cudaSuccess ||
+        cudaMalloc(&flags.p, 4) != cudaSuccess)
+        return fail(AFQMC_ERR_OOM, "debug: allocation");
+    AFQMC_CUDA_TRY(cudaMemcpy(ds.p, S, n * 16, cudaMemcpyHostToDevice));
+    cudaMemset(flags.p, 0, 4);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    LaunchPolicy saved = launch_policy();
+    launch_policy().gj_variant = variant;
+    cudaEventRecord(e0, 0);
+    batched_inverse_logdet(static_cast<cplx*>(ds.p), (int64_t)N * N, N, count, static_cast<cplx*>(dl.p),
+                           with_inverse != 0, static_cast<unsigned*>(flags.p), 0);
+    cudaEventRecord(e1, 0);
+    launch_policy() = saved;
+    const cudaError_t le = cudaGetLastError();
+    const cudaError_t se = cudaEventSynchronize(e1);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AFQMC_CUDA_TRY(le);
+    AFQMC_CUDA_TRY(se);
+    if (ms) *ms = t;
+    unsigned fl = 0;
+    AFQMC_CUDA_TRY(cudaMemcpy(&fl, flags.p, 4, cudaMemcpyDeviceToHost));
+    AFQMC_CUDA_TRY(cudaMemcpy(logdet, dl.p, (int64_t)count * 16, cudaMemcpyDeviceToHost));
+    if (with_inverse) AFQMC_CUDA_TRY(cudaMemcpy(Sout, ds.p, n * 16, cudaMemcpyDeviceToHost));
+    if (fl & FLAG_SINGULAR) return fail(AFQMC_ERR_SINGULAR, "debug_inverse: singular matrix");
+    if (fl & FLAG_NONFINITE) return fail(AFQMC_ERR_NONFINITE, "debug_inverse: non-finite matrix");
+    return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_set_energy_window(int ws_super) {
+    if (ws_super < 0) return fail(AFQMC_ERR_BADARG, "debug_set_energy_window: negative window");
+    launch_policy().energy_ws_super = ws_super;
+    return AFQMC_OK;
 }
 
 extern "C" int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk) {

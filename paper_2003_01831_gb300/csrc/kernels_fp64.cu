@@ -553,6 +553,236 @@ __global__ void __launch_bounds__(kGJT)
     if (C > 1) cluster_sync_all();
 }
 
+// ------------------------------------------------------- Gauss-Jordan in registers
+// The inverse and log-determinant of an N x N complex matrix, 32 < N <= 128, held entirely in
+// registers: one CTA for N <= 64, else a cluster of two CTAs (the two halves of a 128 x 128
+// complex matrix fill two register files).  CTA r owns the 64 consecutive columns
+// [64 r, 64 r + 64); warp w of it owns four of them, and lane l holds rows l, l + 32, ... (RQ of
+// them), so the thread's block is a[RQ][4].  Pivoting is implicit: step k picks, among the rows
+// not pivoted yet, the one with the largest |re| + |im| in column k (lowest row on ties), scales
+// it and eliminates column k from every other row, in place, so that after N steps the stored
+// array X satisfies X[p_k][j] = inverse[k][p_j] for the pivot rows p_k.  det = sign(p) prod(pivot).
+// The warp owning column k+1 updates that column first, searches its pivot and publishes the
+// column and the pivot row (to both CTAs' shared memory) before finishing its own update, so one
+// cluster barrier per step orders the steps and the search is off the critical path.  The
+// pivot row reaches the other lanes of each warp by shuffles; the column k multipliers are
+// read from shared memory.  FP64 throughput bounds the elimination.
+constexpr int kGJRegCols = 64;      // columns per CTA
+constexpr int kGJRegThreads = 512;  // 16 warps x 4 columns
+
+template <int RQ>
+__device__ __forceinline__ cplx sel_q(const cplx (&v)[RQ][4], int q, int u) {
+    cplx r = v[0][u];
+#pragma unroll
+    for (int i = 1; i < RQ; ++i)
+        if (q == i) r = v[i][u];
+    return r;
+}
+template <int RQ>
+__device__ __forceinline__ cplx sel_u(const cplx (&v)[RQ][4], int q, int u) {
+    cplx r = v[q][0];
+#pragma unroll
+    for (int i = 1; i < 4; ++i)
+        if (u == i) r = v[q][i];
+    return r;
+}
+
+// Pivot search over column k (local sub-column uk of the calling warp) and publication of the
+// column (pre-elimination values), the pivot row (or -1 singular / -2 non-finite) and the
+// pivot's reciprocal, computed once here instead of by every thread.
+template <int C, int RQ>
+__device__ __forceinline__ void gj_reg_publish(const cplx (&a)[RQ][4], int uk, unsigned used, int N, int lane,
+                                               int owner_rank, cplx* colbuf, int* pbuf, cplx* invbuf) {
+    double best = -1.0;
+    int bi = N;
+    cplx col[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        col[q] = sel_u<RQ>(a, q, uk);
+        const int i = lane + 32 * q;
+        if (i < N && !((used >> q) & 1u)) {
+            const double v = abs1(col[q]);
+            if (v > best || (v != v && best == best)) { best = v; bi = i; }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > best || (v2 == best && i2 < bi) || (v2 != v2 && best == best)) { best = v2; bi = i2; }
+    }
+    const int code = best > 0.0 ? bi : (best != best ? -2 : -1);
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        const int i = lane + 32 * q;
+        colbuf[i] = col[q];
+        if (C > 1) {
+            const uint32_t ad = peer_addr(&colbuf[i], (uint32_t)(owner_rank ^ 1));
+            st_peer_f64(ad, col[q].re);
+            st_peer_f64(ad + 8, col[q].im);
+        }
+    }
+    // the pivot value from the lane that holds row bi
+    const int bl = code >= 0 ? (code & 31) : 0, bq = code >= 0 ? (code >> 5) : 0;
+    cplx pv = col[0];
+#pragma unroll
+    for (int q = 1; q < RQ; ++q)
+        if (bq == q) pv = col[q];
+    pv = cplx{__shfl_sync(0xffffffffu, pv.re, bl), __shfl_sync(0xffffffffu, pv.im, bl)};
+    if (lane == 0) {
+        const cplx inv = code >= 0 ? cdiv(cplx{1.0, 0.0}, pv) : cplx{0.0, 0.0};
+        *pbuf = code;
+        *invbuf = inv;
+        if (C > 1) {
+            st_peer_s32(peer_addr(pbuf, (uint32_t)(owner_rank ^ 1)), code);
+            const uint32_t ad = peer_addr(invbuf, (uint32_t)(owner_rank ^ 1));
+            st_peer_f64(ad, inv.re);
+            st_peer_f64(ad + 8, inv.im);
+        }
+    }
+}
+
+template <int C, int RQ>
+__global__ void __launch_bounds__(kGJRegThreads, 1)
+    gj_reg_kernel(cplx* Sbase, int64_t stride, int N, cplx* logdet, unsigned* flags) {
+    constexpr int NR = 32 * RQ;
+    __shared__ cplx colbuf[2][NR];
+    __shared__ int pbuf[2];
+    __shared__ cplx invbuf[2];
+    __shared__ int perm[NR];
+    __shared__ int pinv[NR];
+    __shared__ cplx pivs[NR];
+    const int rank = C == 1 ? 0 : (int)cluster_rank();
+    const int64_t mat = C == 1 ? blockIdx.x : blockIdx.x / C;
+    cplx* G = Sbase + mat * stride;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = rank * kGJRegCols + warp * 4;   // first global column of this thread
+    cplx a[RQ][4];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        const int i = lane + 32 * q;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = c0 + u;
+            a[q][u] = (i < N && j < N) ? G[(int64_t)i * N + j] : cplx{0.0, 0.0};
+        }
+    }
+    unsigned used = 0;   // bit q: row lane + 32 q is a pivot row already
+    auto owns = [&](int k) { return k < N && (k >> 6) == rank && ((k & 63) >> 2) == warp; };
+    if (owns(0)) gj_reg_publish<C, RQ>(a, 0, used, N, lane, rank, colbuf[0], &pbuf[0], &invbuf[0]);
+    gj_sync<C>();
+    int singular = 0;
+    for (int k = 0; k < N; ++k) {
+        const int b = k & 1;
+        const int p = pbuf[b];
+        if (p < 0) { singular = p; break; }
+        const cplx inv = invbuf[b];
+        if (threadIdx.x == 0) { perm[k] = p; pivs[k] = colbuf[b][p]; }
+        const int pl = p & 31, pq = p >> 5;
+        // the warp's four pivot-row entries: gathered from lane pl, each scaled by one lane
+        // (lane u % 4 scales entry u), then shared again
+        cplx rp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const cplx v = sel_q<RQ>(a, pq, u);
+            rp[u] = cplx{__shfl_sync(0xffffffffu, v.re, pl), __shfl_sync(0xffffffffu, v.im, pl)};
+        }
+        cplx mine = rp[0];
+#pragma unroll
+        for (int u = 1; u < 4; ++u)
+            if ((lane & 3) == u) mine = rp[u];
+        mine = mine * inv;
+        cplx prow[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            prow[u] = cplx{__shfl_sync(0xffffffffu, mine.re, u), __shfl_sync(0xffffffffu, mine.im, u)};
+        if (lane == pl) used |= 1u << pq;
+        const bool ownk = owns(k);
+        const int uk = k & 3;
+        const bool own1 = owns(k + 1);
+        const int u1 = (k + 1) & 3;
+        // one element: a -= m prow; column k of the inverse: -m / piv; the pivot row: prow, 1 / piv
+        auto upd = [&](int q, int u, cplx m) {
+            const int i = lane + 32 * q;
+            cplx v = a[q][u];
+            cfma(v, cplx{-m.re, -m.im}, prow[u]);
+            if (ownk && u == uk) {
+                const cplx w = m * inv;
+                v = i == p ? inv : cplx{-w.re, -w.im};
+            } else if (i == p) {
+                v = prow[u];
+            }
+            a[q][u] = v;
+        };
+        if (own1) {   // look-ahead: column k+1 first, then its pivot search and publication
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                const cplx m = colbuf[b][lane + 32 * q];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u == u1) upd(q, u, m);
+            }
+            gj_reg_publish<C, RQ>(a, u1, used, N, lane, rank, colbuf[b ^ 1], &pbuf[b ^ 1], &invbuf[b ^ 1]);
+        }
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+            const cplx m = colbuf[b][lane + 32 * q];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (!(own1 && u == u1)) upd(q, u, m);
+        }
+        gj_sync<C>();
+    }
+    if (singular) {
+        if (threadIdx.x == 0 && rank == 0) {
+            logdet[mat] = cplx{-INFINITY, 0.0};
+            atomicOr(flags, singular == -2 ? FLAG_NONFINITE : FLAG_SINGULAR);
+        }
+        if (C > 1) cluster_sync_all();   // keep shared memory alive until the peer is done
+        return;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) pinv[perm[threadIdx.x]] = threadIdx.x;
+    if (rank == 0 && warp == 0) {
+        // log|det| and arg det: sums over the pivots in a fixed order, plus pi for an odd
+        // pivot permutation (N - number of cycles transpositions)
+        double la = 0.0, ph = 0.0;
+        for (int k = lane; k < N; k += 32) {
+            la += log(hypot(pivs[k].re, pivs[k].im));
+            ph += atan2(pivs[k].im, pivs[k].re);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            la += __shfl_xor_sync(0xffffffffu, la, o);
+            ph += __shfl_xor_sync(0xffffffffu, ph, o);
+        }
+        if (lane == 0) {
+            unsigned seen[4] = {0u, 0u, 0u, 0u};
+            int cycles = 0;
+            for (int s0 = 0; s0 < N; ++s0) {
+                if ((seen[s0 >> 5] >> (s0 & 31)) & 1u) continue;
+                ++cycles;
+                for (int x = s0; !((seen[x >> 5] >> (x & 31)) & 1u); x = perm[x]) seen[x >> 5] |= 1u << (x & 31);
+            }
+            if ((N - cycles) & 1) ph += M_PI;
+            logdet[mat] = cplx{la, atan2(sin(ph), cos(ph))};
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+        const int i = lane + 32 * q;
+        if (i >= N) continue;
+        const int64_t orow = (int64_t)pinv[i] * N;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = c0 + u;
+            if (j < N) G[orow + perm[j]] = a[q][u];
+        }
+    }
+    if (C > 1) cluster_sync_all();
+}
+
 // ------------------------------------------------------------------ traces of T
 __global__ void __launch_bounds__(kThreads)
     trace_kernel(const cplx* T, int W, int N, int n0, cplx* t_out, cplx* X_out, int64_t ldo) {
@@ -830,6 +1060,28 @@ void zgemm(const GemmArgs& g, cudaStream_t st) {
 void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet, bool with_inverse,
                             unsigned* flags, cudaStream_t st) {
     if (count <= 0) return;
+    const int variant = launch_policy().gj_variant;   // 0 auto, 1 shared memory, 2 registers
+    if (with_inverse && N > 32 && N <= 2 * kGJRegCols && variant != 1) {
+        count_launch();
+        if (N <= kGJRegCols) {
+            gj_reg_kernel<1, 2><<<count, kGJRegThreads, 0, st>>>(S, stride, N, logdet, flags);
+            return;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)count * 2);
+        cfg.blockDim = dim3(kGJRegThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, gj_reg_kernel<2, 4>, S, stride, N, logdet, flags);
+        return;
+    }
     if (N <= kGJSmemMax) {
         const int C = N <= kGJSmemOne ? 1 : 2;
         const int H = (N + C - 1) / C;

@@ -89,56 +89,7 @@ __device__ __forceinline__ bool wait_drain(uint64_t* bar, uint32_t parity) {
 }
 
 // --------------------------------------------------------------------------- epilogues
-__device__ __forceinline__ void store_split(bf16* hi, bf16* lo, int64_t idx, float v) {
-    bf16 h, l;
-    split_bf16(v, h, l);
-    hi[idx] = h;
-    lo[idx] = l;
-}
-
 __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
-
-// 32 consecutive values (times sgn) as a plain bf16 pair, 16-byte stores when aligned.
-__device__ __forceinline__ void store_split32(bf16* hi, bf16* lo, int64_t base, const float (&v)[32], float sgn) {
-    bf16* H = hi + base;
-    bf16* L = lo + base;
-    if (aligned16(H) && aligned16(L)) {
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint32_t ph[4], pl[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                bf16 h0, l0, h1, l1;
-                split_bf16(sgn * v[8 * g + 2 * q], h0, l0);
-                split_bf16(sgn * v[8 * g + 2 * q + 1], h1, l1);
-                ph[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                pl[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            }
-            reinterpret_cast<uint4*>(H)[g] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-            reinterpret_cast<uint4*>(L)[g] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-        }
-    } else {
-        for (int q = 0; q < 32; ++q) store_split(hi, lo, base + q, sgn * v[q]);
-    }
-}
-
-// acc[base + q] (+)= sgn * v[q], 16-byte accesses when aligned
-__device__ __forceinline__ void acc32(float* acc, int64_t base, const float (&v)[32], float sgn, bool add) {
-    float* A = acc + base;
-    if (aligned16(A)) {
-#pragma unroll
-        for (int g = 0; g < 8; ++g) {
-            float4 o = add ? reinterpret_cast<float4*>(A)[g] : make_float4(0.f, 0.f, 0.f, 0.f);
-            o.x += sgn * v[4 * g];
-            o.y += sgn * v[4 * g + 1];
-            o.z += sgn * v[4 * g + 2];
-            o.w += sgn * v[4 * g + 3];
-            reinterpret_cast<float4*>(A)[g] = o;
-        }
-    } else {
-        for (int q = 0; q < 32; ++q) A[q] = (add ? A[q] : 0.f) + sgn * v[q];
-    }
-}
 
 // Writes 32 consecutive output columns [c0, c0+32) of row r (per batch b).
 __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, const float (&v)[32]) {
@@ -154,149 +105,9 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
                 for (int g = 0; g < 8; ++g)
                     reinterpret_cast<float4*>(o)[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
             } else {
-                for (int j = 0; j < ncol; ++j) o[j] = v[j];
-            }
-            break;
-        }
-        case EPI_F64: {
-            double* o = e.out_f64 + b * e.ob + r * e.ld + c0;
-            if (full && aligned16(o)) {
 #pragma unroll
-                for (int g = 0; g < 16; ++g)
-                    reinterpret_cast<double2*>(o)[g] = make_double2((double)v[2 * g], (double)v[2 * g + 1]);
-            } else {
-                for (int j = 0; j < ncol; ++j) o[j] = (double)v[j];
-            }
-            break;
-        }
-        case EPI_SPLIT: {
-            const int64_t base = b * e.ob + r * e.ld + c0;
-            if (full) store_split32(e.out_hi, e.out_lo, base, v, 1.0f);
-            else
-                for (int j = 0; j < ncol; ++j) store_split(e.out_hi, e.out_lo, base + j, v[j]);
-            break;
-        }
-        case EPI_HSPOT: {
-            // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
-            const int64_t w = r >> 1, c = r & 1;
-            const int64_t i0 = c0 / e.M, k0 = c0 % e.M;
-            if (full && k0 + 32 <= e.M) {
-                store_split32(e.out_hi, e.out_lo, (w * e.M + i0) * (2 * e.M) + c * e.M + k0, v, 1.0f);
-            } else {
-                for (int j = 0; j < ncol; ++j) {
-                    const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
-                    store_split(e.out_hi, e.out_lo, (w * e.M + i) * (2 * e.M) + c * e.M + k, v[j]);
-                }
-            }
-            break;
-        }
-        case EPI_BFIRST: {
-            // row r = ((w*2 + s)*2 + c)*N + j over all walkers; P_c[j][i] for i in [c0, c0+32)
-            const int64_t N = e.N, M = e.M;
-            const int64_t ws = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
-            const int64_t re_row = (ws * 2 + 0) * N + jj, im_row = (ws * 2 + 1) * N + jj;
-            if (full) {
-                acc32(e.acc, r * M + c0, v, 1.0f, false);
-                if (c == 0) {
-                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + c0, v, 1.0f);
-                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + M + c0, v, 1.0f);
-                } else {
-                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + M + c0, v, -1.0f);
-                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + c0, v, 1.0f);
-                }
-                break;
-            }
-            for (int j = 0; j < ncol; ++j) {
-                const int64_t i = c0 + j;
-                const float p = v[j];
-                e.acc[r * M + i] = p;
-                if (c == 0) {
-                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + i, p);
-                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + M + i, p);
-                } else {
-                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + M + i, -p);
-                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + i, p);
-                }
-            }
-            break;
-        }
-        case EPI_TAYLOR: {
-            // batch b = walker; row r = (s*2 + c)*N + j; C = (P A^T)_c[j][i]; new = i*scale*C
-            const int64_t N = e.N, M = e.M;
-            const int64_t s = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
-            const int64_t ws = (int64_t)b * 2 + s;
-            const int64_t re_row = (ws * 2 + 0) * N + jj, im_row = (ws * 2 + 1) * N + jj;
-            const float sc = e.scale;
-            if (full) {
-                if (c == 0) {  // C_re -> new_im = sc * C_re
-                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + M + c0, v, -sc);
-                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + c0, v, sc);
-                    acc32(e.acc, im_row * M + c0, v, sc, true);
-                } else {       // C_im -> new_re = -sc * C_im
-                    store_split32(e.out_hi, e.out_lo, re_row * 2 * M + c0, v, -sc);
-                    store_split32(e.out_hi, e.out_lo, im_row * 2 * M + M + c0, v, -sc);
-                    acc32(e.acc, re_row * M + c0, v, -sc, true);
-                }
-                break;
-            }
-            for (int j = 0; j < ncol; ++j) {
-                const int64_t i = c0 + j;
-                if (c == 0) {
-                    const float ni = sc * v[j];
-                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + M + i, -ni);
-                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + i, ni);
-                    e.acc[im_row * M + i] += ni;
-                } else {
-                    const float nr = -sc * v[j];
-                    store_split(e.out_hi, e.out_lo, re_row * 2 * M + i, nr);
-                    store_split(e.out_hi, e.out_lo, im_row * 2 * M + M + i, nr);
-                    e.acc[re_row * M + i] += nr;
-                }
-            }
-            break;
-        }
-        case EPI_HSPOT_F32: {
-            // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
-            const int64_t w = r >> 1, c = r & 1;
-            const int64_t i0 = c0 / e.M, k0 = c0 % e.M;
-            if (full && k0 + 32 <= e.M) {
-                float* o = e.out_f32 + (w * e.M + i0) * (2 * e.M) + c * e.M + k0;
-                if (aligned16(o)) {
-#pragma unroll
-                    for (int g = 0; g < 8; ++g)
-                        reinterpret_cast<float4*>(o)[g] =
-                            make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
-                } else {
-                    for (int j = 0; j < 32; ++j) o[j] = v[j];
-                }
-            } else {
-                for (int j = 0; j < ncol; ++j) {
-                    const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
-                    e.out_f32[(w * e.M + i) * (2 * e.M) + c * e.M + k] = v[j];
-                }
-            }
-            break;
-        }
-        case EPI_TAYLOR_F32: {
-            // batch b = walker; row r = (s*2 + c)*N + j of the doubled operand; C = (P A^T)_c[j][i].
-            // New term i*scale*C: C_re (c = 0) -> imaginary row, C_im (c = 1) -> real row, negated.
-            const int64_t N = e.N, M = e.M;
-            const int64_t s = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
-            const int64_t ws = (int64_t)b * 2 + s;
-            const int64_t row = (ws * 2 + (c == 0 ? 1 : 0)) * N + jj;
-            const float sg = c == 0 ? e.scale : -e.scale;
-            float* o = e.out_f32 + row * M + c0;
-            if (full && aligned16(o)) {
-#pragma unroll
-                for (int g = 0; g < 8; ++g)
-                    reinterpret_cast<float4*>(o)[g] =
-                        make_float4(sg * v[4 * g], sg * v[4 * g + 1], sg * v[4 * g + 2], sg * v[4 * g + 3]);
-                acc32(e.acc, row * M + c0, v, sg, true);
-            } else {
-                for (int j = 0; j < ncol; ++j) {
-                    o[j] = sg * v[j];
-                    e.acc[row * M + c0 + j] += sg * v[j];
-                }
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) o[j] = v[j];
             }
             break;
         }
@@ -305,8 +116,19 @@ __device__ void epilogue_row(const EpiParams& e, int b, int64_t r, int64_t c0, c
     }
 }
 
-// FP64 epilogue of the three-slice GEMM: 32 consecutive columns [c0, c0+32) of row r.
-__device__ void epilogue_row64(const EpiParams& e, int b, int64_t r, int64_t c0, const double (&v)[32]) {
+// Epilogue of the three-slice GEMM: 32 consecutive columns [c0, c0+32) of row r, each value a
+// float-float pair vh + vl.
+__device__ __forceinline__ void st32f(float* o, const float (&v)[32]) {
+    if (aligned16(o)) {
+#pragma unroll
+        for (int g = 0; g < 8; ++g)
+            reinterpret_cast<float4*>(o)[g] = make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+    } else {
+        for (int j = 0; j < 32; ++j) o[j] = v[j];
+    }
+}
+__device__ void epilogue_row3(const EpiParams& e, int b, int64_t r, int64_t c0, const float (&vh)[32],
+                              const float (&vl)[32]) {
     if (r >= e.rows_valid) return;
     const int ncol = (int)(e.cols_valid - c0 < 32 ? e.cols_valid - c0 : 32);
     if (ncol <= 0) return;
@@ -316,57 +138,48 @@ __device__ void epilogue_row64(const EpiParams& e, int b, int64_t r, int64_t c0,
             double* o = e.out_f64 + b * e.ob + r * e.ld + c0;
             if (full && aligned16(o)) {
 #pragma unroll
-                for (int g = 0; g < 16; ++g) reinterpret_cast<double2*>(o)[g] = make_double2(v[2 * g], v[2 * g + 1]);
+                for (int g = 0; g < 16; ++g)
+                    reinterpret_cast<double2*>(o)[g] =
+                        make_double2((double)vh[2 * g] + (double)vl[2 * g], (double)vh[2 * g + 1] + (double)vl[2 * g + 1]);
             } else {
-                for (int j = 0; j < ncol; ++j) o[j] = v[j];
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) o[j] = (double)vh[j] + (double)vl[j];
             }
             break;
         }
-        case EPI3_HSPOT: {
+        case EPI3_FF: {
+            const int64_t off = b * e.ob + r * e.ld + c0;
+            if (full) {
+                st32f(e.out_f32 + off, vh);
+                st32f(e.out_lo32 + off, vl);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) {
+                        e.out_f32[off + j] = vh[j];
+                        e.out_lo32[off + j] = vl[j];
+                    }
+            }
+            break;
+        }
+        case EPI3_HSPOT_FF: {
             // row r = 2 w + c (coefficient re/im), column = i*M + k  ->  [w][i][c*M + k]
             const int64_t w = r >> 1, c = r & 1;
             const int64_t i0 = c0 / e.M, k0 = c0 % e.M;
             if (full && k0 + 32 <= e.M) {
-                double* o = e.out_f64 + (w * e.M + i0) * (2 * e.M) + c * e.M + k0;
-                if (aligned16(o)) {
-#pragma unroll
-                    for (int g = 0; g < 16; ++g) reinterpret_cast<double2*>(o)[g] = make_double2(v[2 * g], v[2 * g + 1]);
-                } else {
-                    for (int j = 0; j < 32; ++j) o[j] = v[j];
-                }
+                const int64_t off = (w * e.M + i0) * (2 * e.M) + c * e.M + k0;
+                st32f(e.out_f32 + off, vh);
+                st32f(e.out_lo32 + off, vl);
             } else {
-                for (int j = 0; j < ncol; ++j) {
-                    const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
-                    e.out_f64[(w * e.M + i) * (2 * e.M) + c * e.M + k] = v[j];
-                }
-            }
-            break;
-        }
-        case EPI3_TAYLOR: {
-            // batch b = walker; row r = (s*2 + c)*N + j of the doubled operand; new term i*scale*C:
-            // C_re (c = 0) -> imaginary row, C_im (c = 1) -> real row, negated
-            const int64_t N = e.N, M = e.M;
-            const int64_t s = r / (2 * N), rem = r % (2 * N), c = rem / N, jj = rem % N;
-            const int64_t ws = (int64_t)b * 2 + s;
-            const int64_t row = (ws * 2 + (c == 0 ? 1 : 0)) * N + jj;
-            const double sg = c == 0 ? e.scale64 : -e.scale64;
-            double* o = e.out_f64 + row * M + c0;
-            double* a = e.acc64 + row * M + c0;
-            if (full && aligned16(o) && aligned16(a)) {
 #pragma unroll
-                for (int g = 0; g < 16; ++g) {
-                    const double2 t = make_double2(sg * v[2 * g], sg * v[2 * g + 1]);
-                    reinterpret_cast<double2*>(o)[g] = t;
-                    double2 q = reinterpret_cast<double2*>(a)[g];
-                    q.x += t.x;
-                    q.y += t.y;
-                    reinterpret_cast<double2*>(a)[g] = q;
-                }
-            } else {
-                for (int j = 0; j < ncol; ++j) {
-                    o[j] = sg * v[j];
-                    a[j] += sg * v[j];
-                }
+                for (int j = 0; j < 32; ++j)
+                    if (j < ncol) {
+                        const int64_t col = c0 + j, i = col / e.M, k = col % e.M;
+                        const int64_t off = (w * e.M + i) * (2 * e.M) + c * e.M + k;
+                        e.out_f32[off] = vh[j];
+                        e.out_lo32[off] = vl[j];
+                    }
             }
             break;
         }
@@ -653,8 +466,10 @@ __device__ __forceinline__ int named_bar_and(int pred) {
 // (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  The epilogue drains both
 // accumulators into a 128 x 256 fp32 tile in shared memory (XOR-swizzled within 32-column groups
 // so row and column reads are both conflict-free), releases TMEM at once, and computes the
-// traces from shared memory while the tensor cores run the next tile.  The operands come from
-// L2 at ~1 us latency; the narrower chunks keep three stages in flight instead of one.
+// traces from shared memory while the tensor cores run the next tile.  With the walker-spin
+// window below, both operands are L2 hits and the wider chunks (half the barrier round trips
+// per flop) are faster: at M = 512, N = 128, Nchol = 2560, 2048 walker-spins one launch takes
+// 463 ms with BK = 32 and an 8-group window against 513 ms with BK = 16 and a 128-group one.
 constexpr int kEStageRing = 96 * 1024;
 template <int BK>
 struct ECfg {
@@ -664,7 +479,11 @@ struct ECfg {
     static constexpr int kStages = kEStageRing / kStageBytes;
     static_assert(kStages >= 2 && kStages <= 4, "stage ring");
 };
-constexpr int kEBKDefault = 16;
+constexpr int kEBKDefault = 32;
+// Walker-spin groups per L2 window: the window's Theta pairs (512 KB per group at M = 512) stay
+// in L2 while the L~ pairs stream through it once per window; the 152 CTAs then share ~19 L~
+// n-groups and 8 Theta groups at a time.
+constexpr int kEWsSuperDefault = 8;
 constexpr int kETileFloats = 128 * 256;
 
 template <int BK>
@@ -1086,31 +905,6 @@ __global__ void __launch_bounds__(256) split_rows_f32_kernel(const float* src, i
 // ~1e-9 of |x_a||x_b|.
 constexpr double kS3 = 1.0 / 128.0;
 
-__global__ void __launch_bounds__(256) split3_rows_kernel(const double* src, int64_t rows, int64_t K, __half* h,
-                                                          __half* m, __half* l, float* scale) {
-    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
-    const double* x = src + r * K;
-    double ss = 0.0;
-    for (int64_t k = lane; k < K; k += 32) ss += x[k] * x[k];
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const double nrm = sqrt(ss);
-    int e = 0;
-    if (nrm > 0.0) frexp(nrm, &e);
-    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
-    if (lane == 0) scale[r] = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
-    for (int64_t k = lane; k < K; k += 32) {
-        const double y = x[k] * inv;
-        const double hv = rint(y);
-        const double rr = (y - hv) * 128.0;
-        const double mv = rint(rr);
-        h[r * K + k] = __double2half(hv);
-        m[r * K + k] = __double2half(mv);
-        l[r * K + k] = __double2half(rr - mv);
-    }
-}
-
 constexpr int kG3ABytes = kBM * kBK * 2;          // one plane, 128 rows x 64
 constexpr int kG3BBytes = 128 * kBK * 2;          // B tile: 128 rows
 constexpr int kG3StageBytes = 3 * (kG3ABytes + kG3BBytes);   // 96 KB
@@ -1231,28 +1025,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int az = three_d ? (b / sh.am.div) % sh.am.mod : 0;
             const int bz = three_d ? (b / sh.bm.div) % sh.bm.mod : 0;
             const int64_t r = (int64_t)rt * kBM + g4 * 32 + lane;
-            const double sa = r < sh.a_rows ? (double)sh.a_scale[(int64_t)az * sh.a_rows + r] : 0.0;
+            const float sa = r < sh.a_rows ? sh.a_scale[(int64_t)az * sh.a_rows + r] : 0.0f;
+            // value = sa sb (acc1 + 2^-7 (acc2 + acc3) + 2^-14 acc4) as the float-float pair
+            // hi = sa sb acc1 (an integer times powers of two: exact), lo = sa sb (the rest);
+            // the row and column scales are powers of two, so both products are exact
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 uint32_t a1[32], a2[32];
-                tmem_ld32_nw(tb + c * 32, a1);
-                tmem_ld32_nw(tb + 128 + c * 32, a2);
+                float vh[32], vl[32];
+                tmem_ld32_nw(tb + 128 + c * 32, a1);   // acc2
+                tmem_ld32_nw(tb + 256 + c * 32, a2);   // acc3
                 tmem_ld_wait();
-                double v[32];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = (double)__uint_as_float(a1[q]) + kS3 * (double)__uint_as_float(a2[q]);
-                tmem_ld32_nw(tb + 256 + c * 32, a1);
-                tmem_ld32_nw(tb + 384 + c * 32, a2);
+                for (int q = 0; q < 32; ++q) vl[q] = __uint_as_float(a1[q]) + __uint_as_float(a2[q]);
+                tmem_ld32_nw(tb + c * 32, a1);         // acc1
+                tmem_ld32_nw(tb + 384 + c * 32, a2);   // acc4
                 tmem_ld_wait();
                 const int64_t c0 = (int64_t)ct * 128 + c * 32;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int64_t col = c0 + q;
-                    const double sb = col < sh.b_rows ? (double)sh.b_scale[(int64_t)bz * sh.b_rows + col] : 0.0;
-                    v[q] = (v[q] + kS3 * (double)__uint_as_float(a1[q]) + kS3 * kS3 * (double)__uint_as_float(a2[q])) *
-                           sa * sb;
+                    const float sc = col < sh.b_rows ? sa * sh.b_scale[(int64_t)bz * sh.b_rows + col] : 0.0f;
+                    vl[q] = fmaf((float)kS3, vl[q], (float)(kS3 * kS3) * __uint_as_float(a2[q])) * sc;
+                    vh[q] = __uint_as_float(a1[q]) * sc;
                 }
-                epilogue_row64(epi, b, r, c0, v);
+                epilogue_row3(epi, b, r, c0, vh, vl);
             }
             tc_fence_before();
             mbar_arrive(&ctl->tempty[0]);
@@ -1267,38 +1064,155 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
 }
 
-// doubled three-slice split of a planar FP64 term (see split3_doubled)
-__global__ void __launch_bounds__(256) split3_doubled_kernel(const double* P, int64_t WS, int N, int M, __half* h,
-                                                             __half* m, __half* l, float* scale) {
+// Row scale 2^(e-11) from a float sum of squares, raised by 2^-10 so ||x||_2 < 2^e holds.
+__device__ __forceinline__ void row_scale(float ss, float& inv, float& sc) {
+    const float nrm = sqrtf(ss) * (1.0f + 0x1p-10f);
+    int e = 0;
+    if (nrm > 0.f) frexpf(nrm, &e);
+    inv = nrm > 0.f ? ldexpf(1.0f, 11 - e) : 0.f;
+    sc = nrm > 0.f ? ldexpf(1.0f, e - 11) : 1.0f;
+}
+
+// Three slices of FP64 rows (same slicing as split3_rows_ff_kernel).  One warp per row: pass 1
+// finds the row's largest exponent and its sum of squares relative to it (fp32, rescaled as
+// the maximum grows, then merged across lanes), which fixes the row scale 2^(e-11) with
+// ||x||_2 < 2^e; pass 2 forms y = x 2^(11-e) as a float pair and slices it.
+__global__ void __launch_bounds__(256) split3_rows_kernel(const double* src, int64_t rows, int64_t K, __half* h,
+                                                          __half* m, __half* l, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const double* x = src + r * K;
+    int emax = 0;          // largest biased exponent met (0: none)
+    float ss = 0.f;        // sum of squares in units of 2^(2 (emax - 1023))
+    bool bad = false;
+    for (int64_t k = lane; k < K; k += 32) {
+        const uint32_t bh = (uint32_t)((unsigned long long)__double_as_longlong(x[k]) >> 32);
+        const int E = (int)((bh >> 20) & 0x7ffu);
+        if (E == 0x7ff) bad = true;
+        if (E == 0 || E == 0x7ff) continue;
+        if (E > emax) {
+            const int d = 2 * (emax - E);   // rescale the sum to the new maximum
+            ss = (emax == 0 || d < -126) ? 0.f : ss * __uint_as_float((uint32_t)(d + 127) << 23);
+            emax = E;
+        }
+        const int d = E - emax;             // <= 0
+        const float v = d < -60 ? 0.f : __uint_as_float(0x3f800000u | ((bh & 0xfffffu) << 3)) *
+                                            __uint_as_float((uint32_t)(d + 127) << 23);
+        ss = fmaf(v, v, ss);
+    }
+    int wmax = emax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    {
+        const int d = 2 * (emax - wmax);
+        ss = (emax == 0 || d < -126) ? 0.f : ss * __uint_as_float((uint32_t)(d + 127) << 23);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    bad = __any_sync(0xffffffffu, bad);
+    // ||x|| < 2^(en) 2^(wmax - 1023); the 2^-10 margin covers the truncated mantissas and the
+    // fp32 sum
+    int kexp = 0;
+    float sc = 1.0f;
+    if (wmax > 0 && ss > 0.f) {
+        int en = 0;
+        frexpf(sqrtf(ss) * (1.0f + 0x1p-10f), &en);
+        const int e = en + wmax - 1023;
+        kexp = 11 - e;
+        sc = ldexpf(1.0f, e - 11);
+    }
+    if (bad) sc = __int_as_float(0x7fc00000);
+    if (lane == 0) scale[r] = sc;
+    const bool zero = !(wmax > 0 && ss > 0.f);
+    for (int64_t k = lane; k < K; k += 32) {
+        float yh = 0.f, yl = 0.f;
+        if (!zero) dbl_scaled_ff(x[k], kexp, yh, yl);
+        if (bad) yh = __int_as_float(0x7fc00000);
+        slice3(yh, yl, h[r * K + k], m[r * K + k], l[r * K + k]);
+    }
+}
+
+__global__ void __launch_bounds__(256) split3_rows_ff_kernel(const float* xh, const float* xl, int64_t rows, int64_t K,
+                                                             __half* h, __half* m, __half* l, float* scale) {
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    const float* a = xh + r * K;
+    const float* b = xl + r * K;
+    float ss = 0.f;
+    for (int64_t k = lane; k < K; k += 32) ss = fmaf(a[k], a[k], ss);
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    float inv, sc;
+    row_scale(ss, inv, sc);
+    if (lane == 0) scale[r] = sc;
+    for (int64_t k = lane; k < K; k += 32) slice3(a[k] * inv, b[k] * inv, h[r * K + k], m[r * K + k], l[r * K + k]);
+}
+
+// Float-float helpers: exact product error and sum error (FMA-based).
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& ph, float& pl) {
+    ph = ah * bh;
+    pl = fmaf(ah, bh, -ph) + (ah * bl + al * bh);
+}
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& sh, float& sl) {
+    sh = ah + bh;
+    const float v = sh - ah;
+    sl = ((ah - (sh - v)) + (bh - v)) + (al + bl);
+}
+
+// One warp per (ws, j): P = i s C (or P = Pacc when C is null), Pacc += P, doubled three-slice
+// split of P when `split`.
+__global__ void __launch_bounds__(256) taylor_step_ff_kernel(const float* Ch, const float* Cl, float s_hi, float s_lo,
+                                                             float* Ph, float* Pl, int64_t WS, int N, int M, int split,
+                                                             __half* h, __half* m, __half* l, float* scale) {
     const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // (ws, j)
     const int lane = threadIdx.x & 31;
     if (r >= WS * N) return;
     const int64_t ws = r / N;
     const int j = (int)(r % N);
-    const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;
-    const double* pr = P + row0 * M;
-    const double* pi = P + row1 * M;
-    double ss = 0.0;
-    for (int k = lane; k < M; k += 32) ss += pr[k] * pr[k] + pi[k] * pi[k];
+    const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;   // re, im rows
+    float ss = 0.f;
+    // pass 1: P, Pacc update, row norm (P is recomputed in pass 2: M values do not fit registers)
+    for (int k = lane; k < M; k += 32) {
+        float prh, prl, pih, pil;
+        if (Ch) {
+            ff_mul(-Ch[row1 * M + k], -Cl[row1 * M + k], s_hi, s_lo, prh, prl);   // Re P = -s Im C
+            ff_mul(Ch[row0 * M + k], Cl[row0 * M + k], s_hi, s_lo, pih, pil);     // Im P =  s Re C
+            float ah, al;
+            ff_add(Ph[row0 * M + k], Pl[row0 * M + k], prh, prl, ah, al);
+            Ph[row0 * M + k] = ah;
+            Pl[row0 * M + k] = al;
+            ff_add(Ph[row1 * M + k], Pl[row1 * M + k], pih, pil, ah, al);
+            Ph[row1 * M + k] = ah;
+            Pl[row1 * M + k] = al;
+        } else {
+            prh = Ph[row0 * M + k];
+            pih = Ph[row1 * M + k];
+        }
+        ss = fmaf(prh, prh, fmaf(pih, pih, ss));
+    }
+    if (!split) return;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    const double nrm = sqrt(ss);
-    int e = 0;
-    if (nrm > 0.0) frexp(nrm, &e);
-    const double inv = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
-    const float sc = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+    float inv, sc;
+    row_scale(ss, inv, sc);
     if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
     const int64_t K2 = 2LL * M;
     for (int k = lane; k < M; k += 32) {
-        const double yr = pr[k] * inv, yi = pi[k] * inv;
-        const double hr = rint(yr), hI = rint(yi);
-        const double rr = (yr - hr) * 128.0, ri = (yi - hI) * 128.0;
-        const double mr = rint(rr), mI = rint(ri);
-        const __half Hr = __double2half(hr), Mr = __double2half(mr), Lr = __double2half(rr - mr);
-        const __half Hi = __double2half(hI), Mi = __double2half(mI), Li = __double2half(ri - mI);
-        h[row0 * K2 + k] = Hr;  m[row0 * K2 + k] = Mr;  l[row0 * K2 + k] = Lr;                  // Re
-        h[row0 * K2 + M + k] = __hneg(Hi);  m[row0 * K2 + M + k] = __hneg(Mi);  l[row0 * K2 + M + k] = __hneg(Li);  // -Im
-        h[row1 * K2 + k] = Hi;  m[row1 * K2 + k] = Mi;  l[row1 * K2 + k] = Li;                  // Im
-        h[row1 * K2 + M + k] = Hr;  m[row1 * K2 + M + k] = Mr;  l[row1 * K2 + M + k] = Lr;      // Re
+        float prh, prl, pih, pil;
+        if (Ch) {
+            ff_mul(-Ch[row1 * M + k], -Cl[row1 * M + k], s_hi, s_lo, prh, prl);
+            ff_mul(Ch[row0 * M + k], Cl[row0 * M + k], s_hi, s_lo, pih, pil);
+        } else {
+            prh = Ph[row0 * M + k]; prl = Pl[row0 * M + k];
+            pih = Ph[row1 * M + k]; pil = Pl[row1 * M + k];
+        }
+        __half Hr, Mr, Lr, Hi, Mi, Li;
+        slice3(prh * inv, prl * inv, Hr, Mr, Lr);
+        slice3(pih * inv, pil * inv, Hi, Mi, Li);
+        h[row0 * K2 + k] = Hr;  m[row0 * K2 + k] = Mr;  l[row0 * K2 + k] = Lr;                     // Re
+        h[row0 * K2 + M + k] = __hneg(Hi);  m[row0 * K2 + M + k] = __hneg(Mi);  l[row0 * K2 + M + k] = __hneg(Li);
+        h[row1 * K2 + k] = Hi;  m[row1 * K2 + k] = Mi;  l[row1 * K2 + k] = Li;                     // Im
+        h[row1 * K2 + M + k] = Hr;  m[row1 * K2 + M + k] = Mr;  l[row1 * K2 + M + k] = Lr;          // Re
     }
 }
 
@@ -1429,7 +1343,7 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
     if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
-    const int BK = launch_policy().energy_bk == 32 ? 32 : kEBKDefault;
+    const int BK = launch_policy().energy_bk != 0 ? launch_policy().energy_bk : kEBKDefault;
     const int swz = 2 * BK;   // bytes per swizzled row of the K chunk
     CUtensorMap m[4];
     AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, swz));
@@ -1444,7 +1358,8 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     es.nws = nws;
     es.n_groups = (Nchol + es.G - 1) / es.G;
     es.ws_groups = (nws + es.G - 1) / es.G;
-    es.ws_super = std::min(es.ws_groups, 128);
+    es.ws_super = std::min(es.ws_groups, launch_policy().energy_ws_super > 0 ? launch_policy().energy_ws_super
+                                                                                : kEWsSuperDefault);
     es.tiles = (int64_t)es.n_groups * es.ws_groups;
     es.nk = M / BK;
     es.lolo = terms == 4 ? 1 : 0;
@@ -1540,12 +1455,22 @@ int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, c
     return tc_gemm3(A, BatchMap{1, nws}, B, BatchMap{1, 1}, rows, N, M, nws, e, flags, st);
 }
 
-void split3_doubled(const double* P, int64_t WS, int N, int M, bf16* h, bf16* m, bf16* l, float* scale,
-                    cudaStream_t st) {
+void split3_rows_ff(const float* hi, const float* lo, int64_t rows, int64_t K, bf16* h, bf16* m, bf16* l,
+                    float* scale, cudaStream_t st) {
+    if (rows <= 0) return;
+    count_launch();
+    split3_rows_ff_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+        hi, lo, rows, K, reinterpret_cast<__half*>(h), reinterpret_cast<__half*>(m), reinterpret_cast<__half*>(l),
+        scale);
+}
+
+void taylor_step_ff(const float* Ch, const float* Cl, float s_hi, float s_lo, float* Ph, float* Pl, int64_t WS,
+                    int N, int M, bool split, bf16* h, bf16* m, bf16* l, float* scale, cudaStream_t st) {
     if (WS * N <= 0) return;
     count_launch();
-    split3_doubled_kernel<<<(unsigned)((WS * N + 7) / 8), 256, 0, st>>>(
-        P, WS, N, M, reinterpret_cast<__half*>(h), reinterpret_cast<__half*>(m), reinterpret_cast<__half*>(l), scale);
+    taylor_step_ff_kernel<<<(unsigned)((WS * N + 7) / 8), 256, 0, st>>>(
+        Ch, Cl, s_hi, s_lo, Ph, Pl, WS, N, M, split ? 1 : 0, reinterpret_cast<__half*>(h),
+        reinterpret_cast<__half*>(m), reinterpret_cast<__half*>(l), scale);
 }
 
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,

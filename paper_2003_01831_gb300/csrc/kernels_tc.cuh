@@ -40,20 +40,45 @@ struct BatchMap {
     int mod = 1 << 30;
 };
 
-// Output tile epilogues of the generic GEMM (kind selects the write pattern).
+// Float pair of x * 2^k read from the bits of the double x: hi = its sign, exponent and leading
+// 24 significant bits, lo = its remaining 29 bits rounded to float, so hi + lo = x 2^k to
+// 2^-47 relative, using integer and fp32 instructions only (GB300's FP64 pipe is ~1/64 of its
+// fp32 pipe).  k must keep |x 2^k| below 2^127; results below 2^-100 are flushed to zero and
+// inf / NaN give NaN.
+__device__ __forceinline__ void dbl_scaled_ff(double x, int k, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
+    const int E = (int)((bh >> 20) & 0x7ffu);
+    const int ey = E - 1023 + k;
+    if (E == 0x7ff) { hi = __int_as_float(0x7fc00000); lo = 0.f; return; }
+    if (E == 0 || ey < -100) { hi = 0.f; lo = 0.f; return; }
+    const uint32_t sign = bh & 0x80000000u;
+    hi = __uint_as_float(sign | ((uint32_t)(ey + 127) << 23) | ((bh & 0xfffffu) << 3) | (bl >> 29));
+    const int el = ey - 52;   // weight of the lowest fraction bit
+    lo = el < -126 ? 0.f : __uint2float_rn(bl & 0x1fffffffu) * __uint_as_float((uint32_t)(el + 127) << 23);
+    if (sign) lo = -lo;
+}
+
+// Three slices of a float-float value (yh + yl already divided by the row scale, |y| < 2^11):
+// h = rint(yh), r = (yh - h) + yl (|r| <= 0.5 + 2^-13), m = rint(128 r), l = fp16(128 r - m).
+__device__ __forceinline__ void slice3(float yh, float yl, __half& h, __half& m, __half& l) {
+    const float hv = rintf(yh);
+    const float rr = ((yh - hv) + yl) * 128.0f;
+    const float mv = rintf(rr);
+    h = __float2half_rn(hv);
+    m = __float2half_rn(mv);
+    l = __float2half_rn(rr - mv);
+}
+
+// Output tile epilogues (kind selects the write pattern): EPI_F32 for the two-slice GEMM.
 enum EpiKind : int {
     EPI_F32 = 0,       // out_f32[b*ob + r*ld + c]
-    EPI_SPLIT = 1,     // out_hi/out_lo[b*ob + r*ld + c]  (plain bf16 pair)
-    EPI_HSPOT = 2,     // A potential: row (w, c), col (i, k) -> hi/lo[w][i][c*M + k]
-    EPI_BFIRST = 3,    // B Phi: doubled operand for the Taylor series + accumulator init
-    EPI_TAYLOR = 4,    // (i s) P A^T: doubled operand of the next term + accumulator update
-    EPI_F64 = 5,       // out_f64[b*ob + r*ld + c]
-    EPI_HSPOT_F32 = 6, // A potential in fp32: row (w, c), col (i, k) -> out_f32[w][i][c*M + k]
-    EPI_TAYLOR_F32 = 7,// next Taylor term i*scale*C in fp32 (planar rows) + accumulator update
-    // three-slice GEMM (tc_gemm3) epilogues, FP64 values:
+    // three-slice GEMM (tc_gemm3) epilogues.  Values leave the accumulators as float-float
+    // pairs (hi + lo, each exact in its scaling); "FF" outputs keep them as two fp32 planes
+    // (out_f32 = hi, out_lo32 = lo), EPI3_F64 adds them in FP64.
     EPI3_F64 = 8,      // out_f64[b*ob + r*ld + c]
-    EPI3_HSPOT = 9,    // A potential: row (w, c), col (i, k) -> out_f64[w][i][c*M + k]
-    EPI3_TAYLOR = 10,  // next Taylor term i*scale*C -> out_f64 (planar rows), acc64 += term
+    EPI3_FF = 9,       // out_f32 / out_lo32 [b*ob + r*ld + c]
+    EPI3_HSPOT_FF = 10,// A potential: row (w, c), col (i, k) -> [w][i][c*M + k] (both planes)
 };
 
 struct EpiParams {
@@ -61,14 +86,9 @@ struct EpiParams {
     int64_t rows_valid = 0, cols_valid = 0;  // per batch
     int64_t ld = 0, ob = 0;                  // row / batch strides of the output (elements)
     float* out_f32 = nullptr;
-    bf16* out_hi = nullptr;
-    bf16* out_lo = nullptr;
     double* out_f64 = nullptr;
-    float* acc = nullptr;                    // Taylor accumulator (fp32)
-    double* acc64 = nullptr;                 // Taylor accumulator (FP64, three-slice GEMM)
-    int M = 0, N = 0;                        // orbitals, electrons per spin
-    float scale = 1.0f;                      // Taylor factor sqrt(tau)/k
-    double scale64 = 1.0;                    // the same in FP64 (three-slice GEMM)
+    float* out_lo32 = nullptr;               // low plane of float-float outputs (EPI3_FF*)
+    int M = 0;                               // orbitals (EPI3_HSPOT_FF column split)
 };
 
 // Three fp16 slices of a matrix [batch][rows][K] (planes h, m, l; see split3_rows) with
@@ -85,10 +105,15 @@ struct Split3 {
 // exactness of the h*m sums (still ~1e-8).
 int tc_gemm3(const Split3& A, BatchMap amap, const Split3& B, BatchMap bmap, int64_t rows, int64_t cols, int64_t K,
              int nbatch, const EpiParams& epi, unsigned* flags, cudaStream_t st);
-// Doubled complex operand of a planar FP64 term P [WS][2][N][M] as three slices:
-// row (ws, 0, j) = [Re P_j | -Im P_j], row (ws, 1, j) = [Im P_j | Re P_j] (length 2M).
-void split3_doubled(const double* P, int64_t WS, int N, int M, bf16* h, bf16* m, bf16* l, float* scale,
-                    cudaStream_t st);
+// Three-slice split of float-float rows (hi, lo planes [rows][K]).
+void split3_rows_ff(const float* hi, const float* lo, int64_t rows, int64_t K, bf16* h, bf16* m, bf16* l,
+                    float* scale, cudaStream_t st);
+// One Taylor step on float-float planar data [WS][2][N][M] (hi, lo planes):
+// P = i s C with s = s_hi + s_lo; Pacc += P (hi, lo planes); when `split`, P's doubled operand
+// row (ws, 0, j) = [Re P_j | -Im P_j], row (ws, 1, j) = [Im P_j | Re P_j] (length 2M) as three
+// slices.  With C == nullptr, P is taken from Pacc itself (the first term, s = 1, no update).
+void taylor_step_ff(const float* Ch, const float* Cl, float s_hi, float s_lo, float* Ph, float* Pl, int64_t WS,
+                    int N, int M, bool split, bf16* h, bf16* m, bf16* l, float* scale, cudaStream_t st);
 
 // C[b] = A[b] . B[b]^T (split bf16, fp32 accumulation in TMEM), 128 x BN tiles.
 // exact = true needs row-scaled A and B and BN = 128.

@@ -16,14 +16,17 @@
 //   Lt     [Nchol][N][M]   Ltilde_n = Psi^T L_n (trial real, same for both spins): row-scaled
 //          pair for the energy; Ltp the same rows over all N*M entries (force bias only)
 //   LT3    [M*M][Nchol]    L transposed, three slices (HS potential GEMM operand)
-//   A64    [W][M][2M]      HS potential sum_n c_n L_n, re | im columns, FP64 (+ three slices)
-//   Pk64   [W][2][2][N][M] Taylor term, FP64; PD3 [W][2][2N][2M] its doubled form
-//                          [[Re, -Im], [Im, Re]] as three slices
-//   Pacc64 [W][2][2][N][M] Taylor sum, FP64 (three slices for the final B product)
+//   A      [W][M][2M]      HS potential sum_n c_n L_n, re | im columns, float-float (+ three
+//                          slices)
+//   C      [W][2][2][N][M] product P_{k-1} A^T of a Taylor step, float-float; PD3
+//                          [W][2][2N][2M] the doubled form [[Re, -Im], [Im, Re]] of the term
+//                          P_k = (i sqrt(tau)/k) C as three slices
+//   Pacc   [W][2][2][N][M] Taylor sum, float-float (three slices for the final B product)
 // Contractions use row-scaled fp16 operands with exact accumulation of the leading products
 // (kernels_tc.cu): the Green's-function and energy contractions with two slices (hi*hi summed
 // exactly, remainders in a second accumulator), the overlap and the whole propagation with
-// three slices and FP64 intermediates (~1e-9), because the walkers' overlaps set the weights.
+// three slices and float-float (hi + lo fp32) intermediates (~1e-9), because the walkers'
+// overlaps set the weights; the float-float arithmetic keeps that work off the narrow FP64 pipe.
 #include <algorithm>
 #include <utility>
 #include <vector>
@@ -74,13 +77,13 @@ struct TcState {
     double* cfp = nullptr;                 // [W][2][Nchol] HS coefficients, planar
     bf16* cf3[3] = {nullptr, nullptr, nullptr};
     float* cf3_s = nullptr;
-    double* A64 = nullptr;                 // [W][M][2M] HS potential, re | im columns
+    float *A_hi = nullptr, *A_lo = nullptr;   // [W][M][2M] HS potential (re | im columns), float-float
     bf16* A3[3] = {nullptr, nullptr, nullptr};
     float* A3_s = nullptr;
-    double* Pk64 = nullptr;                // [W][2][2][N][M] Taylor term
-    bf16* PD3[3] = {nullptr, nullptr, nullptr};   // its doubled form [W][2][2N][2M]
+    float *C_hi = nullptr, *C_lo = nullptr;   // [W][2][2][N][M] product P_{k-1} A^T of a Taylor step
+    bf16* PD3[3] = {nullptr, nullptr, nullptr};   // doubled form of the term [W][2][2N][2M]
     float* PD3_s = nullptr;
-    double* Pacc64 = nullptr;              // Taylor sum
+    float *Pacc_hi = nullptr, *Pacc_lo = nullptr;   // Taylor sum, float-float
     bf16* Pacc3[3] = {nullptr, nullptr, nullptr};
     float* Pacc3_s = nullptr;
     bf16 *Pacc_h = nullptr, *Pacc_l = nullptr;   // scratch pair of the force-bias-only contraction
@@ -165,49 +168,89 @@ __global__ void phiT_to_canon_kernel(const double* PhiT, int s, int W, int M, in
     const int64_t base = (((int64_t)w * 2 + s) * 2) * N * M;
     Phi[i] = cplx{PhiT[base + (int64_t)j * M + k], PhiT[base + (int64_t)N * M + (int64_t)j * M + k]};
 }
-// PhiT FP64 [WS][2N][M] -> Phi [WS][M][2N] row-scaled fp16 pair (row = orbital k over the 2N
-// values re | im).  Block = (32 orbitals, one walker-spin); the 2N x 32 tile sits in
-// shared memory, each orbital's scale comes from the 2-norm of its column of the tile.
+// PhiT FP64 [WS][2N][M] -> Phi [WS][M][2N] row-scaled fp16 pair, or three slices (SLICES = 3,
+// as split3_rows; planes hi, lo, lo2), row = orbital k over the 2N values re | im.  Block = (32 orbitals, one walker-spin); the 2N x 32 tile sits in
+// shared memory, each orbital's scale comes from the 2-norm of its column of the tile.  The
+// norm (largest exponent per column, then fp32 squares relative to it) and the split (the
+// scaled value as a float pair from the double's bits) use no FP64 instructions.
+template <int SLICES>
 __global__ void __launch_bounds__(kT) phi_untranspose_split_kernel(const double* PhiT, int M, int N2, __half* hi,
-                                                                     __half* lo, float* scale) {
+                                                                     __half* lo, __half* lo2, float* scale) {
     extern __shared__ double tile[];  // [N2][33]
-    __shared__ double cmax[8][32];
-    __shared__ double inv_s[32];
+    __shared__ int cexp[8][32];
+    __shared__ float css[8][32];
+    __shared__ int kexp[32];
+    __shared__ int cbad[32];
     const int64_t ws = blockIdx.y;
     const int k0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const double* src = PhiT + ws * (int64_t)N2 * M;
-    double m = 0.0;
+    int emax = 0, bad = 0;
     for (int r = ty; r < N2; r += 8) {
         const int k = k0 + tx;
         const double v = k < M ? src[(int64_t)r * M + k] : 0.0;
         tile[r * 33 + tx] = v;
-        m += v * v;
+        const int E = (int)(((uint32_t)((unsigned long long)__double_as_longlong(v) >> 32) >> 20) & 0x7ffu);
+        if (E == 0x7ff) bad = 1;
+        else emax = max(emax, E);
     }
-    cmax[ty][tx] = m;
+    cexp[ty][tx] = emax;
+    cbad[tx] = 0;
+    __syncthreads();
+    if (bad) cbad[tx] = 1;
+    int cm = cexp[0][tx];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) cm = max(cm, cexp[q][tx]);
+    float ss = 0.f;
+    if (cm > 0) {
+        for (int r = ty; r < N2; r += 8) {
+            const uint32_t bh = (uint32_t)((unsigned long long)__double_as_longlong(tile[r * 33 + tx]) >> 32);
+            const int E = (int)((bh >> 20) & 0x7ffu);
+            const int d = E - cm;
+            if (E == 0 || E == 0x7ff || d < -60) continue;
+            const float v = __uint_as_float(0x3f800000u | ((bh & 0xfffffu) << 3)) *
+                            __uint_as_float((uint32_t)(d + 127) << 23);
+            ss = fmaf(v, v, ss);
+        }
+    }
+    css[ty][tx] = ss;
     __syncthreads();
     if (ty == 0) {
-        double ss = cmax[0][tx];
-        for (int q = 1; q < 8; ++q) ss += cmax[q][tx];
-        const double nrm = sqrt(ss);
-        int e = 0;
-        if (nrm > 0.0) frexp(nrm, &e);
-        inv_s[tx] = nrm > 0.0 ? ldexp(1.0, 11 - e) : 0.0;
+        float t = css[0][tx];
+        for (int q = 1; q < 8; ++q) t += css[q][tx];
         const int k = k0 + tx;
-        if (k < M) scale[ws * M + k] = nrm > 0.0 ? (float)ldexp(1.0, e - 11) : 1.0f;
+        float sc = 1.0f;
+        int kx = 0;
+        if (cm > 0 && t > 0.f) {
+            int en = 0;
+            frexpf(sqrtf(t) * (1.0f + 0x1p-10f), &en);   // margin: truncated mantissas, fp32 sum
+            const int e = en + cm - 1023;                 // ||column|| < 2^e
+            kx = 11 - e;
+            sc = ldexpf(1.0f, e - 11);
+        } else {
+            kx = 0x40000;                                 // zero column: every value flushes to 0
+        }
+        if (cbad[tx]) sc = __int_as_float(0x7fc00000);
+        kexp[tx] = kx;
+        if (k < M) scale[ws * M + k] = sc;
     }
     __syncthreads();
     // write: row k (= k0 + kk) has N2 contiguous outputs; threads along the row
     for (int kk = ty; kk < 32; kk += 8) {
         const int k = k0 + kk;
         if (k >= M) continue;
-        __half* H = hi + (ws * M + k) * (int64_t)N2;
-        __half* Lo = lo + (ws * M + k) * (int64_t)N2;
+        const int64_t o = (ws * M + k) * (int64_t)N2;
+        const int kx = kexp[kk];
         for (int r = tx; r < N2; r += 32) {
-            const double y = tile[r * 33 + kk] * inv_s[kk];
-            const double s1 = rint(y);
-            H[r] = __double2half(s1);
-            Lo[r] = __double2half(y - s1);
+            float yh = 0.f, yl = 0.f;
+            if (kx != 0x40000) dbl_scaled_ff(tile[r * 33 + kk], kx, yh, yl);
+            if (SLICES == 3) {
+                slice3(yh, yl, hi[o + r], lo[o + r], lo2[o + r]);
+            } else {
+                const float s1 = rintf(yh);
+                hi[o + r] = __float2half_rn(s1);
+                lo[o + r] = __float2half_rn((yh - s1) + yl);
+            }
         }
     }
 }
@@ -486,6 +529,47 @@ __global__ void __launch_bounds__(kT) chol_inv_kernel(cplx* G, int N, const cplx
     }
 }
 
+// Tensor-core Cholesky QR (M >= 2N): the Gram matrix and the product Phi R^-1 as three-slice
+// GEMMs on the planar real forms, FP64 results, ~1e-9 relative.
+//   Gram: C = PhiT PhiT^T per walker-spin ([2N][M] rows re | im), C [2N][2N]:
+//         G[i][j] = C[i][j] + C[N+i][N+j] + i (C[i][N+j] - C[N+i][j]).
+//   Apply: PhiT' = D PhiT with D [2N][2N] = [[Xr^T, -Xi^T], [Xi^T, Xr^T]], X = R^-1, formed as
+//         D . (PhiT^T)^T with the untransposed walker [M][2N] as the second operand.
+__global__ void gram_combine_kernel(const double* C, int WS, int N, cplx* G) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)WS * N * N) return;
+    const int64_t ws = t / ((int64_t)N * N);
+    const int i = (int)((t / N) % N), j = (int)(t % N);
+    const int64_t N2 = 2LL * N;
+    const double* c = C + ws * N2 * N2;
+    G[t] = cplx{c[i * N2 + j] + c[(N + i) * N2 + N + j], c[i * N2 + N + j] - c[(N + i) * N2 + j]};
+}
+// D [WS][2N][2N] from X = R^-1 [WS][N][N] (complex); 32 x 32 tiles of X pass through shared
+// memory so that both the reads of X rows and the writes of D rows are coalesced.
+__global__ void __launch_bounds__(kT) rinv_doubled_kernel(const cplx* X, int N, double* D) {
+    __shared__ cplx tile[32][33];
+    const int64_t ws = blockIdx.z;
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const cplx* Xw = X + ws * (int64_t)N * N;
+    for (int r = ty; r < 32; r += 8) {   // tile[i][j] = X[i0 + i][j0 + j]
+        const int i = i0 + r, j = j0 + tx;
+        tile[r][tx] = (i < N && j < N) ? Xw[(int64_t)i * N + j] : cplx{0.0, 0.0};
+    }
+    __syncthreads();
+    const int64_t N2 = 2LL * N;
+    double* Dw = D + ws * N2 * N2;
+    for (int r = ty; r < 32; r += 8) {   // D row j = j0 + r, columns i = i0 + tx
+        const int j = j0 + r, i = i0 + tx;
+        if (j >= N || i >= N) continue;
+        const cplx v = tile[tx][r];      // X[i][j]
+        Dw[j * N2 + i] = v.re;
+        Dw[j * N2 + N + i] = -v.im;
+        Dw[(N + j) * N2 + i] = v.im;
+        Dw[(N + j) * N2 + N + i] = v.re;
+    }
+}
+
 // Q^T rows: out[ws][j] = sum_{i <= j} X[i][j] * PhiT[ws] row i (complex, planar), X = R^-1
 // upper triangular.  Tile: 64 rows j x 64 orbitals k.
 __global__ void __launch_bounds__(kT) apply_rinv_kernel(const double* PhiT, const cplx* X, int M, int N,
@@ -563,16 +647,29 @@ SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t bat
 void untranspose_walkers(TcState* s, cudaStream_t st) {
     dim3 g((s->M + 31) / 32, 2 * s->W);
     const size_t sm = (size_t)2 * s->N * 33 * sizeof(double);
-    cudaFuncSetAttribute(phi_untranspose_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(phi_untranspose_split_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
-    phi_untranspose_split_kernel<<<g, kT, sm, st>>>(s->PhiT[s->cur], s->M, 2 * s->N, reinterpret_cast<__half*>(s->Phi_h),
-                                                    reinterpret_cast<__half*>(s->Phi_l), s->Phi_s);
+    phi_untranspose_split_kernel<2><<<g, kT, sm, st>>>(s->PhiT[s->cur], s->M, 2 * s->N,
+                                                       reinterpret_cast<__half*>(s->Phi_h),
+                                                       reinterpret_cast<__half*>(s->Phi_l), nullptr, s->Phi_s);
 }
 
 void refresh_operands(TcState* s, cudaStream_t st) { untranspose_walkers(s, st); }
 
 // S = Psi^T Phi for the walkers in buffer b -> Sout (inverted in place when `inverse`), per-spin
 // log-determinants -> ldout
+// Three-slice operand [batch][rows][K] of tc_gemm3
+Split3 sp3(bf16* const* p, const float* sc, int64_t K, int64_t rows, int64_t batch = 1) {
+    Split3 x;
+    for (int q = 0; q < 3; ++q) x.p[q] = p[q];
+    x.scale = sc;
+    x.K = K;
+    x.rows = rows;
+    x.batch = batch;
+    x.batch_stride = rows * K;
+    return x;
+}
+
 int overlap_logdet(afqmc_walkers* wk, int b, bool inverse, cplx* Sout, cplx* ldout, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, WS = 2 * s->W;
@@ -639,9 +736,12 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->Pacc3_s, (int64_t)W * 4 * N));
     AFQMC_TRY(talloc(s, &s->A3_s, (int64_t)W * M));
     AFQMC_TRY(talloc(s, &s->cf3_s, (int64_t)W * 2));
-    AFQMC_TRY(talloc(s, &s->Pk64, wall));
-    AFQMC_TRY(talloc(s, &s->Pacc64, wall));
-    AFQMC_TRY(talloc(s, &s->A64, (int64_t)W * M * 2 * M));
+    AFQMC_TRY(talloc(s, &s->C_hi, wall));
+    AFQMC_TRY(talloc(s, &s->C_lo, wall));
+    AFQMC_TRY(talloc(s, &s->Pacc_hi, wall));
+    AFQMC_TRY(talloc(s, &s->Pacc_lo, wall));
+    AFQMC_TRY(talloc(s, &s->A_hi, (int64_t)W * M * 2 * M));
+    AFQMC_TRY(talloc(s, &s->A_lo, (int64_t)W * M * 2 * M));
     AFQMC_TRY(talloc(s, &s->Phi_h, wall));
     AFQMC_TRY(talloc(s, &s->Phi_l, wall));
     AFQMC_TRY(talloc(s, &s->Phi_s, (int64_t)W * 2 * M));
@@ -790,60 +890,56 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     count_launch();
     coef_planar_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->coef, W, nch, s->cfp);
     split3_rows(s->cfp, 2LL * W, nch, s->cf3[0], s->cf3[1], s->cf3[2], s->cf3_s, st);
-    auto sp3 = [](bf16* const* p, const float* sc, int64_t K, int64_t rows, int64_t batch = 1) {
-        Split3 x;
-        for (int q = 0; q < 3; ++q) x.p[q] = p[q];
-        x.scale = sc;
-        x.K = K;
-        x.rows = rows;
-        x.batch = batch;
-        x.batch_stride = rows * K;
-        return x;
-    };
-    {   // A_w = sum_n c_wn L_n  -> FP64 [W][M][2M], then its three slices
+    {   // A_w = sum_n c_wn L_n  -> float-float [W][M][2M], then its three slices
         EpiParams e;
-        e.kind = EPI3_HSPOT;
+        e.kind = EPI3_HSPOT_FF;
         e.rows_valid = 2LL * W;
         e.cols_valid = MM;
         e.M = M;
-        e.out_f64 = s->A64;
+        e.out_f32 = s->A_hi;
+        e.out_lo32 = s->A_lo;
         AFQMC_TRY(tc_gemm3(sp3(s->cf3, s->cf3_s, nch, 2LL * W), BatchMap{}, sp3(s->LT3, s->LT3_s, nch, MM),
                            BatchMap{}, 2LL * W, MM, nch, 1, e, wk->flags, st));
-        split3_rows(s->A64, (int64_t)W * M, 2LL * M, s->A3[0], s->A3[1], s->A3[2], s->A3_s, st);
+        split3_rows_ff(s->A_hi, s->A_lo, (int64_t)W * M, 2LL * M, s->A3[0], s->A3[1], s->A3[2], s->A3_s, st);
     }
     const int64_t rowsAll = (int64_t)W * 4 * N;
     const int64_t WS = 2LL * W;
-    {   // P0 = B Phi -> Taylor sum (FP64)
+    {   // P0 = B Phi -> Taylor sum (float-float), then the doubled operand of the first term
         split3_rows(s->PhiT[s->cur], rowsAll, M, s->PhiT3[0], s->PhiT3[1], s->PhiT3[2], s->PhiT3_s, st);
         EpiParams e;
-        e.kind = EPI3_F64;
+        e.kind = EPI3_FF;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
         e.ld = M;
-        e.out_f64 = s->Pacc64;
+        e.out_f32 = s->Pacc_hi;
+        e.out_lo32 = s->Pacc_lo;
         AFQMC_TRY(tc_gemm3(sp3(s->PhiT3, s->PhiT3_s, M, rowsAll), BatchMap{}, sp3(s->Bh3, s->Bh3_s, M, M), BatchMap{},
                            rowsAll, M, M, 1, e, wk->flags, st));
+        taylor_step_ff(nullptr, nullptr, 1.0f, 0.0f, s->Pacc_hi, s->Pacc_lo, WS, N, M, true, s->PD3[0], s->PD3[1],
+                       s->PD3[2], s->PD3_s, st);
     }
     const double sq = sqrt(wk->tau);
     for (int k = 1; k <= wk->opts.k_taylor; ++k) {
-        // doubled operand of the previous term (P0 = the sum before any term is added)
-        split3_doubled(k == 1 ? s->Pacc64 : s->Pk64, WS, N, M, s->PD3[0], s->PD3[1], s->PD3[2], s->PD3_s, st);
-        EpiParams e;   // P_k = (i sqrt(tau) / k) P_{k-1} A^T  -> Pk64, Pacc64 += P_k
-        e.kind = EPI3_TAYLOR;
+        EpiParams e;   // C = P_{k-1} A^T (planar re / im rows)
+        e.kind = EPI3_FF;
         e.rows_valid = 4LL * N;
         e.cols_valid = M;
-        e.M = M;
-        e.N = N;
-        e.out_f64 = s->Pk64;
-        e.acc64 = s->Pacc64;
-        e.scale64 = sq / (double)k;
+        e.ld = M;
+        e.ob = 4LL * N * M;
+        e.out_f32 = s->C_hi;
+        e.out_lo32 = s->C_lo;
         AFQMC_TRY(tc_gemm3(sp3(s->PD3, s->PD3_s, 2LL * M, 4LL * N, W), BatchMap{1, W},
                            sp3(s->A3, s->A3_s, 2LL * M, M, W), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, wk->flags,
                            st));
+        // P_k = (i sqrt(tau) / k) C, Pacc += P_k, doubled operand of P_k for the next term
+        const double sk = sq / (double)k;
+        const float sh = (float)sk, sl = (float)(sk - (double)sh);
+        taylor_step_ff(s->C_hi, s->C_lo, sh, sl, s->Pacc_hi, s->Pacc_lo, WS, N, M, k < wk->opts.k_taylor, s->PD3[0],
+                       s->PD3[1], s->PD3[2], s->PD3_s, st);
     }
     const int nxt = s->cur ^ 1;
     {   // Phi' = B Pacc  (FP64 master of the proposed walkers)
-        split3_rows(s->Pacc64, rowsAll, M, s->Pacc3[0], s->Pacc3[1], s->Pacc3[2], s->Pacc3_s, st);
+        split3_rows_ff(s->Pacc_hi, s->Pacc_lo, rowsAll, M, s->Pacc3[0], s->Pacc3[1], s->Pacc3[2], s->Pacc3_s, st);
         EpiParams e;
         e.kind = EPI3_F64;
         e.rows_valid = rowsAll;
@@ -907,17 +1003,64 @@ int tc_qr(afqmc_walkers* wk, cudaStream_t st) {
     const int N = s->N, M = s->M, WS = 2 * s->W;
     if (N > kT) return fail(AFQMC_ERR_UNSUPPORTED, "tc_qr: N above the Cholesky kernel's row limit");
     const int nt = (N + kQT - 1) / kQT;
-    // Gram matrices into the (idle) overlap buffer S [WS][N][N]
-    count_launch();
-    gram_planar_kernel<<<dim3(nt, nt, WS), kT, 0, st>>>(s->PhiT[s->cur], M, N, wk->weight, s->S);
+    const int nxt = s->cur ^ 1;
+    const int64_t N2 = 2LL * N;
+    // tensor-core path: the [2N][2N] FP64 scratch of every walker-spin fits in the proposal buffer
+    const bool tc = M >= 2 * N;
+    if (tc) {
+        // Gram matrices: C = PhiT PhiT^T from the three slices of the current walkers
+        split3_rows(s->PhiT[s->cur], (int64_t)WS * N2, M, s->PhiT3[0], s->PhiT3[1], s->PhiT3[2], s->PhiT3_s, st);
+        EpiParams e;
+        e.kind = EPI3_F64;
+        e.rows_valid = N2;
+        e.cols_valid = N2;
+        e.ld = N2;
+        e.ob = N2 * N2;
+        e.out_f64 = s->PhiT[nxt];
+        AFQMC_TRY(tc_gemm3(sp3(s->PhiT3, s->PhiT3_s, M, N2, WS), BatchMap{1, WS}, sp3(s->PhiT3, s->PhiT3_s, M, N2, WS),
+                           BatchMap{1, WS}, N2, N2, M, WS, e, wk->flags, st));
+        count_launch();
+        gram_combine_kernel<<<nb((int64_t)WS * N * N), kT, 0, st>>>(s->PhiT[nxt], WS, N, s->S);
+    } else {
+        count_launch();
+        gram_planar_kernel<<<dim3(nt, nt, WS), kT, 0, st>>>(s->PhiT[s->cur], M, N, wk->weight, s->S);
+    }
+    // Cholesky factor and its inverse X = R^-1 in place of the Gram matrices (dead walkers: X = I)
     const size_t sm = (size_t)N * (N + 1) / 2 * sizeof(cplx);
     cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     count_launch();
     chol_inv_kernel<<<WS, kT, sm, st>>>(s->S, N, wk->weight, wk->flags);
-    // Q^T into the proposal buffer, then back over the current walkers (dead walkers: X = I)
-    const int nxt = s->cur ^ 1;
-    count_launch();
-    apply_rinv_kernel<<<dim3((M + kQT - 1) / kQT, nt, WS), kT, 0, st>>>(s->PhiT[s->cur], s->S, M, N, s->PhiT[nxt]);
+    // Q^T = (Phi X)^T into the proposal buffer, then back over the current walkers
+    if (tc) {
+        count_launch();
+        rinv_doubled_kernel<<<dim3((N + 31) / 32, (N + 31) / 32, WS), kT, 0, st>>>(s->S, N, s->PhiT[nxt]);
+        // D's three slices: planes of the HS-potential operand (W M 2M >= WS (2N)^2 halves for
+        // M >= 2N), scales in the Taylor operand's scale buffer (W 4N = WS 2N rows); both idle here
+        split3_rows(s->PhiT[nxt], (int64_t)WS * N2, N2, s->A3[0], s->A3[1], s->A3[2], s->PD3_s, st);
+        // the untransposed walkers [WS][M][2N] as three slices: planes of the Taylor operand
+        // (8 W N M halves each), scales in the two-slice operand's scale buffer (rebuilt below)
+        dim3 g((M + 31) / 32, WS);
+        const size_t tsm = (size_t)N2 * 33 * sizeof(double);
+        cudaFuncSetAttribute(phi_untranspose_split_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+        count_launch();
+        phi_untranspose_split_kernel<3><<<g, kT, tsm, st>>>(s->PhiT[s->cur], M, (int)N2,
+                                                            reinterpret_cast<__half*>(s->PD3[0]),
+                                                            reinterpret_cast<__half*>(s->PD3[1]),
+                                                            reinterpret_cast<__half*>(s->PD3[2]), s->Phi_s);
+        EpiParams e;
+        e.kind = EPI3_F64;
+        e.rows_valid = N2;
+        e.cols_valid = M;
+        e.ld = M;
+        e.ob = N2 * M;
+        e.out_f64 = s->PhiT[nxt];
+        AFQMC_TRY(tc_gemm3(sp3(s->A3, s->PD3_s, N2, N2, WS), BatchMap{1, WS}, sp3(s->PD3, s->Phi_s, N2, M, WS),
+                           BatchMap{1, WS}, N2, M, N2, WS, e, wk->flags, st));
+    } else {
+        count_launch();
+        apply_rinv_kernel<<<dim3((M + kQT - 1) / kQT, nt, WS), kT, 0, st>>>(s->PhiT[s->cur], s->S, M, N,
+                                                                          s->PhiT[nxt]);
+    }
     AFQMC_CUDA_TRY(cudaMemcpyAsync(s->PhiT[s->cur], s->PhiT[nxt], sizeof(double) * (size_t)WS * 2 * N * M,
                                    cudaMemcpyDeviceToDevice, st));
     refresh_operands(s, st);

@@ -100,3 +100,25 @@ def test_unsupported_shapes_rejected():
     with pytest.raises(api.AfqmcError) as e:
         AFQMC(h, L, E0, Psi[0], Psi[1], 2, 0.01, precision=api.PREC_BF16X3)
     assert e.value.code == -8
+
+
+@pytest.mark.parametrize("M,N,nch,W", [(128, 32, 64, 4), (256, 128, 96, 3)])
+def test_qr_matches_fp64_path(M, N, nch, W):
+    """One step with a QR at its end (k_qr = 1): the mixed path's Cholesky QR (tensor-core Gram
+    and R^-1 product) leaves orthonormal walkers, equal to the FP64 path's Q (R has a positive
+    real diagonal, so Q is unique) up to the step's mixed-precision error."""
+    h, L, E0, Psi = system(M, N, nch, 31)
+    x = syn.make_fields(1, W, nch, seed=4)
+    a, b = pair(h, L, E0, Psi, W, 0.01, 1)
+    with a, b:
+        a.step(1, x, measure_every=0)
+        b.step(1, x, measure_every=0)
+        Qa = a.walkers()
+        Qb = b.walkers()
+    for s in range(2):
+        G = np.einsum("wki,wkj->wij", Qb[s].conj(), Qb[s])
+        orth = np.max(np.abs(G - np.eye(N)))
+        diff = np.max(np.abs(Qb[s] - Qa[s]))
+        print(f"M={M} N={N} spin {s}: |Q^H Q - I| {orth:.2e}, |Q - Q_fp64| {diff:.2e}")
+        assert orth < 1e-7
+        assert diff < 1e-6

@@ -215,3 +215,26 @@ def test_mixed_intermediates_match_numpy(dbg, M, N, nch, W):
             assert et < 5e-7 * np.linalg.cond(S) + 2e-6 and ex < 5e-7 * np.linalg.cond(S) + 2e-6
             e1 += np.sum((P.T @ h) * Th.T)
         assert abs(E1[w] - e1) < 1e-5 * abs(e1)
+
+
+def test_energy_tile_window_does_not_change_results(dbg):
+    """The L2 window only reorders independent tiles: every window gives bit-identical traces."""
+    dbg.afqmc_debug_set_energy_window.argtypes = [ctypes.c_int]
+    Np, Nchol, nws, M = 128, 5, 7, 128
+    rng = np.random.default_rng(99)
+    Lt = rng.standard_normal((Nchol, Np, M)) * 0.1
+    Th = rng.standard_normal((nws, 2, Np, M)) * 0.1
+    outs = []
+    try:
+        for ws in (0, 1, 2, 3, 64):
+            assert dbg.afqmc_debug_set_energy_window(ws) == 0
+            t = np.zeros((nws, Nchol), dtype=np.complex128)
+            X = np.zeros((nws, Nchol), dtype=np.complex128)
+            rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, 4, t.ctypes.data,
+                                        X.ctypes.data)
+            assert rc == 0, api.afqmc_last_error()
+            outs.append((t, X))
+    finally:
+        dbg.afqmc_debug_set_energy_window(0)
+    for t, X in outs[1:]:
+        assert np.array_equal(t, outs[0][0]) and np.array_equal(X, outs[0][1])
