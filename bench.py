@@ -17,6 +17,7 @@ For N > 1 launch with torch.distributed.run; each rank owns an independent walke
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -39,7 +40,7 @@ WORKLOAD = ("solid-like synthetic Hamiltonian: M=512, N_up=N_dn=128, Nchol=2560,
 # dram__bytes_write.sum, one ncu capture of this script; the summary and its command are in
 # profiles/).  The figure holds for the kernel source it was taken on: a digest of that source
 # (the energy-kernel section of kernels_tc.cu and the PTX wrappers) gates it.
-ENERGY_TRAFFIC = {"bytes": 172671584128, "src_digest": "c30cb62d1cedcdf6"}
+ENERGY_TRAFFIC = {"bytes": 174152465152, "src_digest": "430bd62f3ad98a3a"}
 
 
 def energy_src_digest() -> str:
@@ -366,7 +367,14 @@ def main():
            "h2d_bytes_per_step": int(xn.nbytes), "d2h_bytes_per_step": int(trace.nbytes)}
     _, kernels_per_step = api.afqmc_last_step_stats(g.wk)
 
-    # roofline of the dominant kernel: the fused energy contraction
+    # roofline of the dominant kernel: the fused energy contraction; issued tensor flops are the
+    # mean number of split products per tile times the algorithmic ones
+    lib = api.lib()
+    lib.afqmc_debug_energy_products.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    mean_products = ctypes.c_double(0.0)
+    issued = None
+    if prec == api.PREC_BF16X3 and lib.afqmc_debug_energy_products(g.wk, ctypes.addressof(mean_products)) == 0:
+        issued = mean_products.value
     bf16_burst, bf16_sust, hbm, src = peaks()
     N, M, nch, W = wl.Nup, wl.M, wl.Nchol, wl.W
     alg_flops = 8.0 * W * nch * N * N * M          # 2 spins x real-complex T = Ltilde Theta
@@ -376,7 +384,7 @@ def main():
         ach = alg_flops / (e_avg / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s",
                 "frac": ach / bf16_sust, "traffic": energy_traffic() if args.walkers == 0 else None, "kernel": "tc_energy_kernel<128>",
-                "avg_launch_ms": e_avg, "issued_over_algorithmic": float(args.energy_terms or 4),
+                "avg_launch_ms": e_avg, "issued_over_algorithmic": issued,
                 "peak_source": f"bf16_tflops_sustained of {src} peaks (kernel timed inside a long step)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,

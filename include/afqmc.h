@@ -69,7 +69,9 @@ typedef struct afqmc_opts {
                             population split over processes as consecutive walker
                             ranges draws exactly the fields of the whole population  */
     int    energy_terms; /* BF16X3 energy contraction: 3 = hi*hi + hi*lo + lo*hi,
-                            4 = + lo*lo, 0 = library default                         */
+                            4 = + lo*lo for every Cholesky vector, 0 = adaptive
+                            (default): + lo*lo except for the smallest vectors whose
+                            norms ||Ltilde_n||_F add up to at most 1% of the total     */
     int    reserved[6];  /* must be zero                                           */
 } afqmc_opts;
 

@@ -64,6 +64,14 @@ int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk);
 int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with_inverse, double* Sout,
                         double* logdet, float* ms);
 
+/* The adaptive choice of energy products (afqmc_opts.energy_terms = 0) on host data: for the
+ * Frobenius norms norms[n] >= 0 of the nch rotated Cholesky vectors Ltilde_n, flags[g] = 1
+ * (the lo*lo product is formed) for every group g of G consecutive vectors except the groups
+ * made only of the smallest vectors whose norms add up to at most eta of the total (ties:
+ * lower index first), 0 for those.  ceil(nch / G) flags.  Host only, no device work; the
+ * step uses eta = 0.01 and G = 128 / N. */
+int afqmc_debug_select_energy_groups(const double* norms, int nch, int G, double eta, unsigned char* flags);
+
 /* Tile order of the calling thread's later energy-kernel launches: the (Cholesky vector,
  * walker-spin) tiles run in windows of ws_super walker-spin groups (0 = default), sweeping
  * every Cholesky vector inside a window, so the window's Green's functions stay in L2 while
@@ -72,6 +80,12 @@ int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with
 int afqmc_debug_set_energy_window(int ws_super);
 int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X,
                             double* E1);
+
+/* Mean number of split products per energy tile of a BF16X3 walker set (3 or 4 under a
+ * fixed energy_terms; 3 + the fraction of tiles that form lo*lo under the adaptive default).
+ * The issued tensor-core flops of the energy contraction are this many times the algorithmic
+ * ones.  Host only. */
+int afqmc_debug_energy_products(afqmc_wk_debug_t wk, double* mean);
 
 #ifdef __cplusplus
 }

@@ -1,5 +1,6 @@
 // Diagnostic entry points (include/afqmc_debug.h): one tensor-core building block per
 // call, host arrays in and out, for isolated parity tests.
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -105,7 +106,7 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M; sa.scale = static_cast<float*>(asc.p);
     sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
     sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M; sb.scale = static_cast<float*>(bsc.p);
-    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p), terms,
+    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p), terms, nullptr,
                         static_cast<unsigned*>(flags.p), 0));
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
     unsigned fl = 0;
@@ -161,10 +162,26 @@ extern "C" int afqmc_debug_inverse(const double* S, int N, int count, int varian
     return AFQMC_OK;
 }
 
+extern "C" int afqmc_debug_select_energy_groups(const double* norms, int nch, int G, double eta,
+                                                unsigned char* flags) {
+    if (!norms || !flags || nch < 1 || G < 1 || !(eta >= 0.0 && eta < 1.0))
+        return fail(AFQMC_ERR_BADARG, "debug_select_energy_groups: bad arguments");
+    for (int n = 0; n < nch; ++n)
+        if (!(norms[n] >= 0.0) || !std::isfinite(norms[n]))
+            return fail(AFQMC_ERR_BADARG, "debug_select_energy_groups: norms must be finite and >= 0");
+    select_lolo_groups(norms, nch, G, eta, flags);
+    return AFQMC_OK;
+}
+
 extern "C" int afqmc_debug_set_energy_window(int ws_super) {
     if (ws_super < 0) return fail(AFQMC_ERR_BADARG, "debug_set_energy_window: negative window");
     launch_policy().energy_ws_super = ws_super;
     return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_energy_products(afqmc_wk_debug_t wk, double* mean) {
+    if (!wk || !mean) return fail(AFQMC_ERR_BADARG, "debug_energy_products: NULL argument");
+    return tc_energy_products(wk, mean);
 }
 
 extern "C" int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk) {

@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 #include <mutex>
 
 #include "kernels_tc.cuh"
@@ -71,8 +72,8 @@ struct TileShape {
 };
 
 struct SharedCtl {
-    uint64_t full[4];
-    uint64_t empty[4];
+    uint64_t full[8];
+    uint64_t empty[8];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t done;
@@ -429,6 +430,7 @@ struct EnergyShape {
     int64_t tiles;
     int nk;
     int lolo;               // 1: also form lo*lo (four products), 0: three
+    const uint8_t* lolo_group;   // if set: per n-group choice (1: four products, 0: three)
     const float* a_scale;   // [Nchol*Np]
     const float* b_scale;   // [nws*2*Np]
     cplx* t_out;
@@ -445,46 +447,30 @@ __device__ __forceinline__ void energy_tile(const EnergyShape& s, int64_t t, int
     wg = (int)(first + rem % width);
 }
 
-__device__ __forceinline__ void named_bar_epi() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-
-// AND of `pred` over the 128 epilogue threads (named barrier 1).
-__device__ __forceinline__ int named_bar_and(int pred) {
-    int r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.s32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 128, p;\n\t"
-        "selp.s32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(pred)
-        : "memory");
-    return r;
-}
-
-// Energy kernel pipeline: K chunks of BK = 16 (32-byte swizzle, four 24 KB stages) or 32
-// (64-byte swizzle, two 48 KB stages) in 96 KB of shared memory, one TMEM buffer
-// (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  The epilogue drains both
-// accumulators into a 128 x 256 fp32 tile in shared memory (XOR-swizzled within 32-column groups
-// so row and column reads are both conflict-free), releases TMEM at once, and computes the
-// traces from shared memory while the tensor cores run the next tile.  With the walker-spin
-// window below, both operands are L2 hits and the wider chunks (half the barrier round trips
-// per flop) are faster: at M = 512, N = 128, Nchol = 2560, 2048 walker-spins one launch takes
-// 463 ms with BK = 32 and an 8-group window against 513 ms with BK = 16 and a 128-group one.
-constexpr int kEStageRing = 96 * 1024;
+// Energy kernel pipeline: K chunks of BK = 16 (32-byte swizzle, six 24 KB stages) or 32
+// (64-byte swizzle, three 48 KB stages) in 144 KB of shared memory, one TMEM buffer
+// (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  The operands come from L2
+// (~1-2 us under load), so the ring holds as many stages as the shared memory left by the
+// epilogue allows: the epilogue keeps the real part of its rows of T in registers and stages
+// only one plane (128 x 128 fp32, 66 KB) in shared memory (see the epilogue).  With the
+// walker-spin window below, the wider chunks (half the barrier round trips per flop) are
+// faster.
+constexpr int kEStageRing = 144 * 1024;
 template <int BK>
 struct ECfg {
     static constexpr int kABytes = kBM * BK * 2;       // per plane
     static constexpr int kBBytes = 256 * BK * 2;       // per plane
     static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
     static constexpr int kStages = kEStageRing / kStageBytes;
-    static_assert(kStages >= 2 && kStages <= 4, "stage ring");
+    static_assert(kStages >= 2 && kStages <= 8, "stage ring");
 };
 constexpr int kEBKDefault = 32;
 // Walker-spin groups per L2 window: the window's Theta pairs (512 KB per group at M = 512) stay
 // in L2 while the L~ pairs stream through it once per window; the 152 CTAs then share ~19 L~
 // n-groups and 8 Theta groups at a time.
 constexpr int kEWsSuperDefault = 8;
-constexpr int kETileFloats = 128 * 256;
+constexpr int kEPitch = 129;                     // plane tile row pitch (floats): conflict-free
+constexpr int kETileFloats = 128 * kEPitch;      // rows and columns
 
 template <int BK>
 __device__ __forceinline__ uint64_t edesc(uint32_t saddr) {
@@ -529,6 +515,9 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
     int it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < es.tiles && ok; t += gridDim.x, ++it) {
+        int ng, wg;
+        energy_tile(es, t, ng, wg);
+        const bool lolo = es.lolo_group ? es.lolo_group[ng] != 0 : es.lolo != 0;
         if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
         tc_fence_after();
         for (int kb = 0; kb < es.nk; ++kb, ++g) {
@@ -547,7 +536,7 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
                 mma_bf16(d1, ah, bh, idesc, acc);
                 mma_bf16(d2, ah, bl, idesc, acc);
                 mma_bf16(d2, al, bh, idesc, 1u);
-                if (es.lolo) mma_bf16(d2, al, bl, idesc, 1u);
+                if (lolo) mma_bf16(d2, al, bl, idesc, 1u);
             }
             mma_commit(&ctl->empty[st]);
         }
@@ -559,8 +548,8 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
 }
 
 // Energy CTA: warp 0 = TMA producer, warp 1 = TMEM allocator + MMA issuer, warps 2..9 = epilogue
-// (two warps per TMEM lane quadrant; warp w drains lanes 32 (w % 4) .. + 31, half (w - 2) / 4 of
-// the columns, and computes half of the traces of those rows).
+// (two warps per TMEM lane quadrant; warp w drains lanes 32 (w % 4) .. + 31 and half
+// h = (w - 2) / 4 of the walker-spin columns, and forms the traces of those rows and columns).
 constexpr int kEThreads = 320;
 constexpr int kEEpi = 256;
 __device__ __forceinline__ void ebar() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
@@ -576,12 +565,6 @@ __device__ __forceinline__ int ebar_and(int pred) {
         : "memory");
     return r;
 }
-// Tile element (row, col) of the 128 x 256 fp32 tile: 16-byte groups XOR-swizzled by the row
-// within each 32-column block, so a row's 4-column group is one conflict-free 16-byte access
-// and a column read across 32 rows hits 32 different banks.
-__device__ __forceinline__ int swz4(int row, int col) {
-    return row * 256 + (col & ~31) + ((((col >> 2) ^ row) & 7) << 2) + (col & 3);
-}
 
 template <int Np, int BK>
 __global__ void __launch_bounds__(kEThreads, 1)
@@ -593,10 +576,10 @@ __global__ void __launch_bounds__(kEThreads, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     using C = ECfg<BK>;
-    float* tile = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
+    float* plane = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
     // 256 column scales of the tile, reused after the drain for the partial traces
     // ered[((h * 4 + q) * 4 + j) * 4 + v]
-    float* colscale = tile + kETileFloats;
+    float* colscale = plane + kETileFloats;       // 128 x 129 floats: 16-byte aligned
     double* ered = reinterpret_cast<double*>(colscale);
     SharedCtl* ctl = reinterpret_cast<SharedCtl*>(colscale + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -630,20 +613,26 @@ __global__ void __launch_bounds__(kEThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) energy_mma<BK>(sbase, ctl, es);
     } else {
+        // Epilogue.  The tile's accumulator columns are, per walker-spin j of the tile, Np real
+        // columns then Np imaginary ones.  Compact column cc = j Np + b (b < Np) names element b
+        // of walker-spin j; this thread owns row `row` and the 64 compact columns
+        // [64 h, 64 h + 64).  Per (n-block, walker-spin) block, with T = Tr + i Ti:
+        //   t = Tr_aa + i Ti_aa,
+        //   X = sum_ab T_ab T_ba = sum Tr_ab Tr_ba - sum Ti_ab Ti_ba + 2 i sum Tr_ab Ti_ba
+        // (sum Ti_ab Tr_ba = sum Tr_ab Ti_ba by relabelling).  The drain keeps the thread's Tr
+        // in registers and writes Ti to the plane tile; the TiTi and TrTi sums read it; then Tr
+        // replaces it for the TrTr sum.  Partner reads T_ba run along a row of the plane (lanes
+        // = consecutive a), own-row reads down a column (pitch 129): both conflict-free.
         const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
-        const int h = (warp - 2) >> 2;         // column half (drain) / trace half
-        const int row = q * 32 + lane;         // tile row = (n-block i_blk, a')
-        const int i_blk = row / Np, ap = row % Np;
+        const int h = (warp - 2) >> 2;         // compact columns [64 h, 64 h + 64)
+        const int row = q * 32 + lane;         // tile row = (n-block i_blk, a)
+        const int i_blk = row / Np, a = row % Np;
         const int et = threadIdx.x - 64;       // 0..255
-        const uint32_t t1 = ctl->tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * 128);
-        const uint32_t t2 = t1 + 256;
-        // trace work of this half: G >= 2: walker-spins j in [h G/2, (h+1) G/2), every b;
-        // G == 1: j = 0, b in [h Np/2, (h+1) Np/2)
-        constexpr int JH = G >= 2 ? G / 2 : 1;
+        const uint32_t tq = ctl->tmem_base + ((uint32_t)(q * 32) << 16);
+        constexpr int JH = G >= 2 ? G / 2 : 1;     // walker-spins per half
         const int j0 = G >= 2 ? h * JH : 0;
-        const int b0 = G >= 2 ? 0 : h * (Np / 2);
-        constexpr int NB = G >= 2 ? Np : Np / 2;
-        const int r7 = row & 7;
+        float* own = plane + row * kEPitch;                      // this row of the plane
+        const float* pbase = plane + (i_blk * Np) * kEPitch + a; // partner T_ba: row i_blk Np + b
         int it = 0;
         for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
             int ng, wg;
@@ -658,78 +647,94 @@ __global__ void __launch_bounds__(kEThreads, 1)
             const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
             if (!ebar_and(got ? 1 : 0)) break;   // all eight warps leave together
             tc_fence_after();
-            // drain this half's 128 columns of both accumulators, scaled to true units
-#pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                uint32_t a1[32], a2[32];
-                tmem_ld32_nw(t1 + c * 32, a1);
-                tmem_ld32_nw(t2 + c * 32, a2);
-                tmem_ld_wait();
-                const int col0 = h * 128 + c * 32;
-                float* trow = tile + row * 256 + col0;
+            // drain: Tr -> registers, Ti -> plane, both scaled to true units
+            float tr[64];
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float4 cs = *reinterpret_cast<const float4*>(colscale + col0 + 4 * g);   // broadcast
-                    float4 v;
-                    v.x = (__uint_as_float(a1[4 * g]) + __uint_as_float(a2[4 * g])) * (sa * cs.x);
-                    v.y = (__uint_as_float(a1[4 * g + 1]) + __uint_as_float(a2[4 * g + 1])) * (sa * cs.y);
-                    v.z = (__uint_as_float(a1[4 * g + 2]) + __uint_as_float(a2[4 * g + 2])) * (sa * cs.z);
-                    v.w = (__uint_as_float(a1[4 * g + 3]) + __uint_as_float(a2[4 * g + 3])) * (sa * cs.w);
-                    *reinterpret_cast<float4*>(trow + ((g ^ r7) << 2)) = v;
+            for (int c = 0; c < 2; ++c) {
+                const int cc0 = h * 64 + c * 32;          // 32 compact columns in one walker-spin
+                const int col_re = (cc0 / Np) * 2 * Np + cc0 % Np, col_im = col_re + Np;
+                {
+                    uint32_t a1[32], a2[32];
+                    tmem_ld32_nw(tq + col_re, a1);
+                    tmem_ld32_nw(tq + 256 + col_re, a2);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float4 cs = *reinterpret_cast<const float4*>(colscale + col_re + 4 * g);
+                        tr[c * 32 + 4 * g + 0] = (__uint_as_float(a1[4 * g + 0]) + __uint_as_float(a2[4 * g + 0])) * (sa * cs.x);
+                        tr[c * 32 + 4 * g + 1] = (__uint_as_float(a1[4 * g + 1]) + __uint_as_float(a2[4 * g + 1])) * (sa * cs.y);
+                        tr[c * 32 + 4 * g + 2] = (__uint_as_float(a1[4 * g + 2]) + __uint_as_float(a2[4 * g + 2])) * (sa * cs.z);
+                        tr[c * 32 + 4 * g + 3] = (__uint_as_float(a1[4 * g + 3]) + __uint_as_float(a2[4 * g + 3])) * (sa * cs.w);
+                    }
+                }
+                {
+                    uint32_t i1[32], i2[32];
+                    tmem_ld32_nw(tq + col_im, i1);
+                    tmem_ld32_nw(tq + 256 + col_im, i2);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float4 cs = *reinterpret_cast<const float4*>(colscale + col_im + 4 * g);
+                        own[cc0 + 4 * g + 0] = (__uint_as_float(i1[4 * g + 0]) + __uint_as_float(i2[4 * g + 0])) * (sa * cs.x);
+                        own[cc0 + 4 * g + 1] = (__uint_as_float(i1[4 * g + 1]) + __uint_as_float(i2[4 * g + 1])) * (sa * cs.y);
+                        own[cc0 + 4 * g + 2] = (__uint_as_float(i1[4 * g + 2]) + __uint_as_float(i2[4 * g + 2])) * (sa * cs.z);
+                        own[cc0 + 4 * g + 3] = (__uint_as_float(i1[4 * g + 3]) + __uint_as_float(i2[4 * g + 3])) * (sa * cs.w);
+                    }
                 }
             }
             tc_fence_before();
             mbar_arrive(&ctl->tempty[0]);              // tensor memory free: next tile's MMAs start
-            ebar();                                    // tile complete; colscale no longer needed
+            ebar();                                    // Ti plane complete
+            // TiTi and TrTi sums over this thread's b, and the diagonal Ti_aa
+            float sii[JH], sri[JH], srr[JH], dre[JH], dim_[JH];
+#pragma unroll
+            for (int jl = 0; jl < JH; ++jl) { sii[jl] = 0.f; sri[jl] = 0.f; srr[jl] = 0.f; dre[jl] = 0.f; dim_[jl] = 0.f; }
+#pragma unroll
+            for (int k = 0; k < 64; ++k) {
+                const int cc = h * 64 + k, j = cc / Np, b = cc % Np;
+                const int jl = G >= 2 ? j - j0 : 0;
+                const float p = pbase[b * kEPitch + j * Np];    // Ti[b][a] of walker-spin j
+                sii[jl] = fmaf(own[cc], p, sii[jl]);
+                sri[jl] = fmaf(tr[k], p, sri[jl]);
+            }
+#pragma unroll
+            for (int jl = 0; jl < JH; ++jl) {
+                const int cd = (j0 + jl) * Np + a;               // compact column of the diagonal
+                if (cd >= h * 64 && cd < h * 64 + 64) dim_[jl] = own[cd];
+            }
+            ebar();                                    // every read of the Ti plane done
+#pragma unroll
+            for (int k = 0; k < 64; ++k) own[h * 64 + k] = tr[k];
+            ebar();                                    // Tr plane complete
+            // TrTr sum continues the -TiTi one, so Re X is accumulated in one register
+#pragma unroll
+            for (int jl = 0; jl < JH; ++jl) srr[jl] = -sii[jl];
+#pragma unroll
+            for (int k = 0; k < 64; ++k) {
+                const int cc = h * 64 + k, j = cc / Np, b = cc % Np;
+                const int jl = G >= 2 ? j - j0 : 0;
+                srr[jl] = fmaf(tr[k], pbase[b * kEPitch + j * Np], srr[jl]);
+            }
+#pragma unroll
+            for (int jl = 0; jl < JH; ++jl) {
+                const int cd = (j0 + jl) * Np + a;
+                if (cd >= h * 64 && cd < h * 64 + 64) dre[jl] = own[cd];
+            }
             float part[JH][4];                         // [j of this half][tr, ti, Xr, Xi]
 #pragma unroll
             for (int jl = 0; jl < JH; ++jl) {
-                const int j = j0 + jl;
-                const int cre = j * 2 * Np, cim = cre + Np;
-                const float* own = tile + row * 256;
-                // Partner column cre + ap (cim + ap: Np further, same swizzle) in rows
-                // rb = i_blk Np + b + u.  With b a multiple of 8 the swizzle slot of row rb is
-                // ((cre + ap) / 4 ^ u) & 7, so the 8 offsets are set up once.
-                const int pc = cre + ap;
-                int poff[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) poff[u] = (pc & ~31) + (((((pc >> 2) & 7) ^ u)) << 2) + (pc & 3) + u * 256;
-                float xr[4] = {0.f, 0.f, 0.f, 0.f}, xi[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-                for (int b = b0; b < b0 + NB; b += 8) {
-                    const float* prow0 = tile + (i_blk * Np + b) * 256;
-#pragma unroll
-                    for (int hq = 0; hq < 2; ++hq) {   // b .. b+3, b+4 .. b+7
-                        const int slot = ((((b >> 2) + hq) ^ row) & 7) << 2;
-                        const float4 orv = *reinterpret_cast<const float4*>(own + ((cre + b) & ~31) + slot);
-                        const float4 oiv = *reinterpret_cast<const float4*>(own + ((cim + b) & ~31) + slot);
-                        const float orr[4] = {orv.x, orv.y, orv.z, orv.w}, oii[4] = {oiv.x, oiv.y, oiv.z, oiv.w};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float pr = prow0[poff[4 * hq + u]], pi = prow0[poff[4 * hq + u] + Np];
-                            xr[u] = fmaf(orr[u], pr, fmaf(-oii[u], pi, xr[u]));
-                            xi[u] = fmaf(orr[u], pi, fmaf(oii[u], pr, xi[u]));
-                        }
-                    }
-                }
-                float tr = 0.f, ti = 0.f;
-                if (ap >= b0 && ap < b0 + NB) {      // the diagonal element lies in this half
-                    tr = tile[swz4(row, cre + ap)];
-                    ti = tile[swz4(row, cim + ap)];
-                }
-                float Xr = (xr[0] + xr[1]) + (xr[2] + xr[3]);
-                float Xi = (xi[0] + xi[1]) + (xi[2] + xi[3]);
+                float v0 = dre[jl], v1 = dim_[jl], v2 = srr[jl], v3 = 2.0f * sri[jl];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    tr += __shfl_xor_sync(0xffffffffu, tr, o);
-                    ti += __shfl_xor_sync(0xffffffffu, ti, o);
-                    Xr += __shfl_xor_sync(0xffffffffu, Xr, o);
-                    Xi += __shfl_xor_sync(0xffffffffu, Xi, o);
+                    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                    v3 += __shfl_xor_sync(0xffffffffu, v3, o);
                 }
-                part[jl][0] = tr;
-                part[jl][1] = ti;
-                part[jl][2] = Xr;
-                part[jl][3] = Xi;
+                part[jl][0] = v0;
+                part[jl][1] = v1;
+                part[jl][2] = v2;
+                part[jl][3] = v3;
             }
             if (lane < 16) {   // ered[h][q][j][v] for every j slot (zeros where this half has none)
                 const int jj = lane >> 2, v = lane & 3;
@@ -761,7 +766,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
                     es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
                 }
             }
-            ebar();   // ered (aliasing colscale) is read before the next tile rewrites it
+            ebar();   // ered (aliasing colscale) and the plane are read before the next tile
         }
     }
     tc_fence_before();
@@ -777,10 +782,6 @@ __global__ void __launch_bounds__(kEThreads, 1)
 // One warp per row: scale = 2^(e-11) with ||x||_2 < 2^e, hi = rint(x/scale) (|hi| <= 2048, an
 // integer, exact in fp16), lo = fp16(x/scale - hi).  ||hi||_2 <= 2^11 + sqrt(K)/2, so by
 // Cauchy-Schwarz every partial sum of hi_A . hi_B is an integer below 2^23: exact in fp32.
-__device__ __forceinline__ void load4(const float* p, double (&v)[4]) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-}
 __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
     const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
@@ -1338,7 +1339,7 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
 }
 
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
-              cplx* X_out, int terms, unsigned* flags, cudaStream_t st) {
+              cplx* X_out, int terms, const uint8_t* lolo_group, unsigned* flags, cudaStream_t st) {
     if (terms != 3 && terms != 4) return fail(AFQMC_ERR_BADARG, "tc_energy: terms must be 3 or 4");
     if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
@@ -1363,6 +1364,7 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     es.tiles = (int64_t)es.n_groups * es.ws_groups;
     es.nk = M / BK;
     es.lolo = terms == 4 ? 1 : 0;
+    es.lolo_group = lolo_group;
     es.a_scale = Lt.scale;
     es.b_scale = ThetaT.scale;
     es.t_out = t_out;
@@ -1378,6 +1380,27 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
         case 32: return launch_energy<32, 16>(m, es, flags, st);
         case 64: return launch_energy<64, 16>(m, es, flags, st);
         default: return launch_energy<128, 16>(m, es, flags, st);
+    }
+}
+
+void select_lolo_groups(const double* nrm, int nch, int G, double eta, uint8_t* flags) {
+    std::vector<int> order((size_t)nch);
+    for (int n = 0; n < nch; ++n) order[(size_t)n] = n;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nrm[a] < nrm[b]; });
+    double total = 0.0;
+    for (int n = 0; n < nch; ++n) total += nrm[n];
+    std::vector<uint8_t> three((size_t)nch, 0);
+    double acc = 0.0;
+    for (int n : order) {
+        if (acc + nrm[n] > eta * total) break;
+        acc += nrm[n];
+        three[(size_t)n] = 1;
+    }
+    const int ng = (nch + G - 1) / G;
+    for (int g = 0; g < ng; ++g) {
+        uint8_t four = 0;
+        for (int n = g * G; n < std::min(nch, (g + 1) * G); ++n) four |= three[(size_t)n] ? 0 : 1;
+        flags[g] = four;
     }
 }
 

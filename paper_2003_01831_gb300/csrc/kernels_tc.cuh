@@ -124,9 +124,16 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
 // all n and walker-spin pairs ws; emits t = Tr T and X = Tr(T T) per (ws, n) into
 // t_out/X_out [nws][Nchol] (complex FP64).  Lt: [Nchol*Np][M], ThetaT: [nws*2*Np][M]
 // (rows (ws, re/im, b)), both row-scaled; exact accumulation of the leading product.
-// terms = 3 (hi*hi exact, hi*lo + lo*hi) or 4 (+ lo*lo) split products.
+// terms = 3 (hi*hi exact, hi*lo + lo*hi) or 4 (+ lo*lo) split products; lolo_group (device,
+// one byte per group of 128/Np Cholesky vectors, or null) overrides terms per group: 1 four
+// products, 0 three.
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
-              cplx* X_out, int terms, unsigned* flags, cudaStream_t st);
+              cplx* X_out, int terms, const uint8_t* lolo_group, unsigned* flags, cudaStream_t st);
+
+// Cholesky-vector groups whose energy tiles form the lo*lo product (flags[g] = 1): every group
+// except those made only of the smallest vectors, by Frobenius norm nrm[n] of Ltilde_n, whose
+// norms add up to at most eta of the total.  G vectors per group, ceil(nch / G) flags.
+void select_lolo_groups(const double* nrm, int nch, int G, double eta, uint8_t* flags);
 
 // Three-slice row split (see kernels_tc.cu): h, m, l fp16 planes [rows][K] and row scales.
 void split3_rows(const double* src, int64_t rows, int64_t K, bf16* h, bf16* m, bf16* l, float* scale,

@@ -99,5 +99,6 @@ int tc_qr(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_debug_terms(afqmc_walkers* wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X, double* E1);
+int tc_energy_products(afqmc_walkers* wk, double* mean);
 
 }  // namespace afqmc

@@ -1,0 +1,83 @@
+"""Host-side choice of the adaptive energy products (afqmc_opts.energy_terms = 0): which groups
+of Cholesky vectors form the lo*lo split product.  Checked against the rule written out in
+numpy (drop the smallest vectors, by norm, while their norms add up to at most eta of the
+total; a group keeps four products if any of its vectors does).  No device work."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2003_01831_gb300 import api, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    L = api.lib()
+    L.afqmc_debug_select_energy_groups.restype = ctypes.c_int
+    L.afqmc_debug_select_energy_groups.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                   ctypes.c_void_p]
+    return L
+
+
+def select(lib, nrm, G, eta):
+    nrm = np.ascontiguousarray(nrm, dtype=np.float64)
+    ng = (nrm.size + G - 1) // G if G > 0 else nrm.size
+    flags = np.full(ng, 7, dtype=np.uint8)
+    rc = lib.afqmc_debug_select_energy_groups(nrm.ctypes.data, nrm.size, G, eta, flags.ctypes.data)
+    return rc, flags
+
+
+def rule(nrm, G, eta):
+    order = np.argsort(nrm, kind="stable")
+    three = np.zeros(nrm.size, bool)
+    acc, budget = 0.0, eta * nrm.sum()
+    for n in order:
+        if acc + nrm[n] > budget:
+            break
+        acc += nrm[n]
+        three[n] = True
+    ng = (nrm.size + G - 1) // G
+    return np.array([0 if three[g * G:(g + 1) * G].all() else 1 for g in range(ng)], dtype=np.uint8)
+
+
+def test_exponential_decay_splits_at_the_budget(lib):
+    """Norms exp(-n/200) (the m512 workload's decay): the tail beyond n0 with exp(-n0/200) ~ eta
+    skips lo*lo."""
+    n = np.arange(2560)
+    nrm = np.exp(-n / 200.0)
+    rc, f = select(lib, nrm, 1, 0.01)
+    assert rc == 0
+    assert np.array_equal(f, rule(nrm, 1, 0.01))
+    n0 = int(np.argmin(f))                           # first vector without lo*lo
+    assert f[:n0].all() and not f[n0:].any()
+    tail = nrm[n0:].sum() / nrm.sum()
+    assert tail <= 0.01 < nrm[n0 - 1:].sum() / nrm.sum()
+    assert abs(n0 - 200 * np.log(100)) < 3           # exp(-n0/200) = 1%: n0 ~ 921
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+@pytest.mark.parametrize("eta", [0.0, 0.01, 0.3, 0.999])
+def test_unsorted_norms_and_groups(lib, G, eta):
+    rng = np.random.default_rng(G * 100 + int(eta * 1000))
+    nrm = rng.exponential(1.0, 301) ** 3
+    nrm[[5, 77, 200]] = 0.0                          # zero vectors: always droppable
+    nrm[10:14] = nrm[9]                              # ties
+    rc, f = select(lib, nrm, G, eta)
+    assert rc == 0
+    assert np.array_equal(f, rule(nrm, G, eta))
+
+
+def test_eta_zero_keeps_every_nonzero_vector(lib):
+    nrm = np.array([0.0, 1.0, 2.0, 0.0, 3.0, 0.0, 0.0, 0.0])
+    rc, f = select(lib, nrm, 2, 0.0)
+    assert rc == 0
+    assert f.tolist() == [1, 1, 1, 0]
+
+
+def test_bad_arguments_rejected(lib):
+    nrm = np.ones(4)
+    assert select(lib, nrm, 0, 0.01)[0] == -1
+    assert select(lib, nrm, 1, 1.0)[0] == -1
+    assert select(lib, np.array([1.0, np.nan]), 1, 0.01)[0] == -1
+    assert select(lib, np.array([1.0, -1.0]), 1, 0.01)[0] == -1
