@@ -56,9 +56,10 @@ int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk);
  * float64, row-major [count][N][N]) by FP64 Gauss-Jordan elimination with partial pivoting
  * (the LU / inverse / log-det row of the walker step, Sec. V).  logdet [count] complex
  * receives log|det S| + i arg det S; with_inverse = 1 also writes the inverses to Sout (same
- * layout).  variant: 0 = the kernel the
- * step uses, 1 = the shared-memory kernel, 2 = the register kernel (32 < N <= 128 with
- * with_inverse; other cases fall back to 1).  *ms (if not NULL) receives the kernel time.
+ * layout).  variant: 0 = the FP64 kernel the
+ * FP64 step uses, 1 = the shared-memory kernel, 2 = the register kernel, 3 = the register
+ * kernel with float-pair elimination (~2^-44 relative, what the BF16X3 step uses); 2 and 3
+ * apply for 32 < N <= 128 with with_inverse, other cases fall back to 1.  *ms (if not NULL) receives the kernel time.
  * Returns AFQMC_ERR_SINGULAR / AFQMC_ERR_NONFINITE (logdet = -inf + 0i for such a matrix,
  * its inverse unwritten) if a pivot column is zero / not finite. */
 int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with_inverse, double* Sout,

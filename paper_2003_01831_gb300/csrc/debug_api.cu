@@ -125,7 +125,7 @@ extern "C" int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* 
 
 extern "C" int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with_inverse, double* Sout,
                                    double* logdet, float* ms) {
-    if (!S || !logdet || N < 1 || count < 1 || variant < 0 || variant > 2 || (with_inverse && !Sout))
+    if (!S || !logdet || N < 1 || count < 1 || variant < 0 || variant > 3 || (with_inverse && !Sout))
         return fail(AFQMC_ERR_BADARG, "debug_inverse: bad arguments");
     const int64_t n = (int64_t)count * N * N;
     DevBuf ds, dl, flags;

@@ -570,17 +570,93 @@ __global__ void __launch_bounds__(kGJT)
 constexpr int kGJRegCols = 64;      // columns per CTA
 constexpr int kGJRegThreads = 512;  // 16 warps x 4 columns
 
-template <int RQ>
-__device__ __forceinline__ cplx sel_q(const cplx (&v)[RQ][4], int q, int u) {
-    cplx r = v[0][u];
+// Element arithmetic of the register Gauss-Jordan kernel.  NumD: FP64 complex.  NumFF: each of
+// re, im a float pair hi + lo (~2^-44 relative, the TwoProduct / TwoSum error-free transforms on
+// the fp32 pipe, which is ~64x GB300's FP64 pipe); pivot reciprocals, the read-out and the
+// log-determinant are FP64 either way.
+struct __align__(16) ffc {   // 16-byte aligned: the peer CTA receives it as one 16-byte store
+    float rh, rl, ih, il;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float v = s - a;
+    e = (a - (s - v)) + (b - v);
+}
+// (h, l) + x y for float pairs: TwoProduct of the leading parts, first-order cross terms
+__device__ __forceinline__ void ff_fma(float& h, float& l, float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    float pe = fmaf(xh, yh, -p);
+    pe = fmaf(xh, yl, fmaf(xl, yh, pe));
+    float s, e;
+    two_sum(h, p, s, e);
+    e += l + pe;
+    h = s + e;
+    l = e - (h - s);
+}
+struct NumD {
+    using T = cplx;
+    __device__ static T from(cplx v) { return v; }
+    __device__ static cplx to(const T& v) { return v; }
+    __device__ static double mag(const T& v) { return abs1(v); }
+    __device__ static T mul(const T& a, const T& b) { return a * b; }
+    __device__ static void upd(T& a, const T& m, const T& p) { cfma(a, cplx{-m.re, -m.im}, p); }   // a -= m p
+    __device__ static T negmul(const T& m, const T& b) { const cplx w = m * b; return cplx{-w.re, -w.im}; }
+    __device__ static T shfl(const T& v, int src) {
+        return cplx{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+    }
+    __device__ static void st_peer(uint32_t ad, const T& v) {
+        st_peer_f64(ad, v.re);
+        st_peer_f64(ad + 8, v.im);
+    }
+};
+struct NumFF {
+    using T = ffc;
+    __device__ static T from(cplx v) {
+        const float rh = (float)v.re, ih = (float)v.im;
+        return ffc{rh, (float)(v.re - (double)rh), ih, (float)(v.im - (double)ih)};
+    }
+    __device__ static cplx to(const T& v) { return cplx{(double)v.rh + (double)v.rl, (double)v.ih + (double)v.il}; }
+    __device__ static double mag(const T& v) { return (double)(fabsf(v.rh) + fabsf(v.ih)); }
+    __device__ static T mul(const T& a, const T& b) {
+        T r{0.f, 0.f, 0.f, 0.f};
+        ff_fma(r.rh, r.rl, a.rh, a.rl, b.rh, b.rl);
+        ff_fma(r.rh, r.rl, -a.ih, -a.il, b.ih, b.il);
+        ff_fma(r.ih, r.il, a.rh, a.rl, b.ih, b.il);
+        ff_fma(r.ih, r.il, a.ih, a.il, b.rh, b.rl);
+        return r;
+    }
+    __device__ static void upd(T& a, const T& m, const T& p) {   // a -= m p
+        ff_fma(a.rh, a.rl, -m.rh, -m.rl, p.rh, p.rl);
+        ff_fma(a.rh, a.rl, m.ih, m.il, p.ih, p.il);
+        ff_fma(a.ih, a.il, -m.rh, -m.rl, p.ih, p.il);
+        ff_fma(a.ih, a.il, -m.ih, -m.il, p.rh, p.rl);
+    }
+    __device__ static T negmul(const T& m, const T& b) {
+        const T w = mul(m, b);
+        return ffc{-w.rh, -w.rl, -w.ih, -w.il};
+    }
+    __device__ static T shfl(const T& v, int src) {
+        return ffc{__shfl_sync(0xffffffffu, v.rh, src), __shfl_sync(0xffffffffu, v.rl, src),
+                   __shfl_sync(0xffffffffu, v.ih, src), __shfl_sync(0xffffffffu, v.il, src)};
+    }
+    __device__ static void st_peer(uint32_t ad, const T& v) {
+        asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(ad), "f"(v.rh), "f"(v.rl), "f"(v.ih),
+                     "f"(v.il)
+                     : "memory");
+    }
+};
+
+template <class T, int RQ>
+__device__ __forceinline__ T sel_q(const T (&v)[RQ][4], int q, int u) {
+    T r = v[0][u];
 #pragma unroll
     for (int i = 1; i < RQ; ++i)
         if (q == i) r = v[i][u];
     return r;
 }
-template <int RQ>
-__device__ __forceinline__ cplx sel_u(const cplx (&v)[RQ][4], int q, int u) {
-    cplx r = v[q][0];
+template <class T, int RQ>
+__device__ __forceinline__ T sel_u(const T (&v)[RQ][4], int q, int u) {
+    T r = v[q][0];
 #pragma unroll
     for (int i = 1; i < 4; ++i)
         if (u == i) r = v[q][i];
@@ -589,19 +665,21 @@ __device__ __forceinline__ cplx sel_u(const cplx (&v)[RQ][4], int q, int u) {
 
 // Pivot search over column k (local sub-column uk of the calling warp) and publication of the
 // column (pre-elimination values), the pivot row (or -1 singular / -2 non-finite) and the
-// pivot's reciprocal, computed once here instead of by every thread.
-template <int C, int RQ>
-__device__ __forceinline__ void gj_reg_publish(const cplx (&a)[RQ][4], int uk, unsigned used, int N, int lane,
-                                               int owner_rank, cplx* colbuf, int* pbuf, cplx* invbuf) {
+// pivot's reciprocal (FP64 Smith division, once here instead of in every thread).
+template <class Num, int C, int RQ>
+__device__ __forceinline__ void gj_reg_publish(const typename Num::T (&a)[RQ][4], int uk, unsigned used, int N,
+                                               int lane, int owner_rank, typename Num::T* colbuf, int* pbuf,
+                                               typename Num::T* invbuf, cplx* pivbuf) {
+    using T = typename Num::T;
     double best = -1.0;
     int bi = N;
-    cplx col[RQ];
+    T col[RQ];
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
-        col[q] = sel_u<RQ>(a, q, uk);
+        col[q] = sel_u<T, RQ>(a, q, uk);
         const int i = lane + 32 * q;
         if (i < N && !((used >> q) & 1u)) {
-            const double v = abs1(col[q]);
+            const double v = Num::mag(col[q]);
             if (v > best || (v != v && best == best)) { best = v; bi = i; }
         }
     }
@@ -616,39 +694,38 @@ __device__ __forceinline__ void gj_reg_publish(const cplx (&a)[RQ][4], int uk, u
     for (int q = 0; q < RQ; ++q) {
         const int i = lane + 32 * q;
         colbuf[i] = col[q];
-        if (C > 1) {
-            const uint32_t ad = peer_addr(&colbuf[i], (uint32_t)(owner_rank ^ 1));
-            st_peer_f64(ad, col[q].re);
-            st_peer_f64(ad + 8, col[q].im);
-        }
+        if (C > 1) Num::st_peer(peer_addr(&colbuf[i], (uint32_t)(owner_rank ^ 1)), col[q]);
     }
     // the pivot value from the lane that holds row bi
     const int bl = code >= 0 ? (code & 31) : 0, bq = code >= 0 ? (code >> 5) : 0;
-    cplx pv = col[0];
+    T pv = col[0];
 #pragma unroll
     for (int q = 1; q < RQ; ++q)
         if (bq == q) pv = col[q];
-    pv = cplx{__shfl_sync(0xffffffffu, pv.re, bl), __shfl_sync(0xffffffffu, pv.im, bl)};
+    pv = Num::shfl(pv, bl);
     if (lane == 0) {
-        const cplx inv = code >= 0 ? cdiv(cplx{1.0, 0.0}, pv) : cplx{0.0, 0.0};
+        const cplx pc = Num::to(pv);
+        const T inv = Num::from(code >= 0 ? cdiv(cplx{1.0, 0.0}, pc) : cplx{0.0, 0.0});
         *pbuf = code;
         *invbuf = inv;
+        *pivbuf = pc;
         if (C > 1) {
             st_peer_s32(peer_addr(pbuf, (uint32_t)(owner_rank ^ 1)), code);
-            const uint32_t ad = peer_addr(invbuf, (uint32_t)(owner_rank ^ 1));
-            st_peer_f64(ad, inv.re);
-            st_peer_f64(ad + 8, inv.im);
+            Num::st_peer(peer_addr(invbuf, (uint32_t)(owner_rank ^ 1)), inv);
+            NumD::st_peer(peer_addr(pivbuf, (uint32_t)(owner_rank ^ 1)), pc);
         }
     }
 }
 
-template <int C, int RQ>
+template <class Num, int C, int RQ>
 __global__ void __launch_bounds__(kGJRegThreads, 1)
     gj_reg_kernel(cplx* Sbase, int64_t stride, int N, cplx* logdet, unsigned* flags) {
+    using T = typename Num::T;
     constexpr int NR = 32 * RQ;
-    __shared__ cplx colbuf[2][NR];
+    __shared__ T colbuf[2][NR];
     __shared__ int pbuf[2];
-    __shared__ cplx invbuf[2];
+    __shared__ T invbuf[2];
+    __shared__ cplx pivbuf[2];
     __shared__ int perm[NR];
     __shared__ int pinv[NR];
     __shared__ cplx pivs[NR];
@@ -657,58 +734,53 @@ __global__ void __launch_bounds__(kGJRegThreads, 1)
     cplx* G = Sbase + mat * stride;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = rank * kGJRegCols + warp * 4;   // first global column of this thread
-    cplx a[RQ][4];
+    T a[RQ][4];
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
         const int i = lane + 32 * q;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = c0 + u;
-            a[q][u] = (i < N && j < N) ? G[(int64_t)i * N + j] : cplx{0.0, 0.0};
+            a[q][u] = Num::from((i < N && j < N) ? G[(int64_t)i * N + j] : cplx{0.0, 0.0});
         }
     }
     unsigned used = 0;   // bit q: row lane + 32 q is a pivot row already
     auto owns = [&](int k) { return k < N && (k >> 6) == rank && ((k & 63) >> 2) == warp; };
-    if (owns(0)) gj_reg_publish<C, RQ>(a, 0, used, N, lane, rank, colbuf[0], &pbuf[0], &invbuf[0]);
+    if (owns(0)) gj_reg_publish<Num, C, RQ>(a, 0, used, N, lane, rank, colbuf[0], &pbuf[0], &invbuf[0], &pivbuf[0]);
     gj_sync<C>();
     int singular = 0;
     for (int k = 0; k < N; ++k) {
         const int b = k & 1;
         const int p = pbuf[b];
         if (p < 0) { singular = p; break; }
-        const cplx inv = invbuf[b];
-        if (threadIdx.x == 0) { perm[k] = p; pivs[k] = colbuf[b][p]; }
+        const T inv = invbuf[b];
+        if (threadIdx.x == 0) { perm[k] = p; pivs[k] = pivbuf[b]; }
         const int pl = p & 31, pq = p >> 5;
         // the warp's four pivot-row entries: gathered from lane pl, each scaled by one lane
         // (lane u % 4 scales entry u), then shared again
-        cplx rp[4];
+        T rp[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const cplx v = sel_q<RQ>(a, pq, u);
-            rp[u] = cplx{__shfl_sync(0xffffffffu, v.re, pl), __shfl_sync(0xffffffffu, v.im, pl)};
-        }
-        cplx mine = rp[0];
+        for (int u = 0; u < 4; ++u) rp[u] = Num::shfl(sel_q<T, RQ>(a, pq, u), pl);
+        T mine = rp[0];
 #pragma unroll
         for (int u = 1; u < 4; ++u)
             if ((lane & 3) == u) mine = rp[u];
-        mine = mine * inv;
-        cplx prow[4];
+        mine = Num::mul(mine, inv);
+        T prow[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            prow[u] = cplx{__shfl_sync(0xffffffffu, mine.re, u), __shfl_sync(0xffffffffu, mine.im, u)};
+        for (int u = 0; u < 4; ++u) prow[u] = Num::shfl(mine, u);
         if (lane == pl) used |= 1u << pq;
         const bool ownk = owns(k);
         const int uk = k & 3;
         const bool own1 = owns(k + 1);
         const int u1 = (k + 1) & 3;
         // one element: a -= m prow; column k of the inverse: -m / piv; the pivot row: prow, 1 / piv
-        auto upd = [&](int q, int u, cplx m) {
+        auto upd = [&](int q, int u, const T& m) {
             const int i = lane + 32 * q;
-            cplx v = a[q][u];
-            cfma(v, cplx{-m.re, -m.im}, prow[u]);
+            T v = a[q][u];
+            Num::upd(v, m, prow[u]);
             if (ownk && u == uk) {
-                const cplx w = m * inv;
-                v = i == p ? inv : cplx{-w.re, -w.im};
+                v = i == p ? inv : Num::negmul(m, inv);
             } else if (i == p) {
                 v = prow[u];
             }
@@ -717,16 +789,17 @@ __global__ void __launch_bounds__(kGJRegThreads, 1)
         if (own1) {   // look-ahead: column k+1 first, then its pivot search and publication
 #pragma unroll
             for (int q = 0; q < RQ; ++q) {
-                const cplx m = colbuf[b][lane + 32 * q];
+                const T m = colbuf[b][lane + 32 * q];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (u == u1) upd(q, u, m);
             }
-            gj_reg_publish<C, RQ>(a, u1, used, N, lane, rank, colbuf[b ^ 1], &pbuf[b ^ 1], &invbuf[b ^ 1]);
+            gj_reg_publish<Num, C, RQ>(a, u1, used, N, lane, rank, colbuf[b ^ 1], &pbuf[b ^ 1], &invbuf[b ^ 1],
+                                       &pivbuf[b ^ 1]);
         }
 #pragma unroll
         for (int q = 0; q < RQ; ++q) {
-            const cplx m = colbuf[b][lane + 32 * q];
+            const T m = colbuf[b][lane + 32 * q];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (!(own1 && u == u1)) upd(q, u, m);
@@ -777,7 +850,7 @@ __global__ void __launch_bounds__(kGJRegThreads, 1)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = c0 + u;
-            if (j < N) G[orow + perm[j]] = a[q][u];
+            if (j < N) G[orow + perm[j]] = Num::to(a[q][u]);
         }
     }
     if (C > 1) cluster_sync_all();
@@ -1058,13 +1131,15 @@ void zgemm(const GemmArgs& g, cudaStream_t st) {
 }
 
 void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet, bool with_inverse,
-                            unsigned* flags, cudaStream_t st) {
+                            unsigned* flags, cudaStream_t st, bool float_float) {
     if (count <= 0) return;
-    const int variant = launch_policy().gj_variant;   // 0 auto, 1 shared memory, 2 registers
+    const int variant = launch_policy().gj_variant;   // 0 auto, 1 shared memory, 2 registers, 3 float-float
     if (with_inverse && N > 32 && N <= 2 * kGJRegCols && variant != 1) {
+        const bool ff = variant == 3 || (variant == 0 && float_float);
         count_launch();
         if (N <= kGJRegCols) {
-            gj_reg_kernel<1, 2><<<count, kGJRegThreads, 0, st>>>(S, stride, N, logdet, flags);
+            if (ff) gj_reg_kernel<NumFF, 1, 2><<<count, kGJRegThreads, 0, st>>>(S, stride, N, logdet, flags);
+            else gj_reg_kernel<NumD, 1, 2><<<count, kGJRegThreads, 0, st>>>(S, stride, N, logdet, flags);
             return;
         }
         cudaLaunchConfig_t cfg = {};
@@ -1079,7 +1154,8 @@ void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* log
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, gj_reg_kernel<2, 4>, S, stride, N, logdet, flags);
+        if (ff) cudaLaunchKernelEx(&cfg, gj_reg_kernel<NumFF, 2, 4>, S, stride, N, logdet, flags);
+        else cudaLaunchKernelEx(&cfg, gj_reg_kernel<NumD, 2, 4>, S, stride, N, logdet, flags);
         return;
     }
     if (N <= kGJSmemMax) {

@@ -35,8 +35,10 @@ void zgemm(const GemmArgs& g, cudaStream_t st);
 // In-place Gauss-Jordan inverse (with_inverse) or LU elimination (log-det only) of `count`
 // complex N x N matrices at S + i*stride, partial pivoting on max |re|+|im|.  logdet[i] =
 // log|det| + i arg(det) (arg wrapped to (-pi, pi]); sets FLAG_SINGULAR on an exact zero pivot.
+// float_float: the register kernel's elimination in float pairs (~2^-44 relative; pivot
+// reciprocals and the log-determinant stay FP64), for callers whose S is itself less exact.
 void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet,
-                            bool with_inverse, unsigned* flags, cudaStream_t st);
+                            bool with_inverse, unsigned* flags, cudaStream_t st, bool float_float = false);
 
 // Traces of T[c][w] (N x N, chunk of Nchol entries): t = Tr T, X = Tr(T T), written to
 // t_out[w*ldo + n0 + c], X_out[...].  T layout [nc][W][N][N].

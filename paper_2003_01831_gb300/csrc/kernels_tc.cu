@@ -547,18 +547,18 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
     wait_drain(&ctl->done, 0);
 }
 
-// Energy CTA: warp 0 = TMA producer, warp 1 = TMEM allocator + MMA issuer, warps 2..9 = epilogue
-// (two warps per TMEM lane quadrant; warp w drains lanes 32 (w % 4) .. + 31 and half
+// Energy CTA: warp 0 = TMA producer, warp 1 = TMEM allocator + MMA issuer, warps 2..17 = epilogue
+// (four warps per TMEM lane quadrant; warp w drains lanes 32 (w % 4) .. + 31 and quarter
 // h = (w - 2) / 4 of the walker-spin columns, and forms the traces of those rows and columns).
-constexpr int kEThreads = 320;
-constexpr int kEEpi = 256;
-__device__ __forceinline__ void ebar() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+constexpr int kEThreads = 576;
+constexpr int kEEpi = 512;
+__device__ __forceinline__ void ebar() { asm volatile("bar.sync 2, 512;" ::: "memory"); }
 __device__ __forceinline__ int ebar_and(int pred) {
     int r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.s32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 2, 256, p;\n\t"
+        "bar.red.and.pred q, 2, 512, p;\n\t"
         "selp.s32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
         : "r"(pred)
@@ -577,11 +577,10 @@ __global__ void __launch_bounds__(kEThreads, 1)
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     using C = ECfg<BK>;
     float* plane = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
-    // 256 column scales of the tile, reused after the drain for the partial traces
-    // ered[((h * 4 + q) * 4 + j) * 4 + v]
+    // 256 column scales of the tile; partial traces ered[((h * 4 + q) * 4 + j) * 4 + v]
     float* colscale = plane + kETileFloats;       // 128 x 129 floats: 16-byte aligned
-    double* ered = reinterpret_cast<double*>(colscale);
-    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(colscale + 256);
+    double* ered = reinterpret_cast<double*>(colscale + 256);
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(ered + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tAh);
@@ -615,29 +614,33 @@ __global__ void __launch_bounds__(kEThreads, 1)
     } else {
         // Epilogue.  The tile's accumulator columns are, per walker-spin j of the tile, Np real
         // columns then Np imaginary ones.  Compact column cc = j Np + b (b < Np) names element b
-        // of walker-spin j; this thread owns row `row` and the 64 compact columns
-        // [64 h, 64 h + 64).  Per (n-block, walker-spin) block, with T = Tr + i Ti:
+        // of walker-spin j; this thread owns row `row` and the 32 compact columns
+        // [32 h, 32 h + 32), all in one walker-spin j.  Per (n-block, walker-spin) block, with
+        // T = Tr + i Ti:
         //   t = Tr_aa + i Ti_aa,
         //   X = sum_ab T_ab T_ba = sum Tr_ab Tr_ba - sum Ti_ab Ti_ba + 2 i sum Tr_ab Ti_ba
-        // (sum Ti_ab Tr_ba = sum Tr_ab Ti_ba by relabelling).  The drain keeps the thread's Tr
-        // in registers and writes Ti to the plane tile; the TiTi and TrTi sums read it; then Tr
-        // replaces it for the TrTr sum.  Partner reads T_ba run along a row of the plane (lanes
-        // = consecutive a), own-row reads down a column (pitch 129): both conflict-free.
+        // (sum Ti_ab Tr_ba = sum Tr_ab Ti_ba by relabelling).  The drain writes Ti to the plane
+        // tile and keeps the thread's Tr in registers; the TiTi and TrTi sums read the plane;
+        // then Tr replaces it for the TrTr sum.  Partner reads T_ba run along a row of the plane
+        // (lanes = consecutive a), own-row reads down a column (pitch 129): both conflict-free.
         const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
-        const int h = (warp - 2) >> 2;         // compact columns [64 h, 64 h + 64)
+        const int h = (warp - 2) >> 2;         // compact columns [32 h, 32 h + 32)
         const int row = q * 32 + lane;         // tile row = (n-block i_blk, a)
         const int i_blk = row / Np, a = row % Np;
-        const int et = threadIdx.x - 64;       // 0..255
+        const int et = threadIdx.x - 64;       // 0..511
         const uint32_t tq = ctl->tmem_base + ((uint32_t)(q * 32) << 16);
-        constexpr int JH = G >= 2 ? G / 2 : 1;     // walker-spins per half
-        const int j0 = G >= 2 ? h * JH : 0;
+        const int cc0 = h * 32;                      // first compact column of this thread
+        const int j = cc0 / Np, b0 = cc0 % Np;       // its walker-spin and first element
+        const int col_re = j * 2 * Np + b0, col_im = col_re + Np;
         float* own = plane + row * kEPitch;                      // this row of the plane
-        const float* pbase = plane + (i_blk * Np) * kEPitch + a; // partner T_ba: row i_blk Np + b
+        const float* pbase = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;   // T_(b0+k) a
+        const int cd = j * Np + a;                               // compact column of T_aa
+        const bool diag = cd >= cc0 && cd < cc0 + 32;
         int it = 0;
         for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
             int ng, wg;
             energy_tile(es, t, ng, wg);
-            {
+            if (et < 256) {
                 const int64_t brow = (int64_t)wg * 256 + et;
                 colscale[et] = brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
             }
@@ -645,128 +648,94 @@ __global__ void __launch_bounds__(kEThreads, 1)
             const float sa = arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
             ebar();
             const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
-            if (!ebar_and(got ? 1 : 0)) break;   // all eight warps leave together
+            if (!ebar_and(got ? 1 : 0)) break;   // all sixteen warps leave together
             tc_fence_after();
-            // drain: Tr -> registers, Ti -> plane, both scaled to true units
-            float tr[64];
+            // drain: Ti -> plane, then Tr -> registers, both scaled to true units
+            float tr[32];
+            {
+                uint32_t u1[32], u2[32];
+                tmem_ld32_nw(tq + col_im, u1);
+                tmem_ld32_nw(tq + 256 + col_im, u2);
+                tmem_ld_wait();
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int cc0 = h * 64 + c * 32;          // 32 compact columns in one walker-spin
-                const int col_re = (cc0 / Np) * 2 * Np + cc0 % Np, col_im = col_re + Np;
-                {
-                    uint32_t a1[32], a2[32];
-                    tmem_ld32_nw(tq + col_re, a1);
-                    tmem_ld32_nw(tq + 256 + col_re, a2);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int g = 0; g < 8; ++g) {
-                        const float4 cs = *reinterpret_cast<const float4*>(colscale + col_re + 4 * g);
-                        tr[c * 32 + 4 * g + 0] = (__uint_as_float(a1[4 * g + 0]) + __uint_as_float(a2[4 * g + 0])) * (sa * cs.x);
-                        tr[c * 32 + 4 * g + 1] = (__uint_as_float(a1[4 * g + 1]) + __uint_as_float(a2[4 * g + 1])) * (sa * cs.y);
-                        tr[c * 32 + 4 * g + 2] = (__uint_as_float(a1[4 * g + 2]) + __uint_as_float(a2[4 * g + 2])) * (sa * cs.z);
-                        tr[c * 32 + 4 * g + 3] = (__uint_as_float(a1[4 * g + 3]) + __uint_as_float(a2[4 * g + 3])) * (sa * cs.w);
-                    }
+                for (int g = 0; g < 8; ++g) {
+                    const float4 cs = *reinterpret_cast<const float4*>(colscale + col_im + 4 * g);
+                    own[cc0 + 4 * g + 0] = (__uint_as_float(u1[4 * g + 0]) + __uint_as_float(u2[4 * g + 0])) * (sa * cs.x);
+                    own[cc0 + 4 * g + 1] = (__uint_as_float(u1[4 * g + 1]) + __uint_as_float(u2[4 * g + 1])) * (sa * cs.y);
+                    own[cc0 + 4 * g + 2] = (__uint_as_float(u1[4 * g + 2]) + __uint_as_float(u2[4 * g + 2])) * (sa * cs.z);
+                    own[cc0 + 4 * g + 3] = (__uint_as_float(u1[4 * g + 3]) + __uint_as_float(u2[4 * g + 3])) * (sa * cs.w);
                 }
-                {
-                    uint32_t i1[32], i2[32];
-                    tmem_ld32_nw(tq + col_im, i1);
-                    tmem_ld32_nw(tq + 256 + col_im, i2);
-                    tmem_ld_wait();
+            }
+            {
+                uint32_t u1[32], u2[32];
+                tmem_ld32_nw(tq + col_re, u1);
+                tmem_ld32_nw(tq + 256 + col_re, u2);
+                tmem_ld_wait();
 #pragma unroll
-                    for (int g = 0; g < 8; ++g) {
-                        const float4 cs = *reinterpret_cast<const float4*>(colscale + col_im + 4 * g);
-                        own[cc0 + 4 * g + 0] = (__uint_as_float(i1[4 * g + 0]) + __uint_as_float(i2[4 * g + 0])) * (sa * cs.x);
-                        own[cc0 + 4 * g + 1] = (__uint_as_float(i1[4 * g + 1]) + __uint_as_float(i2[4 * g + 1])) * (sa * cs.y);
-                        own[cc0 + 4 * g + 2] = (__uint_as_float(i1[4 * g + 2]) + __uint_as_float(i2[4 * g + 2])) * (sa * cs.z);
-                        own[cc0 + 4 * g + 3] = (__uint_as_float(i1[4 * g + 3]) + __uint_as_float(i2[4 * g + 3])) * (sa * cs.w);
-                    }
+                for (int g = 0; g < 8; ++g) {
+                    const float4 cs = *reinterpret_cast<const float4*>(colscale + col_re + 4 * g);
+                    tr[4 * g + 0] = (__uint_as_float(u1[4 * g + 0]) + __uint_as_float(u2[4 * g + 0])) * (sa * cs.x);
+                    tr[4 * g + 1] = (__uint_as_float(u1[4 * g + 1]) + __uint_as_float(u2[4 * g + 1])) * (sa * cs.y);
+                    tr[4 * g + 2] = (__uint_as_float(u1[4 * g + 2]) + __uint_as_float(u2[4 * g + 2])) * (sa * cs.z);
+                    tr[4 * g + 3] = (__uint_as_float(u1[4 * g + 3]) + __uint_as_float(u2[4 * g + 3])) * (sa * cs.w);
                 }
             }
             tc_fence_before();
             mbar_arrive(&ctl->tempty[0]);              // tensor memory free: next tile's MMAs start
             ebar();                                    // Ti plane complete
             // TiTi and TrTi sums over this thread's b, and the diagonal Ti_aa
-            float sii[JH], sri[JH], srr[JH], dre[JH], dim_[JH];
+            float sii = 0.f, sri = 0.f;
 #pragma unroll
-            for (int jl = 0; jl < JH; ++jl) { sii[jl] = 0.f; sri[jl] = 0.f; srr[jl] = 0.f; dre[jl] = 0.f; dim_[jl] = 0.f; }
-#pragma unroll
-            for (int k = 0; k < 64; ++k) {
-                const int cc = h * 64 + k, j = cc / Np, b = cc % Np;
-                const int jl = G >= 2 ? j - j0 : 0;
-                const float p = pbase[b * kEPitch + j * Np];    // Ti[b][a] of walker-spin j
-                sii[jl] = fmaf(own[cc], p, sii[jl]);
-                sri[jl] = fmaf(tr[k], p, sri[jl]);
+            for (int k = 0; k < 32; ++k) {
+                const float p = pbase[k * kEPitch];    // Ti[b0 + k][a] of walker-spin j
+                sii = fmaf(own[cc0 + k], p, sii);
+                sri = fmaf(tr[k], p, sri);
             }
-#pragma unroll
-            for (int jl = 0; jl < JH; ++jl) {
-                const int cd = (j0 + jl) * Np + a;               // compact column of the diagonal
-                if (cd >= h * 64 && cd < h * 64 + 64) dim_[jl] = own[cd];
-            }
+            const float dim_ = diag ? own[cd] : 0.f;
             ebar();                                    // every read of the Ti plane done
 #pragma unroll
-            for (int k = 0; k < 64; ++k) own[h * 64 + k] = tr[k];
+            for (int k = 0; k < 32; ++k) own[cc0 + k] = tr[k];
             ebar();                                    // Tr plane complete
             // TrTr sum continues the -TiTi one, so Re X is accumulated in one register
+            float srr = -sii;
 #pragma unroll
-            for (int jl = 0; jl < JH; ++jl) srr[jl] = -sii[jl];
+            for (int k = 0; k < 32; ++k) srr = fmaf(tr[k], pbase[k * kEPitch], srr);
+            const float dre = diag ? own[cd] : 0.f;
+            float v0 = dre, v1 = dim_, v2 = srr, v3 = 2.0f * sri;
 #pragma unroll
-            for (int k = 0; k < 64; ++k) {
-                const int cc = h * 64 + k, j = cc / Np, b = cc % Np;
-                const int jl = G >= 2 ? j - j0 : 0;
-                srr[jl] = fmaf(tr[k], pbase[b * kEPitch + j * Np], srr[jl]);
+            for (int o = 16; o > 0; o >>= 1) {
+                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                v3 += __shfl_xor_sync(0xffffffffu, v3, o);
             }
-#pragma unroll
-            for (int jl = 0; jl < JH; ++jl) {
-                const int cd = (j0 + jl) * Np + a;
-                if (cd >= h * 64 && cd < h * 64 + 64) dre[jl] = own[cd];
-            }
-            float part[JH][4];                         // [j of this half][tr, ti, Xr, Xi]
-#pragma unroll
-            for (int jl = 0; jl < JH; ++jl) {
-                float v0 = dre[jl], v1 = dim_[jl], v2 = srr[jl], v3 = 2.0f * sri[jl];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-                    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-                    v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-                    v3 += __shfl_xor_sync(0xffffffffu, v3, o);
-                }
-                part[jl][0] = v0;
-                part[jl][1] = v1;
-                part[jl][2] = v2;
-                part[jl][3] = v3;
-            }
-            if (lane < 16) {   // ered[h][q][j][v] for every j slot (zeros where this half has none)
+            if (lane < 16) {   // ered[h][q][jj][v] for every walker-spin slot (zeros but j)
                 const int jj = lane >> 2, v = lane & 3;
-                float val = 0.f;
-#pragma unroll
-                for (int jl = 0; jl < JH; ++jl)
-                    if (jj == j0 + jl)
-                        val = v == 0 ? part[jl][0] : (v == 1 ? part[jl][1] : (v == 2 ? part[jl][2] : part[jl][3]));
+                const float val = jj != j ? 0.f : (v == 0 ? v0 : (v == 1 ? v1 : (v == 2 ? v2 : v3)));
                 ered[((h * 4 + q) * 4 + jj) * 4 + v] = val;
             }
             ebar();
             // one thread per (n-block, walker-spin) output: sum over the n-block's quadrants and
-            // the two halves
+            // the four column quarters
             if (et < G * G) {
-                const int ib = et / G, j = et % G;
+                const int ib = et / G, jo = et % G;
                 double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                for (int hh = 0; hh < 2; ++hh)
+                for (int hh = 0; hh < 4; ++hh)
                     for (int qq = ib * Q; qq < (ib + 1) * Q; ++qq) {
-                        const double* e = ered + ((hh * 4 + qq) * 4 + j) * 4;
+                        const double* e = ered + ((hh * 4 + qq) * 4 + jo) * 4;
                         s0 += e[0];
                         s1 += e[1];
                         s2 += e[2];
                         s3 += e[3];
                     }
                 const int n = ng * G + ib;
-                const int ws = wg * G + j;
+                const int ws = wg * G + jo;
                 if (n < es.Nchol && ws < es.nws) {
                     es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
                     es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
                 }
             }
-            ebar();   // ered (aliasing colscale) and the plane are read before the next tile
+            ebar();   // ered, colscale and the plane are read before the next tile rewrites them
         }
     }
     tc_fence_before();
@@ -1262,7 +1231,7 @@ size_t gemm_smem() {
 }
 
 size_t energy_smem() {
-    return 1024 + (size_t)kEStageRing + (size_t)kETileFloats * 4 + 256 * 4 + sizeof(SharedCtl);
+    return 1024 + (size_t)kEStageRing + (size_t)kETileFloats * 4 + 256 * 4 + 256 * 8 + sizeof(SharedCtl);
 }
 
 int g_num_sms = 0;

@@ -701,7 +701,8 @@ int overlap_logdet(afqmc_walkers* wk, int b, bool inverse, cplx* Sout, cplx* ldo
     AFQMC_TRY(tc_overlap3(a3, s->PhiT3_s, WS, 2 * N, b3, s->PsiT3_s, N, M, s->ST64, wk->flags, st));
     count_launch();
     st64_to_S_kernel<<<nb((int64_t)WS * N * N), kT, 0, st>>>(s->ST64, WS, N, Sout);
-    batched_inverse_logdet(Sout, (int64_t)N * N, N, WS, ldout, inverse, wk->flags, st);
+    // S is formed to ~1e-9 here, so the float-float elimination loses nothing
+    batched_inverse_logdet(Sout, (int64_t)N * N, N, WS, ldout, inverse, wk->flags, st, true);
     return AFQMC_OK;
 }
 

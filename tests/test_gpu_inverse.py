@@ -46,7 +46,7 @@ def phase_close(a, b):
 
 
 @pytest.mark.parametrize("N", [33, 40, 63, 64, 65, 96, 100, 127, 128])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_inverse_and_logdet_match_oracle(lib, N, variant):
     rng = np.random.default_rng(N * 10 + variant)
     S = walker_like(rng, 5, N)
@@ -70,9 +70,16 @@ def test_register_and_shared_kernels_agree(lib, N):
     S = walker_like(rng, 7, N)
     _, X1, l1, _ = run(lib, S, 1)
     _, X2, l2, _ = run(lib, S, 2)
+    _, X3, l3, _ = run(lib, S, 3)
     # same pivots (max |re|+|im|, lowest row on ties), different update order: rounding only
     assert np.max(np.abs(X1 - X2)) < 1e-12 * np.max(np.abs(X1))
     assert np.max(np.abs(l1 - l2)) < 1e-12 * N
+    # float-pair elimination: ~2^-44 per operation, times the condition number
+    kappa = max(np.linalg.cond(s) for s in S)
+    print(f"N={N}: float-pair vs FP64 |dX| / |X| {np.max(np.abs(X1 - X3)) / np.max(np.abs(X1)):.2e}, "
+          f"|d logdet| {np.max(np.abs(l1 - l3)):.2e}, kappa {kappa:.0f}")
+    assert np.max(np.abs(X1 - X3)) < 1e-12 * kappa * np.max(np.abs(X1))
+    assert np.max(np.abs(l1 - l3)) < 1e-11 * N
 
 
 @pytest.mark.parametrize("N", [40, 64, 100, 128])
@@ -82,7 +89,7 @@ def test_permutation_matrices(lib, N):
     perms = [rng.permutation(N) for _ in range(4)] + [np.arange(N), np.arange(N)[::-1].copy()]
     S = np.stack([np.eye(N)[p] for p in perms]).astype(np.complex128)
     S[1] *= np.exp(0.7j)        # a phase on every entry: det picks up exp(0.7 i N)
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         rc, X, ld, _ = run(lib, S, variant)
         assert rc == 0, api.afqmc_last_error()
         assert np.array_equal(X[0], S[0].T)
@@ -97,7 +104,7 @@ def test_singular_and_nonfinite(lib, N):
     rng = np.random.default_rng(3)
     S = walker_like(rng, 3, N)
     S[1][:, 5] = 0.0                # a zero column: singular at some step
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         rc, X, ld, _ = run(lib, S, variant)
         assert rc == -5, rc                     # AFQMC_ERR_SINGULAR
         assert ld[1].real == -np.inf
@@ -105,7 +112,7 @@ def test_singular_and_nonfinite(lib, N):
         assert np.max(np.abs(ld[[0, 2]].real - ref.real)) < 1e-12 * N
     T = walker_like(rng, 2, N)
     T[0][3, 3] = np.nan
-    for variant in (1, 2):
+    for variant in (1, 2, 3):
         rc, X, ld, _ = run(lib, T, variant)
         assert rc == -4, rc                     # AFQMC_ERR_NONFINITE
         assert ld[0].real == -np.inf
@@ -126,7 +133,7 @@ def test_inverse_timing_report(lib):
     rng = np.random.default_rng(5)
     S = walker_like(rng, 2048, 128)
     out = {}
-    for variant in (1, 2, 1, 2):
+    for variant in (1, 2, 3, 1, 2, 3):
         rc, _, _, ms = run(lib, S, variant)
         assert rc == 0
         out[variant] = ms
