@@ -7,6 +7,7 @@
 // the Cholesky factorisation of Eq. (3).  All reductions run in a fixed order for
 // a fixed launch shape, so results are bitwise reproducible run to run.
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 
 #include <algorithm>
@@ -646,6 +647,16 @@ struct NumFF {
     }
 };
 
+// 1 / z with one FP64 division: z is first scaled by an exact power of two so that its larger
+// component lies in [1, 2), which keeps |z|^2 away from overflow and underflow.
+__device__ __forceinline__ cplx crecip(cplx z) {
+    int e = 0;
+    frexp(fmax(fabs(z.re), fabs(z.im)), &e);
+    const double xr = ldexp(z.re, 1 - e), xi = ldexp(z.im, 1 - e);
+    const double r = 1.0 / fma(xr, xr, xi * xi);
+    return cplx{ldexp(xr * r, 1 - e), ldexp(-xi * r, 1 - e)};
+}
+
 template <class T, int RQ>
 __device__ __forceinline__ T sel_q(const T (&v)[RQ][4], int q, int u) {
     T r = v[0][u];
@@ -689,7 +700,8 @@ __device__ __forceinline__ void gj_reg_publish(const typename Num::T (&a)[RQ][4]
         const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
         if (v2 > best || (v2 == best && i2 < bi) || (v2 != v2 && best == best)) { best = v2; bi = i2; }
     }
-    const int code = best > 0.0 ? bi : (best != best ? -2 : -1);
+    // a zero column is singular; a NaN or infinite pivot magnitude is non-finite
+    const int code = (best > 0.0 && best <= DBL_MAX) ? bi : (best == 0.0 ? -1 : -2);
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
         const int i = lane + 32 * q;
@@ -705,7 +717,7 @@ __device__ __forceinline__ void gj_reg_publish(const typename Num::T (&a)[RQ][4]
     pv = Num::shfl(pv, bl);
     if (lane == 0) {
         const cplx pc = Num::to(pv);
-        const T inv = Num::from(code >= 0 ? cdiv(cplx{1.0, 0.0}, pc) : cplx{0.0, 0.0});
+        const T inv = Num::from(code >= 0 ? crecip(pc) : cplx{0.0, 0.0});
         *pbuf = code;
         *invbuf = inv;
         *pivbuf = pc;
@@ -774,17 +786,12 @@ __global__ void __launch_bounds__(kGJRegThreads, 1)
         const int uk = k & 3;
         const bool own1 = owns(k + 1);
         const int u1 = (k + 1) & 3;
-        // one element: a -= m prow; column k of the inverse: -m / piv; the pivot row: prow, 1 / piv
+        // one element: a -= m prow, or prow in the pivot row; column k of the inverse (-m / piv,
+        // 1 / piv in the pivot row) is written afterwards by its owner warp alone
         auto upd = [&](int q, int u, const T& m) {
-            const int i = lane + 32 * q;
             T v = a[q][u];
             Num::upd(v, m, prow[u]);
-            if (ownk && u == uk) {
-                v = i == p ? inv : Num::negmul(m, inv);
-            } else if (i == p) {
-                v = prow[u];
-            }
-            a[q][u] = v;
+            a[q][u] = lane + 32 * q == p ? prow[u] : v;
         };
         if (own1) {   // look-ahead: column k+1 first, then its pivot search and publication
 #pragma unroll
@@ -803,6 +810,15 @@ __global__ void __launch_bounds__(kGJRegThreads, 1)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (!(own1 && u == u1)) upd(q, u, m);
+        }
+        if (ownk) {   // warp-uniform: column k of the inverse
+#pragma unroll
+            for (int q = 0; q < RQ; ++q) {
+                const T val = lane + 32 * q == p ? inv : Num::negmul(colbuf[b][lane + 32 * q], inv);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u == uk) a[q][u] = val;
+            }
         }
         gj_sync<C>();
     }

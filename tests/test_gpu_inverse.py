@@ -116,6 +116,12 @@ def test_singular_and_nonfinite(lib, N):
         rc, X, ld, _ = run(lib, T, variant)
         assert rc == -4, rc                     # AFQMC_ERR_NONFINITE
         assert ld[0].real == -np.inf
+    U = walker_like(rng, 2, N)
+    U[1][:, 0] = np.inf                         # an infinite pivot column in the first step
+    for variant in (2, 3):
+        rc, X, ld, _ = run(lib, U, variant)
+        assert rc == -4, rc
+        assert ld[1].real == -np.inf
 
 
 def test_logdet_only_path(lib):
