@@ -1456,10 +1456,118 @@ void split3_rows_ff(const float* hi, const float* lo, int64_t rows, int64_t K, b
         scale);
 }
 
+// The same Taylor step for M = 128 NG: lane t handles the four consecutive orbitals
+// k = 4 t + 128 i (i < NG) of both rows, kept in registers from the norm pass to the split, with
+// 16-byte loads and 8-byte stores of four fp16 slices.
+__device__ __forceinline__ void st4h(__half* p, __half a, __half b, __half c, __half d) {
+    uint2 u;
+    u.x = (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+    u.y = (uint32_t)__half_as_ushort(c) | ((uint32_t)__half_as_ushort(d) << 16);
+    *reinterpret_cast<uint2*>(p) = u;
+}
+template <int NG>
+__global__ void __launch_bounds__(256) taylor_step_ff_v4_kernel(const float* Ch, const float* Cl, float s_hi,
+                                                                float s_lo, float* Ph, float* Pl, int64_t WS, int N,
+                                                                int split, __half* h, __half* m, __half* l,
+                                                                float* scale) {
+    constexpr int M = 128 * NG;
+    const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);   // (ws, j)
+    const int lane = threadIdx.x & 31;
+    if (r >= WS * N) return;
+    const int64_t ws = r / N;
+    const int j = (int)(r % N);
+    const int64_t row0 = ws * 2 * N + j, row1 = row0 + N;   // re, im rows
+    float rh[NG][4], rl[NG][4], ih[NG][4], il[NG][4];       // this step's term P (re, im)
+    float ss = 0.f;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int k = 4 * lane + 128 * i;
+        if (Ch) {
+            const float4 c0h = *reinterpret_cast<const float4*>(Ch + row0 * M + k);
+            const float4 c0l = *reinterpret_cast<const float4*>(Cl + row0 * M + k);
+            const float4 c1h = *reinterpret_cast<const float4*>(Ch + row1 * M + k);
+            const float4 c1l = *reinterpret_cast<const float4*>(Cl + row1 * M + k);
+            const float a0h[4] = {c0h.x, c0h.y, c0h.z, c0h.w}, a0l[4] = {c0l.x, c0l.y, c0l.z, c0l.w};
+            const float a1h[4] = {c1h.x, c1h.y, c1h.z, c1h.w}, a1l[4] = {c1l.x, c1l.y, c1l.z, c1l.w};
+            float4 p0h = *reinterpret_cast<const float4*>(Ph + row0 * M + k);
+            float4 p0l = *reinterpret_cast<const float4*>(Pl + row0 * M + k);
+            float4 p1h = *reinterpret_cast<const float4*>(Ph + row1 * M + k);
+            float4 p1l = *reinterpret_cast<const float4*>(Pl + row1 * M + k);
+            float s0h[4] = {p0h.x, p0h.y, p0h.z, p0h.w}, s0l[4] = {p0l.x, p0l.y, p0l.z, p0l.w};
+            float s1h[4] = {p1h.x, p1h.y, p1h.z, p1h.w}, s1l[4] = {p1l.x, p1l.y, p1l.z, p1l.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ff_mul(-a1h[u], -a1l[u], s_hi, s_lo, rh[i][u], rl[i][u]);   // Re P = -s Im C
+                ff_mul(a0h[u], a0l[u], s_hi, s_lo, ih[i][u], il[i][u]);     // Im P =  s Re C
+                ff_add(s0h[u], s0l[u], rh[i][u], rl[i][u], s0h[u], s0l[u]);
+                ff_add(s1h[u], s1l[u], ih[i][u], il[i][u], s1h[u], s1l[u]);
+                ss = fmaf(rh[i][u], rh[i][u], fmaf(ih[i][u], ih[i][u], ss));
+            }
+            *reinterpret_cast<float4*>(Ph + row0 * M + k) = make_float4(s0h[0], s0h[1], s0h[2], s0h[3]);
+            *reinterpret_cast<float4*>(Pl + row0 * M + k) = make_float4(s0l[0], s0l[1], s0l[2], s0l[3]);
+            *reinterpret_cast<float4*>(Ph + row1 * M + k) = make_float4(s1h[0], s1h[1], s1h[2], s1h[3]);
+            *reinterpret_cast<float4*>(Pl + row1 * M + k) = make_float4(s1l[0], s1l[1], s1l[2], s1l[3]);
+        } else {
+            const float4 p0h = *reinterpret_cast<const float4*>(Ph + row0 * M + k);
+            const float4 p0l = *reinterpret_cast<const float4*>(Pl + row0 * M + k);
+            const float4 p1h = *reinterpret_cast<const float4*>(Ph + row1 * M + k);
+            const float4 p1l = *reinterpret_cast<const float4*>(Pl + row1 * M + k);
+            rh[i][0] = p0h.x; rh[i][1] = p0h.y; rh[i][2] = p0h.z; rh[i][3] = p0h.w;
+            rl[i][0] = p0l.x; rl[i][1] = p0l.y; rl[i][2] = p0l.z; rl[i][3] = p0l.w;
+            ih[i][0] = p1h.x; ih[i][1] = p1h.y; ih[i][2] = p1h.z; ih[i][3] = p1h.w;
+            il[i][0] = p1l.x; il[i][1] = p1l.y; il[i][2] = p1l.z; il[i][3] = p1l.w;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ss = fmaf(rh[i][u], rh[i][u], fmaf(ih[i][u], ih[i][u], ss));
+        }
+    }
+    if (!split) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    float inv, sc;
+    row_scale(ss, inv, sc);
+    if (lane == 0) { scale[row0] = sc; scale[row1] = sc; }
+    constexpr int K2 = 2 * M;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+        const int k = 4 * lane + 128 * i;
+        __half Hr[4], Mr[4], Lr[4], Hi[4], Mi[4], Li[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            slice3(rh[i][u] * inv, rl[i][u] * inv, Hr[u], Mr[u], Lr[u]);
+            slice3(ih[i][u] * inv, il[i][u] * inv, Hi[u], Mi[u], Li[u]);
+        }
+        // doubled rows: row0 = [Re | -Im], row1 = [Im | Re]
+        st4h(h + row0 * K2 + k, Hr[0], Hr[1], Hr[2], Hr[3]);
+        st4h(m + row0 * K2 + k, Mr[0], Mr[1], Mr[2], Mr[3]);
+        st4h(l + row0 * K2 + k, Lr[0], Lr[1], Lr[2], Lr[3]);
+        st4h(h + row0 * K2 + M + k, __hneg(Hi[0]), __hneg(Hi[1]), __hneg(Hi[2]), __hneg(Hi[3]));
+        st4h(m + row0 * K2 + M + k, __hneg(Mi[0]), __hneg(Mi[1]), __hneg(Mi[2]), __hneg(Mi[3]));
+        st4h(l + row0 * K2 + M + k, __hneg(Li[0]), __hneg(Li[1]), __hneg(Li[2]), __hneg(Li[3]));
+        st4h(h + row1 * K2 + k, Hi[0], Hi[1], Hi[2], Hi[3]);
+        st4h(m + row1 * K2 + k, Mi[0], Mi[1], Mi[2], Mi[3]);
+        st4h(l + row1 * K2 + k, Li[0], Li[1], Li[2], Li[3]);
+        st4h(h + row1 * K2 + M + k, Hr[0], Hr[1], Hr[2], Hr[3]);
+        st4h(m + row1 * K2 + M + k, Mr[0], Mr[1], Mr[2], Mr[3]);
+        st4h(l + row1 * K2 + M + k, Lr[0], Lr[1], Lr[2], Lr[3]);
+    }
+}
+
 void taylor_step_ff(const float* Ch, const float* Cl, float s_hi, float s_lo, float* Ph, float* Pl, int64_t WS,
                     int N, int M, bool split, bf16* h, bf16* m, bf16* l, float* scale, cudaStream_t st) {
     if (WS * N <= 0) return;
     count_launch();
+    const unsigned grid = (unsigned)((WS * N + 7) / 8);
+    auto v4 = [&](auto kern) {
+        kern<<<grid, 256, 0, st>>>(Ch, Cl, s_hi, s_lo, Ph, Pl, WS, N, split ? 1 : 0, reinterpret_cast<__half*>(h),
+                                   reinterpret_cast<__half*>(m), reinterpret_cast<__half*>(l), scale);
+    };
+    switch (M) {   // the register form for M = 128, 256, 384, 512
+        case 128: v4(taylor_step_ff_v4_kernel<1>); return;
+        case 256: v4(taylor_step_ff_v4_kernel<2>); return;
+        case 384: v4(taylor_step_ff_v4_kernel<3>); return;
+        case 512: v4(taylor_step_ff_v4_kernel<4>); return;
+        default: break;
+    }
     taylor_step_ff_kernel<<<(unsigned)((WS * N + 7) / 8), 256, 0, st>>>(
         Ch, Cl, s_hi, s_lo, Ph, Pl, WS, N, M, split ? 1 : 0, reinterpret_cast<__half*>(h),
         reinterpret_cast<__half*>(m), reinterpret_cast<__half*>(l), scale);
