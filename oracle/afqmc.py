@@ -34,7 +34,14 @@ notes of the repository):
   * weight: w <- w |I| max(0, cos dtheta), I = r exp(x.xbar - xbar.xbar/2)
     exp(tau (E_T - E0)), r = <Psi|Phi'>/<Psi|Phi>, dtheta = arg r (non-conjugated
     bilinear forms in the exponent).
-  * E_T is the trial's own local energy, fixed.  No population control.
+  * E_T is the trial's own local energy, fixed.
+  * local-energy weights (mode "local"): w <- w exp(-tau (E_b - E_T)) max(0, cos dtheta)
+    with E_b = Re E_L(Phi) of the pre-propagation walker, bounded to E_T +- 2/sqrt(tau).
+    This is the first-order form of the hybrid weight: averaged over the fields, the
+    hybrid importance factor is exp(-tau (E_L - E_T)) + O(tau^2).
+  * population control (comb, outside the step): W slots at (k + xi) W_tot / W against
+    the running sum of the weights; slot k takes the walker whose interval holds it; every
+    new walker gets weight W_tot / W.
   * walkers with w == 0 are frozen; the energy is measured at the
     pre-propagation Phi with the weights before the update.
   * QR every k_qr steps with diag(R) > 0; logS <- logS - sum log det R.
@@ -86,7 +93,8 @@ class Params:
     k_taylor: int = 6
     k_qr: int = 0            # 0: never re-orthonormalise
     fb_cap: float = 1.0      # <= 0 disables the cap
-    mode: str = "phaseless"  # or "free" (free projection: complex weights, no cap, no cos)
+    mode: str = "phaseless"  # "free" (free projection: complex weights, no cap, no cos) or
+                             # "local" (local-energy weights with the energy bound)
 
 
 @dataclass
@@ -269,6 +277,8 @@ def step(ham: Hamiltonian, Psi: Sequence[np.ndarray], B: np.ndarray, wk: Walkers
     ok = alive & np.isfinite(newlogS)
     if free:
         neww = wk.w * np.exp(expo)
+    elif p.mode == "local":
+        neww = wk.w * local_energy_factor(E_L, wk.E_T, p.tau) * np.maximum(0.0, np.cos(dl.imag))
     else:
         neww = wk.w * np.exp(expo.real) * np.maximum(0.0, np.cos(dl.imag))
     wk.w = np.where(ok, neww, np.where(alive, 0.0, wk.w))
@@ -283,6 +293,57 @@ def step(ham: Hamiltonian, Psi: Sequence[np.ndarray], B: np.ndarray, wk: Walkers
             wk.Phi[s] = np.where(live[:, None, None], Q, wk.Phi[s])
             wk.logS = np.where(live, wk.logS - ldr, wk.logS)
     return E_L, E_mix
+
+
+def energy_bound(E_L: np.ndarray, E_T: float, tau: float) -> np.ndarray:
+    """Re E_L clipped to E_T +- 2/sqrt(tau)."""
+    b = 2.0 / np.sqrt(tau)
+    return np.clip(np.real(E_L), E_T - b, E_T + b)
+
+
+def local_energy_factor(E_L: np.ndarray, E_T: float, tau: float) -> np.ndarray:
+    """exp(-tau (E_b - E_T)) with the bounded local energy E_b."""
+    return np.exp(-tau * (energy_bound(E_L, E_T, tau) - E_T))
+
+
+def comb(w: np.ndarray, xi: float) -> np.ndarray:
+    """Comb population control: indices of the W walkers that fill the W new slots.
+
+    Slot k (k = 0..W-1) sits at u_k = (k + xi) W_tot / W on the running sum of the weights
+    c_j = w_0 + ... + w_j (accumulated left to right in float64); it takes the first walker
+    j with c_j > u_k (the last live walker if rounding leaves none).  A walker of weight w_j is copied floor or ceil of W w_j / W_tot times;
+    walkers of weight 0 are never taken.  xi in [0, 1) is the one random number of the comb."""
+    w = np.asarray(w, dtype=np.float64)
+    W = w.size
+    c = np.empty(W)
+    acc = 0.0
+    for j in range(W):
+        acc += w[j]
+        c[j] = acc
+    total = acc
+    live = np.nonzero(w > 0)[0]
+    last = int(live[-1]) if live.size else W - 1   # a slot rounded onto the total takes it
+    idx = np.empty(W, dtype=np.int64)
+    j = 0
+    for k in range(W):
+        u = (k + xi) * total / W
+        while j < last and not (c[j] > u):
+            j += 1
+        idx[k] = j
+    return idx
+
+
+def population_control(wk: Walkers, xi: float) -> np.ndarray:
+    """Apply the comb to walkers in place (phaseless weights only); returns the indices."""
+    if np.iscomplexobj(wk.w):
+        raise ValueError("population control needs real weights")
+    idx = comb(wk.w, xi)
+    total = float(np.sum(wk.w))
+    for s in range(2):
+        wk.Phi[s] = wk.Phi[s][idx].copy()
+    wk.logS = wk.logS[idx].copy()
+    wk.w = np.full(wk.w.size, total / wk.w.size)
+    return idx
 
 
 def run(ham: Hamiltonian, Psi: Sequence[np.ndarray], W: int, fields: np.ndarray, p: Params,
