@@ -58,6 +58,9 @@ extern "C" {
 
 #define AFQMC_WEIGHT_PHASELESS 0  /* w <- w |I| max(0, cos dtheta)  (hybrid form)        */
 #define AFQMC_WEIGHT_FREE      1  /* free projection: complex weights, no cap, no cos   */
+#define AFQMC_WEIGHT_LOCAL     2  /* local energy: w <- w exp(-tau (E_b - E_T)) max(0, cos dtheta),
+                                     E_b = Re E_L of the pre-step walker clipped to E_T +- 2/sqrt(tau);
+                                     measures E_L every step                                   */
 
 typedef struct afqmc_opts {
     int    precision;    /* AFQMC_PREC_*                                           */
@@ -152,6 +155,18 @@ int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_
  * Computed in FP64 whatever the walker set's precision. */
 int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, double* dPsi_up,
                           double* dPsi_dn, double* dL, void* stream);
+
+/* Comb population control (outside the step; phaseless or local-energy weights).  With
+ * W_tot = sum_j w_j and the running sums c_j = w_0 + ... + w_j (FP64, left to right), new walker
+ * k (k = 0..W-1) is a copy of the first walker j with c_j > (k + xi) W_tot / W (the last live
+ * walker if rounding leaves none), and every new weight is W_tot / W.  A walker is copied floor
+ * or ceil of W w_j / W_tot times; dead walkers are never copied.  xi in [0, 1) is the comb's one
+ * random number, supplied by the caller.  idx (host or device, W ints, may be NULL) receives
+ * the source walker of every new walker.  The walkers' overlaps and (BF16X3) split operands
+ * are rebuilt.  Errors: BADARG (null handle, xi outside [0, 1), free-projection weights,
+ * no live walker), CUDA.  The paper does not describe population control; this is the
+ * standard comb, applied between steps. */
+int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream);
 
 /* ---- Walker state (checkpoint / resume and inspection) -------------------
  * Phi  complex [W][M*Nup + M*Ndn] (layout of Phi0), w [W] (complex [W] for

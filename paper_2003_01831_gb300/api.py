@@ -27,7 +27,7 @@ ERRORS = {
     -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED",
 }
 PREC_FP64, PREC_BF16X3 = 0, 1
-WEIGHT_PHASELESS, WEIGHT_FREE = 0, 1
+WEIGHT_PHASELESS, WEIGHT_FREE, WEIGHT_LOCAL = 0, 1, 2
 
 EXPORTED = [
     "afqmc_default_opts", "afqmc_create_hamiltonian", "afqmc_destroy_hamiltonian",
@@ -35,7 +35,7 @@ EXPORTED = [
     "afqmc_energy_backward", "afqmc_get_walkers", "afqmc_set_walkers",
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
     "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
-    "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune",
+    "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune", "afqmc_population_control",
 ]
 PAD_AUTO, PAD_ALWAYS = 0, 1
 SEED_STRIDE = 0x9E3779B97F4A7C15   # system s of a batch draws with key seed + s * SEED_STRIDE
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
         "afqmc_batch_get_walkers": (i, [vp, i, vp, vp, ctypes.POINTER(i64), vp]),
         "afqmc_batch_info": (i, [vp, i, vp, ctypes.POINTER(i)]),
         "afqmc_batch_autotune": (i, [vp, i, ctypes.POINTER(d), vp]),
+        "afqmc_population_control": (i, [vp, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -207,6 +208,12 @@ def afqmc_get_walkers(wk: int, Phi=None, w=None, stream=None) -> int:
 
 def afqmc_set_walkers(wk: int, Phi=None, w=None, step: int = 0, stream=None):
     _check(lib().afqmc_set_walkers(wk, _ptr(Phi), _ptr(w), int(step), _stream(stream)))
+
+
+def afqmc_population_control(wk: int, xi: float, idx=None, stream=None):
+    """Comb population control with the uniform number xi in [0, 1); idx (int32 [W]) receives
+    the source walker of every new walker."""
+    _check(lib().afqmc_population_control(wk, float(xi), _ptr(idx), _stream(stream)))
 
 
 def afqmc_philox_fields(seed: int, step: int, W: int, Nchol: int, x, stream=None):

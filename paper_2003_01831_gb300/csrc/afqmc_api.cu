@@ -212,7 +212,8 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         return fail(AFQMC_ERR_SHAPE, "init_walkers: need 1 <= Nup, Ndn <= min(M, 128) and W >= 1");
     if (!(tau > 0.0) || !isfinite(tau)) return fail(AFQMC_ERR_BADARG, "init_walkers: tau must be > 0");
     if (o.k_taylor < 1 || o.k_taylor > 32 || o.k_qr < 0 ||
-        (o.weight_mode != AFQMC_WEIGHT_PHASELESS && o.weight_mode != AFQMC_WEIGHT_FREE) ||
+        (o.weight_mode != AFQMC_WEIGHT_PHASELESS && o.weight_mode != AFQMC_WEIGHT_FREE &&
+         o.weight_mode != AFQMC_WEIGHT_LOCAL) ||
         (o.precision != AFQMC_PREC_FP64 && o.precision != AFQMC_PREC_BF16X3) || !isfinite(o.fb_cap))
         return fail(AFQMC_ERR_BADARG, "init_walkers: invalid option value");
     for (int r : o.reserved)
@@ -426,9 +427,11 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
     const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
     wk->ev_valid = false;
     const long long launches0 = launch_count();
+    // local-energy weights need E_L of every pre-step walker
+    const bool local = wk->opts.weight_mode == AFQMC_WEIGHT_LOCAL;
     for (int s = 0; s < nsteps; ++s) {
         const bool meas = measure_every > 0 && s % measure_every == 0;
-        AFQMC_TRY(tc ? tc_measure(wk, meas, st) : fp64_measure(wk, meas, st));
+        AFQMC_TRY(tc ? tc_measure(wk, meas || local, st) : fp64_measure(wk, meas || local, st));
         if (meas) mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix + s / measure_every, st);
         const double* xs;
         if (x_dev) {
@@ -452,6 +455,53 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
     unsigned fl = 0;
     AFQMC_TRY(read_flags(wk->flags, st, &fl));
     return flags_to_error(fl, "step");
+}
+
+int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "population_control: NULL handle");
+    if (!(xi >= 0.0 && xi < 1.0)) return fail(AFQMC_ERR_BADARG, "population_control: xi must lie in [0, 1)");
+    if (wk->opts.weight_mode == AFQMC_WEIGHT_FREE)
+        return fail(AFQMC_ERR_BADARG, "population_control: needs real (phaseless or local-energy) weights");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
+    const int W = wk->W, M = wk->M;
+    struct Scratch {
+        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Scratch() {
+            for (void* q : p)
+                if (q) cudaFree(q);
+        }
+    } sc;
+    if (cudaMalloc(&sc.p[0], sizeof(int) * W) != cudaSuccess || cudaMalloc(&sc.p[1], sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&sc.p[2], sizeof(cplx) * (size_t)W * M * std::max(wk->N[0], wk->N[1])) != cudaSuccess ||
+        cudaMalloc(&sc.p[3], sizeof(cplx) * W) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AFQMC_ERR_OOM, "population_control: scratch");
+    }
+    int* d_idx = static_cast<int*>(sc.p[0]);
+    double* d_total = static_cast<double*>(sc.p[1]);
+    cplx* tmp = static_cast<cplx*>(sc.p[2]);
+    comb_indices(wk->weight, W, xi, d_idx, d_total, st);
+    double total = 0.0;
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(&total, d_total, sizeof(double), cudaMemcpyDeviceToHost, st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(total > 0.0) || !isfinite(total)) return fail(AFQMC_ERR_BADARG, "population_control: no live walker");
+    if (tc) AFQMC_TRY(tc_sync_walkers_to_fp64(wk, st));
+    for (int s = 0; s < 2; ++s) {
+        const int64_t per = (int64_t)M * wk->N[s];
+        gather_rows(wk->f.Phi[s], per, d_idx, W, tmp, st);
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(wk->f.Phi[s], tmp, sizeof(cplx) * per * W, cudaMemcpyDeviceToDevice, st));
+    }
+    cplx* ltmp = static_cast<cplx*>(sc.p[3]);
+    gather_rows(wk->logS_old, 1, d_idx, W, ltmp, st);
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(wk->logS_old, ltmp, sizeof(cplx) * W, cudaMemcpyDeviceToDevice, st));
+    equal_weights(wk->weight, W, d_total, st);
+    if (tc) AFQMC_TRY(tc_sync_walkers_from_fp64(wk, st));
+    if (idx) AFQMC_CUDA_TRY(cudaMemcpyAsync(idx, d_idx, sizeof(int) * W, cudaMemcpyDefault, st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    unsigned fl = 0;
+    AFQMC_TRY(read_flags(wk->flags, st, &fl));
+    return flags_to_error(fl, "population_control");
 }
 
 int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_mix, void* stream) {

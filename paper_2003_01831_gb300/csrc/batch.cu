@@ -413,6 +413,8 @@ int afqmc_create_batch(int nsys, const afqmc_system* sys, double tau, const afqm
     afqmc_opts o;
     afqmc_default_opts(&o);
     if (opts) o = *opts;
+    if (o.weight_mode == AFQMC_WEIGHT_LOCAL)   // the captured steps measure E_L only on measuring steps
+        return fail(AFQMC_ERR_UNSUPPORTED, "create_batch: local-energy weights are not supported in batches");
     for (int s = 0; s < nsys; ++s) {
         const afqmc_system& y = sys[s];
         if (!y.h || !y.L || !y.Psi_up || !y.Psi_dn)

@@ -1017,6 +1017,13 @@ __global__ void __launch_bounds__(kThreads) weight_kernel(WeightArgs a) {
     if (a.mode == AFQMC_WEIGHT_FREE) {
         const double m = exp(ex.re);
         a.weight[w] = w0 * cplx{m * cos(ex.im), m * sin(ex.im)};
+    } else if (a.mode == AFQMC_WEIGHT_LOCAL) {
+        // exp(-tau (E_b - E_T)), E_b the pre-step Re E_L bounded to E_T +- ebound
+        const double el = a.E_L[w].re;
+        if (!(el == el)) { a.accept[w] = 0; a.weight[w] = cplx{0.0, 0.0}; return; }
+        const double eb = fmin(fmax(el, a.E_T - a.ebound), a.E_T + a.ebound);
+        const double c = cos(dl.im);
+        a.weight[w] = cplx{w0.re * exp(-a.tau * (eb - a.E_T)) * (c > 0.0 ? c : 0.0), 0.0};
     } else {
         const double c = cos(dl.im);
         a.weight[w] = cplx{w0.re * exp(ex.re) * (c > 0.0 ? c : 0.0), 0.0};
@@ -1241,6 +1248,54 @@ void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int 
                      unsigned* flags, cudaStream_t st) {
     count_launch();
     hs_coeff_kernel<<<blocks_for((int64_t)W * Nchol), kThreads, 0, st>>>(x, xbar, weight, W, Nchol, c, flags);
+}
+
+// Comb population control on one thread: the running sums must be formed left to right in
+// FP64 so that every slot falls in the same interval as in any other implementation of the same
+// definition.  Slot k sits at (k + xi) total / W (no fused multiply-add can form here).
+__global__ void comb_kernel(const cplx* weight, int W, double xi, int* idx, double* total_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double total = 0.0;
+    int last = W - 1;
+    bool any = false;
+    for (int j = 0; j < W; ++j) {
+        total += weight[j].re;
+        if (weight[j].re > 0.0) { last = j; any = true; }
+    }
+    if (!any) last = W - 1;
+    *total_out = total;
+    int j = 0;
+    double c = weight[0].re;
+    for (int k = 0; k < W; ++k) {
+        const double u = ((double)k + xi) * total / (double)W;
+        while (j < last && !(c > u)) c += weight[++j].re;
+        idx[k] = j;
+    }
+}
+__global__ void gather_rows_kernel(const cplx* src, int64_t per, const int* idx, int W, cplx* dst) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)W * per) return;
+    const int64_t w = i / per, e = i % per;
+    dst[i] = src[(int64_t)idx[w] * per + e];
+}
+__global__ void equal_weights_kernel(cplx* weight, int W, const double* total) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < W) weight[w] = cplx{*total / (double)W, 0.0};
+}
+
+void comb_indices(const cplx* weight, int W, double xi, int* idx, double* total, cudaStream_t st) {
+    count_launch();
+    comb_kernel<<<1, 32, 0, st>>>(weight, W, xi, idx, total);
+}
+void gather_rows(const cplx* src, int64_t per, const int* idx, int W, cplx* dst, cudaStream_t st) {
+    const int64_t n = (int64_t)W * per;
+    if (n <= 0) return;
+    count_launch();
+    gather_rows_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(src, per, idx, W, dst);
+}
+void equal_weights(cplx* weight, int W, const double* total, cudaStream_t st) {
+    count_launch();
+    equal_weights_kernel<<<(W + kThreads - 1) / kThreads, kThreads, 0, st>>>(weight, W, total);
 }
 
 void weight_update(const WeightArgs& a, cudaStream_t st) {

@@ -81,10 +81,20 @@ struct WeightArgs {
     const cplx* logS_old;
     const cplx* logS_new;
     double tau, E_T, E0;
+    const cplx* E_L;   // local-energy mode: pre-step local energies
+    double ebound;     // local-energy mode: |Re E_L - E_T| bound
     cplx* weight;      // in/out
     int* accept;       // out: 1 = take Phi'
 };
 void weight_update(const WeightArgs& a, cudaStream_t st);
+
+// Comb population control: idx[k] = source walker of new walker k, *total = sum of the weights
+// real parts (the new weight is total / W).  One thread, running sums left to right in FP64.
+void comb_indices(const cplx* weight, int W, double xi, int* idx, double* total, cudaStream_t st);
+// dst[w] = src[idx[w]] for W rows of `per` complex elements.
+void gather_rows(const cplx* src, int64_t per, const int* idx, int W, cplx* dst, cudaStream_t st);
+// weight[w] = total / W (real).
+void equal_weights(cplx* weight, int W, const double* total, cudaStream_t st);
 
 // Phi[w] <- Phi_new[w] where accept[w]; `per_walker` complex elements per walker.
 void commit_walkers(cplx* Phi, const cplx* Phi_new, const int* accept, int W, int64_t per_walker,

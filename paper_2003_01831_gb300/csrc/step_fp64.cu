@@ -194,6 +194,7 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
     WeightArgs a;
     a.W = W; a.Nchol = nch; a.mode = wk->opts.weight_mode;
     a.x = x; a.xbar = wk->xbar; a.logS_old = wk->logS_old; a.logS_new = wk->logS_new;
+    a.E_L = wk->E_L; a.ebound = 2.0 / sqrt(wk->tau);
     a.tau = wk->tau; a.E_T = wk->E_T; a.E0 = wk->ham->E0;
     a.weight = wk->weight; a.accept = wk->accept;
     weight_update(a, st);

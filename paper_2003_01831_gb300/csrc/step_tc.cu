@@ -1006,6 +1006,8 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     a.xbar = wk->xbar;
     a.logS_old = wk->logS_old;
     a.logS_new = wk->logS_new;
+    a.E_L = wk->E_L;
+    a.ebound = 2.0 / sqrt(wk->tau);
     a.tau = wk->tau;
     a.E_T = wk->E_T;
     a.E0 = wk->ham->E0;

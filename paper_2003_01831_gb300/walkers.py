@@ -80,6 +80,13 @@ class AFQMC:
         step = api.afqmc_get_walkers(self.wk, Phi, w, self.stream)
         return Phi[:, :M * Nu].reshape(self.W, M, Nu), Phi[:, M * Nu:].reshape(self.W, M, Nd), w, step
 
+    def population_control(self, xi: float) -> np.ndarray:
+        """Comb population control (phaseless or local-energy weights); returns the source
+        walker of every new walker."""
+        idx = np.zeros(self.W, dtype=np.int32)
+        api.afqmc_population_control(self.wk, xi, idx, self.stream)
+        return idx
+
     def set_walkers(self, Phi_up, Phi_dn, w, step: int):
         Phi = np.ascontiguousarray(np.concatenate(
             [np.asarray(Phi_up).reshape(self.W, -1), np.asarray(Phi_dn).reshape(self.W, -1)], axis=1),

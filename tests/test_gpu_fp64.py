@@ -44,7 +44,7 @@ def run_parity(h, L, E0, Psi, W, tau, nsteps, k_qr, x, Phi0=None, fb_cap=1.0, mo
     p = O.Params(tau=tau, k_taylor=K, k_qr=k_qr, fb_cap=fb_cap, mode=mode)
     B = O.half_one_body_propagator(ham, tau)
     wk = O.init_walkers(ham, Psi, W, Phi0, complex_weights=(mode == "free"))
-    wm = api.WEIGHT_FREE if mode == "free" else api.WEIGHT_PHASELESS
+    wm = {"free": api.WEIGHT_FREE, "local": api.WEIGHT_LOCAL}.get(mode, api.WEIGHT_PHASELESS)
     with AFQMC(h, L, E0, Psi[0], Psi[1], W, tau, Phi0=Phi0, k_taylor=K, k_qr=k_qr, fb_cap=fb_cap,
                weight_mode=wm) as g:
         E_L, w, logS, Emix = g.energy()
