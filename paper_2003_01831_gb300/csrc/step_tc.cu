@@ -1,7 +1,9 @@
 // Mixed-precision (BF16X3) walker-step driver.  The dense contractions of the phaseless
-// step (Sec. V; Zhang & Krakauer 2003, Motta & Zhang 2018) run on tcgen05 tensor cores
-// through the split-bf16 GEMM engine; the overlap LU / log-det / inverse, the QR
-// re-orthonormalisation, the energy and weight reductions stay in FP64 (kernels_fp64.cu).
+// step (Sec. V; Zhang & Krakauer 2003, Motta & Zhang 2018) run on tcgen05 tensor cores with
+// row-scaled fp16 split operands (two slices for the Green's function and the energy, three
+// for the overlap, the propagation and the QR's Gram matrix and R^-1 product); the overlap
+// inverse runs in float pairs with FP64 pivots and log-determinant, the Cholesky factor and
+// the energy and weight reductions in FP64 (kernels_fp64.cu).
 //
 // Device layouts (W walkers, both spins, N electrons per spin, complex stored planar):
 //   PhiT   [W][2][2][N][M] FP64 master walkers, transposed (row (s, c, j) = column j of
@@ -73,7 +75,7 @@ struct TcState {
     cplx *tE = nullptr, *XE = nullptr;
     float* tFB = nullptr;
     cplx* E1 = nullptr;
-    // propagation (three-slice operands, FP64 intermediates)
+    // propagation (three-slice operands, float-float intermediates)
     double* cfp = nullptr;                 // [W][2][Nchol] HS coefficients, planar
     bf16* cf3[3] = {nullptr, nullptr, nullptr};
     float* cf3_s = nullptr;
