@@ -14,6 +14,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "ffc.cuh"
 #include "kernels_fp64.cuh"
 
 namespace afqmc {
@@ -575,25 +576,6 @@ constexpr int kGJRegThreads = 512;  // 16 warps x 4 columns
 // re, im a float pair hi + lo (~2^-44 relative, the TwoProduct / TwoSum error-free transforms on
 // the fp32 pipe, which is ~64x GB300's FP64 pipe); pivot reciprocals, the read-out and the
 // log-determinant are FP64 either way.
-struct __align__(16) ffc {   // 16-byte aligned: the peer CTA receives it as one 16-byte store
-    float rh, rl, ih, il;
-};
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float v = s - a;
-    e = (a - (s - v)) + (b - v);
-}
-// (h, l) + x y for float pairs: TwoProduct of the leading parts, first-order cross terms
-__device__ __forceinline__ void ff_fma(float& h, float& l, float xh, float xl, float yh, float yl) {
-    const float p = xh * yh;
-    float pe = fmaf(xh, yh, -p);
-    pe = fmaf(xh, yl, fmaf(xl, yh, pe));
-    float s, e;
-    two_sum(h, p, s, e);
-    e += l + pe;
-    h = s + e;
-    l = e - (h - s);
-}
 struct NumD {
     using T = cplx;
     __device__ static T from(cplx v) { return v; }

@@ -33,6 +33,7 @@
 #include <utility>
 #include <vector>
 
+#include "ffc.cuh"
 #include "kernels_tc.cuh"
 #include "state.cuh"
 #include "tc_ptx.cuh"
@@ -475,13 +476,40 @@ __global__ void __launch_bounds__(kT) gram_planar_kernel(const double* PhiT, int
 
 // In place on G[ws]: upper Cholesky factor R (G = R^H R, real positive diagonal), then its
 // inverse, left in the upper triangle (the strict lower triangle is zeroed).  The upper
-// triangle is staged in shared memory, packed row by row.  A non-positive or non-finite
-// pivot sets FLAG_NONFINITE and leaves the identity (the walker keeps its orbitals).
+// triangle is staged in shared memory, packed row by row, as float pairs (ffc.cuh: ~2^-44
+// relative on the fp32 pipe; the Gram matrix it factors is formed to ~1e-9), with the square
+// roots and reciprocals of the diagonal in FP64.  A non-positive or non-finite pivot sets
+// FLAG_NONFINITE and leaves the identity (the walker keeps its orbitals).
 __device__ __forceinline__ int upk(int i, int j, int N) { return i * N - (i * (i - 1)) / 2 + (j - i); }
+__device__ __forceinline__ ffc ff_from(cplx v) {
+    const float rh = (float)v.re, ih = (float)v.im;
+    return ffc{rh, (float)(v.re - (double)rh), ih, (float)(v.im - (double)ih)};
+}
+__device__ __forceinline__ cplx ff_to(const ffc& v) {
+    return cplx{(double)v.rh + (double)v.rl, (double)v.ih + (double)v.il};
+}
+__device__ __forceinline__ ffc ff_scaled(const ffc& a, float sh, float sl) {   // a s, s real
+    ffc r{0.f, 0.f, 0.f, 0.f};
+    ff_fma(r.rh, r.rl, a.rh, a.rl, sh, sl);
+    ff_fma(r.ih, r.il, a.ih, a.il, sh, sl);
+    return r;
+}
+__device__ __forceinline__ void ff_sub_conj_mul(ffc& a, const ffc& x, const ffc& y) {   // a -= conj(x) y
+    ff_fma(a.rh, a.rl, -x.rh, -x.rl, y.rh, y.rl);
+    ff_fma(a.rh, a.rl, -x.ih, -x.il, y.ih, y.il);
+    ff_fma(a.ih, a.il, -x.rh, -x.rl, y.ih, y.il);
+    ff_fma(a.ih, a.il, x.ih, x.il, y.rh, y.rl);
+}
+__device__ __forceinline__ void ff_add_mul(ffc& a, const ffc& x, const ffc& y) {   // a += x y
+    ff_fma(a.rh, a.rl, x.rh, x.rl, y.rh, y.rl);
+    ff_fma(a.rh, a.rl, -x.ih, -x.il, y.ih, y.il);
+    ff_fma(a.ih, a.il, x.rh, x.rl, y.ih, y.il);
+    ff_fma(a.ih, a.il, x.ih, x.il, y.rh, y.rl);
+}
 
 __global__ void __launch_bounds__(kT) chol_inv_kernel(cplx* G, int N, const cplx* weight, unsigned* flags) {
     extern __shared__ __align__(16) unsigned char qsm[];
-    cplx* U = reinterpret_cast<cplx*>(qsm);        // packed upper triangle, N (N+1) / 2
+    ffc* U = reinterpret_cast<ffc*>(qsm);          // packed upper triangle, N (N+1) / 2
     __shared__ int s_bad;
     const int ws = blockIdx.x, t = threadIdx.x;
     cplx* Gw = G + (int64_t)ws * N * N;
@@ -489,29 +517,30 @@ __global__ void __launch_bounds__(kT) chol_inv_kernel(cplx* G, int N, const cplx
     const int NP = N * (N + 1) / 2;
     if (t == 0) s_bad = 0;
     for (int i = 0; i < N; ++i)
-        for (int j = i + t; j < N; j += kT) U[upk(i, j, N)] = dead ? cplx{i == j ? 1.0 : 0.0, 0.0} : Gw[(int64_t)i * N + j];
+        for (int j = i + t; j < N; j += kT)
+            U[upk(i, j, N)] = ff_from(dead ? cplx{i == j ? 1.0 : 0.0, 0.0} : Gw[(int64_t)i * N + j]);
     __syncthreads();
     if (!dead) {
         // right-looking Cholesky: row k of R, then the trailing upper triangle
         for (int k = 0; k < N; ++k) {
-            const double d2 = U[upk(k, k, N)].re;
+            const double d2 = (double)U[upk(k, k, N)].rh + (double)U[upk(k, k, N)].rl;
             if (!(d2 > 0.0) || !isfinite(d2)) {
                 if (t == 0) s_bad = 1;
                 break;
             }
             const double d = sqrt(d2), id = 1.0 / d;
+            const float idh = (float)id, idl = (float)(id - (double)idh);
             __syncthreads();
             for (int j = k + t; j < N; j += kT) {
-                const cplx v = U[upk(k, j, N)];
-                U[upk(k, j, N)] = j == k ? cplx{d, 0.0} : id * v;
+                const int e = upk(k, j, N);
+                U[e] = j == k ? ff_from(cplx{d, 0.0}) : ff_scaled(U[e], idh, idl);
             }
             __syncthreads();
             const int nr = N - k - 1;
             for (int e = t; e < nr * nr; e += kT) {   // trailing upper triangle k < i <= j
                 const int ii = k + 1 + e / nr, jj = k + 1 + e % nr;
                 if (jj < ii) continue;
-                const cplx rki = U[upk(k, ii, N)], rkj = U[upk(k, jj, N)];
-                cfma(U[upk(ii, jj, N)], cplx{0.0, 0.0} - conjg(rki), rkj);
+                ff_sub_conj_mul(U[upk(ii, jj, N)], U[upk(k, ii, N)], U[upk(k, jj, N)]);
             }
             __syncthreads();
         }
@@ -521,19 +550,19 @@ __global__ void __launch_bounds__(kT) chol_inv_kernel(cplx* G, int N, const cplx
             // X[j][j] = 1 / R[j][j]; X[i][j] = -(sum_{p=i..j-1} X[i][p] R[p][j]) / R[j][j]
             // (N <= kT: thread i owns row i of column j)
             for (int j = 0; j < N; ++j) {
-                const double rjj = U[upk(j, j, N)].re;
-                const double ir = 1.0 / rjj;
+                const double ir = 1.0 / ((double)U[upk(j, j, N)].rh + (double)U[upk(j, j, N)].rl);
+                const float irh = (float)ir, irl = (float)(ir - (double)irh);
                 // row i < j reads X[i][p] (p < j, final) and R[p][j] (column j, still R): the new
                 // column is written only after every row has read it
-                cplx val{0.0, 0.0};
+                ffc val{0.f, 0.f, 0.f, 0.f};
                 if (t < j) {
-                    cplx acc{0.0, 0.0};
-                    for (int p = t; p < j; ++p) cfma(acc, U[upk(t, p, N)], U[upk(p, j, N)]);
-                    val = cplx{-acc.re * ir, -acc.im * ir};
+                    ffc acc{0.f, 0.f, 0.f, 0.f};
+                    for (int p = t; p < j; ++p) ff_add_mul(acc, U[upk(t, p, N)], U[upk(p, j, N)]);
+                    val = ff_scaled(acc, -irh, -irl);
                 }
                 __syncthreads();
                 if (t < j) U[upk(t, j, N)] = val;
-                if (t == 0) U[upk(j, j, N)] = cplx{ir, 0.0};
+                if (t == 0) U[upk(j, j, N)] = ff_from(cplx{ir, 0.0});
                 __syncthreads();
             }
         }
@@ -541,14 +570,14 @@ __global__ void __launch_bounds__(kT) chol_inv_kernel(cplx* G, int N, const cplx
     __syncthreads();
     if (s_bad) {
         if (t == 0) atomicOr(flags, FLAG_NONFINITE);
-        for (int e = t; e < NP; e += kT) U[e] = cplx{0.0, 0.0};
+        for (int e = t; e < NP; e += kT) U[e] = ffc{0.f, 0.f, 0.f, 0.f};
         __syncthreads();
-        for (int i = t; i < N; i += kT) U[upk(i, i, N)] = cplx{1.0, 0.0};
+        for (int i = t; i < N; i += kT) U[upk(i, i, N)] = ffc{1.f, 0.f, 0.f, 0.f};
         __syncthreads();
     }
     for (int e = t; e < N * N; e += kT) {
         const int i = e / N, j = e % N;
-        Gw[e] = i <= j ? U[upk(i, j, N)] : cplx{0.0, 0.0};
+        Gw[e] = i <= j ? ff_to(U[upk(i, j, N)]) : cplx{0.0, 0.0};
     }
 }
 
