@@ -7,7 +7,11 @@ What the paper fixes (Sec. V):
   * Eq. (1): H = sum_ij h_ij c+_i c_j + 1/2 sum_ijkl v_ijkl c+_i c+_j c_l c_k + E_II
     (spin summed; E_II is called E0 here).
   * Eq. (3): v_ijkl = V_(ik),(lj) ~= sum_n L^n_ik L^n*_lj with Nchol Cholesky
-    vectors.  This oracle takes real symmetric L_n, so v_ijkl = sum_n L^n_ik L^n_jl.
+    vectors.  The step works with Hermitian L_n (real symmetric ones in the production
+    workloads), for which v_ijkl = sum_n L^n_ik L^n_jl.  General complex L_n are reduced to
+    2 Nchol Hermitian ones by ``hermitian_split``: with A_n = (L_n + L_n^+)/2 and
+    B_n = (L_n - L_n^+)/(2i), sum_n L^n_ik L^n*_lj and sum_n (A_ik A*_lj + B_ik B*_lj) differ
+    only by the exchange of the two electrons, so they are the same two-body operator.
   * The Hubbard-Stratonovich transformation enabled by that factorisation and
     the phaseless AFQMC algorithm are cited, not written out (Zhang & Krakauer
     2003; Motta & Zhang 2018).  The step below restates that textbook algorithm
@@ -115,14 +119,32 @@ class Walkers:
 # --------------------------------------------------------------------------------------------
 
 def hprime(ham: Hamiltonian) -> np.ndarray:
-    """h' = h - 1/2 sum_n L_n L_n^dagger (from Eq. (1) with Eq. (3) after normal ordering)."""
-    return ham.h - 0.5 * np.einsum("nik,njk->ij", ham.L, ham.L.conj()).real
+    """h' = h - 1/2 sum_n L_n L_n^dagger (from Eq. (1) with Eq. (3) after normal ordering);
+    real for real inputs, Hermitian for complex ones."""
+    hp = ham.h - 0.5 * np.einsum("nik,njk->ij", ham.L, ham.L.conj())
+    return hp.real if np.isrealobj(ham.L) and np.isrealobj(ham.h) else hp
 
 
 def half_one_body_propagator(ham: Hamiltonian, tau: float) -> np.ndarray:
-    """B = exp(-tau h'/2) from the eigendecomposition of the symmetric h'."""
+    """B = exp(-tau h'/2) from the eigendecomposition of the Hermitian h'."""
     e, v = np.linalg.eigh(hprime(ham))
-    return (v * np.exp(-0.5 * tau * e)) @ v.T
+    return (v * np.exp(-0.5 * tau * e)) @ v.conj().T
+
+
+def hermitian_split(L: np.ndarray) -> np.ndarray:
+    """2 Nchol Hermitian operators [A_0, B_0, A_1, B_1, ...] from complex L [Nchol, M, M]:
+    A_n = (L_n + L_n^+)/2, B_n = (L_n - L_n^+)/(2i).  They give the same two-body operator as
+    L (the four-index tensors differ only by the exchange of the two electrons).  Written as
+    1/2 sum (A^2 + B^2) the interaction needs h' = h - 1/4 sum (L L^+ + L^+ L), which is what
+    hprime returns for the split vectors; 1/2 sum L L^+ differs from it by the one-body
+    commutator term 1/4 sum [L, L^+]."""
+    Ld = np.conj(np.swapaxes(L, 1, 2))
+    A = 0.5 * (L + Ld)
+    B = (L - Ld) / 2j
+    out = np.empty((2 * L.shape[0],) + L.shape[1:], dtype=np.complex128)
+    out[0::2] = A
+    out[1::2] = B
+    return out
 
 
 # --------------------------------------------------------------------------------------------
