@@ -95,6 +95,24 @@ typedef struct afqmc_walkers* afqmc_wk_t;
  * Errors: BADARG (null), SHAPE, NONFINITE (NaN/Inf in h or L), OOM, CUDA. */
 int afqmc_create_hamiltonian(const double* h, const double* L, double E0, int M, int Nchol,
                              void* stream, afqmc_ham_t* out);
+
+/* ---- Hamiltonian with general complex Cholesky vectors (Sec. V, Eq. (3)) ----
+ * h     [M][M]        real symmetric one-body matrix h_ij.
+ * L     [Nchol][M][M] complex128 (interleaved re, im) Cholesky vectors, any
+ *                     complex matrices: v_ijkl = sum_n L^n_ik conj(L^n_lj).
+ * E0    constant energy.
+ * The library replaces each L_n by its Hermitian split A_n = (L_n + L_n^+)/2,
+ * B_n = (L_n - L_n^+)/(2i), which gives the same two-body operator, so walker
+ * sets on this Hamiltonian have 2 Nchol Cholesky vectors in the order
+ * A_0, B_0, A_1, B_1, ...: caller fields x of afqmc_step are [nsteps][W][2 Nchol]
+ * and Philox draws 2 Nchol fields per walker.  The one-body matrix of the
+ * propagator is then the complex Hermitian h' = h - 1/2 sum_m V_m V_m^+ over the
+ * split vectors V_m (= h - 1/4 sum_n (L_n L_n^+ + L_n^+ L_n)).
+ * Only the FP64 path runs it: a BF16X3 walker set and afqmc_energy_backward on
+ * such a walker set return UNSUPPORTED.  Device memory: 2 Nchol M^2 complex.
+ * Errors: BADARG (null), SHAPE, NONFINITE (NaN/Inf in h or L), OOM, CUDA. */
+int afqmc_create_hamiltonian_complex(const double* h, const double* L, double E0, int M, int Nchol,
+                                     void* stream, afqmc_ham_t* out);
 int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
 
 /* ---- Walker set ---------------------------------------------------------
@@ -152,7 +170,8 @@ int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_
  *           tensor.
  * dE, dlogS complex [W]; either may be NULL (treated as zero).  Theta is
  * recomputed, never stored.  Outputs may be NULL to skip them.
- * Computed in FP64 whatever the walker set's precision. */
+ * Computed in FP64 whatever the walker set's precision; UNSUPPORTED on a
+ * Hamiltonian made by afqmc_create_hamiltonian_complex. */
 int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, double* dPsi_up,
                           double* dPsi_dn, double* dL, void* stream);
 

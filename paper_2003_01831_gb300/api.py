@@ -30,7 +30,8 @@ PREC_FP64, PREC_BF16X3 = 0, 1
 WEIGHT_PHASELESS, WEIGHT_FREE, WEIGHT_LOCAL = 0, 1, 2
 
 EXPORTED = [
-    "afqmc_default_opts", "afqmc_create_hamiltonian", "afqmc_destroy_hamiltonian",
+    "afqmc_default_opts", "afqmc_create_hamiltonian", "afqmc_create_hamiltonian_complex",
+    "afqmc_destroy_hamiltonian",
     "afqmc_init_walkers", "afqmc_destroy_walkers", "afqmc_step", "afqmc_energy",
     "afqmc_energy_backward", "afqmc_get_walkers", "afqmc_set_walkers",
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
     sig = {
         "afqmc_default_opts": (None, [ctypes.POINTER(Opts)]),
         "afqmc_create_hamiltonian": (i, [vp, vp, d, i, i, vp, ctypes.POINTER(vp)]),
+        "afqmc_create_hamiltonian_complex": (i, [vp, vp, d, i, i, vp, ctypes.POINTER(vp)]),
         "afqmc_destroy_hamiltonian": (i, [vp]),
         "afqmc_init_walkers": (i, [vp, vp, vp, i, i, i, vp, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]),
         "afqmc_destroy_walkers": (i, [vp]),
@@ -165,6 +167,14 @@ def afqmc_create_hamiltonian(h, L, E0: float, M: int, Nchol: int, stream=None) -
     out = ctypes.c_void_p()
     _check(lib().afqmc_create_hamiltonian(_ptr(h), _ptr(L), float(E0), int(M), int(Nchol),
                                           _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def afqmc_create_hamiltonian_complex(h, L, E0: float, M: int, Nchol: int, stream=None) -> int:
+    """L: complex128 [Nchol, M, M]; the walker sets see its 2 Nchol Hermitian-split vectors."""
+    out = ctypes.c_void_p()
+    _check(lib().afqmc_create_hamiltonian_complex(_ptr(h), _ptr(L), float(E0), int(M), int(Nchol),
+                                                  _stream(stream), ctypes.byref(out)))
     return out.value
 
 

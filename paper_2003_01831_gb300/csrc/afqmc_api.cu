@@ -176,6 +176,62 @@ int afqmc_create_hamiltonian(const double* h, const double* L, double E0, int M,
     return AFQMC_OK;
 }
 
+int afqmc_create_hamiltonian_complex(const double* h, const double* L, double E0, int M, int Nchol, void* stream,
+                                     afqmc_ham_t* out) {
+    if (!out) return fail(AFQMC_ERR_BADARG, "create_hamiltonian_complex: out is NULL");
+    *out = nullptr;
+    if (!h || !L) return fail(AFQMC_ERR_BADARG, "create_hamiltonian_complex: h or L is NULL");
+    if (M < 1 || M > 1024 || Nchol < 1 || Nchol > (1 << 29))
+        return fail(AFQMC_ERR_SHAPE, "create_hamiltonian_complex: need 1 <= M <= 1024, Nchol >= 1");
+    if (!isfinite(E0)) return fail(AFQMC_ERR_NONFINITE, "create_hamiltonian_complex: E0 not finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    afqmc_ham* H = new afqmc_ham();
+    AFQMC_CUDA_TRY(cudaGetDevice(&H->device));
+    const int Nv = 2 * Nchol;   // Hermitian split: two vectors per input vector
+    H->M = M;
+    H->Nchol = Nv;
+    H->E0 = E0;
+    H->cplx_L = true;
+    const size_t mm = (size_t)M * M;
+    cplx* Lin = nullptr;
+    auto cleanup = [&](int rc) {
+        if (Lin) cudaFree(Lin);
+        if (H->h) cudaFree(H->h);
+        if (H->L) cudaFree(H->L);
+        if (H->hp) cudaFree(H->hp);
+        if (H->flags) cudaFree(H->flags);
+        delete H;
+        return rc;
+    };
+    if (cudaMalloc(&H->h, mm * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&Lin, mm * Nchol * sizeof(cplx)) != cudaSuccess ||
+        cudaMalloc(&H->L, mm * Nv * sizeof(cplx)) != cudaSuccess ||
+        cudaMalloc(&H->hp, mm * sizeof(cplx)) != cudaSuccess ||
+        cudaMalloc(&H->flags, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(AFQMC_ERR_OOM, "create_hamiltonian_complex: device allocation failed"));
+    }
+    int rc = copy_in(H->h, h, mm * sizeof(double), st);
+    if (rc == AFQMC_OK) rc = copy_in(Lin, L, mm * Nchol * sizeof(cplx), st);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    cudaMemsetAsync(H->flags, 0, sizeof(unsigned), st);
+    check_finite(H->h, (int64_t)mm, H->flags, st);
+    check_finite(reinterpret_cast<const double*>(Lin), 2 * (int64_t)mm * Nchol, H->flags, st);
+    unsigned f = 0;
+    rc = read_flags(H->flags, st, &f);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    if (f & FLAG_NONFINITE) return cleanup(fail(AFQMC_ERR_NONFINITE, "create_hamiltonian_complex: NaN/Inf in h or L"));
+    hermitian_split(Lin, M, Nchol, reinterpret_cast<cplx*>(H->L), st);
+    build_hprime_hermitian(H->h, reinterpret_cast<const cplx*>(H->L), M, Nv, reinterpret_cast<cplx*>(H->hp), st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cleanup(fail(AFQMC_ERR_CUDA, std::string("create_hamiltonian_complex: ") + cudaGetErrorString(e)));
+    cudaFree(Lin);
+    Lin = nullptr;
+    *out = H;
+    return AFQMC_OK;
+}
+
 int afqmc_destroy_hamiltonian(afqmc_ham_t H) {
     if (!H) return fail(AFQMC_ERR_BADARG, "destroy_hamiltonian: NULL handle");
     if (H->live_walker_sets > 0) return fail(AFQMC_ERR_BADARG, "destroy_hamiltonian: walker sets still use it");
@@ -285,7 +341,10 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
         if (fl[0] & FLAG_NONFINITE) return bail(fail(AFQMC_ERR_NONFINITE, "init_walkers: NaN/Inf in the trial"));
         wk->trial_real = fl[1] == 0;
+        wk->Lt_real = wk->trial_real && !ham->cplx_L;
     }
+    if (o.precision == AFQMC_PREC_BF16X3 && ham->cplx_L)
+        return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs real Cholesky vectors"));
     if (o.precision == AFQMC_PREC_BF16X3) {
         if (!wk->trial_real || Nup != Ndn || M % 64 != 0 || nch % 8 != 0)
             return bail(fail(AFQMC_ERR_UNSUPPORTED,
@@ -300,11 +359,11 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         GemmArgs g;   // tmp[n] = Psi^+ L_n   [N][M]
         g.m = N; g.n = M; g.k = M; g.nb1 = nch;
         g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = N;
-        g.B.ptr = ham->L; g.B.real = true; g.B.ld = M; g.B.s1 = (int64_t)M * M;
+        g.B.ptr = ham->L; g.B.real = !ham->cplx_L; g.B.ld = M; g.B.s1 = (int64_t)M * M;
         g.C = tmp; g.ldc = M; g.sc1 = (int64_t)N * M;
         zgemm(g, st);
         const int64_t tot = (int64_t)nch * N * M;
-        if (wk->trial_real) {
+        if (wk->Lt_real) {
             double* Lr = static_cast<double*>(f.Lt[s]);
             count_launch();
             cplx_real_part_kernel<<<nblk(tot), 256, 0, st>>>(tmp, Lr, tot);
@@ -323,7 +382,9 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         zgemm(gh, st);
         cudaFreeAsync(tmp, st);
     }
-    rc = expm_real(ham->hp, -0.5 * tau, M, f.Bh, st);
+    rc = ham->cplx_L ? expm_complex(reinterpret_cast<const cplx*>(ham->hp), -0.5 * tau, M,
+                                    reinterpret_cast<cplx*>(f.Bh), st)
+                     : expm_real(ham->hp, -0.5 * tau, M, f.Bh, st);
     if (rc) return bail(rc);
     // trial energy E_T from walker 0 placed at the trial
     for (int s = 0; s < 2; ++s)
@@ -605,6 +666,7 @@ int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x
 int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, double* dPsi_up, double* dPsi_dn,
                           double* dL, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "energy_backward: NULL handle");
+    if (wk->ham->cplx_L) return fail(AFQMC_ERR_UNSUPPORTED, "energy_backward: needs real Cholesky vectors");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return fp64_backward(wk, reinterpret_cast<const cplx*>(dE), reinterpret_cast<const cplx*>(dlogS),
                          reinterpret_cast<cplx*>(dPsi_up), reinterpret_cast<cplx*>(dPsi_dn), dL, st);

@@ -128,8 +128,8 @@ int fp64_backward(afqmc_walkers* wk, const cplx* dE, const cplx* dlogS, cplx* dP
             {   // T[c][w] = Lt_{n0+c} Theta_w
                 GemmArgs g;
                 g.m = N; g.n = N; g.k = M; g.nb1 = nc; g.nb2 = W;
-                g.A.real = wk->trial_real;
-                g.A.ptr = wk->trial_real
+                g.A.real = wk->Lt_real;
+                g.A.ptr = wk->Lt_real
                               ? (const void*)(static_cast<const double*>(f.Lt[s]) + (int64_t)n0 * N * M)
                               : (const void*)(static_cast<const cplx*>(f.Lt[s]) + (int64_t)n0 * N * M);
                 g.A.ld = M; g.A.s1 = (int64_t)N * M;

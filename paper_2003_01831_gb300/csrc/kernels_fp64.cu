@@ -1109,6 +1109,31 @@ __global__ void hprime_reduce_kernel(const double* h, const cplx* parts, int npa
     hp[id] = h[id] - 0.5 * acc;
 }
 
+// Hermitian split of general complex Cholesky vectors (Sec. V, Eq. (3) with complex L_n):
+// V[2n] = (L_n + L_n^+)/2, V[2n+1] = (L_n - L_n^+)/(2i).  Both are Hermitian and
+// sum_m V_m (x) V_m is the two-body operator of sum_n L_n (x) L_n^+ up to the exchange of the
+// two electrons, which the antisymmetric fermion pair cannot see.
+__global__ void herm_split_kernel(const cplx* L, int M, int Nchol, cplx* V) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t mm = (int64_t)M * M;
+    if (id >= (int64_t)Nchol * mm) return;
+    const int64_t n = id / mm, e = id % mm;
+    const int i = (int)(e / M), k = (int)(e % M);
+    const cplx a = L[id];
+    const cplx b = conjg(L[n * mm + (int64_t)k * M + i]);   // (L_n^+)_ik
+    const cplx d = a - b;
+    V[2 * n * mm + e] = 0.5 * (a + b);
+    V[(2 * n + 1) * mm + e] = cplx{0.5 * d.im, -0.5 * d.re};   // d / (2i)
+}
+
+__global__ void hprime_reduce_c_kernel(const double* h, const cplx* parts, int nparts, int M, cplx* hp) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M * M) return;
+    cplx acc{0.0, 0.0};
+    for (int p = 0; p < nparts; ++p) acc = acc + parts[(int64_t)p * M * M + id];
+    hp[id] = cplx{h[id] - 0.5 * acc.re, -0.5 * acc.im};
+}
+
 __global__ void c2r_scale_kernel(const cplx* s, double* d, int64_t n) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id < n) d[id] = s[id].re;
@@ -1328,16 +1353,18 @@ void check_symmetric(const double* L, int M, int Nchol, unsigned* flags, cudaStr
     sym_kernel<<<blocks_for(n), kThreads, 0, st>>>(L, M, Nchol, flags);
 }
 
-void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp, cudaStream_t st) {
-    // L_n symmetric: sum_n L_n L_n^T = X^T X with X[(n, k)][i] = L[n][k][i], a contiguous
-    // [Nchol*M][M] matrix.  Split the K = Nchol*M reduction into `parts` batched GEMMs
-    // (fixed split, fixed-order reduction) to fill the GPU.
-    const int parts = std::min(Nchol, 16);
+namespace {
+
+// sum_n L_n L_n^+ for symmetric (real) or Hermitian (complex) L_n, in `parts` partial sums:
+// for such L_n it equals X^+ X with X[(n, k)][i] = L[n][k][i], a contiguous [Nchol*M][M]
+// matrix.  The K = Nchol*M reduction is split into `parts` GEMMs (fixed split, reduced in a
+// fixed order by the caller's kernel) to fill the GPU.  Returns the workspace, or NULL.
+cplx* gram_of_cholesky(const void* L, bool real, int M, int Nchol, int parts, cudaStream_t st) {
     const int per = (Nchol + parts - 1) / parts;  // Cholesky vectors per part
     cplx* buf = nullptr;
     if (cudaMallocAsync(&buf, sizeof(cplx) * (size_t)parts * M * M, st) != cudaSuccess) {
         fail(AFQMC_ERR_OOM, "hprime workspace");
-        return;
+        return nullptr;
     }
     fill_cplx(buf, (int64_t)parts * M * M, cplx{0.0, 0.0}, st);
     for (int p = 0; p < parts; ++p) {
@@ -1346,41 +1373,75 @@ void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp
         GemmArgs g;
         g.m = g.n = M;
         g.k = (n1 - n0) * M;
-        const double* X = L + (int64_t)n0 * M * M;
-        g.A.ptr = X; g.A.real = true; g.A.op = OP_T; g.A.ld = M;
-        g.B.ptr = X; g.B.real = true; g.B.op = OP_N; g.B.ld = M;
+        const void* X = real ? (const void*)(static_cast<const double*>(L) + (int64_t)n0 * M * M)
+                             : (const void*)(static_cast<const cplx*>(L) + (int64_t)n0 * M * M);
+        g.A.ptr = X; g.A.real = real; g.A.op = real ? OP_T : OP_C; g.A.ld = M;
+        g.B.ptr = X; g.B.real = real; g.B.op = OP_N; g.B.ld = M;
         g.C = buf + (int64_t)p * M * M; g.ldc = M;
         zgemm(g, st);
     }
+    return buf;
+}
+
+}  // namespace
+
+void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp, cudaStream_t st) {
+    const int parts = std::min(Nchol, 16);
+    cplx* buf = gram_of_cholesky(L, true, M, Nchol, parts, st);
+    if (!buf) return;
     count_launch();
     hprime_reduce_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(h, buf, parts, M, hp);
     cudaFreeAsync(buf, st);
 }
 
-int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
-    // exp(s X) = (T_q(s X / 2^j))^(2^j): Taylor order 18 by Horner, j squarings so that
-    // ||s X / 2^j||_1 <= 1/4 (truncation error below 1e-20 relative).
-    std::vector<double> hX((size_t)M * M);
-    cudaError_t e = cudaMemcpyAsync(hX.data(), X, sizeof(double) * M * M, cudaMemcpyDefault, st);
+void build_hprime_hermitian(const double* h, const cplx* V, int M, int Nv, cplx* hp, cudaStream_t st) {
+    const int parts = std::min(Nv, 16);
+    cplx* buf = gram_of_cholesky(V, false, M, Nv, parts, st);
+    if (!buf) return;
+    count_launch();
+    hprime_reduce_c_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(h, buf, parts, M, hp);
+    cudaFreeAsync(buf, st);
+}
+
+void hermitian_split(const cplx* L, int M, int Nchol, cplx* V, cudaStream_t st) {
+    const int64_t n = (int64_t)Nchol * M * M;
+    count_launch();
+    herm_split_kernel<<<blocks_for(n), kThreads, 0, st>>>(L, M, Nchol, V);
+}
+
+namespace {
+
+// ||X||_1 (largest column sum of |x|) of a device M x M matrix, read on the host.
+int norm1_on_host(const void* X, bool real, int M, cudaStream_t st, double* nrm) {
+    const size_t n = (size_t)M * M;
+    std::vector<cplx> hX(real ? 0 : n);
+    std::vector<double> hR(real ? n : 0);
+    cudaError_t e = real ? cudaMemcpyAsync(hR.data(), X, sizeof(double) * n, cudaMemcpyDefault, st)
+                         : cudaMemcpyAsync(hX.data(), X, sizeof(cplx) * n, cudaMemcpyDefault, st);
     if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, "expm copy");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, "expm sync");
-    double nrm = 0.0;
+    *nrm = 0.0;
     for (int j = 0; j < M; ++j) {
         double c = 0.0;
-        for (int i = 0; i < M; ++i) c += fabs(hX[(size_t)i * M + j]);
-        nrm = std::max(nrm, c);
+        for (int i = 0; i < M; ++i)
+            c += real ? fabs(hR[(size_t)i * M + j]) : hypot(hX[(size_t)i * M + j].re, hX[(size_t)i * M + j].im);
+        *nrm = std::max(*nrm, c);
     }
+    return AFQMC_OK;
+}
+
+// E = exp(s Y) for a complex device matrix Y with ||Y||_1 = nrm:
+// (T_q(s Y / 2^j))^(2^j), Taylor order 18 by Horner, j squarings so that ||s Y / 2^j||_1 <= 1/4
+// (truncation error below 1e-20 relative).  E must not alias Y.
+int expm_taylor_squaring(const cplx* Y, double nrm, double s, int M, cplx* E, cudaStream_t st) {
     nrm *= fabs(s);
     int sq = 0;
     while (nrm > 0.25 && sq < 60) { nrm *= 0.5; ++sq; }
     const double sc = s / ldexp(1.0, sq);
-    cplx *Y = nullptr, *E = nullptr, *Tm = nullptr;
-    const size_t bytes = sizeof(cplx) * M * M;
-    if (cudaMallocAsync(&Y, bytes, st) != cudaSuccess || cudaMallocAsync(&E, bytes, st) != cudaSuccess ||
-        cudaMallocAsync(&Tm, bytes, st) != cudaSuccess)
-        return fail(AFQMC_ERR_OOM, "expm workspace");
-    real_to_cplx(X, Y, (int64_t)M * M, st);
+    cplx* Tm = nullptr;
+    cplx* E0 = E;
+    if (cudaMallocAsync(&Tm, sizeof(cplx) * M * M, st) != cudaSuccess) return fail(AFQMC_ERR_OOM, "expm workspace");
     // E = I
     fill_cplx(E, (int64_t)M * M, cplx{0.0, 0.0}, st);
     count_launch();
@@ -1408,12 +1469,38 @@ int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
         zgemm(g, st);
         std::swap(E, Tm);
     }
-    count_launch();
-    c2r_scale_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(E, out, (int64_t)M * M);
-    cudaFreeAsync(Y, st);
-    cudaFreeAsync(E, st);
+    if (E != E0) {   // the result sits in the workspace: move it to the caller's buffer
+        cudaMemcpyAsync(E0, E, sizeof(cplx) * M * M, cudaMemcpyDeviceToDevice, st);
+        Tm = E;
+    }
     cudaFreeAsync(Tm, st);
     return AFQMC_OK;
+}
+
+}  // namespace
+
+int expm_real(const double* X, double s, int M, double* out, cudaStream_t st) {
+    double nrm = 0.0;
+    AFQMC_TRY(norm1_on_host(X, true, M, st, &nrm));
+    cplx *Y = nullptr, *E = nullptr;
+    const size_t bytes = sizeof(cplx) * M * M;
+    if (cudaMallocAsync(&Y, bytes, st) != cudaSuccess || cudaMallocAsync(&E, bytes, st) != cudaSuccess)
+        return fail(AFQMC_ERR_OOM, "expm workspace");
+    real_to_cplx(X, Y, (int64_t)M * M, st);
+    const int rc = expm_taylor_squaring(Y, nrm, s, M, E, st);
+    if (rc == AFQMC_OK) {
+        count_launch();
+        c2r_scale_kernel<<<blocks_for((int64_t)M * M), kThreads, 0, st>>>(E, out, (int64_t)M * M);
+    }
+    cudaFreeAsync(Y, st);
+    cudaFreeAsync(E, st);
+    return rc;
+}
+
+int expm_complex(const cplx* X, double s, int M, cplx* out, cudaStream_t st) {
+    double nrm = 0.0;
+    AFQMC_TRY(norm1_on_host(X, false, M, st, &nrm));
+    return expm_taylor_squaring(X, nrm, s, M, out, st);
 }
 
 }  // namespace afqmc

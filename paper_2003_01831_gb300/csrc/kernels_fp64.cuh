@@ -115,8 +115,14 @@ void real_to_cplx(const double* src, cplx* dst, int64_t n, cudaStream_t st);
 void check_finite(const double* p, int64_t n, unsigned* flags, cudaStream_t st);
 // h' = h - 1/2 sum_n L_n L_n^T (real, FP64)
 void build_hprime(const double* h, const double* L, int M, int Nchol, double* hp, cudaStream_t st);
+// h' = h - 1/2 sum_m V_m V_m^+ for Hermitian complex V [Nv][M][M] and real h (complex Hermitian h')
+void build_hprime_hermitian(const double* h, const cplx* V, int M, int Nv, cplx* hp, cudaStream_t st);
+// V[2n] = (L_n + L_n^+)/2, V[2n+1] = (L_n - L_n^+)/(2i) for complex L [Nchol][M][M]; V [2 Nchol][M][M]
+void hermitian_split(const cplx* L, int M, int Nchol, cplx* V, cudaStream_t st);
 // exp(s * X) for a real symmetric M x M matrix by scaling-and-squaring of a Taylor series (FP64).
 int expm_real(const double* X, double s, int M, double* out, cudaStream_t st);
+// the same for a complex M x M matrix (out must not alias X)
+int expm_complex(const cplx* X, double s, int M, cplx* out, cudaStream_t st);
 // max |L_n - L_n^T| > tol * max|L| sets FLAG_NONFINITE-independent flag 8
 void check_symmetric(const double* L, int M, int Nchol, unsigned* flags, cudaStream_t st);
 

@@ -11,8 +11,11 @@ struct afqmc_ham {
     int M = 0, Nchol = 0;
     double E0 = 0.0;
     double* h = nullptr;    // [M][M]
-    double* L = nullptr;    // [Nchol][M][M]
-    double* hp = nullptr;   // h' = h - 1/2 sum L L^T
+    double* L = nullptr;    // [Nchol][M][M]; interleaved complex when cplx_L
+    double* hp = nullptr;   // h' = h - 1/2 sum L L^+ [M][M]; interleaved complex when cplx_L
+    // Built from general complex Cholesky vectors: L holds their Hermitian split (2 per input
+    // vector, Nchol counts the split vectors).  Only the FP64 step supports it.
+    bool cplx_L = false;
     unsigned* flags = nullptr;
     int live_walker_sets = 0;
 };
@@ -28,7 +31,7 @@ struct Fp64Buffers {
     void* Lt[2] = {nullptr, nullptr};      // Psi_s^+ L_n: [Nchol][N_s][M] (double if trial real)
     void* LtT[2] = {nullptr, nullptr};     // transposed: [Nchol][M][N_s] (force-bias-only path)
     cplx* ht[2] = {nullptr, nullptr};      // Psi_s^+ h: [N_s][M]
-    double* Bh = nullptr;                  // exp(-tau h'/2): [M][M]
+    double* Bh = nullptr;                  // exp(-tau h'/2): [M][M], interleaved complex if cplx_L
     cplx* Phi[2] = {nullptr, nullptr};     // [W][M][N_s]
     cplx* Pnew[2] = {nullptr, nullptr};    // propagated walkers / Taylor accumulator
     cplx* Pa[2] = {nullptr, nullptr};      // Taylor term ping
@@ -52,6 +55,7 @@ struct afqmc_walkers {
     double tau = 0.0;
     afqmc_opts opts{};
     bool trial_real = false;
+    bool Lt_real = false;             // Psi^+ L_n real: a real trial and real L
     double E_T = 0.0;
     int64_t step = 0;
 

@@ -62,7 +62,7 @@ int fp64_alloc(afqmc_walkers* wk) {
         AFQMC_TRY(dalloc(&f.t[s], (size_t)W * nch));
         AFQMC_TRY(dalloc(&f.X[s], (size_t)W * nch));
     }
-    AFQMC_TRY(dalloc(&f.Bh, (size_t)M * M));
+    AFQMC_TRY(dalloc(&f.Bh, (size_t)M * M * (wk->ham->cplx_L ? 2 : 1)));
     const int Nmax = std::max(wk->N[0], wk->N[1]);
     const size_t per_n = (size_t)W * Nmax * Nmax * sizeof(cplx);
     const size_t budget = (size_t)512 << 20;
@@ -110,8 +110,8 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
                 const int nc = std::min(f.nc, nch - n0);
                 GemmArgs g;   // T[c][w] = Lt_{n0+c} Theta_w
                 g.m = N; g.n = N; g.k = M; g.nb1 = nc; g.nb2 = W;
-                g.A.real = wk->trial_real;
-                g.A.ptr = wk->trial_real
+                g.A.real = wk->Lt_real;
+                g.A.ptr = wk->Lt_real
                               ? (const void*)(static_cast<const double*>(f.Lt[s]) + (int64_t)n0 * N * M)
                               : (const void*)(static_cast<const cplx*>(f.Lt[s]) + (int64_t)n0 * N * M);
                 g.A.ld = M; g.A.s1 = (int64_t)N * M; g.A.s2 = 0;
@@ -125,7 +125,7 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
             GemmArgs g;
             g.m = W; g.n = nch; g.k = M * N;
             g.A.ptr = f.Theta[s]; g.A.op = OP_N; g.A.ld = (int64_t)M * N;
-            g.B.real = wk->trial_real; g.B.ptr = f.LtT[s]; g.B.op = OP_T; g.B.ld = (int64_t)M * N;
+            g.B.real = wk->Lt_real; g.B.ptr = f.LtT[s]; g.B.op = OP_T; g.B.ld = (int64_t)M * N;
             g.C = f.t[s]; g.ldc = nch;
             zgemm(g, st);
         }
@@ -153,7 +153,7 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
         GemmArgs g;
         g.m = W; g.n = M * M; g.k = nch;
         g.A.ptr = wk->coef; g.A.ld = nch;
-        g.B.ptr = wk->ham->L; g.B.real = true; g.B.ld = (int64_t)M * M;
+        g.B.ptr = wk->ham->L; g.B.real = !wk->ham->cplx_L; g.B.ld = (int64_t)M * M;
         g.C = f.A; g.ldc = (int64_t)M * M;
         zgemm(g, st);
     }
@@ -165,7 +165,7 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
         cplx* P1 = f.Pb[s];
         GemmArgs g;   // P0 = B Phi
         g.m = M; g.n = N; g.k = M; g.nb1 = W;
-        g.A.ptr = f.Bh; g.A.real = true; g.A.ld = M;
+        g.A.ptr = f.Bh; g.A.real = !wk->ham->cplx_L; g.A.ld = M;
         g.B.ptr = f.Phi[s]; g.B.ld = N; g.B.s1 = mn;
         g.C = P0; g.ldc = N; g.sc1 = mn;
         zgemm(g, st);
@@ -183,7 +183,7 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
         }
         GemmArgs b2;  // Phi' = B Pnew  -> Pa
         b2.m = M; b2.n = N; b2.k = M; b2.nb1 = W;
-        b2.A.ptr = f.Bh; b2.A.real = true; b2.A.ld = M;
+        b2.A.ptr = f.Bh; b2.A.real = !wk->ham->cplx_L; b2.A.ld = M;
         b2.B.ptr = f.Pnew[s]; b2.B.ld = N; b2.B.s1 = mn;
         b2.C = f.Pa[s]; b2.ldc = N; b2.sc1 = mn;
         zgemm(b2, st);

@@ -20,16 +20,22 @@ class AFQMC:
                  k_taylor=6, k_qr=5, fb_cap=1.0, weight_mode=api.WEIGHT_PHASELESS, walker_offset=0, energy_terms=0,
                  stream=None):
         h = np.ascontiguousarray(h, dtype=np.float64)
-        L = np.ascontiguousarray(L, dtype=np.float64)
+        # complex L: general complex Cholesky vectors, run as their 2 Nchol Hermitian-split
+        # vectors (A_0, B_0, A_1, B_1, ...), which is what fields and Nchol refer to
+        self.complex_L = np.iscomplexobj(L)
+        L = np.ascontiguousarray(L, dtype=np.complex128 if self.complex_L else np.float64)
         self.M = h.shape[0]
-        self.Nchol = L.shape[0]
+        self.Nchol = L.shape[0] * (2 if self.complex_L else 1)
         self.Psi = [np.ascontiguousarray(Psi_up, dtype=np.complex128),
                     np.ascontiguousarray(Psi_dn, dtype=np.complex128)]
         self.N = [self.Psi[0].shape[1], self.Psi[1].shape[1]]
         self.W = int(W)
         self.weight_mode = weight_mode
         self.stream = stream
-        self.ham = api.afqmc_create_hamiltonian(h, L, E0, self.M, self.Nchol, stream)
+        if self.complex_L:
+            self.ham = api.afqmc_create_hamiltonian_complex(h, L, E0, self.M, L.shape[0], stream)
+        else:
+            self.ham = api.afqmc_create_hamiltonian(h, L, E0, self.M, self.Nchol, stream)
         opts = api.afqmc_default_opts()
         opts.precision = precision
         opts.k_taylor = k_taylor
@@ -98,7 +104,7 @@ class AFQMC:
         dlogS = None if dlogS is None else np.ascontiguousarray(dlogS, dtype=np.complex128)
         dPu = np.zeros((self.M, self.N[0]), dtype=np.complex128)
         dPd = np.zeros((self.M, self.N[1]), dtype=np.complex128)
-        dL = np.zeros((self.Nchol, self.M, self.M), dtype=np.float64) if want_L else None
+        dL = np.zeros((self.Nchol, self.M, self.M), dtype=np.float64) if want_L and not self.complex_L else None
         api.afqmc_energy_backward(self.wk, dE, dlogS, dPu, dPd, dL, self.stream)
         return dPu, dPd, dL
 

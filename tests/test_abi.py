@@ -57,6 +57,12 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
     assert lib.afqmc_create_hamiltonian(h.ctypes.data, L.ctypes.data, float("nan"), 4, 2, None,
                                         ctypes.byref(out)) == -4
     assert b"E0" in lib.afqmc_last_error()
+    Lc = np.zeros((2, 4, 4), dtype=np.complex128)
+    mk = lib.afqmc_create_hamiltonian_complex
+    assert mk(h.ctypes.data, Lc.ctypes.data, 0.0, 4, 2, None, None) == -1
+    assert mk(h.ctypes.data, None, 0.0, 4, 2, None, ctypes.byref(out)) == -1
+    assert mk(h.ctypes.data, Lc.ctypes.data, 0.0, 4, 0, None, ctypes.byref(out)) == -2
+    assert mk(h.ctypes.data, Lc.ctypes.data, float("inf"), 4, 2, None, ctypes.byref(out)) == -4
     assert lib.afqmc_step(None, 1, None, 0, 0, None, None) == -1
     assert lib.afqmc_energy(None, None, None, None, None, None) == -1
     assert lib.afqmc_destroy_walkers(None) == -1
