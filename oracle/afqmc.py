@@ -279,17 +279,20 @@ def mixed_energy(w: np.ndarray, E_L: np.ndarray) -> complex:
 
 
 def step(ham: Hamiltonian, Psi: Sequence[np.ndarray], B: np.ndarray, wk: Walkers,
-         x: np.ndarray, p: Params):
+         x: np.ndarray, p: Params, record: Optional[list] = None):
     """One phaseless step for every walker with fields x [W, Nchol].
 
     Returns (E_L [W] at the pre-step walkers, E_mix with the pre-step weights).
-    Updates wk in place."""
+    Updates wk in place.  If `record` is a list, the shifted fields c = x - xbar that drove
+    each walker's propagator are appended to it ([W, Nchol]; zero rows for frozen walkers)."""
     E_L, t_sum, _ = local_energy(ham, Psi, wk.Phi)
     E_mix = mixed_energy(wk.w, E_L)
     free = p.mode == "free"
     xbar = force_bias(t_sum, p.tau, 0.0 if free else p.fb_cap)
     alive = wk.w != 0
     c = x - xbar
+    if record is not None:
+        record.append(np.where(alive[:, None], c, 0.0))
     A = hs_potential(c, ham.L)
     newPhi = [propagate(wk.Phi[s], A, B, p.tau, p.k_taylor) for s in range(2)]
     newlogS = sum(log_det(overlap_matrix(Psi[s], newPhi[s])) for s in range(2))
