@@ -187,6 +187,34 @@ int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, 
  * standard comb, applied between steps. */
 int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream);
 
+/* ---- Back-propagated one-body density matrix (Sec. V: the back-propagation
+ * estimator for observables that do not commute with H) -----------------------
+ * afqmc_bp_begin opens a window of nbp >= 0 steps at the current walkers: it keeps a
+ * copy of them, Phi_w(0), and records for each of the next nbp steps the shifted
+ * fields c_wn = x_wn - xbar_wn that drove every walker.  A window already open is
+ * discarded.
+ * afqmc_bp_rdm1, once exactly nbp steps have run, carries the trial back through
+ * the adjoints of those steps' propagators,
+ *     Psi_bp,w = B_w(1)^+ ... B_w(nbp)^+ Psi_T,
+ *     B_w(k) = exp(-tau h'/2) T_K(i sqrt(tau) sum_n c_wn(k) L_n) exp(-tau h'/2),
+ * and writes the one-body density matrix of each spin,
+ *     G_s[i][j] = sum_w w_w <Psi_bp,w| c+_is c_js |Phi_w(0)> / <Psi_bp,w|Phi_w(0)> / sum_w w_w
+ *               = sum_w w_w [Phi_w(0) (Psi_bp,w^+ Phi_w(0))^-1 Psi_bp,w^+]_ji / sum_w w_w,
+ * with w the current (end-of-window) weights; walkers of weight 0 do not contribute.
+ * nbp = 0 gives the mixed estimate.  The window stays open, so the call may be
+ * repeated, until the next afqmc_bp_begin.
+ *   rdm_up, rdm_dn  complex [M][M] (either may be NULL).
+ * afqmc_population_control inside a window gives every new walker its source
+ * walker's Phi_w(0) and field history; afqmc_set_walkers closes the window.
+ * Computed in FP64 whatever the walker set's precision; device memory
+ * W (M (Nup + Ndn) + nbp Nchol) complex for the window and ~6 W M max(Nup, Ndn)
+ * complex during afqmc_bp_rdm1.
+ * Errors: BADARG (null handle, nbp < 0; for bp_rdm1: no window, fewer than nbp
+ * steps recorded, or a step run after the window was complete), NONFINITE (a live
+ * walker whose back-propagated overlap vanishes), OOM, CUDA. */
+int afqmc_bp_begin(afqmc_wk_t wk, int nbp, void* stream);
+int afqmc_bp_rdm1(afqmc_wk_t wk, double* rdm_up, double* rdm_dn, void* stream);
+
 /* ---- Walker state (checkpoint / resume and inspection) -------------------
  * Phi  complex [W][M*Nup + M*Ndn] (layout of Phi0), w [W] (complex [W] for
  * free projection), step = global step counter (drives the Philox counter).

@@ -37,6 +37,7 @@ EXPORTED = [
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
     "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
     "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune", "afqmc_population_control",
+    "afqmc_bp_begin", "afqmc_bp_rdm1",
 ]
 PAD_AUTO, PAD_ALWAYS = 0, 1
 SEED_STRIDE = 0x9E3779B97F4A7C15   # system s of a batch draws with key seed + s * SEED_STRIDE
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
         "afqmc_batch_info": (i, [vp, i, vp, ctypes.POINTER(i)]),
         "afqmc_batch_autotune": (i, [vp, i, ctypes.POINTER(d), vp]),
         "afqmc_population_control": (i, [vp, d, vp, vp]),
+        "afqmc_bp_begin": (i, [vp, i, vp]),
+        "afqmc_bp_rdm1": (i, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -224,6 +227,16 @@ def afqmc_population_control(wk: int, xi: float, idx=None, stream=None):
     """Comb population control with the uniform number xi in [0, 1); idx (int32 [W]) receives
     the source walker of every new walker."""
     _check(lib().afqmc_population_control(wk, float(xi), _ptr(idx), _stream(stream)))
+
+
+def afqmc_bp_begin(wk: int, nbp: int, stream=None):
+    """Open a back-propagation window of nbp steps at the current walkers."""
+    _check(lib().afqmc_bp_begin(wk, int(nbp), _stream(stream)))
+
+
+def afqmc_bp_rdm1(wk: int, rdm_up=None, rdm_dn=None, stream=None):
+    """Back-propagated one-body density matrices (complex128 [M, M] per spin) of the window."""
+    _check(lib().afqmc_bp_rdm1(wk, _ptr(rdm_up), _ptr(rdm_dn), _stream(stream)))
 
 
 def afqmc_philox_fields(seed: int, step: int, W: int, Nchol: int, x, stream=None):

@@ -244,6 +244,7 @@ int afqmc_destroy_hamiltonian(afqmc_ham_t H) {
 }
 
 static void free_walkers(afqmc_walkers* wk) {
+    bp_close(wk);
     fp64_free(wk);
     tc_free(wk);
     void* ps[] = {wk->weight, wk->logS_old, wk->logS_new, wk->E_L, wk->xbar, wk->coef,
@@ -505,6 +506,7 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
             xs = wk->x;
         }
         AFQMC_TRY(tc ? tc_propagate_and_weight(wk, xs, st) : fp64_propagate_and_weight(wk, xs, st));
+        bp_record(wk, st);
         wk->step++;
         if (wk->opts.k_qr > 0 && wk->step % wk->opts.k_qr == 0) AFQMC_TRY(tc ? tc_qr(wk, st) : fp64_qr(wk, st));
     }
@@ -534,7 +536,8 @@ int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream) {
         }
     } sc;
     if (cudaMalloc(&sc.p[0], sizeof(int) * W) != cudaSuccess || cudaMalloc(&sc.p[1], sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&sc.p[2], sizeof(cplx) * (size_t)W * M * std::max(wk->N[0], wk->N[1])) != cudaSuccess ||
+        cudaMalloc(&sc.p[2], sizeof(cplx) * (size_t)W * std::max<size_t>((size_t)M * std::max(wk->N[0], wk->N[1]),
+                                                                          (size_t)wk->Nchol)) != cudaSuccess ||
         cudaMalloc(&sc.p[3], sizeof(cplx) * W) != cudaSuccess) {
         cudaGetLastError();
         return fail(AFQMC_ERR_OOM, "population_control: scratch");
@@ -557,6 +560,7 @@ int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream) {
     gather_rows(wk->logS_old, 1, d_idx, W, ltmp, st);
     AFQMC_CUDA_TRY(cudaMemcpyAsync(wk->logS_old, ltmp, sizeof(cplx) * W, cudaMemcpyDeviceToDevice, st));
     equal_weights(wk->weight, W, d_total, st);
+    AFQMC_TRY(bp_follow_comb(wk, d_idx, tmp, st));
     if (tc) AFQMC_TRY(tc_sync_walkers_from_fp64(wk, st));
     if (idx) AFQMC_CUDA_TRY(cudaMemcpyAsync(idx, d_idx, sizeof(int) * W, cudaMemcpyDefault, st));
     AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -620,6 +624,7 @@ int afqmc_get_walkers(afqmc_wk_t wk, double* Phi, double* w, int64_t* step, void
 int afqmc_set_walkers(afqmc_wk_t wk, const double* Phi, const double* w, int64_t step, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "set_walkers: NULL handle");
     if (step < 0) return fail(AFQMC_ERR_BADARG, "set_walkers: negative step");
+    bp_close(wk);   // the window's walkers and history no longer describe these walkers
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int M = wk->M, W = wk->W;
     const size_t per = (size_t)M * (wk->N[0] + wk->N[1]) * sizeof(cplx);

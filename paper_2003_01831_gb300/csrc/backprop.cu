@@ -1,0 +1,312 @@
+// Back-propagated one-body density matrix: the back-propagation estimator Sec. V lists for
+// observables that do not commute with H (Zhang, Carlson & Gubernatis 1997; Purwanto &
+// Zhang 2004; Motta & Zhang 2017).
+//
+// A window opened at the walkers Phi(0) records the shifted fields c = x - xbar that drove
+// each of the next n steps.  The estimate carries the trial back through the adjoints of
+// those steps' propagators,
+//     Psi_bp,w = B_w(1)^+ ... B_w(n)^+ Psi_T,
+//     B_w(k)^+ = B T_K(-i sqrt(tau) A_w(k)^+) B,   A_w(k)^+ = sum_n conj(c_wn(k)) L_n
+// (B = exp(-tau h'/2) and every L_n are Hermitian), and averages
+//     G[i][j] = <c+_i c_j> = [Phi_w(0) (Psi_bp,w^+ Phi_w(0))^-1 Psi_bp,w^+]_ji
+// over the walkers with their end-of-window weights (weight-0 walkers contribute nothing).
+// The walker sum is one GEMM over K = W N: G^T = sum_w (w_w / sum w) Theta_w Psi_bp,w^+ with
+// both factors laid out row-major over (walker, orbital).  The back-propagated trial is
+// re-orthonormalised every k_qr steps, which leaves the estimate unchanged.
+//
+// FP64 on the DFMA pipe (zgemm and the batched inverse) whatever the walker set's precision.
+#include <algorithm>
+
+#include "state.cuh"
+
+namespace afqmc {
+
+namespace {
+
+constexpr int kT = 256;
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
+
+__global__ void conj_kernel(const cplx* a, cplx* b, int64_t n) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) b[id] = conjg(a[id]);
+}
+
+// *tot = sum_w w[w], one block of kT threads, fixed order
+__global__ void weight_total_kernel(const cplx* w, int W, cplx* tot) {
+    __shared__ double re[kT], im[kT];
+    double r = 0.0, i = 0.0;
+    for (int k = threadIdx.x; k < W; k += kT) {
+        r += w[k].re;
+        i += w[k].im;
+    }
+    re[threadIdx.x] = r;
+    im[threadIdx.x] = i;
+    __syncthreads();
+    for (int h = kT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            re[threadIdx.x] += re[threadIdx.x + h];
+            im[threadIdx.x] += im[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *tot = cplx{re[0], im[0]};
+}
+
+// dst[i][w][a] = f_w src[w][i][a] for W walkers of M x N, with f_w = w_w / tot (exactly 0
+// where w_w == 0) when weights are given, else 1.
+__global__ void to_orbital_major_kernel(const cplx* src, int W, int M, int N, const cplx* weight,
+                                        const cplx* tot, cplx* dst) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t mn = (int64_t)M * N;
+    if (id >= (int64_t)W * mn) return;
+    const int w = (int)(id / mn);
+    const int64_t r = id % mn;
+    const int i = (int)(r / N), a = (int)(r % N);
+    cplx v = src[id];
+    if (weight) {
+        const cplx ww = weight[w];
+        v = (ww.re == 0.0 && ww.im == 0.0) ? cplx{0.0, 0.0} : cdiv(ww, *tot) * v;
+    }
+    dst[((int64_t)i * W + w) * N + a] = v;
+}
+
+__global__ void transpose_kernel(const cplx* a, int M, cplx* b) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)M * M) return;
+    const int i = (int)(id / M), j = (int)(id % M);
+    b[(int64_t)j * M + i] = a[id];
+}
+
+struct Scratch {
+    std::vector<void*> p;
+    cudaStream_t st;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    template <typename T>
+    T* get(size_t count) {
+        void* q = nullptr;
+        if (cudaMallocAsync(&q, sizeof(T) * std::max<size_t>(count, 1), st) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p.push_back(q);
+        return static_cast<T*>(q);
+    }
+    ~Scratch() {
+        for (void* q : p) cudaFreeAsync(q, st);
+    }
+};
+
+}  // namespace
+
+void bp_close(afqmc_walkers* wk) {
+    for (int s = 0; s < 2; ++s) {
+        if (wk->bp_Phi[s]) cudaFree(wk->bp_Phi[s]);
+        wk->bp_Phi[s] = nullptr;
+    }
+    if (wk->bp_coef) cudaFree(wk->bp_coef);
+    wk->bp_coef = nullptr;
+    wk->bp_n = -1;
+    wk->bp_k = 0;
+    wk->bp_overrun = false;
+}
+
+int bp_open(afqmc_walkers* wk, int nbp, cudaStream_t st) {
+    bp_close(wk);
+    const int M = wk->M, W = wk->W;
+    bool ok = true;
+    for (int s = 0; s < 2; ++s)
+        ok = ok && cudaMalloc(&wk->bp_Phi[s], sizeof(cplx) * (size_t)W * M * wk->N[s]) == cudaSuccess;
+    ok = ok && cudaMalloc(&wk->bp_coef, sizeof(cplx) * (size_t)std::max(nbp, 1) * W * wk->Nchol) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        bp_close(wk);
+        return fail(AFQMC_ERR_OOM, "bp_begin: window buffers");
+    }
+    if (wk->opts.precision == AFQMC_PREC_BF16X3) AFQMC_TRY(tc_sync_walkers_to_fp64(wk, st));
+    for (int s = 0; s < 2; ++s)
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(wk->bp_Phi[s], wk->f.Phi[s], sizeof(cplx) * (size_t)W * M * wk->N[s],
+                                       cudaMemcpyDeviceToDevice, st));
+    wk->bp_n = nbp;
+    return AFQMC_OK;
+}
+
+void bp_record(afqmc_walkers* wk, cudaStream_t st) {
+    if (wk->bp_n < 0) return;
+    if (wk->bp_k < wk->bp_n) {
+        const size_t per = (size_t)wk->W * wk->Nchol;
+        cudaMemcpyAsync(wk->bp_coef + (size_t)wk->bp_k * per, wk->coef, sizeof(cplx) * per,
+                        cudaMemcpyDeviceToDevice, st);
+        ++wk->bp_k;
+    } else {
+        wk->bp_overrun = true;
+    }
+}
+
+int bp_follow_comb(afqmc_walkers* wk, const int* idx, cplx* tmp, cudaStream_t st) {
+    if (wk->bp_n < 0) return AFQMC_OK;
+    const int W = wk->W;
+    for (int s = 0; s < 2; ++s) {
+        const int64_t per = (int64_t)wk->M * wk->N[s];
+        gather_rows(wk->bp_Phi[s], per, idx, W, tmp, st);
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(wk->bp_Phi[s], tmp, sizeof(cplx) * per * W, cudaMemcpyDeviceToDevice, st));
+    }
+    const int64_t per = wk->Nchol;
+    for (int k = 0; k < wk->bp_k; ++k) {
+        cplx* slot = wk->bp_coef + (int64_t)k * W * per;
+        gather_rows(slot, per, idx, W, tmp, st);
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(slot, tmp, sizeof(cplx) * per * W, cudaMemcpyDeviceToDevice, st));
+    }
+    return AFQMC_OK;
+}
+
+namespace {
+
+// G[s] (device, M x M each) from a complete window.  flag: device word, FLAG_NONFINITE when
+// G is not finite.
+int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
+    Fp64Buffers& f = wk->f;
+    const int M = wk->M, W = wk->W, nch = wk->Nchol, K = wk->opts.k_taylor;
+    const int Nmax = std::max(wk->N[0], wk->N[1]);
+    const int64_t MM = (int64_t)M * M, big = (int64_t)W * M * Nmax;
+    const bool rB = !wk->ham->cplx_L;   // B and L are real unless the Hamiltonian is complex
+    const double sq = sqrt(wk->tau);
+    Scratch sc(st);
+    cplx* Q = sc.get<cplx>(big);
+    cplx* P0 = sc.get<cplx>(big);
+    cplx* P1 = sc.get<cplx>(big);
+    cplx* acc = sc.get<cplx>(big);
+    cplx* Th = sc.get<cplx>(big);
+    cplx* cc = sc.get<cplx>((size_t)W * nch);
+    cplx* S = sc.get<cplx>((size_t)W * Nmax * Nmax);
+    cplx* ld = sc.get<cplx>(W);
+    cplx* H = sc.get<cplx>(MM);
+    cplx* tot = sc.get<cplx>(1);
+    unsigned* sing = sc.get<unsigned>(1);
+    if (!Q || !P0 || !P1 || !acc || !Th || !cc || !S || !ld || !H || !tot || !sing)
+        return fail(AFQMC_ERR_OOM, "bp_rdm1: workspace");
+    count_launch();
+    weight_total_kernel<<<1, kT, 0, st>>>(wk->weight, W, tot);
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        const int64_t mn = (int64_t)M * N;
+        replicate(Q, f.Psi[s], mn, W, mn, st);
+        for (int k = wk->bp_n - 1; k >= 0; --k) {
+            // A(k)^+ = sum_n conj(c_n) L_n for every walker
+            count_launch();
+            conj_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->bp_coef + (int64_t)k * W * nch, cc,
+                                                            (int64_t)W * nch);
+            GemmArgs g;
+            g.m = W; g.n = (int)MM; g.k = nch;
+            g.A.ptr = cc; g.A.ld = nch;
+            g.B.ptr = wk->ham->L; g.B.real = rB; g.B.ld = MM;
+            g.C = f.A; g.ldc = MM;
+            zgemm(g, st);
+            GemmArgs b1;   // P0 = B Q
+            b1.m = M; b1.n = N; b1.k = M; b1.nb1 = W;
+            b1.A.ptr = f.Bh; b1.A.real = rB; b1.A.ld = M;
+            b1.B.ptr = Q; b1.B.ld = N; b1.B.s1 = mn;
+            b1.C = P0; b1.ldc = N; b1.sc1 = mn;
+            zgemm(b1, st);
+            AFQMC_CUDA_TRY(cudaMemcpyAsync(acc, P0, sizeof(cplx) * W * mn, cudaMemcpyDeviceToDevice, st));
+            cplx* p0 = P0;
+            cplx* p1 = P1;
+            for (int t = 1; t <= K; ++t) {
+                GemmArgs tg;   // p1 = (-i sqrt(tau) / t) A^+ p0 ;  acc += p1
+                tg.m = M; tg.n = N; tg.k = M; tg.nb1 = W;
+                tg.A.ptr = f.A; tg.A.ld = M; tg.A.s1 = MM;
+                tg.B.ptr = p0; tg.B.ld = N; tg.B.s1 = mn;
+                tg.alpha = cplx{0.0, -sq / t};
+                tg.C = p1; tg.ldc = N; tg.sc1 = mn;
+                tg.D = acc; tg.ldd = N; tg.sd1 = mn;
+                zgemm(tg, st);
+                std::swap(p0, p1);
+            }
+            GemmArgs b2;   // Q = B acc
+            b2.m = M; b2.n = N; b2.k = M; b2.nb1 = W;
+            b2.A.ptr = f.Bh; b2.A.real = rB; b2.A.ld = M;
+            b2.B.ptr = acc; b2.B.ld = N; b2.B.s1 = mn;
+            b2.C = Q; b2.ldc = N; b2.sc1 = mn;
+            zgemm(b2, st);
+            const int done = wk->bp_n - k;
+            if (wk->opts.k_qr > 0 && done % wk->opts.k_qr == 0 && k > 0)
+                qr_reorthonormalise(Q, mn, M, N, W, wk->weight, st);
+        }
+        {   // S = Psi_bp^+ Phi(0), inverted in place
+            GemmArgs g;
+            g.m = N; g.n = N; g.k = M; g.nb1 = W;
+            g.A.ptr = Q; g.A.op = OP_C; g.A.ld = N; g.A.s1 = mn;
+            g.B.ptr = wk->bp_Phi[s]; g.B.ld = N; g.B.s1 = mn;
+            g.C = S; g.ldc = N; g.sc1 = (int64_t)N * N;
+            zgemm(g, st);
+        }
+        AFQMC_CUDA_TRY(cudaMemsetAsync(sing, 0, sizeof(unsigned), st));
+        batched_inverse_logdet(S, (int64_t)N * N, N, W, ld, true, sing, st);
+        {   // Theta = Phi(0) S^-1
+            GemmArgs g;
+            g.m = M; g.n = N; g.k = N; g.nb1 = W;
+            g.A.ptr = wk->bp_Phi[s]; g.A.ld = N; g.A.s1 = mn;
+            g.B.ptr = S; g.B.ld = N; g.B.s1 = (int64_t)N * N;
+            g.C = Th; g.ldc = N; g.sc1 = mn;
+            zgemm(g, st);
+        }
+        // H = sum_w (w_w / sum w) Theta_w Psi_bp,w^+ over K = (walker, orbital); G = H^T
+        count_launch();
+        to_orbital_major_kernel<<<nb((int64_t)W * mn), kT, 0, st>>>(Th, W, M, N, wk->weight, tot, P0);
+        count_launch();
+        to_orbital_major_kernel<<<nb((int64_t)W * mn), kT, 0, st>>>(Q, W, M, N, nullptr, nullptr, P1);
+        GemmArgs g;
+        g.m = M; g.n = M; g.k = W * N;
+        g.A.ptr = P0; g.A.ld = (int64_t)W * N;
+        g.B.ptr = P1; g.B.op = OP_C; g.B.ld = (int64_t)W * N;
+        g.C = H; g.ldc = M;
+        zgemm(g, st);
+        count_launch();
+        transpose_kernel<<<nb(MM), kT, 0, st>>>(H, M, G[s]);
+        check_finite(reinterpret_cast<const double*>(G[s]), 2 * MM, flag, st);
+    }
+    return AFQMC_OK;
+}
+
+}  // namespace
+
+}  // namespace afqmc
+
+using namespace afqmc;
+
+extern "C" {
+
+int afqmc_bp_begin(afqmc_wk_t wk, int nbp, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "bp_begin: NULL handle");
+    if (nbp < 0) return fail(AFQMC_ERR_BADARG, "bp_begin: negative window length");
+    return bp_open(wk, nbp, static_cast<cudaStream_t>(stream));
+}
+
+int afqmc_bp_rdm1(afqmc_wk_t wk, double* rdm_up, double* rdm_dn, void* stream) {
+    if (!wk) return fail(AFQMC_ERR_BADARG, "bp_rdm1: NULL handle");
+    if (wk->bp_n < 0) return fail(AFQMC_ERR_BADARG, "bp_rdm1: no back-propagation window is open");
+    if (wk->bp_overrun) return fail(AFQMC_ERR_BADARG, "bp_rdm1: a step ran after the window was complete");
+    if (wk->bp_k != wk->bp_n)
+        return fail(AFQMC_ERR_BADARG, "bp_rdm1: the window has " + std::to_string(wk->bp_k) + " of its " +
+                                          std::to_string(wk->bp_n) + " steps");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t MM = (int64_t)wk->M * wk->M;
+    Scratch sc(st);
+    cplx* G = sc.get<cplx>(2 * MM);
+    unsigned* flag = sc.get<unsigned>(1);
+    if (!G || !flag) return fail(AFQMC_ERR_OOM, "bp_rdm1: output buffers");
+    AFQMC_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
+    cplx* Gs[2] = {G, G + MM};
+    AFQMC_TRY(bp_rdm1(wk, Gs, flag, st));
+    bool sync = false;
+    AFQMC_TRY(copy_out(rdm_up, Gs[0], sizeof(cplx) * MM, st, &sync));
+    AFQMC_TRY(copy_out(rdm_dn, Gs[1], sizeof(cplx) * MM, st, &sync));
+    unsigned fl = 0;
+    AFQMC_TRY(read_flags(flag, st, &fl));
+    if (fl & FLAG_NONFINITE)
+        return fail(AFQMC_ERR_NONFINITE, "bp_rdm1: a live walker's back-propagated overlap vanished");
+    AFQMC_TRY(read_flags(wk->flags, st, &fl));
+    return flags_to_error(fl, "bp_rdm1");
+}
+
+}  // extern "C"

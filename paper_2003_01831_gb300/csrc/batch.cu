@@ -32,12 +32,6 @@
 
 #include "state.cuh"
 
-namespace afqmc {
-bool is_device_ptr(const void* p);
-int read_flags(unsigned* dflags, cudaStream_t st, unsigned* out);
-int flags_to_error(unsigned f, const char* where);
-}  // namespace afqmc
-
 using namespace afqmc;
 
 struct afqmc_batch {

@@ -76,6 +76,14 @@ struct afqmc_walkers {
     int emix_cap = 0;
     unsigned* flags = nullptr;
 
+    // back-propagation window (backprop.cu): walkers at its start and the shifted fields
+    // c = x - xbar of the steps recorded since
+    int bp_n = -1;                    // window length in steps; -1: no window open
+    int bp_k = 0;                     // steps recorded so far
+    bool bp_overrun = false;          // a step ran after the window was complete
+    afqmc::cplx* bp_Phi[2] = {nullptr, nullptr};   // [W][M][N_s]
+    afqmc::cplx* bp_coef = nullptr;   // [bp_n][W][Nchol]
+
     // timing of the energy contraction (device events around it in the last step)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_valid = false;
@@ -104,5 +112,21 @@ int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_debug_terms(afqmc_walkers* wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X, double* E1);
 int tc_energy_products(afqmc_walkers* wk, double* mean);
+
+// back-propagation window (backprop.cu)
+int bp_open(afqmc_walkers* wk, int nbp, cudaStream_t st);
+void bp_close(afqmc_walkers* wk);
+void bp_record(afqmc_walkers* wk, cudaStream_t st);
+// after population control: every walker's window copy and history from its source idx[w];
+// tmp holds at least W * max(M * max N_s, Nchol) complex elements
+int bp_follow_comb(afqmc_walkers* wk, const int* idx, cplx* tmp, cudaStream_t st);
+
+// host helpers of the C-ABI front end (afqmc_api.cu)
+bool is_device_ptr(const void* p);
+int copy_in(void* dst, const void* src, size_t bytes, cudaStream_t st);
+// copies to a caller pointer; *needs_sync is set when the destination is host memory
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st, bool* needs_sync);
+int read_flags(unsigned* dflags, cudaStream_t st, unsigned* out);   // synchronises st
+int flags_to_error(unsigned f, const char* where);
 
 }  // namespace afqmc

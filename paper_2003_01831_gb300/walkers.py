@@ -93,6 +93,17 @@ class AFQMC:
         api.afqmc_population_control(self.wk, xi, idx, self.stream)
         return idx
 
+    def bp_begin(self, nbp: int):
+        """Open a back-propagation window of nbp steps at the current walkers."""
+        api.afqmc_bp_begin(self.wk, nbp, self.stream)
+
+    def bp_rdm1(self):
+        """(G_up, G_dn): back-propagated one-body density matrices, G[i, j] = <c+_i c_j>,
+        once the window's nbp steps have run."""
+        G = [np.zeros((self.M, self.M), dtype=np.complex128) for _ in range(2)]
+        api.afqmc_bp_rdm1(self.wk, G[0], G[1], self.stream)
+        return G[0], G[1]
+
     def set_walkers(self, Phi_up, Phi_dn, w, step: int):
         Phi = np.ascontiguousarray(np.concatenate(
             [np.asarray(Phi_up).reshape(self.W, -1), np.asarray(Phi_dn).reshape(self.W, -1)], axis=1),

@@ -64,6 +64,8 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
     assert mk(h.ctypes.data, Lc.ctypes.data, 0.0, 4, 0, None, ctypes.byref(out)) == -2
     assert mk(h.ctypes.data, Lc.ctypes.data, float("inf"), 4, 2, None, ctypes.byref(out)) == -4
     assert lib.afqmc_step(None, 1, None, 0, 0, None, None) == -1
+    assert lib.afqmc_bp_begin(None, 3, None) == -1
+    assert lib.afqmc_bp_rdm1(None, None, None, None) == -1
     assert lib.afqmc_energy(None, None, None, None, None, None) == -1
     assert lib.afqmc_destroy_walkers(None) == -1
     assert lib.afqmc_destroy_hamiltonian(None) == -1
