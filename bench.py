@@ -259,6 +259,82 @@ def run_batch(args, rank, world):
     return 0
 
 
+def run_bp(args, rank, world):
+    """Back-propagated one-body density matrix at the throughput system: W walkers (BF16X3 by
+    default) take --warmup steps, open a window of nbp = --steps steps and step through it;
+    afqmc_bp_rdm1 then carries the trial back through the window's adjoint propagators and
+    forms the weighted density matrices (FP64 zgemm and the batched inverse).  value =
+    back-propagated walker-steps per second of that call, timed with CUDA events on the
+    launching stream."""
+    import torch
+    from paper_2003_01831_gb300 import api, synthetic as syn
+    from paper_2003_01831_gb300.walkers import AFQMC
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    wl = syn.workload("m512", W=args.walkers or 1024)
+    h, L, E0, Psi = build_system(wl)
+    prec = api.PREC_BF16X3 if args.precision == "bf16x3" else api.PREC_FP64
+    stream = torch.cuda.current_stream().cuda_stream
+    g = AFQMC(h, L, E0, Psi[0], Psi[1], wl.W, wl.tau, k_qr=wl.k_qr, precision=prec, stream=stream,
+              walker_offset=rank * wl.W)
+    del L
+    seed, nbp, M, K = 1234, args.steps, wl.M, 6
+    for _ in range(args.warmup):
+        g.step(1, None, seed=seed, measure_every=1)
+    g.bp_begin(nbp)
+    g.step(nbp, None, seed=seed, measure_every=1)
+    torch.cuda.synchronize()
+    G = [torch.empty((M, M), dtype=torch.complex128, device="cuda") for _ in range(2)]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record()
+        api.afqmc_bp_rdm1(g.wk, G[0], G[1], stream)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    trace = [float(torch.trace(G[s]).real) for s in range(2)]
+    # end to end through the public API: the same call with host outputs
+    Gh = [np.zeros((M, M), dtype=np.complex128) for _ in range(2)]
+    t0 = time.perf_counter()
+    api.afqmc_bp_rdm1(g.wk, Gh[0], Gh[1], stream)
+    e2e_s = time.perf_counter() - t0
+    g.close()
+    W, nch, Ns = wl.W, wl.Nchol, (wl.Nup, wl.Ndn)
+    # algorithmic FP64 flops: per back step the HS potential (complex x real, 4 W M^2 Nchol), K
+    # Taylor terms (complex, 8 W M^2 N each) and B twice (complex x real) per spin; then per spin
+    # the overlap, Theta (8 W M N^2 each), the inverse (~8 W N^3) and the walker sum (8 M^2 W N)
+    back = nbp * (4.0 * W * M * M * nch + sum((8.0 * K + 8.0) * W * M * M * n for n in Ns))
+    est = sum(16.0 * W * M * n * n + 8.0 * W * n ** 3 + 8.0 * M * M * W * n for n in Ns)
+    clocks = clk.summary()
+    fp64_peak = 304 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks.get("sm_max_mhz") else None
+    ach = (back + est) / (ms / 1e3) / 1e12
+    # launches: per back step conj + HS GEMM + per spin (B, K Taylor terms, B, QR every k_qr);
+    # then per spin overlap, inverse, Theta, two layout passes, walker-sum GEMM, transpose, check
+    qr = sum(1 for k in range(nbp) if wl.k_qr > 0 and (k + 1) % wl.k_qr == 0 and k + 1 < nbp)
+    launches = 1 + 2 + nbp * (2 + 2 * (K + 2)) + 2 * qr + 2 * 8
+    line = {"metric": "back-propagated walker-steps/sec (one-body density matrix of a window at M=512, N=128, "
+                      "Nchol=2560)",
+            "value": world * W * nbp / (ms / 1e3), "unit": "walker-steps/s", "n_gpus": world, "steps": nbp,
+            "warmup": args.warmup, "ms_per_step": ms / nbp, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}; back-propagation window of {nbp} steps, walkers "
+                                   f"{'BF16X3' if prec == api.PREC_BF16X3 else 'FP64'}",
+                       "l2": "inputs larger than L2 (L 5.4 GB, walkers 1.1 GB per spin)",
+                       "parallelism": f"walker replicas x{world}"},
+            "clocks": clocks, "gpu_launches": launches,
+            "e2e": {"value": world * W * nbp / e2e_s, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 2 * 16 * M * M, "per": "one afqmc_bp_rdm1 call, host outputs"},
+            "traces": trace,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": ach / fp64_peak if fp64_peak else None, "traffic": None,
+                         "kernel": "afqmc_bp_rdm1 (FP64 zgemm and batched inverse)",
+                         "peak_source": "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -276,6 +352,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     from paper_2003_01831_gb300 import synthetic as syn
+    if args.workload == "bp512":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
+                              "single-system throughput workload only"}), flush=True)
+            return 0
+        return run_bp(args, rank, world)
     wl = syn.workload(args.workload if args.workload != "batch64" else "m512")
     if args.walkers:
         wl = syn.workload(wl.name, W=args.walkers)

@@ -172,7 +172,7 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
     const bool rB = !wk->ham->cplx_L;   // B and L are real unless the Hamiltonian is complex
     const double sq = sqrt(wk->tau);
     Scratch sc(st);
-    cplx* Q = sc.get<cplx>(big);
+    cplx* Qs[2] = {sc.get<cplx>(big), sc.get<cplx>(big)};
     cplx* P0 = sc.get<cplx>(big);
     cplx* P1 = sc.get<cplx>(big);
     cplx* acc = sc.get<cplx>(big);
@@ -183,25 +183,26 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
     cplx* H = sc.get<cplx>(MM);
     cplx* tot = sc.get<cplx>(1);
     unsigned* sing = sc.get<unsigned>(1);
-    if (!Q || !P0 || !P1 || !acc || !Th || !cc || !S || !ld || !H || !tot || !sing)
+    if (!Qs[0] || !Qs[1] || !P0 || !P1 || !acc || !Th || !cc || !S || !ld || !H || !tot || !sing)
         return fail(AFQMC_ERR_OOM, "bp_rdm1: workspace");
     count_launch();
     weight_total_kernel<<<1, kT, 0, st>>>(wk->weight, W, tot);
-    for (int s = 0; s < 2; ++s) {
-        const int N = wk->N[s];
-        const int64_t mn = (int64_t)M * N;
-        replicate(Q, f.Psi[s], mn, W, mn, st);
-        for (int k = wk->bp_n - 1; k >= 0; --k) {
-            // A(k)^+ = sum_n conj(c_n) L_n for every walker
-            count_launch();
-            conj_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->bp_coef + (int64_t)k * W * nch, cc,
-                                                            (int64_t)W * nch);
-            GemmArgs g;
-            g.m = W; g.n = (int)MM; g.k = nch;
-            g.A.ptr = cc; g.A.ld = nch;
-            g.B.ptr = wk->ham->L; g.B.real = rB; g.B.ld = MM;
-            g.C = f.A; g.ldc = MM;
-            zgemm(g, st);
+    for (int s = 0; s < 2; ++s)
+        replicate(Qs[s], f.Psi[s], (int64_t)M * wk->N[s], W, (int64_t)M * wk->N[s], st);
+    for (int k = wk->bp_n - 1; k >= 0; --k) {
+        // A(k)^+ = sum_n conj(c_n) L_n for every walker, shared by both spins
+        count_launch();
+        conj_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->bp_coef + (int64_t)k * W * nch, cc, (int64_t)W * nch);
+        GemmArgs g;
+        g.m = W; g.n = (int)MM; g.k = nch;
+        g.A.ptr = cc; g.A.ld = nch;
+        g.B.ptr = wk->ham->L; g.B.real = rB; g.B.ld = MM;
+        g.C = f.A; g.ldc = MM;
+        zgemm(g, st);
+        for (int s = 0; s < 2; ++s) {
+            const int N = wk->N[s];
+            const int64_t mn = (int64_t)M * N;
+            cplx* Q = Qs[s];
             GemmArgs b1;   // P0 = B Q
             b1.m = M; b1.n = N; b1.k = M; b1.nb1 = W;
             b1.A.ptr = f.Bh; b1.A.real = rB; b1.A.ld = M;
@@ -232,6 +233,11 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
             if (wk->opts.k_qr > 0 && done % wk->opts.k_qr == 0 && k > 0)
                 qr_reorthonormalise(Q, mn, M, N, W, wk->weight, st);
         }
+    }
+    for (int s = 0; s < 2; ++s) {
+        const int N = wk->N[s];
+        const int64_t mn = (int64_t)M * N;
+        const cplx* Q = Qs[s];
         {   // S = Psi_bp^+ Phi(0), inverted in place
             GemmArgs g;
             g.m = N; g.n = N; g.k = M; g.nb1 = W;
