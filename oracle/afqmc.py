@@ -210,6 +210,23 @@ def local_energy(ham: Hamiltonian, Psi: Sequence[np.ndarray], Phi: Sequence[np.n
     return ham.E0 + E1 + E2, t_sum, thetas
 
 
+def trial_local_energy(ham: Hamiltonian, Psi, Phi: Sequence[np.ndarray]):
+    """(E_L [W], t_sum [W, Nchol]) for a single-determinant trial (the pair of orbital
+    matrices Psi) or a multi-determinant one (an object with its own ``local_energy``,
+    ``oracle.msd.MSDTrial``)."""
+    if hasattr(Psi, "local_energy"):
+        return Psi.local_energy(ham, Phi)
+    E_L, t_sum, _ = local_energy(ham, Psi, Phi)
+    return E_L, t_sum
+
+
+def trial_log_overlap(Psi, Phi: Sequence[np.ndarray]) -> np.ndarray:
+    """log <Psi_T|Phi_w>: [W] (single determinant: sum over spins of log det(Psi^+ Phi))."""
+    if hasattr(Psi, "log_overlap"):
+        return Psi.log_overlap(Phi)
+    return sum(log_det(overlap_matrix(Psi[s], Phi[s])) for s in range(2))
+
+
 def force_bias(t_sum: np.ndarray, tau: float, fb_cap: float) -> np.ndarray:
     """xbar_n = -i sqrt(tau) <L_n>, each component capped at |xbar_n| <= fb_cap."""
     xbar = -1j * np.sqrt(tau) * t_sum
@@ -262,13 +279,17 @@ def qr_reorthonormalise(Phi: np.ndarray):
 
 def init_walkers(ham: Hamiltonian, Psi: Sequence[np.ndarray], W: int,
                  Phi0: Optional[Sequence[np.ndarray]] = None, complex_weights: bool = False) -> Walkers:
-    """Walkers start at Phi0 (or the trial), w = 1, E_T = E_L(trial)."""
+    """Walkers start at Phi0 (or the trial; a multi-determinant trial's largest-weight
+    determinant), w = 1, E_T = the trial's variational energy (for one determinant its own
+    local energy)."""
+    multi = hasattr(Psi, "variational_energy")
     if Phi0 is None:
-        Phi = [np.repeat(p[None].astype(np.complex128), W, axis=0) for p in Psi]
+        ref = Psi.reference() if multi else Psi
+        Phi = [np.repeat(np.asarray(p, dtype=np.complex128)[None], W, axis=0) for p in ref]
     else:
         Phi = [np.array(p, dtype=np.complex128) for p in Phi0]
-    logS = sum(log_det(overlap_matrix(Psi[s], Phi[s])) for s in range(2))
-    E_T = local_energy(ham, Psi, [p[None] for p in Psi])[0][0].real
+    logS = trial_log_overlap(Psi, Phi)
+    E_T = Psi.variational_energy(ham).real if multi else local_energy(ham, Psi, [p[None] for p in Psi])[0][0].real
     w = np.ones(W, dtype=np.complex128 if complex_weights else np.float64)
     return Walkers(Phi=Phi, w=w, logS=logS, E_T=E_T)
 
@@ -283,9 +304,10 @@ def step(ham: Hamiltonian, Psi: Sequence[np.ndarray], B: np.ndarray, wk: Walkers
     """One phaseless step for every walker with fields x [W, Nchol].
 
     Returns (E_L [W] at the pre-step walkers, E_mix with the pre-step weights).
-    Updates wk in place.  If `record` is a list, the shifted fields c = x - xbar that drove
+    Updates wk in place.  Psi is the trial: the pair of orbital matrices of a single
+    determinant, or an ``oracle.msd.MSDTrial``.  If `record` is a list, the shifted fields c = x - xbar that drove
     each walker's propagator are appended to it ([W, Nchol]; zero rows for frozen walkers)."""
-    E_L, t_sum, _ = local_energy(ham, Psi, wk.Phi)
+    E_L, t_sum = trial_local_energy(ham, Psi, wk.Phi)
     E_mix = mixed_energy(wk.w, E_L)
     free = p.mode == "free"
     xbar = force_bias(t_sum, p.tau, 0.0 if free else p.fb_cap)
@@ -295,7 +317,7 @@ def step(ham: Hamiltonian, Psi: Sequence[np.ndarray], B: np.ndarray, wk: Walkers
         record.append(np.where(alive[:, None], c, 0.0))
     A = hs_potential(c, ham.L)
     newPhi = [propagate(wk.Phi[s], A, B, p.tau, p.k_taylor) for s in range(2)]
-    newlogS = sum(log_det(overlap_matrix(Psi[s], newPhi[s])) for s in range(2))
+    newlogS = trial_log_overlap(Psi, newPhi)
     dl = newlogS - wk.logS
     expo = dl + np.sum(x * xbar, axis=1) - 0.5 * np.sum(xbar * xbar, axis=1) \
         + p.tau * (wk.E_T - ham.E0)

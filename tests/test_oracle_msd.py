@@ -1,0 +1,109 @@
+"""Pins of the multi-determinant trial oracle (oracle/msd.py; Sec. V: |psi_T> = sum_I c_I |D_I>,
+orthogonal CI or non-orthogonal with <D_I|D_J> = S_IJ).
+
+* Overlap, local energy, force-bias traces and the variational energy (the place where S_IJ
+  enters) against brute-force Fock-space vectors sum_I c_I |D_I>.
+* One determinant and a repeated determinant reduce to the single-determinant functions; a
+  re-gauged expansion (D_I -> D_I R_I, c_I -> c_I / det R_I: the same state) changes nothing.
+* The phaseless step runs with the expansion, and a one-determinant expansion reproduces the
+  single-determinant trajectory."""
+import numpy as np
+
+from oracle import afqmc as O
+from oracle.fock import FockSpace, four_index_from_cholesky
+from oracle.msd import MSDTrial
+from paper_2003_01831_gb300 import synthetic as syn
+
+
+def crandn(rng, *shape):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def system(seed, M=5, Nup=2, Ndn=2, nch=4, ND=3):
+    rng = np.random.default_rng(seed)
+    h, L, _ = syn.make_hamiltonian(M, nch, rng)
+    ham = O.Hamiltonian(h=h, L=L, E0=0.4)
+    dets = [(crandn(rng, M, Nup), crandn(rng, M, Ndn)) for _ in range(ND)]
+    c = crandn(rng, ND)
+    Phi = [crandn(rng, 3, M, Nup), crandn(rng, 3, M, Ndn)]
+    return ham, MSDTrial(dets, c), Phi, rng
+
+
+def fock_vector(fs, trial):
+    return sum(c * fs.slater_vector(*D) for c, D in zip(trial.c, trial.dets))
+
+
+def test_mixed_estimates_against_fock_space():
+    ham, trial, Phi, _ = system(3)
+    fs = FockSpace(5, 2, 2)
+    H = fs.hamiltonian(ham.h, four_index_from_cholesky(ham.L), ham.E0)
+    vp = fock_vector(fs, trial)
+    lo = trial.log_overlap(Phi)
+    E, t = trial.local_energy(ham, Phi)
+    for w in range(3):
+        vf = fs.slater_vector(Phi[0][w], Phi[1][w])
+        ov = np.vdot(vp, vf)
+        assert abs(np.exp(lo[w]) - ov) < 1e-12 * abs(ov)
+        ref = np.vdot(vp, H @ vf) / ov
+        assert abs(E[w] - ref) < 1e-11 * max(1.0, abs(ref)), w
+        for n in range(ham.Nchol):
+            tref = np.vdot(vp, fs.one_body_operator(ham.L[n]) @ vf) / ov
+            assert abs(t[w, n] - tref) < 1e-11 * max(1.0, abs(tref)), (w, n)
+    Ev = np.vdot(vp, H @ vp) / np.vdot(vp, vp)
+    assert abs(trial.variational_energy(ham) - Ev) < 1e-11 * abs(Ev)
+    assert abs(Ev.imag) < 1e-12 * abs(Ev)
+
+
+def test_one_and_repeated_determinants_reduce_to_the_single_determinant():
+    ham, trial, Phi, _ = system(4)
+    D = trial.dets[1]
+    E1, t1, _ = O.local_energy(ham, D, Phi)
+    ld = sum(O.log_det(O.overlap_matrix(D[s], Phi[s])) for s in range(2))
+    for tr, cs in ((MSDTrial([D], [2.0 - 1.0j]), 2.0 + 1.0j), (MSDTrial([D, D], [0.3 + 0.2j, 1.1 - 0.7j]), 1.4 + 0.5j)):
+        E, t = tr.local_energy(ham, Phi)
+        assert np.max(np.abs(E - E1)) < 1e-12 * np.max(np.abs(E1))
+        assert np.max(np.abs(t - t1)) < 1e-12 * np.max(np.abs(t1))
+        assert np.max(np.abs(np.exp(tr.log_overlap(Phi) - ld) - cs)) < 1e-12
+    E_T = O.local_energy(ham, D, [D[0][None], D[1][None]])[0][0]
+    assert abs(MSDTrial([D], [0.5j]).variational_energy(ham) - E_T) < 1e-12 * abs(E_T)
+
+
+def test_regauged_expansion_is_the_same_state():
+    ham, trial, Phi, rng = system(5)
+    dets, c = [], []
+    for cI, (Du, Dd) in zip(trial.c, trial.dets):
+        Ru = crandn(rng, 2, 2) + 2 * np.eye(2)
+        Rd = crandn(rng, 2, 2) + 2 * np.eye(2)
+        dets.append((Du @ Ru, Dd @ Rd))
+        c.append(cI / (np.linalg.det(Ru) * np.linalg.det(Rd)))
+    g = MSDTrial(dets, c)
+    E, t = trial.local_energy(ham, Phi)
+    Eg, tg = g.local_energy(ham, Phi)
+    assert np.max(np.abs(Eg - E)) < 1e-11 * np.max(np.abs(E))
+    assert np.max(np.abs(tg - t)) < 1e-11 * np.max(np.abs(t))
+    assert np.max(np.abs(np.exp(g.log_overlap(Phi) - trial.log_overlap(Phi)) - 1)) < 1e-11
+    assert abs(g.variational_energy(ham) - trial.variational_energy(ham)) < 1e-11 * abs(trial.variational_energy(ham))
+    # negative control: forgetting the determinant factor changes the state
+    bad = MSDTrial(dets, trial.c)
+    assert np.max(np.abs(bad.local_energy(ham, Phi)[0] - E)) > 1e-6
+
+
+def test_phaseless_run_with_an_expansion():
+    rng = np.random.default_rng(8)
+    M, N, nch = 6, 2, 8
+    h, L, E0 = syn.make_hamiltonian(M, nch, rng)
+    ham = O.Hamiltonian(h=h, L=L, E0=E0)
+    Psi = syn.make_trial(h, N, N)
+    p = O.Params(tau=0.01, k_taylor=6, k_qr=2)
+    x = rng.standard_normal((5, 4, nch))
+    single = O.run(ham, Psi, 4, x, p)
+    one = O.run(ham, MSDTrial([Psi], [1.0]), 4, x, p)
+    assert np.max(np.abs(np.array(one["E_mix"]) - np.array(single["E_mix"]))) < 1e-12
+    # a second determinant: the trial's lowest orbitals with one excitation per spin
+    _, v = np.linalg.eigh(h)
+    D2 = v[:, [0, 2]]
+    tr = MSDTrial([Psi, (D2, D2)], [1.0, 0.2])
+    out = O.run(ham, tr, 4, x, p)
+    assert np.all(np.isfinite(np.array(out["E_mix"])))
+    assert np.all(out["walkers"].w > 0)
+    assert abs(out["E_T"] - tr.variational_energy(ham).real) == 0.0
