@@ -27,6 +27,11 @@ Readings of what the paper leaves open (also listed in the design notes):
     ties).
   * Log-overlaps are summed over determinants as a complex log-sum-exp shifted by the
     largest real part, so no overlap under- or overflows.
+  * Each determinant's term is evaluated as <D_I|Phi> times its own mixed estimate, which needs
+    <D_I|Phi> away from zero: this is the non-orthogonal (NOMSD) evaluation, without fast
+    updates.  An orthogonal CI expansion whose walkers sit exactly on the reference makes the
+    excited determinants' terms ill-conditioned; their Sherman-Morrison evaluation relative to
+    the reference is not restated here.
 
 Pins (tests/test_oracle_msd.py): overlap, local energy, force bias and variational energy
 against Fock-space vectors sum_I c_I |D_I>; one determinant, a repeated determinant and a

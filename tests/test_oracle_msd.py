@@ -99,9 +99,9 @@ def test_phaseless_run_with_an_expansion():
     single = O.run(ham, Psi, 4, x, p)
     one = O.run(ham, MSDTrial([Psi], [1.0]), 4, x, p)
     assert np.max(np.abs(np.array(one["E_mix"]) - np.array(single["E_mix"]))) < 1e-12
-    # a second determinant: the trial's lowest orbitals with one excitation per spin
+    # a second, non-orthogonal determinant: the trial's second orbital rotated towards the third
     _, v = np.linalg.eigh(h)
-    D2 = v[:, [0, 2]]
+    D2 = np.stack([v[:, 0], np.cos(0.4) * v[:, 1] + np.sin(0.4) * v[:, 2]], axis=1)
     tr = MSDTrial([Psi, (D2, D2)], [1.0, 0.2])
     out = O.run(ham, tr, 4, x, p)
     assert np.all(np.isfinite(np.array(out["E_mix"])))
