@@ -132,6 +132,32 @@ int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
 int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn,
                        int W, const double* Phi0, double tau, const afqmc_opts* opts, void* stream,
                        afqmc_wk_t* out);
+
+/* ---- Walker set on a multi-determinant trial (Sec. V) ----------------------
+ * |psi_T> = sum_I c_I |D_I> over ND determinants, orthogonal (CI) or not (NOMSD,
+ * <D_I|D_J> = S_IJ).
+ * D_up [ND][M][Nup], D_dn [ND][M][Ndn]  complex orbitals of the determinants.
+ * c    complex [ND] coefficients (finite, not all zero).
+ * Every mixed estimate is the overlap-weighted average of the determinants' own:
+ * with u_I = conj(c_I) <D_I|Phi> / <psi_T|Phi>, E_L = sum_I u_I E_L,I and the force
+ * bias uses <L_n> = sum_I u_I <L_n>_I; the weights use <psi_T|Phi> (a log-sum-exp of
+ * the determinants' log-overlaps).  E_T is the trial's variational energy
+ * sum_IJ conj(c_I) c_J S_IJ E_L,I(D_J) / sum_IJ conj(c_I) c_J S_IJ; without Phi0 the
+ * walkers start at the determinant with the largest |c_I| (lowest index on ties).
+ * Each determinant's term is formed as <D_I|Phi> times its own mixed estimate
+ * (no fast updates), which needs <D_I|Phi> away from zero: orthogonal CI expansions
+ * whose walkers sit exactly on the reference are ill-conditioned this way.
+ * A determinant whose overlap with a walker is exactly zero contributes nothing;
+ * SINGULAR is reported for a walker orthogonal to every determinant.  afqmc_energy's
+ * logS is log <psi_T|Phi>; with ND = 1 the coefficient is dropped (a constant factor
+ * changes no estimate) and the single-determinant path runs.
+ * Other arguments, sizes and errors as afqmc_init_walkers, plus SHAPE for ND outside
+ * 1..1024.  Only the FP64 path runs it: BF16X3, afqmc_energy_backward and
+ * afqmc_bp_begin return UNSUPPORTED for ND > 1.  Cost per step: ND times the
+ * single-determinant measurement and overlap. */
+int afqmc_init_walkers_msd(afqmc_ham_t ham, int ND, const double* D_up, const double* D_dn, const double* c,
+                           int Nup, int Ndn, int W, const double* Phi0, double tau, const afqmc_opts* opts,
+                           void* stream, afqmc_wk_t* out);
 int afqmc_destroy_walkers(afqmc_wk_t wk);
 
 /* ---- The walker step -----------------------------------------------------

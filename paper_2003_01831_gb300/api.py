@@ -32,7 +32,7 @@ WEIGHT_PHASELESS, WEIGHT_FREE, WEIGHT_LOCAL = 0, 1, 2
 EXPORTED = [
     "afqmc_default_opts", "afqmc_create_hamiltonian", "afqmc_create_hamiltonian_complex",
     "afqmc_destroy_hamiltonian",
-    "afqmc_init_walkers", "afqmc_destroy_walkers", "afqmc_step", "afqmc_energy",
+    "afqmc_init_walkers", "afqmc_init_walkers_msd", "afqmc_destroy_walkers", "afqmc_step", "afqmc_energy",
     "afqmc_energy_backward", "afqmc_get_walkers", "afqmc_set_walkers",
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
     "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
         "afqmc_create_hamiltonian_complex": (i, [vp, vp, d, i, i, vp, ctypes.POINTER(vp)]),
         "afqmc_destroy_hamiltonian": (i, [vp]),
         "afqmc_init_walkers": (i, [vp, vp, vp, i, i, i, vp, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]),
+        "afqmc_init_walkers_msd": (i, [vp, i, vp, vp, vp, i, i, i, vp, d, ctypes.POINTER(Opts), vp,
+                                       ctypes.POINTER(vp)]),
         "afqmc_destroy_walkers": (i, [vp]),
         "afqmc_step": (i, [vp, i, vp, u64, i, vp, vp]),
         "afqmc_energy": (i, [vp, vp, vp, vp, vp, vp]),
@@ -191,6 +193,16 @@ def afqmc_init_walkers(ham: int, Psi_up, Psi_dn, Nup: int, Ndn: int, W: int, Phi
     _check(lib().afqmc_init_walkers(ham, _ptr(Psi_up), _ptr(Psi_dn), int(Nup), int(Ndn), int(W), _ptr(Phi0),
                                     float(tau), ctypes.byref(opts) if opts is not None else None,
                                     _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def afqmc_init_walkers_msd(ham: int, ND: int, D_up, D_dn, c, Nup: int, Ndn: int, W: int, Phi0, tau: float,
+                           opts: Optional[Opts] = None, stream=None) -> int:
+    """Walker set on the trial sum_I c_I |D_I>: D_up [ND, M, Nup], D_dn [ND, M, Ndn], c [ND] complex."""
+    out = ctypes.c_void_p()
+    _check(lib().afqmc_init_walkers_msd(ham, int(ND), _ptr(D_up), _ptr(D_dn), _ptr(c), int(Nup), int(Ndn), int(W),
+                                        _ptr(Phi0), float(tau), ctypes.byref(opts) if opts is not None else None,
+                                        _stream(stream), ctypes.byref(out)))
     return out.value
 
 

@@ -256,11 +256,30 @@ static void free_walkers(afqmc_walkers* wk) {
     delete wk;
 }
 
-int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn, int W,
-                       const double* Phi0, double tau, const afqmc_opts* opts, void* stream, afqmc_wk_t* out) {
+}  // extern "C"
+
+// Walker set on a trial of ND determinants (coef: their complex coefficients, or NULL for one
+// determinant); Psi_up / Psi_dn hold the determinants one after another.
+static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, const double* Psi_dn, const double* coef,
+                             int Nup, int Ndn, int W, const double* Phi0, double tau, const afqmc_opts* opts,
+                             void* stream, afqmc_wk_t* out) {
     if (!out) return fail(AFQMC_ERR_BADARG, "init_walkers: out is NULL");
     *out = nullptr;
     if (!ham || !Psi_up || !Psi_dn) return fail(AFQMC_ERR_BADARG, "init_walkers: NULL handle or trial");
+    if (ND < 1 || ND > kMaxDets) return fail(AFQMC_ERR_SHAPE, "init_walkers: need 1 <= ND <= 1024 determinants");
+    std::vector<cplx> c_host(ND, cplx{1.0, 0.0});
+    int ref = 0;   // walkers start at the determinant with the largest |c_I| (lowest index on ties)
+    if (coef) {
+        AFQMC_CUDA_TRY(cudaMemcpy(c_host.data(), coef, sizeof(cplx) * ND, cudaMemcpyDefault));
+        bool any = false;
+        for (int I = 0; I < ND; ++I) {
+            if (!isfinite(c_host[I].re) || !isfinite(c_host[I].im))
+                return fail(AFQMC_ERR_NONFINITE, "init_walkers: non-finite determinant coefficient");
+            any = any || c_host[I].re != 0.0 || c_host[I].im != 0.0;
+            if (hypot(c_host[I].re, c_host[I].im) > hypot(c_host[ref].re, c_host[ref].im)) ref = I;
+        }
+        if (!any) return fail(AFQMC_ERR_BADARG, "init_walkers: every determinant coefficient is zero");
+    }
     afqmc_opts o;
     afqmc_default_opts(&o);
     if (opts) o = *opts;
@@ -291,6 +310,7 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
     wk->N[0] = Nup;
     wk->N[1] = Ndn;
     wk->W = W;
+    wk->ND = ND;
     wk->tau = tau;
     wk->opts = o;
     const int nch = ham->Nchol;
@@ -329,12 +349,17 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
     // flags[0]: latched status bits; flags[1]: scratch word (imaginary part of the trial)
     cudaMemsetAsync(wk->flags, 0, 2 * sizeof(unsigned), st);
     for (int s = 0; s < 2; ++s) {
-        rc = copy_in(f.Psi[s], psis[s], sizeof(cplx) * M * wk->N[s], st);
+        const int64_t n = (int64_t)ND * M * wk->N[s];
+        rc = copy_in(f.Psi[s], psis[s], sizeof(cplx) * n, st);
         if (rc) return bail(rc);
-        check_finite(reinterpret_cast<const double*>(f.Psi[s]), 2LL * M * wk->N[s], wk->flags, st);
+        check_finite(reinterpret_cast<const double*>(f.Psi[s]), 2 * n, wk->flags, st);
         count_launch();
-        max_abs_imag_kernel<<<nblk((int64_t)M * wk->N[s]), 256, 0, st>>>(f.Psi[s], (int64_t)M * wk->N[s],
-                                                                          wk->flags + 1);
+        max_abs_imag_kernel<<<nblk(n), 256, 0, st>>>(f.Psi[s], n, wk->flags + 1);
+    }
+    if (ND > 1) {   // conj(c_I), the factors of <psi_T| = sum_I conj(c_I) <D_I|
+        for (cplx& c : c_host) c.im = -c.im;
+        rc = copy_in(f.msd_cc, c_host.data(), sizeof(cplx) * ND, st);
+        if (rc) return bail(rc);
     }
     {
         unsigned fl[2] = {0, 0};
@@ -346,55 +371,91 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
     }
     if (o.precision == AFQMC_PREC_BF16X3 && ham->cplx_L)
         return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs real Cholesky vectors"));
+    if (o.precision == AFQMC_PREC_BF16X3 && ND > 1)
+        return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs a single-determinant trial"));
     if (o.precision == AFQMC_PREC_BF16X3) {
         if (!wk->trial_real || Nup != Ndn || M % 64 != 0 || nch % 8 != 0)
             return bail(fail(AFQMC_ERR_UNSUPPORTED,
                              "init_walkers: BF16X3 needs a real trial, Nup == Ndn, M % 64 == 0, Nchol % 8 == 0"));
     }
-    // rotated Cholesky tensor, its transpose, rotated one-body matrix
+    // rotated Cholesky tensor, its transpose, rotated one-body matrix, per determinant
     for (int s = 0; s < 2; ++s) {
         const int N = wk->N[s];
+        const int64_t mn = (int64_t)M * N, tot = (int64_t)nch * N * M;
         cplx* tmp = nullptr;
-        if (cudaMallocAsync(&tmp, sizeof(cplx) * (size_t)nch * N * M, st) != cudaSuccess)
+        if (cudaMallocAsync(&tmp, sizeof(cplx) * (size_t)tot, st) != cudaSuccess)
             return bail(fail(AFQMC_ERR_OOM, "init_walkers: workspace"));
-        GemmArgs g;   // tmp[n] = Psi^+ L_n   [N][M]
-        g.m = N; g.n = M; g.k = M; g.nb1 = nch;
-        g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = N;
-        g.B.ptr = ham->L; g.B.real = !ham->cplx_L; g.B.ld = M; g.B.s1 = (int64_t)M * M;
-        g.C = tmp; g.ldc = M; g.sc1 = (int64_t)N * M;
-        zgemm(g, st);
-        const int64_t tot = (int64_t)nch * N * M;
-        if (wk->Lt_real) {
-            double* Lr = static_cast<double*>(f.Lt[s]);
-            count_launch();
-            cplx_real_part_kernel<<<nblk(tot), 256, 0, st>>>(tmp, Lr, tot);
-            count_launch();
-            batched_transpose_kernel<double><<<nblk(tot), 256, 0, st>>>(Lr, static_cast<double*>(f.LtT[s]), nch, N, M);
-        } else {
-            cudaMemcpyAsync(f.Lt[s], tmp, sizeof(cplx) * tot, cudaMemcpyDeviceToDevice, st);
-            count_launch();
-            batched_transpose_kernel<cplx><<<nblk(tot), 256, 0, st>>>(tmp, static_cast<cplx*>(f.LtT[s]), nch, N, M);
+        for (int I = 0; I < ND; ++I) {
+            const cplx* Psi = f.Psi[s] + I * mn;
+            GemmArgs g;   // tmp[n] = Psi^+ L_n   [N][M]
+            g.m = N; g.n = M; g.k = M; g.nb1 = nch;
+            g.A.ptr = Psi; g.A.op = OP_C; g.A.ld = N;
+            g.B.ptr = ham->L; g.B.real = !ham->cplx_L; g.B.ld = M; g.B.s1 = (int64_t)M * M;
+            g.C = tmp; g.ldc = M; g.sc1 = (int64_t)N * M;
+            zgemm(g, st);
+            if (wk->Lt_real) {
+                double* Lr = static_cast<double*>(f.Lt[s]) + I * tot;
+                count_launch();
+                cplx_real_part_kernel<<<nblk(tot), 256, 0, st>>>(tmp, Lr, tot);
+                count_launch();
+                batched_transpose_kernel<double><<<nblk(tot), 256, 0, st>>>(
+                    Lr, static_cast<double*>(f.LtT[s]) + I * tot, nch, N, M);
+            } else {
+                cudaMemcpyAsync(static_cast<cplx*>(f.Lt[s]) + I * tot, tmp, sizeof(cplx) * tot,
+                                cudaMemcpyDeviceToDevice, st);
+                count_launch();
+                batched_transpose_kernel<cplx><<<nblk(tot), 256, 0, st>>>(
+                    tmp, static_cast<cplx*>(f.LtT[s]) + I * tot, nch, N, M);
+            }
+            GemmArgs gh;  // ht = Psi^+ h   [N][M]
+            gh.m = N; gh.n = M; gh.k = M;
+            gh.A.ptr = Psi; gh.A.op = OP_C; gh.A.ld = N;
+            gh.B.ptr = ham->h; gh.B.real = true; gh.B.ld = M;
+            gh.C = f.ht[s] + I * mn; gh.ldc = M;
+            zgemm(gh, st);
         }
-        GemmArgs gh;  // ht = Psi^+ h   [N][M]
-        gh.m = N; gh.n = M; gh.k = M;
-        gh.A.ptr = f.Psi[s]; gh.A.op = OP_C; gh.A.ld = N;
-        gh.B.ptr = ham->h; gh.B.real = true; gh.B.ld = M;
-        gh.C = f.ht[s]; gh.ldc = M;
-        zgemm(gh, st);
         cudaFreeAsync(tmp, st);
     }
     rc = ham->cplx_L ? expm_complex(reinterpret_cast<const cplx*>(ham->hp), -0.5 * tau, M,
                                     reinterpret_cast<cplx*>(f.Bh), st)
                      : expm_real(ham->hp, -0.5 * tau, M, f.Bh, st);
     if (rc) return bail(rc);
-    // trial energy E_T from walker 0 placed at the trial
-    for (int s = 0; s < 2; ++s)
-        cudaMemcpyAsync(f.Phi[s], f.Psi[s], sizeof(cplx) * M * wk->N[s], cudaMemcpyDeviceToDevice, st);
+    // trial energy E_T: the trial's variational energy.  One determinant: its local energy with
+    // walker 0 placed at it.  ND determinants: with walker 0 at each D_J in turn, the local
+    // energies E_IJ and log-overlaps log S_IJ of every D_I, then
+    // sum_IJ conj(c_I) c_J S_IJ E_IJ / sum_IJ conj(c_I) c_J S_IJ.
     fill_cplx(wk->weight, W, cplx{1.0, 0.0}, st);
-    rc = fp64_measure(wk, true, st, 1);
-    if (rc) return bail(rc);
     cplx et;
-    AFQMC_CUDA_TRY(cudaMemcpyAsync(&et, wk->E_L, sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    if (ND == 1) {
+        for (int s = 0; s < 2; ++s)
+            cudaMemcpyAsync(f.Phi[s], f.Psi[s], sizeof(cplx) * M * wk->N[s], cudaMemcpyDeviceToDevice, st);
+        rc = fp64_measure(wk, true, st, 1);
+        if (rc) return bail(rc);
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(&et, wk->E_L, sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    } else {
+        cplx *EIJ = nullptr, *LIJ = nullptr, *d_et = nullptr;
+        if (cudaMallocAsync(&EIJ, sizeof(cplx) * ND * ND, st) != cudaSuccess ||
+            cudaMallocAsync(&LIJ, sizeof(cplx) * ND * ND, st) != cudaSuccess ||
+            cudaMallocAsync(&d_et, sizeof(cplx), st) != cudaSuccess)
+            return bail(fail(AFQMC_ERR_OOM, "init_walkers: workspace"));
+        for (int J = 0; J < ND; ++J) {
+            for (int s = 0; s < 2; ++s)
+                cudaMemcpyAsync(f.Phi[s], f.Psi[s] + (int64_t)J * M * wk->N[s], sizeof(cplx) * M * wk->N[s],
+                                cudaMemcpyDeviceToDevice, st);
+            rc = fp64_measure(wk, true, st, 1);
+            if (rc) return bail(rc);
+            // column J of [ND][ND] from the first entries of the [ND][W] per-determinant arrays
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(EIJ + J, sizeof(cplx) * ND, f.msd_E, sizeof(cplx) * W, sizeof(cplx), ND,
+                                             cudaMemcpyDeviceToDevice, st));
+            AFQMC_CUDA_TRY(cudaMemcpy2DAsync(LIJ + J, sizeof(cplx) * ND, f.msd_ls, sizeof(cplx) * W, sizeof(cplx), ND,
+                                             cudaMemcpyDeviceToDevice, st));
+        }
+        msd_variational_energy(f.msd_cc, EIJ, LIJ, ND, d_et, st);
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(&et, d_et, sizeof(cplx), cudaMemcpyDeviceToHost, st));
+        cudaFreeAsync(EIJ, st);
+        cudaFreeAsync(LIJ, st);
+        cudaFreeAsync(d_et, st);
+    }
     AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
     wk->E_T = et.re;
     // walkers
@@ -410,23 +471,29 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
         }
     } else {
         for (int s = 0; s < 2; ++s)
-            replicate(f.Phi[s], f.Psi[s], (int64_t)M * wk->N[s], W, (int64_t)M * wk->N[s], st);
+            replicate(f.Phi[s], f.Psi[s] + (int64_t)ref * M * wk->N[s], (int64_t)M * wk->N[s], W,
+                      (int64_t)M * wk->N[s], st);
     }
     cudaMemsetAsync(wk->flags, 0, sizeof(unsigned), st);
     if (o.precision == AFQMC_PREC_BF16X3) {
         rc = tc_alloc(wk, st);
         if (rc) return bail(rc);
     }
-    // check the walkers' overlaps once
-    for (int s = 0; s < 2; ++s) {
-        const int N = wk->N[s];
-        GemmArgs g;
-        g.m = N; g.n = N; g.k = M; g.nb1 = W;
-        g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = N;
-        g.B.ptr = f.Phi[s]; g.B.ld = N; g.B.s1 = (int64_t)M * N;
-        g.C = f.S[s]; g.ldc = N; g.sc1 = (int64_t)N * N;
-        zgemm(g, st);
-        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, wk->flags, st);
+    // check the walkers' overlaps with the trial once (several determinants: the combined one)
+    if (ND == 1) {
+        for (int s = 0; s < 2; ++s) {
+            const int N = wk->N[s];
+            GemmArgs g;
+            g.m = N; g.n = N; g.k = M; g.nb1 = W;
+            g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = N;
+            g.B.ptr = f.Phi[s]; g.B.ld = N; g.B.s1 = (int64_t)M * N;
+            g.C = f.S[s]; g.ldc = N; g.sc1 = (int64_t)N * N;
+            zgemm(g, st);
+            batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, wk->flags, st);
+        }
+    } else {
+        rc = fp64_measure(wk, false, st);
+        if (rc) return bail(rc);
     }
     unsigned fl = 0;
     rc = read_flags(wk->flags, st, &fl);
@@ -437,6 +504,23 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
     ham->live_walker_sets++;
     *out = wk;
     return AFQMC_OK;
+}
+
+extern "C" {
+
+int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn, int W,
+                       const double* Phi0, double tau, const afqmc_opts* opts, void* stream, afqmc_wk_t* out) {
+    return init_walkers_impl(ham, 1, Psi_up, Psi_dn, nullptr, Nup, Ndn, W, Phi0, tau, opts, stream, out);
+}
+
+int afqmc_init_walkers_msd(afqmc_ham_t ham, int ND, const double* D_up, const double* D_dn, const double* c,
+                           int Nup, int Ndn, int W, const double* Phi0, double tau, const afqmc_opts* opts,
+                           void* stream, afqmc_wk_t* out) {
+    if (!c) {
+        if (out) *out = nullptr;
+        return fail(AFQMC_ERR_BADARG, "init_walkers_msd: NULL coefficients");
+    }
+    return init_walkers_impl(ham, ND, D_up, D_dn, c, Nup, Ndn, W, Phi0, tau, opts, stream, out);
 }
 
 int afqmc_destroy_walkers(afqmc_wk_t wk) {
@@ -672,6 +756,7 @@ int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, 
                           double* dL, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "energy_backward: NULL handle");
     if (wk->ham->cplx_L) return fail(AFQMC_ERR_UNSUPPORTED, "energy_backward: needs real Cholesky vectors");
+    if (wk->ND > 1) return fail(AFQMC_ERR_UNSUPPORTED, "energy_backward: needs a single-determinant trial");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return fp64_backward(wk, reinterpret_cast<const cplx*>(dE), reinterpret_cast<const cplx*>(dlogS),
                          reinterpret_cast<cplx*>(dPsi_up), reinterpret_cast<cplx*>(dPsi_dn), dL, st);

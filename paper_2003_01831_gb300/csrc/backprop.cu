@@ -285,6 +285,7 @@ extern "C" {
 int afqmc_bp_begin(afqmc_wk_t wk, int nbp, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "bp_begin: NULL handle");
     if (nbp < 0) return fail(AFQMC_ERR_BADARG, "bp_begin: negative window length");
+    if (wk->ND > 1) return fail(AFQMC_ERR_UNSUPPORTED, "bp_begin: needs a single-determinant trial");
     return bp_open(wk, nbp, static_cast<cudaStream_t>(stream));
 }
 

@@ -1134,6 +1134,94 @@ __global__ void hprime_reduce_c_kernel(const double* h, const cplx* parts, int n
     hp[id] = cplx{h[id] - 0.5 * acc.re, -0.5 * acc.im};
 }
 
+__device__ __forceinline__ cplx clog(cplx z) { return cplx{log(hypot(z.re, z.im)), atan2(z.im, z.re)}; }
+__device__ __forceinline__ cplx cexp(cplx z) {
+    const double r = exp(z.re);
+    return cplx{r * cos(z.im), r * sin(z.im)};
+}
+__device__ __forceinline__ bool usable(cplx c, cplx l) {
+    return (c.re != 0.0 || c.im != 0.0) && isfinite(l.re) && isfinite(l.im);
+}
+
+__global__ void __launch_bounds__(kThreads) msd_combine_kernel(MsdArgs a) {
+    __shared__ cplx u[kMaxDets];
+    __shared__ cplx sh[kThreads];
+    const int w = blockIdx.x;
+    if (w == 0 && threadIdx.x == 0 && a.inv_flags && (*a.inv_flags & FLAG_NONFINITE))
+        atomicOr(a.flags, FLAG_NONFINITE);
+    if (threadIdx.x == 0) {
+        double m = -INFINITY;
+        for (int I = 0; I < a.ND; ++I) {
+            const cplx l = a.ls[(int64_t)I * a.ldw + w];
+            if (usable(a.cc[I], l)) m = fmax(m, (clog(a.cc[I]) + l).re);
+        }
+        cplx Z{0.0, 0.0};
+        for (int I = 0; I < a.ND; ++I) {
+            const cplx l = a.ls[(int64_t)I * a.ldw + w];
+            u[I] = usable(a.cc[I], l) ? cexp(clog(a.cc[I]) + l - cplx{m, 0.0}) : cplx{0.0, 0.0};
+            Z = Z + u[I];
+        }
+        if (Z.re == 0.0 && Z.im == 0.0) {
+            atomicOr(a.flags, FLAG_SINGULAR);
+            a.logS[w] = cplx{-INFINITY, 0.0};
+        } else {
+            const cplx lz = clog(Z);
+            a.logS[w] = cplx{m + lz.re, lz.im};
+            for (int I = 0; I < a.ND; ++I) u[I] = cdiv(u[I], Z);
+        }
+    }
+    __syncthreads();
+    if (a.E) {
+        cplx e{0.0, 0.0};
+        for (int I = threadIdx.x; I < a.ND; I += kThreads)
+            if (u[I].re != 0.0 || u[I].im != 0.0) e = e + u[I] * a.E[(int64_t)I * a.ldw + w];
+        e = block_sum(e, sh);
+        if (threadIdx.x == 0) {
+            a.E_L[w] = e;
+            if (!finite_c(e)) atomicOr(a.flags, FLAG_NONFINITE);
+        }
+    }
+    if (a.t) {
+        const double sq = sqrt(a.tau);
+        for (int n = threadIdx.x; n < a.Nchol; n += kThreads) {
+            cplx ts{0.0, 0.0};
+            for (int I = 0; I < a.ND; ++I)
+                if (u[I].re != 0.0 || u[I].im != 0.0) ts = ts + u[I] * a.t[((int64_t)I * a.ldw + w) * a.Nchol + n];
+            cplx xb{sq * ts.im, -sq * ts.re};  // -i sqrt(tau) t
+            if (a.fb_cap > 0.0) {
+                const double mag = hypot(xb.re, xb.im);
+                if (mag > a.fb_cap) xb = (a.fb_cap / mag) * xb;
+            }
+            a.xbar[(int64_t)w * a.Nchol + n] = xb;
+        }
+    }
+}
+
+__global__ void msd_variational_kernel(const cplx* cc, const cplx* E, const cplx* L, int ND, cplx* out) {
+    double m = -INFINITY;
+    for (int I = 0; I < ND; ++I)
+        for (int J = 0; J < ND; ++J) {
+            const cplx l = L[(int64_t)I * ND + J];
+            if (usable(cc[I], l) && (cc[J].re != 0.0 || cc[J].im != 0.0))
+                m = fmax(m, (clog(cc[I]) + clog(conjg(cc[J])) + l).re);
+        }
+    cplx num{0.0, 0.0}, den{0.0, 0.0};
+    for (int I = 0; I < ND; ++I)
+        for (int J = 0; J < ND; ++J) {
+            const cplx l = L[(int64_t)I * ND + J];
+            if (!usable(cc[I], l) || (cc[J].re == 0.0 && cc[J].im == 0.0)) continue;
+            const cplx f = cexp(clog(cc[I]) + clog(conjg(cc[J])) + l - cplx{m, 0.0});
+            num = num + f * E[(int64_t)I * ND + J];
+            den = den + f;
+        }
+    *out = cdiv(num, den);
+}
+
+__global__ void cplx_add_kernel(const cplx* a, const cplx* b, cplx* d, int64_t n) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id < n) d[id] = a[id] + b[id];
+}
+
 __global__ void c2r_scale_kernel(const cplx* s, double* d, int64_t n) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (id < n) d[id] = s[id].re;
@@ -1231,6 +1319,21 @@ void trace_terms(const cplx* T, int nc, int W, int N, int n0, cplx* t_out, cplx*
     dim3 grid(W, nc);
     count_launch();
     trace_kernel<<<grid, kThreads, 0, st>>>(T, W, N, n0, t_out, X_out, ldo);
+}
+
+void msd_combine(const MsdArgs& a, cudaStream_t st) {
+    count_launch();
+    msd_combine_kernel<<<a.W, kThreads, 0, st>>>(a);
+}
+
+void msd_variational_energy(const cplx* cc, const cplx* E, const cplx* logS, int ND, cplx* out, cudaStream_t st) {
+    count_launch();
+    msd_variational_kernel<<<1, 1, 0, st>>>(cc, E, logS, ND, out);
+}
+
+void cplx_add(const cplx* a, const cplx* b, cplx* dst, int64_t n, cudaStream_t st) {
+    count_launch();
+    cplx_add_kernel<<<blocks_for(n), kThreads, 0, st>>>(a, b, dst, n);
 }
 
 void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st) {

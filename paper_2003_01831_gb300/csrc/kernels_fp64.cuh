@@ -73,6 +73,35 @@ void philox_fields_dev(const int64_t* params, uint64_t seed_add, int W, int Ncho
 void hs_coefficients(const double* x, const cplx* xbar, const cplx* weight, int W, int Nchol,
                      cplx* c, unsigned* flags, cudaStream_t st);
 
+// Multi-determinant trial |psi_T> = sum_I c_I |D_I> (Sec. V), ND <= kMaxDets determinants:
+// per walker, <psi_T|Phi> = sum_I conj(c_I) <D_I|Phi> as a log-sum-exp of the determinants'
+// log-overlaps (shifted by the largest real part), u_I = conj(c_I) <D_I|Phi> / <psi_T|Phi>,
+// and, where given, E_L = sum_I u_I E_I and the force bias from t_n = sum_I u_I t_In, capped per
+// component as for one determinant.  Determinants with c_I == 0 or a non-finite log-overlap
+// (an exactly singular overlap) contribute nothing; a walker with no contribution at all has a
+// zero overlap with the trial and sets FLAG_SINGULAR.
+constexpr int kMaxDets = 1024;
+struct MsdArgs {
+    int W, ND, Nchol;  // walkers combined (the first W), determinants, Cholesky vectors
+    int ldw;           // walker stride of the per-determinant arrays (>= W)
+    const cplx* cc;    // conj(c_I) [ND]
+    const cplx* ls;    // log <D_I|Phi_w> [ND][ldw]
+    const cplx* E;     // E_L with trial D_I [ND][ldw], or null
+    const cplx* t;     // sum over spins of t_n with trial D_I [ND][ldw][Nchol], or null
+    double tau, fb_cap;
+    cplx* logS;        // [W]
+    cplx* E_L;         // [W] (with E)
+    cplx* xbar;        // [W][Nchol] (with t)
+    const unsigned* inv_flags;   // status of the per-determinant inverses: NONFINITE is passed on
+    unsigned* flags;
+};
+void msd_combine(const MsdArgs& a, cudaStream_t st);
+// out = <psi_T|H|psi_T> / <psi_T|psi_T> = sum_IJ conj(c_I) c_J S_IJ E_IJ / sum_IJ conj(c_I) c_J S_IJ
+// from E_IJ (E_L of trial D_I at walker D_J) and log S_IJ = log <D_I|D_J>, both [ND][ND].
+void msd_variational_energy(const cplx* cc, const cplx* E, const cplx* logS, int ND, cplx* out, cudaStream_t st);
+// dst = a + b over n complex elements
+void cplx_add(const cplx* a, const cplx* b, cplx* dst, int64_t n, cudaStream_t st);
+
 // Weight update (phaseless or free) and acceptance mask.
 struct WeightArgs {
     int W, Nchol, mode;

@@ -26,11 +26,13 @@ struct TcState;  // tensor-core buffers (kernels_tc.cu)
 
 // Device buffers of the FP64 path.  Walkers, Green's functions and traces are kept per
 // spin; complex arrays are interleaved FP64 pairs.
+// Trial quantities hold one block per determinant of the trial (ND of them), the first at the
+// pointer itself.
 struct Fp64Buffers {
-    cplx* Psi[2] = {nullptr, nullptr};     // [M][N_s]
-    void* Lt[2] = {nullptr, nullptr};      // Psi_s^+ L_n: [Nchol][N_s][M] (double if trial real)
-    void* LtT[2] = {nullptr, nullptr};     // transposed: [Nchol][M][N_s] (force-bias-only path)
-    cplx* ht[2] = {nullptr, nullptr};      // Psi_s^+ h: [N_s][M]
+    cplx* Psi[2] = {nullptr, nullptr};     // [ND][M][N_s]
+    void* Lt[2] = {nullptr, nullptr};      // Psi_s^+ L_n: [ND][Nchol][N_s][M] (double if trial real)
+    void* LtT[2] = {nullptr, nullptr};     // transposed: [ND][Nchol][M][N_s] (force-bias-only path)
+    cplx* ht[2] = {nullptr, nullptr};      // Psi_s^+ h: [ND][N_s][M]
     double* Bh = nullptr;                  // exp(-tau h'/2): [M][M], interleaved complex if cplx_L
     cplx* Phi[2] = {nullptr, nullptr};     // [W][M][N_s]
     cplx* Pnew[2] = {nullptr, nullptr};    // propagated walkers / Taylor accumulator
@@ -44,6 +46,12 @@ struct Fp64Buffers {
     cplx* T = nullptr;                     // trace chunk [nc][W][N][N]
     int nc = 0;
     cplx* A = nullptr;                     // [W][M][M] HS potential
+    // multi-determinant trial (ND > 1): per-determinant results of the current walkers
+    cplx* msd_cc = nullptr;                // conj(c_I): [ND]
+    cplx* msd_ls = nullptr;                // log <D_I|Phi_w>: [ND][W]
+    cplx* msd_E = nullptr;                 // E_L with trial D_I: [ND][W]
+    cplx* msd_t = nullptr;                 // sum_s t_n with trial D_I: [ND][W][Nchol]
+    unsigned* msd_flag = nullptr;          // status of the per-determinant inverses [0], local energies [1]
 };
 
 }  // namespace afqmc
@@ -52,6 +60,7 @@ struct afqmc_walkers {
     afqmc_ham* ham = nullptr;
     int device = 0;
     int M = 0, Nchol = 0, N[2] = {0, 0}, W = 0;
+    int ND = 1;                       // determinants in the trial expansion
     double tau = 0.0;
     afqmc_opts opts{};
     bool trial_real = false;

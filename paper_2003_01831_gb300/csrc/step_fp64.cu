@@ -44,14 +44,14 @@ void overlap(const cplx* Psi, const cplx* Phi, cplx* S, int M, int N, int W, cud
 
 int fp64_alloc(afqmc_walkers* wk) {
     Fp64Buffers& f = wk->f;
-    const int M = wk->M, W = wk->W, nch = wk->Nchol;
+    const int M = wk->M, W = wk->W, nch = wk->Nchol, ND = wk->ND;
     for (int s = 0; s < 2; ++s) {
         const int N = wk->N[s];
         const size_t mn = (size_t)M * N;
-        AFQMC_TRY(dalloc(&f.Psi[s], mn));
-        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.Lt[s]), (size_t)nch * mn));
-        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.LtT[s]), (size_t)nch * mn));
-        AFQMC_TRY(dalloc(&f.ht[s], mn));
+        AFQMC_TRY(dalloc(&f.Psi[s], ND * mn));
+        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.Lt[s]), ND * (size_t)nch * mn));
+        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.LtT[s]), ND * (size_t)nch * mn));
+        AFQMC_TRY(dalloc(&f.ht[s], ND * mn));
         AFQMC_TRY(dalloc(&f.Phi[s], (size_t)W * mn));
         AFQMC_TRY(dalloc(&f.Pnew[s], (size_t)W * mn));
         AFQMC_TRY(dalloc(&f.Pa[s], (size_t)W * mn));
@@ -70,6 +70,13 @@ int fp64_alloc(afqmc_walkers* wk) {
     f.nc = std::min(f.nc, 65535);
     AFQMC_TRY(dalloc(&f.T, (size_t)f.nc * W * Nmax * Nmax));
     AFQMC_TRY(dalloc(&f.A, (size_t)W * M * M));
+    if (ND > 1) {
+        AFQMC_TRY(dalloc(&f.msd_cc, (size_t)ND));
+        AFQMC_TRY(dalloc(&f.msd_ls, (size_t)ND * W));
+        AFQMC_TRY(dalloc(&f.msd_E, (size_t)ND * W));
+        AFQMC_TRY(dalloc(&f.msd_t, (size_t)ND * W * nch));
+        AFQMC_TRY(dalloc(&f.msd_flag, 2));
+    }
     return AFQMC_OK;
 }
 
@@ -81,21 +88,32 @@ void fp64_free(afqmc_walkers* wk) {
         for (void* p : ps)
             if (p) cudaFree(p);
     }
-    if (f.Bh) cudaFree(f.Bh);
-    if (f.T) cudaFree(f.T);
-    if (f.A) cudaFree(f.A);
+    void* more[] = {f.Bh, f.T, f.A, f.msd_cc, f.msd_ls, f.msd_E, f.msd_t, f.msd_flag};
+    for (void* p : more)
+        if (p) cudaFree(p);
     f = Fp64Buffers{};
 }
 
-int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
+namespace {
+
+// Green's function, traces, local energy and force bias at the first W walkers with the
+// trial's determinant I alone: logS -> logS_out, E_L -> E_out, xbar -> wk->xbar.  Status bits
+// of the inverses go to inv_flags, those of the local energy to le_flags.
+void measure_det(afqmc_walkers* wk, int I, bool measure, int W, cplx* logS_out, cplx* E_out,
+                 unsigned* inv_flags, unsigned* le_flags, cudaStream_t st) {
     Fp64Buffers& f = wk->f;
     const int M = wk->M, nch = wk->Nchol;
-    const int W = Wm > 0 ? Wm : wk->W;
-    const bool timed = !stream_capturing(st);
+    const bool timed = !stream_capturing(st) && I == 0;
     for (int s = 0; s < 2; ++s) {
         const int N = wk->N[s];
-        overlap(f.Psi[s], f.Phi[s], f.S[s], M, N, W, st);
-        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], true, wk->flags, st);
+        const int64_t mn = (int64_t)M * N, lt = (int64_t)I * nch * mn;
+        const cplx* Psi = f.Psi[s] + I * mn;
+        const void* Lt = wk->Lt_real ? (const void*)(static_cast<const double*>(f.Lt[s]) + lt)
+                                     : (const void*)(static_cast<const cplx*>(f.Lt[s]) + lt);
+        const void* LtT = wk->Lt_real ? (const void*)(static_cast<const double*>(f.LtT[s]) + lt)
+                                      : (const void*)(static_cast<const cplx*>(f.LtT[s]) + lt);
+        overlap(Psi, f.Phi[s], f.S[s], M, N, W, st);
+        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], true, inv_flags, st);
         {   // Theta_w = Phi_w S_w^-1
             GemmArgs g;
             g.m = M; g.n = N; g.k = N; g.nb1 = W;
@@ -112,8 +130,8 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
                 g.m = N; g.n = N; g.k = M; g.nb1 = nc; g.nb2 = W;
                 g.A.real = wk->Lt_real;
                 g.A.ptr = wk->Lt_real
-                              ? (const void*)(static_cast<const double*>(f.Lt[s]) + (int64_t)n0 * N * M)
-                              : (const void*)(static_cast<const cplx*>(f.Lt[s]) + (int64_t)n0 * N * M);
+                              ? (const void*)(static_cast<const double*>(Lt) + (int64_t)n0 * N * M)
+                              : (const void*)(static_cast<const cplx*>(Lt) + (int64_t)n0 * N * M);
                 g.A.ld = M; g.A.s1 = (int64_t)N * M; g.A.s2 = 0;
                 g.B.ptr = f.Theta[s]; g.B.ld = N; g.B.s1 = 0; g.B.s2 = (int64_t)M * N;
                 g.C = f.T; g.ldc = N; g.sc1 = (int64_t)W * N * N; g.sc2 = (int64_t)N * N;
@@ -125,23 +143,52 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
             GemmArgs g;
             g.m = W; g.n = nch; g.k = M * N;
             g.A.ptr = f.Theta[s]; g.A.op = OP_N; g.A.ld = (int64_t)M * N;
-            g.B.real = wk->Lt_real; g.B.ptr = f.LtT[s]; g.B.op = OP_T; g.B.ld = (int64_t)M * N;
+            g.B.real = wk->Lt_real; g.B.ptr = LtT; g.B.op = OP_T; g.B.ld = (int64_t)M * N;
             g.C = f.t[s]; g.ldc = nch;
             zgemm(g, st);
         }
         if (s == 1 && wk->ev1 && timed) { cudaEventRecord(wk->ev1, st); wk->ev_valid = true; }
     }
-    add_logdet(f.ld[0], f.ld[1], wk->logS_old, W, st);
+    add_logdet(f.ld[0], f.ld[1], logS_out, W, st);
     LocalEnergyArgs a;
     a.W = W; a.M = M; a.Nchol = nch; a.Nup = wk->N[0]; a.Ndn = wk->N[1];
     for (int s = 0; s < 2; ++s) {
-        a.ht[s] = f.ht[s]; a.Theta[s] = f.Theta[s]; a.t[s] = f.t[s];
+        a.ht[s] = f.ht[s] + (int64_t)I * M * wk->N[s]; a.Theta[s] = f.Theta[s]; a.t[s] = f.t[s];
         a.X[s] = measure ? f.X[s] : nullptr;
     }
     a.E0 = wk->ham->E0; a.tau = wk->tau;
     a.fb_cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
-    a.E_L = wk->E_L; a.xbar = wk->xbar; a.flags = wk->flags;
+    a.E_L = E_out; a.xbar = wk->xbar; a.flags = le_flags;
     local_energy_forcebias(a, st);
+}
+
+}  // namespace
+
+int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
+    const int W = Wm > 0 ? Wm : wk->W;
+    if (wk->ND == 1) {
+        measure_det(wk, 0, measure, W, wk->logS_old, wk->E_L, wk->flags, wk->flags, st);
+        return AFQMC_OK;
+    }
+    // multi-determinant trial: every determinant alone, then the overlap-weighted combination.
+    // A determinant with an exactly zero overlap has a non-finite term of weight zero: its
+    // local-energy status goes to a discarded word, and the combination checks the result.
+    Fp64Buffers& f = wk->f;
+    const int nch = wk->Nchol;
+    cudaMemsetAsync(f.msd_flag, 0, sizeof(unsigned), st);
+    for (int I = 0; I < wk->ND; ++I) {
+        measure_det(wk, I, measure, W, f.msd_ls + (int64_t)I * wk->W, f.msd_E + (int64_t)I * wk->W, f.msd_flag,
+                    f.msd_flag + 1, st);
+        cplx_add(f.t[0], f.t[1], f.msd_t + (int64_t)I * wk->W * nch, (int64_t)W * nch, st);
+    }
+    MsdArgs a;
+    a.W = W; a.ND = wk->ND; a.Nchol = nch; a.ldw = wk->W;
+    a.cc = f.msd_cc; a.ls = f.msd_ls; a.E = measure ? f.msd_E : nullptr; a.t = f.msd_t;
+    a.tau = wk->tau;
+    a.fb_cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
+    a.logS = wk->logS_old; a.E_L = wk->E_L; a.xbar = wk->xbar;
+    a.inv_flags = f.msd_flag; a.flags = wk->flags;
+    msd_combine(a, st);
     return AFQMC_OK;
 }
 
@@ -187,10 +234,31 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
         b2.B.ptr = f.Pnew[s]; b2.B.ld = N; b2.B.s1 = mn;
         b2.C = f.Pa[s]; b2.ldc = N; b2.sc1 = mn;
         zgemm(b2, st);
-        overlap(f.Psi[s], f.Pa[s], f.S[s], M, N, W, st);
-        batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, wk->flags, st);
+        if (wk->ND == 1) {
+            overlap(f.Psi[s], f.Pa[s], f.S[s], M, N, W, st);
+            batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, wk->flags, st);
+        }
     }
-    add_logdet(f.ld[0], f.ld[1], wk->logS_new, W, st);
+    if (wk->ND == 1) {
+        add_logdet(f.ld[0], f.ld[1], wk->logS_new, W, st);
+    } else {   // log <psi_T|Phi'> over the determinants
+        cudaMemsetAsync(f.msd_flag, 0, sizeof(unsigned), st);
+        for (int I = 0; I < wk->ND; ++I) {
+            for (int s = 0; s < 2; ++s) {
+                const int N = wk->N[s];
+                overlap(f.Psi[s] + (int64_t)I * M * N, f.Pa[s], f.S[s], M, N, W, st);
+                batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, f.msd_flag, st);
+            }
+            add_logdet(f.ld[0], f.ld[1], f.msd_ls + (int64_t)I * W, W, st);
+        }
+        MsdArgs a;
+        a.W = W; a.ND = wk->ND; a.Nchol = nch; a.ldw = W;
+        a.cc = f.msd_cc; a.ls = f.msd_ls; a.E = nullptr; a.t = nullptr;
+        a.tau = wk->tau; a.fb_cap = 0.0;
+        a.logS = wk->logS_new; a.E_L = nullptr; a.xbar = nullptr;
+        a.inv_flags = f.msd_flag; a.flags = wk->flags;
+        msd_combine(a, st);
+    }
     WeightArgs a;
     a.W = W; a.Nchol = nch; a.mode = wk->opts.weight_mode;
     a.x = x; a.xbar = wk->xbar; a.logS_old = wk->logS_old; a.logS_new = wk->logS_new;

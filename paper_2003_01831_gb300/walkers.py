@@ -14,11 +14,14 @@ from . import api
 
 
 class AFQMC:
-    """Owns an ``afqmc_ham_t`` and an ``afqmc_wk_t``; release with ``close()``."""
+    """Owns an ``afqmc_ham_t`` and an ``afqmc_wk_t``; release with ``close()``.
+
+    With ``coeffs`` (complex [ND]) the trial is the expansion sum_I c_I |D_I>, and Psi_up /
+    Psi_dn hold the determinants ([ND, M, Nup] / [ND, M, Ndn])."""
 
     def __init__(self, h, L, E0, Psi_up, Psi_dn, W, tau, Phi0=None, precision=api.PREC_FP64,
                  k_taylor=6, k_qr=5, fb_cap=1.0, weight_mode=api.WEIGHT_PHASELESS, walker_offset=0, energy_terms=0,
-                 stream=None):
+                 stream=None, coeffs=None):
         h = np.ascontiguousarray(h, dtype=np.float64)
         # complex L: general complex Cholesky vectors, run as their 2 Nchol Hermitian-split
         # vectors (A_0, B_0, A_1, B_1, ...), which is what fields and Nchol refer to
@@ -28,7 +31,7 @@ class AFQMC:
         self.Nchol = L.shape[0] * (2 if self.complex_L else 1)
         self.Psi = [np.ascontiguousarray(Psi_up, dtype=np.complex128),
                     np.ascontiguousarray(Psi_dn, dtype=np.complex128)]
-        self.N = [self.Psi[0].shape[1], self.Psi[1].shape[1]]
+        self.N = [self.Psi[0].shape[-1], self.Psi[1].shape[-1]]
         self.W = int(W)
         self.weight_mode = weight_mode
         self.stream = stream
@@ -50,8 +53,13 @@ class AFQMC:
                 [np.asarray(Phi0[0]).reshape(self.W, -1), np.asarray(Phi0[1]).reshape(self.W, -1)], axis=1),
                 dtype=np.complex128)
         try:
-            self.wk = api.afqmc_init_walkers(self.ham, self.Psi[0], self.Psi[1], self.N[0], self.N[1], self.W,
-                                             phi0, tau, opts, stream)
+            if coeffs is None:
+                self.wk = api.afqmc_init_walkers(self.ham, self.Psi[0], self.Psi[1], self.N[0], self.N[1], self.W,
+                                                 phi0, tau, opts, stream)
+            else:
+                c = np.ascontiguousarray(coeffs, dtype=np.complex128)
+                self.wk = api.afqmc_init_walkers_msd(self.ham, c.size, self.Psi[0], self.Psi[1], c, self.N[0],
+                                                     self.N[1], self.W, phi0, tau, opts, stream)
         except Exception:
             api.afqmc_destroy_hamiltonian(self.ham)
             self.ham = None
