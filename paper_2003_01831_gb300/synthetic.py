@@ -37,6 +37,7 @@ __all__ = [
     "make_trial",
     "make_fields",
     "make_random_walkers",
+    "make_thc",
     "WORKLOADS",
     "workload",
     "uneven_batch",
@@ -133,6 +134,17 @@ def make_random_walkers(M: int, N: int, W: int, seed: int) -> np.ndarray:
     z = rng.standard_normal((W, M, N)) + 1j * rng.standard_normal((W, M, N))
     q, _ = np.linalg.qr(z)
     return np.ascontiguousarray(q)
+
+
+def make_thc(M: int, Nmu: int, rng: np.random.Generator, complex_orbitals: bool = False):
+    """THC factors of Sec. V, Eq. (5): orbital values X [M, Nmu] at Nmu interpolating points,
+    entries ~ N(0, 1/M) (complex: independent real and imaginary parts), and a positive
+    semidefinite kernel Mmat = B B^T [Nmu, Nmu] with B ~ N(0, 0.5 / sqrt(Nmu)); X drawn first."""
+    X = rng.normal(0.0, 1.0 / np.sqrt(M), size=(M, Nmu))
+    if complex_orbitals:
+        X = X + 1j * rng.normal(0.0, 1.0 / np.sqrt(M), size=(M, Nmu))
+    B = rng.normal(0.0, 0.5 / np.sqrt(Nmu), size=(Nmu, Nmu))
+    return X, B @ B.T
 
 
 @dataclass
