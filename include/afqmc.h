@@ -213,6 +213,15 @@ int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, 
  * standard comb, applied between steps. */
 int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream);
 
+/* The comb's selection alone, on any weight vector: w [W] real weights (host or
+ * device; >= 0), xi in [0, 1) -> idx [W] (host or device) the source of every slot,
+ * and *total (host or device, may be NULL) their sum, by the same kernel and rule as
+ * afqmc_population_control.  A population split over processes gathers its weights,
+ * runs this on every rank and moves the selected walkers between ranks.
+ * Synchronises the stream.  Errors: BADARG (null pointer, xi outside [0, 1), weights
+ * not summing to a positive number), SHAPE (W < 1), OOM, CUDA. */
+int afqmc_comb_indices(const double* w, int W, double xi, int* idx, double* total, void* stream);
+
 /* ---- Back-propagated one-body density matrix (Sec. V: the back-propagation
  * estimator for observables that do not commute with H) -----------------------
  * afqmc_bp_begin opens a window of nbp >= 0 steps at the current walkers: it keeps a

@@ -37,7 +37,7 @@ EXPORTED = [
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
     "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
     "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune", "afqmc_population_control",
-    "afqmc_bp_begin", "afqmc_bp_rdm1",
+    "afqmc_bp_begin", "afqmc_bp_rdm1", "afqmc_comb_indices",
 ]
 PAD_AUTO, PAD_ALWAYS = 0, 1
 SEED_STRIDE = 0x9E3779B97F4A7C15   # system s of a batch draws with key seed + s * SEED_STRIDE
@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
         "afqmc_batch_autotune": (i, [vp, i, ctypes.POINTER(d), vp]),
         "afqmc_population_control": (i, [vp, d, vp, vp]),
         "afqmc_bp_begin": (i, [vp, i, vp]),
+        "afqmc_comb_indices": (i, [vp, i, d, vp, vp, vp]),
         "afqmc_bp_rdm1": (i, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -239,6 +240,15 @@ def afqmc_population_control(wk: int, xi: float, idx=None, stream=None):
     """Comb population control with the uniform number xi in [0, 1); idx (int32 [W]) receives
     the source walker of every new walker."""
     _check(lib().afqmc_population_control(wk, float(xi), _ptr(idx), _stream(stream)))
+
+
+def afqmc_comb_indices(w, xi: float, stream=None):
+    """The comb's selection on the real weights w: (idx int32 [W], total)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    idx = np.zeros(w.size, dtype=np.int32)
+    total = np.zeros(1, dtype=np.float64)
+    _check(lib().afqmc_comb_indices(_ptr(w), int(w.size), float(xi), _ptr(idx), _ptr(total), _stream(stream)))
+    return idx, float(total[0])
 
 
 def afqmc_bp_begin(wk: int, nbp: int, stream=None):

@@ -653,6 +653,40 @@ int afqmc_population_control(afqmc_wk_t wk, double xi, int* idx, void* stream) {
     return flags_to_error(fl, "population_control");
 }
 
+int afqmc_comb_indices(const double* w, int W, double xi, int* idx, double* total, void* stream) {
+    if (!w || !idx) return fail(AFQMC_ERR_BADARG, "comb_indices: NULL pointer");
+    if (W < 1) return fail(AFQMC_ERR_SHAPE, "comb_indices: need W >= 1");
+    if (!(xi >= 0.0 && xi < 1.0)) return fail(AFQMC_ERR_BADARG, "comb_indices: xi must lie in [0, 1)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    struct Scratch {
+        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Scratch() {
+            for (void* q : p)
+                if (q) cudaFree(q);
+        }
+    } sc;
+    if (cudaMalloc(&sc.p[0], sizeof(double) * W) != cudaSuccess || cudaMalloc(&sc.p[1], sizeof(cplx) * W) != cudaSuccess ||
+        cudaMalloc(&sc.p[2], sizeof(int) * W) != cudaSuccess || cudaMalloc(&sc.p[3], sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AFQMC_ERR_OOM, "comb_indices: scratch");
+    }
+    double* dw = static_cast<double*>(sc.p[0]);
+    cplx* wc = static_cast<cplx*>(sc.p[1]);
+    int* d_idx = static_cast<int*>(sc.p[2]);
+    double* d_total = static_cast<double*>(sc.p[3]);
+    AFQMC_TRY(copy_in(dw, w, sizeof(double) * W, st));
+    real_to_cplx(dw, wc, W, st);
+    comb_indices(wc, W, xi, d_idx, d_total, st);
+    double tot = 0.0;
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(&tot, d_total, sizeof(double), cudaMemcpyDeviceToHost, st));
+    AFQMC_CUDA_TRY(cudaMemcpyAsync(idx, d_idx, sizeof(int) * W, cudaMemcpyDefault, st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!(tot > 0.0) || !isfinite(tot)) return fail(AFQMC_ERR_BADARG, "comb_indices: weights must sum to a positive number");
+    if (total) AFQMC_TRY(copy_in(total, &tot, sizeof(double), st));
+    AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFQMC_OK;
+}
+
 int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_mix, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "energy: NULL handle");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

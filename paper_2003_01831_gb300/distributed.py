@@ -4,13 +4,20 @@ Walkers are independent once their fields are fixed, so a population of ``W_tota
 is split into consecutive ranges, one per rank, with no exchange on the data path.  Each
 rank's walker set is created with ``walker_offset`` = the global index of its first walker,
 so the Philox fields -- and with them every walker's trajectory -- are exactly those of a
-single run over the whole population.  The only cross-rank quantity is the mixed estimator
-``E_mix = sum_w w E_L / sum_w w``, combined from per-rank partial sums by one all-reduce of
-four doubles per measurement.
+single run over the whole population.  The cross-rank quantities are:
+
+* the mixed estimator ``E_mix = sum_w w E_L / sum_w w``, combined from per-rank partial sums
+  by one all-reduce of four doubles per measurement;
+* population control over the whole population (the comb of ``afqmc_population_control``,
+  which acts within one walker set): the ranks gather every weight, each runs the same comb
+  on the full vector, and the selected walkers move between ranks point to point (each
+  source walker once per destination).  Every rank keeps its walker count, so the slot
+  ranges, and with them the Philox streams, stay those of one process running the whole
+  population and its comb.
 """
 from __future__ import annotations
 
-from typing import Tuple
+from typing import Callable, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -46,3 +53,110 @@ def combine_emix(partial: np.ndarray, group=None) -> complex:
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     s = t.cpu().numpy()
     return complex(s[0], s[1]) / complex(s[2], s[3])
+
+
+def _device_for(group):
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+
+
+def _library_comb(w: np.ndarray, xi: float):
+    from . import api
+    return api.afqmc_comb_indices(w, xi)
+
+
+def comb_across_ranks(w_local: np.ndarray, xi: float, group=None,
+                      comb: Optional[Callable[[np.ndarray, float], Tuple[np.ndarray, float]]] = None):
+    """The comb over the whole population.  Returns (idx [W_total]: the global source walker of
+    every global slot, counts [world]: walkers per rank in rank order, total weight); every
+    rank computes the same.  comb(w, xi) -> (idx, total) selects; by default the library's
+    kernel (afqmc_comb_indices)."""
+    import torch
+    import torch.distributed as dist
+    comb = comb or _library_comb
+    w_local = np.asarray(w_local, dtype=np.float64).real
+    world = dist.get_world_size(group)
+    dev = _device_for(group)
+    n = torch.tensor([w_local.size], dtype=torch.int64, device=dev)
+    ns = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(ns, n, group=group)
+    counts = np.array([int(t.item()) for t in ns])
+    pad = torch.zeros(int(counts.max()), dtype=torch.float64, device=dev)
+    pad[:w_local.size] = torch.from_numpy(w_local).to(dev)
+    parts = [torch.zeros_like(pad) for _ in range(world)]
+    dist.all_gather(parts, pad, group=group)
+    w_all = np.concatenate([p.cpu().numpy()[:c] for p, c in zip(parts, counts)])
+    idx, total = comb(w_all, xi)
+    return np.asarray(idx, dtype=np.int64), counts, float(total)
+
+
+def exchange_walkers(P_local: np.ndarray, idx: np.ndarray, counts: Sequence[int], group=None) -> np.ndarray:
+    """This rank's walkers after the comb: row k is global walker idx[off + k] (off = this
+    rank's first global slot).  P_local [W_r, ...] holds this rank's walkers (any dtype, one
+    row each); rows owned by other ranks arrive by point-to-point messages, each source row
+    once per destination."""
+    import torch
+    import torch.distributed as dist
+    rank = dist.get_rank(group)
+    world = dist.get_world_size(group)
+    dev = _device_for(group)
+    counts = np.asarray(counts, dtype=np.int64)
+    offs = np.concatenate([[0], np.cumsum(counts)])
+    P_local = np.ascontiguousarray(P_local)
+    row_shape = P_local.shape[1:]
+
+    def owner(j):
+        return int(np.searchsorted(offs, j, side="right") - 1)
+
+    def needs(r):   # sorted global indices rank r's slots take from each owner
+        src = idx[offs[r]:offs[r + 1]]
+        out = {}
+        for j in np.unique(src):
+            out.setdefault(owner(int(j)), []).append(int(j))
+        return out
+
+    def pack(rows):
+        a = np.ascontiguousarray(rows)
+        return torch.from_numpy(a.view(np.float64).reshape(-1).copy()).to(dev)
+
+    reqs, incoming = [], {}
+    for r in range(world):           # what this rank sends
+        if r == rank:
+            continue
+        mine = needs(r).get(rank, [])
+        if mine:
+            reqs.append(dist.isend(pack(P_local[np.array(mine) - offs[rank]]), dst=r, group=group))
+    for q, js in needs(rank).items():   # what this rank receives
+        if q == rank:
+            continue
+        buf = torch.zeros(len(js) * P_local[0].nbytes // 8, dtype=torch.float64, device=dev)
+        reqs.append(dist.irecv(buf, src=q, group=group))
+        incoming[q] = (js, buf)
+    for rq in reqs:
+        rq.wait()
+    rows = {}
+    for q, (js, buf) in incoming.items():
+        got = buf.cpu().numpy().view(P_local.dtype).reshape((len(js),) + row_shape)
+        for j, row in zip(js, got):
+            rows[j] = row
+    out = np.empty((int(counts[rank]),) + row_shape, dtype=P_local.dtype)
+    for k, j in enumerate(idx[offs[rank]:offs[rank + 1]]):
+        j = int(j)
+        out[k] = P_local[j - offs[rank]] if owner(j) == rank else rows[j]
+    return out
+
+
+def population_control(g, xi: float, group=None) -> np.ndarray:
+    """Comb population control of a walker population spread over the ranks, one
+    ``walkers.AFQMC`` walker set per rank (phaseless or local-energy weights).  Every new
+    walker gets the weight total / W_total.  Returns the global source of every global slot.
+    A back-propagation window open on a walker set is closed (``set_walkers``)."""
+    Pu, Pd, w, step = g.walkers()
+    W = w.size
+    idx, counts, total = comb_across_ranks(w, xi, group)
+    P = np.concatenate([Pu.reshape(W, -1), Pd.reshape(W, -1)], axis=1)
+    P = exchange_walkers(P, idx, counts, group)
+    n_up = Pu[0].size
+    w_new = np.full(W, total / float(np.sum(counts)))
+    g.set_walkers(P[:, :n_up].reshape(Pu.shape), P[:, n_up:].reshape(Pd.shape), w_new, step)
+    return idx

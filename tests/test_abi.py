@@ -65,6 +65,11 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
     assert mk(h.ctypes.data, Lc.ctypes.data, float("inf"), 4, 2, None, ctypes.byref(out)) == -4
     assert lib.afqmc_step(None, 1, None, 0, 0, None, None) == -1
     assert lib.afqmc_bp_begin(None, 3, None) == -1
+    wv = np.ones(3)
+    iv = np.zeros(3, dtype=np.int32)
+    assert lib.afqmc_comb_indices(None, 3, 0.5, iv.ctypes.data, None, None) == -1
+    assert lib.afqmc_comb_indices(wv.ctypes.data, 0, 0.5, iv.ctypes.data, None, None) == -2
+    assert lib.afqmc_comb_indices(wv.ctypes.data, 3, 1.0, iv.ctypes.data, None, None) == -1
     assert lib.afqmc_bp_rdm1(None, None, None, None) == -1
     assert lib.afqmc_energy(None, None, None, None, None, None) == -1
     assert lib.afqmc_destroy_walkers(None) == -1

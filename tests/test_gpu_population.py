@@ -108,3 +108,51 @@ def test_population_control_rejects_bad_input():
     with AFQMC(h, L, E0, Psi[0], Psi[1], 4, 0.01, weight_mode=api.WEIGHT_FREE) as g:
         with pytest.raises(RuntimeError):
             g.population_control(0.5)                     # complex weights
+
+
+def test_standalone_comb_indices_match_oracle():
+    """afqmc_comb_indices: the same kernel and rule on any weight vector."""
+    rng = np.random.default_rng(9)
+    w = rng.uniform(0.2, 2.0, 37)
+    w[[3, 17]] = 0.0
+    for xi in (0.13, 0.5, 0.91):
+        idx, total = api.afqmc_comb_indices(w, xi)
+        assert np.array_equal(idx, O.comb(w, xi))
+        assert abs(total - np.sum(w)) < 1e-12 * np.sum(w)
+    with pytest.raises(api.AfqmcError) as e:
+        api.afqmc_comb_indices(np.zeros(4), 0.5)
+    assert e.value.code == -1
+
+
+def test_population_wide_comb_on_one_rank_equals_the_walker_set_comb():
+    """distributed.population_control (gathered weights, library comb, walker exchange, then
+    set_walkers) on a one-rank gloo group gives the walkers, weights and trajectory of
+    afqmc_population_control."""
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_2003_01831_gb300 import distributed as D
+    rng = np.random.default_rng(10)
+    M, N, nch, W = 12, 3, 10, 9
+    h, L, E0 = syn.make_hamiltonian(M, nch, rng)
+    Psi = syn.make_trial(h, N, N)
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=0, world_size=1)
+    try:
+        with AFQMC(h, L, E0, Psi[0], Psi[1], W, 0.02) as g1, AFQMC(h, L, E0, Psi[0], Psi[1], W, 0.02) as g2:
+            g1.step(3, seed=4)
+            g2.step(3, seed=4)
+            idx1 = g1.population_control(0.29)
+            idx2 = D.population_control(g2, 0.29)
+            assert np.array_equal(idx1, idx2)
+            a, b = g1.walkers(), g2.walkers()
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+            t1 = g1.step(2, seed=4, measure_every=1)
+            t2 = g2.step(2, seed=4, measure_every=1)
+            assert np.max(np.abs(t1 - t2)) <= 1e-13 * np.max(np.abs(t1))
+    finally:
+        dist.destroy_process_group()
