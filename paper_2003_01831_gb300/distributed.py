@@ -8,6 +8,8 @@ single run over the whole population.  The cross-rank quantities are:
 
 * the mixed estimator ``E_mix = sum_w w E_L / sum_w w``, combined from per-rank partial sums
   by one all-reduce of four doubles per measurement;
+* back-propagated density matrices, from every rank's estimate and weight sum by one
+  all-reduce (``combine_rdm1``);
 * population control over the whole population (the comb of ``afqmc_population_control``,
   which acts within one walker set): the ranks gather every weight, each runs the same comb
   on the full vector, and the selected walkers move between ranks point to point (each
@@ -53,6 +55,23 @@ def combine_emix(partial: np.ndarray, group=None) -> complex:
         dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     s = t.cpu().numpy()
     return complex(s[0], s[1]) / complex(s[2], s[3])
+
+
+def combine_rdm1(G_up: np.ndarray, G_dn: np.ndarray, w_sum: complex, group=None):
+    """Population back-propagated density matrices from every rank's afqmc_bp_rdm1 result
+    (each normalised by its own weights): sum_r W_r G_r / sum_r W_r, with W_r = sum of the
+    rank's end-of-window weights.  One all-reduce of 4 M^2 + 2 doubles."""
+    import torch
+    import torch.distributed as dist
+    M = G_up.shape[0]
+    w_sum = complex(w_sum)
+    buf = np.concatenate([(w_sum * np.asarray(G_up)).ravel(), (w_sum * np.asarray(G_dn)).ravel(), [w_sum]])
+    t = torch.from_numpy(buf.astype(np.complex128).view(np.float64).copy())
+    if dist.is_available() and dist.is_initialized():
+        t = t.to(_device_for(group))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    s = t.cpu().numpy().view(np.complex128)
+    return s[:M * M].reshape(M, M) / s[-1], s[M * M:2 * M * M].reshape(M, M) / s[-1]
 
 
 def _device_for(group):

@@ -11,6 +11,7 @@ import torch.distributed as dist
 import torch.multiprocessing as mp
 
 from oracle import afqmc as O
+from oracle import backprop as BP
 from oracle.philox import philox_fields
 from paper_2003_01831_gb300 import distributed as D
 from paper_2003_01831_gb300 import synthetic as syn
@@ -146,3 +147,50 @@ def test_three_rank_walker_exchange():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == {0: True, 1: True, 2: True}
+
+
+def run_bp_oracle(offset, count):
+    """A back-propagation window of 3 steps after 1, for walkers [offset, offset + count):
+    (G_up, G_dn, sum of the end-of-window weights)."""
+    h, L, E0, Psi = system()
+    ham = O.Hamiltonian(h=h, L=L, E0=E0)
+    p = O.Params(tau=TAU, k_taylor=6, k_qr=2)
+    B = O.half_one_body_propagator(ham, TAU)
+    wk = O.init_walkers(ham, Psi, count)
+    O.step(ham, Psi, B, wk, philox_fields(SEED, 0, W_TOTAL, L.shape[0])[offset:offset + count], p)
+    win = BP.Window(wk.Phi)
+    for t in range(1, 4):
+        O.step(ham, Psi, B, wk, philox_fields(SEED, t, W_TOTAL, L.shape[0])[offset:offset + count], p,
+               record=win.coefs)
+    G = win.estimate(L, Psi, B, wk.w, TAU, 6)
+    return G[0], G[1], np.sum(wk.w)
+
+
+def bp_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        off, cnt = D.shard(W_TOTAL, rank, world)
+        Gu, Gd, ws = run_bp_oracle(off, cnt)
+        out = D.combine_rdm1(Gu, Gd, ws)
+        if rank == 0:
+            q.put(out)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_back_propagated_rdm1_equals_single_process():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=bp_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    Gu, Gd = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    Su, Sd, _ = run_bp_oracle(0, W_TOTAL)
+    assert np.max(np.abs(Gu - Su)) < 1e-12 * np.max(np.abs(Su))
+    assert np.max(np.abs(Gd - Sd)) < 1e-12 * np.max(np.abs(Sd))
