@@ -65,6 +65,13 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
     assert mk(h.ctypes.data, Lc.ctypes.data, float("inf"), 4, 2, None, ctypes.byref(out)) == -4
     assert lib.afqmc_step(None, 1, None, 0, 0, None, None) == -1
     assert lib.afqmc_bp_begin(None, 3, None) == -1
+    D = np.zeros((2, 4, 2), dtype=np.complex128)
+    cf = np.ones(2, dtype=np.complex128)
+    init = lib.afqmc_init_walkers_msd
+    assert init(None, 2, D.ctypes.data, D.ctypes.data, cf.ctypes.data, 2, 2, 3, None, 0.01, None, None,
+                ctypes.byref(out)) == -1                      # no Hamiltonian
+    assert init(None, 2, D.ctypes.data, D.ctypes.data, None, 2, 2, 3, None, 0.01, None, None,
+                ctypes.byref(out)) == -1                      # no coefficients
     wv = np.ones(3)
     iv = np.zeros(3, dtype=np.int32)
     assert lib.afqmc_comb_indices(None, 3, 0.5, iv.ctypes.data, None, None) == -1
