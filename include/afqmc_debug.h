@@ -88,6 +88,15 @@ int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, doubl
  * ones.  Host only. */
 int afqmc_debug_energy_products(afqmc_wk_debug_t wk, double* mean);
 
+/* Failure detection without a fault: one warp waits, by the library's bounded mbarrier wait
+ * (try_wait polled against a clock64 budget) with a budget of limit_cycles SM clock cycles
+ * (1 .. the production bound of 4e9), on a barrier phase that completes only if
+ * release != 0 (one thread arrives first).  *status
+ * receives the status word: FLAG_TIMEOUT (4) when the wait ran out, 0 when it completed;
+ * *ms (may be NULL) the kernel's duration.  The kernel returns either way, so the context
+ * stays usable.  Errors: BADARG (null status, limit out of range), OOM, CUDA. */
+int afqmc_debug_wait_probe(long long limit_cycles, int release, unsigned* status, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

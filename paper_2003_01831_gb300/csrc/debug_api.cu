@@ -18,6 +18,29 @@ __global__ void split_kernel(const double* src, bf16* hi, bf16* lo, int64_t n) {
     if (i < n) tc::split_bf16(src[i], hi[i], lo[i]);
 }
 
+// Failure detection without a fault: one warp waits for a barrier phase that only completes
+// when `release` is set (thread 0 arrives first), by the tensor-core kernels' bounded wait
+// (mbarrier try_wait polled against a clock64 budget) with a budget of `limit` cycles.  A
+// wait that runs out records FLAG_TIMEOUT and the kernel returns.
+__global__ void wait_probe_kernel(long long limit, int release, unsigned* flags) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (release && threadIdx.x == 0) tc::mbar_arrive(&bar);
+    const long long t0 = clock64();
+    bool ok = true;
+    while (!tc::mbar_try_wait(&bar, 0)) {
+        if (clock64() - t0 > limit) {
+            ok = false;
+            break;
+        }
+    }
+    if (!ok) atomicOr(flags, FLAG_TIMEOUT);
+}
+
 struct DevBuf {
     void* p = nullptr;
     ~DevBuf() {
@@ -192,5 +215,30 @@ extern "C" int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energ
     p.grid_cap = grid_cap;
     p.bn_max = bn_max == 0 ? 256 : bn_max;
     p.energy_bk = energy_bk;
+    return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_wait_probe(long long limit_cycles, int release, unsigned* status, float* ms) {
+    if (!status) return fail(AFQMC_ERR_BADARG, "debug_wait_probe: status is NULL");
+    if (limit_cycles < 1 || limit_cycles > tc::kTimeoutCycles)
+        return fail(AFQMC_ERR_BADARG, "debug_wait_probe: limit outside 1 .. the production bound");
+    DevBuf flags;
+    if (cudaMalloc(&flags.p, sizeof(unsigned)) != cudaSuccess) return fail(AFQMC_ERR_OOM, "debug_wait_probe: flags");
+    AFQMC_CUDA_TRY(cudaMemset(flags.p, 0, sizeof(unsigned)));
+    cudaEvent_t e0, e1;
+    AFQMC_CUDA_TRY(cudaEventCreate(&e0));
+    AFQMC_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEventRecord(e0);
+    count_launch();
+    wait_probe_kernel<<<1, 32>>>(limit_cycles, release, static_cast<unsigned*>(flags.p));
+    cudaEventRecord(e1);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("debug_wait_probe: ") + cudaGetErrorString(e));
+    AFQMC_CUDA_TRY(cudaMemcpy(status, flags.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (ms) *ms = t;
     return AFQMC_OK;
 }

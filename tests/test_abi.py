@@ -65,6 +65,11 @@ def test_bad_arguments_are_rejected_without_a_gpu(lib):
     assert mk(h.ctypes.data, Lc.ctypes.data, float("inf"), 4, 2, None, ctypes.byref(out)) == -4
     assert lib.afqmc_step(None, 1, None, 0, 0, None, None) == -1
     assert lib.afqmc_bp_begin(None, 3, None) == -1
+    lib.afqmc_debug_wait_probe.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    st = ctypes.c_uint(0)
+    assert lib.afqmc_debug_wait_probe(1000, 0, None, None) == -1
+    assert lib.afqmc_debug_wait_probe(0, 0, ctypes.byref(st), None) == -1
+    assert lib.afqmc_debug_wait_probe(5_000_000_000, 0, ctypes.byref(st), None) == -1
     D = np.zeros((2, 4, 2), dtype=np.complex128)
     cf = np.ones(2, dtype=np.complex128)
     init = lib.afqmc_init_walkers_msd
