@@ -15,6 +15,10 @@ Modules:
   fock     -- brute-force Fock-space Hamiltonian, FCI and exact propagation on
               tiny systems (used only to pin the other modules).
   philox   -- Philox4x32-10 counter-based generator and Box-Muller fields.
+  backprop -- the back-propagated one-body density matrix of a window of steps.
+  msd      -- multi-determinant trial expansions (orthogonal or non-orthogonal).
+  thc      -- tensor-hypercontraction Hamiltonians: their structured Cholesky form and
+              the direct local energy.
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, brute force or library routines; see the module

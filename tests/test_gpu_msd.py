@@ -88,7 +88,7 @@ def test_msd_weight_modes_from_the_largest_determinant(mode):
     h, L, E0, trial, rng = msd_system(43, M, N, N, nch, 4)
     trial.c[1] = 3.0 + 1.0j
     x = rng.standard_normal((steps, W, nch))
-    wk = run_parity(h, L, E0, trial, W, 0.005, steps, 3, x, mode=mode)
+    run_parity(h, L, E0, trial, W, 0.005, steps, 3, x, mode=mode)
     assert trial.reference() is trial.dets[1]
 
 
