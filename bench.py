@@ -335,6 +335,79 @@ def run_bp(args, rank, world):
     return 0
 
 
+def run_fp64_variant(args, rank, world):
+    """The wider rows on the FP64 path, at the m128 system (M=128, N=32+32, Nchol=640,
+    W=512, tau=0.005, QR/10, energy every step, Philox fields):
+      cplx128 -- general complex Cholesky vectors (complex N(0,1) x 0.5 e^{-n/20} / sqrt(M)),
+                 run as their 1280 Hermitian-split vectors;
+      msd128  -- a 4-determinant non-orthogonal trial (the lowest orbitals of h plus 0.3 x
+                 complex N(0,1) per determinant, complex N(0,1) coefficients).
+    value = walker-steps/s (CUDA events); roofline: the step's algorithmic FP64 flops of the
+    energy contraction (per determinant) over the DFMA pipe's peak at the maximum SM clock."""
+    import torch
+    from paper_2003_01831_gb300 import api, synthetic as syn
+    from paper_2003_01831_gb300.walkers import AFQMC
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    wl = syn.workload("m128", W=args.walkers or 512)
+    rng = wl.rng()
+    h, L, E0 = syn.make_hamiltonian(wl.M, wl.Nchol, rng, decay=wl.decay, band=wl.band, reading=wl.reading)
+    P = syn.make_trial(h, wl.Nup, wl.Ndn)
+    kw, Psi, ND, nv, lt_complex = {}, P, 1, wl.Nchol, False
+    if args.workload == "cplx128":
+        scale = 0.5 * np.exp(-np.arange(wl.Nchol) / wl.decay)[:, None, None] / np.sqrt(wl.M)
+        L = scale * (rng.standard_normal(L.shape) + 1j * rng.standard_normal(L.shape))
+        nv, lt_complex = 2 * wl.Nchol, True
+        desc = f"complex Cholesky vectors (Hermitian split: {nv} vectors)"
+    else:
+        ND = 4
+        crn = lambda *sh: rng.standard_normal(sh) + 1j * rng.standard_normal(sh)
+        Psi = [np.stack([P[s] + 0.3 * crn(wl.M, P[s].shape[1]) for _ in range(ND)]) for s in range(2)]
+        kw["coeffs"] = crn(ND)
+        lt_complex = True
+        desc = f"{ND}-determinant non-orthogonal trial"
+    stream = torch.cuda.current_stream().cuda_stream
+    g = AFQMC(h, L, E0, Psi[0], Psi[1], wl.W, wl.tau, k_qr=wl.k_qr, precision=api.PREC_FP64, stream=stream,
+              walker_offset=rank * wl.W, **kw)
+    seed = 1234
+    for _ in range(args.warmup):
+        g.step(1, None, seed=seed, measure_every=1)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            g.step(1, None, seed=seed, measure_every=1)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    _, kernels_per_step = api.afqmc_last_step_stats(g.wk)
+    g.close()
+    W, M, N = wl.W, wl.M, wl.Nup
+    # T = Ltilde Theta per determinant, spin and vector: N x M x N complex MACs (8 flops), or
+    # real x complex (4 flops) for a real trial and real L
+    alg = ND * 2 * W * nv * N * N * M * (8.0 if lt_complex else 4.0)
+    clocks = clk.summary()
+    peak = 304 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks.get("sm_max_mhz") else None
+    ach = alg / (ms / 1e3) / 1e12
+    line = {"metric": f"walker-steps/sec at M=128, N=32, Nchol=640 with {desc} (FP64 path)",
+            "value": world * W / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"m128 molecule-like system, W={W} walkers/GPU, tau=0.005, QR/10, energy every "
+                                   f"step, {desc}", "l2": "inputs larger than L2",
+                       "parallelism": f"walker replicas x{world}"},
+            "clocks": clocks, "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak if peak else None, "traffic": None,
+                         "kernel": "whole FP64 step (energy-contraction flops / step time)",
+                         "peak_source": "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,6 +425,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     from paper_2003_01831_gb300 import synthetic as syn
+    if args.workload in ("cplx128", "msd128"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
+                              "single-system throughput workload only"}), flush=True)
+            return 0
+        return run_fp64_variant(args, rank, world)
     if args.workload == "bp512":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
