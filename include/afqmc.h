@@ -142,7 +142,9 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
  * with u_I = conj(c_I) <D_I|Phi> / <psi_T|Phi>, E_L = sum_I u_I E_L,I and the force
  * bias uses <L_n> = sum_I u_I <L_n>_I; the weights use <psi_T|Phi> (a log-sum-exp of
  * the determinants' log-overlaps).  E_T is the trial's variational energy
- * sum_IJ conj(c_I) c_J S_IJ E_L,I(D_J) / sum_IJ conj(c_I) c_J S_IJ; without Phi0 the
+ * sum_IJ conj(c_I) c_J S_IJ E_L,I(D_J) / sum_IJ conj(c_I) c_J S_IJ, in which pairs with an
+ * exactly singular overlap (orthogonal determinants) are left out, so it is approximate for
+ * orthogonal CI expansions (E_mix does not depend on E_T); without Phi0 the
  * walkers start at the determinant with the largest |c_I| (lowest index on ties).
  * Each determinant's term is formed as <D_I|Phi> times its own mixed estimate
  * (no fast updates), which needs <D_I|Phi> away from zero: orthogonal CI expansions

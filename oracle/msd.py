@@ -22,7 +22,10 @@ Readings of what the paper leaves open (also listed in the design notes):
     = sum_IJ conj(c_I) c_J S_IJ E_I(D_J) / sum_IJ conj(c_I) c_J S_IJ, with E_I(D_J) the
     mixed local energy of trial D_I at walker D_J; this is where the overlaps S_IJ of a
     non-orthogonal expansion enter.  For one determinant it is the trial's own local energy,
-    as before.
+    as before.  A pair with an exactly singular overlap (S_IJ = 0, as between the determinants
+    of an orthogonal CI expansion) drops out of both sums: its <D_I|H|D_J> would need the
+    Slater-Condon rules, which are not restated, so for such expansions E_T is approximate.
+    E_T enters the hybrid weights as a common factor, so E_mix does not depend on it.
   * Walkers start, unless given, at the determinant with the largest |c_I| (lowest index on
     ties).
   * Log-overlaps are summed over determinants as a complex log-sum-exp shifted by the
@@ -111,7 +114,10 @@ class MSDTrial:
                 w = np.conj(self.c[I]) * self.c[J]
                 if w == 0:
                     continue
-                S = np.exp(sum(O.log_det(O.overlap_matrix(DI[s], DJ[s][None]))[0] for s in range(2)))
+                logS = sum(O.log_det(O.overlap_matrix(DI[s], DJ[s][None]))[0] for s in range(2))
+                if not np.isfinite(logS.real):
+                    continue               # exactly orthogonal pair
+                S = np.exp(logS)
                 E_IJ = O.local_energy(ham, DI, [DJ[0][None], DJ[1][None]])[0][0]
                 num += w * S * E_IJ
                 den += w * S

@@ -107,3 +107,39 @@ def test_phaseless_run_with_an_expansion():
     assert np.all(np.isfinite(np.array(out["E_mix"])))
     assert np.all(out["walkers"].w > 0)
     assert abs(out["E_T"] - tr.variational_energy(ham).real) == 0.0
+
+
+def test_exact_ground_state_expansion_has_zero_variance_local_energy():
+    """Two electrons (one per spin): the FCI ground state is exactly sum_ij C_ij |i up, j dn>, an
+    orthogonal expansion over M^2 determinants.  With it as the trial, H|psi_T> = E|psi_T>, so
+    the mixed local energy equals E_FCI at any walker (generic walkers overlap every
+    determinant); the force-bias traces equal the Fock-space mixed estimates of every L_n.
+    The variational energy skips the exactly orthogonal pairs of such an expansion (the oracle's
+    stated reading), so only its diagonal part is checked here."""
+    rng = np.random.default_rng(12)
+    M, nch = 4, 5
+    h, L, _ = syn.make_hamiltonian(M, nch, rng)
+    ham = O.Hamiltonian(h=h, L=L, E0=0.2)
+    fs = FockSpace(M, 1, 1)
+    H = fs.hamiltonian(h, four_index_from_cholesky(L), ham.E0)
+    e, V = np.linalg.eigh(H)
+    I = np.eye(M)
+    dets, c = [], []
+    for i in range(M):
+        for j in range(M):
+            D = (I[:, [i]], I[:, [j]])
+            dets.append(D)
+            c.append(np.vdot(fs.slater_vector(*D), V[:, 0]))
+    trial = MSDTrial(dets, c)
+    assert np.max(np.abs(fock_vector(fs, trial) - V[:, 0])) < 1e-12
+    Phi = [crandn(rng, 5, M, 1), crandn(rng, 5, M, 1)]
+    E, t = trial.local_energy(ham, Phi)
+    assert np.max(np.abs(E - e[0])) < 1e-10 * abs(e[0])
+    diag = sum(abs(cI) ** 2 * np.vdot(fs.slater_vector(*D), H @ fs.slater_vector(*D)) for cI, D in zip(c, dets))
+    assert abs(trial.variational_energy(ham) - diag / np.sum(np.abs(c) ** 2)) < 1e-12 * abs(e[0])
+    vp = V[:, 0]
+    for w in range(5):
+        vf = fs.slater_vector(Phi[0][w], Phi[1][w])
+        ov = np.vdot(vp, vf)
+        for n in range(nch):
+            assert abs(t[w, n] - np.vdot(vp, fs.one_body_operator(L[n]) @ vf) / ov) < 1e-10
