@@ -121,7 +121,7 @@ class Walkers:
 def hprime(ham: Hamiltonian) -> np.ndarray:
     """h' = h - 1/2 sum_n L_n L_n^dagger (from Eq. (1) with Eq. (3) after normal ordering);
     real for real inputs, Hermitian for complex ones."""
-    hp = ham.h - 0.5 * np.einsum("nik,njk->ij", ham.L, ham.L.conj())
+    hp = ham.h - 0.5 * np.tensordot(ham.L, ham.L.conj(), axes=([0, 2], [0, 2]))   # sum_nk L_nik L*_njk
     return hp.real if np.isrealobj(ham.L) and np.isrealobj(ham.h) else hp
 
 
@@ -170,8 +170,8 @@ def half_rotated_green(Psi: np.ndarray, Phi: np.ndarray) -> np.ndarray:
 
 
 def rotated_cholesky(Psi: np.ndarray, L: np.ndarray) -> np.ndarray:
-    """Ltilde_n = Psi^dagger L_n: [Nchol, N, M]."""
-    return np.einsum("ka,nkl->nal", Psi.conj(), L)
+    """Ltilde_n = Psi^dagger L_n: [Nchol, N, M] (one library matrix product per vector)."""
+    return np.matmul(Psi.conj().T, L)
 
 
 def trace_terms(Lt: np.ndarray, Theta: np.ndarray):
