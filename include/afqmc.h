@@ -52,9 +52,15 @@ extern "C" {
 
 /* ---- options ----------------------------------------------------------- */
 #define AFQMC_PREC_FP64    0  /* every contraction in FP64 (DFMA)                       */
-#define AFQMC_PREC_BF16X3  1  /* contractions on tcgen05 tensor cores, each operand split
-                                 into bf16 hi + lo, three products, FP32 accumulation;
-                                 LU/inverse/log-det, QR and reductions stay FP64        */
+#define AFQMC_PREC_BF16X3  1  /* contractions on tcgen05 tensor cores (kind::f16, FP32
+                                 accumulation) on operands split into row-scaled fp16
+                                 slices whose leading products sum exactly: two slices
+                                 for the Green's function and the energy, three for the
+                                 overlap, the propagation and the QR's Gram matrix and
+                                 R^-1 product (see energy_terms for the energy's split
+                                 products); the overlap inverse and the QR's Cholesky
+                                 factor in float pairs with FP64 pivots, square roots and
+                                 log-determinants; reductions and weights in FP64      */
 
 #define AFQMC_WEIGHT_PHASELESS 0  /* w <- w |I| max(0, cos dtheta)  (hybrid form)        */
 #define AFQMC_WEIGHT_FREE      1  /* free projection: complex weights, no cap, no cos   */
@@ -189,6 +195,20 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
  * E_mix complex scalar sum_w w E_L / sum_w w
  * Any output may be NULL. */
 int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_mix, void* stream);
+
+/* ---- Partial sums of the mixed estimator ------------------------------------
+ * For a population split over processes (each holding consecutive walkers, see
+ * afqmc_opts.walker_offset): E_mix of the whole population is
+ * sum_r S_r / sum_r D_r over the processes r, with this walker set's partial sums
+ *     S = sum_w w_w E_L,w,   D = sum_w w_w
+ * (the numerator and denominator of the estimator's definition above).
+ * sums [nmeas][4] doubles (host or device): (Re S, Im S, Re D, Im D) for each measurement of
+ * the last afqmc_step call, in order, or for the one measurement of the last afqmc_energy
+ * call.  nmeas must equal the number of measurements that call made (BADARG otherwise, and
+ * after a failed call).  Formed on the device by the same FP64 reduction as E_mix; a device
+ * output is written asynchronously on `stream`, so an all-reduce on that stream can follow
+ * without a host round trip. */
+int afqmc_mixed_sums(afqmc_wk_t wk, int nmeas, double* sums, void* stream);
 
 /* ---- Adjoint of the local energy and log-overlap -------------------------
  * For the real loss  ell = sum_w Re(conj(dE_w) E_L,w + conj(dlogS_w) logS_w)
@@ -349,7 +369,10 @@ int afqmc_batch_autotune(afqmc_batch_t b, int reps, double* best_ms, void* strea
  * holds it until the process exits); the call needs W*(Nup^2 + Ndn^2 + 2)*16 + 256 bytes of
  * it and returns AFQMC_ERR_SHAPE beyond that.  No device memory is allocated or freed.
  * The first call on a device looks up that device's scratch address (cudaGetSymbolAddress,
- * with the device current); make that first call before any stream capture.
+ * with the device current); make that first call before any stream capture.  The address is
+ * kept per device together with the id of the context it belongs to; a call made after that
+ * context was reset (cudaDeviceReset, or another library resetting the primary context) looks
+ * the address up again, so make such a call, too, outside stream capture.
  * Every call shares the one scratch array and leaves its contents behind; calls whose device
  * work overlaps (different streams or threads on the same device) race on it, so serialise
  * them.  The call synchronises `stream` to read its status word.

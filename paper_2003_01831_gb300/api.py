@@ -37,7 +37,7 @@ EXPORTED = [
     "afqmc_philox_fields", "afqmc_last_step_stats", "afqmc_last_error", "afqmc_log_overlap_noalloc",
     "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
     "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune", "afqmc_population_control",
-    "afqmc_bp_begin", "afqmc_bp_rdm1", "afqmc_comb_indices",
+    "afqmc_bp_begin", "afqmc_bp_rdm1", "afqmc_comb_indices", "afqmc_mixed_sums",
 ]
 PAD_AUTO, PAD_ALWAYS = 0, 1
 SEED_STRIDE = 0x9E3779B97F4A7C15   # system s of a batch draws with key seed + s * SEED_STRIDE
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "afqmc_destroy_walkers": (i, [vp]),
         "afqmc_step": (i, [vp, i, vp, u64, i, vp, vp]),
         "afqmc_energy": (i, [vp, vp, vp, vp, vp, vp]),
+        "afqmc_mixed_sums": (i, [vp, i, vp, vp]),
         "afqmc_energy_backward": (i, [vp, vp, vp, vp, vp, vp, vp]),
         "afqmc_get_walkers": (i, [vp, vp, vp, ctypes.POINTER(i64), vp]),
         "afqmc_set_walkers": (i, [vp, vp, vp, i64, vp]),
@@ -219,6 +220,12 @@ def afqmc_step(wk: int, nsteps: int, x=None, seed: int = 0, measure_every: int =
 
 def afqmc_energy(wk: int, E_L=None, w=None, logS=None, E_mix=None, stream=None):
     _check(lib().afqmc_energy(wk, _ptr(E_L), _ptr(w), _ptr(logS), _ptr(E_mix), _stream(stream)))
+
+
+def afqmc_mixed_sums(wk: int, nmeas: int, sums, stream=None):
+    """Partial sums (Re, Im of sum w E_L; Re, Im of sum w) of the last call's measurements
+    into sums (float64 [nmeas, 4], host or device)."""
+    _check(lib().afqmc_mixed_sums(wk, int(nmeas), _ptr(sums), _stream(stream)))
 
 
 def afqmc_energy_backward(wk: int, dE=None, dlogS=None, dPsi_up=None, dPsi_dn=None, dL=None, stream=None):

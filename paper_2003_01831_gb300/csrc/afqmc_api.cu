@@ -248,7 +248,7 @@ static void free_walkers(afqmc_walkers* wk) {
     fp64_free(wk);
     tc_free(wk);
     void* ps[] = {wk->weight, wk->logS_old, wk->logS_new, wk->E_L, wk->xbar, wk->coef,
-                  wk->accept, wk->x, wk->emix, wk->flags};
+                  wk->accept, wk->x, wk->emix, wk->esum, wk->flags};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (wk->ev0) cudaEventDestroy(wk->ev0);
@@ -335,6 +335,7 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
     rc = rc ? rc : al((void**)&wk->accept, sizeof(int) * W);
     rc = rc ? rc : al((void**)&wk->x, sizeof(double) * W * nch);
     rc = rc ? rc : al((void**)&wk->emix, sizeof(cplx) * 64);
+    rc = rc ? rc : al((void**)&wk->esum, sizeof(cplx) * 2 * 64);
     rc = rc ? rc : al((void**)&wk->flags, 2 * sizeof(unsigned));
     if (rc) return bail(rc);
     wk->x_cap = 1;
@@ -547,8 +548,10 @@ static int ensure_x(afqmc_walkers* wk, int steps) {
 static int ensure_emix(afqmc_walkers* wk, int n) {
     if (n <= wk->emix_cap) return AFQMC_OK;
     cudaFree(wk->emix);
+    cudaFree(wk->esum);
     wk->emix = nullptr;
-    if (cudaMalloc(&wk->emix, sizeof(cplx) * n) != cudaSuccess) {
+    wk->esum = nullptr;
+    if (cudaMalloc(&wk->emix, sizeof(cplx) * n) != cudaSuccess || cudaMalloc(&wk->esum, sizeof(cplx) * 2 * n) != cudaSuccess) {
         cudaGetLastError();
         wk->emix_cap = 0;
         return fail(AFQMC_ERR_OOM, "step: trace buffer");
@@ -570,6 +573,7 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
     if (!x) AFQMC_TRY(ensure_x(wk, 1));
     const int nmeas = measure_every > 0 ? (nsteps + measure_every - 1) / measure_every : 0;
     AFQMC_TRY(ensure_emix(wk, std::max(nmeas, 1)));
+    wk->nmeas_last = 0;
     const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
     wk->ev_valid = false;
     const long long launches0 = launch_count();
@@ -578,7 +582,9 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
     for (int s = 0; s < nsteps; ++s) {
         const bool meas = measure_every > 0 && s % measure_every == 0;
         AFQMC_TRY(tc ? tc_measure(wk, meas || local, st) : fp64_measure(wk, meas || local, st));
-        if (meas) mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix + s / measure_every, st);
+        if (meas)
+            mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix + s / measure_every, st,
+                         wk->esum + 2 * (s / measure_every));
         const double* xs;
         if (x_dev) {
             xs = x + (int64_t)s * per_step;
@@ -595,6 +601,7 @@ int afqmc_step(afqmc_wk_t wk, int nsteps, const double* x, uint64_t seed, int me
         if (wk->opts.k_qr > 0 && wk->step % wk->opts.k_qr == 0) AFQMC_TRY(tc ? tc_qr(wk, st) : fp64_qr(wk, st));
     }
     wk->kernels_per_step = (int)((launch_count() - launches0) / nsteps);
+    wk->nmeas_last = nmeas;
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("step: launch failed: ") + cudaGetErrorString(le));
     bool sync = false;
@@ -693,7 +700,8 @@ int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_
     const bool tc = wk->opts.precision == AFQMC_PREC_BF16X3;
     if (tc) AFQMC_TRY(tc_sync_walkers_to_fp64(wk, st));
     AFQMC_TRY(tc ? tc_measure(wk, true, st) : fp64_measure(wk, true, st));
-    mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix, st);
+    mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix, st, wk->esum);
+    wk->nmeas_last = 1;
     bool sync = false;
     const int W = wk->W;
     AFQMC_TRY(copy_out(E_L, wk->E_L, sizeof(cplx) * W, st, &sync));
@@ -711,6 +719,18 @@ int afqmc_energy(afqmc_wk_t wk, double* E_L, double* w, double* logS, double* E_
     unsigned fl = 0;
     AFQMC_TRY(read_flags(wk->flags, st, &fl));
     return flags_to_error(fl, "energy");
+}
+
+int afqmc_mixed_sums(afqmc_wk_t wk, int nmeas, double* sums, void* stream) {
+    if (!wk || !sums) return fail(AFQMC_ERR_BADARG, "mixed_sums: NULL handle or pointer");
+    if (nmeas != wk->nmeas_last || nmeas < 1)
+        return fail(AFQMC_ERR_BADARG, "mixed_sums: nmeas must equal the measurements of the last step/energy call (" +
+                                          std::to_string(wk->nmeas_last) + ")");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool sync = false;
+    AFQMC_TRY(copy_out(sums, wk->esum, sizeof(cplx) * 2 * (size_t)nmeas, st, &sync));
+    if (sync) AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFQMC_OK;
 }
 
 int afqmc_get_walkers(afqmc_wk_t wk, double* Phi, double* w, int64_t* step, void* stream) {

@@ -1055,7 +1055,10 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-__global__ void __launch_bounds__(kThreads) emix_kernel(const cplx* weight, const cplx* E_L, int W, cplx* out) {
+// E_mix = sum_w w E_L / sum_w w (fixed-order FP64); with `sums` also the two partial sums, from
+// which processes holding parts of one population combine their E_mix.
+__global__ void __launch_bounds__(kThreads) emix_kernel(const cplx* weight, const cplx* E_L, int W, cplx* out,
+                                                        cplx* sums) {
     __shared__ cplx sh[kThreads];
     cplx num{0.0, 0.0}, den{0.0, 0.0};
     for (int w = threadIdx.x; w < W; w += kThreads) {
@@ -1064,7 +1067,13 @@ __global__ void __launch_bounds__(kThreads) emix_kernel(const cplx* weight, cons
     }
     num = block_sum(num, sh);
     den = block_sum(den, sh);
-    if (threadIdx.x == 0) out[0] = cdiv(num, den);
+    if (threadIdx.x == 0) {
+        out[0] = cdiv(num, den);
+        if (sums) {
+            sums[0] = num;
+            sums[1] = den;
+        }
+    }
 }
 
 __global__ void fill_kernel(cplx* p, int64_t n, cplx v) {
@@ -1425,9 +1434,9 @@ void qr_reorthonormalise(cplx* Phi, int64_t stride, int M, int N, int W, const c
     qr_kernel<<<W, kThreads, sm, st>>>(Phi, stride, M, N, weight);
 }
 
-void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st) {
+void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st, cplx* sums) {
     count_launch();
-    emix_kernel<<<1, kThreads, 0, st>>>(weight, E_L, W, out);
+    emix_kernel<<<1, kThreads, 0, st>>>(weight, E_L, W, out, sums);
 }
 
 void fill_cplx(cplx* p, int64_t n, cplx v, cudaStream_t st) {

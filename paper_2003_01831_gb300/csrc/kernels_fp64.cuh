@@ -135,7 +135,8 @@ void qr_reorthonormalise(cplx* Phi, int64_t stride, int M, int N, int W, const c
                          cudaStream_t st);
 
 // E_mix = sum_w w E_L / sum_w w (single block, fixed order); writes out[0].
-void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st);
+// E_mix into out[0]; if sums is set, also (sum_w w E_L, sum_w w) into sums[0..1]
+void mixed_energy(const cplx* weight, const cplx* E_L, int W, cplx* out, cudaStream_t st, cplx* sums = nullptr);
 
 // small helpers
 void fill_cplx(cplx* p, int64_t n, cplx v, cudaStream_t st);

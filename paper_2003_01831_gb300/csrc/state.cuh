@@ -82,7 +82,9 @@ struct afqmc_walkers {
     double* x = nullptr;              // fields, x_cap steps of [W][Nchol]
     int x_cap = 0;
     afqmc::cplx* emix = nullptr;      // measurement trace, emix_cap entries
+    afqmc::cplx* esum = nullptr;      // their partial sums (sum w E_L, sum w), 2 emix_cap entries
     int emix_cap = 0;
+    int nmeas_last = 0;               // measurements made by the last step / energy call
     unsigned* flags = nullptr;
 
     // back-propagation window (backprop.cu): walkers at its start and the shifted fields

@@ -7,7 +7,9 @@ so the Philox fields -- and with them every walker's trajectory -- are exactly t
 single run over the whole population.  The cross-rank quantities are:
 
 * the mixed estimator ``E_mix = sum_w w E_L / sum_w w``, combined from per-rank partial sums
-  by one all-reduce of four doubles per measurement;
+  by one all-reduce of four doubles per measurement.  On GPUs the library forms the partial
+  sums on the device (``afqmc_mixed_sums``) and the all-reduce runs on the device tensor, so
+  nothing of the estimator is computed in Python;
 * back-propagated density matrices, from every rank's estimate and weight sum by one
   all-reduce (``combine_rdm1``);
 * population control over the whole population (the comb of ``afqmc_population_control``,
@@ -36,25 +38,52 @@ def shard(W_total: int, rank: int, world: int) -> Tuple[int, int]:
 
 
 def partial_sums(w: np.ndarray, E_L: np.ndarray) -> np.ndarray:
-    """[Re, Im] of sum_w w E_L and of sum_w w over this rank's walkers (float64[4])."""
+    """[Re, Im] of sum_w w E_L and of sum_w w over this rank's walkers (float64[4]), from host
+    arrays: the form used where a CPU model of a rank stands in for its GPU (the tests); a
+    GPU walker set gives the same sums on the device through ``device_partial_sums``."""
     w = np.asarray(w)
     num = np.sum(w * np.asarray(E_L))
     den = np.sum(w)
     return np.array([num.real, num.imag, np.real(den), np.imag(den)], dtype=np.float64)
 
 
-def combine_emix(partial: np.ndarray, group=None) -> complex:
+def device_partial_sums(g, nmeas: int = 1):
+    """The partial sums of the last measurement call of a ``walkers.AFQMC`` walker set, as a
+    float64 [nmeas, 4] CUDA tensor written by the library on the walker set's stream."""
+    import torch
+    from . import api
+    t = torch.empty((nmeas, 4), dtype=torch.float64, device="cuda")
+    api.afqmc_mixed_sums(g.wk, nmeas, t, g.stream)
+    return t
+
+
+def allreduce_sums(t, group=None):
+    """Sum partial sums ([..., 4] float64 tensor) over the ranks in place.  Under NCCL a CUDA
+    tensor stays on the device (no host round trip); under gloo the tensor must be on the
+    host."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return t
+
+
+def emix_from_sums(t) -> np.ndarray:
+    """E_mix = S / D for every row (S, D complex from (Re S, Im S, Re D, Im D))."""
+    s = np.asarray(t.cpu().numpy() if hasattr(t, "cpu") else t, dtype=np.float64).reshape(-1, 4)
+    return (s[:, 0] + 1j * s[:, 1]) / (s[:, 2] + 1j * s[:, 3])
+
+
+def combine_emix(partial, group=None) -> complex:
     """All-reduce the partial sums of every rank (torch.distributed, any backend) and
-    return the population's E_mix."""
+    return the population's E_mix.  partial: float64[4] (numpy, or a tensor on the group's
+    device)."""
     import torch
     import torch.distributed as dist
-    t = torch.as_tensor(np.asarray(partial, dtype=np.float64))
+    t = partial if isinstance(partial, torch.Tensor) else torch.as_tensor(np.asarray(partial, dtype=np.float64))
     if dist.is_available() and dist.is_initialized():
-        if dist.get_backend(group) == "nccl":
-            t = t.cuda()
-        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    s = t.cpu().numpy()
-    return complex(s[0], s[1]) / complex(s[2], s[3])
+        t = t.to(_device_for(group))
+        allreduce_sums(t, group)
+    return complex(emix_from_sums(t)[0])
 
 
 def combine_rdm1(G_up: np.ndarray, G_dn: np.ndarray, w_sum: complex, group=None):
@@ -138,21 +167,25 @@ def exchange_walkers(P_local: np.ndarray, idx: np.ndarray, counts: Sequence[int]
         a = np.ascontiguousarray(rows)
         return torch.from_numpy(a.view(np.float64).reshape(-1).copy()).to(dev)
 
-    reqs, incoming = [], {}
+    # every send and receive of this rank goes into one batch_isend_irecv, so a backend whose
+    # point-to-point calls between two ranks share one stream (NCCL) sees them as one group
+    # instead of two blocking sends facing each other
+    ops, incoming = [], {}
     for r in range(world):           # what this rank sends
         if r == rank:
             continue
         mine = needs(r).get(rank, [])
         if mine:
-            reqs.append(dist.isend(pack(P_local[np.array(mine) - offs[rank]]), dst=r, group=group))
+            ops.append(dist.P2POp(dist.isend, pack(P_local[np.array(mine) - offs[rank]]), r, group))
     for q, js in needs(rank).items():   # what this rank receives
         if q == rank:
             continue
         buf = torch.zeros(len(js) * P_local[0].nbytes // 8, dtype=torch.float64, device=dev)
-        reqs.append(dist.irecv(buf, src=q, group=group))
+        ops.append(dist.P2POp(dist.irecv, buf, q, group))
         incoming[q] = (js, buf)
-    for rq in reqs:
-        rq.wait()
+    if ops:
+        for rq in dist.batch_isend_irecv(ops):
+            rq.wait()
     rows = {}
     for q, (js, buf) in incoming.items():
         got = buf.cpu().numpy().view(P_local.dtype).reshape((len(js),) + row_shape)

@@ -1,8 +1,12 @@
-"""Isolated parity of the tcgen05 split-bf16 kernels (diagnostic C ABI, include/afqmc_debug.h).
+"""Isolated parity of the tcgen05 split-operand kernels (diagnostic C ABI, include/afqmc_debug.h).
 
-The reference emulates the operand split exactly (hi = bf16(x), lo = bf16(x - hi), both
-round-to-nearest-even) and forms hi*hi + hi*lo + lo*hi in float64, so the only difference
-left is the fp32 accumulation order inside the tensor cores (bound ~ K * 2^-24)."""
+Two operand splits are covered.  The plain GEMM mode splits each operand into a bf16 pair
+(hi = bf16(x), lo = bf16(x - hi), both round-to-nearest-even) and forms hi*hi + hi*lo + lo*hi.
+The exact mode used by the walker step splits each row into row-scaled fp16 slices (hi an
+integer with row 2-norm <= 2^11, lo = fp16 of the remainder), sums hi*hi exactly in one
+accumulator and the remainder products in a second.  The reference emulates each split
+exactly and forms the same products in float64, so the only difference left is the fp32
+accumulation inside the tensor cores (bound ~ K * 2^-24 of the accumulated magnitude)."""
 import ctypes
 
 import numpy as np
