@@ -11,6 +11,8 @@
 // per-spin log-determinants and a status word.  Every call reuses the same array and leaves
 // its contents behind; calls whose device work overlaps (two streams, or two host threads on
 // the same device) race on it and must be serialised by the caller.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -29,6 +31,33 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};   // context the address belongs to
+
+// Unique id of the calling thread's current context (cuCtxGetId through the runtime's driver
+// entry point), or 0 when it cannot be read.  A device's primary context that was reset
+// (cudaDeviceReset, or another library in the process) comes back with a new id, and the
+// scratch array then lives at a new address.
+unsigned long long current_context_id() {
+    typedef CUresult (*GetCtxFn)(CUcontext*);
+    typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+    static GetCtxFn get_ctx = nullptr;
+    static GetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = reinterpret_cast<GetCtxFn>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(p);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_ctx || !get_id || get_ctx(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // logS[w] = ld0[w] + ld1[w] with the phase wrapped to (-pi, pi]
 __global__ void noalloc_sum_kernel(const cplx* ld0, const cplx* ld1, int W, cplx* out) {
@@ -39,20 +68,23 @@ __global__ void noalloc_sum_kernel(const cplx* ld0, const cplx* ld1, int W, cplx
 }
 
 // Device address of this device's scratch, looked up once per device (with that device
-// current, which is the caller's current device).
+// current, which is the caller's current device), and again if the device's context has
+// changed since (a reset context places the array elsewhere).
 int scratch_for_current_device(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("log_overlap_noalloc: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(AFQMC_ERR_UNSUPPORTED, "log_overlap_noalloc: device index too large");
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return fail(AFQMC_ERR_CUDA, std::string("log_overlap_noalloc: cudaGetSymbolAddress failed: ") +
                                             cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
     return AFQMC_OK;
