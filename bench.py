@@ -158,22 +158,97 @@ def extrapolate(n1, t1, n2, t2, n):
     return max(t1 + b * (n - n1), t2)
 
 
-CPU_SAMPLE = (16, 48)   # Cholesky-vector counts of the two timed truncations
+CPU_SAMPLE = (64, 256)   # Cholesky-vector counts of the reference arm's two timed truncations
+CHECK_W = 4              # walkers of the full-size oracle check (walker 0 is compared)
 
 
-def cpu_baseline(wl):
-    """The oracle as it stands on the host cores, on a bounded sample of the workload."""
+def oracle_config1():
+    """The oracle on the small molecule-like workload in full: M=24, N=5+5, Nchol=120, 16
+    walkers, 50 steps, QR every 5 steps, energy measured every step (caller fields)."""
+    from oracle import afqmc as O
+    from paper_2003_01831_gb300 import synthetic as syn
+    wl = syn.workload("m24")
+    h, L, E0 = syn.make_hamiltonian(wl.M, wl.Nchol, wl.rng(), decay=wl.decay, band=wl.band, reading=wl.reading)
+    Psi = syn.make_trial(h, wl.Nup, wl.Ndn)
+    ham = O.Hamiltonian(h=h, L=L, E0=E0)
+    p = O.Params(tau=wl.tau, k_taylor=6, k_qr=wl.k_qr)
+    B = O.half_one_body_propagator(ham, wl.tau)
+    wk = O.init_walkers(ham, Psi, wl.W)
+    x = syn.make_fields(wl.nsteps, wl.W, wl.Nchol, seed=0)
+    t0 = time.perf_counter()
+    for s in range(wl.nsteps):
+        O.step(ham, Psi, B, wk, x[s], p)
+    t = time.perf_counter() - t0
+    return {"value": wl.W * wl.nsteps / t, "unit": UNIT, "walkers": wl.W, "steps": wl.nsteps, "seconds": t,
+            "extrapolated": False,
+            "workload": "molecule-like M=24, N=5+5, Nchol=120, tau=0.005, QR/5, energy every step, measured in full"}
+
+
+def cpu_baseline(wl, h, L, E0, Psi):
+    """The oracle as it stands, on the host cores: one walker-step of the full-size throughput
+    system (M=512, N=128+128, Nchol=2560), timed directly, beside the small workload run in
+    full.  The same oracle step doubles as a full-size check of the mixed-precision GPU path:
+    a BF16X3 walker set takes one step with the same caller fields, and walker 0's local
+    energy, weight and log-overlap after the step are compared with the oracle's."""
+    import torch
+    from oracle import afqmc as O
+    from paper_2003_01831_gb300 import api, synthetic as syn
+    from paper_2003_01831_gb300.walkers import AFQMC
+    cores = len(os.sched_getaffinity(0))
+    x = syn.make_fields(1, CHECK_W, wl.Nchol, seed=99)
+    stream = torch.cuda.current_stream().cuda_stream
+    with AFQMC(h, L, E0, Psi[0], Psi[1], CHECK_W, wl.tau, k_qr=wl.k_qr, precision=api.PREC_BF16X3,
+               stream=stream) as g:
+        g.step(1, x, measure_every=1)
+        E_gpu, w_gpu, l_gpu, _ = g.energy()
+    ham = O.Hamiltonian(h=h, L=L, E0=E0)
+    p = O.Params(tau=wl.tau, k_taylor=6, k_qr=wl.k_qr)
+    B = O.half_one_body_propagator(ham, wl.tau)
+    wk = O.init_walkers(ham, Psi, 1)
+    t0 = time.perf_counter()
+    O.step(ham, Psi, B, wk, x[0, :1], p)
+    t = time.perf_counter() - t0
+    E_o = O.local_energy(ham, Psi, wk.Phi)[0][0]
+    check = {"walker": 0, "after_steps": 1, "E_L_gpu_mixed": [E_gpu[0].real, E_gpu[0].imag],
+             "E_L_oracle": [E_o.real, E_o.imag], "abs_dE_L_Ha": float(abs(E_gpu[0] - E_o)),
+             "rel_dw": float(abs(w_gpu[0] - wk.w[0]) / abs(wk.w[0])),
+             "abs_dlogS": float(abs(l_gpu[0] - wk.logS[0])), "bar_Ha": 1e-3}
+    return {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": False,
+            "sample": f"one walker-step of the throughput system itself (M={wl.M}, N={wl.Nup}+{wl.Ndn}, "
+                      f"Nchol={wl.Nchol}, energy measured), timed directly: {t:.1f} s; set-up excluded",
+            "config1": oracle_config1(), "full_size_check": check}
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return 0
     cores = len(os.sched_getaffinity(0))
     n1, n2 = CPU_SAMPLE
     a, b = OracleSample(wl, n1), OracleSample(wl, n2)
-    t1 = (a.step() + a.step()) / 2
-    t2 = b.step()
-    t = extrapolate(n1, t1, n2, t2, wl.Nchol)
-    return {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one walker, energy measured every step, on the same system truncated to its first {n1} "
-                      f"Cholesky vectors (2 steps, {t1:.2f} s each) and {n2} (1 step, {t2:.2f} s); the oracle's step "
-                      f"cost is affine in Nchol, extrapolated to Nchol={wl.Nchol}: {t:.1f} s per walker-step; "
-                      f"set-up excluded"}
+    for _ in range(max(args.warmup, 0)):
+        a.step()
+    # every timed step: one oracle walker-step at each truncation; the pair gives the
+    # extrapolated time of one full walker-step
+    pts = [(a.step(), b.step()) for _ in range(args.steps)]
+    per = [extrapolate(n1, t1, n2, t2, wl.Nchol) for t1, t2 in pts]
+    t = float(np.mean(per))
+    v = 1.0 / t
+    t1m, t2m = float(np.mean([p[0] for p in pts])), float(np.mean([p[1] for p in pts]))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t * wl.W, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": True,
+                             "measured_points": [{"Nchol": n1, "s_per_walker_step": t1m},
+                                                 {"Nchol": n2, "s_per_walker_step": t2m}],
+                             "sample": f"each step: one oracle walker-step on the system truncated to its first "
+                                       f"{n1} and {n2} Cholesky vectors, extrapolated (affine in Nchol) to "
+                                       f"Nchol={wl.Nchol}; ms_per_step = that time x {wl.W} walkers (walkers are "
+                                       f"independent, so the walker count scales the time exactly); the full-size "
+                                       f"walker-step itself is timed directly in the default arm's cpu_baseline"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args, wl, rank, world):
@@ -200,6 +275,60 @@ def run_reference(args, wl, rank, world):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def step_floor(wl, bf16_sust, hbm_gbs, sm_max_mhz):
+    """Roofline time of one whole step (every phase at its own bound, summed): the dense
+    contractions -- energy T = Ltilde Theta (8 W Nchol N^2 M), HS potential (4 W M^2 Nchol),
+    Taylor terms (2 spins x K x 8 W M^2 N), the two one-body factors (2 spins x 2 x 4 W M^2 N),
+    overlaps and Green's function (2 spins x (2 x 4 + 8) W M N^2) -- at the sustained tensor
+    peak; the overlap inverse (2W complex N^3 Gauss-Jordan, 8 N^3 flops each) and the QR
+    (2W x (16 M N^2 + 8 N^3) per QR, every k_qr steps) at the FP64 DFMA peak; the bytes
+    that must move (Ltilde pair, L^T slices, walkers in and out) at the copy bandwidth."""
+    W, M, N, nch, K = wl.W, wl.M, wl.Nup, wl.Nchol, 6
+    tensor = (8.0 * W * nch * N * N * M + 4.0 * W * M * M * nch + 2 * K * 8.0 * W * M * M * N
+              + 2 * 2 * 4.0 * W * M * M * N + 2 * 16.0 * W * M * N * N)
+    fp64 = 2 * W * 8.0 * N ** 3 + 2 * W * (16.0 * M * N * N + 8.0 * N ** 3) / max(wl.k_qr, 1)
+    fp64_peak = 304 * 2 * sm_max_mhz * 1e6
+    nbytes = nch * N * M * 4 + 3 * M * M * nch * 2 + 2 * 2 * W * 2 * N * M * 8
+    t = tensor / (bf16_sust * 1e12) + fp64 / fp64_peak + nbytes / (hbm_gbs * 1e9)
+    return 1e3 * t, {"tensor_flops": tensor, "fp64_flops": fp64, "bytes": nbytes}
+
+
+FP64_CMP = (64, 10)     # walkers and steps of the FP64-versus-mixed comparison
+
+
+def fp64_compare(wl, h, L, E0, Psi, seed):
+    """The plain FP64 GPU step against the mixed-precision (BF16X3) step on the same system,
+    walkers and fields: both walker sets start at the trial and draw the same Philox fields
+    (same seed and walker offset), with the energy measured every step and QR every k_qr
+    steps.  Each is timed with CUDA events over the whole run (E_mix written to device
+    memory, so nothing synchronises inside)."""
+    import torch
+    from paper_2003_01831_gb300 import api
+    from paper_2003_01831_gb300.walkers import AFQMC
+    W, steps = FP64_CMP
+    stream = torch.cuda.current_stream().cuda_stream
+    out, traces = {}, {}
+    for name, prec in (("fp64", api.PREC_FP64), ("mixed", api.PREC_BF16X3)):
+        with AFQMC(h, L, E0, Psi[0], Psi[1], W, wl.tau, k_qr=wl.k_qr, precision=prec, stream=stream) as g:
+            tr = torch.zeros(steps, dtype=torch.complex128, device="cuda")
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.afqmc_step(g.wk, steps, None, seed, 1, tr, stream)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            traces[name] = tr.cpu().numpy()
+            out[name] = {"value": W * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps}
+    d = np.abs(traces["fp64"] - traces["mixed"])
+    out.update({"walkers": W, "steps": steps, "fields": f"device Philox, seed {seed}, identical for both",
+                "E_mix_fp64": [float(v) for v in traces["fp64"].real],
+                "max_abs_dE_mix_Ha": float(d.max()), "bar_Ha": 1e-3,
+                "mixed_over_fp64_same_walkers": out["mixed"]["value"] / out["fp64"]["value"]})
+    return out
 
 
 def run_batch(args, rank, world):
@@ -419,6 +548,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--energy-terms", type=int, default=0, choices=[0, 3, 4])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -455,7 +585,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2003_01831_gb300 import api
+    from paper_2003_01831_gb300 import api, distributed
     from paper_2003_01831_gb300.walkers import AFQMC
 
     h, L, E0, Psi = build_system(wl)
@@ -478,15 +608,23 @@ def main():
     # timed region: device-resident inputs (fields drawn on the device)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    # with several ranks every measured step also combines the population's E_mix: the library
+    # writes this rank's partial sums (sum w E_L, sum w) to device memory and NCCL all-reduces
+    # them on the device
+    sums = torch.zeros((args.steps, 4), dtype=torch.float64, device="cuda") if dist is not None else None
     with Clocks(local) as clk:
         torch.cuda.nvtx.range_push("afqmc_timed")
         ev0.record()
-        for _ in range(args.steps):
+        for i in range(args.steps):
             g.step(1, None, seed=seed, measure_every=1)
+            if dist is not None:
+                api.afqmc_mixed_sums(g.wk, 1, sums[i], stream)
+                distributed.allreduce_sums(sums[i])
         ev1.record()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     ms_total = ev0.elapsed_time(ev1)
+    emix_population = distributed.emix_from_sums(sums) if dist is not None else None
     # secondary number: energy measured every 10th step (the other steps contract only the force
     # bias, t_n = Tr(Ltilde_n Theta))
     barrier()
@@ -547,6 +685,13 @@ def main():
                 "frac": ach / bf16_sust, "traffic": energy_traffic() if args.walkers == 0 else None, "kernel": "tc_energy_kernel<128>",
                 "avg_launch_ms": e_avg, "issued_over_algorithmic": issued,
                 "peak_source": f"bf16_tflops_sustained of {src} peaks (kernel timed inside a long step)"}
+    if roof is not None:
+        floor_ms, floor_parts = step_floor(wl, bf16_sust, hbm, clocks.get("sm_max_mhz") or 2070.0)
+        roof["step_frac"] = floor_ms / (ms_total / args.steps)
+        roof["step_floor_ms"] = floor_ms
+        roof["step_floor_parts"] = floor_parts
+        if issued:
+            roof["issued_ceiling_frac"] = 1.0 / issued
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -558,9 +703,15 @@ def main():
             "clocks": clocks, "e2e": e2e, "secondary": secondary,
             "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,
             "roofline": roof}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
+    if emix_population is not None:
+        line["population_E_mix"] = [float(v) for v in emix_population.real]
     g.close()
+    if world == 1 and not args.no_fp64_compare:
+        cmp = fp64_compare(wl, h, L, E0, Psi, seed)
+        cmp["mixed_over_fp64_at_bench_walkers"] = value / cmp["fp64"]["value"]
+        line["fp64_compare"] = cmp
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, h, L, E0, Psi)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
