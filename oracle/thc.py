@@ -21,9 +21,13 @@ positive semidefinite.  Restated from the mathematics:
     and the force bias of the factorised fields is <Lhat_n> = sum_mu U_{mu n} g_mu.
   * The HS potential is sum_n c_n L^n = X^* diag(U c) X^T: O(N_mu M^2) instead of O(Nchol M^2).
 
-Readings: U is taken from the eigendecomposition M = V diag(lambda) V^+ as U = V diag(sqrt(lambda))
-over the eigenvalues above 1e-12 of the largest (M is positive semidefinite; the others are
-dropped), so Nchol <= N_mu.
+Readings: U is the modified (diagonally pivoted) Cholesky factor of M -- the factorisation Sec. V
+applies to the two-electron integrals themselves, here applied to the kernel: step r takes the
+largest remaining diagonal entry p (lowest index on ties), sets column r of U to
+(M[:, p] - U[:, :r] U[p, :r]^T) / sqrt(d_p) and subtracts its square from the remaining diagonal,
+and it stops once the largest remaining diagonal is at most 1e-12 of the largest initial one.
+So U U^+ = M up to that threshold, Nchol <= N_mu, and U is unique for a given pivot order (no
+sign or ordering freedom), which lets independent implementations draw the same fields.
 
 Pins (tests/test_oracle_thc.py): the four-index tensor of Eq. (5) against the one rebuilt from
 the L^n; the direct local energy against the Cholesky-form local energy and Fock-space matrix
@@ -42,10 +46,22 @@ __all__ = ["thc_factor", "cholesky_from_thc", "four_index_thc", "local_energy_th
 
 
 def thc_factor(Mmat: np.ndarray, rtol: float = 1e-12) -> np.ndarray:
-    """U with M = U U^+ (N_mu x Nchol), from the eigenvalues above rtol of the largest."""
-    lam, V = np.linalg.eigh(Mmat)
-    keep = lam > rtol * np.max(lam)
-    return V[:, keep] * np.sqrt(lam[keep])
+    """U with M = U U^+ (N_mu x Nchol): diagonally pivoted Cholesky, stopping once the largest
+    remaining diagonal entry is at most rtol of the largest initial one."""
+    n = Mmat.shape[0]
+    d = np.real(np.diag(Mmat)).astype(np.float64).copy()
+    stop = rtol * np.max(d)
+    cols = []
+    for r in range(n):
+        p = int(np.argmax(d))                       # first index of the maximum
+        if d[p] <= stop:
+            break
+        Ur = np.array(cols).T if cols else np.zeros((n, 0), dtype=Mmat.dtype)
+        col = (Mmat[:, p] - Ur @ np.conj(Ur[p, :])) / np.sqrt(d[p])
+        cols.append(col)
+        d = d - np.abs(col) ** 2
+        d[p] = 0.0
+    return np.array(cols).T if cols else np.zeros((n, 0), dtype=Mmat.dtype)
 
 
 def cholesky_from_thc(X: np.ndarray, Mmat: np.ndarray) -> np.ndarray:

@@ -72,3 +72,29 @@ def test_hs_potential_and_real_orbitals():
     Lr = T.cholesky_from_thc(Xr, Mr)
     assert np.isrealobj(Lr)
     assert np.max(np.abs(Lr - np.swapaxes(Lr, 1, 2))) < 1e-15
+
+
+def test_thc_factor_is_the_diagonally_pivoted_cholesky_factor():
+    """U U^T = M; in the pivot order read off U (the row that stays zero in every later column),
+    U is LAPACK's Cholesky factor of the permuted kernel, and every pivot is the row with the
+    largest remaining diagonal at its step; a kernel of rank 3 stops after three columns."""
+    import scipy.linalg
+    rng = np.random.default_rng(4)
+    _, Mmat = syn.make_thc(6, 10, rng)
+    U = T.thc_factor(Mmat)
+    assert U.shape == (10, 10)
+    assert rel(U @ U.T, Mmat) < 1e-12
+    piv = []
+    for r in range(U.shape[1]):
+        rest = [i for i in range(10) if i not in piv]
+        later = np.max(np.abs(U[rest, r + 1:]), axis=1) if r + 1 < U.shape[1] else np.zeros(len(rest))
+        cand = [i for i, z in zip(rest, later) if z < 1e-12 * np.max(np.abs(U))]
+        assert len(cand) == 1
+        piv.append(cand[0])
+        d = np.array([Mmat[i, i] - np.sum(U[i, :r] ** 2) for i in rest])
+        assert rest[int(np.argmax(d))] == piv[-1]
+    L = scipy.linalg.cholesky(Mmat[np.ix_(piv, piv)], lower=True)
+    assert np.max(np.abs(L - U[piv])) < 1e-12 * np.max(np.abs(L))
+    B = rng.standard_normal((10, 3))
+    U3 = T.thc_factor(B @ B.T)
+    assert U3.shape == (10, 3) and rel(U3 @ U3.T, B @ B.T) < 1e-12
