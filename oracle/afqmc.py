@@ -282,14 +282,14 @@ def init_walkers(ham: Hamiltonian, Psi: Sequence[np.ndarray], W: int,
     """Walkers start at Phi0 (or the trial; a multi-determinant trial's largest-weight
     determinant), w = 1, E_T = the trial's variational energy (for one determinant its own
     local energy)."""
-    multi = hasattr(Psi, "variational_energy")
+    multi = hasattr(Psi, "energy_shift")
     if Phi0 is None:
         ref = Psi.reference() if multi else Psi
         Phi = [np.repeat(np.asarray(p, dtype=np.complex128)[None], W, axis=0) for p in ref]
     else:
         Phi = [np.array(p, dtype=np.complex128) for p in Phi0]
     logS = trial_log_overlap(Psi, Phi)
-    E_T = Psi.variational_energy(ham).real if multi else local_energy(ham, Psi, [p[None] for p in Psi])[0][0].real
+    E_T = Psi.energy_shift(ham).real if multi else local_energy(ham, Psi, [p[None] for p in Psi])[0][0].real
     w = np.ones(W, dtype=np.complex128 if complex_weights else np.float64)
     return Walkers(Phi=Phi, w=w, logS=logS, E_T=E_T)
 

@@ -18,14 +18,16 @@ mathematics:
   single determinants (the oracle's single-determinant functions evaluate each one).
 
 Readings of what the paper leaves open (also listed in the design notes):
-  * E_T is the trial's variational energy <psi_T|H|psi_T> / <psi_T|psi_T>
-    = sum_IJ conj(c_I) c_J S_IJ E_I(D_J) / sum_IJ conj(c_I) c_J S_IJ, with E_I(D_J) the
-    mixed local energy of trial D_I at walker D_J; this is where the overlaps S_IJ of a
-    non-orthogonal expansion enter.  For one determinant it is the trial's own local energy,
-    as before.  A pair with an exactly singular overlap (S_IJ = 0, as between the determinants
-    of an orthogonal CI expansion) drops out of both sums: its <D_I|H|D_J> would need the
-    Slater-Condon rules, which are not restated, so for such expansions E_T is approximate.
-    E_T enters the hybrid weights as a common factor, so E_mix does not depend on it.
+  * E_T is the trial's energy shift sum'_IJ conj(c_I) c_J S_IJ E_I(D_J) / sum'_IJ conj(c_I) c_J S_IJ
+    (primed sums: pairs with a non-singular overlap S_IJ), with E_I(D_J) the mixed local energy
+    of trial D_I at walker D_J; this is where the overlaps S_IJ of a non-orthogonal expansion
+    enter.  Without exactly orthogonal pairs -- one determinant (its own local energy), or a
+    NOMSD expansion -- it is the variational energy <psi_T|H|psi_T> / <psi_T|psi_T>.  A pair with
+    S_IJ = 0 (the determinants of an orthogonal CI expansion) would need the Slater-Condon
+    rules for <D_I|H|D_J>, which are not restated, so for such expansions E_T is a shift, not
+    the variational energy.  With phaseless (hybrid) weights it is a common factor of all
+    weights, so E_mix does not depend on it; with local-energy weights it also centres the
+    clip window E_T +- 2/sqrt(tau) of the energy bound.
   * Walkers start, unless given, at the determinant with the largest |c_I| (lowest index on
     ties).
   * Log-overlaps are summed over determinants as a complex log-sum-exp shifted by the
@@ -36,7 +38,7 @@ Readings of what the paper leaves open (also listed in the design notes):
     excited determinants' terms ill-conditioned; their Sherman-Morrison evaluation relative to
     the reference is not restated here.
 
-Pins (tests/test_oracle_msd.py): overlap, local energy, force bias and variational energy
+Pins (tests/test_oracle_msd.py): overlap, local energy, force bias and energy shift (the variational energy of a NOMSD expansion)
 against Fock-space vectors sum_I c_I |D_I>; one determinant, a repeated determinant and a
 re-gauged expansion (D_I -> D_I R_I, c_I -> c_I / det R_I, the same state) against the single-determinant
 results; a short phaseless run.
@@ -105,8 +107,9 @@ class MSDTrial:
             t = t + u[:, I][:, None] * t_I
         return E, t
 
-    def variational_energy(self, ham: O.Hamiltonian) -> complex:
-        """<psi_T|H|psi_T> / <psi_T|psi_T> through the overlaps S_IJ = <D_I|D_J>."""
+    def energy_shift(self, ham: O.Hamiltonian) -> complex:
+        """E_T through the overlaps S_IJ = <D_I|D_J> over the pairs with S_IJ != 0: the
+        variational energy <psi_T|H|psi_T> / <psi_T|psi_T> when no pair is orthogonal."""
         num = 0.0
         den = 0.0
         for I, DI in enumerate(self.dets):

@@ -1,8 +1,9 @@
 """Pins of the multi-determinant trial oracle (oracle/msd.py; Sec. V: |psi_T> = sum_I c_I |D_I>,
 orthogonal CI or non-orthogonal with <D_I|D_J> = S_IJ).
 
-* Overlap, local energy, force-bias traces and the variational energy (the place where S_IJ
-  enters) against brute-force Fock-space vectors sum_I c_I |D_I>.
+* Overlap, local energy, force-bias traces and the energy shift E_T (the place where S_IJ
+  enters; the variational energy of a non-orthogonal expansion) against brute-force Fock-space
+  vectors sum_I c_I |D_I>.
 * One determinant and a repeated determinant reduce to the single-determinant functions; a
   re-gauged expansion (D_I -> D_I R_I, c_I -> c_I / det R_I: the same state) changes nothing.
 * The phaseless step runs with the expansion, and a one-determinant expansion reproduces the
@@ -50,7 +51,7 @@ def test_mixed_estimates_against_fock_space():
             tref = np.vdot(vp, fs.one_body_operator(ham.L[n]) @ vf) / ov
             assert abs(t[w, n] - tref) < 1e-11 * max(1.0, abs(tref)), (w, n)
     Ev = np.vdot(vp, H @ vp) / np.vdot(vp, vp)
-    assert abs(trial.variational_energy(ham) - Ev) < 1e-11 * abs(Ev)
+    assert abs(trial.energy_shift(ham) - Ev) < 1e-11 * abs(Ev)
     assert abs(Ev.imag) < 1e-12 * abs(Ev)
 
 
@@ -65,7 +66,7 @@ def test_one_and_repeated_determinants_reduce_to_the_single_determinant():
         assert np.max(np.abs(t - t1)) < 1e-12 * np.max(np.abs(t1))
         assert np.max(np.abs(np.exp(tr.log_overlap(Phi) - ld) - cs)) < 1e-12
     E_T = O.local_energy(ham, D, [D[0][None], D[1][None]])[0][0]
-    assert abs(MSDTrial([D], [0.5j]).variational_energy(ham) - E_T) < 1e-12 * abs(E_T)
+    assert abs(MSDTrial([D], [0.5j]).energy_shift(ham) - E_T) < 1e-12 * abs(E_T)
 
 
 def test_regauged_expansion_is_the_same_state():
@@ -82,7 +83,7 @@ def test_regauged_expansion_is_the_same_state():
     assert np.max(np.abs(Eg - E)) < 1e-11 * np.max(np.abs(E))
     assert np.max(np.abs(tg - t)) < 1e-11 * np.max(np.abs(t))
     assert np.max(np.abs(np.exp(g.log_overlap(Phi) - trial.log_overlap(Phi)) - 1)) < 1e-11
-    assert abs(g.variational_energy(ham) - trial.variational_energy(ham)) < 1e-11 * abs(trial.variational_energy(ham))
+    assert abs(g.energy_shift(ham) - trial.energy_shift(ham)) < 1e-11 * abs(trial.energy_shift(ham))
     # negative control: forgetting the determinant factor changes the state
     bad = MSDTrial(dets, trial.c)
     assert np.max(np.abs(bad.local_energy(ham, Phi)[0] - E)) > 1e-6
@@ -106,7 +107,7 @@ def test_phaseless_run_with_an_expansion():
     out = O.run(ham, tr, 4, x, p)
     assert np.all(np.isfinite(np.array(out["E_mix"])))
     assert np.all(out["walkers"].w > 0)
-    assert abs(out["E_T"] - tr.variational_energy(ham).real) == 0.0
+    assert abs(out["E_T"] - tr.energy_shift(ham).real) == 0.0
 
 
 def test_exact_ground_state_expansion_has_zero_variance_local_energy():
@@ -114,8 +115,9 @@ def test_exact_ground_state_expansion_has_zero_variance_local_energy():
     orthogonal expansion over M^2 determinants.  With it as the trial, H|psi_T> = E|psi_T>, so
     the mixed local energy equals E_FCI at any walker (generic walkers overlap every
     determinant); the force-bias traces equal the Fock-space mixed estimates of every L_n.
-    The variational energy skips the exactly orthogonal pairs of such an expansion (the oracle's
-    stated reading), so only its diagonal part is checked here."""
+    The energy shift E_T skips the exactly orthogonal pairs of such an expansion (the oracle's
+    stated reading: it is a shift there, not the variational energy), so only its diagonal part
+    is checked here."""
     rng = np.random.default_rng(12)
     M, nch = 4, 5
     h, L, _ = syn.make_hamiltonian(M, nch, rng)
@@ -136,7 +138,7 @@ def test_exact_ground_state_expansion_has_zero_variance_local_energy():
     E, t = trial.local_energy(ham, Phi)
     assert np.max(np.abs(E - e[0])) < 1e-10 * abs(e[0])
     diag = sum(abs(cI) ** 2 * np.vdot(fs.slater_vector(*D), H @ fs.slater_vector(*D)) for cI, D in zip(c, dets))
-    assert abs(trial.variational_energy(ham) - diag / np.sum(np.abs(c) ** 2)) < 1e-12 * abs(e[0])
+    assert abs(trial.energy_shift(ham) - diag / np.sum(np.abs(c) ** 2)) < 1e-12 * abs(e[0])
     vp = V[:, 0]
     for w in range(5):
         vf = fs.slater_vector(Phi[0][w], Phi[1][w])
