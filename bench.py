@@ -363,8 +363,13 @@ def run_batch(args, rank, world):
     Wtot = sum(d.W for d in dims)
     value = world * Wtot * args.steps / (ms / 1e3)
     _, nk = b.info(0)
-    # algorithmic flops of the energy contraction (the dominant term): 8 W Nchol N^2 M per system
+    # algorithmic flops of the energy contraction (the dominant term): 8 W Nchol N^2 M per system,
+    # and the flops the padded shapes (M', N', Nchol') run
     alg = sum(8.0 * d.W * d.Nchol * d.N * d.N * d.M for d in dims)
+    padded = 0.0
+    for i, d in enumerate(dims):
+        sh_i, _ = b.info(i)
+        padded += 8.0 * d.W * int(sh_i[2]) * int(sh_i[1]) ** 2 * int(sh_i[0])
     _, bf16_sust, _, src = peaks()
     ach = alg / (ms / args.steps / 1e3) / 1e12
     line = {"metric": "walker-steps/sec, 64 uneven systems (M~U{32..256}, N=M/4, Nchol=5M, W~U{32..256})",
@@ -376,7 +381,11 @@ def run_batch(args, rank, world):
                                    "energy every step, padded to tensor-core shapes, one graph launch per step",
                        "l2": "inputs larger than L2", "parallelism": f"walker replicas x{world}",
                        "autotuned": {"graph_branches": int(shape[3]), "gemm_bn_max": int(shape[4]),
-                                     "grid_cap": int(shape[5]), "tuned_ms_per_step": tuned_ms}},
+                                     "grid_cap": int(shape[5]),
+                                     "energy_launch": "one persistent launch over every system" if int(shape[6])
+                                     else "one launch per system", "energy_k_chunk": int(shape[7]),
+                                     "tuned_ms_per_step": tuned_ms},
+                       "padded_energy_flops_over_algorithmic": padded / alg},
             "clocks": clk.summary(), "gpu_launches": int(nk) * args.steps if nk > 0 else None,
             "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s",
                          "frac": ach / bf16_sust, "traffic": None,
@@ -428,6 +437,14 @@ def run_bp(args, rank, world):
     t0 = time.perf_counter()
     api.afqmc_bp_rdm1(g.wk, Gh[0], Gh[1], stream)
     e2e_s = time.perf_counter() - t0
+    # the final estimate alone: a window of no steps (the same overlap, inverse and walker sum)
+    g.bp_begin(0)
+    torch.cuda.synchronize()
+    ev0.record()
+    api.afqmc_bp_rdm1(g.wk, G[0], G[1], stream)
+    ev1.record()
+    torch.cuda.synchronize()
+    est_ms = ev0.elapsed_time(ev1)
     g.close()
     W, nch, Ns = wl.W, wl.Nchol, (wl.Nup, wl.Ndn)
     # algorithmic FP64 flops: per back step the HS potential (complex x real, 4 W M^2 Nchol), K
@@ -436,17 +453,34 @@ def run_bp(args, rank, world):
     back = nbp * (4.0 * W * M * M * nch + sum((8.0 * K + 8.0) * W * M * M * n for n in Ns))
     est = sum(16.0 * W * M * n * n + 8.0 * W * n ** 3 + 8.0 * M * M * W * n for n in Ns)
     clocks = clk.summary()
-    fp64_peak = 304 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks.get("sm_max_mhz") else None
-    ach = (back + est) / (ms / 1e3) / 1e12
+    fp64_peak = 304 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    _, bf16_sust, _, src = peaks()
+    tc_back = prec == api.PREC_BF16X3
+    back_ms = max(ms - est_ms, 1e-6)
+    back_peak = bf16_sust if tc_back else fp64_peak
+    phases = {"back_steps": {"ms": back_ms, "algorithmic_flops": back,
+                             "achieved_tflops": back / (back_ms / 1e3) / 1e12,
+                             "peak": back_peak, "bound": "tensor" if tc_back else "alu (FP64 DFMA)",
+                             "frac": back / (back_ms / 1e3) / 1e12 / back_peak},
+              "final_estimate": {"ms": est_ms, "algorithmic_flops": est,
+                                 "achieved_tflops": est / (est_ms / 1e3) / 1e12, "peak": fp64_peak,
+                                 "bound": "alu (FP64 DFMA)",
+                                 "frac": est / (est_ms / 1e3) / 1e12 / fp64_peak}}
+    dom = "back_steps" if back_ms >= est_ms else "final_estimate"
     # launches: per back step conj + HS GEMM + per spin (B, K Taylor terms, B, QR every k_qr);
     # then per spin overlap, inverse, Theta, two layout passes, walker-sum GEMM, transpose, check
     qr = sum(1 for k in range(nbp) if wl.k_qr > 0 and (k + 1) % wl.k_qr == 0 and k + 1 < nbp)
-    launches = 1 + 2 + nbp * (2 + 2 * (K + 2)) + 2 * qr + 2 * 8
+    if prec == api.PREC_BF16X3:   # layout passes, per back step the three-slice propagation's kernels
+        launches = 1 + 2 + 2 + nbp * (8 + 2 * K) + qr * 6 + 2 + 2 * 8
+    else:
+        launches = 1 + 2 + nbp * (2 + 2 * (K + 2)) + 2 * qr + 2 * 8
     line = {"metric": "back-propagated walker-steps/sec (one-body density matrix of a window at M=512, N=128, "
                       "Nchol=2560)",
             "value": world * W * nbp / (ms / 1e3), "unit": "walker-steps/s", "n_gpus": world, "steps": nbp,
             "warmup": args.warmup, "ms_per_step": ms / nbp, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": "f16 row-scaled splits (3 slices) + f64" if prec == api.PREC_BF16X3 else "f64",
+            "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}; back-propagation window of {nbp} steps, walkers "
                                    f"{'BF16X3' if prec == api.PREC_BF16X3 else 'FP64'}",
                        "l2": "inputs larger than L2 (L 5.4 GB, walkers 1.1 GB per spin)",
@@ -454,11 +488,20 @@ def run_bp(args, rank, world):
             "clocks": clocks, "gpu_launches": launches,
             "e2e": {"value": world * W * nbp / e2e_s, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 2 * 16 * M * M, "per": "one afqmc_bp_rdm1 call, host outputs"},
-            "traces": trace,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                         "frac": ach / fp64_peak if fp64_peak else None, "traffic": None,
-                         "kernel": "afqmc_bp_rdm1 (FP64 zgemm and batched inverse)",
-                         "peak_source": "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock"}}
+            "traces": trace, "phases": phases,
+            # the phase that takes most of the call: back steps (three-slice tcgen05 propagation on
+            # a BF16X3 walker set, zgemm on an FP64 one) or the FP64 final estimate
+            "roofline": {"bound": "tensor" if dom == "back_steps" and tc_back else "alu",
+                         "achieved": phases[dom]["achieved_tflops"], "peak": phases[dom]["peak"],
+                         "unit": "TFLOP/s", "frac": phases[dom]["frac"], "traffic": None,
+                         "kernel": ("afqmc_bp_rdm1 back steps (tcgen05 three-slice propagation, adjoint)"
+                                    if tc_back else "afqmc_bp_rdm1 back steps (FP64 zgemm)")
+                         if dom == "back_steps" else
+                         "afqmc_bp_rdm1 final estimate (FP64 zgemm, batched inverse, split walker sum)",
+                         "phase": dom,
+                         "peak_source": (f"bf16_tflops_sustained of {src} peaks (algorithmic complex flops)"
+                                         if dom == "back_steps" and tc_back else
+                                         "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock")}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -537,6 +580,65 @@ def run_fp64_variant(args, rank, world):
     return 0
 
 
+def run_thc(args, rank, world):
+    """Tensor-hypercontraction Hamiltonian (Sec. V, Eqs. (4)-(6)) on the FP64 path, shaped like the
+    molecule-like throughput system: M=128, N=32+32, N_mu = 8 M = 1024 interpolating points
+    (X ~ N(0, 1/M), kernel B B^T with B ~ N(0, 0.5/sqrt(N_mu))), h molecule-like, W=512,
+    tau=0.005, QR/10, energy measured every step, Philox fields.  value = walker-steps/s (CUDA
+    events); roofline: the step's algorithmic FP64 flops of the contractions through the points
+    (Z = Theta^T X, T = (Psi^+ X)^T Z, X diag(U c) X^T) over the DFMA pipe's peak."""
+    import torch
+    from paper_2003_01831_gb300 import api, synthetic as syn
+    from paper_2003_01831_gb300.walkers import AFQMC
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    M, N, Nmu, W, tau, kqr = 128, 32, 1024, args.walkers or 512, 0.005, 10
+    rng = np.random.default_rng(1006)
+    h, _, E0 = syn.make_hamiltonian(M, 1, rng)
+    X, Mk = syn.make_thc(M, Nmu, rng)
+    Psi = syn.make_trial(h, N, N)
+    stream = torch.cuda.current_stream().cuda_stream
+    g = AFQMC(h, None, E0, Psi[0], Psi[1], W, tau, k_qr=kqr, precision=api.PREC_FP64, stream=stream,
+              walker_offset=rank * W, thc=(X, Mk))
+    nch = g.Nchol
+    seed = 1234
+    for _ in range(args.warmup):
+        g.step(1, None, seed=seed, measure_every=1)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            g.step(1, None, seed=seed, measure_every=1)
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    _, kernels_per_step = api.afqmc_last_step_stats(g.wk)
+    g.close()
+    # per walker and spin: Z (complex x real, 4 N M Nmu), T (4 N Nmu^2); per walker: the HS
+    # potential X diag(d) X^T (complex x real, 4 M^2 Nmu) -- the contractions through the points
+    alg = W * (2 * (4.0 * N * M * Nmu + 4.0 * N * Nmu * Nmu) + 4.0 * M * M * Nmu)
+    clocks = clk.summary()
+    peak = 304 * 2 * clocks["sm_max_mhz"] * 1e6 / 1e12 if clocks.get("sm_max_mhz") else None
+    ach = alg / (ms / 1e3) / 1e12
+    line = {"metric": "walker-steps/sec at M=128, N=32, N_mu=1024 with a THC Hamiltonian (FP64 path)",
+            "value": world * W / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"THC molecule-like system: M={M}, N={N}+{N}, N_mu={Nmu} (rank {nch} "
+                                   f"fields), W={W} walkers/GPU, tau={tau}, QR/{kqr}, energy every step",
+                       "l2": "inputs larger than L2", "parallelism": f"walker replicas x{world}"},
+            "clocks": clocks, "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak if peak else None, "traffic": None,
+                         "kernel": "whole FP64 step (THC contraction flops / step time)",
+                         "peak_source": "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -546,7 +648,9 @@ def main():
     ap.add_argument("--workload", default="m512")
     ap.add_argument("--walkers", type=int, default=0)
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
-    ap.add_argument("--energy-terms", type=int, default=0, choices=[0, 3, 4])
+    ap.add_argument("--energy-terms", type=int, default=0, choices=[0, 1, 3, 4])
+    ap.add_argument("--energy-pair", type=int, default=-1, choices=[-1, 0, 1],
+                    help="energy kernel form: 0 one CTA per tile, 1 CTA pairs, -1 the library default")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
@@ -561,6 +665,12 @@ def main():
                               "single-system throughput workload only"}), flush=True)
             return 0
         return run_fp64_variant(args, rank, world)
+    if args.workload == "thc128":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
+                              "single-system throughput workload only"}), flush=True)
+            return 0
+        return run_thc(args, rank, world)
     if args.workload == "bp512":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
@@ -591,6 +701,9 @@ def main():
     h, L, E0, Psi = build_system(wl)
     prec = api.PREC_BF16X3 if args.precision == "bf16x3" else api.PREC_FP64
     stream = torch.cuda.current_stream().cuda_stream
+    if args.energy_pair >= 0:
+        api.lib().afqmc_debug_set_energy_variant.argtypes = [ctypes.c_int]
+        api._check(api.lib().afqmc_debug_set_energy_variant(args.energy_pair))
     # rank r holds walkers [r W, (r + 1) W) of one population: same seed, offset Philox counter
     g = AFQMC(h, L, E0, Psi[0], Psi[1], wl.W, wl.tau, k_qr=wl.k_qr, precision=prec, stream=stream,
               walker_offset=rank * wl.W, energy_terms=args.energy_terms)
@@ -682,7 +795,9 @@ def main():
     if e_avg:
         ach = alg_flops / (e_avg / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s",
-                "frac": ach / bf16_sust, "traffic": energy_traffic() if args.walkers == 0 else None, "kernel": "tc_energy_kernel<128>",
+                "frac": ach / bf16_sust, "traffic": energy_traffic() if args.walkers == 0 else None,
+                "kernel": "tc_energy_kernel<128> (one CTA per tile)" if args.energy_pair == 0
+                else "tc_energy_pair_kernel<128> (CTA pairs, cta_group::2)",
                 "avg_launch_ms": e_avg, "issued_over_algorithmic": issued,
                 "peak_source": f"bf16_tflops_sustained of {src} peaks (kernel timed inside a long step)"}
     if roof is not None:

@@ -77,10 +77,17 @@ typedef struct afqmc_opts {
     int    walker_offset;/* global index of walker 0 in the Philox counter (>= 0): a
                             population split over processes as consecutive walker
                             ranges draws exactly the fields of the whole population  */
-    int    energy_terms; /* BF16X3 energy contraction: 3 = hi*hi + hi*lo + lo*hi,
-                            4 = + lo*lo for every Cholesky vector, 0 = adaptive
-                            (default): + lo*lo except for the smallest vectors whose
-                            norms ||Ltilde_n||_F add up to at most 1% of the total     */
+    int    energy_terms; /* BF16X3 energy contraction's split products, with the
+                            row-scaled operands y = x / scale, hi = rint(y),
+                            lo = fp16(y - hi):
+                            0 (default) = hi*hi + r*lo + lo*hi, r = fp16(y) of
+                                Ltilde_n: three products whose r carries the leading
+                                part of lo*lo (the accuracy of four);
+                            3 = hi*hi + hi*lo + lo*hi;
+                            4 = + lo*lo for every Cholesky vector;
+                            1 = adaptive: four products except for the smallest
+                                vectors whose norms ||Ltilde_n||_F add up to at most
+                                1% of the total, three for those                     */
     int    reserved[6];  /* must be zero                                           */
 } afqmc_opts;
 
@@ -119,6 +126,36 @@ int afqmc_create_hamiltonian(const double* h, const double* L, double E0, int M,
  * Errors: BADARG (null), SHAPE, NONFINITE (NaN/Inf in h or L), OOM, CUDA. */
 int afqmc_create_hamiltonian_complex(const double* h, const double* L, double E0, int M, int Nchol,
                                      void* stream, afqmc_ham_t* out);
+
+/* ---- Hamiltonian in tensor-hypercontraction form (Sec. V, Eqs. (4)-(6)) ----
+ * h     [M][M]        real symmetric one-body matrix h_ij.
+ * X     [M][Nmu]      real orbital values X_{i mu} = phi_i(r_mu) at Nmu interpolating points
+ *                     (Eq. (4)).
+ * Mk    [Nmu][Nmu]    real symmetric positive semidefinite Coulomb kernel M_{mu nu} between
+ *                     the interpolating vectors (Eq. (6)).
+ * E0    constant energy.
+ * The two-electron tensor is Eq. (5): v_ijkl = sum_{mu nu} X_{i mu} X_{k mu} M_{mu nu}
+ * X_{j nu} X_{l nu}.  The library factors the kernel Mk = U U^T by modified (diagonally
+ * pivoted) Cholesky: each column takes the largest remaining diagonal entry (lowest index on
+ * ties), and the factor stops once that entry is at most 1e-12 of the largest initial one.  Its
+ * rank is the Hamiltonian's Nchol (afqmc_hamiltonian_info): afqmc_step draws, or takes from the
+ * caller, Nchol fields per walker, one per column of U.  The equivalent Cholesky vectors
+ * L^n = X diag(U[:, n]) X^T are never formed: the step contracts through the interpolating
+ * points (per walker and spin: Z = Theta^T X, T = (Psi^+ X)^T Z, the density g_mu = T_mu mu,
+ * exchange sum_{mu nu} M_{mu nu} T_{mu nu} T_{nu mu}, force bias U^T g, HS potential
+ * X diag(U c) X^T), and h' = h - 1/2 X [(X^T X) o (U U^T)] X^T.  Memory: O(M Nmu + Nmu^2).
+ * Only the FP64 path with a single-determinant trial runs it: BF16X3 and multi-determinant
+ * walker sets, afqmc_bp_begin and afqmc_energy_backward return UNSUPPORTED.
+ * Sizes: 1 <= M <= 1024, 1 <= Nmu <= 8192.  The factor runs in one CTA, O(Nmu^3) FP64.
+ * Errors: BADARG (null, a kernel that is not symmetric or has no positive diagonal), SHAPE,
+ * NONFINITE (NaN/Inf in h, X or Mk), OOM, CUDA. */
+int afqmc_create_hamiltonian_thc(const double* h, const double* X, const double* Mk, double E0, int M, int Nmu,
+                                 void* stream, afqmc_ham_t* out);
+
+/* Sizes of a Hamiltonian: M, Nchol (fields per walker: Cholesky vectors, their Hermitian split,
+ * or the rank of a THC kernel's factor) and Nmu (interpolating points of a THC Hamiltonian,
+ * 0 otherwise).  Any output may be NULL.  Errors: BADARG (null handle). */
+int afqmc_hamiltonian_info(afqmc_ham_t ham, int* M, int* Nchol, int* Nmu);
 int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
 
 /* ---- Walker set ---------------------------------------------------------
@@ -147,10 +184,13 @@ int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_
  * Every mixed estimate is the overlap-weighted average of the determinants' own:
  * with u_I = conj(c_I) <D_I|Phi> / <psi_T|Phi>, E_L = sum_I u_I E_L,I and the force
  * bias uses <L_n> = sum_I u_I <L_n>_I; the weights use <psi_T|Phi> (a log-sum-exp of
- * the determinants' log-overlaps).  E_T is the trial's variational energy
- * sum_IJ conj(c_I) c_J S_IJ E_L,I(D_J) / sum_IJ conj(c_I) c_J S_IJ, in which pairs with an
- * exactly singular overlap (orthogonal determinants) are left out, so it is approximate for
- * orthogonal CI expansions (E_mix does not depend on E_T); without Phi0 the
+ * the determinants' log-overlaps).  E_T is the trial's energy shift
+ * sum'_IJ conj(c_I) c_J S_IJ E_L,I(D_J) / sum'_IJ conj(c_I) c_J S_IJ over the pairs with a
+ * non-singular overlap S_IJ: the variational energy of the trial when no pair of determinants
+ * is orthogonal (NOMSD), a shift otherwise (orthogonal CI), since the left-out pairs' <D_I|H|D_J>
+ * would need the Slater-Condon rules.  With phaseless weights E_T is a common factor, so E_mix
+ * does not depend on it; with local-energy weights it also centres the clip window
+ * E_T +- 2/sqrt(tau).  Without Phi0 the
  * walkers start at the determinant with the largest |c_I| (lowest index on ties).
  * Each determinant's term is formed as <D_I|Phi> times its own mixed estimate
  * (no fast updates), which needs <D_I|Phi> away from zero: orthogonal CI expansions
@@ -292,7 +332,10 @@ int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x
  * shape (M, N, Nchol) and walker count -- advanced together.  Every afqmc_batch_step step
  * replays one CUDA graph holding the whole step of every system (one chain of kernels per
  * system; the chains run as parallel graph branches, so small systems fill the GPU
- * together).  The per-system arithmetic is exactly that of afqmc_step.
+ * together).  In a measuring BF16X3 step the energy contractions of all systems -- the
+ * step's dominant cost -- run as one persistent tcgen05 launch over a work list of every
+ * system's tiles, between the systems' Green's functions and the rest of their steps.  The
+ * per-system arithmetic is exactly that of afqmc_step.
  *
  * Systems the tensor-core path cannot tile (BF16X3 with M % 64 != 0, N not 32/64/128 or
  * Nchol % 8 != 0), and every system under AFQMC_PAD_ALWAYS, are padded exactly: extra
@@ -341,14 +384,18 @@ int afqmc_batch_energy(afqmc_batch_t b, int sys, double* E_L, double* w, double*
                        void* stream);
 int afqmc_batch_get_walkers(afqmc_batch_t b, int sys, double* Phi, double* w, int64_t* step, void* stream);
 
-/* shape[6] = {M', N', Nchol' of system sys, graph branches, widest plain-GEMM tile,
- * persistent grid cap (0 = one CTA per SM)}; kernels_per_step = kernels in the measuring
- * step graph (-1 before the first step).  Either output may be NULL. */
+/* shape[8] = {M', N', Nchol' of system sys, graph branches, widest plain-GEMM tile,
+ * persistent grid cap (0 = one CTA per SM), energy launch of a measuring BF16X3 step (1: one
+ * persistent launch over every system's tiles, 0: one launch per system in its branch),
+ * K chunk of that launch (16 or 32)}; kernels_per_step = kernels in the measuring step graph
+ * (-1 before the first step).  Either output may be NULL. */
 int afqmc_batch_info(afqmc_batch_t b, int sys, int* shape, int* kernels_per_step);
 
 /* Autotuner: times the measuring step graph (`reps` replays after one warm-up) for a
  * coordinate search over the graph's branch count (1, 2, 4, ... up to 32), the widest
- * plain-GEMM tile (256 or 128 columns) and the persistent grid size (all SMs, 1/2, 1/4),
+ * plain-GEMM tile (256 or 128 columns), the persistent grid size (all SMs, 1/2, 1/4) and,
+ * for BF16X3, the energy launch (one multi-system launch with K chunks of 32 or 16, or one
+ * launch per system),
  * keeps the fastest and restores the walkers, weights and step counters it advanced.
  * best_ms (may be NULL) = the chosen shape's time per step. */
 int afqmc_batch_autotune(afqmc_batch_t b, int reps, double* best_ms, void* stream);

@@ -26,8 +26,9 @@ extern "C" {
 int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int rows, int cols, int K, int BN,
                            int exact, double* C);
 
-/* The fused energy contraction on its own (row-scaled operands, exact leading product;
- * terms = 3: hi*hi + hi*lo + lo*hi, terms = 4: + lo*lo):
+/* The fused energy contraction on its own (row-scaled operands y = x / scale, hi = rint(y),
+ * lo = fp16(y - hi), exact leading product; terms = 3: hi*hi + hi*lo + lo*hi, terms = 4:
+ * + lo*lo, terms = 5: hi*hi + r*lo + lo*hi with r = fp16(y) of Lt, the library default):
  * for Lt [Nchol][Np][M] (real) and walker-spin
  * Green's functions ThetaT [nws][2][Np][M] (re plane then im plane of Theta^T), returns
  * t [nws][Nchol] = Tr(Lt_n Theta_ws) and X [nws][Nchol] = Tr((Lt_n Theta_ws)^2) as complex
@@ -79,6 +80,19 @@ int afqmc_debug_select_energy_groups(const double* norms, int nch, int G, double
  * Ltilde streams through once per window.  For tuning experiments; results do not depend
  * on it. */
 int afqmc_debug_set_energy_window(int ws_super);
+
+/* Form of the calling process's later fused energy contractions: pair = 1 (the default),
+ * clusters of two CTAs on two SMs, each pair computing two tiles of the same walker-spin group
+ * with MMAs of M = 256 issued by one CTA (cta_group::2), every SM staging half of the
+ * Green's-function rows; pair = 0, one CTA per 128 x 256 tile (kind::f16 MMAs of M = 128).
+ * Results are the same arithmetic in the same order.  Errors: BADARG for other values. */
+int afqmc_debug_set_energy_variant(int pair);
+
+/* Energy launch of a batch's later measuring BF16X3 steps (b: an afqmc_batch_t): multi = 1 one
+ * persistent launch over every system's tiles with K chunks of bk (16 or 32), multi = 0 one
+ * launch per system in its graph branch.  The arithmetic of every tile is the same.  Errors:
+ * BADARG. */
+int afqmc_debug_set_batch_energy(void* b, int multi, int bk);
 int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X,
                             double* E1);
 

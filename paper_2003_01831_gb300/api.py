@@ -38,6 +38,7 @@ EXPORTED = [
     "afqmc_create_batch", "afqmc_destroy_batch", "afqmc_batch_step", "afqmc_batch_energy",
     "afqmc_batch_get_walkers", "afqmc_batch_info", "afqmc_batch_autotune", "afqmc_population_control",
     "afqmc_bp_begin", "afqmc_bp_rdm1", "afqmc_comb_indices", "afqmc_mixed_sums",
+    "afqmc_create_hamiltonian_thc", "afqmc_hamiltonian_info",
 ]
 PAD_AUTO, PAD_ALWAYS = 0, 1
 SEED_STRIDE = 0x9E3779B97F4A7C15   # system s of a batch draws with key seed + s * SEED_STRIDE
@@ -96,6 +97,8 @@ def lib() -> ctypes.CDLL:
         "afqmc_create_hamiltonian": (i, [vp, vp, d, i, i, vp, ctypes.POINTER(vp)]),
         "afqmc_create_hamiltonian_complex": (i, [vp, vp, d, i, i, vp, ctypes.POINTER(vp)]),
         "afqmc_destroy_hamiltonian": (i, [vp]),
+        "afqmc_create_hamiltonian_thc": (i, [vp, vp, vp, d, i, i, vp, ctypes.POINTER(vp)]),
+        "afqmc_hamiltonian_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "afqmc_init_walkers": (i, [vp, vp, vp, i, i, i, vp, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]),
         "afqmc_init_walkers_msd": (i, [vp, i, vp, vp, vp, i, i, i, vp, d, ctypes.POINTER(Opts), vp,
                                        ctypes.POINTER(vp)]),
@@ -183,6 +186,21 @@ def afqmc_create_hamiltonian_complex(h, L, E0: float, M: int, Nchol: int, stream
     _check(lib().afqmc_create_hamiltonian_complex(_ptr(h), _ptr(L), float(E0), int(M), int(Nchol),
                                                   _stream(stream), ctypes.byref(out)))
     return out.value
+
+
+def afqmc_create_hamiltonian_thc(h, X, Mk, E0: float, M: int, Nmu: int, stream=None) -> int:
+    """THC Hamiltonian (Eq. (5)): real orbital values X [M, Nmu] and kernel Mk [Nmu, Nmu]."""
+    out = ctypes.c_void_p()
+    _check(lib().afqmc_create_hamiltonian_thc(_ptr(h), _ptr(X), _ptr(Mk), float(E0), int(M), int(Nmu),
+                                              _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def afqmc_hamiltonian_info(ham: int):
+    """(M, Nchol, Nmu) of a Hamiltonian."""
+    m, n, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().afqmc_hamiltonian_info(ham, ctypes.byref(m), ctypes.byref(n), ctypes.byref(q)))
+    return m.value, n.value, q.value
 
 
 def afqmc_destroy_hamiltonian(ham: int):
@@ -317,7 +335,7 @@ def afqmc_batch_get_walkers(b: int, sys: int, Phi=None, w=None, stream=None) -> 
 
 
 def afqmc_batch_info(b: int, sys: int):
-    shape = np.zeros(6, dtype=np.int32)
+    shape = np.zeros(8, dtype=np.int32)
     k = ctypes.c_int()
     _check(lib().afqmc_batch_info(b, int(sys), _ptr(shape), ctypes.byref(k)))
     return shape, k.value

@@ -232,12 +232,124 @@ int afqmc_create_hamiltonian_complex(const double* h, const double* L, double E0
     return AFQMC_OK;
 }
 
+int afqmc_create_hamiltonian_thc(const double* h, const double* X, const double* Mk, double E0, int M, int Nmu,
+                                 void* stream, afqmc_ham_t* out) {
+    if (!out) return fail(AFQMC_ERR_BADARG, "create_hamiltonian_thc: out is NULL");
+    *out = nullptr;
+    if (!h || !X || !Mk) return fail(AFQMC_ERR_BADARG, "create_hamiltonian_thc: h, X or Mk is NULL");
+    if (M < 1 || M > 1024 || Nmu < 1 || Nmu > 8192)
+        return fail(AFQMC_ERR_SHAPE, "create_hamiltonian_thc: need 1 <= M <= 1024, 1 <= Nmu <= 8192");
+    if (!isfinite(E0)) return fail(AFQMC_ERR_NONFINITE, "create_hamiltonian_thc: E0 not finite");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    afqmc_ham* H = new afqmc_ham();
+    AFQMC_CUDA_TRY(cudaGetDevice(&H->device));
+    H->M = M;
+    H->E0 = E0;
+    H->Nmu = Nmu;
+    const size_t mm = (size_t)M * M, mq = (size_t)M * Nmu, qq = (size_t)Nmu * Nmu;
+    double* work = nullptr;   // factor scratch, then real Nmu x Nmu products
+    cplx* cw = nullptr;       // complex GEMM outputs (Nmu x Nmu, then M x Nmu and M x M)
+    auto cleanup = [&](int rc) {
+        void* ps[] = {H->h, H->hp, H->X, H->Mk, H->U, H->flags, work, cw};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+        delete H;
+        return rc;
+    };
+    if (cudaMalloc(&H->h, mm * sizeof(double)) != cudaSuccess || cudaMalloc(&H->hp, mm * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&H->X, mq * sizeof(double)) != cudaSuccess || cudaMalloc(&H->Mk, qq * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&H->U, qq * sizeof(double)) != cudaSuccess || cudaMalloc(&H->flags, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&work, (qq + 3 * (size_t)Nmu) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&cw, std::max(qq, std::max(mq, mm)) * sizeof(cplx)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(AFQMC_ERR_OOM, "create_hamiltonian_thc: device allocation failed"));
+    }
+    int rc = copy_in(H->h, h, mm * sizeof(double), st);
+    if (rc == AFQMC_OK) rc = copy_in(H->X, X, mq * sizeof(double), st);
+    if (rc == AFQMC_OK) rc = copy_in(H->Mk, Mk, qq * sizeof(double), st);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    cudaMemsetAsync(H->flags, 0, sizeof(unsigned), st);
+    check_finite(H->h, (int64_t)mm, H->flags, st);
+    check_finite(H->X, (int64_t)mq, H->flags, st);
+    check_finite(H->Mk, (int64_t)qq, H->flags, st);
+    check_symmetric(H->Mk, Nmu, 1, H->flags, st);
+    unsigned f = 0;
+    rc = read_flags(H->flags, st, &f);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    if (f & FLAG_NONFINITE) return cleanup(fail(AFQMC_ERR_NONFINITE, "create_hamiltonian_thc: NaN/Inf in h, X or Mk"));
+    if (f & 8u) return cleanup(fail(AFQMC_ERR_BADARG, "create_hamiltonian_thc: the kernel Mk must be symmetric"));
+    // M = U U^T: the modified (diagonally pivoted) Cholesky of the kernel
+    int rank = 0;
+    rc = thc_pivoted_cholesky(H->Mk, Nmu, 1e-12, work, H->U, &rank, st);
+    if (rc != AFQMC_OK) return cleanup(rc);
+    if (rank < 1) return cleanup(fail(AFQMC_ERR_BADARG, "create_hamiltonian_thc: the kernel has no positive direction"));
+    H->Nchol = rank;
+    // h' = h - 1/2 X [(X^T X) o (U U^T)] X^T
+    double* P = work;   // [Nmu][Nmu] real
+    {
+        GemmArgs g;   // cw = U U^T
+        g.m = Nmu; g.n = Nmu; g.k = rank;
+        g.A.ptr = H->U; g.A.real = true; g.A.ld = rank;
+        g.B.ptr = H->U; g.B.real = true; g.B.op = OP_T; g.B.ld = rank;
+        g.C = cw; g.ldc = Nmu;
+        zgemm(g, st);
+        real_part(cw, P, (int64_t)qq, st);                // P = U U^T
+        GemmArgs x;   // cw = X^T X
+        x.m = Nmu; x.n = Nmu; x.k = M;
+        x.A.ptr = H->X; x.A.real = true; x.A.op = OP_T; x.A.ld = Nmu;
+        x.B.ptr = H->X; x.B.real = true; x.B.ld = Nmu;
+        x.C = cw; x.ldc = Nmu;
+        zgemm(x, st);
+        real_part_times(cw, P, P, (int64_t)qq, st);       // P = (X^T X) o (U U^T)
+        GemmArgs g1;   // cw = X P   [M][Nmu]
+        g1.m = M; g1.n = Nmu; g1.k = Nmu;
+        g1.A.ptr = H->X; g1.A.real = true; g1.A.ld = Nmu;
+        g1.B.ptr = P; g1.B.real = true; g1.B.ld = Nmu;
+        g1.C = cw; g1.ldc = Nmu;
+        zgemm(g1, st);
+    }
+    cplx* R = nullptr;
+    if (cudaMallocAsync(&R, mm * sizeof(cplx), st) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(AFQMC_ERR_OOM, "create_hamiltonian_thc: workspace"));
+    }
+    {
+        GemmArgs g2;   // R = (X P) X^T   [M][M]
+        g2.m = M; g2.n = M; g2.k = Nmu;
+        g2.A.ptr = cw; g2.A.ld = Nmu;
+        g2.B.ptr = H->X; g2.B.real = true; g2.B.op = OP_T; g2.B.ld = Nmu;
+        g2.C = R; g2.ldc = M;
+        zgemm(g2, st);
+    }
+    hprime_from(H->h, R, H->hp, (int64_t)mm, st);
+    cudaFreeAsync(R, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(work);
+    cudaFree(cw);
+    work = nullptr;
+    cw = nullptr;
+    if (e != cudaSuccess) return cleanup(fail(AFQMC_ERR_CUDA, std::string("create_hamiltonian_thc: ") + cudaGetErrorString(e)));
+    *out = H;
+    return AFQMC_OK;
+}
+
+int afqmc_hamiltonian_info(afqmc_ham_t H, int* M, int* Nchol, int* Nmu) {
+    if (!H) return fail(AFQMC_ERR_BADARG, "hamiltonian_info: NULL handle");
+    if (M) *M = H->M;
+    if (Nchol) *Nchol = H->Nchol;
+    if (Nmu) *Nmu = H->Nmu;
+    return AFQMC_OK;
+}
+
 int afqmc_destroy_hamiltonian(afqmc_ham_t H) {
     if (!H) return fail(AFQMC_ERR_BADARG, "destroy_hamiltonian: NULL handle");
     if (H->live_walker_sets > 0) return fail(AFQMC_ERR_BADARG, "destroy_hamiltonian: walker sets still use it");
     cudaFree(H->h);
     cudaFree(H->L);
     cudaFree(H->hp);
+    cudaFree(H->X);
+    cudaFree(H->Mk);
+    cudaFree(H->U);
     cudaFree(H->flags);
     delete H;
     return AFQMC_OK;
@@ -295,8 +407,8 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
     for (int r : o.reserved)
         if (r != 0) return fail(AFQMC_ERR_BADARG, "init_walkers: reserved options must be zero");
     if (o.walker_offset < 0) return fail(AFQMC_ERR_BADARG, "init_walkers: walker_offset must be >= 0");
-    if (o.energy_terms != 0 && o.energy_terms != 3 && o.energy_terms != 4)
-        return fail(AFQMC_ERR_BADARG, "init_walkers: energy_terms must be 0, 3 or 4");
+    if (o.energy_terms != 0 && o.energy_terms != 1 && o.energy_terms != 3 && o.energy_terms != 4)
+        return fail(AFQMC_ERR_BADARG, "init_walkers: energy_terms must be 0, 1, 3 or 4");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     AFQMC_CUDA_TRY(cudaGetDevice(&dev));
@@ -372,6 +484,8 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
     }
     if (o.precision == AFQMC_PREC_BF16X3 && ham->cplx_L)
         return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs real Cholesky vectors"));
+    if (ham->Nmu > 0 && (o.precision == AFQMC_PREC_BF16X3 || ND > 1))
+        return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: a THC Hamiltonian runs on the FP64 path with one determinant"));
     if (o.precision == AFQMC_PREC_BF16X3 && ND > 1)
         return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs a single-determinant trial"));
     if (o.precision == AFQMC_PREC_BF16X3) {
@@ -379,8 +493,23 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
             return bail(fail(AFQMC_ERR_UNSUPPORTED,
                              "init_walkers: BF16X3 needs a real trial, Nup == Ndn, M % 64 == 0, Nchol % 8 == 0"));
     }
-    // rotated Cholesky tensor, its transpose, rotated one-body matrix, per determinant
-    for (int s = 0; s < 2; ++s) {
+    // rotated Cholesky tensor (THC: the half-rotated orbital values Psi^+ X), its transpose,
+    // rotated one-body matrix, per determinant
+    for (int s = 0; s < 2 && ham->Nmu > 0; ++s) {
+        GemmArgs g;   // Yt = Psi^+ X   [N][Nmu]
+        g.m = wk->N[s]; g.n = ham->Nmu; g.k = M;
+        g.A.ptr = f.Psi[s]; g.A.op = OP_C; g.A.ld = wk->N[s];
+        g.B.ptr = ham->X; g.B.real = true; g.B.ld = ham->Nmu;
+        g.C = f.Yt[s]; g.ldc = ham->Nmu;
+        zgemm(g, st);
+        GemmArgs gh;  // ht = Psi^+ h   [N][M]
+        gh.m = wk->N[s]; gh.n = M; gh.k = M;
+        gh.A.ptr = f.Psi[s]; gh.A.op = OP_C; gh.A.ld = wk->N[s];
+        gh.B.ptr = ham->h; gh.B.real = true; gh.B.ld = M;
+        gh.C = f.ht[s]; gh.ldc = M;
+        zgemm(gh, st);
+    }
+    for (int s = 0; s < 2 && ham->Nmu == 0; ++s) {
         const int N = wk->N[s];
         const int64_t mn = (int64_t)M * N, tot = (int64_t)nch * N * M;
         cplx* tmp = nullptr;
@@ -810,6 +939,7 @@ int afqmc_energy_backward(afqmc_wk_t wk, const double* dE, const double* dlogS, 
                           double* dL, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "energy_backward: NULL handle");
     if (wk->ham->cplx_L) return fail(AFQMC_ERR_UNSUPPORTED, "energy_backward: needs real Cholesky vectors");
+    if (wk->ham->Nmu > 0) return fail(AFQMC_ERR_UNSUPPORTED, "energy_backward: needs Cholesky vectors (not THC)");
     if (wk->ND > 1) return fail(AFQMC_ERR_UNSUPPORTED, "energy_backward: needs a single-determinant trial");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return fp64_backward(wk, reinterpret_cast<const cplx*>(dE), reinterpret_cast<const cplx*>(dlogS),

@@ -71,11 +71,27 @@ __global__ void to_orbital_major_kernel(const cplx* src, int W, int M, int N, co
     dst[((int64_t)i * W + w) * N + a] = v;
 }
 
-__global__ void transpose_kernel(const cplx* a, int M, cplx* b) {
+// b = (sum_c a_c)^T over nc partial M x M products a_c = a + c M^2, summed in chunk order
+__global__ void sum_transpose_kernel(const cplx* a, int nc, int M, cplx* b) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (int64_t)M * M) return;
+    const int64_t MM = (int64_t)M * M;
+    if (id >= MM) return;
     const int i = (int)(id / M), j = (int)(id % M);
-    b[(int64_t)j * M + i] = a[id];
+    cplx acc = a[id];
+    for (int c = 1; c < nc; ++c) acc = acc + a[c * MM + id];
+    b[(int64_t)j * M + i] = acc;
+}
+
+// Walker chunks for the walker-sum GEMM: its M x M output alone has few 64 x 64 tiles, so the
+// K = W N sum is split into chunks of whole walkers, about four CTAs per SM in all.  The
+// largest divisor of W not above that target.
+int walker_chunks(int W, int M) {
+    const int64_t tiles = (int64_t)((M + 63) / 64) * ((M + 63) / 64);
+    const int64_t target = std::max<int64_t>(1, (4 * (int64_t)tc_num_sms() + tiles - 1) / tiles);
+    int best = 1;
+    for (int d = 1; d <= W && d <= target; ++d)
+        if (W % d == 0) best = d;
+    return best;
 }
 
 struct Scratch {
@@ -180,7 +196,8 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
     cplx* cc = sc.get<cplx>((size_t)W * nch);
     cplx* S = sc.get<cplx>((size_t)W * Nmax * Nmax);
     cplx* ld = sc.get<cplx>(W);
-    cplx* H = sc.get<cplx>(MM);
+    const int nck = walker_chunks(W, M);
+    cplx* H = sc.get<cplx>(MM * nck);
     cplx* tot = sc.get<cplx>(1);
     unsigned* sing = sc.get<unsigned>(1);
     if (!Qs[0] || !Qs[1] || !P0 || !P1 || !acc || !Th || !cc || !S || !ld || !H || !tot || !sing)
@@ -189,7 +206,29 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
     weight_total_kernel<<<1, kT, 0, st>>>(wk->weight, W, tot);
     for (int s = 0; s < 2; ++s)
         replicate(Qs[s], f.Psi[s], (int64_t)M * wk->N[s], W, (int64_t)M * wk->N[s], st);
-    for (int k = wk->bp_n - 1; k >= 0; --k) {
+    if (wk->tc) {
+        // BF16X3 walker set: every back step on the tensor cores, through the forward step's own
+        // three-slice propagation with conjugated coefficients and -i sqrt(tau) (the adjoint
+        // B(k)^+ = B T_K(-i sqrt(tau) A(k)^+) B); QR in FP64 on the canonical layout
+        const int64_t nT = (int64_t)W * 4 * wk->N[0] * M;
+        double* QT = sc.get<double>(nT);
+        double* QT2 = sc.get<double>(nT);
+        if (!QT || !QT2) return fail(AFQMC_ERR_OOM, "bp_rdm1: workspace");
+        tc_canon_to_T(wk, Qs, QT, st);
+        for (int k = wk->bp_n - 1; k >= 0; --k) {
+            AFQMC_TRY(tc_apply_propagator(wk, wk->bp_coef + (int64_t)k * W * nch, true, -1.0, QT, QT2, st));
+            std::swap(QT, QT2);
+            const int done = wk->bp_n - k;
+            if (wk->opts.k_qr > 0 && done % wk->opts.k_qr == 0 && k > 0) {
+                tc_T_to_canon(wk, QT, Qs, st);
+                for (int s = 0; s < 2; ++s)
+                    qr_reorthonormalise(Qs[s], (int64_t)M * wk->N[s], M, wk->N[s], W, wk->weight, st);
+                tc_canon_to_T(wk, Qs, QT, st);
+            }
+        }
+        tc_T_to_canon(wk, QT, Qs, st);
+    }
+    for (int k = wk->tc ? -1 : wk->bp_n - 1; k >= 0; --k) {
         // A(k)^+ = sum_n conj(c_n) L_n for every walker, shared by both spins
         count_launch();
         conj_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->bp_coef + (int64_t)k * W * nch, cc, (int64_t)W * nch);
@@ -256,19 +295,22 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
             g.C = Th; g.ldc = N; g.sc1 = mn;
             zgemm(g, st);
         }
-        // H = sum_w (w_w / sum w) Theta_w Psi_bp,w^+ over K = (walker, orbital); G = H^T
+        // H = sum_w (w_w / sum w) Theta_w Psi_bp,w^+ over K = (walker, orbital); G = H^T.  The
+        // K sum runs as nck batched partial products over chunks of W / nck walkers, added in
+        // chunk order with the transpose
         count_launch();
         to_orbital_major_kernel<<<nb((int64_t)W * mn), kT, 0, st>>>(Th, W, M, N, wk->weight, tot, P0);
         count_launch();
         to_orbital_major_kernel<<<nb((int64_t)W * mn), kT, 0, st>>>(Q, W, M, N, nullptr, nullptr, P1);
+        const int kc = (W / nck) * N;
         GemmArgs g;
-        g.m = M; g.n = M; g.k = W * N;
-        g.A.ptr = P0; g.A.ld = (int64_t)W * N;
-        g.B.ptr = P1; g.B.op = OP_C; g.B.ld = (int64_t)W * N;
-        g.C = H; g.ldc = M;
+        g.m = M; g.n = M; g.k = kc; g.nb1 = nck;
+        g.A.ptr = P0; g.A.ld = (int64_t)W * N; g.A.s1 = kc;
+        g.B.ptr = P1; g.B.op = OP_C; g.B.ld = (int64_t)W * N; g.B.s1 = kc;
+        g.C = H; g.ldc = M; g.sc1 = MM;
         zgemm(g, st);
         count_launch();
-        transpose_kernel<<<nb(MM), kT, 0, st>>>(H, M, G[s]);
+        sum_transpose_kernel<<<nb(MM), kT, 0, st>>>(H, nck, M, G[s]);
         check_finite(reinterpret_cast<const double*>(G[s]), 2 * MM, flag, st);
     }
     return AFQMC_OK;
@@ -286,6 +328,7 @@ int afqmc_bp_begin(afqmc_wk_t wk, int nbp, void* stream) {
     if (!wk) return fail(AFQMC_ERR_BADARG, "bp_begin: NULL handle");
     if (nbp < 0) return fail(AFQMC_ERR_BADARG, "bp_begin: negative window length");
     if (wk->ND > 1) return fail(AFQMC_ERR_UNSUPPORTED, "bp_begin: needs a single-determinant trial");
+    if (wk->ham->Nmu > 0) return fail(AFQMC_ERR_UNSUPPORTED, "bp_begin: needs a Hamiltonian with Cholesky vectors (not THC)");
     return bp_open(wk, nbp, static_cast<cudaStream_t>(stream));
 }
 

@@ -66,6 +66,15 @@ struct afqmc_batch {
     int bn_max = 256;
     int grid_cap = 0;
     double tuned_ms = -1.0;
+    // energy contractions of a measuring BF16X3 step: one multi-system launch (1) or one
+    // launch per system in its branch (0); K chunk of the multi-system launch
+    int multi_energy = 1;
+    int energy_bk = 32;
+    EnergySys* esys = nullptr;       // device [n]: each system's operands and shape
+    EnergyWork* work = nullptr;      // device [nwork]: pair tiles of every system
+    int64_t nwork = 0;
+    int esys_bk = 0;                 // K chunk esys was described with (0: not built)
+    std::vector<cudaEvent_t> ev2;    // second fork / join around the multi-system launch
 };
 
 namespace {
@@ -280,6 +289,41 @@ int system_step(afqmc_batch* b, int s, bool meas, bool qr, cudaStream_t st) {
     return AFQMC_OK;
 }
 
+// Operands, shapes and work list of the multi-system energy contraction (device arrays, built
+// once per K chunk: the systems' buffers never move).
+int ensure_energy_work(afqmc_batch* b) {
+    if (b->esys && b->esys_bk == b->energy_bk) return AFQMC_OK;
+    if (b->esys) cudaFree(b->esys);
+    if (b->work) cudaFree(b->work);
+    b->esys = nullptr;
+    b->work = nullptr;
+    std::vector<EnergySys> hs((size_t)b->n);
+    for (int s = 0; s < b->n; ++s) AFQMC_TRY(tc_energy_system(b->wk[s], b->energy_bk, &hs[(size_t)s]));
+    std::vector<EnergyWork> hw;
+    energy_work_list(hs.data(), b->n, hw);
+    if (cudaMalloc(&b->esys, sizeof(EnergySys) * hs.size()) != cudaSuccess ||
+        cudaMalloc(&b->work, sizeof(EnergyWork) * std::max<size_t>(hw.size(), 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AFQMC_ERR_OOM, "batch: energy work list");
+    }
+    AFQMC_CUDA_TRY(cudaMemcpy(b->esys, hs.data(), sizeof(EnergySys) * hs.size(), cudaMemcpyHostToDevice));
+    AFQMC_CUDA_TRY(cudaMemcpy(b->work, hw.data(), sizeof(EnergyWork) * hw.size(), cudaMemcpyHostToDevice));
+    b->nwork = (int64_t)hw.size();
+    b->esys_bk = b->energy_bk;
+    return AFQMC_OK;
+}
+
+// The rest of a measuring BF16X3 step of system s once its energy contraction has run.
+int system_step_after_energy(afqmc_batch* b, int s, bool qr, cudaStream_t st) {
+    afqmc_walkers* wk = b->wk[s];
+    AFQMC_TRY(tc_measure_post(wk, true, st));
+    mixed_energy(wk->weight, wk->E_L, wk->W, wk->emix, st);
+    philox_fields_dev(b->params, (uint64_t)s * kSeedStride, wk->W, wk->Nchol, wk->x, st, wk->opts.walker_offset);
+    AFQMC_TRY(tc_propagate_and_weight(wk, wk->x, st));
+    if (qr) AFQMC_TRY(tc_qr(wk, st));
+    return AFQMC_OK;
+}
+
 // Captures one batch step (every system) into an executable graph.
 int capture(afqmc_batch* b, bool meas, bool qr, cudaGraphExec_t* out, int* nkern) {
     const int K = std::max(1, std::min(b->concurrency > 0 ? b->concurrency : b->n, (int)b->br.size()));
@@ -297,14 +341,43 @@ int capture(afqmc_batch* b, bool meas, bool qr, cudaGraphExec_t* out, int* nkern
     LaunchPolicy saved = launch_policy();
     launch_policy().grid_cap = b->grid_cap;
     launch_policy().bn_max = b->bn_max;
+    const bool tc = b->opts.precision == AFQMC_PREC_BF16X3;
+    const bool multi = meas && tc && b->multi_energy;
+    if (multi) {
+        const int r0 = ensure_energy_work(b);
+        if (r0) {
+            launch_policy() = saved;
+            return r0;
+        }
+    }
     cudaGraph_t g = nullptr;
     int rc = AFQMC_OK;
     AFQMC_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    if (multi) {
+        // every system's Green's function, then one energy launch over all of them, then every
+        // system's local energy, propagation and weights
+        cudaEventRecord(b->ev2[0], b->cap);
+        for (int k = 0; k < K && rc == AFQMC_OK; ++k) {
+            cudaStreamWaitEvent(b->br[k], b->ev2[0], 0);
+            for (int s : chain[k]) {
+                rc = tc_measure_pre(b->wk[s], b->br[k]);
+                if (rc) break;
+            }
+            cudaEventRecord(b->ev2[1 + k], b->br[k]);
+            cudaStreamWaitEvent(b->cap, b->ev2[1 + k], 0);
+        }
+        if (rc == AFQMC_OK)
+            rc = tc_energy_multi(b->esys, b->work, b->nwork, b->energy_bk,
+                                 b->opts.energy_terms == 0 ? kEnergyRounded
+                                                           : (b->opts.energy_terms == 1 ? kEnergyFour
+                                                                                        : b->opts.energy_terms),
+                                 b->wk[0]->flags, b->cap);
+    }
     cudaEventRecord(b->ev[0], b->cap);
     for (int k = 0; k < K && rc == AFQMC_OK; ++k) {
         cudaStreamWaitEvent(b->br[k], b->ev[0], 0);
         for (int s : chain[k]) {
-            rc = system_step(b, s, meas, qr, b->br[k]);
+            rc = multi ? system_step_after_energy(b, s, qr, b->br[k]) : system_step(b, s, meas, qr, b->br[k]);
             if (rc) break;
         }
         cudaEventRecord(b->ev[1 + k], b->br[k]);
@@ -383,10 +456,11 @@ void free_batch(afqmc_batch* b) {
         if (b->wk[s]) afqmc_destroy_walkers(b->wk[s]);
         if (b->ham[s]) afqmc_destroy_hamiltonian(b->ham[s]);
     }
-    void* ps[] = {b->params, b->trace_idx, b->trace, b->emix_ptrs, b->flag_ptrs, b->flags};
+    void* ps[] = {b->params, b->trace_idx, b->trace, b->emix_ptrs, b->flag_ptrs, b->flags, b->esys, b->work};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (auto e : b->ev) cudaEventDestroy(e);
+    for (auto e : b->ev2) cudaEventDestroy(e);
     for (auto q : b->br) cudaStreamDestroy(q);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -494,12 +568,14 @@ int afqmc_create_batch(int nsys, const afqmc_system* sys, double tau, const afqm
     const int nb = std::min(nsys, 32);
     b->br.resize(nb, nullptr);
     b->ev.resize(nb + 1, nullptr);
+    b->ev2.resize(nb + 1, nullptr);
     for (auto& q : b->br)
         if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess)
             return bail(fail(AFQMC_ERR_CUDA, "create_batch: stream"));
-    for (auto& e : b->ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-            return bail(fail(AFQMC_ERR_CUDA, "create_batch: event"));
+    for (auto* evs : {&b->ev, &b->ev2})
+        for (auto& e : *evs)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return bail(fail(AFQMC_ERR_CUDA, "create_batch: event"));
     b->concurrency = nb;
     {
         const int rc = ensure_trace(b, 64);
@@ -579,8 +655,20 @@ int afqmc_batch_info(afqmc_batch_t b, int sys, int* shape, int* kernels_per_step
         shape[3] = b->concurrency;
         shape[4] = b->bn_max;
         shape[5] = b->grid_cap;
+        shape[6] = b->opts.precision == AFQMC_PREC_BF16X3 ? b->multi_energy : 0;
+        shape[7] = b->energy_bk;
     }
     if (kernels_per_step) *kernels_per_step = b->kernels[1][0] > 0 ? b->kernels[1][0] : -1;
+    return AFQMC_OK;
+}
+
+int afqmc_debug_set_batch_energy(afqmc_batch_t b, int multi, int bk) {
+    if (!b) return fail(AFQMC_ERR_BADARG, "debug_set_batch_energy: NULL handle");
+    if ((multi != 0 && multi != 1) || (bk != 16 && bk != 32))
+        return fail(AFQMC_ERR_BADARG, "debug_set_batch_energy: multi must be 0 or 1, bk 16 or 32");
+    b->multi_energy = multi;
+    b->energy_bk = bk;
+    destroy_graphs(b);
     return AFQMC_OK;
 }
 
@@ -614,7 +702,7 @@ int afqmc_batch_autotune(afqmc_batch_t b, int reps, double* best_ms, void* strea
         }
     }
     const int64_t step0 = b->step;
-    const int c0 = b->concurrency, bn0 = b->bn_max, g0 = b->grid_cap;
+    const int c0 = b->concurrency, bn0 = b->bn_max, g0 = b->grid_cap, m0 = b->multi_energy, k0 = b->energy_bk;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -665,6 +753,22 @@ int afqmc_batch_autotune(afqmc_batch_t b, int reps, double* best_ms, void* strea
         if (ms < best) { best = ms; bg = gcap; }
     }
     b->grid_cap = bg;
+    if (b->opts.precision == AFQMC_PREC_BF16X3) {
+        // energy contractions: one multi-system launch with K chunks of 32 or 16, or one launch
+        // per system in its branch
+        int bm = b->multi_energy, bk = b->energy_bk;
+        for (auto mk : {std::make_pair(1, 32), std::make_pair(1, 16), std::make_pair(0, 32)}) {
+            if (rc) break;
+            if (mk.first == bm && mk.second == bk) continue;   // timed already as the current shape
+            b->multi_energy = mk.first;
+            b->energy_bk = mk.second;
+            double ms = 0;
+            if ((rc = timeit(&ms))) break;
+            if (ms < best) { best = ms; bm = mk.first; bk = mk.second; }
+        }
+        b->multi_energy = bm;
+        b->energy_bk = bk;
+    }
     destroy_graphs(b);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -678,6 +782,8 @@ int afqmc_batch_autotune(afqmc_batch_t b, int reps, double* best_ms, void* strea
         b->concurrency = c0;
         b->bn_max = bn0;
         b->grid_cap = g0;
+        b->multi_energy = m0;
+        b->energy_bk = k0;
         return rc;
     }
     unsigned fl = 0;

@@ -62,6 +62,7 @@ struct LaunchPolicy {
     int energy_bk = 0;   // K chunk of the fused energy kernel: 16 or 32 (default)
     int energy_ws_super = 0;   // walker-spin groups per L2 window of the energy kernel (0: default)
     int gj_variant = 0;        // batched inverse: 0 auto, 1 shared-memory kernel, 2 register kernel
+    int energy_pair = 1;       // fused energy kernel: 1 CTA pairs (cta_group::2, default), 0 one CTA per tile
 };
 LaunchPolicy& launch_policy();
 

@@ -49,15 +49,17 @@ struct DevBuf {
 };
 
 // Upload n = rows * K values; plain split, or row-scaled split when sc is given.
-int upload_split(const double* h, int64_t rows, int64_t K, DevBuf& d64, DevBuf& hi, DevBuf& lo, DevBuf* sc) {
+int upload_split(const double* h, int64_t rows, int64_t K, DevBuf& d64, DevBuf& hi, DevBuf& lo, DevBuf* sc,
+                 DevBuf* rnd = nullptr) {
     const int64_t n = rows * K;
     if (cudaMalloc(&d64.p, n * 8) != cudaSuccess || cudaMalloc(&hi.p, n * 2) != cudaSuccess ||
-        cudaMalloc(&lo.p, n * 2) != cudaSuccess || (sc && cudaMalloc(&sc->p, rows * 4) != cudaSuccess))
+        cudaMalloc(&lo.p, n * 2) != cudaSuccess || (sc && cudaMalloc(&sc->p, rows * 4) != cudaSuccess) ||
+        (rnd && cudaMalloc(&rnd->p, n * 2) != cudaSuccess))
         return fail(AFQMC_ERR_OOM, "debug: allocation");
     AFQMC_CUDA_TRY(cudaMemcpy(d64.p, h, n * 8, cudaMemcpyHostToDevice));
     if (sc) {
         split_rows(static_cast<double*>(d64.p), K, rows, K, static_cast<bf16*>(hi.p), static_cast<bf16*>(lo.p),
-                   static_cast<float*>(sc->p), 0);
+                   static_cast<float*>(sc->p), 0, rnd ? static_cast<bf16*>(rnd->p) : nullptr);
     } else {
         split_kernel<<<(unsigned)((n + 255) / 256), 256>>>(static_cast<double*>(d64.p), static_cast<bf16*>(hi.p),
                                                            static_cast<bf16*>(lo.p), n);
@@ -116,8 +118,9 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     if (!Lt || !ThetaT || !t || !X || Nchol < 1 || nws < 1 || M < 64)
         return fail(AFQMC_ERR_BADARG, "debug_energy: bad arguments");
     const int64_t na = (int64_t)Nchol * Np * M, nb = (int64_t)nws * 2 * Np * M;
-    DevBuf a64, ahi, alo, b64, bhi, blo, dt, dx, flags, asc, bsc;
-    AFQMC_TRY(upload_split(Lt, na / M, M, a64, ahi, alo, &asc));
+    if (terms != 3 && terms != 4 && terms != 5) return fail(AFQMC_ERR_BADARG, "debug_energy: terms must be 3, 4 or 5");
+    DevBuf a64, ahi, alo, arn, b64, bhi, blo, dt, dx, flags, asc, bsc;
+    AFQMC_TRY(upload_split(Lt, na / M, M, a64, ahi, alo, &asc, terms == 5 ? &arn : nullptr));
     AFQMC_TRY(upload_split(ThetaT, nb / M, M, b64, bhi, blo, &bsc));
     const int64_t no = (int64_t)nws * Nchol;
     if (cudaMalloc(&dt.p, no * 16) != cudaSuccess || cudaMalloc(&dx.p, no * 16) != cudaSuccess ||
@@ -129,7 +132,8 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M; sa.scale = static_cast<float*>(asc.p);
     sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
     sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M; sb.scale = static_cast<float*>(bsc.p);
-    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p), terms, nullptr,
+    AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p),
+                        terms == 5 ? kEnergyRounded : terms, nullptr, static_cast<bf16*>(arn.p),
                         static_cast<unsigned*>(flags.p), 0));
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
     unsigned fl = 0;
@@ -215,6 +219,12 @@ extern "C" int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energ
     p.grid_cap = grid_cap;
     p.bn_max = bn_max == 0 ? 256 : bn_max;
     p.energy_bk = energy_bk;
+    return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_set_energy_variant(int pair) {
+    if (pair != 0 && pair != 1) return fail(AFQMC_ERR_BADARG, "debug_set_energy_variant: pair must be 0 or 1");
+    launch_policy().energy_pair = pair;
     return AFQMC_OK;
 }
 

@@ -891,13 +891,13 @@ __global__ void __launch_bounds__(kThreads) local_energy_kernel(LocalEnergyArgs 
     }
     const double sq = sqrt(a.tau);
     cplx e2{0.0, 0.0};
-    const bool energy = a.X[0] != nullptr;
+    const bool energy = a.X[0] != nullptr || a.exch[0] != nullptr;
     for (int n = threadIdx.x; n < a.Nchol; n += kThreads) {
         const int64_t i = (int64_t)w * a.Nchol + n;
         const cplx ts = a.t[0][i] + a.t[1][i];
         if (energy) {
             cfma(e2, ts, ts);
-            e2 = e2 - a.X[0][i] - a.X[1][i];
+            if (a.X[0]) e2 = e2 - a.X[0][i] - a.X[1][i];
         }
         cplx xb{sq * ts.im, -sq * ts.re};  // -i sqrt(tau) ts
         if (a.fb_cap > 0.0) {
@@ -910,6 +910,7 @@ __global__ void __launch_bounds__(kThreads) local_energy_kernel(LocalEnergyArgs 
         e1 = block_sum(e1, sh);
         e2 = block_sum(e2, sh);
         if (threadIdx.x == 0) {
+            if (a.exch[0]) e2 = e2 - a.exch[0][w] - a.exch[1][w];
             const cplx E = cplx{a.E0 + e1.re + 0.5 * e2.re, e1.im + 0.5 * e2.im};
             a.E_L[w] = E;
             if (!finite_c(E)) atomicOr(a.flags, FLAG_NONFINITE);

@@ -54,12 +54,35 @@ struct LocalEnergyArgs {
     const cplx* Theta[2];
     const cplx* t[2];
     const cplx* X[2];
+    // THC Hamiltonians: per-walker exchange sums sum_{mu nu} M_{mu nu} T_{mu nu} T_{nu mu} of each
+    // spin, [W], in place of the per-vector X (which is then null); null otherwise
+    const cplx* exch[2] = {nullptr, nullptr};
     double E0, tau, fb_cap;
     cplx* E_L;
     cplx* xbar;
     unsigned* flags;
 };
 void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st);
+
+// ---- tensor hypercontraction (THC, Sec. V, Eq. (5)) ----
+// Diagonally pivoted (modified) Cholesky of the symmetric positive semidefinite n x n kernel
+// Mk: U [n][rank] (row-major, ld = rank) with U U^T = Mk up to the stopping threshold (largest
+// remaining diagonal <= rtol x largest initial one; pivot = largest remaining diagonal, lowest
+// index on ties).  work: n*n + 2n doubles of device scratch.  *rank is read back (synchronises).
+int thc_pivoted_cholesky(const double* Mk, int n, double rtol, double* work, double* U_out, int* rank,
+                         cudaStream_t st);
+// Per walker w of a chunk: g[w][mu] = T_w[mu][mu] and ex[w] = sum_{mu nu} Mk[mu][nu] T_w[mu][nu]
+// T_w[nu][mu], for T [wc][Nmu][Nmu] complex (fixed summation order).
+void thc_exchange(const cplx* T, int wc, int Nmu, const double* Mk, cplx* g, cplx* ex, cudaStream_t st);
+// Force-bias-only densities: g[w][mu] = sum_a Yt[a][mu] Z[w][a][mu] (Yt [N][Nmu], Z [W][N][Nmu]).
+void thc_gdiag(const cplx* Yt, const cplx* Z, int W, int N, int Nmu, cplx* g, cudaStream_t st);
+// XD[w][i][mu] = X[i][mu] d[w][mu] for the walkers of a chunk (X real [M][Nmu]).
+void thc_scale_columns(const double* X, const cplx* d, int wc, int M, int Nmu, cplx* XD, cudaStream_t st);
+// out[i] = Re a[i];  out[i] = Re a[i] * b[i]
+void real_part(const cplx* a, double* out, int64_t n, cudaStream_t st);
+void real_part_times(const cplx* a, const double* b, double* out, int64_t n, cudaStream_t st);
+// out[i] = h[i] - 0.5 * Re(R[i])
+void hprime_from(const double* h, const cplx* R, double* out, int64_t n, cudaStream_t st);
 
 // Philox4x32-10 + Box-Muller fields x[w][n] for global step `step`.
 // x[w][n] for walkers w0 + w (w < W): counter (n/4, w0 + w, step, 0)

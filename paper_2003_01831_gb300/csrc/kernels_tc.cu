@@ -421,30 +421,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 // --------------------------------------------------------------------------- energy kernel
 // Tiles: (n-group of G = 128/Np Cholesky vectors) x (group of G walker-spin pairs).
 // Accumulator columns of one ws: [re b = 0..Np) [im b = 0..Np).  Exact mode, one TMEM
-// buffer (accumulator 1 in columns 0..255, accumulator 2 in 256..511).
-struct EnergyShape {
-    int Np, Q, G;
-    int Nchol, nws;
-    int n_groups, ws_groups;
-    int ws_super;     // ws groups per L2 super-block
-    int64_t tiles;
-    int nk;
-    int lolo;               // 1: also form lo*lo (four products), 0: three
-    const uint8_t* lolo_group;   // if set: per n-group choice (1: four products, 0: three)
-    const float* a_scale;   // [Nchol*Np]
-    const float* b_scale;   // [nws*2*Np]
-    cplx* t_out;
-    cplx* X_out;
-};
+// buffer (accumulator 1 in columns 0..255, accumulator 2 in 256..511).  EnergyShape,
+// EnergySys and EnergyWork are in kernels_tc.cuh.
 
-__device__ __forceinline__ void energy_tile(const EnergyShape& s, int64_t t, int& ng, int& wg) {
-    const int64_t per_super = (int64_t)s.ws_super * s.n_groups;
+// Tile t -> (row group ng of nrow, walker-spin group wg): windows of ws_super walker-spin
+// groups, each sweeping every row group.
+__device__ __forceinline__ void energy_tile_rows(const EnergyShape& s, int64_t t, int nrow, int& ng, int& wg) {
+    const int64_t per_super = (int64_t)s.ws_super * nrow;
     const int64_t sup = t / per_super;
     const int64_t rem = t % per_super;
     const int64_t first = sup * s.ws_super;
     const int width = (int)(s.ws_groups - first < s.ws_super ? s.ws_groups - first : s.ws_super);
     ng = (int)(rem / width);
     wg = (int)(first + rem % width);
+}
+__device__ __forceinline__ void energy_tile(const EnergyShape& s, int64_t t, int& ng, int& wg) {
+    energy_tile_rows(s, t, s.n_groups, ng, wg);
 }
 
 // Energy kernel pipeline: K chunks of BK = 16 (32-byte swizzle, six 24 KB stages) or 32
@@ -456,13 +448,17 @@ __device__ __forceinline__ void energy_tile(const EnergyShape& s, int64_t t, int
 // walker-spin window below, the wider chunks (half the barrier round trips per flop) are
 // faster.
 constexpr int kEStageRing = 144 * 1024;
-template <int BK>
-struct ECfg {
-    static constexpr int kABytes = kBM * BK * 2;       // per plane
-    static constexpr int kBBytes = 256 * BK * 2;       // per plane
-    static constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;
-    static constexpr int kStages = kEStageRing / kStageBytes;
-    static_assert(kStages >= 2 && kStages <= 8, "stage ring");
+// One stage: AP planes of the Ltilde rows (hi, lo and, for the rounded products, r) of 128
+// rows each, then the hi and lo planes of BR Theta rows (256 for one CTA per tile, 128 per CTA
+// of a pair), each K chunk of BK columns.
+template <int BK, int AP, int BR>
+struct EStage {
+    static constexpr int kABytes = kBM * BK * 2;       // per A plane
+    static constexpr int kBBytes = BR * BK * 2;        // per B plane
+    static constexpr int kBOff = AP * kABytes;         // first B plane
+    static constexpr int kStageBytes = AP * kABytes + 2 * kBBytes;
+    static constexpr int kStages = kEStageRing / kStageBytes < 8 ? kEStageRing / kStageBytes : 8;
+    static_assert(kStages >= 2, "stage ring");
 };
 constexpr int kEBKDefault = 32;
 // Walker-spin groups per L2 window: the window's Theta pairs (512 KB per group at M = 512) stay
@@ -478,10 +474,11 @@ __device__ __forceinline__ uint64_t edesc(uint32_t saddr) {
 }
 
 
-template <int BK>
+template <int BK, int AP>
 __device__ void energy_producer(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
-                                const CUtensorMap* tBh, const CUtensorMap* tBl, const EnergyShape& es) {
-    using C = ECfg<BK>;
+                                const CUtensorMap* tAr, const CUtensorMap* tBh, const CUtensorMap* tBl,
+                                const EnergyShape& es) {
+    using C = EStage<BK, AP, 256>;
     int64_t g = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < es.tiles && ok; t += gridDim.x) {
@@ -496,8 +493,9 @@ __device__ void energy_producer(uint8_t* sbase, SharedCtl* ctl, const CUtensorMa
             const int x = kb * BK;
             tma_load_2d(s, tAh, &ctl->full[st], x, ng * 128);
             tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], x, ng * 128);
-            tma_load_2d(s + 2 * C::kABytes, tBh, &ctl->full[st], x, wg * 256);
-            tma_load_2d(s + 2 * C::kABytes + C::kBBytes, tBl, &ctl->full[st], x, wg * 256);
+            if (AP == 3) tma_load_2d(s + 2 * C::kABytes, tAr, &ctl->full[st], x, ng * 128);
+            tma_load_2d(s + C::kBOff, tBh, &ctl->full[st], x, wg * 256);
+            tma_load_2d(s + C::kBOff + C::kBBytes, tBl, &ctl->full[st], x, wg * 256);
         }
     }
     if (!ok) {
@@ -506,9 +504,29 @@ __device__ void energy_producer(uint8_t* sbase, SharedCtl* ctl, const CUtensorMa
     }
 }
 
-template <int BK>
+// The split products of one K slice of 16.  AP = 3 (rounded products): D1 += hi*hi,
+// D2 += r*lo + lo*hi, where r = fp16(y) is the row-scaled Ltilde value rounded to fp16: its bits
+// beyond the integer hi carry the leading part of lo, so r*lo + lo*hi holds hi*lo + lo*hi and
+// all of lo*lo but the Ltilde rounding error times lo (three products, the accuracy of four).
+// AP = 2: D1 += hi*hi, D2 += hi*lo + lo*hi (+ lo*lo when `lolo`).
+template <int AP, typename Mma>
+__device__ __forceinline__ void energy_products(Mma mma, uint32_t d1, uint32_t d2, uint64_t ah, uint64_t al,
+                                                uint64_t ar, uint64_t bh, uint64_t bl, uint32_t acc, bool lolo) {
+    if (AP == 3) {
+        mma(d1, ah, bh, acc);
+        mma(d2, ar, bl, acc);
+        mma(d2, al, bh, 1u);
+    } else {
+        mma(d1, ah, bh, acc);
+        mma(d2, ah, bl, acc);
+        mma(d2, al, bh, 1u);
+        if (lolo) mma(d2, al, bl, 1u);
+    }
+}
+
+template <int BK, int AP>
 __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es) {
-    using C = ECfg<BK>;
+    using C = EStage<BK, AP, 256>;
     constexpr uint32_t idesc = idesc_bf16(kBM, 256, true);   // fp16 planes, M=128, N=256
     const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
     int64_t g = 0;
@@ -526,17 +544,14 @@ __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es
             if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
             tc_fence_after();
             const uint32_t sa = smem_u32(sbase + (size_t)st * C::kStageBytes);
-            const uint32_t sal = sa + C::kABytes, sb = sa + 2 * C::kABytes, sbl = sb + C::kBBytes;
+            const uint32_t sal = sa + C::kABytes, sar = sa + 2 * C::kABytes;
+            const uint32_t sb = sa + C::kBOff, sbl = sb + C::kBBytes;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint32_t off = kk * 32;
-                const uint64_t ah = edesc<BK>(sa + off), al = edesc<BK>(sal + off);
-                const uint64_t bh = edesc<BK>(sb + off), bl = edesc<BK>(sbl + off);
-                const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
-                mma_bf16(d1, ah, bh, idesc, acc);
-                mma_bf16(d2, ah, bl, idesc, acc);
-                mma_bf16(d2, al, bh, idesc, 1u);
-                if (lolo) mma_bf16(d2, al, bl, idesc, 1u);
+                energy_products<AP>([&](uint32_t d, uint64_t a, uint64_t b, uint32_t c) { mma_bf16(d, a, b, idesc, c); },
+                                    d1, d2, edesc<BK>(sa + off), edesc<BK>(sal + off), edesc<BK>(sar + off),
+                                    edesc<BK>(sb + off), edesc<BK>(sbl + off), (kb | kk) != 0 ? 1u : 0u, lolo);
             }
             mma_commit(&ctl->empty[st]);
         }
@@ -566,16 +581,166 @@ __device__ __forceinline__ int ebar_and(int pred) {
     return r;
 }
 
-template <int Np, int BK>
-__global__ void __launch_bounds__(kEThreads, 1)
-    tc_energy_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                     const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
-                     EnergyShape es, unsigned* flags) {
+// Epilogue of one tile of the energy kernels (warps 2..17 of a CTA): n-group ng of this CTA's
+// accumulator rows, walker-spin group wg, the CTA's it-th tile (accumulator barrier phase).
+// release() is called by lane 0 of each warp once the warp's tensor-memory reads are complete.
+// Returns false when a wait gave up (all sixteen warps then leave together).
+template <int Np, typename Release>
+__device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, SharedCtl* ctl, float* plane,
+                                                     float* colscale, double* ered, int ng, int wg, int it,
+                                                     Release release) {
     constexpr int Q = Np / 32;     // TMEM quadrants per n-block
     constexpr int G = 128 / Np;    // n-blocks (rows) and walker-spins (columns) per tile
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Epilogue.  The tile's accumulator columns are, per walker-spin j of the tile, Np real
+    // columns then Np imaginary ones.  Compact column cc = j Np + b (b < Np) names element b
+    // of walker-spin j; this thread owns row `row` and the 32 compact columns
+    // [32 h, 32 h + 32), all in one walker-spin j.  Per (n-block, walker-spin) block, with
+    // T = Tr + i Ti:
+    //   t = Tr_aa + i Ti_aa,
+    //   X = sum_ab T_ab T_ba = sum Tr_ab Tr_ba - sum Ti_ab Ti_ba + 2 i sum Tr_ab Ti_ba
+    // (sum Ti_ab Tr_ba = sum Tr_ab Ti_ba by relabelling).  The drain writes Ti to the plane
+    // tile and keeps the thread's Tr in registers; the TiTi and TrTi sums read the plane;
+    // then Tr replaces it for the TrTr sum.  Partner reads T_ba run along a row of the plane
+    // (lanes = consecutive a), own-row reads down a column (pitch 129): both conflict-free.
+    const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
+    const int h = (warp - 2) >> 2;         // compact columns [32 h, 32 h + 32)
+    const int row = q * 32 + lane;         // tile row = (n-block i_blk, a)
+    const int i_blk = row / Np, a = row % Np;
+    const int et = threadIdx.x - 64;       // 0..511
+    const uint32_t tq = ctl->tmem_base + ((uint32_t)(q * 32) << 16);
+    const int cc0 = h * 32;                      // first compact column of this thread
+    const int j = cc0 / Np, b0 = cc0 % Np;       // its walker-spin and first element
+    const int col_re = j * 2 * Np + b0, col_im = col_re + Np;
+    float* own = plane + row * kEPitch;                      // this row of the plane
+    const float* pbase = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;   // T_(b0+k) a
+    const int cd = j * Np + a;                               // compact column of T_aa
+    const bool diag = cd >= cc0 && cd < cc0 + 32;
+    if (et < 256) {
+        const int64_t brow = (int64_t)wg * 256 + et;
+        colscale[et] = brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
+    }
+    const int64_t arow = (int64_t)ng * 128 + row;
+    const float sa = arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
+    ebar();
+    // Drain.  Each warp waits for the tile, moves its Im columns of both accumulators
+    // (scaled to true units) into the plane, loads its Re columns and releases tensor
+    // memory at once (one arrival per warp), so the next tile's MMAs overlap the Re
+    // scaling and everything after it.  If any warp's wait gave up, all sixteen leave
+    // together after the release.
+    const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
+    tc_fence_after();
+    float tr[32];
+    {
+        uint32_t u1[32], u2[32];
+        tmem_ld32_nw(tq + col_im, u1);
+        tmem_ld32_nw(tq + 256 + col_im, u2);
+        tmem_ld_wait();
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const float4 cs = *reinterpret_cast<const float4*>(colscale + col_im + 4 * g);
+            own[cc0 + 4 * g + 0] = (__uint_as_float(u1[4 * g + 0]) + __uint_as_float(u2[4 * g + 0])) * (sa * cs.x);
+            own[cc0 + 4 * g + 1] = (__uint_as_float(u1[4 * g + 1]) + __uint_as_float(u2[4 * g + 1])) * (sa * cs.y);
+            own[cc0 + 4 * g + 2] = (__uint_as_float(u1[4 * g + 2]) + __uint_as_float(u2[4 * g + 2])) * (sa * cs.z);
+            own[cc0 + 4 * g + 3] = (__uint_as_float(u1[4 * g + 3]) + __uint_as_float(u2[4 * g + 3])) * (sa * cs.w);
+        }
+    }
+    {
+        uint32_t u1[32], u2[32];
+        tmem_ld32_nw(tq + col_re, u1);
+        tmem_ld32_nw(tq + 256 + col_re, u2);
+        tmem_ld_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0 && got) release();   // tensor memory free
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+            const float4 cs = *reinterpret_cast<const float4*>(colscale + col_re + 4 * g);
+            tr[4 * g + 0] = (__uint_as_float(u1[4 * g + 0]) + __uint_as_float(u2[4 * g + 0])) * (sa * cs.x);
+            tr[4 * g + 1] = (__uint_as_float(u1[4 * g + 1]) + __uint_as_float(u2[4 * g + 1])) * (sa * cs.y);
+            tr[4 * g + 2] = (__uint_as_float(u1[4 * g + 2]) + __uint_as_float(u2[4 * g + 2])) * (sa * cs.z);
+            tr[4 * g + 3] = (__uint_as_float(u1[4 * g + 3]) + __uint_as_float(u2[4 * g + 3])) * (sa * cs.w);
+        }
+    }
+    if (!ebar_and(got ? 1 : 0)) return false;   // all sixteen warps leave together
+    ebar();                                    // Ti plane complete
+    // TiTi and TrTi sums over this thread's b, and the diagonal Ti_aa
+    float sii = 0.f, sri = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float p = pbase[k * kEPitch];    // Ti[b0 + k][a] of walker-spin j
+        sii = fmaf(own[cc0 + k], p, sii);
+        sri = fmaf(tr[k], p, sri);
+    }
+    const float dim_ = diag ? own[cd] : 0.f;
+    ebar();                                    // every read of the Ti plane done
+#pragma unroll
+    for (int k = 0; k < 32; ++k) own[cc0 + k] = tr[k];
+    ebar();                                    // Tr plane complete
+    // TrTr sum continues the -TiTi one, so Re X is accumulated in one register
+    float srr = -sii;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) srr = fmaf(tr[k], pbase[k * kEPitch], srr);
+    const float dre = diag ? own[cd] : 0.f;
+    float v0 = dre, v1 = dim_, v2 = srr, v3 = 2.0f * sri;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+    }
+    if (lane < 16) {   // ered[h][q][jj][v] for every walker-spin slot (zeros but j)
+        const int jj = lane >> 2, v = lane & 3;
+        const float val = jj != j ? 0.f : (v == 0 ? v0 : (v == 1 ? v1 : (v == 2 ? v2 : v3)));
+        ered[((h * 4 + q) * 4 + jj) * 4 + v] = val;
+    }
+    ebar();
+    // one thread per (n-block, walker-spin) output: sum over the n-block's quadrants and
+    // the four column quarters
+    if (et < G * G) {
+        const int ib = et / G, jo = et % G;
+        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int hh = 0; hh < 4; ++hh)
+            for (int qq = ib * Q; qq < (ib + 1) * Q; ++qq) {
+                const double* e = ered + ((hh * 4 + qq) * 4 + jo) * 4;
+                s0 += e[0];
+                s1 += e[1];
+                s2 += e[2];
+                s3 += e[3];
+            }
+        const int n = ng * G + ib;
+        const int ws = wg * G + jo;
+        if (n < es.Nchol && ws < es.nws) {
+            es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
+            es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
+        }
+    }
+    ebar();   // ered, colscale and the plane are read before the next tile rewrites them
+    return true;
+}
+
+// Epilogue of the single-system energy kernels: tile_of(t, ng, wg) names the tile of persistent
+// iteration t.
+template <int Np, typename TileOf, typename Release>
+__device__ void energy_epilogue(const EnergyShape& es, SharedCtl* ctl, float* plane, float* colscale, double* ered,
+                                int64_t t_first, int64_t t_end, int64_t t_step, TileOf tile_of, Release release) {
+    int it = 0;
+    for (int64_t t = t_first; t < t_end; t += t_step, ++it) {
+        int ng, wg;
+        tile_of(t, ng, wg);
+        if (!energy_epilogue_tile<Np>(es, ctl, plane, colscale, ered, ng, wg, it, release)) break;
+    }
+}
+
+template <int Np, int BK, int AP>
+__global__ void __launch_bounds__(kEThreads, 1)
+    tc_energy_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                     const __grid_constant__ CUtensorMap tAr, const __grid_constant__ CUtensorMap tBh,
+                     const __grid_constant__ CUtensorMap tBl, EnergyShape es, unsigned* flags) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    using C = ECfg<BK>;
+    using C = EStage<BK, AP, 256>;
     float* plane = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
     // 256 column scales of the tile; partial traces ered[((h * 4 + q) * 4 + j) * 4 + v]
     float* colscale = plane + kETileFloats;       // 128 x 129 floats: 16-byte aligned
@@ -585,6 +750,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tAh);
         tma_prefetch_desc(&tAl);
+        if (AP == 3) tma_prefetch_desc(&tAr);
         tma_prefetch_desc(&tBh);
         tma_prefetch_desc(&tBl);
     }
@@ -594,7 +760,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
             mbar_init(&ctl->empty[i], 1);
         }
         mbar_init(&ctl->tfull[0], 1);
-        mbar_init(&ctl->tempty[0], kEEpi);
+        mbar_init(&ctl->tempty[0], kEEpi / 32);   // one arrival per epilogue warp
         mbar_init(&ctl->done, 1);
         ctl->abort = 0;
         fence_mbar_init();
@@ -608,141 +774,338 @@ __global__ void __launch_bounds__(kEThreads, 1)
     tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0) energy_producer<BK>(sbase, ctl, &tAh, &tAl, &tBh, &tBl, es);
+        if (lane == 0) energy_producer<BK, AP>(sbase, ctl, &tAh, &tAl, &tAr, &tBh, &tBl, es);
     } else if (warp == 1) {
-        if (lane == 0) energy_mma<BK>(sbase, ctl, es);
+        if (lane == 0) energy_mma<BK, AP>(sbase, ctl, es);
     } else {
-        // Epilogue.  The tile's accumulator columns are, per walker-spin j of the tile, Np real
-        // columns then Np imaginary ones.  Compact column cc = j Np + b (b < Np) names element b
-        // of walker-spin j; this thread owns row `row` and the 32 compact columns
-        // [32 h, 32 h + 32), all in one walker-spin j.  Per (n-block, walker-spin) block, with
-        // T = Tr + i Ti:
-        //   t = Tr_aa + i Ti_aa,
-        //   X = sum_ab T_ab T_ba = sum Tr_ab Tr_ba - sum Ti_ab Ti_ba + 2 i sum Tr_ab Ti_ba
-        // (sum Ti_ab Tr_ba = sum Tr_ab Ti_ba by relabelling).  The drain writes Ti to the plane
-        // tile and keeps the thread's Tr in registers; the TiTi and TrTi sums read the plane;
-        // then Tr replaces it for the TrTr sum.  Partner reads T_ba run along a row of the plane
-        // (lanes = consecutive a), own-row reads down a column (pitch 129): both conflict-free.
-        const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
-        const int h = (warp - 2) >> 2;         // compact columns [32 h, 32 h + 32)
-        const int row = q * 32 + lane;         // tile row = (n-block i_blk, a)
-        const int i_blk = row / Np, a = row % Np;
-        const int et = threadIdx.x - 64;       // 0..511
-        const uint32_t tq = ctl->tmem_base + ((uint32_t)(q * 32) << 16);
-        const int cc0 = h * 32;                      // first compact column of this thread
-        const int j = cc0 / Np, b0 = cc0 % Np;       // its walker-spin and first element
-        const int col_re = j * 2 * Np + b0, col_im = col_re + Np;
-        float* own = plane + row * kEPitch;                      // this row of the plane
-        const float* pbase = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;   // T_(b0+k) a
-        const int cd = j * Np + a;                               // compact column of T_aa
-        const bool diag = cd >= cc0 && cd < cc0 + 32;
-        int it = 0;
-        for (int64_t t = blockIdx.x; t < es.tiles; t += gridDim.x, ++it) {
-            int ng, wg;
-            energy_tile(es, t, ng, wg);
-            if (et < 256) {
-                const int64_t brow = (int64_t)wg * 256 + et;
-                colscale[et] = brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
-            }
-            const int64_t arow = (int64_t)ng * 128 + row;
-            const float sa = arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
-            ebar();
-            const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
-            if (!ebar_and(got ? 1 : 0)) break;   // all sixteen warps leave together
-            tc_fence_after();
-            // drain: Ti -> plane, then Tr -> registers, both scaled to true units
-            float tr[32];
-            {
-                uint32_t u1[32], u2[32];
-                tmem_ld32_nw(tq + col_im, u1);
-                tmem_ld32_nw(tq + 256 + col_im, u2);
-                tmem_ld_wait();
-#pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float4 cs = *reinterpret_cast<const float4*>(colscale + col_im + 4 * g);
-                    own[cc0 + 4 * g + 0] = (__uint_as_float(u1[4 * g + 0]) + __uint_as_float(u2[4 * g + 0])) * (sa * cs.x);
-                    own[cc0 + 4 * g + 1] = (__uint_as_float(u1[4 * g + 1]) + __uint_as_float(u2[4 * g + 1])) * (sa * cs.y);
-                    own[cc0 + 4 * g + 2] = (__uint_as_float(u1[4 * g + 2]) + __uint_as_float(u2[4 * g + 2])) * (sa * cs.z);
-                    own[cc0 + 4 * g + 3] = (__uint_as_float(u1[4 * g + 3]) + __uint_as_float(u2[4 * g + 3])) * (sa * cs.w);
-                }
-            }
-            {
-                uint32_t u1[32], u2[32];
-                tmem_ld32_nw(tq + col_re, u1);
-                tmem_ld32_nw(tq + 256 + col_re, u2);
-                tmem_ld_wait();
-#pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    const float4 cs = *reinterpret_cast<const float4*>(colscale + col_re + 4 * g);
-                    tr[4 * g + 0] = (__uint_as_float(u1[4 * g + 0]) + __uint_as_float(u2[4 * g + 0])) * (sa * cs.x);
-                    tr[4 * g + 1] = (__uint_as_float(u1[4 * g + 1]) + __uint_as_float(u2[4 * g + 1])) * (sa * cs.y);
-                    tr[4 * g + 2] = (__uint_as_float(u1[4 * g + 2]) + __uint_as_float(u2[4 * g + 2])) * (sa * cs.z);
-                    tr[4 * g + 3] = (__uint_as_float(u1[4 * g + 3]) + __uint_as_float(u2[4 * g + 3])) * (sa * cs.w);
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(&ctl->tempty[0]);              // tensor memory free: next tile's MMAs start
-            ebar();                                    // Ti plane complete
-            // TiTi and TrTi sums over this thread's b, and the diagonal Ti_aa
-            float sii = 0.f, sri = 0.f;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const float p = pbase[k * kEPitch];    // Ti[b0 + k][a] of walker-spin j
-                sii = fmaf(own[cc0 + k], p, sii);
-                sri = fmaf(tr[k], p, sri);
-            }
-            const float dim_ = diag ? own[cd] : 0.f;
-            ebar();                                    // every read of the Ti plane done
-#pragma unroll
-            for (int k = 0; k < 32; ++k) own[cc0 + k] = tr[k];
-            ebar();                                    // Tr plane complete
-            // TrTr sum continues the -TiTi one, so Re X is accumulated in one register
-            float srr = -sii;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) srr = fmaf(tr[k], pbase[k * kEPitch], srr);
-            const float dre = diag ? own[cd] : 0.f;
-            float v0 = dre, v1 = dim_, v2 = srr, v3 = 2.0f * sri;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-                v3 += __shfl_xor_sync(0xffffffffu, v3, o);
-            }
-            if (lane < 16) {   // ered[h][q][jj][v] for every walker-spin slot (zeros but j)
-                const int jj = lane >> 2, v = lane & 3;
-                const float val = jj != j ? 0.f : (v == 0 ? v0 : (v == 1 ? v1 : (v == 2 ? v2 : v3)));
-                ered[((h * 4 + q) * 4 + jj) * 4 + v] = val;
-            }
-            ebar();
-            // one thread per (n-block, walker-spin) output: sum over the n-block's quadrants and
-            // the four column quarters
-            if (et < G * G) {
-                const int ib = et / G, jo = et % G;
-                double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                for (int hh = 0; hh < 4; ++hh)
-                    for (int qq = ib * Q; qq < (ib + 1) * Q; ++qq) {
-                        const double* e = ered + ((hh * 4 + qq) * 4 + jo) * 4;
-                        s0 += e[0];
-                        s1 += e[1];
-                        s2 += e[2];
-                        s3 += e[3];
-                    }
-                const int n = ng * G + ib;
-                const int ws = wg * G + jo;
-                if (n < es.Nchol && ws < es.nws) {
-                    es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
-                    es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
-                }
-            }
-            ebar();   // ered, colscale and the plane are read before the next tile rewrites them
-        }
+        energy_epilogue<Np>(
+            es, ctl, plane, colscale, ered, blockIdx.x, es.tiles, gridDim.x,
+            [&](int64_t t, int& ng, int& wg) { energy_tile(es, t, ng, wg); },
+            [&]() { mbar_arrive(&ctl->tempty[0]); });
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(ctl->tmem_base, 512);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- energy kernel, CTA pairs
+// The same contraction on pairs of SMs (cta_group::2): a cluster of two CTAs computes the tiles
+// of two n-groups (rank r: n-group 2 p + r) against one walker-spin group with one M = 256 MMA
+// per K slice, issued by rank 0.  Each CTA stages its own 128 rows of Ltilde and half of the
+// tile's 256 Theta rows (rank r: rows 128 r .. 128 r + 127), so a stage holds 128 + 128 rows
+// per SM instead of 128 + 256: two thirds of the operand bytes per MMA of the one-CTA kernel,
+// and four stages in the same ring.  Each CTA's tensor memory receives its own n-group's
+// 128 x 256 accumulators, so the epilogue is the one-CTA kernel's.
+// Synchronisation: rank 0's full[] barriers count both CTAs' TMA bytes (rank 0 posts the
+// expected total); rank 0's MMA commits arrive on both CTAs' empty[] and tfull barriers
+// (multicast); every epilogue warp of both CTAs arrives on rank 0's tempty.
+template <int BK, int AP>
+__device__ void energy_producer2(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
+                                 const CUtensorMap* tAr, const CUtensorMap* tBh, const CUtensorMap* tBl,
+                                 const EnergyShape& es, uint32_t rank) {
+    using C = EStage<BK, AP, 128>;
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t t = cluster_id_x(); t < es.tiles2 && ok; t += ncluster_x()) {
+        int ngp, wg;
+        energy_tile_rows(es, t, es.n_pairs, ngp, wg);
+        const int ng = 2 * ngp + (int)rank;
+        for (int kb = 0; kb < es.nk; ++kb, ++g) {
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
+            if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
+            uint8_t* s = sbase + (size_t)st * C::kStageBytes;
+            if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
+            const uint32_t fb = mapa_shared(&ctl->full[st], 0);
+            const int x = kb * BK;
+            tma_load_2d_pair(s, tAh, fb, x, ng * 128);
+            tma_load_2d_pair(s + C::kABytes, tAl, fb, x, ng * 128);
+            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, tAr, fb, x, ng * 128);
+            tma_load_2d_pair(s + C::kBOff, tBh, fb, x, wg * 256 + (int)rank * 128);
+            tma_load_2d_pair(s + C::kBOff + C::kBBytes, tBl, fb, x, wg * 256 + (int)rank * 128);
+        }
+    }
+    if (!ok) {
+        if (rank == 0) {
+            const int64_t first = g > C::kStages ? g - C::kStages : 0;
+            for (int64_t j = first; j < g; ++j)
+                wait_drain(&ctl->full[j % C::kStages], (uint32_t)((j / C::kStages) & 1));
+        } else {
+            // the peer cannot wait on rank 0's barriers: give its copies in flight time to land
+            const long long t0 = clock64();
+            while (clock64() - t0 < (1LL << 22)) {
+            }
+        }
+    }
+}
+
+template <int BK, int AP>
+__device__ void energy_mma2(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es) {
+    using C = EStage<BK, AP, 128>;
+    constexpr uint32_t idesc = idesc_bf16(256, 256, true);   // fp16 planes, M = 256 over the pair, N = 256
+    const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
+    int64_t g = 0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t t = cluster_id_x(); t < es.tiles2 && ok; t += ncluster_x(), ++it) {
+        int ngp, wg;
+        energy_tile_rows(es, t, es.n_pairs, ngp, wg);
+        bool lolo = es.lolo != 0;
+        if (es.lolo_group) {
+            lolo = es.lolo_group[2 * ngp] != 0;
+            if (2 * ngp + 1 < es.n_groups) lolo = lolo || es.lolo_group[2 * ngp + 1] != 0;
+        }
+        if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < es.nk; ++kb, ++g) {
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
+            if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(sbase + (size_t)st * C::kStageBytes);
+            const uint32_t sal = sa + C::kABytes, sar = sa + 2 * C::kABytes;
+            const uint32_t sb = sa + C::kBOff, sbl = sb + C::kBBytes;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                energy_products<AP>(
+                    [&](uint32_t d, uint64_t a, uint64_t b, uint32_t c) { mma_f16_pair(d, a, b, idesc, c); }, d1, d2,
+                    edesc<BK>(sa + off), edesc<BK>(sal + off), edesc<BK>(sar + off), edesc<BK>(sb + off),
+                    edesc<BK>(sbl + off), (kb | kk) != 0 ? 1u : 0u, lolo);
+            }
+            mma_commit_pair(&ctl->empty[st], 3);   // the stage is free in both CTAs
+        }
+        if (!ok) break;
+        mma_commit_pair(&ctl->tfull[0], 3);        // both CTAs' accumulators are complete
+    }
+    mma_commit_pair(&ctl->done, 1);
+    wait_drain(&ctl->done, 0);
+}
+
+template <int Np, int BK, int AP>
+__global__ void __launch_bounds__(kEThreads, 1)
+    tc_energy_pair_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                          const __grid_constant__ CUtensorMap tAr, const __grid_constant__ CUtensorMap tBh,
+                          const __grid_constant__ CUtensorMap tBl, EnergyShape es, unsigned* flags) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    using C = EStage<BK, AP, 128>;
+    float* plane = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
+    float* colscale = plane + kETileFloats;
+    double* ered = reinterpret_cast<double*>(colscale + 256);
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(ered + 256);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&tAh);
+        tma_prefetch_desc(&tAl);
+        if (AP == 3) tma_prefetch_desc(&tAr);
+        tma_prefetch_desc(&tBh);
+        tma_prefetch_desc(&tBl);
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::kStages; ++i) {
+            mbar_init(&ctl->full[i], 1);
+            mbar_init(&ctl->empty[i], 1);
+        }
+        mbar_init(&ctl->tfull[0], 1);
+        mbar_init(&ctl->tempty[0], 2 * (kEEpi / 32));   // one arrival per epilogue warp of both CTAs
+        mbar_init(&ctl->done, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist before any copy or arrival reaches them
+    if (warp == 1) {
+        tmem_alloc_pair(&ctl->tmem_base, 512);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    cluster_sync();   // tensor memory allocated in both CTAs before the first MMA
+
+    if (warp == 0) {
+        if (lane == 0) energy_producer2<BK, AP>(sbase, ctl, &tAh, &tAl, &tAr, &tBh, &tBl, es, rank);
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) energy_mma2<BK, AP>(sbase, ctl, es);
+    } else {
+        const uint32_t tempty0 = mapa_shared(&ctl->tempty[0], 0);
+        energy_epilogue<Np>(
+            es, ctl, plane, colscale, ered, cluster_id_x(), es.tiles2, ncluster_x(),
+            [&](int64_t t, int& ng, int& wg) {
+                int ngp;
+                energy_tile_rows(es, t, es.n_pairs, ngp, wg);
+                ng = 2 * ngp + (int)rank;
+            },
+            [&]() { mbar_arrive_cluster(tempty0); });
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // both CTAs are done with tensor memory and each other's shared memory
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(ctl->tmem_base, 512);
+    }
+    if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- energy kernel, many systems
+// One persistent launch for the energy contractions of several independent systems (a batch of
+// uneven problems): a work list of pair tiles (system, n-group pair, walker-spin group) over
+// every system, each system with its own operands (tensor maps kept in global memory), K,
+// Np and outputs.  Per tile the arithmetic, and its order, are the single-system CTA-pair
+// kernel's; only the tile's source changes.
+template <int BK, int AP>
+__device__ void energy_producer_multi(uint8_t* sbase, SharedCtl* ctl, const EnergySys* sys, const EnergyWork* work,
+                                      int64_t nwork, uint32_t rank) {
+    using C = EStage<BK, AP, 128>;
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t t = cluster_id_x(); t < nwork && ok; t += ncluster_x()) {
+        const EnergyWork w = work[t];
+        const EnergySys* S = sys + w.sys;
+        const int nk = S->es.nk;
+        const int ng = 2 * w.ngp + (int)rank;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
+            if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
+            uint8_t* s = sbase + (size_t)st * C::kStageBytes;
+            if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
+            const uint32_t fb = mapa_shared(&ctl->full[st], 0);
+            const int x = kb * BK;
+            tma_load_2d_pair(s, &S->map[0], fb, x, ng * 128);
+            tma_load_2d_pair(s + C::kABytes, &S->map[1], fb, x, ng * 128);
+            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, &S->map[2], fb, x, ng * 128);
+            tma_load_2d_pair(s + C::kBOff, &S->map[3], fb, x, w.wg * 256 + (int)rank * 128);
+            tma_load_2d_pair(s + C::kBOff + C::kBBytes, &S->map[4], fb, x, w.wg * 256 + (int)rank * 128);
+        }
+    }
+    if (!ok) {
+        if (rank == 0) {
+            const int64_t first = g > C::kStages ? g - C::kStages : 0;
+            for (int64_t j = first; j < g; ++j)
+                wait_drain(&ctl->full[j % C::kStages], (uint32_t)((j / C::kStages) & 1));
+        } else {
+            const long long t0 = clock64();
+            while (clock64() - t0 < (1LL << 22)) {
+            }
+        }
+    }
+}
+
+template <int BK, int AP>
+__device__ void energy_mma_multi(uint8_t* sbase, SharedCtl* ctl, const EnergySys* sys, const EnergyWork* work,
+                                 int64_t nwork) {
+    using C = EStage<BK, AP, 128>;
+    constexpr uint32_t idesc = idesc_bf16(256, 256, true);
+    const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
+    int64_t g = 0;
+    int it = 0;
+    bool ok = true;
+    for (int64_t t = cluster_id_x(); t < nwork && ok; t += ncluster_x(), ++it) {
+        const EnergyWork w = work[t];
+        const EnergyShape& es = sys[w.sys].es;
+        bool lolo = es.lolo != 0;
+        if (es.lolo_group) {
+            lolo = es.lolo_group[2 * w.ngp] != 0;
+            if (2 * w.ngp + 1 < es.n_groups) lolo = lolo || es.lolo_group[2 * w.ngp + 1] != 0;
+        }
+        const int nk = es.nk;
+        if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+            const int st = (int)(g % C::kStages);
+            const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
+            if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(sbase + (size_t)st * C::kStageBytes);
+            const uint32_t sal = sa + C::kABytes, sar = sa + 2 * C::kABytes;
+            const uint32_t sb = sa + C::kBOff, sbl = sb + C::kBBytes;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint32_t off = kk * 32;
+                energy_products<AP>(
+                    [&](uint32_t d, uint64_t a, uint64_t b, uint32_t c) { mma_f16_pair(d, a, b, idesc, c); }, d1, d2,
+                    edesc<BK>(sa + off), edesc<BK>(sal + off), edesc<BK>(sar + off), edesc<BK>(sb + off),
+                    edesc<BK>(sbl + off), (kb | kk) != 0 ? 1u : 0u, lolo);
+            }
+            mma_commit_pair(&ctl->empty[st], 3);
+        }
+        if (!ok) break;
+        mma_commit_pair(&ctl->tfull[0], 3);
+    }
+    mma_commit_pair(&ctl->done, 1);
+    wait_drain(&ctl->done, 0);
+}
+
+template <int BK, int AP>
+__global__ void __launch_bounds__(kEThreads, 1)
+    tc_energy_multi_kernel(const EnergySys* __restrict__ sys, const EnergyWork* __restrict__ work, int64_t nwork,
+                           unsigned* flags) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    using C = EStage<BK, AP, 128>;
+    float* plane = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
+    float* colscale = plane + kETileFloats;
+    double* ered = reinterpret_cast<double*>(colscale + 256);
+    SharedCtl* ctl = reinterpret_cast<SharedCtl*>(ered + 256);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::kStages; ++i) {
+            mbar_init(&ctl->full[i], 1);
+            mbar_init(&ctl->empty[i], 1);
+        }
+        mbar_init(&ctl->tfull[0], 1);
+        mbar_init(&ctl->tempty[0], 2 * (kEEpi / 32));
+        mbar_init(&ctl->done, 1);
+        ctl->abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    cluster_sync();
+    if (warp == 1) {
+        tmem_alloc_pair(&ctl->tmem_base, 512);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    cluster_sync();
+
+    if (warp == 0) {
+        if (lane == 0) energy_producer_multi<BK, AP>(sbase, ctl, sys, work, nwork, rank);
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) energy_mma_multi<BK, AP>(sbase, ctl, sys, work, nwork);
+    } else {
+        const uint32_t tempty0 = mapa_shared(&ctl->tempty[0], 0);
+        auto release = [&]() { mbar_arrive_cluster(tempty0); };
+        int it = 0;
+        for (int64_t t = cluster_id_x(); t < nwork; t += ncluster_x(), ++it) {
+            const EnergyWork w = work[t];
+            const EnergyShape& es = sys[w.sys].es;
+            const int ng = 2 * w.ngp + (int)rank;
+            bool ok;
+            switch (es.Np) {
+                case 32: ok = energy_epilogue_tile<32>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
+                case 64: ok = energy_epilogue_tile<64>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
+                default: ok = energy_epilogue_tile<128>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
+            }
+            if (!ok) break;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(ctl->tmem_base, 512);
     }
     if (threadIdx.x == 0 && ctl->abort) atomicOr(flags, FLAG_TIMEOUT);
 }
@@ -763,9 +1126,11 @@ __device__ __forceinline__ void store4h(__half* p, const __half (&h)[4]) {
     *reinterpret_cast<uint2*>(p) = u;
 }
 
+// With `rnd` set, also r = fp16(x/scale) (the rounded plane of the energy contraction's
+// three rounded products).
 template <typename Src>
 __global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t src_stride, int64_t rows, int64_t K,
-                                                         __half* hi, __half* lo, float* scale) {
+                                                         __half* hi, __half* lo, float* scale, __half* rnd) {
     const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
@@ -792,16 +1157,18 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t
         for (int64_t k = 4 * lane; k < K; k += 128) {
             double v[4];
             load4(x + k, v);
-            __half h[4], l[4];
+            __half h[4], l[4], rr[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const double y = v[q] * inv;   // |y| < 2048
                 const double s1 = rint(y);
                 h[q] = __double2half(s1);
                 l[q] = __double2half(y - s1);
+                rr[q] = __double2half(y);
             }
             store4h(hi + r * K + k, h);
             store4h(lo + r * K + k, l);
+            if (rnd) store4h(rnd + r * K + k, rr);
         }
     } else {
         for (int64_t k = lane; k < K; k += 32) {
@@ -809,6 +1176,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t
             const double s1 = rint(y);
             hi[r * K + k] = __double2half(s1);
             lo[r * K + k] = __double2half(y - s1);
+            if (rnd) rnd[r * K + k] = __double2half(y);
         }
     }
 }
@@ -1230,8 +1598,11 @@ size_t gemm_smem() {
     return 1024 + (size_t)Cfg<BN>::kStages * Cfg<BN>::kStageBytes + sizeof(SharedCtl);
 }
 
+template <int BK, int AP, int BR>
 size_t energy_smem() {
-    return 1024 + (size_t)kEStageRing + (size_t)kETileFloats * 4 + 256 * 4 + 256 * 8 + sizeof(SharedCtl);
+    using C = EStage<BK, AP, BR>;
+    return 1024 + (size_t)C::kStages * C::kStageBytes + (size_t)kETileFloats * 4 + 256 * 4 + 256 * 8 +
+           sizeof(SharedCtl);
 }
 
 int g_num_sms = 0;
@@ -1249,20 +1620,51 @@ int launch_gemm(const CUtensorMap* m, const TileShape& sh, const EpiParams& epi,
     return AFQMC_OK;
 }
 
-template <int Np, int BK>
+template <int Np, int BK, int AP>
 int launch_energy(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
-    const size_t sm = energy_smem();
-    cudaFuncSetAttribute(tc_energy_kernel<Np, BK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = energy_smem<BK, AP, 256>();
+    cudaFuncSetAttribute(tc_energy_kernel<Np, BK, AP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
     const int grid = (int)std::min<int64_t>(es.tiles, cap);
     count_launch();
-    tc_energy_kernel<Np, BK><<<grid, kEThreads, sm, st>>>(m[0], m[1], m[2], m[3], es, flags);
+    tc_energy_kernel<Np, BK, AP><<<grid, kEThreads, sm, st>>>(m[0], m[1], m[2], m[3], m[4], es, flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy launch: ") + cudaGetErrorString(e));
     return AFQMC_OK;
 }
 
 }  // namespace
+
+template <int Np, int BK, int AP>
+int launch_energy_pair(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
+    auto kern = tc_energy_pair_kernel<Np, BK, AP>;
+    const size_t sm = energy_smem<BK, AP, 128>();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kEThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(2 * (tc_num_sms() / 2)));
+    int pairs = 0;   // CTA pairs that fit on the GPU at once (one CTA per SM)
+    if (cudaOccupancyMaxActiveClusters(&pairs, kern, &cfg) != cudaSuccess || pairs < 1) {
+        cudaGetLastError();
+        pairs = tc_num_sms() / 2;
+    }
+    if (launch_policy().grid_cap > 0) pairs = std::max(1, std::min(pairs, launch_policy().grid_cap / 2));
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(es.tiles2, pairs)));
+    count_launch();
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], m[4], es, flags);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy (CTA pairs) launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
 
 int tc_num_sms() {
     if (!g_num_sms) {
@@ -1307,20 +1709,29 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
     return launch_gemm<128, false>(m, sh, epi, flags, st);
 }
 
-int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
-              cplx* X_out, int terms, const uint8_t* lolo_group, unsigned* flags, cudaStream_t st) {
-    if (terms != 3 && terms != 4) return fail(AFQMC_ERR_BADARG, "tc_energy: terms must be 3 or 4");
+namespace {
+
+// Validation, tensor maps and shape of one energy contraction (brows: Theta rows per TMA box,
+// 256 for one CTA per tile, 128 for CTA pairs).
+int energy_setup(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
+                 cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, int BK, int brows,
+                 CUtensorMap* m, EnergyShape& es) {
+    if (terms != kEnergyThree && terms != kEnergyFour && terms != kEnergyRounded)
+        return fail(AFQMC_ERR_BADARG, "tc_energy: terms must be 3, 4 or the rounded three");
+    if (terms == kEnergyRounded && !Lt_round)
+        return fail(AFQMC_ERR_BADARG, "tc_energy: rounded products need the rounded Ltilde plane");
     if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
     if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
-    const int BK = launch_policy().energy_bk != 0 ? launch_policy().energy_bk : kEBKDefault;
+    const bool rounded = terms == kEnergyRounded;
     const int swz = 2 * BK;   // bytes per swizzled row of the K chunk
-    CUtensorMap m[4];
     AFQMC_TRY(make_map(&m[0], Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, swz));
     AFQMC_TRY(make_map(&m[1], Lt.lo, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false, true, swz));
-    AFQMC_TRY(make_map(&m[2], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, swz));
-    AFQMC_TRY(make_map(&m[3], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, 256, false, true, swz));
-    EnergyShape es;
+    AFQMC_TRY(make_map(&m[2], rounded ? Lt_round : Lt.hi, M, (int64_t)Nchol * Np, 1, Lt.row_stride, 0, 128, false,
+                       true, swz));
+    AFQMC_TRY(make_map(&m[3], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, brows, false, true, swz));
+    AFQMC_TRY(make_map(&m[4], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, brows, false, true, swz));
+    es = EnergyShape{};
     es.Np = Np;
     es.Q = Np / 32;
     es.G = 128 / Np;
@@ -1331,25 +1742,110 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     es.ws_super = std::min(es.ws_groups, launch_policy().energy_ws_super > 0 ? launch_policy().energy_ws_super
                                                                                 : kEWsSuperDefault);
     es.tiles = (int64_t)es.n_groups * es.ws_groups;
+    es.n_pairs = (es.n_groups + 1) / 2;
+    es.tiles2 = (int64_t)es.n_pairs * es.ws_groups;
     es.nk = M / BK;
-    es.lolo = terms == 4 ? 1 : 0;
-    es.lolo_group = lolo_group;
+    es.lolo = terms == kEnergyFour ? 1 : 0;
+    es.lolo_group = rounded ? nullptr : lolo_group;
     es.a_scale = Lt.scale;
     es.b_scale = ThetaT.scale;
     es.t_out = t_out;
     es.X_out = X_out;
+    return AFQMC_OK;
+}
+
+template <int BK, int AP>
+int launch_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nwork, unsigned* flags,
+                        cudaStream_t st) {
+    auto kern = tc_energy_multi_kernel<BK, AP>;
+    const size_t sm = energy_smem<BK, AP, 128>();
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kEThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)(2 * (tc_num_sms() / 2)));
+    int pairs = 0;
+    if (cudaOccupancyMaxActiveClusters(&pairs, kern, &cfg) != cudaSuccess || pairs < 1) {
+        cudaGetLastError();
+        pairs = tc_num_sms() / 2;
+    }
+    if (launch_policy().grid_cap > 0) pairs = std::max(1, std::min(pairs, launch_policy().grid_cap / 2));
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(nwork, pairs)));
+    count_launch();
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, sys, work, nwork, flags);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy_multi launch: ") + cudaGetErrorString(e));
+    return AFQMC_OK;
+}
+
+}  // namespace
+
+int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
+              cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, unsigned* flags,
+              cudaStream_t st) {
+    const int BK = launch_policy().energy_bk != 0 ? launch_policy().energy_bk : kEBKDefault;
+    const bool pair = launch_policy().energy_pair != 0;
+    const bool rounded = terms == kEnergyRounded;
+    CUtensorMap m[5];
+    EnergyShape es;
+    AFQMC_TRY(energy_setup(Lt, ThetaT, Np, Nchol, nws, M, t_out, X_out, terms, lolo_group, Lt_round, BK,
+                           pair ? 128 : 256, m, es));
+#define AFQMC_ENERGY_LAUNCH(NP, BKV, APV) \
+    (pair ? launch_energy_pair<NP, BKV, APV>(m, es, flags, st) : launch_energy<NP, BKV, APV>(m, es, flags, st))
+#define AFQMC_ENERGY_NP(BKV, APV)                                        \
+    switch (Np) {                                                       \
+        case 32: return AFQMC_ENERGY_LAUNCH(32, BKV, APV);              \
+        case 64: return AFQMC_ENERGY_LAUNCH(64, BKV, APV);              \
+        default: return AFQMC_ENERGY_LAUNCH(128, BKV, APV);             \
+    }
     if (BK == 32) {
-        switch (Np) {
-            case 32: return launch_energy<32, 32>(m, es, flags, st);
-            case 64: return launch_energy<64, 32>(m, es, flags, st);
-            default: return launch_energy<128, 32>(m, es, flags, st);
+        if (rounded) AFQMC_ENERGY_NP(32, 3)
+        AFQMC_ENERGY_NP(32, 2)
+    }
+    if (rounded) AFQMC_ENERGY_NP(16, 3)
+    AFQMC_ENERGY_NP(16, 2)
+#undef AFQMC_ENERGY_NP
+#undef AFQMC_ENERGY_LAUNCH
+}
+
+int tc_energy_describe(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
+                       cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, int BK,
+                       EnergySys* out) {
+    if (BK != 16 && BK != 32) return fail(AFQMC_ERR_BADARG, "tc_energy_describe: BK must be 16 or 32");
+    return energy_setup(Lt, ThetaT, Np, Nchol, nws, M, t_out, X_out, terms, lolo_group, Lt_round, BK, 128, out->map,
+                        out->es);
+}
+
+void energy_work_list(const EnergySys* sys, int nsys, std::vector<EnergyWork>& out) {
+    out.clear();
+    for (int s = 0; s < nsys; ++s) {
+        const EnergyShape& es = sys[s].es;
+        for (int64_t t = 0; t < es.tiles2; ++t) {   // the single-system tile order (L2 windows)
+            const int64_t per_super = (int64_t)es.ws_super * es.n_pairs;
+            const int64_t sup = t / per_super, rem = t % per_super;
+            const int64_t first = sup * es.ws_super;
+            const int width = (int)std::min<int64_t>(es.ws_groups - first, es.ws_super);
+            out.push_back(EnergyWork{s, (int)(rem / width), (int)(first + rem % width), 0});
         }
     }
-    switch (Np) {
-        case 32: return launch_energy<32, 16>(m, es, flags, st);
-        case 64: return launch_energy<64, 16>(m, es, flags, st);
-        default: return launch_energy<128, 16>(m, es, flags, st);
-    }
+}
+
+int tc_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nwork, int BK, int terms, unsigned* flags,
+                    cudaStream_t st) {
+    if (nwork <= 0) return AFQMC_OK;
+    const bool rounded = terms == kEnergyRounded;
+    if (BK == 32) return rounded ? launch_energy_multi<32, 3>(sys, work, nwork, flags, st)
+                                 : launch_energy_multi<32, 2>(sys, work, nwork, flags, st);
+    return rounded ? launch_energy_multi<16, 3>(sys, work, nwork, flags, st)
+                   : launch_energy_multi<16, 2>(sys, work, nwork, flags, st);
 }
 
 void select_lolo_groups(const double* nrm, int nch, int G, double eta, uint8_t* flags) {
@@ -1574,11 +2070,12 @@ void taylor_step_ff(const float* Ch, const float* Cl, float s_hi, float s_lo, fl
 }
 
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
-                cudaStream_t st) {
+                cudaStream_t st, bf16* rounded) {
     if (rows <= 0) return;
     count_launch();
     split_rows_kernel<double><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
-        src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale);
+        src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale,
+        reinterpret_cast<__half*>(rounded));
 }
 
 void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,

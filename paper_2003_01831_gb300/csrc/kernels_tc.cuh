@@ -5,6 +5,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace afqmc {
@@ -120,15 +122,67 @@ void taylor_step_ff(const float* Ch, const float* Cl, float s_hi, float s_lo, fl
 int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, int64_t rows, int64_t cols,
             int64_t K, int nbatch, const EpiParams& epi, int BN, bool exact, unsigned* flags, cudaStream_t st);
 
+// Shape, operands and outputs of one fused energy contraction (kernels_tc.cu).
+struct EnergyShape {
+    int Np, Q, G;
+    int Nchol, nws;
+    int n_groups, ws_groups;
+    int ws_super;     // ws groups per L2 super-block
+    int64_t tiles;
+    int n_pairs;      // CTA-pair kernel: pairs of n-groups (ceil(n_groups / 2))
+    int64_t tiles2;   // CTA-pair kernel: pair tiles (n_pairs x ws_groups)
+    int nk;
+    int lolo;               // 1: also form lo*lo (four products), 0: three
+    const uint8_t* lolo_group;   // if set: per n-group choice (1: four products, 0: three)
+    const float* a_scale;   // [Nchol*Np]
+    const float* b_scale;   // [nws*2*Np]
+    cplx* t_out;
+    cplx* X_out;
+};
+
+// One system of a multi-system energy contraction (device array, 64-byte aligned): tensor maps
+// of Ltilde hi, lo, rounded (hi again without rounded products) and Theta^T hi, lo (boxes of
+// 128 Theta rows: the CTA-pair form), and its shape.
+struct EnergySys {
+    CUtensorMap map[5];
+    EnergyShape es;
+};
+// One pair tile of a multi-system energy contraction: system, n-group pair, walker-spin group.
+struct EnergyWork {
+    int sys, ngp, wg, pad;
+};
+
+// Split products of the fused energy contraction (row-scaled operands: y = x / scale,
+// hi = rint(y), lo = fp16(y - hi)):
+constexpr int kEnergyThree = 3;     // hi*hi (exact) + hi*lo + lo*hi
+constexpr int kEnergyFour = 4;      // hi*hi (exact) + hi*lo + lo*hi + lo*lo
+constexpr int kEnergyRounded = 5;   // hi*hi (exact) + r*lo + lo*hi, r = fp16(y) of Ltilde: three
+                                    // products, r carrying the leading part of lo*lo
+
 // Fused energy contraction: T_{n,ws} = Lt_n Theta_ws^T (Np x Np complex, Np | 128) for
 // all n and walker-spin pairs ws; emits t = Tr T and X = Tr(T T) per (ws, n) into
 // t_out/X_out [nws][Nchol] (complex FP64).  Lt: [Nchol*Np][M], ThetaT: [nws*2*Np][M]
 // (rows (ws, re/im, b)), both row-scaled; exact accumulation of the leading product.
-// terms = 3 (hi*hi exact, hi*lo + lo*hi) or 4 (+ lo*lo) split products; lolo_group (device,
-// one byte per group of 128/Np Cholesky vectors, or null) overrides terms per group: 1 four
-// products, 0 three.
+// terms: kEnergyThree, kEnergyFour or kEnergyRounded (which needs Lt_round, the rounded plane
+// r of Lt, same layout).  lolo_group (device, one byte per group of 128/Np Cholesky vectors, or
+// null) overrides three/four products per group: 1 four products, 0 three.
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
-              cplx* X_out, int terms, const uint8_t* lolo_group, unsigned* flags, cudaStream_t st);
+              cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, unsigned* flags,
+              cudaStream_t st);
+
+// Fills `out` for one system of a multi-system energy contraction (arguments as tc_energy; BK
+// the K chunk every system of the launch uses).
+int tc_energy_describe(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
+                       cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, int BK,
+                       EnergySys* out);
+// The work list of a multi-system energy contraction: every pair tile of every system, each
+// system's tiles in its own L2 windows (walker-spin groups x every n-group pair).
+void energy_work_list(const EnergySys* sys, int nsys, std::vector<EnergyWork>& out);
+// One persistent launch (CTA pairs) over the work list: sys and work in device memory; every
+// system described with the same BK and the same product set (terms).  The arithmetic of every
+// tile is the single-system contraction's.
+int tc_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nwork, int BK, int terms, unsigned* flags,
+                    cudaStream_t st);
 
 // Cholesky-vector groups whose energy tiles form the lo*lo product (flags[g] = 1): every group
 // except those made only of the smallest vectors, by Frobenius norm nrm[n] of Ltilde_n, whose
@@ -146,7 +200,7 @@ int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, c
 // Row-scaled (fp16) split of `rows` rows of length K (row r at src + r*src_stride) into
 // hi/lo [rows][K] (row stride K) and scale[rows].  FP64 or FP32 source.
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
-                cudaStream_t st);
+                cudaStream_t st, bf16* rounded = nullptr);   // rounded (optional): r = fp16(x / scale)
 void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
                 cudaStream_t st);
 

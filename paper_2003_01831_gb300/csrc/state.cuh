@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "kernels_fp64.cuh"
+#include "kernels_tc.cuh"
 
 struct afqmc_ham {
     int device = 0;
@@ -16,6 +17,13 @@ struct afqmc_ham {
     // Built from general complex Cholesky vectors: L holds their Hermitian split (2 per input
     // vector, Nchol counts the split vectors).  Only the FP64 step supports it.
     bool cplx_L = false;
+    // THC Hamiltonian (afqmc_create_hamiltonian_thc): orbital values X [M][Nmu] at the
+    // interpolating points, kernel Mk [Nmu][Nmu] and its modified-Cholesky factor U [Nmu][Nchol]
+    // (Nchol = its rank).  L is not formed (null); only the FP64 step runs it.
+    int Nmu = 0;
+    double* X = nullptr;
+    double* Mk = nullptr;
+    double* U = nullptr;
     unsigned* flags = nullptr;
     int live_walker_sets = 0;
 };
@@ -52,6 +60,15 @@ struct Fp64Buffers {
     cplx* msd_E = nullptr;                 // E_L with trial D_I: [ND][W]
     cplx* msd_t = nullptr;                 // sum_s t_n with trial D_I: [ND][W][Nchol]
     unsigned* msd_flag = nullptr;          // status of the per-determinant inverses [0], local energies [1]
+    // THC Hamiltonians (Lt, LtT, T are then not allocated)
+    cplx* Yt[2] = {nullptr, nullptr};      // Psi_s^+ X: [N_s][Nmu]
+    cplx* Z[2] = {nullptr, nullptr};       // Theta_s^T X: [W][N_s][Nmu]
+    cplx* gs[2] = {nullptr, nullptr};      // densities at the points, per spin: [W][Nmu]
+    cplx* ex[2] = {nullptr, nullptr};      // exchange sums per spin: [W]
+    cplx* Tthc = nullptr;                  // T = Yt^T Z for a chunk of walkers: [thc_wc][Nmu][Nmu]
+    cplx* dv = nullptr;                    // U c per walker: [W][Nmu]
+    cplx* XD = nullptr;                    // X diag(U c) for a chunk of walkers: [thc_wc][M][Nmu]
+    int thc_wc = 0;
 };
 
 }  // namespace afqmc
@@ -118,6 +135,18 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st);
 void tc_free(afqmc_walkers* wk);
 int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st);
 int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st);
+// The measurement's phases (tc_measure = pre, the energy contraction, post) and the description
+// of a walker set's energy contraction for a multi-system launch (step_tc.cu).
+int tc_measure_pre(afqmc_walkers* wk, cudaStream_t st);
+int tc_measure_post(afqmc_walkers* wk, bool measure, cudaStream_t st);
+int tc_energy_system(afqmc_walkers* wk, int BK, afqmc::EnergySys* out);
+// Phi_out = B T_K(sign i sqrt(tau) sum_n c_n L_n) B Phi_in (conj_c: with conj(c)) on the tensor
+// cores, both spins, transposed planar layout [W][2][2][N][M] (step_tc.cu).
+int tc_apply_propagator(afqmc_walkers* wk, const afqmc::cplx* c, bool conj_c, double sign, const double* Phi_in,
+                        double* Phi_out, cudaStream_t st);
+// Canonical walkers Phi[s] [W][M][N] (both spins) to / from the transposed planar layout.
+void tc_canon_to_T(afqmc_walkers* wk, afqmc::cplx* const* Phi, double* out_T, cudaStream_t st);
+void tc_T_to_canon(afqmc_walkers* wk, const double* in_T, afqmc::cplx* const* Phi, cudaStream_t st);
 int tc_qr(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st);

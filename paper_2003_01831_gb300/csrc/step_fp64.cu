@@ -45,12 +45,20 @@ void overlap(const cplx* Psi, const cplx* Phi, cplx* S, int M, int N, int W, cud
 int fp64_alloc(afqmc_walkers* wk) {
     Fp64Buffers& f = wk->f;
     const int M = wk->M, W = wk->W, nch = wk->Nchol, ND = wk->ND;
+    const int Nmu = wk->ham->Nmu;   // > 0: THC Hamiltonian
     for (int s = 0; s < 2; ++s) {
         const int N = wk->N[s];
         const size_t mn = (size_t)M * N;
         AFQMC_TRY(dalloc(&f.Psi[s], ND * mn));
-        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.Lt[s]), ND * (size_t)nch * mn));
-        AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.LtT[s]), ND * (size_t)nch * mn));
+        if (Nmu > 0) {
+            AFQMC_TRY(dalloc(&f.Yt[s], (size_t)N * Nmu));
+            AFQMC_TRY(dalloc(&f.Z[s], (size_t)W * N * Nmu));
+            AFQMC_TRY(dalloc(&f.gs[s], (size_t)W * Nmu));
+            AFQMC_TRY(dalloc(&f.ex[s], (size_t)W));
+        } else {
+            AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.Lt[s]), ND * (size_t)nch * mn));
+            AFQMC_TRY(dalloc(reinterpret_cast<cplx**>(&f.LtT[s]), ND * (size_t)nch * mn));
+        }
         AFQMC_TRY(dalloc(&f.ht[s], ND * mn));
         AFQMC_TRY(dalloc(&f.Phi[s], (size_t)W * mn));
         AFQMC_TRY(dalloc(&f.Pnew[s], (size_t)W * mn));
@@ -64,11 +72,19 @@ int fp64_alloc(afqmc_walkers* wk) {
     }
     AFQMC_TRY(dalloc(&f.Bh, (size_t)M * M * (wk->ham->cplx_L ? 2 : 1)));
     const int Nmax = std::max(wk->N[0], wk->N[1]);
-    const size_t per_n = (size_t)W * Nmax * Nmax * sizeof(cplx);
     const size_t budget = (size_t)512 << 20;
-    f.nc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nch, budget / std::max<size_t>(per_n, 1)));
-    f.nc = std::min(f.nc, 65535);
-    AFQMC_TRY(dalloc(&f.T, (size_t)f.nc * W * Nmax * Nmax));
+    if (Nmu > 0) {   // walker chunks of the THC densities T and of X diag(U c)
+        const size_t per_w = std::max((size_t)Nmu * Nmu, (size_t)M * Nmu) * sizeof(cplx);
+        f.thc_wc = (int)std::max<size_t>(1, std::min<size_t>((size_t)W, budget / per_w));
+        AFQMC_TRY(dalloc(&f.Tthc, (size_t)f.thc_wc * Nmu * Nmu));
+        AFQMC_TRY(dalloc(&f.XD, (size_t)f.thc_wc * M * Nmu));
+        AFQMC_TRY(dalloc(&f.dv, (size_t)W * Nmu));
+    } else {
+        const size_t per_n = (size_t)W * Nmax * Nmax * sizeof(cplx);
+        f.nc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nch, budget / std::max<size_t>(per_n, 1)));
+        f.nc = std::min(f.nc, 65535);
+        AFQMC_TRY(dalloc(&f.T, (size_t)f.nc * W * Nmax * Nmax));
+    }
     AFQMC_TRY(dalloc(&f.A, (size_t)W * M * M));
     if (ND > 1) {
         AFQMC_TRY(dalloc(&f.msd_cc, (size_t)ND));
@@ -84,11 +100,11 @@ void fp64_free(afqmc_walkers* wk) {
     Fp64Buffers& f = wk->f;
     for (int s = 0; s < 2; ++s) {
         void* ps[] = {f.Psi[s], f.Lt[s], f.LtT[s], f.ht[s], f.Phi[s], f.Pnew[s], f.Pa[s], f.Pb[s],
-                      f.S[s], f.ld[s], f.Theta[s], f.t[s], f.X[s]};
+                      f.S[s], f.ld[s], f.Theta[s], f.t[s], f.X[s], f.Yt[s], f.Z[s], f.gs[s], f.ex[s]};
         for (void* p : ps)
             if (p) cudaFree(p);
     }
-    void* more[] = {f.Bh, f.T, f.A, f.msd_cc, f.msd_ls, f.msd_E, f.msd_t, f.msd_flag};
+    void* more[] = {f.Bh, f.T, f.A, f.msd_cc, f.msd_ls, f.msd_E, f.msd_t, f.msd_flag, f.Tthc, f.dv, f.XD};
     for (void* p : more)
         if (p) cudaFree(p);
     f = Fp64Buffers{};
@@ -123,7 +139,37 @@ void measure_det(afqmc_walkers* wk, int I, bool measure, int W, cplx* logS_out, 
             zgemm(g, st);
         }
         if (s == 0 && wk->ev0 && timed) cudaEventRecord(wk->ev0, st);
-        if (measure) {
+        if (wk->ham->Nmu > 0) {
+            // THC: Z = Theta^T X, densities g_mu and (measuring) T = Yt^T Z with its exchange sum,
+            // then the force-bias traces t_n = sum_mu U_mu n g_mu of this spin
+            const int Nmu = wk->ham->Nmu;
+            GemmArgs z;
+            z.m = N; z.n = Nmu; z.k = M; z.nb1 = W;
+            z.A.ptr = f.Theta[s]; z.A.op = OP_T; z.A.ld = N; z.A.s1 = (int64_t)M * N;
+            z.B.ptr = wk->ham->X; z.B.real = true; z.B.ld = Nmu;
+            z.C = f.Z[s]; z.ldc = Nmu; z.sc1 = (int64_t)N * Nmu;
+            zgemm(z, st);
+            if (measure) {
+                for (int w0 = 0; w0 < W; w0 += f.thc_wc) {
+                    const int wc = std::min(f.thc_wc, W - w0);
+                    GemmArgs g;
+                    g.m = Nmu; g.n = Nmu; g.k = N; g.nb1 = wc;
+                    g.A.ptr = f.Yt[s]; g.A.op = OP_T; g.A.ld = Nmu;
+                    g.B.ptr = f.Z[s] + (int64_t)w0 * N * Nmu; g.B.ld = Nmu; g.B.s1 = (int64_t)N * Nmu;
+                    g.C = f.Tthc; g.ldc = Nmu; g.sc1 = (int64_t)Nmu * Nmu;
+                    zgemm(g, st);
+                    thc_exchange(f.Tthc, wc, Nmu, wk->ham->Mk, f.gs[s] + (int64_t)w0 * Nmu, f.ex[s] + w0, st);
+                }
+            } else {
+                thc_gdiag(f.Yt[s], f.Z[s], W, N, Nmu, f.gs[s], st);
+            }
+            GemmArgs t;
+            t.m = W; t.n = nch; t.k = Nmu;
+            t.A.ptr = f.gs[s]; t.A.ld = Nmu;
+            t.B.ptr = wk->ham->U; t.B.real = true; t.B.ld = nch;
+            t.C = f.t[s]; t.ldc = nch;
+            zgemm(t, st);
+        } else if (measure) {
             for (int n0 = 0; n0 < nch; n0 += f.nc) {
                 const int nc = std::min(f.nc, nch - n0);
                 GemmArgs g;   // T[c][w] = Lt_{n0+c} Theta_w
@@ -154,7 +200,8 @@ void measure_det(afqmc_walkers* wk, int I, bool measure, int W, cplx* logS_out, 
     a.W = W; a.M = M; a.Nchol = nch; a.Nup = wk->N[0]; a.Ndn = wk->N[1];
     for (int s = 0; s < 2; ++s) {
         a.ht[s] = f.ht[s] + (int64_t)I * M * wk->N[s]; a.Theta[s] = f.Theta[s]; a.t[s] = f.t[s];
-        a.X[s] = measure ? f.X[s] : nullptr;
+        a.X[s] = measure && wk->ham->Nmu == 0 ? f.X[s] : nullptr;
+        a.exch[s] = measure && wk->ham->Nmu > 0 ? f.ex[s] : nullptr;
     }
     a.E0 = wk->ham->E0; a.tau = wk->tau;
     a.fb_cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
@@ -196,7 +243,25 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
     Fp64Buffers& f = wk->f;
     const int M = wk->M, W = wk->W, nch = wk->Nchol;
     hs_coefficients(x, wk->xbar, wk->weight, W, nch, wk->coef, wk->flags, st);
-    {   // A_w = sum_n c[w][n] L_n
+    if (wk->ham->Nmu > 0) {   // THC: A_w = X diag(U c_w) X^T
+        const int Nmu = wk->ham->Nmu;
+        GemmArgs d;   // dv = c U^T   [W][Nmu]
+        d.m = W; d.n = Nmu; d.k = nch;
+        d.A.ptr = wk->coef; d.A.ld = nch;
+        d.B.ptr = wk->ham->U; d.B.real = true; d.B.op = OP_T; d.B.ld = nch;
+        d.C = f.dv; d.ldc = Nmu;
+        zgemm(d, st);
+        for (int w0 = 0; w0 < W; w0 += f.thc_wc) {
+            const int wc = std::min(f.thc_wc, W - w0);
+            thc_scale_columns(wk->ham->X, f.dv + (int64_t)w0 * Nmu, wc, M, Nmu, f.XD, st);
+            GemmArgs g;
+            g.m = M; g.n = M; g.k = Nmu; g.nb1 = wc;
+            g.A.ptr = f.XD; g.A.ld = Nmu; g.A.s1 = (int64_t)M * Nmu;
+            g.B.ptr = wk->ham->X; g.B.real = true; g.B.op = OP_T; g.B.ld = Nmu;
+            g.C = f.A + (int64_t)w0 * M * M; g.ldc = M; g.sc1 = (int64_t)M * M;
+            zgemm(g, st);
+        }
+    } else {   // A_w = sum_n c[w][n] L_n
         GemmArgs g;
         g.m = W; g.n = M * M; g.k = nch;
         g.A.ptr = wk->coef; g.A.ld = nch;

@@ -44,6 +44,7 @@ struct TcState {
     int N = 0, M = 0, Nchol = 0, W = 0;
     // static operands
     bf16 *Lt_h = nullptr, *Lt_l = nullptr;
+    bf16* Lt_r = nullptr;   // rounded plane r = fp16(Ltilde row / scale) of the rounded energy products
     float* Lt_s = nullptr;
     bf16 *Ltp_h = nullptr, *Ltp_l = nullptr;      // Ltilde rows n over all N*M entries, row-scaled
     float* Ltp_s = nullptr;
@@ -101,9 +102,11 @@ namespace {
 
 constexpr int kT = 256;
 // Split products of the energy contraction when the options leave it open: hi*hi (exact),
-// hi*lo, lo*hi and lo*lo.  The two-body energy is a difference of large Coulomb and exchange
-// sums, so at energies of ~1e3 Ha the lo*lo term is worth keeping.
-// Adaptive energy products: the lo*lo product is skipped for the smallest Cholesky vectors whose
+// r*lo and lo*hi with the rounded Ltilde plane r = fp16(y).  The two-body energy is a difference
+// of large Coulomb and exchange sums, so at energies of ~1e3 Ha the lo*lo term matters; r carries
+// its leading part at the cost of three products.
+// Adaptive energy products (energy_terms = 1): the lo*lo product is skipped for the smallest
+// Cholesky vectors whose
 // Frobenius norms ||Ltilde_n|| add up to at most this fraction of the total.  The dropped term is
 // ~2^-22 of |Ltilde_n| |Theta| per element, so the added error in every energy and force-bias
 // term is at most this fraction of the three-product error (which is 1.35 mHa in E_mix over 10
@@ -326,12 +329,13 @@ __global__ void __launch_bounds__(kT) ltilde_norm_kernel(const double* Lt, int64
     if (threadIdx.x == 0) nrm[blockIdx.x] = sqrt(red[0]);
 }
 // HS coefficients c [W][Nchol] complex -> planar rows [W][2][Nchol]
-__global__ void coef_planar_kernel(const cplx* c, int64_t W, int nch, double* out) {
+// planar [w][re/im][n] copy of c (im_sign = -1: of conj(c))
+__global__ void coef_planar_kernel(const cplx* c, int64_t W, int nch, double* out, double im_sign) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * nch) return;
     const int64_t w = i / nch, n = i % nch;
     out[(w * 2) * nch + n] = c[i].re;
-    out[(w * 2 + 1) * nch + n] = c[i].im;
+    out[(w * 2 + 1) * nch + n] = im_sign * c[i].im;
 }
 __global__ void fb_combine_kernel(const float* tFB, int64_t WS, int nch, cplx* t) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -756,6 +760,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     const int64_t NM = (int64_t)N * M, MM = (int64_t)M * M;
     AFQMC_TRY(talloc(s, &s->Lt_h, nch * NM));
     AFQMC_TRY(talloc(s, &s->Lt_l, nch * NM));
+    AFQMC_TRY(talloc(s, &s->Lt_r, nch * NM));
     AFQMC_TRY(talloc(s, &s->Lt_s, (int64_t)nch * N));
     AFQMC_TRY(talloc(s, &s->Ltp_h, nch * NM));
     AFQMC_TRY(talloc(s, &s->Ltp_l, nch * NM));
@@ -820,7 +825,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->E1, W));
     // static operands
     const double* Ltr = static_cast<const double*>(wk->f.Lt[0]);  // real [Nchol][N][M]
-    split_rows(Ltr, M, (int64_t)nch * N, M, s->Lt_h, s->Lt_l, s->Lt_s, st);
+    split_rows(Ltr, M, (int64_t)nch * N, M, s->Lt_h, s->Lt_l, s->Lt_s, st, s->Lt_r);
     {   // energy tiles that form lo*lo (adaptive energy products)
         const int G = 128 / N, ng = (nch + G - 1) / G;
         AFQMC_TRY(talloc(s, &s->lolo, ng));
@@ -885,6 +890,24 @@ int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st) {
     return refresh_inverse(wk, st);
 }
 
+void tc_canon_to_T(afqmc_walkers* wk, cplx* const* Phi, double* out_T, cudaStream_t st) {
+    TcState* s = wk->tc;
+    const int64_t n = (int64_t)s->W * s->M * s->N;
+    for (int sp = 0; sp < 2; ++sp) {
+        count_launch();
+        canon_to_phiT_kernel<<<nb(n), kT, 0, st>>>(Phi[sp], sp, s->W, s->M, s->N, out_T);
+    }
+}
+
+void tc_T_to_canon(afqmc_walkers* wk, const double* in_T, cplx* const* Phi, cudaStream_t st) {
+    TcState* s = wk->tc;
+    const int64_t n = (int64_t)s->W * s->M * s->N;
+    for (int sp = 0; sp < 2; ++sp) {
+        count_launch();
+        phiT_to_canon_kernel<<<nb(n), kT, 0, st>>>(in_T, sp, s->W, s->M, s->N, Phi[sp]);
+    }
+}
+
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
     TcState* s = wk->tc;
     if (!s) return AFQMC_OK;
@@ -896,9 +919,14 @@ int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
     return AFQMC_OK;
 }
 
-int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
+// Measurement of the mixed step in three phases, so that a batch of systems can run the energy
+// contractions of all its systems in one launch between the first and the last:
+//   tc_measure_pre:  S^-1 of the current walkers -> Theta^T (exact-mode GEMM) and its split;
+//   the contraction: tc_energy (measuring) or the force-bias-only GEMM;
+//   tc_measure_post: one-body energy, local energy and force bias.
+int tc_measure_pre(afqmc_walkers* wk, cudaStream_t st) {
     TcState* s = wk->tc;
-    const int N = s->N, M = s->M, W = s->W, WS = 2 * W, nch = s->Nchol;
+    const int N = s->N, M = s->M, W = s->W, WS = 2 * W;
     // S^-1 of the current walkers is kept from the step that produced them (the proposals'
     // inverse, committed with them) or recomputed after QR / initialisation
     count_launch();
@@ -919,13 +947,52 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
                           128, true, wk->flags, st));
         split_rows(s->ThT_f, M, (int64_t)WS * 2 * N, M, s->ThT_h, s->ThT_l, s->ThT_s, st);
     }
+    return AFQMC_OK;
+}
+
+namespace {
+// energy_terms: 0 = rounded three products (default), 1 = adaptive four/three, 3, 4
+int energy_terms_of(const afqmc_walkers* wk) {
+    const int et = wk->opts.energy_terms;
+    return et == 0 ? kEnergyRounded : (et == 1 ? kEnergyFour : et);
+}
+}  // namespace
+
+int tc_energy_system(afqmc_walkers* wk, int BK, EnergySys* out) {
+    TcState* s = wk->tc;
+    if (!s) return fail(AFQMC_ERR_BADARG, "energy_system: not a BF16X3 walker set");
+    const int N = s->N, M = s->M, WS = 2 * s->W, nch = s->Nchol;
+    return tc_energy_describe(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N, 1, s->Lt_s),
+                              smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N, 1, s->ThT_s), N, nch, WS, M, s->tE,
+                              s->XE, energy_terms_of(wk), wk->opts.energy_terms == 1 ? s->lolo : nullptr, s->Lt_r, BK,
+                              out);
+}
+
+int tc_measure_post(afqmc_walkers* wk, bool measure, cudaStream_t st) {
+    TcState* s = wk->tc;
+    const int N = s->N, M = s->M, W = s->W, nch = s->Nchol;
+    if (measure) {
+        count_launch();
+        e1_kernel<<<W, kT, 0, st>>>(wk->f.ht[0], wk->f.ht[1], s->ThT_f, M, N, s->E1);
+    }
+    const double cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
+    count_launch();
+    le_mixed_kernel<<<W, kT, 0, st>>>(s->E1, s->tE, s->XE, nch, wk->ham->E0, wk->tau, cap, measure ? 1 : 0, wk->E_L,
+                                      wk->xbar, wk->flags);
+    return AFQMC_OK;
+}
+
+int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
+    TcState* s = wk->tc;
+    const int N = s->N, M = s->M, W = s->W, WS = 2 * W, nch = s->Nchol;
+    AFQMC_TRY(tc_measure_pre(wk, st));
     const bool timed = !stream_capturing(st);
     if (wk->ev0 && timed) cudaEventRecord(wk->ev0, st);
     if (measure) {
         AFQMC_TRY(tc_energy(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N, 1, s->Lt_s),
                             smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N, 1, s->ThT_s), N, nch, WS, M, s->tE,
-                            s->XE, wk->opts.energy_terms > 0 ? wk->opts.energy_terms : 4,
-                            wk->opts.energy_terms > 0 ? nullptr : s->lolo, wk->flags, st));
+                            s->XE, energy_terms_of(wk), wk->opts.energy_terms == 1 ? s->lolo : nullptr, s->Lt_r,
+                            wk->flags, st));
     } else {
         // force bias only: t[ws][n] = sum_{a,k} ThetaT[ws][a][k] Ltilde[n][a][k], one exact-mode GEMM
         // with K = N*M over rows (ws, re/im) of Theta^T (row-scaled pair in the Pacc scratch)
@@ -947,24 +1014,22 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
         cudaEventRecord(wk->ev1, st);
         wk->ev_valid = true;
     }
-    if (measure) {
-        count_launch();
-        e1_kernel<<<W, kT, 0, st>>>(wk->f.ht[0], wk->f.ht[1], s->ThT_f, M, N, s->E1);
-    }
-    const double cap = wk->opts.weight_mode == AFQMC_WEIGHT_FREE ? 0.0 : wk->opts.fb_cap;
-    count_launch();
-    le_mixed_kernel<<<W, kT, 0, st>>>(s->E1, s->tE, s->XE, nch, wk->ham->E0, wk->tau, cap, measure ? 1 : 0, wk->E_L,
-                                      wk->xbar, wk->flags);
-    return AFQMC_OK;
+    return tc_measure_post(wk, measure, st);
 }
 
-int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st) {
+// Phi_out = B T_K(sign i sqrt(tau) A) B Phi_in for every walker and spin, with the HS potential
+// A = sum_n c_n L_n (conj_c: of conj(c)), B = exp(-tau h'/2): three-slice tensor-core GEMMs with
+// float-float intermediates, FP64 result.  Phi_in and Phi_out are in the transposed planar
+// layout of PhiT ([W][2][2][N][M]); they may not alias.  The forward step uses c = x - xbar and
+// sign = +1; back-propagation carries the trial through the adjoint B(k)^+ = B T_K(-i sqrt(tau)
+// A^+) B with A^+ = sum_n conj(c_n) L_n (real symmetric L_n).
+int tc_apply_propagator(afqmc_walkers* wk, const cplx* c, bool conj_c, double sign, const double* Phi_in,
+                        double* Phi_out, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, W = s->W, nch = s->Nchol;
     const int64_t MM = (int64_t)M * M;
-    hs_coefficients(x, wk->xbar, wk->weight, W, nch, wk->coef, wk->flags, st);
     count_launch();
-    coef_planar_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->coef, W, nch, s->cfp);
+    coef_planar_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(c, W, nch, s->cfp, conj_c ? -1.0 : 1.0);
     split3_rows(s->cfp, 2LL * W, nch, s->cf3[0], s->cf3[1], s->cf3[2], s->cf3_s, st);
     {   // A_w = sum_n c_wn L_n  -> float-float [W][M][2M], then its three slices
         EpiParams e;
@@ -981,7 +1046,7 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
     const int64_t rowsAll = (int64_t)W * 4 * N;
     const int64_t WS = 2LL * W;
     {   // P0 = B Phi -> Taylor sum (float-float), then the doubled operand of the first term
-        split3_rows(s->PhiT[s->cur], rowsAll, M, s->PhiT3[0], s->PhiT3[1], s->PhiT3[2], s->PhiT3_s, st);
+        split3_rows(Phi_in, rowsAll, M, s->PhiT3[0], s->PhiT3[1], s->PhiT3[2], s->PhiT3_s, st);
         EpiParams e;
         e.kind = EPI3_FF;
         e.rows_valid = rowsAll;
@@ -1007,24 +1072,32 @@ int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st)
         AFQMC_TRY(tc_gemm3(sp3(s->PD3, s->PD3_s, 2LL * M, 4LL * N, W), BatchMap{1, W},
                            sp3(s->A3, s->A3_s, 2LL * M, M, W), BatchMap{1, W}, 4LL * N, M, 2LL * M, W, e, wk->flags,
                            st));
-        // P_k = (i sqrt(tau) / k) C, Pacc += P_k, doubled operand of P_k for the next term
-        const double sk = sq / (double)k;
+        // P_k = (sign i sqrt(tau) / k) C, Pacc += P_k, doubled operand of P_k for the next term
+        const double sk = sign * sq / (double)k;
         const float sh = (float)sk, sl = (float)(sk - (double)sh);
         taylor_step_ff(s->C_hi, s->C_lo, sh, sl, s->Pacc_hi, s->Pacc_lo, WS, N, M, k < wk->opts.k_taylor, s->PD3[0],
                        s->PD3[1], s->PD3[2], s->PD3_s, st);
     }
-    const int nxt = s->cur ^ 1;
-    {   // Phi' = B Pacc  (FP64 master of the proposed walkers)
+    {   // Phi_out = B Pacc  (FP64)
         split3_rows_ff(s->Pacc_hi, s->Pacc_lo, rowsAll, M, s->Pacc3[0], s->Pacc3[1], s->Pacc3[2], s->Pacc3_s, st);
         EpiParams e;
         e.kind = EPI3_F64;
         e.rows_valid = rowsAll;
         e.cols_valid = M;
         e.ld = M;
-        e.out_f64 = s->PhiT[nxt];
+        e.out_f64 = Phi_out;
         AFQMC_TRY(tc_gemm3(sp3(s->Pacc3, s->Pacc3_s, M, rowsAll), BatchMap{}, sp3(s->Bh3, s->Bh3_s, M, M), BatchMap{},
                            rowsAll, M, M, 1, e, wk->flags, st));
     }
+    return AFQMC_OK;
+}
+
+int tc_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t st) {
+    TcState* s = wk->tc;
+    const int N = s->N, M = s->M, W = s->W, nch = s->Nchol;
+    hs_coefficients(x, wk->xbar, wk->weight, W, nch, wk->coef, wk->flags, st);
+    const int nxt = s->cur ^ 1;
+    AFQMC_TRY(tc_apply_propagator(wk, wk->coef, false, 1.0, s->PhiT[s->cur], s->PhiT[nxt], st));
     // the proposals' inverse is the next step's S^-1 for every accepted walker
     AFQMC_TRY(overlap_logdet(wk, nxt, true, s->S, s->ld, st));
     count_launch();
@@ -1059,7 +1132,7 @@ int tc_energy_products(afqmc_walkers* wk, double* mean) {
     TcState* s = wk->tc;
     if (!s) return fail(AFQMC_ERR_BADARG, "energy_products: not a BF16X3 walker set");
     const int t = wk->opts.energy_terms;
-    *mean = t > 0 ? (double)t : 3.0 + s->lolo_frac;
+    *mean = t == 1 ? 3.0 + s->lolo_frac : (t == 0 ? 3.0 : (double)t);
     return AFQMC_OK;
 }
 

@@ -17,12 +17,15 @@ class AFQMC:
     """Owns an ``afqmc_ham_t`` and an ``afqmc_wk_t``; release with ``close()``.
 
     With ``coeffs`` (complex [ND]) the trial is the expansion sum_I c_I |D_I>, and Psi_up /
-    Psi_dn hold the determinants ([ND, M, Nup] / [ND, M, Ndn])."""
+    Psi_dn hold the determinants ([ND, M, Nup] / [ND, M, Ndn]).  With ``thc=(X, Mk)`` the
+    Hamiltonian is in tensor-hypercontraction form (L is then ignored and may be None)."""
 
     def __init__(self, h, L, E0, Psi_up, Psi_dn, W, tau, Phi0=None, precision=api.PREC_FP64,
                  k_taylor=6, k_qr=5, fb_cap=1.0, weight_mode=api.WEIGHT_PHASELESS, walker_offset=0, energy_terms=0,
-                 stream=None, coeffs=None):
+                 stream=None, coeffs=None, thc=None):
         h = np.ascontiguousarray(h, dtype=np.float64)
+        if thc is not None:
+            L = np.zeros((1, 1, 1))
         # complex L: general complex Cholesky vectors, run as their 2 Nchol Hermitian-split
         # vectors (A_0, B_0, A_1, B_1, ...), which is what fields and Nchol refer to
         self.complex_L = np.iscomplexobj(L)
@@ -35,7 +38,12 @@ class AFQMC:
         self.W = int(W)
         self.weight_mode = weight_mode
         self.stream = stream
-        if self.complex_L:
+        if thc is not None:
+            X = np.ascontiguousarray(thc[0], dtype=np.float64)
+            Mk = np.ascontiguousarray(thc[1], dtype=np.float64)
+            self.ham = api.afqmc_create_hamiltonian_thc(h, X, Mk, E0, self.M, X.shape[1], stream)
+            self.Nchol = api.afqmc_hamiltonian_info(self.ham)[1]
+        elif self.complex_L:
             self.ham = api.afqmc_create_hamiltonian_complex(h, L, E0, self.M, L.shape[0], stream)
         else:
             self.ham = api.afqmc_create_hamiltonian(h, L, E0, self.M, self.Nchol, stream)

@@ -1,4 +1,4 @@
-"""Host-side choice of the adaptive energy products (afqmc_opts.energy_terms = 0): which groups
+"""Host-side choice of the adaptive energy products (afqmc_opts.energy_terms = 1): which groups
 of Cholesky vectors form the lo*lo split product.  Checked against the rule written out in
 numpy (drop the smallest vectors, by norm, while their norms add up to at most eta of the
 total; a group keeps four products if any of its vectors does).  No device work."""

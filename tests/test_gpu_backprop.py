@@ -6,7 +6,8 @@ FP64 path: the window estimate equals the oracle's to 1e-10 relative, for real a
 general complex Cholesky vectors, with a walker killed before the window, QR inside it, and
 a comb between its steps (the window follows the ancestry); a zero-length window gives the
 mixed estimate.  BF16X3 walker sets record the same shifted fields from their tensor-core
-step, so their estimate follows the FP64 one to the mixed path's accuracy.  The window's
+step and carry the trial back on the tensor cores, so their estimate follows the FP64 one and
+the oracle to the mixed path's accuracy.  The window's
 error states are reported, not guessed around."""
 import numpy as np
 import pytest
@@ -98,6 +99,38 @@ def test_bp_rdm1_bf16x3_follows_fp64():
         d = rel(G[api.PREC_BF16X3][s], G[api.PREC_FP64][s])
         print(f"spin {s}: BF16X3 vs FP64 back-propagated 1RDM, max rel diff {d:.2e}")
         assert d < 1e-5
+
+
+def test_bp_rdm1_bf16x3_matches_oracle():
+    """BF16X3 walker set (M=128, N=32+32): the forward steps and every back step run on the tensor
+    cores (the back steps through the forward step's three-slice propagation with conjugated
+    coefficients and -i sqrt(tau)); the estimate follows the oracle's window to the mixed path's
+    accuracy (bar 1e-5 relative), with a QR inside the window."""
+    rng = np.random.default_rng(8)
+    M, N, nch, W, tau, K = 128, 32, 96, 4, 0.005, 6
+    h, L, E0 = syn.make_hamiltonian(M, nch, rng)
+    Psi = syn.make_trial(h, N, N)
+    ham = O.Hamiltonian(h=h, L=L, E0=E0)
+    p = O.Params(tau=tau, k_taylor=K, k_qr=2)
+    B = O.half_one_body_propagator(ham, tau)
+    wk = O.init_walkers(ham, Psi, W)
+    x = rng.standard_normal((5, W, nch))
+    with AFQMC(h, L, E0, Psi[0], Psi[1], W, tau, k_taylor=K, k_qr=2, precision=api.PREC_BF16X3) as g:
+        for s in range(2):
+            O.step(ham, Psi, B, wk, x[s], p)
+        g.step(2, x[0:2])
+        g.bp_begin(3)
+        win = BP.Window(wk.Phi)
+        for s in (2, 3, 4):
+            O.step(ham, Psi, B, wk, x[s], p, record=win.coefs)
+        g.step(3, x[2:5])
+        G = g.bp_rdm1()
+    ref = win.estimate(L, Psi, B, wk.w, tau, K)
+    for s in range(2):
+        d = rel(G[s], ref[s])
+        print(f"spin {s}: BF16X3 back-propagated 1RDM vs oracle, max rel diff {d:.2e}")
+        assert d < 1e-5
+        assert abs(np.trace(G[s]) - N) < 1e-6
 
 
 def test_bp_window_errors():

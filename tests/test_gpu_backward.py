@@ -103,3 +103,36 @@ def test_autograd_function_matches_oracle():
     assert rel(Lt.grad.numpy(), ref[2]) < 1e-10
     E_ref = O.local_energy(O.Hamiltonian(h, L, E0), Psi, Phi)[0]
     assert rel(E.detach().numpy(), E_ref) < 1e-10
+
+
+def test_autograd_on_device_tensors_reuses_the_hamiltonian():
+    """CUDA tensors in, CUDA gradients out (no host round trip); two calls with the same L and h
+    share one library Hamiltonian, and changing L in place builds a new one."""
+    import torch
+    from paper_2003_01831_gb300 import autograd as A
+    M, N, nch, W = 12, 3, 30, 4
+    h, L, E0, Psi, Phi, dE, dS = instance(M, N, nch, W, 11)
+    dev = torch.device("cuda", 0)
+    Lt = torch.tensor(L, device=dev, requires_grad=True)
+    ht = torch.tensor(h, device=dev)
+    Ph = [torch.tensor(p, device=dev) for p in Phi]
+    ref = energy_logdet_backward(O.Hamiltonian(h, L, E0), Psi, Phi, dE, dS)
+    hams = []
+    for it in range(2):
+        Pu = torch.tensor(Psi[0], device=dev, requires_grad=True)
+        Pd = torch.tensor(Psi[1], device=dev, requires_grad=True)
+        E, lS = A.local_energy(Pu, Pd, Lt, ht, E0, Ph[0], Ph[1])
+        assert E.is_cuda and lS.is_cuda
+        loss = torch.sum(torch.real(torch.conj(torch.tensor(dE, device=dev)) * E +
+                                    torch.conj(torch.tensor(dS, device=dev)) * lS))
+        Lt.grad = None
+        loss.backward()
+        assert Pu.grad.is_cuda and Lt.grad.is_cuda
+        assert rel(Pu.grad.cpu().numpy(), ref[0]) < 1e-10
+        assert rel(Lt.grad.cpu().numpy(), ref[2]) < 1e-10
+        hams.append(A._cache["ham"])
+    assert hams[0] is hams[1]
+    with torch.no_grad():
+        Lt.mul_(1.0)                                 # in-place: new version, new Hamiltonian
+    A.local_energy(torch.tensor(Psi[0], device=dev), torch.tensor(Psi[1], device=dev), Lt, ht, E0, Ph[0], Ph[1])
+    assert A._cache["ham"] is not hams[0]

@@ -116,6 +116,32 @@ def test_mixed_batch_within_1mha_of_fp64():
     assert d.max() < MHA
 
 
+def test_energy_launch_forms_agree():
+    """One persistent energy launch over every system's tiles (K chunks of 32 or 16) and one
+    launch per system: the same tiles, the same arithmetic, the same trajectories.  The systems
+    pad to three different tile shapes (N' = 32, 64, 128), so one launch mixes them."""
+    import ctypes
+    dims = [syn.UnevenSystem(M=40, N=10, Nchol=200, W=9), syn.UnevenSystem(M=160, N=40, Nchol=96, W=7),
+            syn.UnevenSystem(M=400, N=100, Nchol=64, W=3)]
+    sysdefs = systems(dims, seed=13)
+    tau, k_qr, nsteps, seed = 0.01, 4, 6, 3
+    lib = api.lib()
+    lib.afqmc_debug_set_batch_energy.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    traces, energies = [], []
+    for multi, bk in ((1, 32), (1, 16), (0, 32)):
+        with Batch(sysdefs, tau, precision=api.PREC_BF16X3, k_qr=k_qr) as b:
+            assert lib.afqmc_debug_set_batch_energy(b.b, multi, bk) == 0
+            assert [int(b.info(s)[0][1]) for s in range(3)] == [32, 64, 128]
+            traces.append(b.step(nsteps, seed=seed, measure_every=1))
+            energies.append([b.energy(s)[0] for s in range(3)])
+            shape, _ = b.info(0)
+            assert int(shape[6]) == multi and int(shape[7]) == bk
+    for t, e in zip(traces[1:], energies[1:]):
+        assert rel(t, traces[0]) < 1e-12
+        for s in range(3):
+            assert rel(e[s], energies[0][s]) < 1e-12
+
+
 def test_autotune_restores_walkers():
     dims = [syn.UnevenSystem(M=64, N=32, Nchol=64, W=8), syn.UnevenSystem(M=45, N=11, Nchol=225, W=7),
             syn.UnevenSystem(M=33, N=8, Nchol=165, W=9)]

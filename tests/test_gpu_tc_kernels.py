@@ -34,25 +34,33 @@ def split(x):
     return hi, lo
 
 
-def split_rows(x):
+def split_rows(x, rounded=False):
     """Row-scaled split: scale = 2^(e-11) with ||x_row||_2 < 2^e, hi = rint(x/scale) (an
-    integer, |hi| <= 2048), lo = fp16(x/scale - hi).  Returns (hi*scale, lo*scale)."""
+    integer, |hi| <= 2048), lo = fp16(x/scale - hi).  Returns (hi*scale, lo*scale), and with
+    rounded=True also r*scale for the rounded plane r = fp16(x/scale)."""
     nrm = np.sqrt(np.sum(x * x, axis=-1, keepdims=True))
     e = np.frexp(np.where(nrm > 0, nrm, 1.0))[1]
     sc = np.where(nrm > 0, np.ldexp(1.0, e - 11), 1.0)
     y = x / sc
     hi = np.rint(y)
     lo = (y - hi).astype(np.float16).astype(np.float64)
+    if rounded:
+        return hi * sc, lo * sc, y.astype(np.float16).astype(np.float64) * sc
     return hi * sc, lo * sc
 
 
-def emul(A, B, exact=False, lolo=None):
+def emul(A, B, exact=False, lolo=None, rounded=False):
     """What the tensor cores form: hi*hi + hi*lo + lo*hi (plain) or + lo*lo (exact mode;
-    lolo=False drops that fourth product)."""
+    lolo=False drops that fourth product); rounded=True (exact mode): hi*hi + r*lo + lo*hi
+    with the rounded plane r of A."""
+    mm = lambda a, b: np.matmul(a, np.swapaxes(b, -1, -2))
+    if rounded:
+        Ah, Al, Ar = split_rows(A, rounded=True)
+        Bh, Bl = split_rows(B)
+        return mm(Ah, Bh) + mm(Ar, Bl) + mm(Al, Bh)
     sp = split_rows if exact else split
     Ah, Al = sp(A)
     Bh, Bl = sp(B)
-    mm = lambda a, b: np.matmul(a, np.swapaxes(b, -1, -2))
     C = mm(Ah, Bh) + mm(Ah, Bl) + mm(Al, Bh)
     if lolo is None:
         lolo = exact
@@ -72,7 +80,22 @@ def dbg():
     L.afqmc_debug_energy.restype = ctypes.c_int
     L.afqmc_debug_energy.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      vp, vp]
+    L.afqmc_debug_set_energy_variant.restype = ctypes.c_int
+    L.afqmc_debug_set_energy_variant.argtypes = [ctypes.c_int]
     return L
+
+
+def energy_call(dbg, Lt, Th, Np, Nchol, nws, M, terms, pair):
+    t = np.zeros((nws, Nchol), dtype=np.complex128)
+    X = np.zeros((nws, Nchol), dtype=np.complex128)
+    assert dbg.afqmc_debug_set_energy_variant(pair) == 0
+    try:
+        rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, terms, t.ctypes.data,
+                                    X.ctypes.data)
+    finally:
+        dbg.afqmc_debug_set_energy_variant(0)
+    assert rc == 0, api.afqmc_last_error()
+    return t, X
 
 
 @pytest.mark.parametrize("nb,rows,cols,K,BN", [
@@ -138,24 +161,28 @@ def test_exact_mode_integer_products_are_exact(dbg):
     assert np.array_equal(C, np.matmul(A, np.swapaxes(B, -1, -2)))
 
 
-@pytest.mark.parametrize("terms", [3, 4])
-@pytest.mark.parametrize("Np,Nchol,nws,M", [(128, 3, 2, 128), (64, 5, 3, 192), (32, 9, 5, 128), (128, 2, 3, 512)])
-def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M, terms):
+@pytest.mark.parametrize("pair", [0, 1])
+@pytest.mark.parametrize("terms", [3, 4, 5])
+@pytest.mark.parametrize("Np,Nchol,nws,M", [(128, 3, 2, 128), (64, 5, 3, 192), (32, 9, 5, 128), (128, 2, 3, 512),
+                                            (128, 41, 9, 256)])
+def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M, terms, pair):
+    """Both kernel forms (one CTA per tile; CTA pairs with M = 256 MMAs) and all three product
+    sets against their exact float64 emulation.  The shapes include an odd number of Cholesky
+    groups (the last pair's second CTA has no rows), ragged walker-spin groups, and more pair
+    tiles than the GPU holds at once (persistent loop, barrier phases wrapping)."""
     rng = np.random.default_rng(Np * 7 + Nchol)
     Lt = rng.standard_normal((Nchol, Np, M)) * 0.1
     Th = rng.standard_normal((nws, 2, Np, M)) * 0.1
-    t = np.zeros((nws, Nchol), dtype=np.complex128)
-    X = np.zeros((nws, Nchol), dtype=np.complex128)
-    rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, terms, t.ctypes.data,
-                                X.ctypes.data)
-    assert rc == 0, api.afqmc_last_error()
-    lolo = terms == 4
-    Tr = np.stack([emul(Lt, np.broadcast_to(Th[w, 0], (Nchol, Np, M)), exact=True, lolo=lolo) for w in range(nws)])
-    Ti = np.stack([emul(Lt, np.broadcast_to(Th[w, 1], (Nchol, Np, M)), exact=True, lolo=lolo) for w in range(nws)])
+    t, X = energy_call(dbg, Lt, Th, Np, Nchol, nws, M, terms, pair)
+    lolo, rnd = terms == 4, terms == 5
+    Tr = np.stack([emul(Lt, np.broadcast_to(Th[w, 0], (Nchol, Np, M)), exact=True, lolo=lolo, rounded=rnd)
+                   for w in range(nws)])
+    Ti = np.stack([emul(Lt, np.broadcast_to(Th[w, 1], (Nchol, Np, M)), exact=True, lolo=lolo, rounded=rnd)
+                   for w in range(nws)])
     T = Tr + 1j * Ti                                     # [nws, Nchol, Np, Np]: T[a][b] = Lt[a] . Th^T[b]
     t_ref = np.trace(T, axis1=2, axis2=3)
     X_ref = np.einsum("wnab,wnba->wn", T, T)
-    print(f"energy Np={Np}: t err {np.max(np.abs(t - t_ref)) / np.max(np.abs(t_ref)):.2e}, "
+    print(f"energy Np={Np} terms={terms} pair={pair}: t err {np.max(np.abs(t - t_ref)) / np.max(np.abs(t_ref)):.2e}, "
           f"X err {np.max(np.abs(X - X_ref)) / np.max(np.abs(X_ref)):.2e}")
     assert np.max(np.abs(t - t_ref)) < 2e-6 * np.max(np.abs(t_ref)) + 1e-9
     assert np.max(np.abs(X - X_ref)) < 2e-6 * np.max(np.abs(X_ref)) + 1e-9
@@ -242,3 +269,45 @@ def test_energy_tile_window_does_not_change_results(dbg):
         dbg.afqmc_debug_set_energy_window(0)
     for t, X in outs[1:]:
         assert np.array_equal(t, outs[0][0]) and np.array_equal(X, outs[0][1])
+
+
+@pytest.mark.parametrize("terms", [4, 5])
+def test_energy_pair_kernel_matches_one_cta_kernel(dbg, terms):
+    """The CTA-pair form issues the same split products in the same K order into the same
+    accumulators: its traces agree with the one-CTA kernel's to the last bits."""
+    Np, Nchol, nws, M = 128, 37, 11, 512
+    rng = np.random.default_rng(123)
+    Lt = rng.standard_normal((Nchol, Np, M)) * np.exp(-np.arange(Nchol) / 20.0)[:, None, None]
+    Th = rng.standard_normal((nws, 2, Np, M)) * 0.05
+    t1, X1 = energy_call(dbg, Lt, Th, Np, Nchol, nws, M, terms, 0)
+    t2, X2 = energy_call(dbg, Lt, Th, Np, Nchol, nws, M, terms, 1)
+    dt = np.max(np.abs(t1 - t2)) / np.max(np.abs(t1))
+    dX = np.max(np.abs(X1 - X2)) / np.max(np.abs(X1))
+    print(f"pair vs one-CTA (terms={terms}): t {dt:.2e}, X {dX:.2e}, identical {np.array_equal(t1, t2) and np.array_equal(X1, X2)}")
+    assert dt < 1e-12 and dX < 1e-12
+
+
+def test_rounded_products_match_four_product_accuracy(dbg):
+    """The rounded three products (r*lo + lo*hi with r = fp16 of the scaled Ltilde) against exact
+    float64 traces, beside three and four plain products: the rounded form has the accuracy of
+    four products, an order of magnitude better than dropping lo*lo."""
+    from paper_2003_01831_gb300 import synthetic as syn
+    M, N, nch, nws = 512, 128, 16, 4
+    h, L, E0 = syn.make_hamiltonian(M, nch, np.random.default_rng(1005), decay=200.0, band=64)
+    P = syn.make_trial(h, N, N)[0].real
+    Lt = np.ascontiguousarray(np.einsum("ka,nkl->nal", P, L))
+    rng = np.random.default_rng(6)
+    Th = np.zeros((nws, 2, N, M))
+    for w in range(nws):
+        Phi = P + 0.05 * (rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N)))
+        Theta = Phi @ np.linalg.inv(P.T @ Phi)
+        Th[w, 0], Th[w, 1] = Theta.real.T, Theta.imag.T
+    T = np.einsum("nak,wbk->wnab", Lt, Th[:, 0]) + 1j * np.einsum("nak,wbk->wnab", Lt, Th[:, 1])
+    X_ref = np.einsum("wnab,wnba->wn", T, T)
+    err = {}
+    for terms in (3, 4, 5):
+        t, X = energy_call(dbg, Lt, Th, N, nch, nws, M, terms, 0)
+        err[terms] = np.max(np.abs(X - X_ref)) / np.max(np.abs(X_ref))
+    print("max |dX| / max |X| for 3, 4, rounded 3:", err)
+    assert err[5] < 2.0 * err[4]
+    assert err[5] < 0.25 * err[3]
