@@ -40,7 +40,12 @@ WORKLOAD = ("solid-like synthetic Hamiltonian: M=512, N_up=N_dn=128, Nchol=2560,
 # dram__bytes_write.sum, one ncu capture of this script; the summary and its command are in
 # profiles/).  The figure holds for the kernel source it was taken on: a digest of that source
 # (the energy-kernel section of kernels_tc.cu and the PTX wrappers) gates it.
-ENERGY_TRAFFIC = {"bytes": 220820940672, "src_digest": "a33a0aa297eb4829"}
+# DRAM bytes per launch of the energy kernel at the bench workload: one-pass ncu counters on a
+# W = 16 launch of the same kernel (4,048,846,080 read + 5,892,352 written), scaled by 64 to
+# W = 1024 -- the kernel streams L~ once per window of 8 walker-spin groups, so its traffic grows
+# in proportion to W (profiles/energy_pair_kernel_traffic_m512.md).  Reported only while the
+# kernel's source matches the digest it was measured on.
+ENERGY_TRAFFIC = {"bytes": 64 * (4048846080 + 5892352), "src_digest": "de2ba17b8fb469f4"}
 
 
 def energy_src_digest() -> str:
@@ -127,38 +132,6 @@ def build_system(wl):
     return h, L, E0, Psi
 
 
-class OracleSample:
-    """The oracle on the workload's system truncated to its first `nch` Cholesky vectors,
-    one walker; step() returns the host time of one walker-step (energy measured)."""
-
-    def __init__(self, wl, nch: int):
-        from oracle import afqmc as O
-        from paper_2003_01831_gb300 import synthetic as syn
-        self.O, self.syn, self.nch = O, syn, nch
-        h, L, E0 = syn.make_hamiltonian(wl.M, nch, wl.rng(), decay=wl.decay, band=wl.band, reading=wl.reading)
-        self.Psi = syn.make_trial(h, wl.Nup, wl.Ndn)
-        self.ham = O.Hamiltonian(h=h, L=L, E0=E0)
-        self.p = O.Params(tau=wl.tau, k_taylor=6, k_qr=wl.k_qr)
-        self.B = O.half_one_body_propagator(self.ham, wl.tau)
-        self.wk = O.init_walkers(self.ham, self.Psi, 1)
-        self.s = 0
-
-    def step(self) -> float:
-        x = self.syn.make_fields(1, 1, self.nch, seed=self.s)[0]
-        self.s += 1
-        t0 = time.perf_counter()
-        self.O.step(self.ham, self.Psi, self.B, self.wk, x, self.p)
-        return time.perf_counter() - t0
-
-
-def extrapolate(n1, t1, n2, t2, n):
-    """The oracle's step cost is affine in Nchol (force bias, HS potential and both energy
-    terms are sums over n): fit t = a + b*Nchol through two samples, evaluate at n."""
-    b = (t2 - t1) / (n2 - n1)
-    return max(t1 + b * (n - n1), t2)
-
-
-CPU_SAMPLE = (64, 256)   # Cholesky-vector counts of the reference arm's two timed truncations
 CHECK_W = 4              # walkers of the full-size oracle check (walker 0 is compared)
 
 
@@ -220,58 +193,36 @@ def cpu_baseline(wl, h, L, E0, Psi):
 
 
 def run_reference(args, wl, rank, world):
+    """The oracle as it stands on the host cores, timed directly on the throughput system
+    itself (M=512, N=128+128, Nchol=2560): every timed step is one oracle walker-step (energy
+    measured, caller fields), about 9 s on 16 cores.  Walkers are independent, so one walker of
+    the workload is the bounded sample of each step; value = walker-steps per second."""
     if rank != 0:
         return 0
+    from oracle import afqmc as O
+    from paper_2003_01831_gb300 import synthetic as syn
     cores = len(os.sched_getaffinity(0))
-    n1, n2 = CPU_SAMPLE
-    a, b = OracleSample(wl, n1), OracleSample(wl, n2)
-    for _ in range(max(args.warmup, 0)):
-        a.step()
-    # every timed step: one oracle walker-step at each truncation; the pair gives the
-    # extrapolated time of one full walker-step
-    pts = [(a.step(), b.step()) for _ in range(args.steps)]
-    per = [extrapolate(n1, t1, n2, t2, wl.Nchol) for t1, t2 in pts]
-    t = float(np.mean(per))
-    v = 1.0 / t
-    t1m, t2m = float(np.mean([p[0] for p in pts])), float(np.mean([p[1] for p in pts]))
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t * wl.W, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": True,
-                             "measured_points": [{"Nchol": n1, "s_per_walker_step": t1m},
-                                                 {"Nchol": n2, "s_per_walker_step": t2m}],
-                             "sample": f"each step: one oracle walker-step on the system truncated to its first "
-                                       f"{n1} and {n2} Cholesky vectors, extrapolated (affine in Nchol) to "
-                                       f"Nchol={wl.Nchol}; ms_per_step = that time x {wl.W} walkers (walkers are "
-                                       f"independent, so the walker count scales the time exactly); the full-size "
-                                       f"walker-step itself is timed directly in the default arm's cpu_baseline"},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_reference(args, wl, rank, world):
-    if rank != 0:
-        return 0
-    cores = len(os.sched_getaffinity(0))
-    n1, n2 = CPU_SAMPLE
-    a, b = OracleSample(wl, n1), OracleSample(wl, n2)
-    for _ in range(max(args.warmup, 0)):
-        a.step()
-    # every timed step: one oracle walker-step at each truncation; the pair gives the
-    # extrapolated time of one full walker-step
-    per = [extrapolate(n1, a.step(), n2, b.step(), wl.Nchol) for _ in range(args.steps)]
-    t = float(np.mean(per))
+    h, L, E0, Psi = build_system(wl)
+    ham = O.Hamiltonian(h=h, L=L, E0=E0)
+    p = O.Params(tau=wl.tau, k_taylor=6, k_qr=wl.k_qr)
+    B = O.half_one_body_propagator(ham, wl.tau)
+    wk = O.init_walkers(ham, Psi, 1)
+    x = syn.make_fields(args.warmup + args.steps, 1, wl.Nchol, seed=0)
+    for s in range(args.warmup):
+        O.step(ham, Psi, B, wk, x[s], p)
+    t0 = time.perf_counter()
+    for s in range(args.warmup, args.warmup + args.steps):
+        O.step(ham, Psi, B, wk, x[s], p)
+    t = (time.perf_counter() - t0) / max(args.steps, 1)
     v = 1.0 / t
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t * wl.W, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: one oracle walker-step on the system truncated to its first "
-                                       f"{n1} and {n2} Cholesky vectors, extrapolated (affine in Nchol) to "
-                                       f"Nchol={wl.Nchol}; ms_per_step = that time x {wl.W} walkers"},
+            "config": {"workload": WORKLOAD + "; each timed step is one walker of it", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "extrapolated": False,
+                             "sample": f"each step: one oracle walker-step of the throughput system itself "
+                                       f"(M={wl.M}, N={wl.Nup}+{wl.Ndn}, Nchol={wl.Nchol}, energy measured), "
+                                       f"timed directly; set-up excluded"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

@@ -169,7 +169,10 @@ int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
  * opts   NULL for defaults.
  * Sets w = 1 and E_T = E_L(trial) (the trial's own mixed energy).
  * Sizes: 1 <= Nup, Ndn <= min(M, 128).  BF16X3 additionally needs Nup == Ndn,
- * M % 64 == 0, Nchol % 8 == 0 and a real trial (UNSUPPORTED otherwise).
+ * M % 64 == 0, Nchol % 8 == 0 and a real trial (UNSUPPORTED otherwise); its fused
+ * energy contraction further needs N in {32, 64, 128} and M <= 1024, so a step that
+ * measures the energy of another shape returns UNSUPPORTED (steps with measure_every
+ * = 0 run; afqmc_create_batch pads any shape exactly).
  * Errors: BADARG, SHAPE, UNSUPPORTED, SINGULAR (a walker with zero overlap),
  * NONFINITE, OOM, CUDA. */
 int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn,
