@@ -296,6 +296,9 @@ def run_batch(args, rank, world):
         h, L, E0, Psi = syn.make_uneven_system(d, i)
         systems.append((h, L, E0, Psi[0], Psi[1], d.W))
     prec = api.PREC_BF16X3 if args.precision == "bf16x3" else api.PREC_FP64
+    lib = api.lib()
+    lib.afqmc_debug_set_batch_padding.argtypes = [ctypes.c_int]
+    api._check(lib.afqmc_debug_set_batch_padding(args.batch_pad_granule))
     b = Batch(systems, 0.01, precision=prec, k_qr=10)
     del systems
     tuned_ms = b.autotune(reps=2)
@@ -317,10 +320,17 @@ def run_batch(args, rank, world):
     # algorithmic flops of the energy contraction (the dominant term): 8 W Nchol N^2 M per system,
     # and the flops the padded shapes (M', N', Nchol') run
     alg = sum(8.0 * d.W * d.Nchol * d.N * d.N * d.M for d in dims)
-    padded = 0.0
+    padded, tiles = 0.0, 0.0
     for i, d in enumerate(dims):
         sh_i, _ = b.info(i)
-        padded += 8.0 * d.W * int(sh_i[2]) * int(sh_i[1]) ** 2 * int(sh_i[0])
+        Mp, Np, Ncp = int(sh_i[0]), int(sh_i[1]), int(sh_i[2])
+        padded += 8.0 * d.W * Ncp * Np ** 2 * Mp
+        # what the tensor cores issue (per product): pair tiles of 2 x 128 rows (floor(128/N')
+        # Cholesky vectors each) by 256 columns (floor(128/N') walker-spins), K = M'
+        G = 128 // Np
+        n_pairs = -(-(-(-Ncp // G)) // 2)
+        ws_groups = -(-(2 * d.W) // G)
+        tiles += 2.0 * n_pairs * ws_groups * 128 * 256 * 2.0 * Mp
     _, bf16_sust, _, src = peaks()
     ach = alg / (ms / args.steps / 1e3) / 1e12
     line = {"metric": "walker-steps/sec, 64 uneven systems (M~U{32..256}, N=M/4, Nchol=5M, W~U{32..256})",
@@ -336,7 +346,10 @@ def run_batch(args, rank, world):
                                      "energy_launch": "one persistent launch over every system" if int(shape[6])
                                      else "one launch per system", "energy_k_chunk": int(shape[7]),
                                      "tuned_ms_per_step": tuned_ms},
-                       "padded_energy_flops_over_algorithmic": padded / alg},
+                       "n_padding": f"N' = N rounded up to a multiple of {args.batch_pad_granule}"
+                                    if args.batch_pad_granule == 8 else "N' in {32, 64, 128}",
+                       "padded_energy_flops_over_algorithmic": padded / alg,
+                       "energy_tile_flops_over_algorithmic": tiles / alg},
             "clocks": clk.summary(), "gpu_launches": int(nk) * args.steps if nk > 0 else None,
             "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_sust, "unit": "TFLOP/s",
                          "frac": ach / bf16_sust, "traffic": None,
@@ -602,6 +615,8 @@ def main():
     ap.add_argument("--energy-terms", type=int, default=0, choices=[0, 1, 3, 4])
     ap.add_argument("--energy-pair", type=int, default=-1, choices=[-1, 0, 1],
                     help="energy kernel form: 0 one CTA per tile, 1 CTA pairs, -1 the library default")
+    ap.add_argument("--batch-pad-granule", type=int, default=8, choices=[8, 32],
+                    help="batch64: pad each system's N to a multiple of 8 (default) or to 32/64/128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()

@@ -170,9 +170,9 @@ int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
  * Sets w = 1 and E_T = E_L(trial) (the trial's own mixed energy).
  * Sizes: 1 <= Nup, Ndn <= min(M, 128).  BF16X3 additionally needs Nup == Ndn,
  * M % 64 == 0, Nchol % 8 == 0 and a real trial (UNSUPPORTED otherwise); its fused
- * energy contraction further needs N in {32, 64, 128} and M <= 1024, so a step that
- * measures the energy of another shape returns UNSUPPORTED (steps with measure_every
- * = 0 run; afqmc_create_batch pads any shape exactly).
+ * energy contraction further needs N % 8 == 0 and M <= 1024, so a step that measures
+ * the energy of another shape returns UNSUPPORTED (steps with measure_every = 0 run;
+ * afqmc_create_batch pads any shape exactly).
  * Errors: BADARG, SHAPE, UNSUPPORTED, SINGULAR (a walker with zero overlap),
  * NONFINITE, OOM, CUDA. */
 int afqmc_init_walkers(afqmc_ham_t ham, const double* Psi_up, const double* Psi_dn, int Nup, int Ndn,
@@ -340,13 +340,15 @@ int afqmc_philox_fields(uint64_t seed, int64_t step, int W, int Nchol, double* x
  * system's tiles, between the systems' Green's functions and the rest of their steps.  The
  * per-system arithmetic is exactly that of afqmc_step.
  *
- * Systems the tensor-core path cannot tile (BF16X3 with M % 64 != 0, N not 32/64/128 or
+ * Systems the tensor-core path cannot tile (BF16X3 with M % 64 != 0, N % 8 != 0 or
  * Nchol % 8 != 0), and every system under AFQMC_PAD_ALWAYS, are padded exactly: extra
  * orbitals on which h and every L_n vanish, one extra electron per extra orbital in the
  * trial and in every walker (S = diag(S, 1), so overlaps, Green's function block, force
  * bias and energies are unchanged), and zero Cholesky vectors up to a multiple of 8.
- * Padded shapes: N' = 32, 64 or 128 (the smallest >= N), M' = the smallest multiple of 64
- * >= M + N' - N, Nchol' = Nchol rounded up to a multiple of 8.  Padding needs Nup == Ndn.
+ * Padded shapes: N' = N rounded up to a multiple of 8 (at least 8), M' = the smallest
+ * multiple of 64 >= M + N' - N, Nchol' = Nchol rounded up to a multiple of 8.  The energy
+ * tiles of a system hold floor(128 / N') Cholesky vectors by floor(128 / N') walker-spins.
+ * Padding needs Nup == Ndn.
  * Fields come from Philox (see afqmc_philox_fields) with key seed + s * 0x9E3779B97F4A7C15
  * (mod 2^64) for system s and the batch's global step; x[w][n] does not depend on Nchol,
  * so a padded system draws the fields of its unpadded self. */

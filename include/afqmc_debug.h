@@ -32,7 +32,7 @@ int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int row
  * for Lt [Nchol][Np][M] (real) and walker-spin
  * Green's functions ThetaT [nws][2][Np][M] (re plane then im plane of Theta^T), returns
  * t [nws][Nchol] = Tr(Lt_n Theta_ws) and X [nws][Nchol] = Tr((Lt_n Theta_ws)^2) as complex
- * (interleaved float64).  Np in {32, 64, 128}, M % 64 == 0.  These traces give the force
+ * (interleaved float64).  Np a multiple of 8 up to 128, M % 64 == 0.  These traces give the force
  * bias and the Coulomb / exchange energies of the mixed estimator. */
 int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np, int Nchol, int nws, int M, int terms,
                        double* t, double* X);
@@ -87,6 +87,11 @@ int afqmc_debug_set_energy_window(int ws_super);
  * Green's-function rows; pair = 0, one CTA per 128 x 256 tile (kind::f16 MMAs of M = 128).
  * Results are the same arithmetic in the same order.  Errors: BADARG for other values. */
 int afqmc_debug_set_energy_variant(int pair);
+
+/* Electron-count padding of batches created after the call: granule 8 (default) pads each
+ * system's N to the next multiple of 8 (energy tiles of floor(128 / N') walker-spins); 32 pads
+ * to 32, 64 or 128.  Errors: BADARG for any other granule. */
+int afqmc_debug_set_batch_padding(int granule);
 
 /* Energy launch of a batch's later measuring BF16X3 steps (b: an afqmc_batch_t): multi = 1 one
  * persistent launch over every system's tiles with K chunks of bk (16 or 32), multi = 0 one

@@ -3,7 +3,7 @@
 // include/afqmc.h).
 //
 // Each system is an ordinary Hamiltonian + walker set.  Systems whose shapes the
-// tensor-core path does not tile (M not a multiple of 64, N not in {32, 64, 128}, Nchol not
+// tensor-core path does not tile (M not a multiple of 64, N not a multiple of 8, Nchol not
 // a multiple of 8) are padded exactly:
 //   * extra orbitals are decoupled: h, every L_n and hence h' vanish on them, so
 //     B = exp(-tau h'/2) is the identity there and A = sum_n c_n L_n has no entries there;
@@ -141,7 +141,13 @@ __global__ void batch_tail_kernel(const cplx* const* emix, unsigned* const* fl, 
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-int tn_pad(int N) { return N <= 32 ? 32 : (N <= 64 ? 64 : 128); }
+// Tensor-core electron count: the energy tiles pack floor(128 / N') walker-spins of any N' that
+// is a multiple of 8, so N is padded to the next multiple of 8 (or, under the debug granule 32,
+// to 32, 64 or 128).
+int tn_pad(int N) {
+    if (launch_policy().batch_n_granule == 32) return N <= 32 ? 32 : (N <= 64 ? 64 : 128);
+    return std::max(8, ((N + 7) / 8) * 8);
+}
 
 // Internal shapes of system s.
 void pick_shapes(afqmc_batch* b, int s, bool pad) {
@@ -159,7 +165,8 @@ void pick_shapes(afqmc_batch* b, int s, bool pad) {
 }
 
 bool tc_tiles(int M, int N, int Nup, int Ndn, int Nchol) {
-    return M % 64 == 0 && Nup == Ndn && (N == 32 || N == 64 || N == 128) && Nchol % 8 == 0;
+    const bool n_ok = launch_policy().batch_n_granule == 32 ? (N == 32 || N == 64 || N == 128) : (N % 8 == 0 && N <= 128);
+    return M % 64 == 0 && M <= 1024 && Nup == Ndn && n_ok && Nchol % 8 == 0;
 }
 
 // Device copy of a caller array (host or device); *tmp owns it when a copy was made.

@@ -63,6 +63,7 @@ struct LaunchPolicy {
     int energy_ws_super = 0;   // walker-spin groups per L2 window of the energy kernel (0: default)
     int gj_variant = 0;        // batched inverse: 0 auto, 1 shared-memory kernel, 2 register kernel
     int energy_pair = 1;       // fused energy kernel: 1 CTA pairs (cta_group::2, default), 0 one CTA per tile
+    int batch_n_granule = 8;   // batches pad N to a multiple of 8 (default), or 32: N' in {32, 64, 128}
 };
 LaunchPolicy& launch_policy();
 

@@ -222,6 +222,12 @@ extern "C" int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energ
     return AFQMC_OK;
 }
 
+extern "C" int afqmc_debug_set_batch_padding(int granule) {
+    if (granule != 8 && granule != 32) return fail(AFQMC_ERR_BADARG, "debug_set_batch_padding: granule must be 8 or 32");
+    launch_policy().batch_n_granule = granule;
+    return AFQMC_OK;
+}
+
 extern "C" int afqmc_debug_set_energy_variant(int pair) {
     if (pair != 0 && pair != 1) return fail(AFQMC_ERR_BADARG, "debug_set_energy_variant: pair must be 0 or 1");
     launch_policy().energy_pair = pair;

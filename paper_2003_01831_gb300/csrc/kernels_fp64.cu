@@ -84,25 +84,30 @@ __device__ __forceinline__ void mac(cplx& acc, cplx a, double b) {
 }
 __device__ __forceinline__ void mac(cplx& acc, cplx a, cplx b) { cfma(acc, a, b); }
 
-template <bool AR, bool BR>
+// Tiles of TS x TS outputs (TS = 64: 4 x 4 per thread; TS = 32: 2 x 2 per thread, for the small
+// blocks of few-electron systems, e.g. the 32 x 32 T_n = Ltilde_n Theta blocks), K in steps of
+// 512 / TS, so each operand tile holds 512 elements either way.
+template <bool AR, bool BR, int TS>
 __global__ void __launch_bounds__(kThreads) zgemm_kernel(GemmArgs g) {
-    constexpr int BM = 64, BN = 64, BK = 8;
+    constexpr int BM = TS, BN = TS, BK = 512 / TS, R = TS / 16;
     using TA = typename Elem<AR>::T;
     using TB = typename Elem<BR>::T;
     __shared__ TA As[BK][BM + 1];
     __shared__ TB Bs[BK][BN + 1];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int nbatch = g.nb1 * g.nb2;
-    for (int b = blockIdx.z; b < nbatch; b += gridDim.z) {
-        const int b1 = b / g.nb2, b2 = b % g.nb2;
-        const int64_t offA = b1 * g.A.s1 + b2 * g.A.s2;
-        const int64_t offB = b1 * g.B.s1 + b2 * g.B.s2;
-        cplx acc[4][4];
+    const int64_t nbatch = (int64_t)g.nb0 * g.nb1 * g.nb2;
+    for (int64_t b = blockIdx.z; b < nbatch; b += gridDim.z) {
+        const int64_t b0 = b / ((int64_t)g.nb1 * g.nb2);
+        const int64_t r12 = b % ((int64_t)g.nb1 * g.nb2);
+        const int64_t b1 = r12 / g.nb2, b2 = r12 % g.nb2;
+        const int64_t offA = b0 * g.A.s0 + b1 * g.A.s1 + b2 * g.A.s2;
+        const int64_t offB = b0 * g.B.s0 + b1 * g.B.s1 + b2 * g.B.s2;
+        cplx acc[R][R];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < R; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = cplx{0.0, 0.0};
+            for (int j = 0; j < R; ++j) acc[i][j] = cplx{0.0, 0.0};
 
         for (int k0 = 0; k0 < g.k; k0 += BK) {
             for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
@@ -136,34 +141,34 @@ __global__ void __launch_bounds__(kThreads) zgemm_kernel(GemmArgs g) {
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
-                TA a[4];
-                TB bv[4];
+                TA a[R];
+                TB bv[R];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+                for (int i = 0; i < R; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+                for (int j = 0; j < R; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < R; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) mac(acc[i][j], a[i], bv[j]);
+                    for (int j = 0; j < R; ++j) mac(acc[i][j], a[i], bv[j]);
             }
             __syncthreads();
         }
         const bool use_beta = (g.beta.re != 0.0 || g.beta.im != 0.0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < R; ++i) {
             const int r = m0 + ty + 16 * i;
             if (r >= g.m) continue;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < R; ++j) {
                 const int c = n0 + tx + 16 * j;
                 if (c >= g.n) continue;
                 cplx v = g.alpha * acc[i][j];
-                cplx* cp = g.C + b1 * g.sc1 + b2 * g.sc2 + (int64_t)r * g.ldc + c;
+                cplx* cp = g.C + b0 * g.sc0 + b1 * g.sc1 + b2 * g.sc2 + (int64_t)r * g.ldc + c;
                 if (use_beta) v = v + g.beta * (*cp);
                 *cp = v;
                 if (g.D) {
-                    cplx* dp = g.D + b1 * g.sd1 + b2 * g.sd2 + (int64_t)r * g.ldd + c;
+                    cplx* dp = g.D + b0 * g.sd0 + b1 * g.sd1 + b2 * g.sd2 + (int64_t)r * g.ldd + c;
                     *dp = *dp + v;
                 }
             }
@@ -883,7 +888,7 @@ __global__ void __launch_bounds__(kThreads) local_energy_kernel(LocalEnergyArgs 
     for (int s = 0; s < 2; ++s) {
         const int Ns = s == 0 ? a.Nup : a.Ndn;
         const cplx* Th = a.Theta[s] + (int64_t)w * a.M * Ns;
-        const cplx* ht = a.ht[s];
+        const cplx* ht = a.ht[s] + (a.wper > 0 ? (int64_t)(w / a.wper) * a.ht_stride[s] : 0);
         for (int64_t e = threadIdx.x; e < (int64_t)a.M * Ns; e += kThreads) {
             const int k = (int)(e / Ns), b = (int)(e % Ns);
             cfma(e1, ht[(int64_t)b * a.M + k], Th[e]);
@@ -904,7 +909,7 @@ __global__ void __launch_bounds__(kThreads) local_energy_kernel(LocalEnergyArgs 
             const double mag = hypot(xb.re, xb.im);
             if (mag > a.fb_cap) xb = (a.fb_cap / mag) * xb;
         }
-        a.xbar[i] = xb;
+        if (a.xbar) a.xbar[i] = xb;
     }
     if (energy) {
         e1 = block_sum(e1, sh);
@@ -1247,15 +1252,25 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n +
 }  // namespace
 
 // ================================================================== launchers
+// 32 x 32 tiles when they cover the output with at most 60% of the 64 x 64 tiles' area
+// (small blocks of few-electron systems), 64 x 64 otherwise.
 void zgemm(const GemmArgs& g, cudaStream_t st) {
     if (g.m <= 0 || g.n <= 0) return;
-    const int nbatch = g.nb1 * g.nb2;
-    dim3 grid((g.n + 63) / 64, (g.m + 63) / 64, std::min(nbatch, 65535));
+    const int64_t nbatch = (int64_t)g.nb0 * g.nb1 * g.nb2;
+    const int64_t a64 = (int64_t)((g.m + 63) / 64) * ((g.n + 63) / 64) * 4096;
+    const int64_t a32 = (int64_t)((g.m + 31) / 32) * ((g.n + 31) / 32) * 1024;
+    const bool small = 10 * a32 <= 6 * a64;
+    const int ts = small ? 32 : 64;
+    dim3 grid((g.n + ts - 1) / ts, (g.m + ts - 1) / ts, (unsigned)std::min<int64_t>(nbatch, 65535));
     count_launch();
-    if (g.A.real && g.B.real) zgemm_kernel<true, true><<<grid, kThreads, 0, st>>>(g);
-    else if (g.A.real) zgemm_kernel<true, false><<<grid, kThreads, 0, st>>>(g);
-    else if (g.B.real) zgemm_kernel<false, true><<<grid, kThreads, 0, st>>>(g);
-    else zgemm_kernel<false, false><<<grid, kThreads, 0, st>>>(g);
+    auto go = [&](auto k32, auto k64) {
+        if (small) k32<<<grid, kThreads, 0, st>>>(g);
+        else k64<<<grid, kThreads, 0, st>>>(g);
+    };
+    if (g.A.real && g.B.real) go(zgemm_kernel<true, true, 32>, zgemm_kernel<true, true, 64>);
+    else if (g.A.real) go(zgemm_kernel<true, false, 32>, zgemm_kernel<true, false, 64>);
+    else if (g.B.real) go(zgemm_kernel<false, true, 32>, zgemm_kernel<false, true, 64>);
+    else go(zgemm_kernel<false, false, 32>, zgemm_kernel<false, false, 64>);
 }
 
 void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* logdet, bool with_inverse,

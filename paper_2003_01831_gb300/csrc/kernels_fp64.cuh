@@ -5,8 +5,8 @@
 
 namespace afqmc {
 
-// Operand of a batched GEMM: element (row r, col c) of op(X) for batch (b1, b2) is read at
-//   ptr + b1*s1 + b2*s2 + (op == N ? r*ld + c : c*ld + r), conjugated when op == C.
+// Operand of a batched GEMM: element (row r, col c) of op(X) for batch (b0, b1, b2) is read at
+//   ptr + b0*s0 + b1*s1 + b2*s2 + (op == N ? r*ld + c : c*ld + r), conjugated when op == C.
 enum Op : int { OP_N = 0, OP_T = 1, OP_C = 2 };
 
 struct GemmOperand {
@@ -15,10 +15,11 @@ struct GemmOperand {
     int op = OP_N;
     int64_t ld = 0;
     int64_t s1 = 0, s2 = 0;
+    int64_t s0 = 0;
 };
 
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b];  if D != null also D[b] += (that result).
-// batch index b = b1 * nb2 + b2, nbatch = nb1 * nb2.
+// batch index b = (b0 * nb1 + b1) * nb2 + b2, nbatch = nb0 * nb1 * nb2.
 struct GemmArgs {
     int m = 0, n = 0, k = 0;
     int nb1 = 1, nb2 = 1;
@@ -28,6 +29,8 @@ struct GemmArgs {
     int64_t ldc = 0, sc1 = 0, sc2 = 0;
     cplx* D = nullptr;
     int64_t ldd = 0, sd1 = 0, sd2 = 0;
+    int nb0 = 1;
+    int64_t sc0 = 0, sd0 = 0;
 };
 
 void zgemm(const GemmArgs& g, cudaStream_t st);
@@ -59,8 +62,12 @@ struct LocalEnergyArgs {
     const cplx* exch[2] = {nullptr, nullptr};
     double E0, tau, fb_cap;
     cplx* E_L;
-    cplx* xbar;
+    cplx* xbar;          // may be null: force bias not written
     unsigned* flags;
+    // walkers in groups of wper sharing one trial determinant: walker w reads ht[s] +
+    // (w / wper) * ht_stride[s] (wper = 0: one ht for all)
+    int wper = 0;
+    int64_t ht_stride[2] = {0, 0};
 };
 void local_energy_forcebias(const LocalEnergyArgs& a, cudaStream_t st);
 

@@ -491,11 +491,12 @@ __device__ void energy_producer(uint8_t* sbase, SharedCtl* ctl, const CUtensorMa
             uint8_t* s = sbase + (size_t)st * C::kStageBytes;
             mbar_arrive_expect_tx(&ctl->full[st], C::kStageBytes);
             const int x = kb * BK;
-            tma_load_2d(s, tAh, &ctl->full[st], x, ng * 128);
-            tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], x, ng * 128);
-            if (AP == 3) tma_load_2d(s + 2 * C::kABytes, tAr, &ctl->full[st], x, ng * 128);
-            tma_load_2d(s + C::kBOff, tBh, &ctl->full[st], x, wg * 256);
-            tma_load_2d(s + C::kBOff + C::kBBytes, tBl, &ctl->full[st], x, wg * 256);
+            const int ya = ng * es.G * es.Np, yb = wg * 2 * es.G * es.Np;   // 128 and 256 rows per group at Np | 128
+            tma_load_2d(s, tAh, &ctl->full[st], x, ya);
+            tma_load_2d(s + C::kABytes, tAl, &ctl->full[st], x, ya);
+            if (AP == 3) tma_load_2d(s + 2 * C::kABytes, tAr, &ctl->full[st], x, ya);
+            tma_load_2d(s + C::kBOff, tBh, &ctl->full[st], x, yb);
+            tma_load_2d(s + C::kBOff + C::kBBytes, tBl, &ctl->full[st], x, yb);
         }
     }
     if (!ok) {
@@ -720,6 +721,174 @@ __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, Shar
     return true;
 }
 
+// Epilogue of one tile for any Np that is a multiple of 8 up to 128 (es.Np at run time; the
+// batch pads each system's N to such an Np).  The tile holds G = floor(128 / Np) n-blocks (rows
+// [0, G Np)) and G walker-spins (compact columns [0, G Np)); rows and compact columns beyond
+// G Np are padding.  The thread owns row `row` and compact columns [32 h, 32 h + 32) as four
+// chunks of 8: chunk c = 4 h + k holds compact columns 8 c .. 8 c + 7, all of walker-spin
+// 8 c / Np since Np is a multiple of 8, read from tensor memory eight columns at a time.  The
+// drain, the plane staging and the three sums are the fixed-Np epilogue's; the sums are kept
+// per chunk, parked in the plane once it is free (part[row][c][4]: Re t, Im t, Re X, Im X),
+// and one warp reduces each (n-block, walker-spin) output over its Np rows and Np / 8 chunks
+// in a fixed order, in double.
+template <typename Release>
+__device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, SharedCtl* ctl, float* plane,
+                                                         float* colscale, int ng, int wg, int it, Release release) {
+    const int Np = es.Np, G = es.G, GN = G * Np;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
+    const int h = (warp - 2) >> 2;         // compact columns [32 h, 32 h + 32)
+    const int row = q * 32 + lane;
+    const bool rok = row < GN;
+    const int i_blk = row / Np, a = row % Np;
+    const int et = threadIdx.x - 64;       // 0..511
+    const uint32_t tq = ctl->tmem_base + ((uint32_t)(q * 32) << 16);
+    float* own = plane + row * kEPitch;
+    if (et < 256) {
+        const int64_t brow = (int64_t)wg * 2 * GN + et;
+        colscale[et] = et < 2 * GN && brow < (int64_t)es.nws * 2 * Np ? es.b_scale[brow] : 0.0f;
+    }
+    const int64_t arow = (int64_t)ng * GN + row;
+    const float sa = rok && arow < (int64_t)es.Nchol * Np ? es.a_scale[arow] : 0.0f;
+    // chunk k: first compact column ccol(k) and the TMEM column tcol(k) of its real part; both
+    // are warp-uniform, so are the chunk conditions below
+    // (a padding chunk reads column 0 instead, in range, and its values are never used)
+    auto ccol = [&](int k) { return 32 * h + 8 * k; };
+    auto tcol = [&](int k) { return ccol(k) < GN ? (ccol(k) / Np) * 2 * Np + ccol(k) % Np : 0; };
+    auto icol = [&](int k) { return ccol(k) < GN ? tcol(k) + Np : 0; };
+    ebar();
+    const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
+    tc_fence_after();
+    // Im of both accumulators, scaled to true units, into the plane: the loads of all four
+    // chunks in flight at once, one wait
+    {
+        uint32_t u[4][2][8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            tmem_ld8_nw(tq + icol(k), u[k][0]);
+            tmem_ld8_nw(tq + 256 + icol(k), u[k][1]);
+        }
+        tmem_ld_wait();
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (ccol(k) < GN) {
+                const int c0 = icol(k);
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    own[ccol(k) + e] =
+                        (__uint_as_float(u[k][0][e]) + __uint_as_float(u[k][1][e])) * (sa * colscale[c0 + e]);
+            }
+    }
+    // Re into registers, two chunks per wait (register budget); tensor memory is then free
+    float tr[32];
+#pragma unroll
+    for (int k2 = 0; k2 < 4; k2 += 2) {
+        uint32_t u[2][2][8];
+#pragma unroll
+        for (int k = k2; k < k2 + 2; ++k) {
+            tmem_ld8_nw(tq + tcol(k), u[k - k2][0]);
+            tmem_ld8_nw(tq + 256 + tcol(k), u[k - k2][1]);
+        }
+        tmem_ld_wait();
+#pragma unroll
+        for (int k = k2; k < k2 + 2; ++k) {
+            const int c0 = tcol(k);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                tr[8 * k + e] = ccol(k) < GN ? (__uint_as_float(u[k - k2][0][e]) + __uint_as_float(u[k - k2][1][e])) *
+                                                   (sa * colscale[c0 + e])
+                                             : 0.f;
+        }
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0 && got) release();
+    if (!ebar_and(got ? 1 : 0)) return false;   // all sixteen warps leave together
+    ebar();                                    // Ti plane complete
+    // per chunk: TiTi and TrTi sums over its b, and the diagonal Ti_aa if the chunk holds it
+    float sii[4], sri[4], dim_[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        sii[k] = 0.f;
+        sri[k] = 0.f;
+        dim_[k] = 0.f;
+        if (rok && ccol(k) < GN) {
+            const int j = ccol(k) / Np, b0 = ccol(k) % Np;
+            const float* pb = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;   // Ti[b0 + e][a]
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float pv = pb[e * kEPitch];
+                sii[k] = fmaf(own[ccol(k) + e], pv, sii[k]);
+                sri[k] = fmaf(tr[8 * k + e], pv, sri[k]);
+            }
+            const int cd = j * Np + a;
+            if (cd >= ccol(k) && cd < ccol(k) + 8) dim_[k] = own[cd];
+        }
+    }
+    ebar();                                    // every read of the Ti plane done
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (ccol(k) < GN) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) own[ccol(k) + e] = tr[8 * k + e];
+        }
+    ebar();                                    // Tr plane complete
+    float srr[4], dre[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        srr[k] = -sii[k];
+        dre[k] = 0.f;
+        if (rok && ccol(k) < GN) {
+            const int j = ccol(k) / Np, b0 = ccol(k) % Np;
+            const float* pb = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) srr[k] = fmaf(tr[8 * k + e], pb[e * kEPitch], srr[k]);
+            const int cd = j * Np + a;
+            if (cd >= ccol(k) && cd < ccol(k) + 8) dre[k] = own[cd];
+        }
+    }
+    ebar();                                    // every read of the Tr plane done
+    float* part = plane;                       // [128 rows][16 chunks][4]
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool v = rok && ccol(k) < GN;
+        *reinterpret_cast<float4*>(part + (row * 16 + 4 * h + k) * 4) =
+            v ? make_float4(dre[k], dim_[k], srr[k], 2.0f * sri[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    ebar();
+    // one warp per (n-block, walker-spin) output: its Np rows x Np / 8 chunks, lanes striding the
+    // items in order, then a fixed shuffle tree
+    const int nck = Np / 8;
+    const int items = Np * nck;
+    for (int o = warp - 2; o < G * G; o += kEEpi / 32) {
+        const int ib = o / G, jo = o % G;
+        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int i = lane; i < items; i += 32) {
+            const int r = ib * Np + i / nck, c = jo * nck + i % nck;
+            const float4 v = *reinterpret_cast<const float4*>(part + (r * 16 + c) * 4);
+            s0 += v.x;
+            s1 += v.y;
+            s2 += v.z;
+            s3 += v.w;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, off);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, off);
+        }
+        const int n = ng * G + ib;
+        const int ws = wg * G + jo;
+        if (lane == 0 && n < es.Nchol && ws < es.nws) {
+            es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
+            es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
+        }
+    }
+    ebar();   // colscale and the partial sums are read before the next tile rewrites them
+    return true;
+}
+
 // Epilogue of the single-system energy kernels: tile_of(t, ng, wg) names the tile of persistent
 // iteration t.
 template <int Np, typename TileOf, typename Release>
@@ -729,7 +898,10 @@ __device__ void energy_epilogue(const EnergyShape& es, SharedCtl* ctl, float* pl
     for (int64_t t = t_first; t < t_end; t += t_step, ++it) {
         int ng, wg;
         tile_of(t, ng, wg);
-        if (!energy_epilogue_tile<Np>(es, ctl, plane, colscale, ered, ng, wg, it, release)) break;
+        bool ok;
+        if constexpr (Np == 0) ok = energy_epilogue_tile_gen(es, ctl, plane, colscale, ng, wg, it, release);
+        else ok = energy_epilogue_tile<Np>(es, ctl, plane, colscale, ered, ng, wg, it, release);
+        if (!ok) break;
     }
 }
 
@@ -822,11 +994,12 @@ __device__ void energy_producer2(uint8_t* sbase, SharedCtl* ctl, const CUtensorM
             if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
             const uint32_t fb = mapa_shared(&ctl->full[st], 0);
             const int x = kb * BK;
-            tma_load_2d_pair(s, tAh, fb, x, ng * 128);
-            tma_load_2d_pair(s + C::kABytes, tAl, fb, x, ng * 128);
-            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, tAr, fb, x, ng * 128);
-            tma_load_2d_pair(s + C::kBOff, tBh, fb, x, wg * 256 + (int)rank * 128);
-            tma_load_2d_pair(s + C::kBOff + C::kBBytes, tBl, fb, x, wg * 256 + (int)rank * 128);
+            const int ya = ng * es.G * es.Np, yb = wg * 2 * es.G * es.Np + (int)rank * 128;
+            tma_load_2d_pair(s, tAh, fb, x, ya);
+            tma_load_2d_pair(s + C::kABytes, tAl, fb, x, ya);
+            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, tAr, fb, x, ya);
+            tma_load_2d_pair(s + C::kBOff, tBh, fb, x, yb);
+            tma_load_2d_pair(s + C::kBOff + C::kBBytes, tBl, fb, x, yb);
         }
     }
     if (!ok) {
@@ -979,11 +1152,12 @@ __device__ void energy_producer_multi(uint8_t* sbase, SharedCtl* ctl, const Ener
             if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
             const uint32_t fb = mapa_shared(&ctl->full[st], 0);
             const int x = kb * BK;
-            tma_load_2d_pair(s, &S->map[0], fb, x, ng * 128);
-            tma_load_2d_pair(s + C::kABytes, &S->map[1], fb, x, ng * 128);
-            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, &S->map[2], fb, x, ng * 128);
-            tma_load_2d_pair(s + C::kBOff, &S->map[3], fb, x, w.wg * 256 + (int)rank * 128);
-            tma_load_2d_pair(s + C::kBOff + C::kBBytes, &S->map[4], fb, x, w.wg * 256 + (int)rank * 128);
+            const int ya = ng * S->es.G * S->es.Np, yb = w.wg * 2 * S->es.G * S->es.Np + (int)rank * 128;
+            tma_load_2d_pair(s, &S->map[0], fb, x, ya);
+            tma_load_2d_pair(s + C::kABytes, &S->map[1], fb, x, ya);
+            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, &S->map[2], fb, x, ya);
+            tma_load_2d_pair(s + C::kBOff, &S->map[3], fb, x, yb);
+            tma_load_2d_pair(s + C::kBOff + C::kBBytes, &S->map[4], fb, x, yb);
         }
     }
     if (!ok) {
@@ -1095,7 +1269,8 @@ __global__ void __launch_bounds__(kEThreads, 1)
             switch (es.Np) {
                 case 32: ok = energy_epilogue_tile<32>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
                 case 64: ok = energy_epilogue_tile<64>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
-                default: ok = energy_epilogue_tile<128>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
+                case 128: ok = energy_epilogue_tile<128>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
+                default: ok = energy_epilogue_tile_gen(es, ctl, plane, colscale, ng, w.wg, it, release); break;
             }
             if (!ok) break;
         }
@@ -1720,7 +1895,7 @@ int energy_setup(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, 
         return fail(AFQMC_ERR_BADARG, "tc_energy: terms must be 3, 4 or the rounded three");
     if (terms == kEnergyRounded && !Lt_round)
         return fail(AFQMC_ERR_BADARG, "tc_energy: rounded products need the rounded Ltilde plane");
-    if (Np != 32 && Np != 64 && Np != 128) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be 32, 64 or 128");
+    if (Np < 8 || Np > 128 || Np % 8) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be a multiple of 8 up to 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
     if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
     const bool rounded = terms == kEnergyRounded;
@@ -1804,7 +1979,8 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
     switch (Np) {                                                       \
         case 32: return AFQMC_ENERGY_LAUNCH(32, BKV, APV);              \
         case 64: return AFQMC_ENERGY_LAUNCH(64, BKV, APV);              \
-        default: return AFQMC_ENERGY_LAUNCH(128, BKV, APV);             \
+        case 128: return AFQMC_ENERGY_LAUNCH(128, BKV, APV);            \
+        default: return AFQMC_ENERGY_LAUNCH(0, BKV, APV);               \
     }
     if (BK == 32) {
         if (rounded) AFQMC_ENERGY_NP(32, 3)

@@ -60,6 +60,9 @@ struct Fp64Buffers {
     cplx* msd_E = nullptr;                 // E_L with trial D_I: [ND][W]
     cplx* msd_t = nullptr;                 // sum_s t_n with trial D_I: [ND][W][Nchol]
     unsigned* msd_flag = nullptr;          // status of the per-determinant inverses [0], local energies [1]
+    int msd_nd = 0;                        // determinants per batched chunk (S, ld, Theta, t, X hold
+                                           // msd_nd x W walkers; T holds nc x msd_nd x W blocks)
+    cplx* msd_Es = nullptr;                // local energies of a chunk when W < the walker count: [msd_nd][W]
     // THC Hamiltonians (Lt, LtT, T are then not allocated)
     cplx* Yt[2] = {nullptr, nullptr};      // Psi_s^+ X: [N_s][Nmu]
     cplx* Z[2] = {nullptr, nullptr};       // Theta_s^T X: [W][N_s][Nmu]

@@ -46,6 +46,14 @@ int fp64_alloc(afqmc_walkers* wk) {
     Fp64Buffers& f = wk->f;
     const int M = wk->M, W = wk->W, nch = wk->Nchol, ND = wk->ND;
     const int Nmu = wk->ham->Nmu;   // > 0: THC Hamiltonian
+    const size_t budget = (size_t)512 << 20;
+    const int Nmax = std::max(wk->N[0], wk->N[1]);
+    // multi-determinant trials: the measurement runs chunks of msd_nd determinants at once, their
+    // Green's functions held for all walkers (both spins within the budget)
+    f.msd_nd = 1;
+    if (ND > 1)
+        f.msd_nd = (int)std::max<size_t>(1, std::min<size_t>((size_t)ND, budget / ((size_t)2 * W * M * Nmax * sizeof(cplx))));
+    const size_t nd = (size_t)f.msd_nd;
     for (int s = 0; s < 2; ++s) {
         const int N = wk->N[s];
         const size_t mn = (size_t)M * N;
@@ -64,15 +72,13 @@ int fp64_alloc(afqmc_walkers* wk) {
         AFQMC_TRY(dalloc(&f.Pnew[s], (size_t)W * mn));
         AFQMC_TRY(dalloc(&f.Pa[s], (size_t)W * mn));
         AFQMC_TRY(dalloc(&f.Pb[s], (size_t)W * mn));
-        AFQMC_TRY(dalloc(&f.S[s], (size_t)W * N * N));
-        AFQMC_TRY(dalloc(&f.ld[s], (size_t)W));
-        AFQMC_TRY(dalloc(&f.Theta[s], (size_t)W * mn));
-        AFQMC_TRY(dalloc(&f.t[s], (size_t)W * nch));
-        AFQMC_TRY(dalloc(&f.X[s], (size_t)W * nch));
+        AFQMC_TRY(dalloc(&f.S[s], nd * W * N * N));
+        AFQMC_TRY(dalloc(&f.ld[s], nd * W));
+        AFQMC_TRY(dalloc(&f.Theta[s], nd * W * mn));
+        AFQMC_TRY(dalloc(&f.t[s], nd * W * nch));
+        AFQMC_TRY(dalloc(&f.X[s], nd * W * nch));
     }
     AFQMC_TRY(dalloc(&f.Bh, (size_t)M * M * (wk->ham->cplx_L ? 2 : 1)));
-    const int Nmax = std::max(wk->N[0], wk->N[1]);
-    const size_t budget = (size_t)512 << 20;
     if (Nmu > 0) {   // walker chunks of the THC densities T and of X diag(U c)
         const size_t per_w = std::max((size_t)Nmu * Nmu, (size_t)M * Nmu) * sizeof(cplx);
         f.thc_wc = (int)std::max<size_t>(1, std::min<size_t>((size_t)W, budget / per_w));
@@ -80,10 +86,10 @@ int fp64_alloc(afqmc_walkers* wk) {
         AFQMC_TRY(dalloc(&f.XD, (size_t)f.thc_wc * M * Nmu));
         AFQMC_TRY(dalloc(&f.dv, (size_t)W * Nmu));
     } else {
-        const size_t per_n = (size_t)W * Nmax * Nmax * sizeof(cplx);
+        const size_t per_n = nd * W * Nmax * Nmax * sizeof(cplx);
         f.nc = (int)std::max<size_t>(1, std::min<size_t>((size_t)nch, budget / std::max<size_t>(per_n, 1)));
         f.nc = std::min(f.nc, 65535);
-        AFQMC_TRY(dalloc(&f.T, (size_t)f.nc * W * Nmax * Nmax));
+        AFQMC_TRY(dalloc(&f.T, (size_t)f.nc * nd * W * Nmax * Nmax));
     }
     AFQMC_TRY(dalloc(&f.A, (size_t)W * M * M));
     if (ND > 1) {
@@ -92,6 +98,7 @@ int fp64_alloc(afqmc_walkers* wk) {
         AFQMC_TRY(dalloc(&f.msd_E, (size_t)ND * W));
         AFQMC_TRY(dalloc(&f.msd_t, (size_t)ND * W * nch));
         AFQMC_TRY(dalloc(&f.msd_flag, 2));
+        AFQMC_TRY(dalloc(&f.msd_Es, nd * W));
     }
     return AFQMC_OK;
 }
@@ -104,7 +111,7 @@ void fp64_free(afqmc_walkers* wk) {
         for (void* p : ps)
             if (p) cudaFree(p);
     }
-    void* more[] = {f.Bh, f.T, f.A, f.msd_cc, f.msd_ls, f.msd_E, f.msd_t, f.msd_flag, f.Tthc, f.dv, f.XD};
+    void* more[] = {f.Bh, f.T, f.A, f.msd_cc, f.msd_ls, f.msd_E, f.msd_t, f.msd_flag, f.msd_Es, f.Tthc, f.dv, f.XD};
     for (void* p : more)
         if (p) cudaFree(p);
     f = Fp64Buffers{};
@@ -209,6 +216,91 @@ void measure_det(afqmc_walkers* wk, int I, bool measure, int W, cplx* logS_out, 
     local_energy_forcebias(a, st);
 }
 
+// Multi-determinant trial (Sec. V, NOMSD): each determinant alone at the first W walkers, with
+// the determinants as an extra GEMM batch dimension.  Per chunk of nd determinants and per spin,
+// one batched GEMM over (determinant, walker) forms every overlap Psi_I^+ Phi_w, one batched
+// inverse covers all nd W of them, one GEMM forms every Theta_{I,w}, and the energy GEMM runs
+// over (Cholesky chunk, determinant, walker) with one trace pass; then one local-energy pass
+// over all (determinant, walker) pairs (each group of W walkers reading its determinant's
+// Psi^+ h).  Results: log-overlaps msd_ls, local energies msd_E and spin-summed traces msd_t,
+// each [ND][wk->W].
+void measure_msd(afqmc_walkers* wk, bool measure, int W, cudaStream_t st) {
+    Fp64Buffers& f = wk->f;
+    const int M = wk->M, nch = wk->Nchol, ND = wk->ND, Wld = wk->W;
+    const bool dense = W == Wld;   // (determinant, walker) pairs contiguous in the [ND][W] outputs
+    for (int I0 = 0; I0 < ND; I0 += f.msd_nd) {
+        const int nd = std::min(f.msd_nd, ND - I0);
+        for (int s = 0; s < 2; ++s) {
+            const int N = wk->N[s];
+            const int64_t mn = (int64_t)M * N, nn = (int64_t)N * N, ltI = (int64_t)nch * mn;
+            GemmArgs g;   // S[I][w] = Psi_I^+ Phi_w
+            g.m = N; g.n = N; g.k = M; g.nb1 = nd; g.nb2 = W;
+            g.A.ptr = f.Psi[s] + I0 * mn; g.A.op = OP_C; g.A.ld = N; g.A.s1 = mn;
+            g.B.ptr = f.Phi[s]; g.B.ld = N; g.B.s2 = mn;
+            g.C = f.S[s]; g.ldc = N; g.sc1 = (int64_t)W * nn; g.sc2 = nn;
+            zgemm(g, st);
+            batched_inverse_logdet(f.S[s], nn, N, nd * W, f.ld[s], true, f.msd_flag, st);
+            GemmArgs t;   // Theta[I][w] = Phi_w S[I][w]^-1
+            t.m = M; t.n = N; t.k = N; t.nb1 = nd; t.nb2 = W;
+            t.A.ptr = f.Phi[s]; t.A.ld = N; t.A.s2 = mn;
+            t.B.ptr = f.S[s]; t.B.ld = N; t.B.s1 = (int64_t)W * nn; t.B.s2 = nn;
+            t.C = f.Theta[s]; t.ldc = N; t.sc1 = (int64_t)W * mn; t.sc2 = mn;
+            zgemm(t, st);
+            const size_t esz = wk->Lt_real ? sizeof(double) : sizeof(cplx);
+            const char* Lt = static_cast<const char*>(f.Lt[s]) + esz * (size_t)(I0 * ltI);
+            const char* LtT = static_cast<const char*>(f.LtT[s]) + esz * (size_t)(I0 * ltI);
+            if (measure) {
+                for (int n0 = 0; n0 < nch; n0 += f.nc) {
+                    const int nc = std::min(f.nc, nch - n0);
+                    GemmArgs e;   // T[c][I][w] = Lt_{I, n0+c} Theta_{I,w}
+                    e.m = N; e.n = N; e.k = M; e.nb0 = nc; e.nb1 = nd; e.nb2 = W;
+                    e.A.real = wk->Lt_real;
+                    e.A.ptr = Lt + esz * (size_t)((int64_t)n0 * N * M);
+                    e.A.ld = M; e.A.s0 = (int64_t)N * M; e.A.s1 = ltI;
+                    e.B.ptr = f.Theta[s]; e.B.ld = N; e.B.s1 = (int64_t)W * mn; e.B.s2 = mn;
+                    e.C = f.T; e.ldc = N; e.sc0 = (int64_t)nd * W * nn; e.sc1 = (int64_t)W * nn; e.sc2 = nn;
+                    zgemm(e, st);
+                    trace_terms(f.T, nc, nd * W, N, n0, f.t[s], f.X[s], nch, st);
+                }
+            } else {
+                GemmArgs b;   // force bias only: t[I][w][n] = sum_{k,a} Theta_{I,w}[k][a] LtT_{I,n}[k][a]
+                b.m = W; b.n = nch; b.k = M * N; b.nb1 = nd;
+                b.A.ptr = f.Theta[s]; b.A.ld = mn; b.A.s1 = (int64_t)W * mn;
+                b.B.real = wk->Lt_real; b.B.ptr = LtT; b.B.op = OP_T; b.B.ld = mn; b.B.s1 = ltI;
+                b.C = f.t[s]; b.ldc = nch; b.sc1 = (int64_t)W * nch;
+                zgemm(b, st);
+            }
+        }
+        LocalEnergyArgs a;
+        a.W = nd * W; a.M = M; a.Nchol = nch; a.Nup = wk->N[0]; a.Ndn = wk->N[1];
+        for (int s = 0; s < 2; ++s) {
+            a.ht[s] = f.ht[s] + (int64_t)I0 * M * wk->N[s]; a.Theta[s] = f.Theta[s]; a.t[s] = f.t[s];
+            a.X[s] = measure ? f.X[s] : nullptr;
+            a.ht_stride[s] = (int64_t)M * wk->N[s];
+        }
+        a.wper = W;
+        a.E0 = wk->ham->E0; a.tau = wk->tau; a.fb_cap = 0.0;
+        a.E_L = dense ? f.msd_E + (int64_t)I0 * Wld : f.msd_Es;
+        a.xbar = nullptr;   // the force bias comes from the combination
+        a.flags = f.msd_flag + 1;
+        local_energy_forcebias(a, st);
+        if (dense) {
+            add_logdet(f.ld[0], f.ld[1], f.msd_ls + (int64_t)I0 * Wld, nd * W, st);
+            cplx_add(f.t[0], f.t[1], f.msd_t + (int64_t)I0 * Wld * nch, (int64_t)nd * W * nch, st);
+        } else {
+            for (int I = 0; I < nd; ++I) {
+                add_logdet(f.ld[0] + (int64_t)I * W, f.ld[1] + (int64_t)I * W, f.msd_ls + (int64_t)(I0 + I) * Wld, W,
+                           st);
+                cplx_add(f.t[0] + (int64_t)I * W * nch, f.t[1] + (int64_t)I * W * nch,
+                         f.msd_t + (int64_t)(I0 + I) * Wld * nch, (int64_t)W * nch, st);
+            }
+            if (measure)
+                cudaMemcpy2DAsync(f.msd_E + (int64_t)I0 * Wld, sizeof(cplx) * Wld, f.msd_Es, sizeof(cplx) * W,
+                                  sizeof(cplx) * W, nd, cudaMemcpyDeviceToDevice, st);
+        }
+    }
+}
+
 }  // namespace
 
 int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
@@ -217,17 +309,14 @@ int fp64_measure(afqmc_walkers* wk, bool measure, cudaStream_t st, int Wm) {
         measure_det(wk, 0, measure, W, wk->logS_old, wk->E_L, wk->flags, wk->flags, st);
         return AFQMC_OK;
     }
-    // multi-determinant trial: every determinant alone, then the overlap-weighted combination.
-    // A determinant with an exactly zero overlap has a non-finite term of weight zero: its
-    // local-energy status goes to a discarded word, and the combination checks the result.
+    // multi-determinant trial: every determinant alone (batched), then the overlap-weighted
+    // combination.  A determinant with an exactly zero overlap has a non-finite term of weight
+    // zero: its local-energy status goes to a discarded word, and the combination checks the
+    // result.
     Fp64Buffers& f = wk->f;
     const int nch = wk->Nchol;
     cudaMemsetAsync(f.msd_flag, 0, sizeof(unsigned), st);
-    for (int I = 0; I < wk->ND; ++I) {
-        measure_det(wk, I, measure, W, f.msd_ls + (int64_t)I * wk->W, f.msd_E + (int64_t)I * wk->W, f.msd_flag,
-                    f.msd_flag + 1, st);
-        cplx_add(f.t[0], f.t[1], f.msd_t + (int64_t)I * wk->W * nch, (int64_t)W * nch, st);
-    }
+    measure_msd(wk, measure, W, st);
     MsdArgs a;
     a.W = W; a.ND = wk->ND; a.Nchol = nch; a.ldw = wk->W;
     a.cc = f.msd_cc; a.ls = f.msd_ls; a.E = measure ? f.msd_E : nullptr; a.t = f.msd_t;
@@ -308,13 +397,20 @@ int fp64_propagate_and_weight(afqmc_walkers* wk, const double* x, cudaStream_t s
         add_logdet(f.ld[0], f.ld[1], wk->logS_new, W, st);
     } else {   // log <psi_T|Phi'> over the determinants
         cudaMemsetAsync(f.msd_flag, 0, sizeof(unsigned), st);
-        for (int I = 0; I < wk->ND; ++I) {
+        for (int I0 = 0; I0 < wk->ND; I0 += f.msd_nd) {   // determinants batched with the walkers
+            const int nd = std::min(f.msd_nd, wk->ND - I0);
             for (int s = 0; s < 2; ++s) {
                 const int N = wk->N[s];
-                overlap(f.Psi[s] + (int64_t)I * M * N, f.Pa[s], f.S[s], M, N, W, st);
-                batched_inverse_logdet(f.S[s], (int64_t)N * N, N, W, f.ld[s], false, f.msd_flag, st);
+                const int64_t mn = (int64_t)M * N, nn = (int64_t)N * N;
+                GemmArgs g;   // S[I][w] = Psi_I^+ Phi'_w
+                g.m = N; g.n = N; g.k = M; g.nb1 = nd; g.nb2 = W;
+                g.A.ptr = f.Psi[s] + I0 * mn; g.A.op = OP_C; g.A.ld = N; g.A.s1 = mn;
+                g.B.ptr = f.Pa[s]; g.B.ld = N; g.B.s2 = mn;
+                g.C = f.S[s]; g.ldc = N; g.sc1 = (int64_t)W * nn; g.sc2 = nn;
+                zgemm(g, st);
+                batched_inverse_logdet(f.S[s], nn, N, nd * W, f.ld[s], false, f.msd_flag, st);
             }
-            add_logdet(f.ld[0], f.ld[1], f.msd_ls + (int64_t)I * W, W, st);
+            add_logdet(f.ld[0], f.ld[1], f.msd_ls + (int64_t)I0 * W, nd * W, st);
         }
         MsdArgs a;
         a.W = W; a.ND = wk->ND; a.Nchol = nch; a.ldw = W;

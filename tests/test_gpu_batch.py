@@ -68,7 +68,7 @@ def test_fp64_batch_matches_oracle(pad):
     with Batch(sysdefs, tau, k_qr=k_qr, pad_mode=pad) as b:
         if pad == api.PAD_ALWAYS:
             shape, _ = b.info(0)
-            assert tuple(shape[:3]) == (64, 32, 32)   # M' >= 12 + 29, N' = 32, Nchol' = 32
+            assert tuple(shape[:3]) == (64, 8, 32)    # M' >= 12 + 5, N' = 8, Nchol' = 32
         trace = b.step(nsteps, seed=seed, measure_every=1)
         for s, sd in enumerate(sysdefs):
             emix, wk, E_now = oracle_run(sd, s, seed, nsteps, tau, k_qr)
@@ -119,9 +119,10 @@ def test_mixed_batch_within_1mha_of_fp64():
 def test_energy_launch_forms_agree():
     """One persistent energy launch over every system's tiles (K chunks of 32 or 16) and one
     launch per system: the same tiles, the same arithmetic, the same trajectories.  The systems
-    pad to three different tile shapes (N' = 32, 64, 128), so one launch mixes them."""
+    pad to three different tile shapes (N' = 16 and 104: the generic epilogue, 8 and 1
+    walker-spins per tile; N' = 32: a fixed-N' epilogue), so one launch mixes them."""
     import ctypes
-    dims = [syn.UnevenSystem(M=40, N=10, Nchol=200, W=9), syn.UnevenSystem(M=160, N=40, Nchol=96, W=7),
+    dims = [syn.UnevenSystem(M=40, N=10, Nchol=200, W=9), syn.UnevenSystem(M=160, N=32, Nchol=96, W=7),
             syn.UnevenSystem(M=400, N=100, Nchol=64, W=3)]
     sysdefs = systems(dims, seed=13)
     tau, k_qr, nsteps, seed = 0.01, 4, 6, 3
@@ -131,7 +132,7 @@ def test_energy_launch_forms_agree():
     for multi, bk in ((1, 32), (1, 16), (0, 32)):
         with Batch(sysdefs, tau, precision=api.PREC_BF16X3, k_qr=k_qr) as b:
             assert lib.afqmc_debug_set_batch_energy(b.b, multi, bk) == 0
-            assert [int(b.info(s)[0][1]) for s in range(3)] == [32, 64, 128]
+            assert [int(b.info(s)[0][1]) for s in range(3)] == [16, 32, 104]
             traces.append(b.step(nsteps, seed=seed, measure_every=1))
             energies.append([b.energy(s)[0] for s in range(3)])
             shape, _ = b.info(0)

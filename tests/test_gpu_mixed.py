@@ -51,7 +51,7 @@ def test_energy_at_start_matches_fp64(M, N, nch, W):
 
 
 @pytest.mark.parametrize("M,N,nch,W,steps,me", [(128, 32, 640, 32, 12, 1), (128, 64, 256, 8, 8, 3),
-                                                 (256, 128, 512, 4, 6, 1)])
+                                                 (256, 128, 512, 4, 6, 1), (128, 24, 320, 12, 8, 1)])
 def test_trajectory_matches_fp64_within_1mha(M, N, nch, W, steps, me):
     h, L, E0, Psi = system(M, N, nch, 21)
     x = syn.make_fields(steps, W, nch, seed=0)

@@ -93,7 +93,7 @@ def energy_call(dbg, Lt, Th, Np, Nchol, nws, M, terms, pair):
         rc = dbg.afqmc_debug_energy(Lt.ctypes.data, Th.ctypes.data, Np, Nchol, nws, M, terms, t.ctypes.data,
                                     X.ctypes.data)
     finally:
-        dbg.afqmc_debug_set_energy_variant(0)
+        dbg.afqmc_debug_set_energy_variant(1)   # the library default: CTA pairs
     assert rc == 0, api.afqmc_last_error()
     return t, X
 
@@ -164,12 +164,17 @@ def test_exact_mode_integer_products_are_exact(dbg):
 @pytest.mark.parametrize("pair", [0, 1])
 @pytest.mark.parametrize("terms", [3, 4, 5])
 @pytest.mark.parametrize("Np,Nchol,nws,M", [(128, 3, 2, 128), (64, 5, 3, 192), (32, 9, 5, 128), (128, 2, 3, 512),
-                                            (128, 41, 9, 256)])
+                                            (128, 41, 9, 256),
+                                            (8, 37, 21, 64), (24, 11, 7, 128), (40, 7, 4, 192), (56, 5, 3, 128),
+                                            (120, 3, 2, 256), (16, 600, 33, 64)])
 def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M, terms, pair):
     """Both kernel forms (one CTA per tile; CTA pairs with M = 256 MMAs) and all three product
     sets against their exact float64 emulation.  The shapes include an odd number of Cholesky
     groups (the last pair's second CTA has no rows), ragged walker-spin groups, and more pair
-    tiles than the GPU holds at once (persistent loop, barrier phases wrapping)."""
+    tiles than the GPU holds at once (persistent loop, barrier phases wrapping).  Np = 32, 64
+    and 128 run the fixed-Np epilogues; the other multiples of 8 the generic one, whose tiles
+    hold floor(128 / Np) Cholesky vectors by floor(128 / Np) walker-spins with padding rows and
+    columns (Np = 40: 120 of 128)."""
     rng = np.random.default_rng(Np * 7 + Nchol)
     Lt = rng.standard_normal((Nchol, Np, M)) * 0.1
     Th = rng.standard_normal((nws, 2, Np, M)) * 0.1
