@@ -309,10 +309,12 @@ def run_batch(args, rank, world):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.nvtx.range_push("afqmc_timed")
         ev0.record()
         b.step(args.steps, seed=seed, measure_every=1)
         ev1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = ev0.elapsed_time(ev1)
     Wtot = sum(d.W for d in dims)
     value = world * Wtot * args.steps / (ms / 1e3)

@@ -48,7 +48,7 @@ extern "C" {
 #define AFQMC_ERR_SINGULAR    -5  /* trial/walker overlap is exactly singular   */
 #define AFQMC_ERR_TIMEOUT     -6  /* a bounded device wait gave up              */
 #define AFQMC_ERR_CUDA        -7  /* a CUDA runtime call failed                 */
-#define AFQMC_ERR_UNSUPPORTED -8  /* valid request this build does not handle   */
+#define AFQMC_ERR_UNSUPPORTED -8  /* valid request the library does not handle  */
 
 /* ---- options ----------------------------------------------------------- */
 #define AFQMC_PREC_FP64    0  /* every contraction in FP64 (DFMA)                       */
