@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -50,6 +52,20 @@ void set_error(int code, const std::string& msg) {
 LaunchPolicy& launch_policy() {
     static thread_local LaunchPolicy p;
     return p;
+}
+
+cudaError_t raise_dyn_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;   // (device, kernel) -> limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = set[{dev, func}];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 bool stream_capturing(cudaStream_t st) {

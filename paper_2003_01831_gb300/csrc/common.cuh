@@ -70,6 +70,16 @@ LaunchPolicy& launch_policy();
 // true while `st` is being captured into a CUDA graph (timing events are then skipped)
 bool stream_capturing(cudaStream_t st);
 
+// Raises `func`'s dynamic shared-memory limit on the current device to at least `bytes`, never
+// lowering it: launches of one kernel with different sizes can sit in one captured graph (a
+// batch of uneven systems), and every node needs the limit to cover its own size whenever it
+// is launched.
+cudaError_t raise_dyn_smem(const void* func, size_t bytes);
+template <typename F>
+cudaError_t raise_dyn_smem(F* func, size_t bytes) {
+    return raise_dyn_smem(reinterpret_cast<const void*>(func), bytes);
+}
+
 #define AFQMC_CUDA_TRY(expr)                                                                   \
     do {                                                                                        \
         cudaError_t _e = (expr);                                                                \

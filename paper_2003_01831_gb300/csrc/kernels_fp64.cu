@@ -1310,14 +1310,14 @@ void batched_inverse_logdet(cplx* S, int64_t stride, int N, int count, cplx* log
         count_launch();
         if (C == 1) {
             auto launch1 = [&](auto kern) {
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                raise_dyn_smem(kern, sm);
                 kern<<<count, kGJT, sm, st>>>(S, stride, N, logdet, wi, flags);
             };
             if (cols == 1) launch1(gj_smem_kernel<1, 1>);
             else if (cols == 2) launch1(gj_smem_kernel<1, 2>);
             else launch1(gj_smem_kernel<1, 3>);
         } else {
-            cudaFuncSetAttribute(gj_smem_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            raise_dyn_smem(gj_smem_kernel<2, 2>, sm);
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3((unsigned)count * 2);
             cfg.blockDim = dim3(kGJT);

@@ -728,19 +728,23 @@ __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, Shar
 // chunks of 8: chunk c = 4 h + k holds compact columns 8 c .. 8 c + 7, all of walker-spin
 // 8 c / Np since Np is a multiple of 8, read from tensor memory eight columns at a time.  The
 // drain, the plane staging and the three sums are the fixed-Np epilogue's; the sums are kept
-// per chunk, parked in the plane once it is free (part[row][c][4]: Re t, Im t, Re X, Im X),
+// per chunk, parked in the plane once it is free (Re t, Im t, Re X, Im X per row and chunk),
 // and one warp reduces each (n-block, walker-spin) output over its Np rows and Np / 8 chunks
-// in a fixed order, in double.
+// in a fixed order.
 template <typename Release>
 __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, SharedCtl* ctl, float* plane,
                                                          float* colscale, int ng, int wg, int it, Release release) {
     const int Np = es.Np, G = es.G, GN = G * Np;
+    // x / Np and x / G by multiply and shift (exact for the x < 256 used here)
+    const uint32_t np_inv = es.np_inv, g_inv = es.g_inv;
+    auto divn = [&](int x) { return (int)(((uint32_t)x * np_inv) >> 16); };
+    auto divg = [&](int x) { return (int)(((uint32_t)x * g_inv) >> 16); };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = warp & 3;                // TMEM lane quadrant: rows 32 q .. 32 q + 31
     const int h = (warp - 2) >> 2;         // compact columns [32 h, 32 h + 32)
     const int row = q * 32 + lane;
     const bool rok = row < GN;
-    const int i_blk = row / Np, a = row % Np;
+    const int i_blk = divn(row), a = row - i_blk * Np;
     const int et = threadIdx.x - 64;       // 0..511
     const uint32_t tq = ctl->tmem_base + ((uint32_t)(q * 32) << 16);
     float* own = plane + row * kEPitch;
@@ -754,7 +758,7 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
     // are warp-uniform, so are the chunk conditions below
     // (a padding chunk reads column 0 instead, in range, and its values are never used)
     auto ccol = [&](int k) { return 32 * h + 8 * k; };
-    auto tcol = [&](int k) { return ccol(k) < GN ? (ccol(k) / Np) * 2 * Np + ccol(k) % Np : 0; };
+    auto tcol = [&](int k) { return ccol(k) < GN ? ccol(k) + divn(ccol(k)) * Np : 0; };   // j 2 Np + b0
     auto icol = [&](int k) { return ccol(k) < GN ? tcol(k) + Np : 0; };
     ebar();
     const bool got = warp_wait(&ctl->tfull[0], (uint32_t)it & 1u, &ctl->abort);
@@ -813,7 +817,7 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
         sri[k] = 0.f;
         dim_[k] = 0.f;
         if (rok && ccol(k) < GN) {
-            const int j = ccol(k) / Np, b0 = ccol(k) % Np;
+            const int j = divn(ccol(k)), b0 = ccol(k) - j * Np;
             const float* pb = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;   // Ti[b0 + e][a]
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
@@ -839,7 +843,7 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
         srr[k] = -sii[k];
         dre[k] = 0.f;
         if (rok && ccol(k) < GN) {
-            const int j = ccol(k) / Np, b0 = ccol(k) % Np;
+            const int j = divn(ccol(k)), b0 = ccol(k) - j * Np;
             const float* pb = plane + (i_blk * Np + b0) * kEPitch + j * Np + a;
 #pragma unroll
             for (int e = 0; e < 8; ++e) srr[k] = fmaf(tr[8 * k + e], pb[e * kEPitch], srr[k]);
@@ -848,28 +852,35 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
         }
     }
     ebar();                                    // every read of the Tr plane done
-    float* part = plane;                       // [128 rows][16 chunks][4]
+    // partial sums part[(c * 4 + v) * 128 + row]: the 32 lanes of a warp (consecutive rows) write
+    // consecutive words, free of bank conflicts
+    float* part = plane;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool v = rok && ccol(k) < GN;
-        *reinterpret_cast<float4*>(part + (row * 16 + 4 * h + k) * 4) =
-            v ? make_float4(dre[k], dim_[k], srr[k], 2.0f * sri[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float* pc = part + (4 * h + k) * 4 * 128 + row;
+        pc[0] = v ? dre[k] : 0.f;
+        pc[128] = v ? dim_[k] : 0.f;
+        pc[256] = v ? srr[k] : 0.f;
+        pc[384] = v ? 2.0f * sri[k] : 0.f;
     }
     ebar();
-    // one warp per (n-block, walker-spin) output: its Np rows x Np / 8 chunks, lanes striding the
-    // items in order, then a fixed shuffle tree
+    // one warp per (n-block, walker-spin) output: lane l adds rows l, l + 32, ... of the n-block
+    // over the output's Np / 8 chunks in order, then a fixed shuffle tree, in fp32 (at most Np^2
+    // products, the order of the fixed-Np epilogue's fp32 sums; GB300's FP64 pipe is 1/64 of the
+    // fp32 one, so double adds in every lane would dominate the tile)
     const int nck = Np / 8;
-    const int items = Np * nck;
     for (int o = warp - 2; o < G * G; o += kEEpi / 32) {
-        const int ib = o / G, jo = o % G;
-        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        for (int i = lane; i < items; i += 32) {
-            const int r = ib * Np + i / nck, c = jo * nck + i % nck;
-            const float4 v = *reinterpret_cast<const float4*>(part + (r * 16 + c) * 4);
-            s0 += v.x;
-            s1 += v.y;
-            s2 += v.z;
-            s3 += v.w;
+        const int ib = divg(o), jo = o - ib * G;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        for (int c = jo * nck; c < (jo + 1) * nck; ++c) {
+            const float* pc = part + c * 4 * 128 + ib * Np;
+            for (int r = lane; r < Np; r += 32) {
+                s0 += pc[r];
+                s1 += pc[128 + r];
+                s2 += pc[256 + r];
+                s3 += pc[384 + r];
+            }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -1785,7 +1796,7 @@ int g_num_sms = 0;
 template <int BN, bool EXACT>
 int launch_gemm(const CUtensorMap* m, const TileShape& sh, const EpiParams& epi, unsigned* flags, cudaStream_t st) {
     const size_t sm = gemm_smem<BN>();
-    cudaFuncSetAttribute(tc_gemm_kernel<BN, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(tc_gemm_kernel<BN, EXACT>, sm);
     const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
     const int grid = (int)std::min<int64_t>(sh.tiles, cap);
     count_launch();
@@ -1798,7 +1809,7 @@ int launch_gemm(const CUtensorMap* m, const TileShape& sh, const EpiParams& epi,
 template <int Np, int BK, int AP>
 int launch_energy(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
     const size_t sm = energy_smem<BK, AP, 256>();
-    cudaFuncSetAttribute(tc_energy_kernel<Np, BK, AP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(tc_energy_kernel<Np, BK, AP>, sm);
     const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
     const int grid = (int)std::min<int64_t>(es.tiles, cap);
     count_launch();
@@ -1814,7 +1825,7 @@ template <int Np, int BK, int AP>
 int launch_energy_pair(const CUtensorMap* m, const EnergyShape& es, unsigned* flags, cudaStream_t st) {
     auto kern = tc_energy_pair_kernel<Np, BK, AP>;
     const size_t sm = energy_smem<BK, AP, 128>();
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(kern, sm);
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(kEThreads);
     cfg.dynamicSmemBytes = sm;
@@ -1910,6 +1921,8 @@ int energy_setup(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, 
     es.Np = Np;
     es.Q = Np / 32;
     es.G = 128 / Np;
+    es.np_inv = (65536u + (uint32_t)Np - 1) / (uint32_t)Np;
+    es.g_inv = (65536u + (uint32_t)es.G - 1) / (uint32_t)es.G;
     es.Nchol = Nchol;
     es.nws = nws;
     es.n_groups = (Nchol + es.G - 1) / es.G;
@@ -1934,7 +1947,7 @@ int launch_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nw
                         cudaStream_t st) {
     auto kern = tc_energy_multi_kernel<BK, AP>;
     const size_t sm = energy_smem<BK, AP, 128>();
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(kern, sm);
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(kEThreads);
     cfg.dynamicSmemBytes = sm;
@@ -2081,7 +2094,7 @@ int tc_gemm3(const Split3& A, BatchMap amap, const Split3& B, BatchMap bmap, int
     sh.a_rows = A.rows;
     sh.b_rows = B.rows;
     const size_t smem = 1024 + (size_t)kG3Stages * kG3StageBytes + sizeof(SharedCtl);
-    cudaFuncSetAttribute(tc_gemm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_dyn_smem(tc_gemm3_kernel, smem);
     const int cap = launch_policy().grid_cap > 0 ? std::min(launch_policy().grid_cap, tc_num_sms()) : tc_num_sms();
     const int grid = (int)std::min<int64_t>(sh.tiles, cap);
     count_launch();

@@ -125,6 +125,7 @@ int tc_gemm(const SplitMat& A, BatchMap amap, const SplitMat& B, BatchMap bmap, 
 // Shape, operands and outputs of one fused energy contraction (kernels_tc.cu).
 struct EnergyShape {
     int Np, Q, G;
+    uint32_t np_inv, g_inv;   // ceil(2^16 / Np), ceil(2^16 / G): x / Np = (x np_inv) >> 16 for x < 256
     int Nchol, nws;
     int n_groups, ws_groups;
     int ws_super;     // ws groups per L2 super-block

@@ -703,7 +703,7 @@ SplitMat smat(const bf16* h, const bf16* l, int64_t K, int64_t rows, int64_t bat
 void untranspose_walkers(TcState* s, cudaStream_t st) {
     dim3 g((s->M + 31) / 32, 2 * s->W);
     const size_t sm = (size_t)2 * s->N * 33 * sizeof(double);
-    cudaFuncSetAttribute(phi_untranspose_split_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(phi_untranspose_split_kernel<2>, sm);
     count_launch();
     phi_untranspose_split_kernel<2><<<g, kT, sm, st>>>(s->PhiT[s->cur], s->M, 2 * s->N,
                                                        reinterpret_cast<__half*>(s->Phi_h),
@@ -1187,7 +1187,7 @@ int tc_qr(afqmc_walkers* wk, cudaStream_t st) {
     }
     // Cholesky factor and its inverse X = R^-1 in place of the Gram matrices (dead walkers: X = I)
     const size_t sm = (size_t)N * (N + 1) / 2 * sizeof(cplx);
-    cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    raise_dyn_smem(chol_inv_kernel, sm);
     count_launch();
     chol_inv_kernel<<<WS, kT, sm, st>>>(s->S, N, wk->weight, wk->flags);
     // Q^T = (Phi X)^T into the proposal buffer, then back over the current walkers
@@ -1201,7 +1201,7 @@ int tc_qr(afqmc_walkers* wk, cudaStream_t st) {
         // (8 W N M halves each), scales in the two-slice operand's scale buffer (rebuilt below)
         dim3 g((M + 31) / 32, WS);
         const size_t tsm = (size_t)N2 * 33 * sizeof(double);
-        cudaFuncSetAttribute(phi_untranspose_split_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm);
+        raise_dyn_smem(phi_untranspose_split_kernel<3>, tsm);
         count_launch();
         phi_untranspose_split_kernel<3><<<g, kT, tsm, st>>>(s->PhiT[s->cur], M, (int)N2,
                                                             reinterpret_cast<__half*>(s->PD3[0]),
