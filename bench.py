@@ -473,6 +473,78 @@ def run_bp(args, rank, world):
     return 0
 
 
+def run_grad(args, rank, world):
+    """Differentiation workload (M=256, N=64+64, Nchol=1280, W=256 walkers near the trial): each
+    timed step is one forward local energy and log-overlap plus the backward pass with respect to
+    the trial orbitals and the Cholesky tensor, through autograd.LocalEnergy on device tensors
+    (FP64 adjoint, Theta recomputed).  value = walker gradients per second."""
+    import torch
+    from paper_2003_01831_gb300 import synthetic as syn
+    from paper_2003_01831_gb300.autograd import local_energy
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = syn.workload("m256", W=args.walkers or 256)
+    rng = wl.rng()
+    h, L, E0 = syn.make_hamiltonian(wl.M, wl.Nchol, rng)
+    Psi = syn.make_trial(h, wl.Nup, wl.Ndn)
+    W, M = wl.W, wl.M
+    Phi = []
+    for s in range(2):
+        z = Psi[s][None] + 0.1 * (rng.standard_normal((W, M, wl.Nup)) + 1j * rng.standard_normal((W, M, wl.Nup)))
+        Phi.append(torch.tensor(np.linalg.qr(z)[0], device=dev))
+    Lt = torch.tensor(L, device=dev, requires_grad=True)
+    del L
+    ht = torch.tensor(h, device=dev)
+    Pu = torch.tensor(Psi[0], device=dev, requires_grad=True)
+    Pd = torch.tensor(Psi[1], device=dev, requires_grad=True)
+    gE = torch.ones(W, dtype=torch.complex128, device=dev)
+
+    def one():
+        E, lS = local_energy(Pu, Pd, Lt, ht, E0, Phi[0], Phi[1])
+        loss = torch.sum(torch.real(torch.conj(gE) * E + lS))
+        Pu.grad = Pd.grad = Lt.grad = None
+        loss.backward()
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            one()
+        ev1.record()
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    N, nch = wl.Nup, wl.Nchol
+    # algorithmic FP64 flops per evaluation, per (Cholesky vector, walker, spin): T = Ltilde Theta in
+    # the forward and again in the backward (4 N^2 M each, real x complex), U = Theta T (8 M N^2),
+    # sum_n L_n U_n (4 M^2 N); plus the dL products F = V Psi^+ (8 M^2 N per vector and spin)
+    flops = 2.0 * W * nch * (16.0 * N * N * M + 4.0 * M * M * N) + 2.0 * nch * 8.0 * M * M * N
+    clocks = clk.summary()
+    fp64_peak = 304 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    ach = flops / (ms / 1e3) / 1e12
+    line = {"metric": "walker gradients/sec (local energy and log-overlap w.r.t. trial and Cholesky tensor) "
+                      "at M=256, N=64, Nchol=1280",
+            "value": world * W / (ms / 1e3), "unit": "walker-gradients/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"differentiation system M=256, N=64+64, Nchol=1280, W={W} walkers near the "
+                                   "trial; one step = forward + backward through autograd.LocalEnergy on device "
+                                   "tensors", "l2": "inputs larger than L2 (L 0.67 GB)",
+                       "parallelism": f"walker replicas x{world}"},
+            "clocks": clocks,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": ach / fp64_peak, "traffic": None,
+                         "kernel": "whole forward + backward (FP64 adjoint GEMMs)",
+                         "peak_source": "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fp64_variant(args, rank, world):
     """The wider rows on the FP64 path, at the m128 system (M=128, N=32+32, Nchol=640,
     W=512, tau=0.005, QR/10, energy every step, Philox fields):
@@ -639,6 +711,12 @@ def main():
                               "single-system throughput workload only"}), flush=True)
             return 0
         return run_thc(args, rank, world)
+    if args.workload == "grad256":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
+                              "single-system throughput workload only"}), flush=True)
+            return 0
+        return run_grad(args, rank, world)
     if args.workload == "bp512":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline is defined for the "
