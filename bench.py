@@ -36,16 +36,39 @@ WORKLOAD = ("solid-like synthetic Hamiltonian: M=512, N_up=N_dn=128, Nchol=2560,
             "L_n decay exp(-n/200), W=1024 walkers/GPU, tau=0.005, QR/5, energy measured every step")
 
 
+def workload_desc(wl):
+    """The config description of a single-system workload (the throughput system's fixed text)."""
+    if wl.name == "m512":
+        return WORKLOAD.replace("W=1024", f"W={wl.W}")
+    kind = "solid-like" if wl.band else "molecule-like"
+    return (f"{kind} synthetic Hamiltonian: M={wl.M}, N_up={wl.Nup}, N_dn={wl.Ndn}, Nchol={wl.Nchol}, "
+            f"L_n decay exp(-n/{wl.decay:g}), W={wl.W} walkers/GPU, tau={wl.tau}, QR/{wl.k_qr}, "
+            "energy measured every step")
+
+
+def workload_metric(wl):
+    return METRIC if wl.name == "m512" else f"walker-steps/sec at M={wl.M},N={wl.Nup},Nchol={wl.Nchol}"
+
+
+def l2_note(wl):
+    """Whether the step's streamed inputs (Ltilde planes, Theta pair) exceed the 129 MB L2."""
+    lt = 3 * 2 * wl.Nchol * wl.Nup * wl.M
+    th = 2 * 2 * 2 * 2 * wl.W * wl.Nup * wl.M
+    big = lt > 129e6 or th > 129e6
+    return (f"inputs larger than L2 (Ltilde planes {lt / 1e9:.2f} GB, Theta pair {th / 1e9:.2f} GB per step)" if big
+            else f"inputs fit in L2 (Ltilde planes {lt / 1e6:.0f} MB, Theta pair {th / 1e6:.0f} MB); no flush")
+
+
 # DRAM bytes of one launch of the energy kernel at this workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, one ncu capture of this script; the summary and its command are in
 # profiles/).  The figure holds for the kernel source it was taken on: a digest of that source
 # (the energy-kernel section of kernels_tc.cu and the PTX wrappers) gates it.
 # DRAM bytes per launch of the energy kernel at the bench workload: one-pass ncu counters on a
-# W = 16 launch of the same kernel (4,048,846,080 read + 5,892,352 written), scaled by 64 to
+# W = 16 launch of the same kernel (4,048,949,248 read + 5,960,448 written), scaled by 64 to
 # W = 1024 -- the kernel streams L~ once per window of 8 walker-spin groups, so its traffic grows
 # in proportion to W (profiles/energy_pair_kernel_traffic_m512.md).  Reported only while the
 # kernel's source matches the digest it was measured on.
-ENERGY_TRAFFIC = {"bytes": 64 * (4048846080 + 5892352), "src_digest": "de2ba17b8fb469f4"}
+ENERGY_TRAFFIC = {"bytes": 64 * (4048949248 + 5960448), "src_digest": "a89eae9f2e13e978"}
 
 
 def energy_src_digest() -> str:
@@ -853,13 +876,12 @@ def main():
         roof["step_floor_parts"] = floor_parts
         if issued:
             roof["issued_ceiling_frac"] = 1.0 / issued
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": workload_metric(wl), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f16 row-scaled splits (2-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.walkers == 0 else WORKLOAD.replace("W=1024", f"W={wl.W}"),
-                       "l2": "inputs larger than L2 (Ltilde 0.67 GB, Theta 1.1 GB per step)",
+            "config": {"workload": workload_desc(wl), "l2": l2_note(wl),
                        "parallelism": f"walker replicas x{world}"},
             "clocks": clocks, "e2e": e2e, "secondary": secondary,
             "gpu_launches": int(kernels_per_step * args.steps) if kernels_per_step > 0 else None,

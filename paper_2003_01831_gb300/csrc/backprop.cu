@@ -71,6 +71,54 @@ __global__ void to_orbital_major_kernel(const cplx* src, int W, int M, int N, co
     dst[((int64_t)i * W + w) * N + a] = v;
 }
 
+// Walker sum of the estimate on the tensor cores (BF16X3 walker sets).  With v_w = (w_w / sum w)
+// Theta_w and K' = (walker, orbital, re|im) = 2 W N, H = sum_w v_w Q_w^+ is the real GEMM
+// [A_re; A_im] . B^T: A_re[i][(w,a,0|1)] = (Re, Im) v_w[i][a], A_im[i][(w,a,0|1)] = (Im, -Re)
+// v_w[i][a], B[j][(w,a,0|1)] = (Re, Im) Q_w[j][a]; then Hr = A_re B^T and Hi = A_im B^T.  K' is
+// cut into nb chunks of kc (the three-slice GEMM's batches; the tail of the last is zero), so
+// A is [nb][2M][kc] and B [nb][M][kc], FP64 before the row split.
+__global__ void bp_pack_kernel(const cplx* Th, const cplx* Q, const cplx* weight, const cplx* tot, int W, int M,
+                               int N, int64_t kc, int nb, double* A, double* B) {
+    const int64_t total = (int64_t)nb * M * kc;
+    const int64_t K2 = 2LL * W * N;
+    for (int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; id < total; id += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t kk = id % kc;
+        const int64_t r = id / kc;
+        const int i = (int)(r % M);
+        const int64_t b = r / M;
+        const int64_t kp = b * kc + kk;
+        double are = 0.0, aim = 0.0, bv = 0.0;
+        if (kp < K2) {
+            const int64_t K = kp >> 1;
+            const int c = (int)(kp & 1);
+            const int w = (int)(K / N), a = (int)(K % N);
+            const int64_t e = ((int64_t)w * M + i) * N + a;
+            const cplx ww = weight[w];
+            const cplx v = (ww.re == 0.0 && ww.im == 0.0) ? cplx{0.0, 0.0} : cdiv(ww, *tot) * Th[e];
+            are = c == 0 ? v.re : v.im;
+            aim = c == 0 ? v.im : -v.re;
+            bv = c == 0 ? Q[e].re : Q[e].im;
+        }
+        A[(b * 2 * M + i) * kc + kk] = are;
+        A[(b * 2 * M + M + i) * kc + kk] = aim;
+        B[(b * M + i) * kc + kk] = bv;
+    }
+}
+
+// G[j][i] = sum_b (P_b[i][j] + i P_b[M + i][j]) over the chunk products P_b [2M][M], in chunk order
+__global__ void bp_combine_kernel(const double* P, int nb, int M, cplx* G) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t MM = (int64_t)M * M;
+    if (id >= MM) return;
+    const int i = (int)(id / M), j = (int)(id % M);
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        re += P[(int64_t)b * 2 * MM + (int64_t)i * M + j];
+        im += P[(int64_t)b * 2 * MM + (int64_t)(M + i) * M + j];
+    }
+    G[(int64_t)j * M + i] = cplx{re, im};
+}
+
 // b = (sum_c a_c)^T over nc partial M x M products a_c = a + c M^2, summed in chunk order
 __global__ void sum_transpose_kernel(const cplx* a, int nc, int M, cplx* b) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -294,6 +342,46 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
             g.B.ptr = S; g.B.ld = N; g.B.s1 = (int64_t)N * N;
             g.C = Th; g.ldc = N; g.sc1 = mn;
             zgemm(g, st);
+        }
+        if (wk->tc) {   // the walker sum on the tensor cores (~1e-8 relative), into G = H^T
+            const int64_t K2 = 2LL * W * N;
+            const int64_t kc = std::min<int64_t>(8192, (K2 + 7) / 8 * 8);
+            const int nbk = (int)((K2 + kc - 1) / kc);
+            const int64_t na = (int64_t)nbk * 2 * M * kc, nbb = (int64_t)nbk * M * kc;
+            Scratch ts(st);
+            double* A64 = ts.get<double>(na);
+            double* B64 = ts.get<double>(nbb);
+            bf16* a3[3] = {ts.get<bf16>(na), ts.get<bf16>(na), ts.get<bf16>(na)};
+            bf16* b3[3] = {ts.get<bf16>(nbb), ts.get<bf16>(nbb), ts.get<bf16>(nbb)};
+            float* as = ts.get<float>((int64_t)nbk * 2 * M);
+            float* bs = ts.get<float>((int64_t)nbk * M);
+            double* Pp = ts.get<double>((int64_t)nbk * 2 * MM);
+            if (!A64 || !B64 || !a3[0] || !a3[1] || !a3[2] || !b3[0] || !b3[1] || !b3[2] || !as || !bs || !Pp)
+                return fail(AFQMC_ERR_OOM, "bp_rdm1: tensor-core walker sum workspace");
+            count_launch();
+            bp_pack_kernel<<<(unsigned)std::min<int64_t>(nb((int64_t)nbk * M * kc), 1 << 20), kT, 0, st>>>(
+                Th, Q, wk->weight, tot, W, M, N, kc, nbk, A64, B64);
+            split3_rows(A64, (int64_t)nbk * 2 * M, kc, a3[0], a3[1], a3[2], as, st);
+            split3_rows(B64, (int64_t)nbk * M, kc, b3[0], b3[1], b3[2], bs, st);
+            Split3 sa, sb;
+            for (int q = 0; q < 3; ++q) {
+                sa.p[q] = a3[q];
+                sb.p[q] = b3[q];
+            }
+            sa.scale = as; sa.K = kc; sa.rows = 2LL * M; sa.batch = nbk; sa.batch_stride = 2LL * M * kc;
+            sb.scale = bs; sb.K = kc; sb.rows = M; sb.batch = nbk; sb.batch_stride = (int64_t)M * kc;
+            EpiParams e;
+            e.kind = EPI3_F64;
+            e.rows_valid = 2LL * M;
+            e.cols_valid = M;
+            e.ld = M;
+            e.ob = 2 * MM;
+            e.out_f64 = Pp;
+            AFQMC_TRY(tc_gemm3(sa, BatchMap{1, nbk}, sb, BatchMap{1, nbk}, 2LL * M, M, kc, nbk, e, flag, st));
+            count_launch();
+            bp_combine_kernel<<<nb(MM), kT, 0, st>>>(Pp, nbk, M, G[s]);
+            check_finite(reinterpret_cast<const double*>(G[s]), 2 * MM, flag, st);
+            continue;
         }
         // H = sum_w (w_w / sum w) Theta_w Psi_bp,w^+ over K = (walker, orbital); G = H^T.  The
         // K sum runs as nck batched partial products over chunks of W / nck walkers, added in
