@@ -440,8 +440,9 @@ def run_bp(args, rank, world):
     # Taylor terms (complex, 8 W M^2 N each) and B twice (complex x real) per spin; then per spin
     # the overlap, Theta (8 W M N^2 each), the inverse (~8 W N^3) and the walker sum (8 M^2 W N)
     back = nbp * (4.0 * W * M * M * nch + sum((8.0 * K + 8.0) * W * M * M * n for n in Ns))
-    # final estimate: overlap, inverse and Theta in FP64; the walker sum M x M x (W N) in FP64 on
-    # an FP64 walker set, on the tensor cores (three slices) on a BF16X3 one
+    # final estimate: overlap, inverse, Theta and the walker sum M x M x (W N): in FP64 on an FP64
+    # walker set; on a BF16X3 one the three GEMMs run on the tensor cores and the inverse in
+    # float pairs on the fp32 pipe
     est_fp64 = sum(16.0 * W * M * n * n + 8.0 * W * n ** 3 for n in Ns)
     est_sum = sum(8.0 * M * M * W * n for n in Ns)
     est = est_fp64 + est_sum
@@ -455,12 +456,11 @@ def run_bp(args, rank, world):
                              "achieved_tflops": back / (back_ms / 1e3) / 1e12,
                              "peak": back_peak, "bound": "tensor" if tc_back else "alu (FP64 DFMA)",
                              "frac": back / (back_ms / 1e3) / 1e12 / back_peak},
-              "final_estimate": ({"ms": est_ms, "algorithmic_flops": est, "fp64_flops": est_fp64,
-                                  "tensor_flops": est_sum,
-                                  "achieved_tflops": est_fp64 / (est_ms / 1e3) / 1e12, "peak": fp64_peak,
-                                  "bound": "alu (FP64 DFMA: overlap, inverse, Theta; the walker sum on tcgen05 "
-                                           "is left out of achieved)",
-                                  "frac": est_fp64 / (est_ms / 1e3) / 1e12 / fp64_peak} if tc_back else
+              "final_estimate": ({"ms": est_ms, "algorithmic_flops": est,
+                                  "achieved_tflops": est / (est_ms / 1e3) / 1e12, "peak": bf16_sust,
+                                  "bound": "tensor (overlap, Theta and walker-sum GEMMs; the inverse in float "
+                                           "pairs on the fp32 pipe)",
+                                  "frac": est / (est_ms / 1e3) / 1e12 / bf16_sust} if tc_back else
                                  {"ms": est_ms, "algorithmic_flops": est,
                                   "achieved_tflops": est / (est_ms / 1e3) / 1e12, "peak": fp64_peak,
                                   "bound": "alu (FP64 DFMA)",
@@ -470,7 +470,7 @@ def run_bp(args, rank, world):
     # then per spin overlap, inverse, Theta, two layout passes, walker-sum GEMM, transpose, check
     qr = sum(1 for k in range(nbp) if wl.k_qr > 0 and (k + 1) % wl.k_qr == 0 and k + 1 < nbp)
     if prec == api.PREC_BF16X3:   # layout passes, per back step the three-slice propagation's kernels
-        launches = 1 + 2 + 2 + nbp * (8 + 2 * K) + qr * 6 + 2 + 2 * 9   # estimate: pack, splits, GEMM, combine
+        launches = 1 + 2 + 2 + nbp * (8 + 2 * K) + qr * 6 + 2 + 14 + 2 * 6   # estimate: Green's functions, walker sums
     else:
         launches = 1 + 2 + nbp * (2 + 2 * (K + 2)) + 2 * qr + 2 * 8
     line = {"metric": "back-propagated walker-steps/sec (one-body density matrix of a window at M=512, N=128, "
@@ -490,18 +490,18 @@ def run_bp(args, rank, world):
             "traces": trace, "phases": phases,
             # the phase that takes most of the call: back steps (three-slice tcgen05 propagation on
             # a BF16X3 walker set, zgemm on an FP64 one) or the FP64 final estimate
-            "roofline": {"bound": "tensor" if dom == "back_steps" and tc_back else "alu",
+            "roofline": {"bound": "tensor" if tc_back else "alu",
                          "achieved": phases[dom]["achieved_tflops"], "peak": phases[dom]["peak"],
                          "unit": "TFLOP/s", "frac": phases[dom]["frac"], "traffic": None,
                          "kernel": ("afqmc_bp_rdm1 back steps (tcgen05 three-slice propagation, adjoint)"
                                     if tc_back else "afqmc_bp_rdm1 back steps (FP64 zgemm)")
                          if dom == "back_steps" else
-                         ("afqmc_bp_rdm1 final estimate (FP64 overlap, batched inverse and Theta; walker sum "
-                          "on tcgen05)" if tc_back else
+                         ("afqmc_bp_rdm1 final estimate (overlap, Theta and walker sum on tcgen05, float-pair "
+                          "inverse)" if tc_back else
                           "afqmc_bp_rdm1 final estimate (FP64 zgemm, batched inverse, split walker sum)"),
                          "phase": dom,
                          "peak_source": (f"bf16_tflops_sustained of {src} peaks (algorithmic complex flops)"
-                                         if dom == "back_steps" and tc_back else
+                                         if tc_back else
                                          "FP64 DFMA pipe: 304 DFMA per clock x 2 flops x max SM clock")}}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -226,6 +226,52 @@ int bp_follow_comb(afqmc_walkers* wk, const int* idx, cplx* tmp, cudaStream_t st
 
 namespace {
 
+// Walker sum of the estimate on the tensor cores (~1e-8 relative): G = H^T with
+// H = sum_w (w_w / sum w) Theta_w Q_w^+, one three-slice GEMM over K' = 2 W N in chunks.
+int bp_walker_sum_tc(afqmc_walkers* wk, const cplx* Th, const cplx* Q, int N, const cplx* tot, cplx* Gs,
+                     unsigned* flag, cudaStream_t st) {
+    const int M = wk->M, W = wk->W;
+    const int64_t MM = (int64_t)M * M;
+    const int64_t K2 = 2LL * W * N;
+    const int64_t kc = std::min<int64_t>(8192, (K2 + 7) / 8 * 8);
+    const int nbk = (int)((K2 + kc - 1) / kc);
+    const int64_t na = (int64_t)nbk * 2 * M * kc, nbb = (int64_t)nbk * M * kc;
+    Scratch ts(st);
+    double* A64 = ts.get<double>(na);
+    double* B64 = ts.get<double>(nbb);
+    bf16* a3[3] = {ts.get<bf16>(na), ts.get<bf16>(na), ts.get<bf16>(na)};
+    bf16* b3[3] = {ts.get<bf16>(nbb), ts.get<bf16>(nbb), ts.get<bf16>(nbb)};
+    float* as = ts.get<float>((int64_t)nbk * 2 * M);
+    float* bs = ts.get<float>((int64_t)nbk * M);
+    double* Pp = ts.get<double>((int64_t)nbk * 2 * MM);
+    if (!A64 || !B64 || !a3[0] || !a3[1] || !a3[2] || !b3[0] || !b3[1] || !b3[2] || !as || !bs || !Pp)
+        return fail(AFQMC_ERR_OOM, "bp_rdm1: tensor-core walker sum workspace");
+    count_launch();
+    bp_pack_kernel<<<(unsigned)std::min<int64_t>(nb((int64_t)nbk * M * kc), 1 << 20), kT, 0, st>>>(
+        Th, Q, wk->weight, tot, W, M, N, kc, nbk, A64, B64);
+    split3_rows(A64, (int64_t)nbk * 2 * M, kc, a3[0], a3[1], a3[2], as, st);
+    split3_rows(B64, (int64_t)nbk * M, kc, b3[0], b3[1], b3[2], bs, st);
+    Split3 sa, sb;
+    for (int q = 0; q < 3; ++q) {
+        sa.p[q] = a3[q];
+        sb.p[q] = b3[q];
+    }
+    sa.scale = as; sa.K = kc; sa.rows = 2LL * M; sa.batch = nbk; sa.batch_stride = 2LL * M * kc;
+    sb.scale = bs; sb.K = kc; sb.rows = M; sb.batch = nbk; sb.batch_stride = (int64_t)M * kc;
+    EpiParams e;
+    e.kind = EPI3_F64;
+    e.rows_valid = 2LL * M;
+    e.cols_valid = M;
+    e.ld = M;
+    e.ob = 2 * MM;
+    e.out_f64 = Pp;
+    AFQMC_TRY(tc_gemm3(sa, BatchMap{1, nbk}, sb, BatchMap{1, nbk}, 2LL * M, M, kc, nbk, e, wk->flags, st));
+    count_launch();
+    bp_combine_kernel<<<nb(MM), kT, 0, st>>>(Pp, nbk, M, Gs);
+    check_finite(reinterpret_cast<const double*>(Gs), 2 * MM, flag, st);
+    return AFQMC_OK;
+}
+
 // G[s] (device, M x M each) from a complete window.  flag: device word, FLAG_NONFINITE when
 // G is not finite.
 int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
@@ -275,8 +321,14 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
             }
         }
         tc_T_to_canon(wk, QT, Qs, st);
+        // the estimate on the tensor cores: Green's functions of both spins, then per spin the
+        // walker sum
+        cplx* Ths[2] = {P0, P1};
+        AFQMC_TRY(tc_bp_green(wk, QT, wk->bp_Phi, Ths, st));
+        for (int s = 0; s < 2; ++s) AFQMC_TRY(bp_walker_sum_tc(wk, Ths[s], Qs[s], wk->N[s], tot, G[s], flag, st));
+        return AFQMC_OK;
     }
-    for (int k = wk->tc ? -1 : wk->bp_n - 1; k >= 0; --k) {
+    for (int k = wk->bp_n - 1; k >= 0; --k) {
         // A(k)^+ = sum_n conj(c_n) L_n for every walker, shared by both spins
         count_launch();
         conj_kernel<<<nb((int64_t)W * nch), kT, 0, st>>>(wk->bp_coef + (int64_t)k * W * nch, cc, (int64_t)W * nch);
@@ -342,46 +394,6 @@ int bp_rdm1(afqmc_walkers* wk, cplx* G[2], unsigned* flag, cudaStream_t st) {
             g.B.ptr = S; g.B.ld = N; g.B.s1 = (int64_t)N * N;
             g.C = Th; g.ldc = N; g.sc1 = mn;
             zgemm(g, st);
-        }
-        if (wk->tc) {   // the walker sum on the tensor cores (~1e-8 relative), into G = H^T
-            const int64_t K2 = 2LL * W * N;
-            const int64_t kc = std::min<int64_t>(8192, (K2 + 7) / 8 * 8);
-            const int nbk = (int)((K2 + kc - 1) / kc);
-            const int64_t na = (int64_t)nbk * 2 * M * kc, nbb = (int64_t)nbk * M * kc;
-            Scratch ts(st);
-            double* A64 = ts.get<double>(na);
-            double* B64 = ts.get<double>(nbb);
-            bf16* a3[3] = {ts.get<bf16>(na), ts.get<bf16>(na), ts.get<bf16>(na)};
-            bf16* b3[3] = {ts.get<bf16>(nbb), ts.get<bf16>(nbb), ts.get<bf16>(nbb)};
-            float* as = ts.get<float>((int64_t)nbk * 2 * M);
-            float* bs = ts.get<float>((int64_t)nbk * M);
-            double* Pp = ts.get<double>((int64_t)nbk * 2 * MM);
-            if (!A64 || !B64 || !a3[0] || !a3[1] || !a3[2] || !b3[0] || !b3[1] || !b3[2] || !as || !bs || !Pp)
-                return fail(AFQMC_ERR_OOM, "bp_rdm1: tensor-core walker sum workspace");
-            count_launch();
-            bp_pack_kernel<<<(unsigned)std::min<int64_t>(nb((int64_t)nbk * M * kc), 1 << 20), kT, 0, st>>>(
-                Th, Q, wk->weight, tot, W, M, N, kc, nbk, A64, B64);
-            split3_rows(A64, (int64_t)nbk * 2 * M, kc, a3[0], a3[1], a3[2], as, st);
-            split3_rows(B64, (int64_t)nbk * M, kc, b3[0], b3[1], b3[2], bs, st);
-            Split3 sa, sb;
-            for (int q = 0; q < 3; ++q) {
-                sa.p[q] = a3[q];
-                sb.p[q] = b3[q];
-            }
-            sa.scale = as; sa.K = kc; sa.rows = 2LL * M; sa.batch = nbk; sa.batch_stride = 2LL * M * kc;
-            sb.scale = bs; sb.K = kc; sb.rows = M; sb.batch = nbk; sb.batch_stride = (int64_t)M * kc;
-            EpiParams e;
-            e.kind = EPI3_F64;
-            e.rows_valid = 2LL * M;
-            e.cols_valid = M;
-            e.ld = M;
-            e.ob = 2 * MM;
-            e.out_f64 = Pp;
-            AFQMC_TRY(tc_gemm3(sa, BatchMap{1, nbk}, sb, BatchMap{1, nbk}, 2LL * M, M, kc, nbk, e, flag, st));
-            count_launch();
-            bp_combine_kernel<<<nb(MM), kT, 0, st>>>(Pp, nbk, M, G[s]);
-            check_finite(reinterpret_cast<const double*>(G[s]), 2 * MM, flag, st);
-            continue;
         }
         // H = sum_w (w_w / sum w) Theta_w Psi_bp,w^+ over K = (walker, orbital); G = H^T.  The
         // K sum runs as nck batched partial products over chunks of W / nck walkers, added in

@@ -150,6 +150,12 @@ int tc_apply_propagator(afqmc_walkers* wk, const afqmc::cplx* c, bool conj_c, do
 // Canonical walkers Phi[s] [W][M][N] (both spins) to / from the transposed planar layout.
 void tc_canon_to_T(afqmc_walkers* wk, afqmc::cplx* const* Phi, double* out_T, cudaStream_t st);
 void tc_T_to_canon(afqmc_walkers* wk, const double* in_T, afqmc::cplx* const* Phi, cudaStream_t st);
+// Green's functions of a back-propagation window's estimate on the tensor cores: per walker-spin
+// S = Psi_bp^+ Phi(0) (three-slice GEMM), S^-1 (float-pair Gauss-Jordan), Theta = Phi(0) S^-1
+// (exact-mode GEMM), written canonical to Theta[s] [W][M][N].  QT: Psi_bp in the transposed
+// planar layout; Phi0: the window's first walkers, canonical (step_tc.cu).
+int tc_bp_green(afqmc_walkers* wk, const double* QT, afqmc::cplx* const* Phi0, afqmc::cplx* const* Theta,
+                cudaStream_t st);
 int tc_qr(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st);
 int tc_sync_walkers_from_fp64(afqmc_walkers* wk, cudaStream_t st);

@@ -172,14 +172,15 @@ __global__ void canon_to_phiT_kernel(const cplx* Phi, int s, int W, int M, int N
     PhiT[base + (int64_t)j * M + k] = v.re;
     PhiT[base + (int64_t)N * M + (int64_t)j * M + k] = v.im;
 }
-__global__ void phiT_to_canon_kernel(const double* PhiT, int s, int W, int M, int N, cplx* Phi) {
+template <typename Real>
+__global__ void phiT_to_canon_kernel(const Real* PhiT, int s, int W, int M, int N, cplx* Phi) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)W * M * N) return;
     const int w = (int)(i / ((int64_t)M * N));
     const int64_t e = i % ((int64_t)M * N);
     const int k = (int)(e / N), j = (int)(e % N);
     const int64_t base = (((int64_t)w * 2 + s) * 2) * N * M;
-    Phi[i] = cplx{PhiT[base + (int64_t)j * M + k], PhiT[base + (int64_t)N * M + (int64_t)j * M + k]};
+    Phi[i] = cplx{(double)PhiT[base + (int64_t)j * M + k], (double)PhiT[base + (int64_t)N * M + (int64_t)j * M + k]};
 }
 // PhiT FP64 [WS][2N][M] -> Phi [WS][M][2N] row-scaled fp16 pair, or three slices (SLICES = 3,
 // as split3_rows; planes hi, lo, lo2), row = orbital k over the 2N values re | im.  Block = (32 orbitals, one walker-spin); the 2N x 32 tile sits in
@@ -904,8 +905,107 @@ void tc_T_to_canon(afqmc_walkers* wk, const double* in_T, cplx* const* Phi, cuda
     const int64_t n = (int64_t)s->W * s->M * s->N;
     for (int sp = 0; sp < 2; ++sp) {
         count_launch();
-        phiT_to_canon_kernel<<<nb(n), kT, 0, st>>>(in_T, sp, s->W, s->M, s->N, Phi[sp]);
+        phiT_to_canon_kernel<double><<<nb(n), kT, 0, st>>>(in_T, sp, s->W, s->M, s->N, Phi[sp]);
     }
+}
+
+namespace {
+// stream-ordered scratch of one call, freed when it goes out of scope
+struct CallScratch {
+    std::vector<void*> p;
+    cudaStream_t st;
+    explicit CallScratch(cudaStream_t s) : st(s) {}
+    template <typename T>
+    T* get(int64_t count) {
+        void* q = nullptr;
+        if (cudaMallocAsync(&q, sizeof(T) * (size_t)std::max<int64_t>(count, 1), st) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        p.push_back(q);
+        return static_cast<T*>(q);
+    }
+    ~CallScratch() {
+        for (void* q : p) cudaFreeAsync(q, st);
+    }
+};
+}  // namespace
+
+int tc_bp_green(afqmc_walkers* wk, const double* QT, cplx* const* Phi0, cplx* const* Theta, cudaStream_t st) {
+    TcState* s = wk->tc;
+    const int N = s->N, M = s->M, W = s->W, WS = 2 * W;
+    const int64_t rows = (int64_t)WS * 2 * N, nT = rows * M, NN = (int64_t)N * N;
+    CallScratch sc(st);
+    double* P0T = sc.get<double>(nT);
+    bf16* q3[3] = {sc.get<bf16>(nT), sc.get<bf16>(nT), sc.get<bf16>(nT)};
+    bf16* p3[3] = {sc.get<bf16>(nT), sc.get<bf16>(nT), sc.get<bf16>(nT)};
+    float* qs = sc.get<float>(rows);
+    float* ps = sc.get<float>(rows);
+    double* C64 = sc.get<double>((int64_t)WS * 4 * NN);
+    cplx* S = sc.get<cplx>((int64_t)WS * NN);
+    cplx* ld = sc.get<cplx>(WS);
+    unsigned* sing = sc.get<unsigned>(1);
+    bf16* SDh = sc.get<bf16>((int64_t)WS * 4 * NN);
+    bf16* SDl = sc.get<bf16>((int64_t)WS * 4 * NN);
+    float* SDs = sc.get<float>(rows);
+    bf16* Ph = sc.get<bf16>(nT);
+    bf16* Pl = sc.get<bf16>(nT);
+    float* Ps = sc.get<float>((int64_t)WS * M);
+    float* ThT = sc.get<float>(nT);
+    if (!P0T || !q3[0] || !q3[1] || !q3[2] || !p3[0] || !p3[1] || !p3[2] || !qs || !ps || !C64 || !S || !ld ||
+        !sing || !SDh || !SDl || !SDs || !Ph || !Pl || !Ps || !ThT)
+        return fail(AFQMC_ERR_OOM, "bp_rdm1: tensor-core estimate workspace");
+    // S = Psi_bp^+ Phi(0) per walker-spin: [Q rows re | im] . [Phi(0) rows re | im]^T (three
+    // slices, FP64 out), combined as for the QR's Gram matrix
+    tc_canon_to_T(wk, Phi0, P0T, st);
+    split3_rows(QT, rows, M, q3[0], q3[1], q3[2], qs, st);
+    split3_rows(P0T, rows, M, p3[0], p3[1], p3[2], ps, st);
+    {
+        EpiParams e;
+        e.kind = EPI3_F64;
+        e.rows_valid = 2 * N;
+        e.cols_valid = 2 * N;
+        e.ld = 2 * N;
+        e.ob = 4 * NN;
+        e.out_f64 = C64;
+        AFQMC_TRY(tc_gemm3(sp3(q3, qs, M, 2 * N, WS), BatchMap{1, WS}, sp3(p3, ps, M, 2 * N, WS), BatchMap{1, WS},
+                           2 * N, 2 * N, M, WS, e, wk->flags, st));
+    }
+    count_launch();
+    gram_combine_kernel<<<nb((int64_t)WS * NN), kT, 0, st>>>(C64, WS, N, S);
+    // S^-1 in float pairs (S is formed to ~1e-9); a singular S belongs to a dead walker, whose
+    // weight removes it from the sum
+    AFQMC_CUDA_TRY(cudaMemsetAsync(sing, 0, sizeof(unsigned), st));
+    batched_inverse_logdet(S, NN, N, WS, ld, true, sing, st, true);
+    // Theta^T = (Phi(0) S^-1)^T: the doubled S^-1 pair times Phi(0)'s untransposed pair (exact mode)
+    count_launch();
+    sinv_doubled_kernel<<<(unsigned)(((int64_t)WS * N + 7) / 8), kT, 0, st>>>(
+        S, WS, N, reinterpret_cast<__half*>(SDh), reinterpret_cast<__half*>(SDl), SDs);
+    {
+        dim3 g((M + 31) / 32, WS);
+        const size_t sm = (size_t)2 * N * 33 * sizeof(double);
+        raise_dyn_smem(phi_untranspose_split_kernel<2>, sm);
+        count_launch();
+        phi_untranspose_split_kernel<2><<<g, kT, sm, st>>>(P0T, M, 2 * N, reinterpret_cast<__half*>(Ph),
+                                                           reinterpret_cast<__half*>(Pl), nullptr, Ps);
+    }
+    {
+        EpiParams e;
+        e.kind = EPI_F32;
+        e.rows_valid = 2 * N;
+        e.cols_valid = M;
+        e.ld = M;
+        e.ob = 2LL * N * M;
+        e.out_f32 = ThT;
+        AFQMC_TRY(tc_gemm(smat(SDh, SDl, 2 * N, 2 * N, WS, SDs), BatchMap{1, WS}, smat(Ph, Pl, 2 * N, M, WS, Ps),
+                          BatchMap{1, WS}, 2 * N, M, 2 * N, WS, e, 128, true, wk->flags, st));
+    }
+    const int64_t n = (int64_t)W * M * N;
+    for (int sp = 0; sp < 2; ++sp) {
+        count_launch();
+        phiT_to_canon_kernel<float><<<nb(n), kT, 0, st>>>(ThT, sp, W, M, N, Theta[sp]);
+    }
+    return AFQMC_OK;
 }
 
 int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
@@ -914,7 +1014,7 @@ int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
     const int64_t n = (int64_t)s->W * s->M * s->N;
     for (int sp = 0; sp < 2; ++sp) {
         count_launch();
-        phiT_to_canon_kernel<<<nb(n), kT, 0, st>>>(s->PhiT[s->cur], sp, s->W, s->M, s->N, wk->f.Phi[sp]);
+        phiT_to_canon_kernel<double><<<nb(n), kT, 0, st>>>(s->PhiT[s->cur], sp, s->W, s->M, s->N, wk->f.Phi[sp]);
     }
     return AFQMC_OK;
 }
