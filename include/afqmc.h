@@ -306,9 +306,11 @@ int afqmc_comb_indices(const double* w, int W, double xi, int* idx, double* tota
  *   rdm_up, rdm_dn  complex [M][M] (either may be NULL).
  * afqmc_population_control inside a window gives every new walker its source
  * walker's Phi_w(0) and field history; afqmc_set_walkers closes the window.
- * Computed in FP64 whatever the walker set's precision; device memory
- * W (M (Nup + Ndn) + nbp Nchol) complex for the window and ~6 W M max(Nup, Ndn)
- * complex during afqmc_bp_rdm1.
+ * Precision follows the walker set: FP64 walker sets in FP64; BF16X3 walker sets on
+ * the tensor cores (the forward step's three-slice propagation for the back steps,
+ * three-slice GEMMs and a float-pair inverse for the estimate; ~1e-7 relative to the
+ * FP64 result).  Device memory W (M (Nup + Ndn) + nbp Nchol) complex for the window
+ * and ~6 W M max(Nup, Ndn) complex during afqmc_bp_rdm1 (BF16X3: about twice that).
  * Errors: BADARG (null handle, nbp < 0; for bp_rdm1: no window, fewer than nbp
  * steps recorded, or a step run after the window was complete), NONFINITE (a live
  * walker whose back-propagated overlap vanishes), OOM, CUDA. */
