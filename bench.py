@@ -305,7 +305,7 @@ def fp64_compare(wl, h, L, E0, Psi, seed):
     return out
 
 
-def run_batch(args, rank, world):
+def batch_line(args, rank, world):
     """Uneven multi-system batch: 64 systems, M ~ U{32..256}, N = floor(M/4), Nchol = 5M,
     W ~ U{32..256}, tau = 0.01, QR every 10 steps, BF16X3 (padded to tensor-core shapes),
     energy measured every step, one CUDA-graph launch per step, autotuned launch shapes."""
@@ -381,9 +381,46 @@ def run_batch(args, rank, world):
                          "kernel": "whole step (energy-contraction flops of every system / step time)",
                          "peak_source": f"bf16_tflops_sustained of {src} peaks"}}
     b.close()
+    return line
+
+
+def run_batch(args, rank, world):
+    line = batch_line(args, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def config2_compare(seed, steps=5):
+    """The molecule-like workload at its stated size (M=128, N=32+32, Nchol=640, W=512, QR/10):
+    the mixed-precision and the plain FP64 GPU step on the same walkers and Philox fields, one
+    untimed step then `steps` timed ones (energy every step), E_mix compared over all of them."""
+    import torch
+    from paper_2003_01831_gb300 import api, synthetic as syn
+    from paper_2003_01831_gb300.walkers import AFQMC
+    wl = syn.workload("m128")
+    h, L, E0, Psi = build_system(wl)
+    stream = torch.cuda.current_stream().cuda_stream
+    out, traces = {}, {}
+    for name, prec in (("fp64", api.PREC_FP64), ("mixed", api.PREC_BF16X3)):
+        with AFQMC(h, L, E0, Psi[0], Psi[1], wl.W, wl.tau, k_qr=wl.k_qr, precision=prec, stream=stream) as g:
+            tr = torch.zeros(steps + 1, dtype=torch.complex128, device="cuda")
+            api.afqmc_step(g.wk, 1, None, seed, 1, tr[:1], stream)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            api.afqmc_step(g.wk, steps, None, seed, 1, tr[1:], stream)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            traces[name] = tr.cpu().numpy()
+            out[name] = {"value": wl.W / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
+    d = np.abs(traces["fp64"] - traces["mixed"])
+    out.update({"workload": workload_desc(wl), "steps": steps + 1, "fields": f"device Philox, seed {seed}",
+                "max_abs_dE_mix_Ha": float(d.max()), "bar_Ha": 1e-3,
+                "mixed_over_fp64": out["mixed"]["value"] / out["fp64"]["value"]})
+    return out
 
 
 def run_bp(args, rank, world):
@@ -728,6 +765,8 @@ def main():
                     help="batch64: pad each system's N to a multiple of 8 (default) or to 32/64/128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-config2", action="store_true", help="skip the m128 mixed-vs-FP64 key of the default line")
+    ap.add_argument("--no-batch-line", action="store_true", help="skip the batch64 key of the default line")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -905,6 +944,15 @@ def main():
         cmp = fp64_compare(wl, h, L, E0, Psi, seed)
         cmp["mixed_over_fp64_at_bench_walkers"] = value / cmp["fp64"]["value"]
         line["fp64_compare"] = cmp
+    if world == 1 and not args.no_config2:
+        line["config2_compare"] = config2_compare(seed)
+    if world == 1 and not args.no_batch_line:
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup = 5, 2
+        bl = batch_line(bargs, rank, world)
+        line["batch64"] = {k: bl[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "clocks",
+                                              "roofline")}
+        line["batch64"]["config"] = bl["config"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, h, L, E0, Psi)
     if rank == 0:
