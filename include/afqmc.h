@@ -168,8 +168,9 @@ int afqmc_destroy_hamiltonian(afqmc_ham_t ham);
  * tau    imaginary time step (> 0).
  * opts   NULL for defaults.
  * Sets w = 1 and E_T = E_L(trial) (the trial's own mixed energy).
- * Sizes: 1 <= Nup, Ndn <= min(M, 128).  BF16X3 additionally needs Nup == Ndn,
- * M % 64 == 0, Nchol % 8 == 0 and a real trial (UNSUPPORTED otherwise); its fused
+ * Sizes: 1 <= Nup, Ndn <= min(M, 128).  BF16X3 additionally needs a real trial with
+ * Psi_up == Psi_dn (one trial operand serves both spins), M % 64 == 0 and
+ * Nchol % 8 == 0 (UNSUPPORTED otherwise); its fused
  * energy contraction further needs N % 8 == 0 and M <= 1024, so a step that measures
  * the energy of another shape returns UNSUPPORTED (steps with measure_every = 0 run;
  * afqmc_create_batch pads any shape exactly).

@@ -35,6 +35,12 @@ __global__ void batched_transpose_kernel(const T* in, T* out, int nb, int rows, 
     out[b * per + (int64_t)c * rows + r] = in[i];
 }
 
+// flag = 1 when the two arrays differ anywhere (exact comparison)
+__global__ void differ_kernel(const cplx* a, const cplx* b, int64_t n, unsigned* flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && (a[i].re != b[i].re || a[i].im != b[i].im)) atomicOr(flag, 1u);
+}
+
 __global__ void max_abs_imag_kernel(const cplx* p, int64_t n, unsigned* flag) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && p[i].im != 0.0) atomicOr(flag, 1u);
@@ -485,18 +491,29 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
         count_launch();
         max_abs_imag_kernel<<<nblk(n), 256, 0, st>>>(f.Psi[s], n, wk->flags + 1);
     }
+    unsigned* dspin = nullptr;   // BF16X3 forms one trial operand for both spins: Psi_up == Psi_dn
+    if (o.precision == AFQMC_PREC_BF16X3 && Nup == Ndn) {
+        if (cudaMallocAsync(&dspin, sizeof(unsigned), st) != cudaSuccess) return bail(fail(AFQMC_ERR_OOM, "init_walkers: workspace"));
+        cudaMemsetAsync(dspin, 0, sizeof(unsigned), st);
+        const int64_t n = (int64_t)ND * M * Nup;
+        count_launch();
+        differ_kernel<<<nblk(n), 256, 0, st>>>(f.Psi[0], f.Psi[1], n, dspin);
+    }
     if (ND > 1) {   // conj(c_I), the factors of <psi_T| = sum_I conj(c_I) <D_I|
         for (cplx& c : c_host) c.im = -c.im;
         rc = copy_in(f.msd_cc, c_host.data(), sizeof(cplx) * ND, st);
         if (rc) return bail(rc);
     }
     {
-        unsigned fl[2] = {0, 0};
+        unsigned fl[3] = {0, 0, 0};
         AFQMC_CUDA_TRY(cudaMemcpyAsync(fl, wk->flags, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        if (dspin) AFQMC_CUDA_TRY(cudaMemcpyAsync(fl + 2, dspin, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
         AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
+        if (dspin) cudaFree(dspin);
         if (fl[0] & FLAG_NONFINITE) return bail(fail(AFQMC_ERR_NONFINITE, "init_walkers: NaN/Inf in the trial"));
         wk->trial_real = fl[1] == 0;
         wk->Lt_real = wk->trial_real && !ham->cplx_L;
+        wk->spin_same = dspin != nullptr && fl[2] == 0;
     }
     if (o.precision == AFQMC_PREC_BF16X3 && ham->cplx_L)
         return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs real Cholesky vectors"));
@@ -505,9 +522,10 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
     if (o.precision == AFQMC_PREC_BF16X3 && ND > 1)
         return bail(fail(AFQMC_ERR_UNSUPPORTED, "init_walkers: BF16X3 needs a single-determinant trial"));
     if (o.precision == AFQMC_PREC_BF16X3) {
-        if (!wk->trial_real || Nup != Ndn || M % 64 != 0 || nch % 8 != 0)
+        if (!wk->trial_real || Nup != Ndn || !wk->spin_same || M % 64 != 0 || nch % 8 != 0)
             return bail(fail(AFQMC_ERR_UNSUPPORTED,
-                             "init_walkers: BF16X3 needs a real trial, Nup == Ndn, M % 64 == 0, Nchol % 8 == 0"));
+                             "init_walkers: BF16X3 needs a real trial with Psi_up == Psi_dn, M % 64 == 0, "
+                             "Nchol % 8 == 0"));
     }
     // rotated Cholesky tensor (THC: the half-rotated orbital values Psi^+ X), its transpose,
     // rotated one-body matrix, per determinant

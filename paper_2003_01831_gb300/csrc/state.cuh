@@ -84,6 +84,7 @@ struct afqmc_walkers {
     double tau = 0.0;
     afqmc_opts opts{};
     bool trial_real = false;
+    bool spin_same = false;           // Psi_up == Psi_dn exactly (checked for BF16X3 walker sets)
     bool Lt_real = false;             // Psi^+ L_n real: a real trial and real L
     double E_T = 0.0;
     int64_t step = 0;

@@ -102,6 +102,20 @@ def test_unsupported_shapes_rejected():
     assert e.value.code == -8
 
 
+def test_spin_unrestricted_trial_rejected():
+    """The tensor-core path forms one trial operand for both spins, so a real trial with
+    Psi_up != Psi_dn (same N) is refused rather than run with Psi_dn replaced by Psi_up; the FP64
+    path takes it."""
+    h, L, E0, Psi = system(128, 32, 64, 5)
+    _, v = np.linalg.eigh(h)
+    Pdn = np.ascontiguousarray(v[:, 1:33].astype(np.complex128))   # a different real determinant
+    with pytest.raises(api.AfqmcError) as e:
+        AFQMC(h, L, E0, Psi[0], Pdn, 4, 0.01, precision=api.PREC_BF16X3)
+    assert e.value.code == -8 and "Psi_up == Psi_dn" in str(e.value)
+    with AFQMC(h, L, E0, Psi[0], Pdn, 4, 0.01, precision=api.PREC_FP64) as g:
+        assert np.isfinite(g.energy()[3])
+
+
 @pytest.mark.parametrize("M,N,nch,W", [(128, 32, 64, 4), (256, 128, 96, 3)])
 def test_qr_matches_fp64_path(M, N, nch, W):
     """One step with a QR at its end (k_qr = 1): the mixed path's Cholesky QR (tensor-core Gram
