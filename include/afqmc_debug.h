@@ -15,7 +15,7 @@ extern "C" {
 #endif
 
 /* C[b] = A[b] B[b]^T for A [nbatch][rows][K], B [nbatch][cols][K] (float64, host), computed
- * by the tcgen05 split-bf16 GEMM and returned as float64 C [nbatch][rows][cols].
+ * by the tcgen05 split-operand GEMM and returned as float64 C [nbatch][rows][cols].
  * exact = 0: plain split (hi = bf16(x), lo = bf16(x - hi)), all three products in one fp32
  *            accumulator; BN = 128 or 256.
  * exact = 1: row-scaled fp16 split: per row a power of two s = 2^(e-11) with ||x||_2 < 2^e,
