@@ -64,11 +64,11 @@ def l2_note(wl):
 # profiles/).  The figure holds for the kernel source it was taken on: a digest of that source
 # (the energy-kernel section of kernels_tc.cu and the PTX wrappers) gates it.
 # DRAM bytes per launch of the energy kernel at the bench workload: one-pass ncu counters on a
-# W = 16 launch of the same kernel (4,048,949,248 read + 5,960,448 written), scaled by 64 to
+# W = 16 launch of the same kernel (2,465,579,264 read + 5,491,968 written), scaled by 64 to
 # W = 1024 -- the kernel streams L~ once per window of 8 walker-spin groups, so its traffic grows
 # in proportion to W (profiles/energy_pair_kernel_traffic_m512.md).  Reported only while the
 # kernel's source matches the digest it was measured on.
-ENERGY_TRAFFIC = {"bytes": 64 * (4048949248 + 5960448), "src_digest": "a89eae9f2e13e978"}
+ENERGY_TRAFFIC = {"bytes": 64 * (2465579264 + 5491968), "src_digest": "ea121992e632cfdb"}
 
 
 def energy_src_digest() -> str:
@@ -361,7 +361,7 @@ def batch_line(args, rank, world):
     line = {"metric": "walker-steps/sec, 64 uneven systems (M~U{32..256}, N=M/4, Nchol=5M, W~U{32..256})",
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16 row-scaled splits (2-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
+            "dtype": "f16 row-scaled splits (1-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
             "data": "synthetic",
             "config": {"workload": f"64 uneven molecule-like systems, {Wtot} walkers in total, tau=0.01, QR/10, "
                                    "energy every step, padded to tensor-core shapes, one graph launch per step",
@@ -758,7 +758,7 @@ def main():
     ap.add_argument("--workload", default="m512")
     ap.add_argument("--walkers", type=int, default=0)
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
-    ap.add_argument("--energy-terms", type=int, default=0, choices=[0, 1, 3, 4])
+    ap.add_argument("--energy-terms", type=int, default=0, choices=[0, 1, 2, 3, 4])
     ap.add_argument("--energy-pair", type=int, default=-1, choices=[-1, 0, 1],
                     help="energy kernel form: 0 one CTA per tile, 1 CTA pairs, -1 the library default")
     ap.add_argument("--batch-pad-granule", type=int, default=8, choices=[8, 32],
@@ -930,7 +930,7 @@ def main():
     line = {"metric": workload_metric(wl), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16 row-scaled splits (2-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
+            "dtype": "f16 row-scaled splits (1-3 slices, f32 accumulate) + f64" if prec == api.PREC_BF16X3 else "f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(wl), "l2": l2_note(wl),
                        "parallelism": f"walker replicas x{world}"},

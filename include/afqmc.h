@@ -80,9 +80,14 @@ typedef struct afqmc_opts {
     int    energy_terms; /* BF16X3 energy contraction's split products, with the
                             row-scaled operands y = x / scale, hi = rint(y),
                             lo = fp16(y - hi):
-                            0 (default) = hi*hi + r*lo + lo*hi, r = fp16(y) of
-                                Ltilde_n: three products whose r carries the leading
-                                part of lo*lo (the accuracy of four);
+                            2 = hi*hi + r*lo + lo*hi, r = fp16(y) of Ltilde_n: three
+                                products whose r carries the leading part of lo*lo
+                                (the accuracy of four);
+                            0 (default) = as 2, except for the smallest Cholesky
+                                vectors, whose squared norms ||Ltilde_n||_F^2 add up
+                                to at most 2^-15 of the total: their tiles form the
+                                one product r*r', r' = fp16(y) of Theta (relative
+                                error ~2^-11 on a share ~2^-15 of the energy);
                             3 = hi*hi + hi*lo + lo*hi;
                             4 = + lo*lo for every Cholesky vector;
                             1 = adaptive: four products except for the smallest

@@ -28,7 +28,10 @@ int afqmc_debug_split_gemm(const double* A, const double* B, int nbatch, int row
 
 /* The fused energy contraction on its own (row-scaled operands y = x / scale, hi = rint(y),
  * lo = fp16(y - hi), exact leading product; terms = 3: hi*hi + hi*lo + lo*hi, terms = 4:
- * + lo*lo, terms = 5: hi*hi + r*lo + lo*hi with r = fp16(y) of Lt, the library default):
+ * + lo*lo, terms = 5: hi*hi + r*lo + lo*hi with r = fp16(y) of Lt; terms = 6: as 5, but the
+ * tiles of n-groups 4p + 2 and 4p + 3 (groups of 128/Np Cholesky vectors) form the single
+ * product r*r' with r' = fp16(y) of ThetaT (the single-product tail of the library default,
+ * on alternate CTA-pair tiles); terms = 7: r*r' for every tile):
  * for Lt [Nchol][Np][M] (real) and walker-spin
  * Green's functions ThetaT [nws][2][Np][M] (re plane then im plane of Theta^T), returns
  * t [nws][Nchol] = Tr(Lt_n Theta_ws) and X [nws][Nchol] = Tr((Lt_n Theta_ws)^2) as complex
@@ -66,13 +69,22 @@ int afqmc_debug_set_launch_policy(int grid_cap, int bn_max, int energy_bk);
 int afqmc_debug_inverse(const double* S, int N, int count, int variant, int with_inverse, double* Sout,
                         double* logdet, float* ms);
 
-/* The adaptive choice of energy products (afqmc_opts.energy_terms = 0) on host data: for the
+/* The adaptive choice of energy products (afqmc_opts.energy_terms = 1) on host data: for the
  * Frobenius norms norms[n] >= 0 of the nch rotated Cholesky vectors Ltilde_n, flags[g] = 1
  * (the lo*lo product is formed) for every group g of G consecutive vectors except the groups
  * made only of the smallest vectors whose norms add up to at most eta of the total (ties:
  * lower index first), 0 for those.  ceil(nch / G) flags.  Host only, no device work; the
  * step uses eta = 0.01 and G = 128 / N. */
 int afqmc_debug_select_energy_groups(const double* norms, int nch, int G, double eta, unsigned char* flags);
+
+/* The single-product tail of the default energy products (afqmc_opts.energy_terms = 0) on host
+ * data: for the squared Frobenius norms sqnorms[n] >= 0 of the nch rotated Cholesky vectors,
+ * flags[g] = 1 (the group's tiles form the one product r*r') for every group g of G
+ * consecutive vectors made only of the smallest vectors whose squared norms add up to at most
+ * eta of the total (ties: lower index first), 0 for the others; a CTA-pair tile forms the
+ * single product when both of its groups are flagged.  ceil(nch / G) flags.  Host only; the
+ * step uses eta = 2^-15 and G = 128 / N. */
+int afqmc_debug_select_single_groups(const double* sqnorms, int nch, int G, double eta, unsigned char* flags);
 
 /* Tile order of the calling thread's later energy-kernel launches: the (Cholesky vector,
  * walker-spin) tiles run in windows of ws_super walker-spin groups (0 = default), sweeping
@@ -101,10 +113,11 @@ int afqmc_debug_set_batch_energy(void* b, int multi, int bk);
 int afqmc_debug_mixed_terms(afqmc_wk_debug_t wk, double* ST, double* Sinv, double* ThetaT, double* t, double* X,
                             double* E1);
 
-/* Mean number of split products per energy tile of a BF16X3 walker set (3 or 4 under a
- * fixed energy_terms; 3 + the fraction of tiles that form lo*lo under the adaptive default).
- * The issued tensor-core flops of the energy contraction are this many times the algorithmic
- * ones.  Host only. */
+/* Mean number of split products per energy tile of a BF16X3 walker set: under the default
+ * (energy_terms = 0) 3 - 2 f, f the fraction of CTA-pair tiles that form the single product
+ * (0 in the one-CTA form); 3 for energy_terms = 2 or 3, 4 for 4; 3 + the fraction of tiles
+ * that form lo*lo under the adaptive choice (1).  The issued tensor-core flops of the energy
+ * contraction are this many times the algorithmic ones.  Host only. */
 int afqmc_debug_energy_products(afqmc_wk_debug_t wk, double* mean);
 
 /* Failure detection without a fault: one warp waits, by the library's bounded mbarrier wait

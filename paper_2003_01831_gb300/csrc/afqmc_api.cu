@@ -429,8 +429,8 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
     for (int r : o.reserved)
         if (r != 0) return fail(AFQMC_ERR_BADARG, "init_walkers: reserved options must be zero");
     if (o.walker_offset < 0) return fail(AFQMC_ERR_BADARG, "init_walkers: walker_offset must be >= 0");
-    if (o.energy_terms != 0 && o.energy_terms != 1 && o.energy_terms != 3 && o.energy_terms != 4)
-        return fail(AFQMC_ERR_BADARG, "init_walkers: energy_terms must be 0, 1, 3 or 4");
+    if (o.energy_terms < 0 || o.energy_terms > 4)
+        return fail(AFQMC_ERR_BADARG, "init_walkers: energy_terms must be 0, 1, 2, 3 or 4");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0;
     AFQMC_CUDA_TRY(cudaGetDevice(&dev));

@@ -375,9 +375,9 @@ int capture(afqmc_batch* b, bool meas, bool qr, cudaGraphExec_t* out, int* nkern
         }
         if (rc == AFQMC_OK)
             rc = tc_energy_multi(b->esys, b->work, b->nwork, b->energy_bk,
-                                 b->opts.energy_terms == 0 ? kEnergyRounded
-                                                           : (b->opts.energy_terms == 1 ? kEnergyFour
-                                                                                        : b->opts.energy_terms),
+                                 (b->opts.energy_terms == 0 || b->opts.energy_terms == 2)
+                                     ? kEnergyRounded
+                                     : (b->opts.energy_terms == 1 ? kEnergyFour : b->opts.energy_terms),
                                  b->wk[0]->flags, b->cap);
     }
     cudaEventRecord(b->ev[0], b->cap);

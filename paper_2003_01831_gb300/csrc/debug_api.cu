@@ -118,23 +118,31 @@ extern "C" int afqmc_debug_energy(const double* Lt, const double* ThetaT, int Np
     if (!Lt || !ThetaT || !t || !X || Nchol < 1 || nws < 1 || M < 64)
         return fail(AFQMC_ERR_BADARG, "debug_energy: bad arguments");
     const int64_t na = (int64_t)Nchol * Np * M, nb = (int64_t)nws * 2 * Np * M;
-    if (terms != 3 && terms != 4 && terms != 5) return fail(AFQMC_ERR_BADARG, "debug_energy: terms must be 3, 4 or 5");
-    DevBuf a64, ahi, alo, arn, b64, bhi, blo, dt, dx, flags, asc, bsc;
-    AFQMC_TRY(upload_split(Lt, na / M, M, a64, ahi, alo, &asc, terms == 5 ? &arn : nullptr));
-    AFQMC_TRY(upload_split(ThetaT, nb / M, M, b64, bhi, blo, &bsc));
+    if (terms < 3 || terms > 7) return fail(AFQMC_ERR_BADARG, "debug_energy: terms must be 3 to 7");
+    const bool rounded = terms >= 5, single = terms >= 6;
+    DevBuf a64, ahi, alo, arn, b64, bhi, blo, brn, dt, dx, flags, asc, bsc, sg;
+    AFQMC_TRY(upload_split(Lt, na / M, M, a64, ahi, alo, &asc, rounded ? &arn : nullptr));
+    AFQMC_TRY(upload_split(ThetaT, nb / M, M, b64, bhi, blo, &bsc, single ? &brn : nullptr));
     const int64_t no = (int64_t)nws * Nchol;
+    const int G = 128 / Np, ng = (Nchol + G - 1) / G;
     if (cudaMalloc(&dt.p, no * 16) != cudaSuccess || cudaMalloc(&dx.p, no * 16) != cudaSuccess ||
-        cudaMalloc(&flags.p, 4) != cudaSuccess)
+        cudaMalloc(&flags.p, 4) != cudaSuccess || (single && cudaMalloc(&sg.p, (size_t)ng) != cudaSuccess))
         return fail(AFQMC_ERR_OOM, "debug: allocation");
     cudaMemset(flags.p, 0, 4);
+    if (single) {   // 6: the odd pair tiles (n-groups 4 p + 2, 4 p + 3) single; 7: every tile
+        std::vector<uint8_t> hs((size_t)ng);
+        for (int g = 0; g < ng; ++g) hs[(size_t)g] = terms == 7 ? 1 : (uint8_t)((g / 2) % 2);
+        AFQMC_CUDA_TRY(cudaMemcpy(sg.p, hs.data(), (size_t)ng, cudaMemcpyHostToDevice));
+    }
     SplitMat sa, sb;
     sa.hi = static_cast<bf16*>(ahi.p); sa.lo = static_cast<bf16*>(alo.p);
     sa.K = M; sa.rows = (int64_t)Nchol * Np; sa.row_stride = M; sa.scale = static_cast<float*>(asc.p);
     sb.hi = static_cast<bf16*>(bhi.p); sb.lo = static_cast<bf16*>(blo.p);
     sb.K = M; sb.rows = (int64_t)nws * 2 * Np; sb.row_stride = M; sb.scale = static_cast<float*>(bsc.p);
     AFQMC_TRY(tc_energy(sa, sb, Np, Nchol, nws, M, static_cast<cplx*>(dt.p), static_cast<cplx*>(dx.p),
-                        terms == 5 ? kEnergyRounded : terms, nullptr, static_cast<bf16*>(arn.p),
-                        static_cast<unsigned*>(flags.p), 0));
+                        rounded ? kEnergyRounded : terms, nullptr, static_cast<bf16*>(arn.p),
+                        static_cast<unsigned*>(flags.p), 0, single ? static_cast<uint8_t*>(sg.p) : nullptr,
+                        static_cast<bf16*>(brn.p)));
     AFQMC_CUDA_TRY(cudaDeviceSynchronize());
     unsigned fl = 0;
     AFQMC_CUDA_TRY(cudaMemcpy(&fl, flags.p, 4, cudaMemcpyDeviceToHost));
@@ -197,6 +205,17 @@ extern "C" int afqmc_debug_select_energy_groups(const double* norms, int nch, in
         if (!(norms[n] >= 0.0) || !std::isfinite(norms[n]))
             return fail(AFQMC_ERR_BADARG, "debug_select_energy_groups: norms must be finite and >= 0");
     select_lolo_groups(norms, nch, G, eta, flags);
+    return AFQMC_OK;
+}
+
+extern "C" int afqmc_debug_select_single_groups(const double* sqnorms, int nch, int G, double eta,
+                                                unsigned char* flags) {
+    if (!sqnorms || !flags || nch < 1 || G < 1 || !(eta >= 0.0 && eta < 1.0))
+        return fail(AFQMC_ERR_BADARG, "debug_select_single_groups: bad arguments");
+    for (int n = 0; n < nch; ++n)
+        if (!(sqnorms[n] >= 0.0) || !std::isfinite(sqnorms[n]))
+            return fail(AFQMC_ERR_BADARG, "debug_select_single_groups: squared norms must be finite and >= 0");
+    select_single_groups(sqnorms, nch, G, eta, flags);
     return AFQMC_OK;
 }
 

@@ -438,6 +438,19 @@ __device__ __forceinline__ void energy_tile_rows(const EnergyShape& s, int64_t t
 __device__ __forceinline__ void energy_tile(const EnergyShape& s, int64_t t, int& ng, int& wg) {
     energy_tile_rows(s, t, s.n_groups, ng, wg);
 }
+// A pair tile (n-groups 2 ngp and 2 ngp + 1) forms the single product r*r' when every one of its
+// n-groups is flagged single (the CTA-pair kernels; the one-CTA kernel never does).
+__device__ __forceinline__ bool energy_pair_single(const EnergyShape& es, int ngp) {
+    if (!es.single_group) return false;
+    bool one = es.single_group[2 * ngp] != 0;
+    if (2 * ngp + 1 < es.n_groups) one = one && es.single_group[2 * ngp + 1] != 0;
+    return one;
+}
+template <int n>
+__device__ __forceinline__ void zero_regs(uint32_t (&u)[n]) {
+#pragma unroll
+    for (int i = 0; i < n; ++i) u[i] = 0u;
+}
 
 // Energy kernel pipeline: K chunks of BK = 16 (32-byte swizzle, six 24 KB stages) or 32
 // (64-byte swizzle, three 48 KB stages) in 144 KB of shared memory, one TMEM buffer
@@ -525,6 +538,60 @@ __device__ __forceinline__ void energy_products(Mma mma, uint32_t d1, uint32_t d
     }
 }
 
+// One stage of a CTA-pair energy tile (mp: Ltilde hi, lo, r and Theta hi, lo, r' tensor maps).
+// Three or two products: K chunk kb of the Ltilde planes and of Theta's hi and lo.  Single
+// product (rounded planes only): K chunks 2 kb and 2 kb + 1 of r (A slots 0 and 1) and r'
+// (B slots 0 and 1), so a stage still carries two MMAs of K = 16 per chunk of 32 and the ring
+// covers twice the K range.
+template <int BK, int AP>
+__device__ __forceinline__ void energy_stage_load_pair(uint8_t* s, SharedCtl* ctl, int st, const CUtensorMap* const* mp,
+                                                       int kb, int ya, int yb, bool single, uint32_t rank) {
+    using C = EStage<BK, AP, 128>;
+    const uint32_t fb = mapa_shared(&ctl->full[st], 0);
+    if (AP == 3 && single) {
+        if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 4 * (C::kABytes + C::kBBytes));   // both CTAs' bytes
+        const int x0 = 2 * kb * BK;
+        tma_load_2d_pair(s, mp[2], fb, x0, ya);
+        tma_load_2d_pair(s + C::kABytes, mp[2], fb, x0 + BK, ya);
+        tma_load_2d_pair(s + C::kBOff, mp[5], fb, x0, yb);
+        tma_load_2d_pair(s + C::kBOff + C::kBBytes, mp[5], fb, x0 + BK, yb);
+        return;
+    }
+    if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
+    const int x = kb * BK;
+    tma_load_2d_pair(s, mp[0], fb, x, ya);
+    tma_load_2d_pair(s + C::kABytes, mp[1], fb, x, ya);
+    if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, mp[2], fb, x, ya);
+    tma_load_2d_pair(s + C::kBOff, mp[3], fb, x, yb);
+    tma_load_2d_pair(s + C::kBOff + C::kBBytes, mp[4], fb, x, yb);
+}
+
+// The MMAs of one such stage (rank 0 of the pair), accumulating from the tile's first stage.
+template <int BK, int AP>
+__device__ __forceinline__ void energy_stage_mma_pair(uint32_t sa, uint32_t d1, uint32_t d2, int kb, bool single,
+                                                      bool lolo) {
+    using C = EStage<BK, AP, 128>;
+    constexpr uint32_t idesc = idesc_bf16(256, 256, true);   // fp16 planes, M = 256 over the pair, N = 256
+    const uint32_t sb = sa + C::kBOff;
+    if (AP == 3 && single) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                mma_f16_pair(d1, edesc<BK>(sa + c * C::kABytes + kk * 32), edesc<BK>(sb + c * C::kBBytes + kk * 32),
+                             idesc, (kb | c | kk) != 0 ? 1u : 0u);
+        return;
+    }
+    const uint32_t sal = sa + C::kABytes, sar = sa + 2 * C::kABytes, sbl = sb + C::kBBytes;
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        energy_products<AP>([&](uint32_t d, uint64_t a, uint64_t b, uint32_t c) { mma_f16_pair(d, a, b, idesc, c); },
+                            d1, d2, edesc<BK>(sa + off), edesc<BK>(sal + off), edesc<BK>(sar + off),
+                            edesc<BK>(sb + off), edesc<BK>(sbl + off), (kb | kk) != 0 ? 1u : 0u, lolo);
+    }
+}
+
 template <int BK, int AP>
 __device__ void energy_mma(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es) {
     using C = EStage<BK, AP, 256>;
@@ -588,7 +655,7 @@ __device__ __forceinline__ int ebar_and(int pred) {
 // Returns false when a wait gave up (all sixteen warps then leave together).
 template <int Np, typename Release>
 __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, SharedCtl* ctl, float* plane,
-                                                     float* colscale, double* ered, int ng, int wg, int it,
+                                                     float* colscale, double* ered, int ng, int wg, int it, bool d2,
                                                      Release release) {
     constexpr int Q = Np / 32;     // TMEM quadrants per n-block
     constexpr int G = 128 / Np;    // n-blocks (rows) and walker-spins (columns) per tile
@@ -635,7 +702,8 @@ __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, Shar
     {
         uint32_t u1[32], u2[32];
         tmem_ld32_nw(tq + col_im, u1);
-        tmem_ld32_nw(tq + 256 + col_im, u2);
+        if (d2) tmem_ld32_nw(tq + 256 + col_im, u2);
+        else zero_regs(u2);   // a single-product tile leaves accumulator 2 unwritten
         tmem_ld_wait();
 #pragma unroll
         for (int g = 0; g < 8; ++g) {
@@ -649,7 +717,8 @@ __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, Shar
     {
         uint32_t u1[32], u2[32];
         tmem_ld32_nw(tq + col_re, u1);
-        tmem_ld32_nw(tq + 256 + col_re, u2);
+        if (d2) tmem_ld32_nw(tq + 256 + col_re, u2);
+        else zero_regs(u2);
         tmem_ld_wait();
         tc_fence_before();
         __syncwarp();
@@ -733,7 +802,8 @@ __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, Shar
 // in a fixed order.
 template <typename Release>
 __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, SharedCtl* ctl, float* plane,
-                                                         float* colscale, int ng, int wg, int it, Release release) {
+                                                         float* colscale, int ng, int wg, int it, bool d2,
+                                                         Release release) {
     const int Np = es.Np, G = es.G, GN = G * Np;
     // x / Np and x / G by multiply and shift (exact for the x < 256 used here)
     const uint32_t np_inv = es.np_inv, g_inv = es.g_inv;
@@ -770,7 +840,8 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             tmem_ld8_nw(tq + icol(k), u[k][0]);
-            tmem_ld8_nw(tq + 256 + icol(k), u[k][1]);
+            if (d2) tmem_ld8_nw(tq + 256 + icol(k), u[k][1]);
+            else zero_regs(u[k][1]);
         }
         tmem_ld_wait();
 #pragma unroll
@@ -791,7 +862,8 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
 #pragma unroll
         for (int k = k2; k < k2 + 2; ++k) {
             tmem_ld8_nw(tq + tcol(k), u[k - k2][0]);
-            tmem_ld8_nw(tq + 256 + tcol(k), u[k - k2][1]);
+            if (d2) tmem_ld8_nw(tq + 256 + tcol(k), u[k - k2][1]);
+            else zero_regs(u[k - k2][1]);
         }
         tmem_ld_wait();
 #pragma unroll
@@ -900,18 +972,19 @@ __device__ __forceinline__ bool energy_epilogue_tile_gen(const EnergyShape& es, 
     return true;
 }
 
-// Epilogue of the single-system energy kernels: tile_of(t, ng, wg) names the tile of persistent
-// iteration t.
+// Epilogue of the single-system energy kernels: tile_of(t, ng, wg, d2) names the tile of persistent
+// iteration t and whether its second accumulator was written (false for a single-product tile).
 template <int Np, typename TileOf, typename Release>
 __device__ void energy_epilogue(const EnergyShape& es, SharedCtl* ctl, float* plane, float* colscale, double* ered,
                                 int64_t t_first, int64_t t_end, int64_t t_step, TileOf tile_of, Release release) {
     int it = 0;
     for (int64_t t = t_first; t < t_end; t += t_step, ++it) {
         int ng, wg;
-        tile_of(t, ng, wg);
+        bool d2;
+        tile_of(t, ng, wg, d2);
         bool ok;
-        if constexpr (Np == 0) ok = energy_epilogue_tile_gen(es, ctl, plane, colscale, ng, wg, it, release);
-        else ok = energy_epilogue_tile<Np>(es, ctl, plane, colscale, ered, ng, wg, it, release);
+        if constexpr (Np == 0) ok = energy_epilogue_tile_gen(es, ctl, plane, colscale, ng, wg, it, d2, release);
+        else ok = energy_epilogue_tile<Np>(es, ctl, plane, colscale, ered, ng, wg, it, d2, release);
         if (!ok) break;
     }
 }
@@ -963,7 +1036,10 @@ __global__ void __launch_bounds__(kEThreads, 1)
     } else {
         energy_epilogue<Np>(
             es, ctl, plane, colscale, ered, blockIdx.x, es.tiles, gridDim.x,
-            [&](int64_t t, int& ng, int& wg) { energy_tile(es, t, ng, wg); },
+            [&](int64_t t, int& ng, int& wg, bool& d2) {
+                energy_tile(es, t, ng, wg);
+                d2 = true;
+            },
             [&]() { mbar_arrive(&ctl->tempty[0]); });
     }
     tc_fence_before();
@@ -989,28 +1065,23 @@ __global__ void __launch_bounds__(kEThreads, 1)
 template <int BK, int AP>
 __device__ void energy_producer2(uint8_t* sbase, SharedCtl* ctl, const CUtensorMap* tAh, const CUtensorMap* tAl,
                                  const CUtensorMap* tAr, const CUtensorMap* tBh, const CUtensorMap* tBl,
-                                 const EnergyShape& es, uint32_t rank) {
+                                 const CUtensorMap* tBr, const EnergyShape& es, uint32_t rank) {
     using C = EStage<BK, AP, 128>;
+    const CUtensorMap* const mp[6] = {tAh, tAl, tAr, tBh, tBl, tBr};
     int64_t g = 0;
     bool ok = true;
     for (int64_t t = cluster_id_x(); t < es.tiles2 && ok; t += ncluster_x()) {
         int ngp, wg;
         energy_tile_rows(es, t, es.n_pairs, ngp, wg);
         const int ng = 2 * ngp + (int)rank;
-        for (int kb = 0; kb < es.nk; ++kb, ++g) {
+        const bool single = energy_pair_single(es, ngp);
+        const int nst = single ? es.nk / 2 : es.nk;   // es.nk is even (M % 64 == 0)
+        const int ya = ng * es.G * es.Np, yb = wg * 2 * es.G * es.Np + (int)rank * 128;
+        for (int kb = 0; kb < nst; ++kb, ++g) {
             const int st = (int)(g % C::kStages);
             const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
             if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
-            uint8_t* s = sbase + (size_t)st * C::kStageBytes;
-            if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
-            const uint32_t fb = mapa_shared(&ctl->full[st], 0);
-            const int x = kb * BK;
-            const int ya = ng * es.G * es.Np, yb = wg * 2 * es.G * es.Np + (int)rank * 128;
-            tma_load_2d_pair(s, tAh, fb, x, ya);
-            tma_load_2d_pair(s + C::kABytes, tAl, fb, x, ya);
-            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, tAr, fb, x, ya);
-            tma_load_2d_pair(s + C::kBOff, tBh, fb, x, yb);
-            tma_load_2d_pair(s + C::kBOff + C::kBBytes, tBl, fb, x, yb);
+            energy_stage_load_pair<BK, AP>(sbase + (size_t)st * C::kStageBytes, ctl, st, mp, kb, ya, yb, single, rank);
         }
     }
     if (!ok) {
@@ -1030,7 +1101,6 @@ __device__ void energy_producer2(uint8_t* sbase, SharedCtl* ctl, const CUtensorM
 template <int BK, int AP>
 __device__ void energy_mma2(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& es) {
     using C = EStage<BK, AP, 128>;
-    constexpr uint32_t idesc = idesc_bf16(256, 256, true);   // fp16 planes, M = 256 over the pair, N = 256
     const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
     int64_t g = 0;
     int it = 0;
@@ -1043,24 +1113,16 @@ __device__ void energy_mma2(uint8_t* sbase, SharedCtl* ctl, const EnergyShape& e
             lolo = es.lolo_group[2 * ngp] != 0;
             if (2 * ngp + 1 < es.n_groups) lolo = lolo || es.lolo_group[2 * ngp + 1] != 0;
         }
+        const bool single = energy_pair_single(es, ngp);
+        const int nst = single ? es.nk / 2 : es.nk;
         if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
         tc_fence_after();
-        for (int kb = 0; kb < es.nk; ++kb, ++g) {
+        for (int kb = 0; kb < nst; ++kb, ++g) {
             const int st = (int)(g % C::kStages);
             const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
             if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sa = smem_u32(sbase + (size_t)st * C::kStageBytes);
-            const uint32_t sal = sa + C::kABytes, sar = sa + 2 * C::kABytes;
-            const uint32_t sb = sa + C::kBOff, sbl = sb + C::kBBytes;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;
-                energy_products<AP>(
-                    [&](uint32_t d, uint64_t a, uint64_t b, uint32_t c) { mma_f16_pair(d, a, b, idesc, c); }, d1, d2,
-                    edesc<BK>(sa + off), edesc<BK>(sal + off), edesc<BK>(sar + off), edesc<BK>(sb + off),
-                    edesc<BK>(sbl + off), (kb | kk) != 0 ? 1u : 0u, lolo);
-            }
+            energy_stage_mma_pair<BK, AP>(smem_u32(sbase + (size_t)st * C::kStageBytes), d1, d2, kb, single, lolo);
             mma_commit_pair(&ctl->empty[st], 3);   // the stage is free in both CTAs
         }
         if (!ok) break;
@@ -1074,7 +1136,8 @@ template <int Np, int BK, int AP>
 __global__ void __launch_bounds__(kEThreads, 1)
     tc_energy_pair_kernel(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
                           const __grid_constant__ CUtensorMap tAr, const __grid_constant__ CUtensorMap tBh,
-                          const __grid_constant__ CUtensorMap tBl, EnergyShape es, unsigned* flags) {
+                          const __grid_constant__ CUtensorMap tBl, const __grid_constant__ CUtensorMap tBr,
+                          EnergyShape es, unsigned* flags) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     using C = EStage<BK, AP, 128>;
@@ -1090,6 +1153,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
         if (AP == 3) tma_prefetch_desc(&tAr);
         tma_prefetch_desc(&tBh);
         tma_prefetch_desc(&tBl);
+        if (AP == 3 && es.single_group) tma_prefetch_desc(&tBr);
     }
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::kStages; ++i) {
@@ -1114,17 +1178,18 @@ __global__ void __launch_bounds__(kEThreads, 1)
     cluster_sync();   // tensor memory allocated in both CTAs before the first MMA
 
     if (warp == 0) {
-        if (lane == 0) energy_producer2<BK, AP>(sbase, ctl, &tAh, &tAl, &tAr, &tBh, &tBl, es, rank);
+        if (lane == 0) energy_producer2<BK, AP>(sbase, ctl, &tAh, &tAl, &tAr, &tBh, &tBl, &tBr, es, rank);
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) energy_mma2<BK, AP>(sbase, ctl, es);
     } else {
         const uint32_t tempty0 = mapa_shared(&ctl->tempty[0], 0);
         energy_epilogue<Np>(
             es, ctl, plane, colscale, ered, cluster_id_x(), es.tiles2, ncluster_x(),
-            [&](int64_t t, int& ng, int& wg) {
+            [&](int64_t t, int& ng, int& wg, bool& d2) {
                 int ngp;
                 energy_tile_rows(es, t, es.n_pairs, ngp, wg);
                 ng = 2 * ngp + (int)rank;
+                d2 = !energy_pair_single(es, ngp);
             },
             [&]() { mbar_arrive_cluster(tempty0); });
     }
@@ -1153,22 +1218,16 @@ __device__ void energy_producer_multi(uint8_t* sbase, SharedCtl* ctl, const Ener
     for (int64_t t = cluster_id_x(); t < nwork && ok; t += ncluster_x()) {
         const EnergyWork w = work[t];
         const EnergySys* S = sys + w.sys;
-        const int nk = S->es.nk;
+        const bool single = energy_pair_single(S->es, w.ngp);
+        const int nst = single ? S->es.nk / 2 : S->es.nk;
         const int ng = 2 * w.ngp + (int)rank;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        const CUtensorMap* const mp[6] = {&S->map[0], &S->map[1], &S->map[2], &S->map[3], &S->map[4], &S->map[5]};
+        const int ya = ng * S->es.G * S->es.Np, yb = w.wg * 2 * S->es.G * S->es.Np + (int)rank * 128;
+        for (int kb = 0; kb < nst; ++kb, ++g) {
             const int st = (int)(g % C::kStages);
             const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
             if (!mbar_wait(&ctl->empty[st], ph ^ 1u, &ctl->abort)) { ok = false; break; }
-            uint8_t* s = sbase + (size_t)st * C::kStageBytes;
-            if (rank == 0) mbar_arrive_expect_tx(&ctl->full[st], 2 * C::kStageBytes);   // both CTAs' bytes
-            const uint32_t fb = mapa_shared(&ctl->full[st], 0);
-            const int x = kb * BK;
-            const int ya = ng * S->es.G * S->es.Np, yb = w.wg * 2 * S->es.G * S->es.Np + (int)rank * 128;
-            tma_load_2d_pair(s, &S->map[0], fb, x, ya);
-            tma_load_2d_pair(s + C::kABytes, &S->map[1], fb, x, ya);
-            if (AP == 3) tma_load_2d_pair(s + 2 * C::kABytes, &S->map[2], fb, x, ya);
-            tma_load_2d_pair(s + C::kBOff, &S->map[3], fb, x, yb);
-            tma_load_2d_pair(s + C::kBOff + C::kBBytes, &S->map[4], fb, x, yb);
+            energy_stage_load_pair<BK, AP>(sbase + (size_t)st * C::kStageBytes, ctl, st, mp, kb, ya, yb, single, rank);
         }
     }
     if (!ok) {
@@ -1188,7 +1247,6 @@ template <int BK, int AP>
 __device__ void energy_mma_multi(uint8_t* sbase, SharedCtl* ctl, const EnergySys* sys, const EnergyWork* work,
                                  int64_t nwork) {
     using C = EStage<BK, AP, 128>;
-    constexpr uint32_t idesc = idesc_bf16(256, 256, true);
     const uint32_t d1 = ctl->tmem_base, d2 = d1 + 256;
     int64_t g = 0;
     int it = 0;
@@ -1201,25 +1259,16 @@ __device__ void energy_mma_multi(uint8_t* sbase, SharedCtl* ctl, const EnergySys
             lolo = es.lolo_group[2 * w.ngp] != 0;
             if (2 * w.ngp + 1 < es.n_groups) lolo = lolo || es.lolo_group[2 * w.ngp + 1] != 0;
         }
-        const int nk = es.nk;
+        const bool single = energy_pair_single(es, w.ngp);
+        const int nst = single ? es.nk / 2 : es.nk;
         if (!mbar_wait(&ctl->tempty[0], ((uint32_t)it & 1u) ^ 1u, &ctl->abort)) break;
         tc_fence_after();
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int kb = 0; kb < nst; ++kb, ++g) {
             const int st = (int)(g % C::kStages);
             const uint32_t ph = (uint32_t)((g / C::kStages) & 1);
             if (!mbar_wait(&ctl->full[st], ph, &ctl->abort)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t sa = smem_u32(sbase + (size_t)st * C::kStageBytes);
-            const uint32_t sal = sa + C::kABytes, sar = sa + 2 * C::kABytes;
-            const uint32_t sb = sa + C::kBOff, sbl = sb + C::kBBytes;
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint32_t off = kk * 32;
-                energy_products<AP>(
-                    [&](uint32_t d, uint64_t a, uint64_t b, uint32_t c) { mma_f16_pair(d, a, b, idesc, c); }, d1, d2,
-                    edesc<BK>(sa + off), edesc<BK>(sal + off), edesc<BK>(sar + off), edesc<BK>(sb + off),
-                    edesc<BK>(sbl + off), (kb | kk) != 0 ? 1u : 0u, lolo);
-            }
+            energy_stage_mma_pair<BK, AP>(smem_u32(sbase + (size_t)st * C::kStageBytes), d1, d2, kb, single, lolo);
             mma_commit_pair(&ctl->empty[st], 3);
         }
         if (!ok) break;
@@ -1276,12 +1325,15 @@ __global__ void __launch_bounds__(kEThreads, 1)
             const EnergyWork w = work[t];
             const EnergyShape& es = sys[w.sys].es;
             const int ng = 2 * w.ngp + (int)rank;
+            const bool d2 = !energy_pair_single(es, w.ngp);
             bool ok;
             switch (es.Np) {
-                case 32: ok = energy_epilogue_tile<32>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
-                case 64: ok = energy_epilogue_tile<64>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
-                case 128: ok = energy_epilogue_tile<128>(es, ctl, plane, colscale, ered, ng, w.wg, it, release); break;
-                default: ok = energy_epilogue_tile_gen(es, ctl, plane, colscale, ng, w.wg, it, release); break;
+                case 32: ok = energy_epilogue_tile<32>(es, ctl, plane, colscale, ered, ng, w.wg, it, d2, release); break;
+                case 64: ok = energy_epilogue_tile<64>(es, ctl, plane, colscale, ered, ng, w.wg, it, d2, release); break;
+                case 128:
+                    ok = energy_epilogue_tile<128>(es, ctl, plane, colscale, ered, ng, w.wg, it, d2, release);
+                    break;
+                default: ok = energy_epilogue_tile_gen(es, ctl, plane, colscale, ng, w.wg, it, d2, release); break;
             }
             if (!ok) break;
         }
@@ -1372,7 +1424,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const Src* src, int64_t
 // ||x||_2 < 2^e still holds (rows at most 2^-10 below a power of two get the next scale up);
 // y = x / scale is exact (a power of two), rint(y) and y - rint(y) are exact in fp32.
 __global__ void __launch_bounds__(256) split_rows_f32_kernel(const float* src, int64_t src_stride, int64_t rows,
-                                                             int64_t K, __half* hi, __half* lo, float* scale) {
+                                                             int64_t K, __half* hi, __half* lo, float* scale,
+                                                             __half* rnd) {
     const int64_t r = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
@@ -1397,21 +1450,24 @@ __global__ void __launch_bounds__(256) split_rows_f32_kernel(const float* src, i
         for (int64_t k = 4 * lane; k < K; k += 128) {
             const float4 a = *reinterpret_cast<const float4*>(x + k);
             const float v[4] = {a.x, a.y, a.z, a.w};
-            __half h[4], l[4];
+            __half h[4], l[4], rr[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const float y = v[q] * inv, s1 = rintf(y);
                 h[q] = __float2half_rn(s1);
                 l[q] = __float2half_rn(y - s1);
+                rr[q] = __float2half_rn(y);
             }
             store4h(hi + r * K + k, h);
             store4h(lo + r * K + k, l);
+            if (rnd) store4h(rnd + r * K + k, rr);
         }
     } else {
         for (int64_t k = lane; k < K; k += 32) {
             const float y = x[k] * inv, s1 = rintf(y);
             hi[r * K + k] = __float2half_rn(s1);
             lo[r * K + k] = __float2half_rn(y - s1);
+            if (rnd) rnd[r * K + k] = __float2half_rn(y);
         }
     }
 }
@@ -1846,7 +1902,7 @@ int launch_energy_pair(const CUtensorMap* m, const EnergyShape& es, unsigned* fl
     if (launch_policy().grid_cap > 0) pairs = std::max(1, std::min(pairs, launch_policy().grid_cap / 2));
     cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(es.tiles2, pairs)));
     count_launch();
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], m[4], es, flags);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], m[4], m[5], es, flags);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return fail(AFQMC_ERR_CUDA, std::string("tc_energy (CTA pairs) launch: ") + cudaGetErrorString(e));
     return AFQMC_OK;
@@ -1901,11 +1957,13 @@ namespace {
 // 256 for one CTA per tile, 128 for CTA pairs).
 int energy_setup(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
                  cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, int BK, int brows,
-                 CUtensorMap* m, EnergyShape& es) {
+                 CUtensorMap* m, EnergyShape& es, const uint8_t* single_group, const bf16* ThetaT_round) {
     if (terms != kEnergyThree && terms != kEnergyFour && terms != kEnergyRounded)
         return fail(AFQMC_ERR_BADARG, "tc_energy: terms must be 3, 4 or the rounded three");
     if (terms == kEnergyRounded && !Lt_round)
         return fail(AFQMC_ERR_BADARG, "tc_energy: rounded products need the rounded Ltilde plane");
+    if (single_group && (terms != kEnergyRounded || !ThetaT_round))
+        return fail(AFQMC_ERR_BADARG, "tc_energy: single-product tiles need the rounded products and Theta plane");
     if (Np < 8 || Np > 128 || Np % 8) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: Np must be a multiple of 8 up to 128");
     if (M % kBK || M > 1024) return fail(AFQMC_ERR_UNSUPPORTED, "tc_energy: M must be a multiple of 64, <= 1024");
     if (!Lt.scale || !ThetaT.scale) return fail(AFQMC_ERR_BADARG, "tc_energy: row-scaled operands required");
@@ -1917,6 +1975,8 @@ int energy_setup(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, 
                        true, swz));
     AFQMC_TRY(make_map(&m[3], ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, brows, false, true, swz));
     AFQMC_TRY(make_map(&m[4], ThetaT.lo, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride, 0, brows, false, true, swz));
+    AFQMC_TRY(make_map(&m[5], single_group ? ThetaT_round : ThetaT.hi, M, (int64_t)nws * 2 * Np, 1, ThetaT.row_stride,
+                       0, brows, false, true, swz));
     es = EnergyShape{};
     es.Np = Np;
     es.Q = Np / 32;
@@ -1935,6 +1995,7 @@ int energy_setup(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, 
     es.nk = M / BK;
     es.lolo = terms == kEnergyFour ? 1 : 0;
     es.lolo_group = rounded ? nullptr : lolo_group;
+    es.single_group = single_group;
     es.a_scale = Lt.scale;
     es.b_scale = ThetaT.scale;
     es.t_out = t_out;
@@ -1978,14 +2039,15 @@ int launch_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nw
 
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
               cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, unsigned* flags,
-              cudaStream_t st) {
+              cudaStream_t st, const uint8_t* single_group, const bf16* ThetaT_round) {
     const int BK = launch_policy().energy_bk != 0 ? launch_policy().energy_bk : kEBKDefault;
     const bool pair = launch_policy().energy_pair != 0;
     const bool rounded = terms == kEnergyRounded;
-    CUtensorMap m[5];
+    CUtensorMap m[6];
     EnergyShape es;
+    // the one-CTA form has no single-product tiles: it forms the rounded three products throughout
     AFQMC_TRY(energy_setup(Lt, ThetaT, Np, Nchol, nws, M, t_out, X_out, terms, lolo_group, Lt_round, BK,
-                           pair ? 128 : 256, m, es));
+                           pair ? 128 : 256, m, es, pair ? single_group : nullptr, ThetaT_round));
 #define AFQMC_ENERGY_LAUNCH(NP, BKV, APV) \
     (pair ? launch_energy_pair<NP, BKV, APV>(m, es, flags, st) : launch_energy<NP, BKV, APV>(m, es, flags, st))
 #define AFQMC_ENERGY_NP(BKV, APV)                                        \
@@ -2007,10 +2069,10 @@ int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int
 
 int tc_energy_describe(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
                        cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, int BK,
-                       EnergySys* out) {
+                       EnergySys* out, const uint8_t* single_group, const bf16* ThetaT_round) {
     if (BK != 16 && BK != 32) return fail(AFQMC_ERR_BADARG, "tc_energy_describe: BK must be 16 or 32");
     return energy_setup(Lt, ThetaT, Np, Nchol, nws, M, t_out, X_out, terms, lolo_group, Lt_round, BK, 128, out->map,
-                        out->es);
+                        out->es, single_group, ThetaT_round);
 }
 
 void energy_work_list(const EnergySys* sys, int nsys, std::vector<EnergyWork>& out) {
@@ -2035,6 +2097,13 @@ int tc_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nwork,
                                  : launch_energy_multi<32, 2>(sys, work, nwork, flags, st);
     return rounded ? launch_energy_multi<16, 3>(sys, work, nwork, flags, st)
                    : launch_energy_multi<16, 2>(sys, work, nwork, flags, st);
+}
+
+void select_single_groups(const double* nrm2, int nch, int G, double eta, uint8_t* flags) {
+    // the complement of the four-product choice on the squared norms: a group is single when
+    // every one of its vectors lies in the tail
+    select_lolo_groups(nrm2, nch, G, eta, flags);
+    for (int g = 0; g < (nch + G - 1) / G; ++g) flags[g] = flags[g] ? 0 : 1;
 }
 
 void select_lolo_groups(const double* nrm, int nch, int G, double eta, uint8_t* flags) {
@@ -2268,11 +2337,12 @@ void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, 
 }
 
 void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
-                cudaStream_t st) {
+                cudaStream_t st, bf16* rounded) {
     if (rows <= 0) return;
     count_launch();
     split_rows_f32_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
-        src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale);
+        src, src_stride, rows, K, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), scale,
+        reinterpret_cast<__half*>(rounded));
 }
 
 }  // namespace afqmc

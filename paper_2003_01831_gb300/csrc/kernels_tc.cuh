@@ -135,6 +135,9 @@ struct EnergyShape {
     int nk;
     int lolo;               // 1: also form lo*lo (four products), 0: three
     const uint8_t* lolo_group;   // if set: per n-group choice (1: four products, 0: three)
+    const uint8_t* single_group; // if set (rounded products, CTA-pair kernels): per n-group, 1 = the
+                                 // group's tiles form the one product r*r' (r' = fp16 of the scaled
+                                 // Theta); a pair tile does so when both of its n-groups are flagged
     const float* a_scale;   // [Nchol*Np]
     const float* b_scale;   // [nws*2*Np]
     cplx* t_out;
@@ -142,10 +145,10 @@ struct EnergyShape {
 };
 
 // One system of a multi-system energy contraction (device array, 64-byte aligned): tensor maps
-// of Ltilde hi, lo, rounded (hi again without rounded products) and Theta^T hi, lo (boxes of
-// 128 Theta rows: the CTA-pair form), and its shape.
+// of Ltilde hi, lo, rounded (hi again without rounded products) and Theta^T hi, lo, rounded (hi
+// again without single-product tiles) (boxes of 128 Theta rows: the CTA-pair form), and its shape.
 struct EnergySys {
-    CUtensorMap map[5];
+    CUtensorMap map[6];
     EnergyShape es;
 };
 // One pair tile of a multi-system energy contraction: system, n-group pair, walker-spin group.
@@ -166,16 +169,19 @@ constexpr int kEnergyRounded = 5;   // hi*hi (exact) + r*lo + lo*hi, r = fp16(y)
 // (rows (ws, re/im, b)), both row-scaled; exact accumulation of the leading product.
 // terms: kEnergyThree, kEnergyFour or kEnergyRounded (which needs Lt_round, the rounded plane
 // r of Lt, same layout).  lolo_group (device, one byte per group of 128/Np Cholesky vectors, or
-// null) overrides three/four products per group: 1 four products, 0 three.
+// null) overrides three/four products per group: 1 four products, 0 three.  single_group
+// (device, same indexing, or null; rounded products only, with ThetaT_round the rounded plane
+// r' = fp16(y) of ThetaT): the pair tiles whose n-groups are all flagged form the one product
+// r*r' instead of three (the one-CTA form ignores it).
 int tc_energy(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
               cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, unsigned* flags,
-              cudaStream_t st);
+              cudaStream_t st, const uint8_t* single_group = nullptr, const bf16* ThetaT_round = nullptr);
 
 // Fills `out` for one system of a multi-system energy contraction (arguments as tc_energy; BK
 // the K chunk every system of the launch uses).
 int tc_energy_describe(const SplitMat& Lt, const SplitMat& ThetaT, int Np, int Nchol, int nws, int M, cplx* t_out,
                        cplx* X_out, int terms, const uint8_t* lolo_group, const bf16* Lt_round, int BK,
-                       EnergySys* out);
+                       EnergySys* out, const uint8_t* single_group = nullptr, const bf16* ThetaT_round = nullptr);
 // The work list of a multi-system energy contraction: every pair tile of every system, each
 // system's tiles in its own L2 windows (walker-spin groups x every n-group pair).
 void energy_work_list(const EnergySys* sys, int nsys, std::vector<EnergyWork>& out);
@@ -189,6 +195,10 @@ int tc_energy_multi(const EnergySys* sys, const EnergyWork* work, int64_t nwork,
 // except those made only of the smallest vectors, by Frobenius norm nrm[n] of Ltilde_n, whose
 // norms add up to at most eta of the total.  G vectors per group, ceil(nch / G) flags.
 void select_lolo_groups(const double* nrm, int nch, int G, double eta, uint8_t* flags);
+// Cholesky-vector groups whose energy tiles form the single product r*r' (flags[g] = 1): the
+// groups made only of the smallest vectors, by squared Frobenius norm nrm2[n] of Ltilde_n, whose
+// squared norms add up to at most eta of the total.  ceil(nch / G) flags.
+void select_single_groups(const double* nrm2, int nch, int G, double eta, uint8_t* flags);
 
 // Three-slice row split (see kernels_tc.cu): h, m, l fp16 planes [rows][K] and row scales.
 void split3_rows(const double* src, int64_t rows, int64_t K, bf16* h, bf16* m, bf16* l, float* scale,
@@ -203,7 +213,7 @@ int tc_overlap3(const bf16* const* a, const float* a_scale, int nws, int rows, c
 void split_rows(const double* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
                 cudaStream_t st, bf16* rounded = nullptr);   // rounded (optional): r = fp16(x / scale)
 void split_rows(const float* src, int64_t src_stride, int64_t rows, int64_t K, bf16* hi, bf16* lo, float* scale,
-                cudaStream_t st);
+                cudaStream_t st, bf16* rounded = nullptr);   // rounded (optional): r = fp16(x / scale)
 
 int tc_num_sms();
 

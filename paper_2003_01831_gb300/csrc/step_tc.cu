@@ -73,6 +73,7 @@ struct TcState {
     float* SD_s = nullptr;
     float* ThT_f = nullptr;
     bf16 *ThT_h = nullptr, *ThT_l = nullptr;
+    bf16* ThT_r = nullptr;   // rounded plane r' = fp16(Theta row / scale) of the single-product tiles
     float* ThT_s = nullptr;
     cplx *tE = nullptr, *XE = nullptr;
     float* tFB = nullptr;
@@ -89,6 +90,9 @@ struct TcState {
     float* PD3_s = nullptr;
     uint8_t* lolo = nullptr;   // [ceil(Nchol / (128 / N))] energy tiles that form lo*lo
     double lolo_frac = 1.0;    // fraction of those groups
+    uint8_t* single = nullptr; // [ceil(Nchol / (128 / N))] energy tiles that form the one product r*r'
+    double single_frac = 0.0;  // fraction of the CTA-pair tiles that do so
+    int n_single = 0;          // number of such groups
     float *Pacc_hi = nullptr, *Pacc_lo = nullptr;   // Taylor sum, float-float
     bf16* Pacc3[3] = {nullptr, nullptr, nullptr};
     float* Pacc3_s = nullptr;
@@ -112,6 +116,13 @@ constexpr int kT = 256;
 // term is at most this fraction of the three-product error (which is 1.35 mHa in E_mix over 10
 // m512 steps, against 0.33 mHa with four products everywhere).
 constexpr double kLoloTail = 0.01;
+// Single-product energy tiles (energy_terms = 0, the default): the tiles of the smallest Cholesky
+// vectors, whose squared norms ||Ltilde_n||_F^2 add up to at most this fraction of the total, form
+// the one product r*r' of the two operands rounded to fp16 after row scaling (relative error
+// ~2^-11 per product) instead of the rounded three.  Those vectors carry about this fraction of
+// the two-body energy and of the force bias, so the added error is about 2^-11 of it, ~1.5e-8 of
+// the two-body energy.
+constexpr double kSingleTail = 0x1p-15;
 inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 
 template <typename T>
@@ -814,6 +825,7 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
     AFQMC_TRY(talloc(s, &s->ThT_f, wall));
     AFQMC_TRY(talloc(s, &s->ThT_h, wall));
     AFQMC_TRY(talloc(s, &s->ThT_l, wall));
+    AFQMC_TRY(talloc(s, &s->ThT_r, wall));
     AFQMC_TRY(talloc(s, &s->ThT_s, (int64_t)W * 4 * N));
     AFQMC_TRY(talloc(s, &s->tE, (int64_t)W * 2 * nch));
     AFQMC_TRY(talloc(s, &s->XE, (int64_t)W * 2 * nch));
@@ -848,6 +860,17 @@ int tc_alloc(afqmc_walkers* wk, cudaStream_t st) {
         for (int g = 0; g < ng; ++g) four += hf[(size_t)g];
         s->lolo_frac = (double)four / ng;
         AFQMC_CUDA_TRY(cudaMemcpyAsync(s->lolo, hf.data(), (size_t)ng, cudaMemcpyHostToDevice, st));
+        // single-product groups, from the squared norms
+        AFQMC_TRY(talloc(s, &s->single, ng));
+        std::vector<double> hn2((size_t)nch);
+        for (int n = 0; n < nch; ++n) hn2[(size_t)n] = hn[(size_t)n] * hn[(size_t)n];
+        std::vector<uint8_t> hs((size_t)ng);
+        select_single_groups(hn2.data(), nch, G, kSingleTail, hs.data());
+        int npairs = (ng + 1) / 2, nsp = 0;
+        for (int g = 0; g < ng; ++g) s->n_single += hs[(size_t)g];
+        for (int p = 0; p < npairs; ++p) nsp += (hs[(size_t)(2 * p)] && (2 * p + 1 >= ng || hs[(size_t)(2 * p + 1)])) ? 1 : 0;
+        s->single_frac = (double)nsp / npairs;
+        AFQMC_CUDA_TRY(cudaMemcpyAsync(s->single, hs.data(), (size_t)ng, cudaMemcpyHostToDevice, st));
         AFQMC_CUDA_TRY(cudaStreamSynchronize(st));
     }
     split_rows(Ltr, NM, nch, NM, s->Ltp_h, s->Ltp_l, s->Ltp_s, st);   // force-bias-only operand
@@ -1024,6 +1047,9 @@ int tc_sync_walkers_to_fp64(afqmc_walkers* wk, cudaStream_t st) {
 //   tc_measure_pre:  S^-1 of the current walkers -> Theta^T (exact-mode GEMM) and its split;
 //   the contraction: tc_energy (measuring) or the force-bias-only GEMM;
 //   tc_measure_post: one-body energy, local energy and force bias.
+// whether the walker set's energy contractions form single-product tiles
+bool single_tiles(const afqmc_walkers* wk) { return wk->opts.energy_terms == 0 && wk->tc && wk->tc->n_single > 0; }
+
 int tc_measure_pre(afqmc_walkers* wk, cudaStream_t st) {
     TcState* s = wk->tc;
     const int N = s->N, M = s->M, W = s->W, WS = 2 * W;
@@ -1045,16 +1071,18 @@ int tc_measure_pre(afqmc_walkers* wk, cudaStream_t st) {
         AFQMC_TRY(tc_gemm(smat(s->SD_h, s->SD_l, 2 * N, 2 * N, WS, s->SD_s), BatchMap{1, WS},
                           smat(s->Phi_h, s->Phi_l, 2 * N, M, WS, s->Phi_s), BatchMap{1, WS}, 2 * N, M, 2 * N, WS, e,
                           128, true, wk->flags, st));
-        split_rows(s->ThT_f, M, (int64_t)WS * 2 * N, M, s->ThT_h, s->ThT_l, s->ThT_s, st);
+        split_rows(s->ThT_f, M, (int64_t)WS * 2 * N, M, s->ThT_h, s->ThT_l, s->ThT_s, st,
+                   single_tiles(wk) ? s->ThT_r : nullptr);
     }
     return AFQMC_OK;
 }
 
 namespace {
-// energy_terms: 0 = rounded three products (default), 1 = adaptive four/three, 3, 4
+// energy_terms: 0 = rounded three products with single-product tail tiles (default), 2 = rounded
+// three products throughout, 1 = adaptive four/three, 3, 4
 int energy_terms_of(const afqmc_walkers* wk) {
     const int et = wk->opts.energy_terms;
-    return et == 0 ? kEnergyRounded : (et == 1 ? kEnergyFour : et);
+    return (et == 0 || et == 2) ? kEnergyRounded : (et == 1 ? kEnergyFour : et);
 }
 }  // namespace
 
@@ -1065,7 +1093,7 @@ int tc_energy_system(afqmc_walkers* wk, int BK, EnergySys* out) {
     return tc_energy_describe(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N, 1, s->Lt_s),
                               smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N, 1, s->ThT_s), N, nch, WS, M, s->tE,
                               s->XE, energy_terms_of(wk), wk->opts.energy_terms == 1 ? s->lolo : nullptr, s->Lt_r, BK,
-                              out);
+                              out, single_tiles(wk) ? s->single : nullptr, s->ThT_r);
 }
 
 int tc_measure_post(afqmc_walkers* wk, bool measure, cudaStream_t st) {
@@ -1092,7 +1120,7 @@ int tc_measure(afqmc_walkers* wk, bool measure, cudaStream_t st) {
         AFQMC_TRY(tc_energy(smat(s->Lt_h, s->Lt_l, M, (int64_t)nch * N, 1, s->Lt_s),
                             smat(s->ThT_h, s->ThT_l, M, (int64_t)WS * 2 * N, 1, s->ThT_s), N, nch, WS, M, s->tE,
                             s->XE, energy_terms_of(wk), wk->opts.energy_terms == 1 ? s->lolo : nullptr, s->Lt_r,
-                            wk->flags, st));
+                            wk->flags, st, single_tiles(wk) ? s->single : nullptr, s->ThT_r));
     } else {
         // force bias only: t[ws][n] = sum_{a,k} ThetaT[ws][a][k] Ltilde[n][a][k], one exact-mode GEMM
         // with K = N*M over rows (ws, re/im) of Theta^T (row-scaled pair in the Pacc scratch)
@@ -1232,7 +1260,9 @@ int tc_energy_products(afqmc_walkers* wk, double* mean) {
     TcState* s = wk->tc;
     if (!s) return fail(AFQMC_ERR_BADARG, "energy_products: not a BF16X3 walker set");
     const int t = wk->opts.energy_terms;
-    *mean = t == 1 ? 3.0 + s->lolo_frac : (t == 0 ? 3.0 : (double)t);
+    // single-product tiles exist only in the CTA-pair form (the default)
+    const double one = launch_policy().energy_pair != 0 && single_tiles(wk) ? s->single_frac : 0.0;
+    *mean = t == 1 ? 3.0 + s->lolo_frac : (t == 0 ? 3.0 - 2.0 * one : (t == 2 ? 3.0 : (double)t));
     return AFQMC_OK;
 }
 

@@ -50,6 +50,41 @@ def test_energy_at_start_matches_fp64(M, N, nch, W):
     assert np.max(np.abs(Eb - Eo)) < MHA
 
 
+def test_single_product_tail_matches_rounded_three():
+    """The default energy products (rounded three, with single-product tiles for the Cholesky
+    vectors whose squared norms make up at most 2^-15 of the total) against the rounded three on
+    every tile, on the same walkers of the molecule-like M = 128 shape, where the tail is most of
+    the tiles: the mean product count drops below 2, and the local energies and force-bias-driven
+    log-overlaps agree far inside the 1 mHa bar."""
+    import ctypes
+    M, N, nch, W = 128, 32, 640, 16
+    h, L, E0, Psi = system(M, N, nch, 11)
+    rng = np.random.default_rng(5)
+    amp = 0.8 / np.sqrt(M)
+    Phi0 = [np.linalg.qr(Psi[s][None] + amp * (rng.standard_normal((W, M, N))
+                                                 + 1j * rng.standard_normal((W, M, N))))[0] for s in range(2)]
+    lib = api.lib()
+    lib.afqmc_debug_energy_products.restype = ctypes.c_int
+    lib.afqmc_debug_energy_products.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    x = syn.make_fields(3, W, nch, seed=4)
+    out = {}
+    for terms in (0, 2):
+        with AFQMC(h, L, E0, Psi[0], Psi[1], W, 0.005, Phi0=Phi0, k_qr=5, precision=api.PREC_BF16X3,
+                   energy_terms=terms) as g:
+            mean = ctypes.c_double(0.0)
+            assert lib.afqmc_debug_energy_products(g.wk, ctypes.addressof(mean)) == 0
+            E0_L = g.energy()[0]
+            tr = g.step(3, x, measure_every=1)
+            out[terms] = (mean.value, E0_L, tr, g.energy())
+    print("mean products:", out[0][0], out[2][0])
+    assert out[2][0] == 3.0 and 1.0 <= out[0][0] < 2.0
+    dE = np.max(np.abs(out[0][1] - out[2][1]))
+    dmix = np.max(np.abs(out[0][2] - out[2][2]))
+    dlog = np.max(np.abs(out[0][3][2].real - out[2][3][2].real))
+    print(f"single tail vs rounded three: E_L {dE:.2e} Ha, E_mix over 3 steps {dmix:.2e} Ha, log-overlap {dlog:.2e}")
+    assert dE < 2e-5 and dmix < 5e-5 and dlog < 1e-5
+
+
 @pytest.mark.parametrize("M,N,nch,W,steps,me", [(128, 32, 640, 32, 12, 1), (128, 64, 256, 8, 8, 3),
                                                  (256, 128, 512, 4, 6, 1), (128, 24, 320, 12, 8, 1)])
 def test_trajectory_matches_fp64_within_1mha(M, N, nch, W, steps, me):

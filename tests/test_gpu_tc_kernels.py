@@ -193,6 +193,54 @@ def test_energy_traces_match_reference(dbg, Np, Nchol, nws, M, terms, pair):
     assert np.max(np.abs(X - X_ref)) < 2e-6 * np.max(np.abs(X_ref)) + 1e-9
 
 
+@pytest.mark.parametrize("terms", [6, 7])
+@pytest.mark.parametrize("Np,Nchol,nws,M", [(128, 9, 3, 512), (128, 41, 9, 256), (64, 13, 5, 192), (32, 37, 4, 128),
+                                            (40, 23, 5, 192), (8, 37, 21, 64)])
+def test_single_product_tiles_match_emulation(dbg, Np, Nchol, nws, M, terms):
+    """Single-product tiles of the CTA-pair kernel (r*r': both operands rounded to fp16 after row
+    scaling, one MMA per K slice into the first accumulator, two K chunks per operand stage), on
+    every tile (terms 7) and alternating pair by pair with rounded-three tiles in one persistent
+    launch (terms 6: stages of both kinds pass through one ring, and the epilogue leaves out the
+    second accumulator only on the single tiles), against their float64 emulation.  The kernel
+    must match the single-product emulation far better than the rounded-three one on those
+    tiles, and the rounded-three emulation on the others."""
+    rng = np.random.default_rng(Np * 11 + Nchol + terms)
+    Lt = rng.standard_normal((Nchol, Np, M)) * 0.1
+    Th = rng.standard_normal((nws, 2, Np, M)) * 0.1
+    t, X = energy_call(dbg, Lt, Th, Np, Nchol, nws, M, terms, 1)
+    G = 128 // Np
+    single = np.array([terms == 7 or ((n // G) // 2) % 2 == 1 for n in range(Nchol)])
+    mm = lambda a, b: np.matmul(a, np.swapaxes(b, -1, -2))
+    Ar = split_rows(Lt, rounded=True)[2]
+    T1, T3 = [], []
+    for w in range(nws):
+        parts1, parts3 = [], []
+        for c in range(2):
+            B = np.broadcast_to(Th[w, c], (Nchol, Np, M))
+            parts1.append(mm(Ar, split_rows(Th[w, c], rounded=True)[2][None]))
+            parts3.append(emul(Lt, B, exact=True, rounded=True))
+        T1.append(parts1[0] + 1j * parts1[1])
+        T3.append(parts3[0] + 1j * parts3[1])
+    T1, T3 = np.stack(T1), np.stack(T3)                 # [nws, Nchol, Np, Np]
+
+    def traces(T):
+        return np.trace(T, axis1=2, axis2=3), np.einsum("wnab,wnba->wn", T, T)
+
+    t1, X1 = traces(T1)
+    t3, X3 = traces(T3)
+    sel = single[None, :]
+    t_ref, X_ref = np.where(sel, t1, t3), np.where(sel, X1, X3)
+    st, sx = np.max(np.abs(t_ref)), np.max(np.abs(X_ref))
+    e1 = max(np.max(np.abs((t - t1)[:, single])) / st, np.max(np.abs((X - X1)[:, single])) / sx)
+    gap = max(np.max(np.abs((t1 - t3)[:, single])) / st, np.max(np.abs((X1 - X3)[:, single])) / sx)
+    print(f"single tiles Np={Np} terms={terms}: err vs r*r' {e1:.2e}, r*r' vs rounded three {gap:.2e}")
+    assert e1 < 5e-5 and e1 < 0.2 * gap
+    if not single.all():
+        e3 = max(np.max(np.abs((t - t3)[:, ~single])) / st, np.max(np.abs((X - X3)[:, ~single])) / sx)
+        print(f"   rounded-three tiles: err {e3:.2e}")
+        assert e3 < 2e-6
+
+
 @pytest.mark.parametrize("M,N,nch,W", [(128, 32, 96, 3), (256, 128, 64, 2)])
 def test_mixed_intermediates_match_numpy(dbg, M, N, nch, W):
     """Theta^T, the traces and the one-body energy of a BF16X3 walker set against numpy."""
