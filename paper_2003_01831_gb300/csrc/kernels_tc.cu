@@ -760,30 +760,34 @@ __device__ __forceinline__ bool energy_epilogue_tile(const EnergyShape& es, Shar
         v2 += __shfl_xor_sync(0xffffffffu, v2, o);
         v3 += __shfl_xor_sync(0xffffffffu, v3, o);
     }
-    if (lane < 16) {   // ered[h][q][jj][v] for every walker-spin slot (zeros but j)
+    // partial sums in fp32: the final reduction runs on one thread per output, and a chain of
+    // FP64 adds there (GB300's FP64 pipe is 1/64 of the fp32 one) cost a third of a
+    // single-product tile's epilogue
+    float* eredf = reinterpret_cast<float*>(ered);
+    if (lane < 16) {   // eredf[h][q][jj][v] for every walker-spin slot (zeros but j)
         const int jj = lane >> 2, v = lane & 3;
         const float val = jj != j ? 0.f : (v == 0 ? v0 : (v == 1 ? v1 : (v == 2 ? v2 : v3)));
-        ered[((h * 4 + q) * 4 + jj) * 4 + v] = val;
+        eredf[((h * 4 + q) * 4 + jj) * 4 + v] = val;
     }
     ebar();
     // one thread per (n-block, walker-spin) output: sum over the n-block's quadrants and
-    // the four column quarters
+    // the four column quarters, in a fixed order
     if (et < G * G) {
         const int ib = et / G, jo = et % G;
-        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
         for (int hh = 0; hh < 4; ++hh)
             for (int qq = ib * Q; qq < (ib + 1) * Q; ++qq) {
-                const double* e = ered + ((hh * 4 + qq) * 4 + jo) * 4;
-                s0 += e[0];
-                s1 += e[1];
-                s2 += e[2];
-                s3 += e[3];
+                const float4 e = *reinterpret_cast<const float4*>(eredf + ((hh * 4 + qq) * 4 + jo) * 4);
+                s0 += e.x;
+                s1 += e.y;
+                s2 += e.z;
+                s3 += e.w;
             }
         const int n = ng * G + ib;
         const int ws = wg * G + jo;
         if (n < es.Nchol && ws < es.nws) {
-            es.t_out[(int64_t)ws * es.Nchol + n] = cplx{s0, s1};
-            es.X_out[(int64_t)ws * es.Nchol + n] = cplx{s2, s3};
+            es.t_out[(int64_t)ws * es.Nchol + n] = cplx{(double)s0, (double)s1};
+            es.X_out[(int64_t)ws * es.Nchol + n] = cplx{(double)s2, (double)s3};
         }
     }
     ebar();   // ered, colscale and the plane are read before the next tile rewrites them
@@ -998,7 +1002,7 @@ __global__ void __launch_bounds__(kEThreads, 1)
     uint8_t* sbase = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     using C = EStage<BK, AP, 256>;
     float* plane = reinterpret_cast<float*>(sbase + C::kStages * C::kStageBytes);
-    // 256 column scales of the tile; partial traces ered[((h * 4 + q) * 4 + j) * 4 + v]
+    // 256 column scales of the tile; partial traces (fp32) at ered: [((h * 4 + q) * 4 + j) * 4 + v]
     float* colscale = plane + kETileFloats;       // 128 x 129 floats: 16-byte aligned
     double* ered = reinterpret_cast<double*>(colscale + 256);
     SharedCtl* ctl = reinterpret_cast<SharedCtl*>(ered + 256);
