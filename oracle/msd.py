@@ -38,10 +38,19 @@ Readings of what the paper leaves open (also listed in the design notes):
     excited determinants' terms ill-conditioned; their Sherman-Morrison evaluation relative to
     the reference is not restated here.
 
+The variational energy itself, orthogonal pairs included, is variational_energy(): the matrix
+elements <D_I|H|D_J> between any two determinants by Loewdin's rules for biorthogonalised
+orbitals (below), which need no inverse of the overlap, so exactly orthogonal pairs (determinants
+that differ in one, two or more orbitals) are covered.  The walker step uses energy_shift() as
+E_T, which is what the GPU path forms; the two agree unless two determinants are exactly
+orthogonal.
+
 Pins (tests/test_oracle_msd.py): overlap, local energy, force bias and energy shift (the variational energy of a NOMSD expansion)
 against Fock-space vectors sum_I c_I |D_I>; one determinant, a repeated determinant and a
 re-gauged expansion (D_I -> D_I R_I, c_I -> c_I / det R_I, the same state) against the single-determinant
-results; a short phaseless run.
+results; a short phaseless run; <D_I|H|D_J> against Fock-space matrix elements for pairs whose
+overlap matrix has rank deficiency 0 to 3, and the variational energy of the exact two-electron
+ground state written as M^2 orthogonal determinants against the FCI energy.
 """
 from __future__ import annotations
 
@@ -51,7 +60,80 @@ import numpy as np
 
 from . import afqmc as O
 
-__all__ = ["MSDTrial"]
+__all__ = ["MSDTrial", "determinant_matrix_elements"]
+
+
+def _spin_orbitals(D: Tuple[np.ndarray, np.ndarray]) -> np.ndarray:
+    """The determinant as one [2M, Nup + Ndn] spin-orbital matrix: spin-up orbitals in rows
+    0..M-1 and columns 0..Nup-1, spin-down ones in rows M..2M-1 (the Fock-space ordering)."""
+    up, dn = D
+    M = up.shape[0]
+    out = np.zeros((2 * M, up.shape[1] + dn.shape[1]), dtype=np.complex128)
+    out[:M, :up.shape[1]] = up
+    out[M:, up.shape[1]:] = dn
+    return out
+
+
+def determinant_matrix_elements(ham: O.Hamiltonian, A: Tuple[np.ndarray, np.ndarray],
+                                B: Tuple[np.ndarray, np.ndarray]) -> Tuple[complex, complex]:
+    """(<A|B>, <A|H|B>) for two Slater determinants (Loewdin's rules).
+
+    Per spin, the singular value decomposition A_s^+ B_s = U_s diag(sigma) V_s^+ gives orbitals
+    a = A U and b = B V with a_k^+ b_l = sigma_k delta_kl; the rotated determinants are
+    |a> = det(U)|A> and |b> = det(V)|B>.  Between such biorthogonal determinants, with
+    P_k = prod_{m != k} sigma_m and P_kl = prod_{m != k, l} sigma_m (k != l),
+
+      <a|b>   = prod_k sigma_k,
+      <a|h|b> = sum_k P_k a_k^+ h b_k,
+      <a|V|b> = 1/2 sum_{k != l} P_kl sum_n [X_n[k,k] Y_n[l,l] - X_n[k,l] Y_n[l,k]],
+
+    with X_n[k,r] = a_k^+ L_n b_r and Y_n[l,s] = a_l^+ L_n^+ b_s (spin-conserving, so an up
+    orbital meets a down one with zero), since v_ijkl = sum_n L^n_ik conj(L^n_lj) (Eq. (3)) makes
+    the two-electron integral <a_k a_l|v|b_r b_s> = sum_n X_n[k,r] Y_n[l,s].  No sigma is inverted,
+    so a singular overlap (orthogonal determinants) needs no special case."""
+    a_list, b_list, sig = [], [], []
+    phase = 1.0 + 0j
+    for s in range(2):
+        S = A[s].conj().T @ B[s]
+        U, sv, Vh = np.linalg.svd(S)
+        V = Vh.conj().T
+        a_list.append(A[s] @ U)
+        b_list.append(B[s] @ V)
+        sig.append(sv)
+        phase *= np.conj(np.linalg.det(U)) * np.linalg.det(V)
+    a = _spin_orbitals((a_list[0], a_list[1]))
+    b = _spin_orbitals((b_list[0], b_list[1]))
+    sigma = np.concatenate(sig).astype(np.complex128)
+    n = sigma.size
+    M = ham.M
+
+    def so(Op):   # spin-conserving one-body operator on spin orbitals
+        out = np.zeros((2 * M, 2 * M), dtype=np.complex128)
+        out[:M, :M] = Op
+        out[M:, M:] = Op
+        return out
+
+    def prod_except(skip):
+        p = 1.0 + 0j
+        for m in range(n):
+            if m not in skip:
+                p *= sigma[m]
+        return p
+
+    ovl = prod_except(())
+    h1 = so(ham.h)
+    e1 = sum(prod_except((k,)) * (a[:, k].conj() @ h1 @ b[:, k]) for k in range(n))
+    e2 = 0.0 + 0j
+    for nv in range(ham.Nchol):
+        Ln = so(ham.L[nv])
+        X = a.conj().T @ Ln @ b
+        Y = a.conj().T @ Ln.conj().T @ b
+        for k in range(n):
+            for l in range(n):
+                if k != l:
+                    e2 += 0.5 * prod_except((k, l)) * (X[k, k] * Y[l, l] - X[k, l] * Y[l, k])
+    H_ab = ham.E0 * ovl + e1 + e2
+    return ovl / phase, H_ab / phase
 
 
 def _logsumexp(l: np.ndarray, axis: int) -> np.ndarray:
@@ -106,6 +188,21 @@ class MSDTrial:
             E = E + u[:, I] * E_I
             t = t + u[:, I][:, None] * t_I
         return E, t
+
+    def variational_energy(self, ham: O.Hamiltonian) -> complex:
+        """<psi_T|H|psi_T> / <psi_T|psi_T> from the matrix elements between every pair of
+        determinants (determinant_matrix_elements), orthogonal pairs included."""
+        num = 0.0
+        den = 0.0
+        for I, DI in enumerate(self.dets):
+            for J, DJ in enumerate(self.dets):
+                w = np.conj(self.c[I]) * self.c[J]
+                if w == 0:
+                    continue
+                S_IJ, H_IJ = determinant_matrix_elements(ham, DI, DJ)
+                num += w * H_IJ
+                den += w * S_IJ
+        return num / den
 
     def energy_shift(self, ham: O.Hamiltonian) -> complex:
         """E_T through the overlaps S_IJ = <D_I|D_J> over the pairs with S_IJ != 0: the

@@ -584,7 +584,8 @@ static int init_walkers_impl(afqmc_ham_t ham, int ND, const double* Psi_up, cons
                                     reinterpret_cast<cplx*>(f.Bh), st)
                      : expm_real(ham->hp, -0.5 * tau, M, f.Bh, st);
     if (rc) return bail(rc);
-    // trial energy E_T: the trial's variational energy.  One determinant: its local energy with
+    // trial energy E_T: the trial's energy shift (its variational energy unless two determinants
+    // of an expansion are exactly orthogonal; those pairs are left out).  One determinant: its local energy with
     // walker 0 placed at it.  ND determinants: with walker 0 at each D_J in turn, the local
     // energies E_IJ and log-overlaps log S_IJ of every D_I, then
     // sum_IJ conj(c_I) c_J S_IJ E_IJ / sum_IJ conj(c_I) c_J S_IJ.

@@ -12,7 +12,7 @@ import numpy as np
 
 from oracle import afqmc as O
 from oracle.fock import FockSpace, four_index_from_cholesky
-from oracle.msd import MSDTrial
+from oracle.msd import MSDTrial, determinant_matrix_elements
 from paper_2003_01831_gb300 import synthetic as syn
 
 
@@ -52,7 +52,39 @@ def test_mixed_estimates_against_fock_space():
             assert abs(t[w, n] - tref) < 1e-11 * max(1.0, abs(tref)), (w, n)
     Ev = np.vdot(vp, H @ vp) / np.vdot(vp, vp)
     assert abs(trial.energy_shift(ham) - Ev) < 1e-11 * abs(Ev)
+    assert abs(trial.variational_energy(ham) - Ev) < 1e-11 * abs(Ev)
     assert abs(Ev.imag) < 1e-12 * abs(Ev)
+
+
+def test_determinant_matrix_elements_against_fock_space():
+    """<A|B> and <A|H|B> by Loewdin's rules against Fock-space vectors, for generic pairs and for
+    pairs whose overlap matrix loses rank 1, 2 (same spin and opposite spins) and 3 (zero by
+    the two-body rank of H), each occupied space also mixed by a random invertible matrix so
+    the singular values and rotations are not trivial.  Dropping the exchange term or a spin
+    block of the integrals fails the rank-2 cases."""
+    rng = np.random.default_rng(31)
+    M, nch = 5, 4
+    h, L, _ = syn.make_hamiltonian(M, nch, rng)
+    ham = O.Hamiltonian(h=h, L=L, E0=0.4)
+    fs = FockSpace(M, 2, 2)
+    H = fs.hamiltonian(h, four_index_from_cholesky(L), ham.E0)
+    I = np.eye(M)
+    pairs = [((crandn(rng, M, 2), crandn(rng, M, 2)), (crandn(rng, M, 2), crandn(rng, M, 2)))]
+    for ua, da, ub, db in [([0, 1], [0, 1], [0, 1], [0, 1]),     # same determinant
+                           ([0, 1], [0, 1], [0, 2], [0, 1]),     # single excitation
+                           ([0, 1], [0, 1], [2, 3], [0, 1]),     # same-spin double
+                           ([0, 1], [0, 1], [0, 2], [1, 3]),     # opposite-spin double
+                           ([0, 1], [0, 1], [2, 3], [2, 4]),     # quadruple: zero
+                           ([0, 1], [0, 1], [2, 3], [0, 4])]:    # triple: zero
+        R = [crandn(rng, 2, 2) for _ in range(4)]
+        pairs.append(((I[:, ua] @ R[0], I[:, da] @ R[1]), (I[:, ub] @ R[2], I[:, db] @ R[3])))
+    for A, B in pairs:
+        S, HAB = determinant_matrix_elements(ham, A, B)
+        va, vb = fs.slater_vector(*A), fs.slater_vector(*B)
+        Sref, Href = np.vdot(va, vb), np.vdot(va, H @ vb)
+        scale = np.linalg.norm(va) * np.linalg.norm(vb)
+        assert abs(S - Sref) < 1e-12 * scale
+        assert abs(HAB - Href) < 1e-12 * scale * np.linalg.norm(H, 2)
 
 
 def test_one_and_repeated_determinants_reduce_to_the_single_determinant():
@@ -116,8 +148,8 @@ def test_exact_ground_state_expansion_has_zero_variance_local_energy():
     the mixed local energy equals E_FCI at any walker (generic walkers overlap every
     determinant); the force-bias traces equal the Fock-space mixed estimates of every L_n.
     The energy shift E_T skips the exactly orthogonal pairs of such an expansion (the oracle's
-    stated reading: it is a shift there, not the variational energy), so only its diagonal part
-    is checked here."""
+    stated reading: it is a shift there, not the variational energy), so it equals the
+    diagonal part; the variational energy, from every pair's matrix element, is E_FCI."""
     rng = np.random.default_rng(12)
     M, nch = 4, 5
     h, L, _ = syn.make_hamiltonian(M, nch, rng)
@@ -139,6 +171,7 @@ def test_exact_ground_state_expansion_has_zero_variance_local_energy():
     assert np.max(np.abs(E - e[0])) < 1e-10 * abs(e[0])
     diag = sum(abs(cI) ** 2 * np.vdot(fs.slater_vector(*D), H @ fs.slater_vector(*D)) for cI, D in zip(c, dets))
     assert abs(trial.energy_shift(ham) - diag / np.sum(np.abs(c) ** 2)) < 1e-12 * abs(e[0])
+    assert abs(trial.variational_energy(ham) - e[0]) < 1e-10 * abs(e[0])
     vp = V[:, 0]
     for w in range(5):
         vf = fs.slater_vector(Phi[0][w], Phi[1][w])
