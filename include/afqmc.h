@@ -87,7 +87,8 @@ typedef struct afqmc_opts {
                                 vectors, whose squared norms ||Ltilde_n||_F^2 add up
                                 to at most 2^-15 of the total: their tiles form the
                                 one product r*r', r' = fp16(y) of Theta (relative
-                                error ~2^-11 on a share ~2^-15 of the energy);
+                                error ~2^-11 on a share ~2^-15 of the energy; the
+                                CTA-pair kernel, the default form, does this);
                             3 = hi*hi + hi*lo + lo*hi;
                             4 = + lo*lo for every Cholesky vector;
                             1 = adaptive: four products except for the smallest
